@@ -1,0 +1,333 @@
+"""Benchmark: reduced-Hessian CG to relative residual 1e-8 on one GB300.
+
+Workload: the 1025^2 L-shaped P1 triangle mesh (784,385 states, 788,481
+controls), 8x8 checkerboard kappa in {1, 1e4}, beta = 1e-4, 8 Gaussian-bump
+desired state (seeded synthetic data).  One step = the whole hot path on that
+input: device assembly, AMG setup of both hierarchies, right-hand side, outer
+CG with the multilevel Hessian preconditioner to ||r||/||b|| <= 1e-8, and the
+recomputed true residual.  Metric: fine-level Hessian applications per
+second of step time (whole job over all ranks); the time to 1e-8 is
+reported beside it.  Both precision forms are timed: FP32 V-cycles with FP64
+refinement ("mixed", the headline) and plain FP64.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl amgh|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Hessian-CG time-to-1e-8 and Hessian matvecs/s, mixed vs FP64, same GB300"
+UNIT = "Hessian-matvecs/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="amgh", choices=["amgh", "reference"])
+    ap.add_argument("--N", type=int, default=1025, help="L-shape grid size (bench workload: 1025)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--forms", default="mixed,fp64")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms while running."""
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+
+    def __enter__(self):
+        os.makedirs(os.path.dirname(self.path), exist_ok=True)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return None
+
+
+# ------------------------------------------------------------------------- amgh arm
+def run_amgh(args, rank, world, local):
+    import torch
+
+    from paper_2001_11533_gb300 import _build, amgh, workloads
+    _build.build()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    w = workloads.lshape_checkerboard(N=args.N)
+    host = [np.ascontiguousarray(w.coords, np.float64), np.ascontiguousarray(w.elements, np.int32),
+            np.ascontiguousarray(w.dirichlet, np.uint8), np.ascontiguousarray(w.kappa, np.float64),
+            np.ascontiguousarray(w.y_d, np.float64)]
+    dev = [torch.from_numpy(a).cuda() for a in host]
+    pinned = [torch.from_numpy(a).pin_memory() for a in host]
+    pinned_np = [t.numpy() for t in pinned]
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # 256 MB > 129 MB L2
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    def step(precision, e2e=False, timing=False):
+        if e2e:
+            prob = amgh.Problem(w.dim, *pinned_np[:4], w.beta, pinned_np[4], on_device=False)
+        else:
+            prob = amgh.Problem(w.dim, dev[0], dev[1], dev[2], dev[3], w.beta, dev[4], on_device=True)
+        prob.amg_setup(precision=precision)
+        if timing:
+            prob.kernel_timing(True)
+        if e2e:
+            u, y, info = prob.solve_host(tol=1e-8)
+        else:
+            u, y, info = prob.solve(tol=1e-8)
+        ks = prob.kernel_stats() if timing else None
+        sizes = prob.sizes
+        prob.close()
+        return info, ks, sizes
+
+    results = {}
+    forms = [f for f in args.forms.split(",") if f]
+    for form in forms:
+        precision = 1 if form == "mixed" else 0
+        for _ in range(args.warmup):
+            step(precision)
+        torch.cuda.synchronize()
+        barrier()
+        torch.cuda.synchronize()
+        times, happ, infos = [], 0, []
+        kstats = {"launches": 0, "ms": 0.0, "bytes": 0.0}
+        launches0 = amgh.launch_count()
+        with ClockSampler(local) as clk:
+            for k in range(args.steps):
+                flush.zero_()
+                ev0 = torch.cuda.Event(enable_timing=True)
+                ev1 = torch.cuda.Event(enable_timing=True)
+                ev0.record(stream)
+                info, ks, sizes = step(precision, timing=True)
+                ev1.record(stream)
+                ev1.synchronize()
+                times.append(ev0.elapsed_time(ev1))
+                happ += info["hessian_applies"]
+                infos.append(info)
+                for key in kstats:
+                    kstats[key] += ks[key]
+        torch.cuda.synchronize()
+        barrier()
+        launches = amgh.launch_count() - launches0
+        t_total = sum(times) / 1000.0
+        # max over ranks of the timed total, sum of work
+        if world > 1:
+            import torch.distributed as dist
+            tt = torch.tensor([t_total], device="cuda")
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            hh = torch.tensor([float(happ)], device="cuda")
+            dist.all_reduce(hh, op=dist.ReduceOp.SUM)
+            t_total, happ_all = float(tt.item()), float(hh.item())
+        else:
+            happ_all = float(happ)
+        results[form] = {
+            "value": happ_all / t_total,
+            "ms_per_step": 1000.0 * t_total / args.steps,
+            "hessian_applies_per_step": happ / args.steps,
+            "outer_iters": infos[-1]["outer_iters"],
+            "final_relres": infos[-1]["final_relres"],
+            "inner_iters_per_step": infos[-1]["inner_iters"],
+            "setup_s": infos[-1]["t_setup_s"],
+            "solve_s": infos[-1]["t_solve_s"],
+            "refinements": infos[-1]["refinements"],
+            "gpu_launches": launches,
+            "kstats": kstats,
+            "clocks": clk.summary(),
+            "levels": {"state": sizes["state"], "control": sizes["control"], "ell": sizes["ell"]},
+        }
+    # end-to-end through the host-buffer entry points (H2D of the inputs, D2H of u and y)
+    head = forms[0]
+    precision = 1 if head == "mixed" else 0
+    step(precision, e2e=True)
+    torch.cuda.synchronize()
+    barrier()
+    t0 = time.perf_counter()
+    e_happ = 0
+    for k in range(max(1, min(args.steps, 3))):
+        info, _, sizes = step(precision, e2e=True)
+        e_happ += info["hessian_applies"]
+    torch.cuda.synchronize()
+    e2e_t = time.perf_counter() - t0
+    h2d = sum(a.nbytes for a in host)
+    d2h = 8 * (sizes["n"] + sizes["m"])
+    e2e = {"value": e_happ / e2e_t, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+    return w, results, e2e
+
+
+def roofline_from(res):
+    ks = res["kstats"]
+    peaks = measured_peaks()
+    if peaks and peaks.get("hbm_gbs"):
+        peak, src = float(peaks["hbm_gbs"]), "measured"
+    else:
+        peak, src = 6800.0, "fallback"
+    if ks["launches"] == 0 or ks["ms"] <= 0:
+        return None
+    achieved = ks["bytes"] / (ks["ms"] / 1000.0) / 1e9
+    return {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+            "frac": round(achieved / peak, 4), "traffic": None, "peak_source": src,
+            "kernel": "fine-level SELL-32 SpMV-class kernels (smoother step, residual, CG p.Ap)",
+            "launches": ks["launches"], "avg_us": round(1000.0 * ks["ms"] / ks["launches"], 2)}
+
+
+# ------------------------------------------------------------------------- oracle (CPU)
+def oracle_apply_rate(w, budget_s, applies=None):
+    """Time the FP64 oracle's Hessian apply on the host (setup untimed)."""
+    from oracle.oracle import Oracle
+    orc = Oracle(w)
+    u = np.random.default_rng(0).standard_normal(w.n_vertices)
+    n, t = 0, 0.0
+    while (applies is None and (t < budget_s or n == 0)) or (applies is not None and n < applies):
+        t0 = time.perf_counter()
+        orc.hessian(u)
+        t += time.perf_counter() - t0
+        n += 1
+    return n, t
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    from oracle import oracle as orc_mod
+    from paper_2001_11533_gb300 import workloads
+    orc_mod.build()
+    w = workloads.lshape_checkerboard(N=args.N)
+    from oracle.oracle import Oracle
+    orc = Oracle(w)
+    u = np.random.default_rng(0).standard_normal(w.n_vertices)
+    for _ in range(min(args.warmup, 1)):
+        orc.hessian(u)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        orc.hessian(u)
+        times.append(time.perf_counter() - t0)
+    tot = sum(times)
+    value = args.steps / tot
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": min(args.warmup, 1), "ms_per_step": 1000.0 * tot / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": f"lshape{args.N}_checkerboard", "m": w.n_interior, "n": w.n_vertices,
+                       "beta": w.beta, "step": "one fine-level Hessian apply of the FP64 CPU oracle"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{args.steps} Hessian applies (2 AMG-CG solves to 1e-10 each)"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------------- main
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    w, results, e2e = run_amgh(args, rank, world, local)
+    if rank != 0:
+        return
+    forms = list(results)
+    head = results[forms[0]]
+    line = {
+        "metric": METRIC, "value": head["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32+f64" if forms[0] == "mixed" else "f64",
+        "data": "synthetic",
+        "config": {"workload": f"lshape{args.N}_checkerboard", "m": w.n_interior, "n": w.n_vertices,
+                   "beta": w.beta, "kappa": "8x8 checkerboard {1,1e4}", "tol": 1e-8,
+                   "precision": forms[0], "parallelism": "replicas" if world > 1 else "single",
+                   "l2": "256 MB buffer written between timed steps",
+                   "step": "assembly + AMG setup + rhs + outer CG to 1e-8 + true residual"},
+        "time_to_1e-8_s": head["ms_per_step"] / 1000.0,
+        "gpu_launches": head["gpu_launches"],
+        "clocks": head["clocks"],
+        "roofline": roofline_from(head),
+        "e2e": e2e,
+        "forms": {f: {k: v for k, v in r.items() if k not in ("kstats", "clocks")} for f, r in results.items()},
+    }
+    if "mixed" in results and "fp64" in results:
+        line["speedup_mixed_vs_fp64"] = results["mixed"]["value"] / results["fp64"]["value"]
+    if world == 1 and not args.no_cpu_baseline:
+        n, t = oracle_apply_rate(w, budget_s=15.0)
+        line["cpu_baseline"] = {"value": n / t, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": f"{n} Hessian applies of the FP64 oracle on the same workload "
+                                          f"({t:.1f} s, setup untimed)"}
+    print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,256 @@
+/*
+ * amgh.h -- C ABI of the GB300 (sm_103a) implementation of AMG preconditioning
+ * of the reduced Hessian for linear-quadratic elliptic optimal control
+ * (Barker & Draganescu, "Algebraic multigrid preconditioning of the Hessian in
+ * PDE-constrained optimization").
+ *
+ * The problem (Sec. 2, Eq. functional/state): minimise
+ *     J(y,u) = 1/2 (y - y_d)^T M_y (y - y_d) + beta/2 u^T M_u u
+ * subject to A y = M_yu u, with P1 finite elements on triangles (dim 2) or
+ * tetrahedra (dim 3).  State dofs y are the non-Dirichlet vertices in
+ * ascending vertex order (m of them); control dofs u are all vertices (n).
+ * The library solves the M_u-scaled first-order system (Sec. 5.2, Eq.
+ * firstorderpractice)
+ *     H u = b,   H = M_yu^T A^-1 M_y A^-1 M_yu + beta M_u,   b = M_yu^T A^-1 M_y y_d,
+ * by conjugate gradients preconditioned with the multilevel Hessian
+ * preconditioner built from the AMG prolongators (Sec. 3, Algorithm MLAS).
+ *
+ * Conventions for every call:
+ *   - Return value: AMGH_OK (0) or a negative AMGH_ERR_* code; nothing aborts
+ *     or throws across this boundary.  amgh_status_string() names a code.
+ *   - Vectors named *_dev are caller-owned device pointers (e.g. a torch
+ *     tensor's data_ptr()) on the current CUDA device, valid for the problem's
+ *     stream (amgh_set_stream); the library never frees them.  Vectors named
+ *     *_host are caller-owned host pointers.  Lengths: control vectors n,
+ *     state vectors m (both from amgh_query_sizes); blocks of ncols columns
+ *     are column-major (column c starts at c*n or c*m).
+ *   - The library copies mesh, kappa and y_d into its own device memory at
+ *     amgh_problem_create; caller buffers may be freed afterwards.
+ *   - Calls enqueue work on the problem's stream and return after it has
+ *     completed (they synchronise that stream), unless stated otherwise.
+ *   - A problem is not thread-safe; distinct problems on distinct streams are.
+ */
+#ifndef AMGH_H
+#define AMGH_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define AMGH_OK 0
+#define AMGH_ERR_INVALID_ARG (-1)   /* bad pointer, size, option or mesh */
+#define AMGH_ERR_NOT_SETUP (-2)     /* amgh_amg_setup has not run */
+#define AMGH_ERR_CUDA (-3)          /* a CUDA runtime call failed */
+#define AMGH_ERR_OOM (-4)           /* device or host allocation failed */
+#define AMGH_ERR_NOT_CONVERGED (-5) /* a CG loop hit its iteration cap */
+#define AMGH_ERR_INDEFINITE (-6)    /* p.Ap <= 0 or r.z <= 0 inside a CG loop */
+#define AMGH_ERR_NUMERIC (-7)       /* NaN/Inf in a residual norm */
+#define AMGH_ERR_TIMEOUT (-8)       /* a bounded device-side wait ran out */
+
+typedef struct amgh_problem amgh_problem; /* opaque, owned by the library */
+
+/* Mesh (Sec. 2: P1 elements).  coords: n_vertices*dim doubles (x fastest);
+ * elements: n_elements*(dim+1) 0-based vertex ids; dirichlet: n_vertices
+ * bytes, 1 = boundary vertex where y = 0.  on_device = 1: coords, elements,
+ * dirichlet and kappa are device pointers; 0: host pointers. */
+typedef struct {
+    int dim;
+    int64_t n_vertices;
+    const double *coords;
+    int64_t n_elements;
+    const int32_t *elements;
+    const uint8_t *dirichlet;
+    int on_device;
+} amgh_mesh;
+
+/* AMG options (Sec. 3.1 smoothed aggregation; Sec. 5.2 usage).
+ *  max_levels      cap on AMG levels of each hierarchy (>= 1)
+ *  hessian_levels  levels l of the Hessian preconditioner (0 = all, Sec. 5.3)
+ *  theta           strength threshold at level 0 (halved per level)
+ *  coarse_max      stop coarsening at or below this many rows
+ *  smoother        0 = l1-Jacobi, 1 = Chebyshev on D_l1^-1 A over [1/30, 1]
+ *  smooth_degree   Jacobi sweeps or Chebyshev degree (1..16)
+ *  precision       0 = FP64 everywhere; 1 = FP32 V-cycles, smoothers and
+ *                  inner CG with FP64 iterative refinement of every PDE solve
+ *  smooth_prolongator 1 = S = (I - omega D^-1 A) S_hat, 0 = S_hat */
+typedef struct {
+    int max_levels;
+    int hessian_levels;
+    double theta;
+    int coarse_max;
+    int smoother;
+    int smooth_degree;
+    int precision;
+    int smooth_prolongator;
+} amgh_amg_opts;
+
+/* Solve options (Sec. 5.2-5.3).
+ *  tol          outer relative residual ||b - H u|| / ||b||
+ *  max_iter     outer CG cap
+ *  inner_tol    relative residual of every state/adjoint solve A y = f
+ *  mass_tol     relative residual of every mass solve M_{u,j} x = b
+ *  precond      0 = none (identity), 1 = multilevel / two-grid (Q_0)
+ *  ncols        columns solved together (1 in this version)
+ *  inner_max_iter, mass_max_iter   caps of the inner CG loops */
+typedef struct {
+    double tol;
+    int max_iter;
+    double inner_tol;
+    double mass_tol;
+    int precond;
+    int ncols;
+    int inner_max_iter;
+    int mass_max_iter;
+} amgh_solve_opts;
+
+/* Counters of the last amgh_solve (or since amgh_reset_counters). */
+typedef struct {
+    int status;
+    int outer_iters;
+    int64_t hessian_applies; /* fine-level H applies (outer CG + true residual) */
+    int64_t inner_iters;     /* all state/adjoint CG iterations, all levels */
+    int64_t mass_iters;      /* all mass-matrix CG iterations */
+    int64_t refinements;     /* FP64 refinement sweeps (precision = 1) */
+    double final_relres;     /* ||b - H u|| / ||b|| recomputed at the end */
+    double t_setup_s;
+    double t_solve_s;
+} amgh_solve_info;
+
+/* Defaults: max_levels 25, hessian_levels 0, theta 0.08, coarse_max 256,
+ * Chebyshev degree 2, precision 0, smoothed prolongator; tol 1e-8,
+ * max_iter 200, inner/mass tol 1e-10, precond 1, ncols 1, caps 1000. */
+void amgh_amg_opts_default(amgh_amg_opts *opts);
+void amgh_solve_opts_default(amgh_solve_opts *opts);
+
+/* Copy the mesh, per-element kappa (Eq. bilform), beta > 0 and the nodal
+ * desired state y_d (n_vertices doubles; on the device iff y_d_on_device) to
+ * the device and assemble A, M_y, M_u, M_yu (Sec. 2) there.  Element
+ * contributions are summed in ascending element order without fused
+ * multiply-add, so the matrices are bit-identical on every run.
+ * Errors: INVALID_ARG (dim not 2/3, sizes <= 0, beta <= 0, vertex id out of
+ * range, degenerate element), OOM, CUDA.  *out is NULL on error. */
+int amgh_problem_create(const amgh_mesh *mesh, const double *kappa, double beta,
+                        const double *y_d, int y_d_on_device, amgh_problem **out);
+
+/* Replace the desired state (same layout as in amgh_problem_create). */
+int amgh_set_yd(amgh_problem *p, const double *y_d, int on_device);
+
+/* Use this cudaStream_t (e.g. torch.cuda.current_stream().cuda_stream) for all
+ * later work of the problem; NULL = the legacy default stream. */
+int amgh_set_stream(amgh_problem *p, void *cuda_stream);
+
+/* Build the state and control smoothed-aggregation hierarchies (Sec. 3.1,
+ * Eq. coarsestiffness/coarsemass) on the device: strength graph, distance-2
+ * maximal independent set by splitmix64 priority, aggregates, smoothed
+ * prolongators S_j (on A) and P_j (on the all-vertex stiffness), Galerkin
+ * products for A, M_y, M_u, M_yu, and the dense coarsest factors.  Aggregates
+ * are bit-identical to the sequential definition.  opts NULL = defaults.
+ * Errors: INVALID_ARG (bad option, coarsest level above 4096 rows), OOM,
+ * INDEFINITE (coarse Hessian not positive definite), CUDA. */
+int amgh_amg_setup(amgh_problem *p, const amgh_amg_opts *opts);
+
+/* Set the tolerances used by amgh_hessian_apply / amgh_precond_apply /
+ * amgh_rhs / amgh_state_solve / amgh_gradient (inner_tol, mass_tol and the
+ * caps; other fields ignored). */
+int amgh_set_solve_opts(amgh_problem *p, const amgh_solve_opts *opts);
+
+/* Hu = H u on the finest level (Eq. firstorderpractice): one forward and one
+ * adjoint AMG-CG solve (Sec. 5.2).  u_dev, Hu_dev: n*ncols doubles, device,
+ * may not alias.  Errors: NOT_SETUP, INVALID_ARG, NOT_CONVERGED, INDEFINITE,
+ * NUMERIC, CUDA. */
+int amgh_hessian_apply(amgh_problem *p, const double *u_dev, double *Hu_dev, int ncols);
+
+/* z = Q_0 r, the multilevel Hessian preconditioner in M_u-scaled form
+ * (Sec. 3.2 Algorithm MLAS with Eq. twogridinmulti/twogridinmultiactual and
+ * the substitution of Sec. 5.2).  r_dev, z_dev: n*ncols doubles, device. */
+int amgh_precond_apply(amgh_problem *p, const double *r_dev, double *z_dev, int ncols);
+
+/* b = M_yu^T A^-1 M_y y_d (right side of Eq. firstorderpractice); b_dev: n
+ * doubles, device. */
+int amgh_rhs(amgh_problem *p, double *b_dev);
+
+/* Outer CG on H u = b (Sec. 5.3) from u0 (NULL = 0), to
+ * ||r_k|| <= opts->tol ||b||; writes u (n doubles) and, if y_dev is not
+ * NULL, the state y = A^-1 M_yu u (m doubles).  All device pointers.
+ * info (may be NULL) receives counters and the recomputed relative residual.
+ * Errors: as amgh_hessian_apply, plus NOT_CONVERGED for the outer loop. */
+int amgh_solve(amgh_problem *p, const double *u0_dev, double *u_dev, double *y_dev,
+               const amgh_solve_opts *opts, amgh_solve_info *info);
+
+/* Same as amgh_solve with HOST buffers: copies u0 (NULL ok) to the device,
+ * solves, copies u (and y if not NULL) back.  This is the end-to-end call. */
+int amgh_solve_host(amgh_problem *p, const double *u0_host, double *u_host, double *y_host,
+                    const amgh_solve_opts *opts, amgh_solve_info *info);
+
+/* State solve y = A^-1 M_yu u (Sec. 2, Eq. solutionopdef) and, if J_host is not
+ * NULL, the reduced cost J(u) (Eq. functional).  u_dev n, y_dev m doubles. */
+int amgh_state_solve(amgh_problem *p, const double *u_dev, double *y_dev, double *J_host);
+
+/* Gradient of the reduced cost by the adjoint solve:
+ * g = M_yu^T A^-1 M_y (y - y_d) + beta M_u u (= H u - b), with y from
+ * amgh_state_solve.  u_dev, g_dev n doubles; y_dev m doubles. */
+int amgh_gradient(amgh_problem *p, const double *u_dev, const double *y_dev, double *g_dev);
+
+/* Level-wise building blocks (for tests and diagnostics).
+ * amgh_vcycle: x = V_l b, one symmetric V-cycle on A_l from x = 0.
+ * amgh_state_solve_level: A_l y = f by AMG-CG to rel. tolerance tol.
+ * amgh_mass_solve: M_{u,l} x = b by Jacobi-CG to the mass tolerance.
+ * amgh_hessian_apply_level: H_l v on level l < hessian levels.
+ * amgh_precond_apply_level: which = 0: Q_l b; which = 1: R_l b (l < ell-1).
+ * All vectors are device pointers of the level's size. */
+int amgh_vcycle(amgh_problem *p, int level, const double *b_dev, double *x_dev);
+int amgh_state_solve_level(amgh_problem *p, int level, const double *f_dev, double *y_dev,
+                           double tol, int64_t *iters);
+int amgh_mass_solve(amgh_problem *p, int level, const double *b_dev, double *x_dev,
+                    int64_t *iters);
+int amgh_hessian_apply_level(amgh_problem *p, int level, const double *v_dev, double *hv_dev);
+int amgh_precond_apply_level(amgh_problem *p, int which, int level, const double *b_dev,
+                             double *z_dev);
+
+/* Sizes: m, n; number of state levels Ls, control levels Lc, Hessian levels
+ * ell; state_sizes / ctrl_sizes receive up to 32 level row counts each
+ * (either may be NULL). */
+int amgh_query_sizes(const amgh_problem *p, int64_t *m, int64_t *n, int *Ls, int *Lc, int *ell,
+                     int64_t *state_sizes, int64_t *ctrl_sizes);
+
+/* Aggregate id of every row of level `level` of hierarchy `hier` (0 = state,
+ * 1 = control); agg_host holds that level's row count int32s; *nagg the
+ * number of aggregates.  level must be below the hierarchy's last level. */
+int amgh_get_aggregates(const amgh_problem *p, int hier, int level, int32_t *agg_host,
+                        int32_t *nagg);
+
+/* Copy a level matrix in CSR (sorted columns) to host buffers.
+ * which: 0 A, 1 M_y, 2 M_yu, 3 S (level -> level+1), 4 K_N (all-vertex
+ * stiffness of the control hierarchy), 5 M_u, 6 P, 7 K_full, 8 M_full.
+ * amgh_get_matrix_info gives rows, cols, nnz; amgh_get_matrix fills
+ * rowptr (rows+1), col (nnz) and val (nnz). */
+int amgh_get_matrix_info(const amgh_problem *p, int which, int level, int64_t *rows,
+                         int64_t *cols, int64_t *nnz);
+int amgh_get_matrix(const amgh_problem *p, int which, int level, int32_t *rowptr_host,
+                    int32_t *col_host, double *val_host);
+
+/* Counters since the last reset (fields as amgh_solve_info). */
+int amgh_get_counters(const amgh_problem *p, amgh_solve_info *info);
+int amgh_reset_counters(amgh_problem *p);
+
+/* Kernel timing for roofline reporting: when enabled, every launch of the
+ * fine-level (level 0) SpMV-class kernels is bracketed by CUDA events on the
+ * problem's stream.  amgh_kernel_stats returns the number of timed launches,
+ * their summed duration in ms, and their summed algorithmic bytes
+ * (nnz*(value+4) + 4*(rows+1) + value*(rows+cols) per SpMV). */
+int amgh_kernel_timing(amgh_problem *p, int enable);
+int amgh_kernel_stats(amgh_problem *p, int64_t *launches, double *ms, double *bytes);
+
+/* Number of kernels this library launched since load (all problems). */
+int64_t amgh_launch_count(void);
+
+void amgh_problem_destroy(amgh_problem *p);
+const char *amgh_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* AMGH_H */

@@ -1,0 +1,345 @@
+"""Python binding of the amgh C ABI (include/amgh.h).
+
+Argument marshalling only: every step of the method runs in the CUDA
+library libamgh.so built in this directory.  There is no fallback -- if the
+library is missing, importing a function raises.  PyTorch supplies device
+memory (tensors) and the current CUDA stream.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libamgh.so")
+
+OK = 0
+ERR = {-1: "INVALID_ARG", -2: "NOT_SETUP", -3: "CUDA", -4: "OOM", -5: "NOT_CONVERGED",
+       -6: "INDEFINITE", -7: "NUMERIC", -8: "TIMEOUT"}
+MATRIX = {"A": 0, "My": 1, "Myu": 2, "S": 3, "KN": 4, "Mu": 5, "P": 6, "Kfull": 7, "Mfull": 8}
+
+
+class AmghError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        super().__init__(f"{what}: {ERR.get(code, code)} ({code})")
+        self.code = code
+
+
+class amgh_mesh(C.Structure):
+    _fields_ = [("dim", C.c_int), ("n_vertices", C.c_int64), ("coords", C.c_void_p),
+                ("n_elements", C.c_int64), ("elements", C.c_void_p), ("dirichlet", C.c_void_p),
+                ("on_device", C.c_int)]
+
+
+class amgh_amg_opts(C.Structure):
+    _fields_ = [("max_levels", C.c_int), ("hessian_levels", C.c_int), ("theta", C.c_double),
+                ("coarse_max", C.c_int), ("smoother", C.c_int), ("smooth_degree", C.c_int),
+                ("precision", C.c_int), ("smooth_prolongator", C.c_int)]
+
+
+class amgh_solve_opts(C.Structure):
+    _fields_ = [("tol", C.c_double), ("max_iter", C.c_int), ("inner_tol", C.c_double),
+                ("mass_tol", C.c_double), ("precond", C.c_int), ("ncols", C.c_int),
+                ("inner_max_iter", C.c_int), ("mass_max_iter", C.c_int)]
+
+
+class amgh_solve_info(C.Structure):
+    _fields_ = [("status", C.c_int), ("outer_iters", C.c_int), ("hessian_applies", C.c_int64),
+                ("inner_iters", C.c_int64), ("mass_iters", C.c_int64), ("refinements", C.c_int64),
+                ("final_relres", C.c_double), ("t_setup_s", C.c_double), ("t_solve_s", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_P, _I, _I64, _D = C.c_void_p, C.c_int, C.c_int64, C.c_double
+_SIGS = {
+    "amgh_amg_opts_default": ([_P], None),
+    "amgh_solve_opts_default": ([_P], None),
+    "amgh_problem_create": ([_P, _P, _D, _P, _I, _P], _I),
+    "amgh_set_yd": ([_P, _P, _I], _I),
+    "amgh_set_stream": ([_P, _P], _I),
+    "amgh_amg_setup": ([_P, _P], _I),
+    "amgh_set_solve_opts": ([_P, _P], _I),
+    "amgh_hessian_apply": ([_P, _P, _P, _I], _I),
+    "amgh_precond_apply": ([_P, _P, _P, _I], _I),
+    "amgh_rhs": ([_P, _P], _I),
+    "amgh_solve": ([_P, _P, _P, _P, _P, _P], _I),
+    "amgh_solve_host": ([_P, _P, _P, _P, _P, _P], _I),
+    "amgh_state_solve": ([_P, _P, _P, _P], _I),
+    "amgh_gradient": ([_P, _P, _P, _P], _I),
+    "amgh_vcycle": ([_P, _I, _P, _P], _I),
+    "amgh_state_solve_level": ([_P, _I, _P, _P, _D, _P], _I),
+    "amgh_mass_solve": ([_P, _I, _P, _P, _P], _I),
+    "amgh_hessian_apply_level": ([_P, _I, _P, _P], _I),
+    "amgh_precond_apply_level": ([_P, _I, _I, _P, _P], _I),
+    "amgh_query_sizes": ([_P, _P, _P, _P, _P, _P, _P, _P], _I),
+    "amgh_get_aggregates": ([_P, _I, _I, _P, _P], _I),
+    "amgh_get_matrix_info": ([_P, _I, _I, _P, _P, _P], _I),
+    "amgh_get_matrix": ([_P, _I, _I, _P, _P, _P], _I),
+    "amgh_get_counters": ([_P, _P], _I),
+    "amgh_reset_counters": ([_P], _I),
+    "amgh_kernel_timing": ([_P, _I], _I),
+    "amgh_kernel_stats": ([_P, _P, _P, _P], _I),
+    "amgh_launch_count": ([], _I64),
+    "amgh_problem_destroy": ([_P], None),
+    "amgh_status_string": ([_I], C.c_char_p),
+}
+_lib = None
+
+
+def declared_symbols():
+    return sorted(_SIGS)
+
+
+def lib():
+    """Load libamgh.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with __graft_entry__.build() "
+                               "(the amgh path has no CPU fallback)")
+        L = C.CDLL(LIB_PATH)
+        for name, (args, res) in _SIGS.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = res
+        _lib = L
+    return _lib
+
+
+def check(code: int, what: str):
+    if code != OK:
+        raise AmghError(code, what)
+
+
+def _ptr(t):
+    """Device or host address of a torch tensor / numpy array (None -> NULL)."""
+    if t is None:
+        return None
+    if isinstance(t, np.ndarray):
+        return t.ctypes.data_as(C.c_void_p)
+    return C.c_void_p(t.data_ptr())
+
+
+def launch_count() -> int:
+    return int(lib().amgh_launch_count())
+
+
+def amg_opts(**kw) -> amgh_amg_opts:
+    o = amgh_amg_opts()
+    lib().amgh_amg_opts_default(C.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+def solve_opts(**kw) -> amgh_solve_opts:
+    o = amgh_solve_opts()
+    lib().amgh_solve_opts_default(C.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+class Problem:
+    """One control problem resident on the current CUDA device.
+
+    Construct from host numpy arrays (`on_device=False`) or CUDA tensors
+    (`on_device=True`); see include/amgh.h for layouts.
+    """
+
+    def __init__(self, dim, coords, elements, dirichlet, kappa, beta, y_d, on_device=None,
+                 stream=None):
+        import torch
+        L = lib()
+        if on_device is None:
+            on_device = not isinstance(coords, np.ndarray)
+        self._keep = (coords, elements, dirichlet, kappa, y_d)
+        mesh = amgh_mesh(dim, int(coords.shape[0]), _ptr(coords), int(elements.shape[0]),
+                         _ptr(elements), _ptr(dirichlet), 1 if on_device else 0)
+        h = C.c_void_p()
+        self.h = None
+        if stream is None and torch.cuda.is_available():
+            stream = torch.cuda.current_stream().cuda_stream
+        check(L.amgh_problem_create(C.byref(mesh), _ptr(kappa), float(beta), _ptr(y_d),
+                                    1 if on_device else 0, C.byref(h)), "amgh_problem_create")
+        self.h = h
+        if stream is not None:
+            check(L.amgh_set_stream(self.h, C.c_void_p(stream)), "amgh_set_stream")
+        self._keep = None
+        self.beta = float(beta)
+        self.dim = dim
+
+    @classmethod
+    def from_workload(cls, w, device=True, y_index=0):
+        """Upload a workloads.Workload (as CUDA tensors when device=True)."""
+        yd = w.y_d if w.y_d.ndim == 1 else w.y_d[y_index]
+        arrs = [np.ascontiguousarray(w.coords, dtype=np.float64),
+                np.ascontiguousarray(w.elements, dtype=np.int32),
+                np.ascontiguousarray(w.dirichlet, dtype=np.uint8),
+                np.ascontiguousarray(w.kappa, dtype=np.float64),
+                np.ascontiguousarray(yd, dtype=np.float64)]
+        if device:
+            import torch
+            arrs = [torch.from_numpy(a).cuda() for a in arrs]
+            torch.cuda.synchronize()
+        return cls(w.dim, arrs[0], arrs[1], arrs[2], arrs[3], w.beta, arrs[4], on_device=device)
+
+    def __del__(self):
+        self.close()
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().amgh_problem_destroy(self.h)
+            self.h = None
+
+    # -- setup and options
+    def amg_setup(self, **kw):
+        o = amg_opts(**kw)
+        check(lib().amgh_amg_setup(self.h, C.byref(o)), "amgh_amg_setup")
+        self.sizes = self.query_sizes()
+        return self
+
+    def set_solve_opts(self, **kw):
+        o = solve_opts(**kw)
+        check(lib().amgh_set_solve_opts(self.h, C.byref(o)), "amgh_set_solve_opts")
+
+    def set_stream(self, stream):
+        check(lib().amgh_set_stream(self.h, C.c_void_p(stream)), "amgh_set_stream")
+
+    def set_yd(self, y_d):
+        on_dev = not isinstance(y_d, np.ndarray)
+        check(lib().amgh_set_yd(self.h, _ptr(y_d), 1 if on_dev else 0), "amgh_set_yd")
+
+    def query_sizes(self):
+        m, n = C.c_int64(), C.c_int64()
+        Ls, Lc, ell = C.c_int(), C.c_int(), C.c_int()
+        ss = np.zeros(32, dtype=np.int64)
+        cs = np.zeros(32, dtype=np.int64)
+        check(lib().amgh_query_sizes(self.h, C.byref(m), C.byref(n), C.byref(Ls), C.byref(Lc),
+                                     C.byref(ell), _ptr(ss), _ptr(cs)), "amgh_query_sizes")
+        return {"m": m.value, "n": n.value, "Ls": Ls.value, "Lc": Lc.value, "ell": ell.value,
+                "state": ss[:Ls.value].tolist(), "control": cs[:Lc.value].tolist()}
+
+    # -- helpers
+    def _new(self, k, like=None):
+        import torch
+        return torch.empty(k, dtype=torch.float64, device="cuda")
+
+    # -- the hot path
+    def hessian_apply(self, u, out=None):
+        out = self._new(u.numel()) if out is None else out
+        ncols = 1 if u.dim() == 1 else u.shape[1]
+        check(lib().amgh_hessian_apply(self.h, _ptr(u), _ptr(out), ncols), "amgh_hessian_apply")
+        return out
+
+    def precond_apply(self, r, out=None):
+        out = self._new(r.numel()) if out is None else out
+        ncols = 1 if r.dim() == 1 else r.shape[1]
+        check(lib().amgh_precond_apply(self.h, _ptr(r), _ptr(out), ncols), "amgh_precond_apply")
+        return out
+
+    def rhs(self):
+        b = self._new(self.sizes["n"])
+        check(lib().amgh_rhs(self.h, _ptr(b)), "amgh_rhs")
+        return b
+
+    def solve(self, u0=None, want_y=True, raise_on_error=True, **kw):
+        o = solve_opts(**kw)
+        u = self._new(self.sizes["n"])
+        y = self._new(self.sizes["m"]) if want_y else None
+        info = amgh_solve_info()
+        st = lib().amgh_solve(self.h, _ptr(u0), _ptr(u), _ptr(y), C.byref(o), C.byref(info))
+        if raise_on_error:
+            check(st, "amgh_solve")
+        return u, y, info.as_dict()
+
+    def solve_host(self, u0=None, want_y=True, **kw):
+        o = solve_opts(**kw)
+        u = np.zeros(self.sizes["n"])
+        y = np.zeros(self.sizes["m"]) if want_y else None
+        info = amgh_solve_info()
+        check(lib().amgh_solve_host(self.h, _ptr(u0), _ptr(u), _ptr(y), C.byref(o), C.byref(info)),
+              "amgh_solve_host")
+        return u, y, info.as_dict()
+
+    def state_solve(self, u):
+        y = self._new(self.sizes["m"])
+        J = C.c_double()
+        check(lib().amgh_state_solve(self.h, _ptr(u), _ptr(y), C.byref(J)), "amgh_state_solve")
+        return y, J.value
+
+    def gradient(self, u, y):
+        g = self._new(self.sizes["n"])
+        check(lib().amgh_gradient(self.h, _ptr(u), _ptr(y), _ptr(g)), "amgh_gradient")
+        return g
+
+    # -- level-wise pieces
+    def vcycle(self, level, b):
+        x = self._new(b.numel())
+        check(lib().amgh_vcycle(self.h, level, _ptr(b), _ptr(x)), "amgh_vcycle")
+        return x
+
+    def state_solve_level(self, level, f, tol):
+        y = self._new(f.numel())
+        it = C.c_int64()
+        check(lib().amgh_state_solve_level(self.h, level, _ptr(f), _ptr(y), float(tol), C.byref(it)),
+              "amgh_state_solve_level")
+        return y, it.value
+
+    def mass_solve(self, level, b):
+        x = self._new(b.numel())
+        it = C.c_int64()
+        check(lib().amgh_mass_solve(self.h, level, _ptr(b), _ptr(x), C.byref(it)), "amgh_mass_solve")
+        return x, it.value
+
+    def hessian_apply_level(self, level, v):
+        hv = self._new(v.numel())
+        check(lib().amgh_hessian_apply_level(self.h, level, _ptr(v), _ptr(hv)),
+              "amgh_hessian_apply_level")
+        return hv
+
+    def precond_apply_level(self, which, level, b):
+        z = self._new(b.numel())
+        check(lib().amgh_precond_apply_level(self.h, which, level, _ptr(b), _ptr(z)),
+              "amgh_precond_apply_level")
+        return z
+
+    # -- inspection
+    def aggregates(self, hier, level):
+        rows = self.sizes["state" if hier == 0 else "control"][level]
+        agg = np.empty(rows, dtype=np.int32)
+        nagg = C.c_int32()
+        check(lib().amgh_get_aggregates(self.h, hier, level, _ptr(agg), C.byref(nagg)),
+              "amgh_get_aggregates")
+        return agg, nagg.value
+
+    def matrix(self, which, level=0):
+        wid = MATRIX[which] if isinstance(which, str) else int(which)
+        r, c, z = C.c_int64(), C.c_int64(), C.c_int64()
+        check(lib().amgh_get_matrix_info(self.h, wid, level, C.byref(r), C.byref(c), C.byref(z)),
+              "amgh_get_matrix_info")
+        rp = np.empty(r.value + 1, dtype=np.int32)
+        ci = np.empty(z.value, dtype=np.int32)
+        v = np.empty(z.value, dtype=np.float64)
+        check(lib().amgh_get_matrix(self.h, wid, level, _ptr(rp), _ptr(ci), _ptr(v)), "amgh_get_matrix")
+        return rp, ci, v, (r.value, c.value)
+
+    def counters(self):
+        info = amgh_solve_info()
+        check(lib().amgh_get_counters(self.h, C.byref(info)), "amgh_get_counters")
+        return info.as_dict()
+
+    def reset_counters(self):
+        check(lib().amgh_reset_counters(self.h), "amgh_reset_counters")
+
+    def kernel_timing(self, enable=True):
+        check(lib().amgh_kernel_timing(self.h, 1 if enable else 0), "amgh_kernel_timing")
+
+    def kernel_stats(self):
+        n, ms, b = C.c_int64(), C.c_double(), C.c_double()
+        check(lib().amgh_kernel_stats(self.h, C.byref(n), C.byref(ms), C.byref(b)), "amgh_kernel_stats")
+        return {"launches": n.value, "ms": ms.value, "bytes": b.value}

@@ -1,0 +1,637 @@
+// amg.cu -- smoothed-aggregation setup on the device (Sec. 3.1; Eq.
+// coarsestiffness, coarsemass): strength graph, distance-2 maximal
+// independent set, aggregates, smoothed prolongator and Galerkin products.
+//
+// Everything that decides an integer (a strength test, a root, an aggregate
+// id, a sparsity pattern) is computed so that it equals the sequential
+// definition exactly:
+//   strength   j ~ i iff a_ij*a_ij >= theta^2 * (a_ii*a_jj), each product
+//              rounded separately (no fused multiply-add);
+//   roots      the greedy distance-2 independent set in decreasing splitmix64
+//              priority, obtained here by parallel rounds with fixed
+//              priorities (a vertex whose priority is the largest among the
+//              undecided vertices within distance 2 becomes a root; vertices
+//              within distance 2 of a root leave) -- with fixed priorities
+//              this returns exactly the greedy set;
+//   aggregates phase 1 = root + strong neighbours (id = root rank), phase 2 =
+//              strongest phase-1 neighbour (ties to the smaller id), phase 3 =
+//              singletons in ascending vertex order;
+//   products   C_iJ = sum over A's row i in ascending column order of
+//              A_ij * B_jJ (rounded products, added in that order), so the
+//              Galerkin matrices -- and the strength tests of the next level
+//              -- are the same bits on every run.
+#include "internal.cuh"
+#include "util.cuh"
+
+#define MAXROW 256
+
+// ------------------------------------------------------------------ helpers
+__device__ __forceinline__ uint64_t splitmix_prio(uint64_t i)
+{
+    // splitmix64 output function (Steele, Lea & Flood 2014) of (seed ^ i)
+    uint64_t z = 0x9E3779B97F4A7C15ULL ^ i;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+__device__ __forceinline__ double row_diag(int i, const int *__restrict__ rp, const int *__restrict__ ci,
+                                           const double *__restrict__ v)
+{
+    int lo = rp[i], hi = rp[i + 1] - 1;
+    while (lo <= hi) {
+        int mid = (lo + hi) >> 1;
+        int c = ci[mid];
+        if (c == i) return v[mid];
+        if (c < i) lo = mid + 1;
+        else hi = mid - 1;
+    }
+    return 0.0;
+}
+
+__global__ void k_diag(int n, const int *__restrict__ rp, const int *__restrict__ ci, const double *__restrict__ v,
+                       double *__restrict__ d)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) d[i] = row_diag(i, rp, ci, v);
+}
+
+// ------------------------------------------------------------------ strength
+__global__ void k_strength(int n, const int *__restrict__ rp, const int *__restrict__ ci,
+                           const double *__restrict__ v, const double *__restrict__ d, double th2,
+                           const int *__restrict__ srp, int *__restrict__ cnt, int *__restrict__ sci,
+                           double *__restrict__ sv)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double di = d[i];
+    int c = 0, pos = srp ? srp[i] : 0;
+    for (int k = rp[i]; k < rp[i + 1]; k++) {
+        int j = ci[k];
+        if (j == i) continue;
+        double a = v[k];
+        if (__dmul_rn(a, a) >= __dmul_rn(th2, __dmul_rn(di, d[j]))) {
+            if (srp) {
+                sci[pos] = j;
+                sv[pos] = a;
+                pos++;
+            }
+            c++;
+        }
+    }
+    if (!srp) cnt[i] = c;
+}
+
+// ------------------------------------------------------------------ MIS-2
+// state: 0 undecided, 1 root, 2 removed
+__global__ void k_mis_m1(int n, const int *__restrict__ rp, const int *__restrict__ ci,
+                         const unsigned char *__restrict__ st, int *__restrict__ m1)
+{
+    int v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= n) return;
+    int best = -1;
+    uint64_t bp = 0;
+    if (st[v] == 0) {
+        best = v;
+        bp = splitmix_prio(v);
+    }
+    for (int k = rp[v]; k < rp[v + 1]; k++) {
+        int u = ci[k];
+        if (st[u] != 0) continue;
+        uint64_t pu = splitmix_prio(u);
+        if (best < 0 || pu > bp) {
+            best = u;
+            bp = pu;
+        }
+    }
+    m1[v] = best;
+}
+
+__global__ void k_mis_select(int n, const int *__restrict__ rp, const int *__restrict__ ci,
+                             const int *__restrict__ m1, unsigned char *__restrict__ st)
+{
+    int v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= n || st[v] != 0) return;
+    int best = m1[v];
+    uint64_t bp = best >= 0 ? splitmix_prio(best) : 0;
+    for (int k = rp[v]; k < rp[v + 1]; k++) {
+        int w = m1[ci[k]];
+        if (w < 0) continue;
+        uint64_t pw = splitmix_prio(w);
+        if (best < 0 || pw > bp) {
+            best = w;
+            bp = pw;
+        }
+    }
+    if (best == v) st[v] = 3; // new root this round (promoted below)
+}
+
+__global__ void k_mis_r1(int n, const int *__restrict__ rp, const int *__restrict__ ci,
+                         const unsigned char *__restrict__ st, unsigned char *__restrict__ r1)
+{
+    int u = blockIdx.x * blockDim.x + threadIdx.x;
+    if (u >= n) return;
+    unsigned char f = st[u] == 3;
+    for (int k = rp[u]; k < rp[u + 1] && !f; k++) f = st[ci[k]] == 3;
+    r1[u] = f;
+}
+
+__global__ void k_mis_r2(int n, const int *__restrict__ rp, const int *__restrict__ ci,
+                         const unsigned char *__restrict__ r1, unsigned char *__restrict__ st,
+                         int *__restrict__ undecided)
+{
+    int v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= n) return;
+    unsigned char s = st[v];
+    if (s != 0) return;
+    unsigned char f = r1[v];
+    for (int k = rp[v]; k < rp[v + 1] && !f; k++) f = r1[ci[k]];
+    if (f) st[v] = 2;
+    else atomicAdd(undecided, 1);
+}
+
+__global__ void k_mis_promote(int n, unsigned char *__restrict__ st)
+{
+    int v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v < n && st[v] == 3) st[v] = 1;
+}
+
+// ------------------------------------------------------------------ aggregation phases
+__global__ void k_root_flag(int n, const unsigned char *__restrict__ st, int *__restrict__ f)
+{
+    int v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v < n) f[v] = st[v] == 1;
+}
+
+__global__ void k_phase1(int n, const int *__restrict__ srp, const int *__restrict__ sci,
+                         const unsigned char *__restrict__ st, const int *__restrict__ rank, int *__restrict__ agg)
+{
+    int v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= n) return;
+    if (st[v] == 1) {
+        agg[v] = rank[v];
+        return;
+    }
+    int a = -1;
+    for (int k = srp[v]; k < srp[v + 1]; k++) {
+        int u = sci[k];
+        if (st[u] == 1) {
+            a = rank[u];
+            break;
+        }
+    }
+    agg[v] = a;
+}
+
+__global__ void k_phase2(int n, const int *__restrict__ srp, const int *__restrict__ sci,
+                         const double *__restrict__ sv, const int *__restrict__ agg1, int *__restrict__ agg2,
+                         int *__restrict__ freeflag)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int a = agg1[i];
+    if (a < 0) {
+        double best = -1.0;
+        int bid = -1;
+        for (int k = srp[i]; k < srp[i + 1]; k++) {
+            int aj = agg1[sci[k]];
+            if (aj < 0) continue;
+            double w = fabs(sv[k]);
+            if (w > best || (w == best && aj < bid)) {
+                best = w;
+                bid = aj;
+            }
+        }
+        a = bid;
+    }
+    agg2[i] = a;
+    freeflag[i] = a < 0;
+}
+
+__global__ void k_phase3(int n, const int *__restrict__ fr, const int *__restrict__ frank, int nroots,
+                         int *__restrict__ agg)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n && fr[i]) agg[i] = nroots + frank[i];
+}
+
+int amg_aggregate(amgh_problem *p, const DevCsr &a, double theta2, int *agg, int *nagg_out)
+{
+    cudaStream_t s = p->stream;
+    int n = a.rows;
+    Scratch sc;
+    double *d = nullptr, *sv = nullptr;
+    int *cnt = nullptr, *srp = nullptr, *sci = nullptr;
+    TRY(sc.alloc(&d, n));
+    TRY(sc.alloc(&cnt, n + 1));
+    TRY(sc.alloc(&srp, n + 1));
+    int nb = ceil_div(n, 256);
+    k_diag<<<nb, 256, 0, s>>>(n, a.rp, a.ci, a.v, d);
+    LAUNCH_CHECK();
+    k_strength<<<nb, 256, 0, s>>>(n, a.rp, a.ci, a.v, d, theta2, nullptr, cnt, nullptr, nullptr);
+    LAUNCH_CHECK();
+    int snnz = 0;
+    TRY(exclusive_scan<int>(cnt, srp, n, s, &snnz));
+    TRY(sc.alloc(&sci, snnz));
+    TRY(sc.alloc(&sv, snnz));
+    k_strength<<<nb, 256, 0, s>>>(n, a.rp, a.ci, a.v, d, theta2, srp, cnt, sci, sv);
+    LAUNCH_CHECK();
+    // MIS-2 by rounds
+    unsigned char *st = nullptr, *r1 = nullptr;
+    int *m1 = nullptr, *und = nullptr;
+    TRY(sc.alloc(&st, n));
+    TRY(sc.alloc(&r1, n));
+    TRY(sc.alloc(&m1, n));
+    TRY(sc.alloc(&und, 1));
+    CU(cudaMemsetAsync(st, 0, n, s));
+    int rounds = 0;
+    for (;;) {
+        CU(cudaMemsetAsync(und, 0, sizeof(int), s));
+        k_mis_m1<<<nb, 256, 0, s>>>(n, srp, sci, st, m1);
+        LAUNCH_CHECK();
+        k_mis_select<<<nb, 256, 0, s>>>(n, srp, sci, m1, st);
+        LAUNCH_CHECK();
+        k_mis_r1<<<nb, 256, 0, s>>>(n, srp, sci, st, r1);
+        LAUNCH_CHECK();
+        k_mis_r2<<<nb, 256, 0, s>>>(n, srp, sci, r1, st, und);
+        LAUNCH_CHECK();
+        k_mis_promote<<<nb, 256, 0, s>>>(n, st);
+        LAUNCH_CHECK();
+        int h = 0;
+        CU(cudaMemcpyAsync(&h, und, sizeof(int), cudaMemcpyDeviceToHost, s));
+        CU(cudaStreamSynchronize(s));
+        rounds++;
+        if (h == 0) break;
+        if (rounds > n + 1) return AMGH_ERR_TIMEOUT; // each round fixes at least one vertex
+    }
+    // phases
+    int *flag = nullptr, *rank = nullptr, *agg1 = nullptr, *fr = nullptr, *frank = nullptr;
+    TRY(sc.alloc(&flag, n + 1));
+    TRY(sc.alloc(&rank, n + 1));
+    TRY(sc.alloc(&agg1, n));
+    TRY(sc.alloc(&fr, n + 1));
+    TRY(sc.alloc(&frank, n + 1));
+    k_root_flag<<<nb, 256, 0, s>>>(n, st, flag);
+    LAUNCH_CHECK();
+    int nroots = 0;
+    TRY(exclusive_scan<int>(flag, rank, n, s, &nroots));
+    k_phase1<<<nb, 256, 0, s>>>(n, srp, sci, st, rank, agg1);
+    LAUNCH_CHECK();
+    k_phase2<<<nb, 256, 0, s>>>(n, srp, sci, sv, agg1, agg, fr);
+    LAUNCH_CHECK();
+    int nfree = 0;
+    TRY(exclusive_scan<int>(fr, frank, n, s, &nfree));
+    if (nfree > 0) {
+        k_phase3<<<nb, 256, 0, s>>>(n, fr, frank, nroots, agg);
+        LAUNCH_CHECK();
+    }
+    CU(cudaStreamSynchronize(s));
+    *nagg_out = nroots + nfree;
+    return AMGH_OK;
+}
+
+// ------------------------------------------------------------------ prolongator
+__global__ void k_rho(int n, const int *__restrict__ rp, const int *__restrict__ ci, const double *__restrict__ v,
+                      unsigned long long *__restrict__ rho_bits)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double s = 0.0, aii = 0.0;
+    for (int k = rp[i]; k < rp[i + 1]; k++) {
+        s = __dadd_rn(s, fabs(v[k]));
+        if (ci[k] == i) aii = v[k];
+    }
+    double r = __ddiv_rn(s, aii);
+    // non-negative doubles order like their bit patterns
+    atomicMax(rho_bits, (unsigned long long)__double_as_longlong(r));
+}
+
+// row i: columns {agg(j)}, values [agg(i)==J] - (omega/a_ii) * sum_{agg(j)=J} a_ij
+__global__ void k_prol(int n, const int *__restrict__ rp, const int *__restrict__ ci, const double *__restrict__ v,
+                       const int *__restrict__ agg, double omega, const int *__restrict__ prp,
+                       int *__restrict__ cnt, int *__restrict__ pci, double *__restrict__ pv, int *__restrict__ bad)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int cols[MAXROW];
+    double acc[MAXROW];
+    int c = 0;
+    double aii = 0.0;
+    for (int k = rp[i]; k < rp[i + 1]; k++) {
+        int J = agg[ci[k]];
+        if (ci[k] == i) aii = v[k];
+        int pos = c;
+        bool found = false;
+        for (int t = 0; t < c; t++) {
+            if (cols[t] == J) {
+                pos = t;
+                found = true;
+                break;
+            }
+            if (cols[t] > J) {
+                pos = t;
+                break;
+            }
+        }
+        if (!found) {
+            if (c >= MAXROW) {
+                atomicOr(bad, 1);
+                return;
+            }
+            for (int t = c; t > pos; t--) {
+                cols[t] = cols[t - 1];
+                acc[t] = acc[t - 1];
+            }
+            cols[pos] = J;
+            acc[pos] = 0.0;
+            c++;
+        }
+        acc[pos] = __dadd_rn(acc[pos], v[k]);
+    }
+    if (!prp) {
+        cnt[i] = c;
+        return;
+    }
+    double wi = __ddiv_rn(omega, aii);
+    int ai = agg[i];
+    int base = prp[i];
+    for (int t = 0; t < c; t++) {
+        double delta = cols[t] == ai ? 1.0 : 0.0;
+        pci[base + t] = cols[t];
+        pv[base + t] = __dsub_rn(delta, __dmul_rn(wi, acc[t]));
+    }
+}
+
+__global__ void k_tentative(int n, const int *__restrict__ agg, int *__restrict__ rp, int *__restrict__ ci,
+                            double *__restrict__ v)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i > n) return;
+    rp[i] = i;
+    if (i < n) {
+        ci[i] = agg[i];
+        v[i] = 1.0;
+    }
+}
+
+int amg_prolongator(amgh_problem *p, Arena &ar, const DevCsr &a, const int *agg, int nagg, int smooth, DevCsr &S)
+{
+    cudaStream_t s = p->stream;
+    int n = a.rows;
+    S.rows = n;
+    S.cols = nagg;
+    int nb = ceil_div(n, 256);
+    if (!smooth) {
+        S.nnz = n;
+        TRY(ar.alloc(&S.rp, n + 1));
+        TRY(ar.alloc(&S.ci, n));
+        TRY(ar.alloc(&S.v, n));
+        k_tentative<<<ceil_div(n + 1, 256), 256, 0, s>>>(n, agg, S.rp, S.ci, S.v);
+        LAUNCH_CHECK();
+        CU(cudaStreamSynchronize(s));
+        return AMGH_OK;
+    }
+    Scratch sc;
+    unsigned long long *rho_bits = nullptr;
+    int *cnt = nullptr, *bad = nullptr;
+    TRY(sc.alloc(&rho_bits, 1));
+    TRY(sc.alloc(&cnt, n + 1));
+    TRY(sc.alloc(&bad, 1));
+    CU(cudaMemsetAsync(rho_bits, 0, sizeof(unsigned long long), s));
+    CU(cudaMemsetAsync(bad, 0, sizeof(int), s));
+    k_rho<<<nb, 256, 0, s>>>(n, a.rp, a.ci, a.v, rho_bits);
+    LAUNCH_CHECK();
+    unsigned long long hb = 0;
+    CU(cudaMemcpyAsync(&hb, rho_bits, sizeof(hb), cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
+    double rho;
+    memcpy(&rho, &hb, sizeof(double));
+    if (!(rho > 0.0)) return AMGH_ERR_NUMERIC;
+    double omega = 4.0 / (3.0 * rho);
+    k_prol<<<nb, 128, 0, s>>>(n, a.rp, a.ci, a.v, agg, omega, nullptr, cnt, nullptr, nullptr, bad);
+    LAUNCH_CHECK();
+    TRY(ar.alloc(&S.rp, n + 1));
+    int nnz = 0;
+    TRY(exclusive_scan<int>(cnt, S.rp, n, s, &nnz));
+    S.nnz = nnz;
+    TRY(ar.alloc(&S.ci, nnz));
+    TRY(ar.alloc(&S.v, nnz));
+    k_prol<<<nb, 128, 0, s>>>(n, a.rp, a.ci, a.v, agg, omega, S.rp, cnt, S.ci, S.v, bad);
+    LAUNCH_CHECK();
+    int hbad = 0;
+    CU(cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
+    return hbad ? AMGH_ERR_INVALID_ARG : AMGH_OK;
+}
+
+// ------------------------------------------------------------------ SpGEMM
+__global__ void k_gemm_ub(int n, const int *__restrict__ arp, const int *__restrict__ aci,
+                          const int *__restrict__ brp, long long *__restrict__ ub)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    long long u = 0;
+    for (int k = arp[i]; k < arp[i + 1]; k++) {
+        int j = aci[k];
+        u += brp[j + 1] - brp[j];
+    }
+    // hash table of the row: power of two >= 2u (at least 2)
+    long long t = 2;
+    while (t < 2 * u) t <<= 1;
+    ub[i] = u > 0 ? t : 0;
+}
+
+__device__ __forceinline__ unsigned hslot(int key, unsigned mask) { return ((unsigned)key * 2654435761u) & mask; }
+
+// accumulate row i into its hash table in canonical order; count uniques
+__global__ void k_gemm_hash(int n, const int *__restrict__ arp, const int *__restrict__ aci,
+                            const double *__restrict__ av, const int *__restrict__ brp,
+                            const int *__restrict__ bci, const double *__restrict__ bv,
+                            const long long *__restrict__ toff, int *__restrict__ tkey, double *__restrict__ tval,
+                            int *__restrict__ cnt)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    long long base = toff[i];
+    unsigned size = (unsigned)(toff[i + 1] - base);
+    int c = 0;
+    if (size > 0) {
+        unsigned mask = size - 1;
+        int *key = tkey + base;
+        double *val = tval + base;
+        for (unsigned t = 0; t < size; t++) key[t] = -1;
+        for (int k = arp[i]; k < arp[i + 1]; k++) {
+            int j = aci[k];
+            double aij = av[k];
+            for (int q = brp[j]; q < brp[j + 1]; q++) {
+                int J = bci[q];
+                double prod = __dmul_rn(aij, bv[q]);
+                unsigned h = hslot(J, mask);
+                for (;;) {
+                    int kk = key[h];
+                    if (kk == J) {
+                        val[h] = __dadd_rn(val[h], prod);
+                        break;
+                    }
+                    if (kk < 0) {
+                        key[h] = J;
+                        val[h] = __dadd_rn(0.0, prod);
+                        c++;
+                        break;
+                    }
+                    h = (h + 1) & mask;
+                }
+            }
+        }
+    }
+    cnt[i] = c;
+}
+
+__global__ void k_gemm_out(int n, const long long *__restrict__ toff, const int *__restrict__ tkey,
+                           const double *__restrict__ tval, const int *__restrict__ crp, int *__restrict__ cci,
+                           double *__restrict__ cv)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    long long base = toff[i];
+    unsigned size = (unsigned)(toff[i + 1] - base);
+    int b = crp[i], c = 0;
+    for (unsigned t = 0; t < size; t++) {
+        int key = tkey[base + t];
+        if (key < 0) continue;
+        double x = tval[base + t];
+        int j = b + c - 1;
+        while (j >= b && cci[j] > key) {
+            cci[j + 1] = cci[j];
+            cv[j + 1] = cv[j];
+            j--;
+        }
+        cci[j + 1] = key;
+        cv[j + 1] = x;
+        c++;
+    }
+}
+
+int spgemm(amgh_problem *p, Arena &ar, const DevCsr &a, const DevCsr &b, DevCsr &c)
+{
+    cudaStream_t s = p->stream;
+    int n = a.rows;
+    c.rows = n;
+    c.cols = b.cols;
+    Scratch sc;
+    long long *ub = nullptr, *toff = nullptr;
+    int *cnt = nullptr, *tkey = nullptr;
+    double *tval = nullptr;
+    TRY(sc.alloc(&ub, n + 1));
+    TRY(sc.alloc(&toff, n + 1));
+    TRY(sc.alloc(&cnt, n + 1));
+    int nb = ceil_div(n, 128);
+    k_gemm_ub<<<nb, 128, 0, s>>>(n, a.rp, a.ci, b.rp, ub);
+    LAUNCH_CHECK();
+    long long tot = 0;
+    TRY(exclusive_scan<long long>(ub, toff, n, s, &tot));
+    TRY(sc.alloc(&tkey, tot));
+    TRY(sc.alloc(&tval, tot));
+    k_gemm_hash<<<nb, 128, 0, s>>>(n, a.rp, a.ci, a.v, b.rp, b.ci, b.v, toff, tkey, tval, cnt);
+    LAUNCH_CHECK();
+    TRY(ar.alloc(&c.rp, n + 1));
+    int nnz = 0;
+    TRY(exclusive_scan<int>(cnt, c.rp, n, s, &nnz));
+    c.nnz = nnz;
+    TRY(ar.alloc(&c.ci, nnz));
+    TRY(ar.alloc(&c.v, nnz));
+    k_gemm_out<<<nb, 128, 0, s>>>(n, toff, tkey, tval, c.rp, c.ci, c.v);
+    LAUNCH_CHECK();
+    CU(cudaStreamSynchronize(s));
+    return AMGH_OK;
+}
+
+// entries below the diagonal take the value of their mirror above it
+__global__ void k_symm(int n, const int *__restrict__ rp, const int *__restrict__ ci, double *__restrict__ v,
+                       int *__restrict__ bad)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    for (int k = rp[i]; k < rp[i + 1]; k++) {
+        int j = ci[k];
+        if (j >= i) break;
+        int lo = rp[j], hi = rp[j + 1] - 1, pos = -1;
+        while (lo <= hi) {
+            int mid = (lo + hi) >> 1;
+            int cm = ci[mid];
+            if (cm == i) {
+                pos = mid;
+                break;
+            }
+            if (cm < i) lo = mid + 1;
+            else hi = mid - 1;
+        }
+        if (pos < 0) {
+            atomicOr(bad, 1);
+            return;
+        }
+        v[k] = v[pos];
+    }
+}
+
+int symmetrize_upper(amgh_problem *p, DevCsr &c)
+{
+    cudaStream_t s = p->stream;
+    Scratch sc;
+    int *bad = nullptr;
+    TRY(sc.alloc(&bad, 1));
+    CU(cudaMemsetAsync(bad, 0, sizeof(int), s));
+    k_symm<<<ceil_div(c.rows, 256), 256, 0, s>>>(c.rows, c.rp, c.ci, c.v, bad);
+    LAUNCH_CHECK();
+    int h = 0;
+    CU(cudaMemcpyAsync(&h, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
+    return h ? AMGH_ERR_INVALID_ARG : AMGH_OK;
+}
+
+int galerkin(amgh_problem *p, Arena &ar, const DevCsr &rt, const DevCsr &a, const DevCsr &pm, int symmetric,
+             DevCsr &c)
+{
+    Arena tmp;
+    DevCsr ap;
+    int st = spgemm(p, tmp, a, pm, ap);
+    if (st == AMGH_OK) st = spgemm(p, ar, rt, ap, c);
+    tmp.free_all();
+    if (st) return st;
+    if (symmetric) TRY(symmetrize_upper(p, c));
+    return AMGH_OK;
+}
+
+// ------------------------------------------------------------------ diagonals
+__global__ void k_l1(int n, const int *__restrict__ rp, const double *__restrict__ v, double *__restrict__ invd,
+                     float *__restrict__ invd32)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double s = 0.0;
+    for (int k = rp[i]; k < rp[i + 1]; k++) s += fabs(v[k]);
+    double r = 1.0 / s;
+    invd[i] = r;
+    if (invd32) invd32[i] = (float)r;
+}
+
+int l1_invdiag(amgh_problem *p, const DevCsr &a, double *invd, float *invd32)
+{
+    k_l1<<<ceil_div(a.rows, 256), 256, 0, p->stream>>>(a.rows, a.rp, a.v, invd, invd32);
+    LAUNCH_CHECK();
+    return AMGH_OK;
+}
+
+__global__ void k_dinv(int n, const int *__restrict__ rp, const int *__restrict__ ci, const double *__restrict__ v,
+                       double *__restrict__ invd)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) invd[i] = 1.0 / row_diag(i, rp, ci, v);
+}
+
+int diag_inv(amgh_problem *p, const DevCsr &a, double *invd)
+{
+    k_dinv<<<ceil_div(a.rows, 256), 256, 0, p->stream>>>(a.rows, a.rp, a.ci, a.v, invd);
+    LAUNCH_CHECK();
+    return AMGH_OK;
+}

@@ -1,0 +1,644 @@
+// api.cu -- the C ABI declared in include/amgh.h.
+#include <math.h>
+#include <string.h>
+
+#include <chrono>
+#include <new>
+
+#include "internal.cuh"
+#include "util.cuh"
+
+static double now_s()
+{
+    using namespace std::chrono;
+    return duration<double>(steady_clock::now().time_since_epoch()).count();
+}
+
+extern "C" void amgh_amg_opts_default(amgh_amg_opts *o)
+{
+    if (!o) return;
+    o->max_levels = 25;
+    o->hessian_levels = 0;
+    o->theta = 0.08;
+    o->coarse_max = 256;
+    o->smoother = 1;
+    o->smooth_degree = 2;
+    o->precision = 0;
+    o->smooth_prolongator = 1;
+}
+
+extern "C" void amgh_solve_opts_default(amgh_solve_opts *o)
+{
+    if (!o) return;
+    o->tol = 1e-8;
+    o->max_iter = 200;
+    o->inner_tol = 1e-10;
+    o->mass_tol = 1e-10;
+    o->precond = 1;
+    o->ncols = 1;
+    o->inner_max_iter = 1000;
+    o->mass_max_iter = 1000;
+}
+
+extern "C" const char *amgh_status_string(int s)
+{
+    switch (s) {
+    case AMGH_OK: return "ok";
+    case AMGH_ERR_INVALID_ARG: return "invalid argument";
+    case AMGH_ERR_NOT_SETUP: return "amg setup has not run";
+    case AMGH_ERR_CUDA: return "CUDA error";
+    case AMGH_ERR_OOM: return "out of memory";
+    case AMGH_ERR_NOT_CONVERGED: return "not converged";
+    case AMGH_ERR_INDEFINITE: return "indefinite operator or preconditioner";
+    case AMGH_ERR_NUMERIC: return "NaN or Inf in a residual";
+    case AMGH_ERR_TIMEOUT: return "bounded wait ran out";
+    }
+    return "unknown status";
+}
+
+static int copy_in(void *dst, const void *src, size_t bytes, int on_device, cudaStream_t s)
+{
+    CU(cudaMemcpyAsync(dst, src, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+    return AMGH_OK;
+}
+
+__global__ void k_gather_state(int m, const int *__restrict__ vos, const double *__restrict__ full,
+                               double *__restrict__ st)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < m) st[i] = full[vos[i]];
+}
+
+static int load_yd(amgh_problem *p, const double *y_d, int on_device)
+{
+    Scratch sc;
+    double *full = nullptr;
+    TRY(sc.alloc(&full, p->nv));
+    if (y_d) TRY(copy_in(full, y_d, sizeof(double) * p->nv, on_device, p->stream));
+    else CU(cudaMemsetAsync(full, 0, sizeof(double) * p->nv, p->stream));
+    if (p->m > 0) {
+        k_gather_state<<<ceil_div(p->m, 256), 256, 0, p->stream>>>(p->m, p->vertex_of_state, full, p->yd_state);
+        LAUNCH_CHECK();
+    }
+    CU(cudaStreamSynchronize(p->stream));
+    return AMGH_OK;
+}
+
+static int create_impl(const amgh_mesh *mesh, const double *kappa, double beta, const double *y_d, int yd_dev,
+                       amgh_problem *p)
+{
+    p->dim = mesh->dim;
+    p->nv = mesh->n_vertices;
+    p->ne = mesh->n_elements;
+    p->beta = beta;
+    amgh_amg_opts_default(&p->aopts);
+    amgh_solve_opts_default(&p->sopts);
+    CU(cudaHostAlloc((void **)&p->h_scal, sizeof(CgScal), cudaHostAllocDefault));
+    int d1 = p->dim + 1;
+    Arena &ar = p->arena;
+    TRY(ar.alloc(&p->coords, p->nv * p->dim));
+    TRY(ar.alloc(&p->elems, p->ne * d1));
+    TRY(ar.alloc(&p->dir, p->nv));
+    TRY(ar.alloc(&p->kappa, p->ne));
+    int od = mesh->on_device;
+    TRY(copy_in(p->coords, mesh->coords, sizeof(double) * p->nv * p->dim, od, p->stream));
+    TRY(copy_in(p->elems, mesh->elements, sizeof(int) * p->ne * d1, od, p->stream));
+    TRY(copy_in(p->dir, mesh->dirichlet, p->nv, od, p->stream));
+    TRY(copy_in(p->kappa, kappa, sizeof(double) * p->ne, od, p->stream));
+    CU(cudaStreamSynchronize(p->stream));
+    TRY(assemble_full(p));
+    TRY(ar.alloc(&p->yd_state, p->m));
+    TRY(load_yd(p, y_d, yd_dev));
+    return AMGH_OK;
+}
+
+extern "C" int amgh_problem_create(const amgh_mesh *mesh, const double *kappa, double beta, const double *y_d,
+                                   int y_d_on_device, amgh_problem **out)
+{
+    if (!out) return AMGH_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!mesh || !kappa || !mesh->coords || !mesh->elements || !mesh->dirichlet) return AMGH_ERR_INVALID_ARG;
+    if ((mesh->dim != 2 && mesh->dim != 3) || mesh->n_vertices <= 0 || mesh->n_elements <= 0) return AMGH_ERR_INVALID_ARG;
+    if (mesh->n_vertices >= (int64_t)1 << 31 || mesh->n_elements * (mesh->dim + 1) >= ((int64_t)1 << 31))
+        return AMGH_ERR_INVALID_ARG;
+    if (!(beta > 0.0) || isinf(beta)) return AMGH_ERR_INVALID_ARG;
+    amgh_problem *p = new (std::nothrow) amgh_problem();
+    if (!p) return AMGH_ERR_OOM;
+    int st = create_impl(mesh, kappa, beta, y_d, y_d_on_device, p);
+    if (st) {
+        amgh_problem_destroy(p);
+        return st;
+    }
+    *out = p;
+    return AMGH_OK;
+}
+
+extern "C" int amgh_set_yd(amgh_problem *p, const double *y_d, int on_device)
+{
+    if (!p || !y_d) return AMGH_ERR_INVALID_ARG;
+    return load_yd(p, y_d, on_device);
+}
+
+extern "C" int amgh_set_stream(amgh_problem *p, void *stream)
+{
+    if (!p) return AMGH_ERR_INVALID_ARG;
+    p->stream = (cudaStream_t)stream;
+    return AMGH_OK;
+}
+
+extern "C" int amgh_set_solve_opts(amgh_problem *p, const amgh_solve_opts *o)
+{
+    if (!p || !o) return AMGH_ERR_INVALID_ARG;
+    if (!(o->inner_tol > 0.0) || !(o->mass_tol > 0.0) || o->inner_max_iter < 1 || o->mass_max_iter < 1)
+        return AMGH_ERR_INVALID_ARG;
+    p->sopts.inner_tol = o->inner_tol;
+    p->sopts.mass_tol = o->mass_tol;
+    p->sopts.inner_max_iter = o->inner_max_iter;
+    p->sopts.mass_max_iter = o->mass_max_iter;
+    return AMGH_OK;
+}
+
+// ------------------------------------------------------------------ setup
+static void reset_hierarchy(amgh_problem *p)
+{
+    p->harena.free_all();
+    for (int l = 0; l < AMGH_MAXL; l++) {
+        p->sl[l] = StateLevel();
+        p->cl[l] = CtrlLevel();
+    }
+    p->Acoarse = Dense();
+    p->Aell = Dense();
+    p->Hcoarse = Dense();
+    p->Ls = p->Lc = p->ell = 0;
+    p->setup_done = 0;
+}
+
+static void smoother_coeffs(amgh_problem *p)
+{
+    const amgh_amg_opts &o = p->aopts;
+    p->nsteps = o.smooth_degree;
+    if (o.smoother == 0) {
+        for (int s = 0; s < p->nsteps; s++) {
+            p->cd[s] = 0.0;
+            p->cr[s] = 1.0;
+        }
+        return;
+    }
+    // Chebyshev on [1/30, 1] for D_l1^-1 A (Saad, Iterative Methods, Alg. 12.1)
+    double lo = 1.0 / 30.0, hi = 1.0;
+    double theta = (hi + lo) / 2.0, delta = (hi - lo) / 2.0, sigma = theta / delta;
+    double rho = 1.0 / sigma;
+    p->cd[0] = 0.0;
+    p->cr[0] = 1.0 / theta;
+    for (int s = 1; s < p->nsteps; s++) {
+        double rn = 1.0 / (2.0 * sigma - rho);
+        p->cd[s] = rn * rho;
+        p->cr[s] = 2.0 * rn / delta;
+        rho = rn;
+    }
+}
+
+static int dense_inverse_of(amgh_problem *p, const DevCsr &a, Dense &out)
+{
+    if (a.rows > AMGH_DENSE_MAX) return AMGH_ERR_INVALID_ARG;
+    int n = a.rows;
+    Scratch sc;
+    double *g = nullptr;
+    int *info = nullptr;
+    TRY(sc.alloc(&g, (int64_t)n * n));
+    TRY(sc.alloc(&info, 1));
+    TRY(p->harena.alloc(&out.inv, (int64_t)n * n));
+    out.n = n;
+    TRY(dense_from_csr(p, a, g));
+    return dense_spd_inverse(p, g, n, out.inv, info);
+}
+
+static int setup_impl(amgh_problem *p)
+{
+    cudaStream_t s = p->stream;
+    Arena &ar = p->harena;
+    const amgh_amg_opts &o = p->aopts;
+    // level 0: state dofs = non-Dirichlet vertices, control dofs = all vertices
+    StateLevel &S0 = p->sl[0];
+    CtrlLevel &C0 = p->cl[0];
+    TRY(extract_sub(ar, p->Kfull, p->state_of_vertex, p->m, p->state_of_vertex, p->m, S0.A, s));
+    TRY(extract_sub(ar, p->Mfull, p->state_of_vertex, p->m, p->state_of_vertex, p->m, S0.My, s));
+    TRY(extract_sub(ar, p->Mfull, p->state_of_vertex, p->m, nullptr, p->n, C0.Myu, s));
+    TRY(extract_sub(ar, p->Kfull, nullptr, p->n, nullptr, p->n, C0.KN, s));
+    TRY(extract_sub(ar, p->Mfull, nullptr, p->n, nullptr, p->n, C0.Mu, s));
+    // state hierarchy on A (theta halved per level)
+    double th = o.theta;
+    p->Ls = 1;
+    for (int l = 0; l + 1 < o.max_levels && p->sl[l].A.rows > o.coarse_max; l++) {
+        StateLevel &S = p->sl[l];
+        int n = S.A.rows;
+        TRY(ar.alloc(&S.agg, n));
+        int nagg = 0;
+        TRY(amg_aggregate(p, S.A, th * th, S.agg, &nagg));
+        if ((double)n < 1.2 * (double)nagg) break;
+        S.nagg = nagg;
+        TRY(amg_prolongator(p, ar, S.A, S.agg, nagg, o.smooth_prolongator, S.S));
+        TRY(csr_transpose(ar, S.S, S.St, s));
+        TRY(galerkin(p, ar, S.St, S.A, S.S, 1, p->sl[l + 1].A));
+        TRY(galerkin(p, ar, S.St, S.My, S.S, 1, p->sl[l + 1].My));
+        p->Ls = l + 2;
+        th = th * 0.5;
+    }
+    // control hierarchy on the all-vertex stiffness K_N
+    th = o.theta;
+    p->Lc = 1;
+    for (int l = 0; l + 1 < o.max_levels && p->cl[l].KN.rows > o.coarse_max; l++) {
+        CtrlLevel &C = p->cl[l];
+        int n = C.KN.rows;
+        TRY(ar.alloc(&C.agg, n));
+        int nagg = 0;
+        TRY(amg_aggregate(p, C.KN, th * th, C.agg, &nagg));
+        if ((double)n < 1.2 * (double)nagg) break;
+        C.nagg = nagg;
+        TRY(amg_prolongator(p, ar, C.KN, C.agg, nagg, o.smooth_prolongator, C.P));
+        TRY(csr_transpose(ar, C.P, C.Pt, s));
+        TRY(galerkin(p, ar, C.Pt, C.KN, C.P, 1, p->cl[l + 1].KN));
+        TRY(galerkin(p, ar, C.Pt, C.Mu, C.P, 1, p->cl[l + 1].Mu));
+        p->Lc = l + 2;
+        th = th * 0.5;
+    }
+    int lmin = p->Ls < p->Lc ? p->Ls : p->Lc;
+    for (int l = 0; l + 1 < lmin; l++)
+        TRY(galerkin(p, ar, p->sl[l].St, p->cl[l].Myu, p->cl[l].P, 0, p->cl[l + 1].Myu));
+    for (int l = 0; l < lmin; l++) TRY(csr_transpose(ar, p->cl[l].Myu, p->cl[l].Myut, s));
+    // SELL copies of the operators applied in the solve phase, smoother and mass diagonals
+    for (int l = 0; l < p->Ls; l++) {
+        StateLevel &S = p->sl[l];
+        TRY(csr_to_sell(ar, S.A, 1, s));
+        TRY(csr_to_sell(ar, S.My, 1, s));
+        if (l + 1 < p->Ls) {
+            TRY(csr_to_sell(ar, S.S, 1, s));
+            TRY(csr_to_sell(ar, S.St, 1, s));
+        }
+        TRY(ar.alloc(&S.invd, S.A.rows));
+        TRY(ar.alloc(&S.invd32, S.A.rows));
+        TRY(l1_invdiag(p, S.A, S.invd, S.invd32));
+    }
+    for (int l = 0; l < p->Lc; l++) {
+        CtrlLevel &C = p->cl[l];
+        TRY(csr_to_sell(ar, C.Mu, 1, s));
+        if (l + 1 < p->Lc) {
+            TRY(csr_to_sell(ar, C.P, 1, s));
+            TRY(csr_to_sell(ar, C.Pt, 1, s));
+        }
+        if (l < lmin) {
+            TRY(csr_to_sell(ar, C.Myu, 1, s));
+            TRY(csr_to_sell(ar, C.Myut, 1, s));
+        }
+        TRY(ar.alloc(&C.mu_invdiag, C.Mu.rows));
+        TRY(diag_inv(p, C.Mu, C.mu_invdiag));
+    }
+    // exact coarsest solves
+    TRY(dense_inverse_of(p, p->sl[p->Ls - 1].A, p->Acoarse));
+    p->ell = lmin;
+    if (o.hessian_levels > 0 && o.hessian_levels < p->ell) p->ell = o.hessian_levels;
+    int c = p->ell - 1;
+    const double *ainv = p->Acoarse.inv;
+    if (c != p->Ls - 1) {
+        TRY(dense_inverse_of(p, p->sl[c].A, p->Aell));
+        ainv = p->Aell.inv;
+    }
+    if (p->cl[c].Mu.rows > AMGH_DENSE_MAX) return AMGH_ERR_INVALID_ARG;
+    int nc = p->cl[c].Mu.rows;
+    TRY(ar.alloc(&p->Hcoarse.inv, (int64_t)nc * nc));
+    p->Hcoarse.n = nc;
+    TRY(dense_coarse_hessian(p, c, ainv, p->Hcoarse.inv));
+    smoother_coeffs(p);
+    TRY(solver_alloc(p));
+    CU(cudaStreamSynchronize(s));
+    return AMGH_OK;
+}
+
+extern "C" int amgh_amg_setup(amgh_problem *p, const amgh_amg_opts *opts)
+{
+    if (!p) return AMGH_ERR_INVALID_ARG;
+    amgh_amg_opts o;
+    if (opts) o = *opts;
+    else amgh_amg_opts_default(&o);
+    if (o.max_levels < 1 || o.max_levels > AMGH_MAXL || o.smooth_degree < 1 || o.smooth_degree > 16 ||
+        o.coarse_max < 1 || !(o.theta >= 0.0) || (o.smoother != 0 && o.smoother != 1) ||
+        (o.precision != 0 && o.precision != 1) || o.hessian_levels < 0)
+        return AMGH_ERR_INVALID_ARG;
+    double t0 = now_s();
+    reset_hierarchy(p);
+    p->aopts = o;
+    int st = setup_impl(p);
+    if (st) {
+        reset_hierarchy(p);
+        return st;
+    }
+    p->setup_done = 1;
+    p->t_setup = now_s() - t0;
+    return AMGH_OK;
+}
+
+// ------------------------------------------------------------------ applies
+#define NEED_SETUP(p)                          \
+    do {                                       \
+        if (!(p)) return AMGH_ERR_INVALID_ARG; \
+        if (!(p)->setup_done) return AMGH_ERR_NOT_SETUP; \
+    } while (0)
+
+extern "C" int amgh_hessian_apply(amgh_problem *p, const double *u, double *hu, int ncols)
+{
+    NEED_SETUP(p);
+    if (!u || !hu || ncols < 1) return AMGH_ERR_INVALID_ARG;
+    for (int c = 0; c < ncols; c++) TRY(hessian_level(p, 0, u + (int64_t)c * p->n, hu + (int64_t)c * p->n));
+    TRY(timer_collect(p));
+    return sync_stream(p);
+}
+
+extern "C" int amgh_precond_apply(amgh_problem *p, const double *r, double *z, int ncols)
+{
+    NEED_SETUP(p);
+    if (!r || !z || ncols < 1) return AMGH_ERR_INVALID_ARG;
+    for (int c = 0; c < ncols; c++) TRY(mlas_Q(p, 0, r + (int64_t)c * p->n, z + (int64_t)c * p->n));
+    TRY(timer_collect(p));
+    return sync_stream(p);
+}
+
+extern "C" int amgh_rhs(amgh_problem *p, double *b)
+{
+    NEED_SETUP(p);
+    if (!b) return AMGH_ERR_INVALID_ARG;
+    TRY(rhs_apply(p, b));
+    return sync_stream(p);
+}
+
+static void fill_info(amgh_problem *p, amgh_solve_info *info)
+{
+    info->hessian_applies = p->c_happ;
+    info->inner_iters = p->c_inner;
+    info->mass_iters = p->c_mass;
+    info->refinements = p->c_refine;
+    info->t_setup_s = p->t_setup;
+}
+
+extern "C" int amgh_solve(amgh_problem *p, const double *u0, double *u, double *y, const amgh_solve_opts *opts,
+                          amgh_solve_info *info)
+{
+    NEED_SETUP(p);
+    if (!u) return AMGH_ERR_INVALID_ARG;
+    amgh_solve_opts o;
+    if (opts) o = *opts;
+    else amgh_solve_opts_default(&o);
+    if (!(o.tol > 0.0) || o.max_iter < 1 || o.ncols != 1) return AMGH_ERR_INVALID_ARG;
+    TRY(amgh_set_solve_opts(p, &o));
+    p->c_inner = p->c_mass = p->c_happ = p->c_refine = 0;
+    amgh_solve_info loc;
+    memset(&loc, 0, sizeof(loc));
+    int st = outer_solve(p, u0, u, &o, &loc);
+    if (st == AMGH_OK && y) {
+        CtrlLevel &C = p->cl[0];
+        int s2 = spmv(p, C.Myu, u, C.t1, nullptr, 0);
+        if (s2 == AMGH_OK) s2 = state_solve(p, 0, C.t1, y, p->sopts.inner_tol, nullptr);
+        st = s2;
+    }
+    fill_info(p, &loc);
+    loc.status = st;
+    if (info) *info = loc;
+    int st2 = timer_collect(p);
+    if (st == AMGH_OK) st = st2;
+    if (st == AMGH_OK) st = sync_stream(p);
+    return st;
+}
+
+extern "C" int amgh_solve_host(amgh_problem *p, const double *u0_host, double *u_host, double *y_host,
+                               const amgh_solve_opts *opts, amgh_solve_info *info)
+{
+    NEED_SETUP(p);
+    if (!u_host) return AMGH_ERR_INVALID_ARG;
+    Scratch sc;
+    double *u0 = nullptr, *u = nullptr, *y = nullptr;
+    TRY(sc.alloc(&u, p->n));
+    if (u0_host) {
+        TRY(sc.alloc(&u0, p->n));
+        CU(cudaMemcpyAsync(u0, u0_host, sizeof(double) * p->n, cudaMemcpyHostToDevice, p->stream));
+    }
+    if (y_host) TRY(sc.alloc(&y, p->m));
+    int st = amgh_solve(p, u0, u, y, opts, info);
+    if (st) return st;
+    CU(cudaMemcpyAsync(u_host, u, sizeof(double) * p->n, cudaMemcpyDeviceToHost, p->stream));
+    if (y_host) CU(cudaMemcpyAsync(y_host, y, sizeof(double) * p->m, cudaMemcpyDeviceToHost, p->stream));
+    return sync_stream(p);
+}
+
+__global__ void k_sub(int n, const double *__restrict__ a, const double *__restrict__ b, double *__restrict__ c)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) c[i] = a[i] - b[i];
+}
+
+extern "C" int amgh_state_solve(amgh_problem *p, const double *u, double *y, double *J)
+{
+    NEED_SETUP(p);
+    if (!u || !y) return AMGH_ERR_INVALID_ARG;
+    CtrlLevel &C = p->cl[0];
+    StateLevel &S = p->sl[0];
+    TRY(spmv(p, C.Myu, u, C.t1, nullptr, 0));
+    TRY(state_solve(p, 0, C.t1, y, p->sopts.inner_tol, nullptr));
+    if (J) {
+        int m = p->m, n = p->n;
+        k_sub<<<ceil_div(m, 256), 256, 0, p->stream>>>(m, y, p->yd_state, C.t1);
+        LAUNCH_CHECK();
+        TRY(spmv(p, S.My, C.t1, C.t2, nullptr, 0));
+        TRY(spmv(p, C.Mu, u, p->oq, nullptr, 0));
+        TRY(vec_dot(p, p->ored, m, C.t1, C.t2, p->dscratch));
+        TRY(vec_dot(p, p->ored, n, u, p->oq, p->dscratch + 1));
+        double h[2];
+        CU(cudaMemcpyAsync(h, p->dscratch, 2 * sizeof(double), cudaMemcpyDeviceToHost, p->stream));
+        CU(cudaStreamSynchronize(p->stream));
+        *J = 0.5 * h[0] + 0.5 * p->beta * h[1];
+    }
+    return sync_stream(p);
+}
+
+extern "C" int amgh_gradient(amgh_problem *p, const double *u, const double *y, double *g)
+{
+    NEED_SETUP(p);
+    if (!u || !y || !g) return AMGH_ERR_INVALID_ARG;
+    CtrlLevel &C = p->cl[0];
+    StateLevel &S = p->sl[0];
+    int m = p->m;
+    k_sub<<<ceil_div(m, 256), 256, 0, p->stream>>>(m, y, p->yd_state, C.t1);
+    LAUNCH_CHECK();
+    TRY(spmv(p, S.My, C.t1, C.t2, nullptr, 0));
+    TRY(state_solve(p, 0, C.t2, C.ps, p->sopts.inner_tol, nullptr));
+    TRY(spmv2(p, C.Myut, C.ps, C.Mu, u, p->beta, g, nullptr));
+    return sync_stream(p);
+}
+
+// ------------------------------------------------------------------ level-wise
+extern "C" int amgh_vcycle(amgh_problem *p, int level, const double *b, double *x)
+{
+    NEED_SETUP(p);
+    if (level < 0 || level >= p->Ls || !b || !x) return AMGH_ERR_INVALID_ARG;
+    TRY(vcycle_run(p, level, 0, b, x, nullptr));
+    return sync_stream(p);
+}
+
+extern "C" int amgh_state_solve_level(amgh_problem *p, int level, const double *f, double *y, double tol,
+                                      int64_t *iters)
+{
+    NEED_SETUP(p);
+    if (level < 0 || level >= p->Ls || !f || !y || !(tol > 0.0)) return AMGH_ERR_INVALID_ARG;
+    TRY(state_solve(p, level, f, y, tol, iters));
+    return sync_stream(p);
+}
+
+extern "C" int amgh_mass_solve(amgh_problem *p, int level, const double *b, double *x, int64_t *iters)
+{
+    NEED_SETUP(p);
+    if (level < 0 || level >= p->Lc || !b || !x) return AMGH_ERR_INVALID_ARG;
+    TRY(mass_solve(p, level, b, x, iters));
+    return sync_stream(p);
+}
+
+extern "C" int amgh_hessian_apply_level(amgh_problem *p, int level, const double *v, double *hv)
+{
+    NEED_SETUP(p);
+    if (level < 0 || level >= p->ell || !v || !hv) return AMGH_ERR_INVALID_ARG;
+    TRY(hessian_level(p, level, v, hv));
+    return sync_stream(p);
+}
+
+extern "C" int amgh_precond_apply_level(amgh_problem *p, int which, int level, const double *b, double *z)
+{
+    NEED_SETUP(p);
+    if (level < 0 || level >= p->ell || !b || !z) return AMGH_ERR_INVALID_ARG;
+    if (which == 0) TRY(mlas_Q(p, level, b, z));
+    else {
+        if (level >= p->ell - 1) return AMGH_ERR_INVALID_ARG;
+        TRY(mlas_R(p, level, b, z));
+    }
+    return sync_stream(p);
+}
+
+// ------------------------------------------------------------------ queries
+extern "C" int amgh_query_sizes(const amgh_problem *p, int64_t *m, int64_t *n, int *Ls, int *Lc, int *ell,
+                                int64_t *ssz, int64_t *csz)
+{
+    if (!p) return AMGH_ERR_INVALID_ARG;
+    if (m) *m = p->m;
+    if (n) *n = p->n;
+    if (Ls) *Ls = p->Ls;
+    if (Lc) *Lc = p->Lc;
+    if (ell) *ell = p->ell;
+    for (int l = 0; l < p->Ls && ssz; l++) ssz[l] = p->sl[l].A.rows;
+    for (int l = 0; l < p->Lc && csz; l++) csz[l] = p->cl[l].Mu.rows;
+    return AMGH_OK;
+}
+
+extern "C" int amgh_get_aggregates(const amgh_problem *p, int hier, int level, int32_t *agg, int32_t *nagg)
+{
+    if (!p || !agg) return AMGH_ERR_INVALID_ARG;
+    if (!p->setup_done) return AMGH_ERR_NOT_SETUP;
+    int L = hier ? p->Lc : p->Ls;
+    if (level < 0 || level + 1 >= L) return AMGH_ERR_INVALID_ARG;
+    const int *src = hier ? p->cl[level].agg : p->sl[level].agg;
+    int rows = hier ? p->cl[level].Mu.rows : p->sl[level].A.rows;
+    CU(cudaMemcpyAsync(agg, src, sizeof(int) * rows, cudaMemcpyDeviceToHost, p->stream));
+    CU(cudaStreamSynchronize(p->stream));
+    if (nagg) *nagg = hier ? p->cl[level].nagg : p->sl[level].nagg;
+    return AMGH_OK;
+}
+
+static const DevCsr *pick(const amgh_problem *p, int which, int l)
+{
+    int lmin = p->Ls < p->Lc ? p->Ls : p->Lc;
+    if (which == 7) return &p->Kfull;
+    if (which == 8) return &p->Mfull;
+    if (!p->setup_done || l < 0 || l >= AMGH_MAXL) return nullptr;
+    switch (which) {
+    case 0: return l < p->Ls ? &p->sl[l].A : nullptr;
+    case 1: return l < p->Ls ? &p->sl[l].My : nullptr;
+    case 2: return l < lmin ? &p->cl[l].Myu : nullptr;
+    case 3: return l + 1 < p->Ls ? &p->sl[l].S : nullptr;
+    case 4: return l < p->Lc ? &p->cl[l].KN : nullptr;
+    case 5: return l < p->Lc ? &p->cl[l].Mu : nullptr;
+    case 6: return l + 1 < p->Lc ? &p->cl[l].P : nullptr;
+    }
+    return nullptr;
+}
+
+extern "C" int amgh_get_matrix_info(const amgh_problem *p, int which, int level, int64_t *rows, int64_t *cols,
+                                    int64_t *nnz)
+{
+    if (!p) return AMGH_ERR_INVALID_ARG;
+    const DevCsr *a = pick(p, which, level);
+    if (!a || !a->rp) return AMGH_ERR_INVALID_ARG;
+    if (rows) *rows = a->rows;
+    if (cols) *cols = a->cols;
+    if (nnz) *nnz = a->nnz;
+    return AMGH_OK;
+}
+
+extern "C" int amgh_get_matrix(const amgh_problem *p, int which, int level, int32_t *rp, int32_t *ci, double *v)
+{
+    if (!p || !rp || !ci || !v) return AMGH_ERR_INVALID_ARG;
+    const DevCsr *a = pick(p, which, level);
+    if (!a || !a->rp) return AMGH_ERR_INVALID_ARG;
+    CU(cudaMemcpyAsync(rp, a->rp, sizeof(int) * (a->rows + 1), cudaMemcpyDeviceToHost, p->stream));
+    CU(cudaMemcpyAsync(ci, a->ci, sizeof(int) * a->nnz, cudaMemcpyDeviceToHost, p->stream));
+    CU(cudaMemcpyAsync(v, a->v, sizeof(double) * a->nnz, cudaMemcpyDeviceToHost, p->stream));
+    CU(cudaStreamSynchronize(p->stream));
+    return AMGH_OK;
+}
+
+extern "C" int amgh_get_counters(const amgh_problem *p, amgh_solve_info *info)
+{
+    if (!p || !info) return AMGH_ERR_INVALID_ARG;
+    memset(info, 0, sizeof(*info));
+    info->hessian_applies = p->c_happ;
+    info->inner_iters = p->c_inner;
+    info->mass_iters = p->c_mass;
+    info->refinements = p->c_refine;
+    info->t_setup_s = p->t_setup;
+    return AMGH_OK;
+}
+
+extern "C" int amgh_reset_counters(amgh_problem *p)
+{
+    if (!p) return AMGH_ERR_INVALID_ARG;
+    p->c_inner = p->c_mass = p->c_happ = p->c_refine = 0;
+    return AMGH_OK;
+}
+
+extern "C" int amgh_kernel_timing(amgh_problem *p, int enable)
+{
+    if (!p) return AMGH_ERR_INVALID_ARG;
+    TRY(timer_collect(p));
+    p->timer.enabled = enable ? 1 : 0;
+    p->timer.launches = 0;
+    p->timer.ms = 0.0;
+    p->timer.bytes = 0.0;
+    return AMGH_OK;
+}
+
+extern "C" int amgh_kernel_stats(amgh_problem *p, int64_t *launches, double *ms, double *bytes)
+{
+    if (!p) return AMGH_ERR_INVALID_ARG;
+    TRY(timer_collect(p));
+    if (launches) *launches = p->timer.launches;
+    if (ms) *ms = p->timer.ms;
+    if (bytes) *bytes = p->timer.bytes;
+    return AMGH_OK;
+}
+
+extern "C" void amgh_problem_destroy(amgh_problem *p)
+{
+    if (!p) return;
+    if (p->stream) cudaStreamSynchronize(p->stream);
+    else cudaDeviceSynchronize();
+    for (auto e : p->timer.ev) cudaEventDestroy(e);
+    for (auto e : p->timer.pool) cudaEventDestroy(e);
+    p->harena.free_all();
+    p->arena.free_all();
+    if (p->h_scal) cudaFreeHost(p->h_scal);
+    delete p;
+}

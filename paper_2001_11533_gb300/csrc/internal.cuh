@@ -1,0 +1,308 @@
+// internal.cuh -- device data structures and kernel entry points shared by the
+// translation units of the amgh library (sm_103a).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "../../include/amgh.h"
+
+#define AMGH_MAXL 32
+#define AMGH_DENSE_MAX 4096
+#define AMGH_SELL_C 32
+
+// ------------------------------------------------------------------ errors
+#define CU(call)                                                               \
+    do {                                                                       \
+        cudaError_t e_ = (call);                                               \
+        if (e_ != cudaSuccess) {                                               \
+            return e_ == cudaErrorMemoryAllocation ? AMGH_ERR_OOM : AMGH_ERR_CUDA; \
+        }                                                                      \
+    } while (0)
+#define TRY(call)                 \
+    do {                          \
+        int s_ = (call);          \
+        if (s_ != AMGH_OK) return s_; \
+    } while (0)
+
+// count of kernels launched by this library (reported to callers)
+void amgh_count_launch(int n = 1);
+#define LAUNCH_CHECK()                         \
+    do {                                       \
+        amgh_count_launch();                   \
+        cudaError_t e_ = cudaGetLastError();   \
+        if (e_ != cudaSuccess) return AMGH_ERR_CUDA; \
+    } while (0)
+
+static inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
+
+// ------------------------------------------------------------------ memory
+// Every device allocation of a problem goes through an Arena so destroy frees all.
+struct Arena {
+    std::vector<void *> ptrs;
+    template <typename T>
+    int alloc(T **p, int64_t count)
+    {
+        *p = nullptr;
+        if (count <= 0) count = 1;
+        void *q = nullptr;
+        cudaError_t e = cudaMalloc(&q, (size_t)count * sizeof(T));
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return e == cudaErrorMemoryAllocation ? AMGH_ERR_OOM : AMGH_ERR_CUDA;
+        }
+        ptrs.push_back(q);
+        *p = (T *)q;
+        return AMGH_OK;
+    }
+    void release(void *q);
+    void free_all();
+};
+
+// Temporary device allocations released at scope exit.
+struct Scratch {
+    std::vector<void *> ptrs;
+    template <typename T>
+    int alloc(T **p, int64_t count)
+    {
+        *p = nullptr;
+        if (count <= 0) count = 1;
+        void *q = nullptr;
+        cudaError_t e = cudaMalloc(&q, (size_t)count * sizeof(T));
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return e == cudaErrorMemoryAllocation ? AMGH_ERR_OOM : AMGH_ERR_CUDA;
+        }
+        ptrs.push_back(q);
+        *p = (T *)q;
+        return AMGH_OK;
+    }
+    ~Scratch()
+    {
+        for (void *q : ptrs) cudaFree(q);
+    }
+};
+
+// ------------------------------------------------------------------ matrices
+// CSR with sorted columns (int32 indices, FP64 values) plus, for operators on
+// the hot path, a SELL-32 copy (slices of 32 consecutive rows, column-major
+// inside a slice so a warp's loads coalesce) in FP64 and FP32.
+struct DevCsr {
+    int rows = 0, cols = 0, nnz = 0;
+    int *rp = nullptr, *ci = nullptr;
+    double *v = nullptr;
+    // SELL-32
+    int nslices = 0, sell_nnz = 0;
+    int *sl_ptr = nullptr, *sl_ci = nullptr;
+    double *sl_v = nullptr;
+    float *sl_v32 = nullptr;
+};
+
+// ------------------------------------------------------------------ reductions
+// Deterministic two-stage reductions: every block writes a partial, the last
+// block to finish (atomic ticket) sums the partials in fixed order and runs a
+// finaliser.  Each reduction site owns its slot so tickets never mix.
+struct RedSlot {
+    double *partials = nullptr; // [capacity]
+    unsigned *ticket = nullptr;
+    int capacity = 0;
+};
+
+// device scalars of one CG loop
+struct CgScal {
+    double rz, pq, alpha, beta, rr, ff, thr; // thr = tol^2 * ff
+    double scale;                             // refinement: ||r||
+    int done, iters, status, maxit;
+    int total_iters;
+    int pad[3];
+};
+
+enum { CG_RUNNING = 0, CG_CONVERGED = 1, CG_INDEFINITE = 2, CG_NUMERIC = 3, CG_MAXIT = 4 };
+
+// ------------------------------------------------------------------ hierarchy
+struct StateLevel {
+    DevCsr A, My, S, St; // S: rows m_l, cols m_{l+1}; St = S^T
+    double *invd = nullptr;   // 1 / l1 row sums
+    float *invd32 = nullptr;
+    int *agg = nullptr;
+    int nagg = 0;
+    // V-cycle work (FP64 and FP32)
+    double *vb, *vx, *vx2, *vd, *vr;
+    float *fb, *fx, *fx2, *fd, *fr;
+    // CG work at this level (FP64): x r z p q; FP32 inner CG: same
+    double *cx, *cr, *cz, *cp, *cq;
+    float *gx, *gr, *gz, *gp, *gq;
+    double *ry; // refinement residual (FP64)
+    CgScal *scal = nullptr;  // FP64 CG loop scalars
+    CgScal *scal32 = nullptr; // FP32 inner CG loop scalars
+    CgScal *rscal = nullptr;  // refinement loop scalars
+    RedSlot red;
+};
+
+struct CtrlLevel {
+    DevCsr KN, Mu, P, Pt, Myu, Myut; // Myu: m_l x n_l (cross), Myut its transpose
+    double *mu_invdiag = nullptr;
+    int *agg = nullptr;
+    int nagg = 0;
+    // mass CG work
+    double *mx, *mr, *mz, *mp, *mq;
+    CgScal *mscal = nullptr;
+    // MLAS work
+    double *bc, *qc, *wc, *w1, *ta, *tb, *hu, *rq, *du; // n_l each (bc, qc, wc: coarse side of R_{l-1})
+    // Hessian work (state-sized at this level, and control-sized)
+    double *t1, *ys, *t2, *ps;
+    RedSlot red;
+};
+
+struct Dense {
+    int n = 0;
+    double *inv = nullptr; // explicit inverse (n x n, row-major)
+};
+
+struct KernelTimer {
+    int enabled = 0;
+    std::vector<cudaEvent_t> ev; // pairs
+    int64_t launches = 0;
+    double ms = 0.0, bytes = 0.0;
+    std::vector<double> pending_bytes;
+    std::vector<cudaEvent_t> pool;
+};
+
+struct amgh_problem {
+    int dim = 0;
+    int64_t nv = 0, ne = 0;
+    double beta = 0.0;
+    int m = 0, n = 0;
+    cudaStream_t stream = 0;
+    Arena arena;
+    // inputs on device
+    double *coords = nullptr, *kappa = nullptr, *yd_state = nullptr;
+    int *elems = nullptr;
+    unsigned char *dir = nullptr;
+    int *state_of_vertex = nullptr; // -1 for Dirichlet
+    int *vertex_of_state = nullptr;
+    DevCsr Kfull, Mfull;
+    // options
+    amgh_amg_opts aopts;
+    amgh_solve_opts sopts;
+    int setup_done = 0;
+    int Ls = 0, Lc = 0, ell = 0;
+    StateLevel sl[AMGH_MAXL];
+    CtrlLevel cl[AMGH_MAXL];
+    Dense Acoarse;  // inverse of A[Ls-1]
+    Dense Aell;     // inverse of A[ell-1] when ell-1 != Ls-1
+    Dense Hcoarse;  // inverse of H[ell-1]
+    int nsteps = 0;
+    double cd[16], cr[16];
+    // outer CG work (control-sized, level 0)
+    double *ou, *or_, *oz, *op, *oq, *ob;
+    CgScal *oscal = nullptr;
+    RedSlot ored;
+    double *dscratch = nullptr;
+    Arena harena; // hierarchy (freed on re-setup)
+    // host mirrors
+    CgScal *h_scal = nullptr; // pinned
+    // counters
+    int64_t c_inner = 0, c_mass = 0, c_happ = 0, c_refine = 0;
+    double t_setup = 0.0;
+    KernelTimer timer;
+    int chunk_hint[AMGH_MAXL];
+    int mchunk_hint[AMGH_MAXL];
+};
+
+// ------------------------------------------------------------------ sparse.cu
+int csr_to_sell(Arena &ar, DevCsr &a, int want32, cudaStream_t s);
+int csr_transpose(Arena &ar, const DevCsr &a, DevCsr &t, cudaStream_t s);
+// y = A x (FP64 or FP32 SELL)
+int spmv(amgh_problem *p, const DevCsr &a, const double *x, double *y, const int *skip, int timed);
+int spmv32(amgh_problem *p, const DevCsr &a, const float *x, float *y, const int *skip, int timed);
+// y = A1 x1 + c * A2 x2 (same row count)
+int spmv2(amgh_problem *p, const DevCsr &a1, const double *x1, const DevCsr &a2, const double *x2,
+          double c, double *y, const int *skip);
+
+template <typename T>
+struct VT;
+
+// V-cycle / smoother kernels (templated on value type, defined in sparse.cu)
+template <typename T>
+int cheb_first(amgh_problem *p, int n, const T *invd, const T *b, T *d, T *x, double c, const int *skip);
+template <typename T>
+int cheb_step(amgh_problem *p, const DevCsr &a, const T *invd, const T *b, const T *x, T *d, T *xn,
+              double cdv, double crv, const int *skip, int timed);
+template <typename T>
+int residual(amgh_problem *p, const DevCsr &a, const T *b, const T *x, T *r, const int *skip, int timed);
+template <typename T>
+int spmv_t(amgh_problem *p, const DevCsr &a, const T *x, T *y, const int *skip, int timed);
+template <typename T>
+int prolong_add(amgh_problem *p, const DevCsr &s, const T *e, T *x, const int *skip);
+template <typename T>
+int dense_gemv(amgh_problem *p, int n, const double *inv, const T *b, T *x, const int *skip);
+
+// ------------------------------------------------------------------ blas.cu
+int red_alloc(Arena &ar, RedSlot &slot, int capacity);
+// CG building blocks (device-side scalars, skip when sc->done)
+template <typename T>
+int cg_start(amgh_problem *p, RedSlot &red, int n, const T *f, T *x, T *r, CgScal *sc,
+             double tol, int maxit, int zero_x);
+template <typename T>
+int cg_rz_first(amgh_problem *p, RedSlot &red, int n, const T *r, const T *z, T *pv, CgScal *sc);
+template <typename T>
+int cg_spmv_pq(amgh_problem *p, RedSlot &red, const DevCsr &a, const T *pv, T *q, CgScal *sc, int timed);
+template <typename T>
+int cg_update(amgh_problem *p, RedSlot &red, int n, T *x, T *r, const T *pv, const T *q, CgScal *sc);
+template <typename T>
+int cg_rz_next(amgh_problem *p, RedSlot &red, int n, const T *r, const T *z, T *pv, CgScal *sc);
+int cg_jacobi(amgh_problem *p, int n, const double *invd, const double *r, double *z, const int *skip);
+int cg_pq_mass(amgh_problem *p, RedSlot &red, const DevCsr &a, const double *pv, double *q, CgScal *sc);
+// refinement loop pieces
+int ref_start(amgh_problem *p, RedSlot &red, int n, const double *f, double *y, double *r,
+              CgScal *rs, double tol, int maxit);
+int ref_to32(amgh_problem *p, RedSlot &red, int n, const double *r, float *r32, CgScal *rs);
+int ref_update(amgh_problem *p, RedSlot &red, const DevCsr &a, const double *f, double *y,
+               const float *e32, double *r, CgScal *rs);
+int vec_axpby(amgh_problem *p, int n, double a, const double *x, double b, const double *y,
+              double *out);
+int vec_fill(amgh_problem *p, int n, double v, double *x);
+int vec_dot(amgh_problem *p, RedSlot &red, int n, const double *x, const double *y, double *out_dev);
+int scatter_state(amgh_problem *p, int m, const int *vertex_of_state, const double *ys,
+                  double *full, double scale_add_beta_u, const double *u);
+
+// ------------------------------------------------------------------ assemble.cu
+int assemble_full(amgh_problem *p);
+int extract_sub(Arena &ar, const DevCsr &a, const int *rmap, int nr, const int *cmap, int nc,
+                DevCsr &out, cudaStream_t s);
+
+// ------------------------------------------------------------------ amg.cu
+int amg_aggregate(amgh_problem *p, const DevCsr &a, double theta2, int *agg, int *nagg);
+int amg_prolongator(amgh_problem *p, Arena &ar, const DevCsr &a, const int *agg, int nagg,
+                    int smooth, DevCsr &s);
+int spgemm(amgh_problem *p, Arena &ar, const DevCsr &a, const DevCsr &b, DevCsr &c);
+int symmetrize_upper(amgh_problem *p, DevCsr &c);
+int galerkin(amgh_problem *p, Arena &ar, const DevCsr &rt, const DevCsr &a, const DevCsr &pm,
+             int symmetric, DevCsr &c);
+int l1_invdiag(amgh_problem *p, const DevCsr &a, double *invd, float *invd32);
+int diag_inv(amgh_problem *p, const DevCsr &a, double *invd);
+
+// ------------------------------------------------------------------ dense.cu
+int dense_from_csr(amgh_problem *p, const DevCsr &a, double *g);
+int dense_spd_inverse(amgh_problem *p, double *g, int n, double *inv, int *info_dev);
+int dense_coarse_hessian(amgh_problem *p, int c, const double *ainv, double *hinv);
+
+// ------------------------------------------------------------------ solver.cu
+int solver_alloc(amgh_problem *p);
+int vcycle_run(amgh_problem *p, int l0, int prec32, const void *b, void *x, const int *skip);
+int state_solve(amgh_problem *p, int l, const double *f, double *y, double tol, int64_t *iters);
+int mass_solve(amgh_problem *p, int l, const double *b, double *x, int64_t *iters);
+int hessian_level(amgh_problem *p, int l, const double *v, double *hv);
+int mlas_Q(amgh_problem *p, int j, const double *b, double *u);
+int mlas_R(amgh_problem *p, int j, const double *b, double *out);
+int rhs_apply(amgh_problem *p, double *b);
+int outer_solve(amgh_problem *p, const double *u0, double *u, const amgh_solve_opts *o, amgh_solve_info *info);
+int sync_stream(amgh_problem *p);
+
+// timing of fine-level SpMV-class kernels
+void timer_begin(amgh_problem *p, int timed);
+void timer_end(amgh_problem *p, int timed, double bytes);
+int timer_collect(amgh_problem *p);

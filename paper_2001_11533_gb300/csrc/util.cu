@@ -1,0 +1,172 @@
+// util.cu -- arena, launch counting, scans and kernel timing shared by the
+// amgh translation units.
+#include <atomic>
+
+#include "internal.cuh"
+#include "util.cuh"
+
+static std::atomic<long long> g_launches{0};
+void amgh_count_launch(int n) { g_launches += n; }
+extern "C" int64_t amgh_launch_count(void) { return (int64_t)g_launches.load(); }
+
+void Arena::release(void *q)
+{
+    for (auto &x : ptrs)
+        if (x == q) {
+            cudaFree(q);
+            x = nullptr;
+        }
+}
+
+void Arena::free_all()
+{
+    for (void *q : ptrs)
+        if (q) cudaFree(q);
+    ptrs.clear();
+}
+
+// ------------------------------------------------------------------ scans
+// Exclusive prefix sum of `n` values into out[0..n] (out[n] = total), in three
+// passes: per-block sums, a single-block scan of the block sums, per-block
+// scans with the block offset.  Integer addition, so the result is exact.
+template <typename T>
+__global__ void k_scan_blocksum(const T *__restrict__ in, int64_t n, T *__restrict__ bsum)
+{
+    __shared__ T sh[1024];
+    int64_t i = (int64_t)blockIdx.x * 1024 + threadIdx.x;
+    sh[threadIdx.x] = i < n ? in[i] : (T)0;
+    __syncthreads();
+    for (int s = 512; s > 0; s >>= 1) {
+        if ((int)threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) bsum[blockIdx.x] = sh[0];
+}
+
+template <typename T>
+__global__ void k_scan_single(T *__restrict__ a, int64_t n, T *__restrict__ total)
+{
+    // one block of 1024 threads; each thread scans a contiguous chunk
+    __shared__ T sh[1024];
+    int64_t chunk = (n + 1023) / 1024;
+    int64_t beg = threadIdx.x * chunk, end = beg + chunk < n ? beg + chunk : n;
+    T s = 0;
+    for (int64_t i = beg; i < end; i++) s += a[i];
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    // Hillis-Steele inclusive scan of the 1024 chunk sums
+    for (int off = 1; off < 1024; off <<= 1) {
+        T v = (int)threadIdx.x >= off ? sh[threadIdx.x - off] : (T)0;
+        __syncthreads();
+        sh[threadIdx.x] += v;
+        __syncthreads();
+    }
+    T run = threadIdx.x ? sh[threadIdx.x - 1] : (T)0;
+    for (int64_t i = beg; i < end; i++) {
+        T v = a[i];
+        a[i] = run;
+        run += v;
+    }
+    if (threadIdx.x == 1023 && total) *total = sh[1023];
+}
+
+template <typename T>
+__global__ void k_scan_apply(const T *__restrict__ in, int64_t n, const T *__restrict__ boff,
+                             T *__restrict__ out)
+{
+    __shared__ T sh[1024];
+    int64_t i = (int64_t)blockIdx.x * 1024 + threadIdx.x;
+    T v = i < n ? in[i] : (T)0;
+    sh[threadIdx.x] = v;
+    __syncthreads();
+    for (int off = 1; off < 1024; off <<= 1) {
+        T t = (int)threadIdx.x >= off ? sh[threadIdx.x - off] : (T)0;
+        __syncthreads();
+        sh[threadIdx.x] += t;
+        __syncthreads();
+    }
+    if (i < n) out[i] = boff[blockIdx.x] + sh[threadIdx.x] - v;
+}
+
+template <typename T>
+__global__ void k_set_total(T *out, int64_t n, const T *total) { out[n] = *total; }
+
+template <typename T>
+int exclusive_scan(const T *in, T *out, int64_t n, cudaStream_t s, T *total_host)
+{
+    // out has n+1 entries; in may alias out only if in == out is not required
+    int nb = ceil_div(n > 0 ? n : 1, 1024);
+    Scratch sc;
+    T *bsum = nullptr, *tot = nullptr;
+    TRY(sc.alloc(&bsum, nb));
+    TRY(sc.alloc(&tot, 1));
+    k_scan_blocksum<T><<<nb, 1024, 0, s>>>(in, n, bsum);
+    LAUNCH_CHECK();
+    k_scan_single<T><<<1, 1024, 0, s>>>(bsum, nb, tot);
+    LAUNCH_CHECK();
+    k_scan_apply<T><<<nb, 1024, 0, s>>>(in, n, bsum, out);
+    LAUNCH_CHECK();
+    k_set_total<T><<<1, 1, 0, s>>>(out, n, tot);
+    LAUNCH_CHECK();
+    if (total_host) {
+        CU(cudaMemcpyAsync(total_host, tot, sizeof(T), cudaMemcpyDeviceToHost, s));
+        CU(cudaStreamSynchronize(s));
+    } else {
+        CU(cudaStreamSynchronize(s)); // Scratch frees bsum/tot at return
+    }
+    return AMGH_OK;
+}
+
+template int exclusive_scan<int>(const int *, int *, int64_t, cudaStream_t, int *);
+template int exclusive_scan<long long>(const long long *, long long *, int64_t, cudaStream_t,
+                                       long long *);
+
+// ------------------------------------------------------------------ timing
+// Events come from a per-problem pool so that timing a launch costs two
+// cudaEventRecord calls and no allocation.
+static cudaEvent_t pool_get(KernelTimer &t)
+{
+    if (!t.pool.empty()) {
+        cudaEvent_t e = t.pool.back();
+        t.pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    return e;
+}
+
+void timer_begin(amgh_problem *p, int timed)
+{
+    if (!timed || !p->timer.enabled) return;
+    cudaEvent_t a = pool_get(p->timer);
+    cudaEventRecord(a, p->stream);
+    p->timer.ev.push_back(a);
+}
+
+void timer_end(amgh_problem *p, int timed, double bytes)
+{
+    if (!timed || !p->timer.enabled) return;
+    cudaEvent_t b = pool_get(p->timer);
+    cudaEventRecord(b, p->stream);
+    p->timer.ev.push_back(b);
+    p->timer.pending_bytes.push_back(bytes);
+}
+
+int timer_collect(amgh_problem *p)
+{
+    KernelTimer &t = p->timer;
+    if (t.ev.empty()) return AMGH_OK;
+    CU(cudaStreamSynchronize(p->stream));
+    for (size_t k = 0; k + 1 < t.ev.size(); k += 2) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, t.ev[k], t.ev[k + 1]);
+        t.ms += ms;
+        t.launches += 1;
+        t.bytes += t.pending_bytes[k / 2];
+    }
+    for (auto e : t.ev) t.pool.push_back(e);
+    t.ev.clear();
+    t.pending_bytes.clear();
+    return AMGH_OK;
+}

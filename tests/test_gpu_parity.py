@@ -1,0 +1,358 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
+
+Bit-exact: assembled matrices, every level's Galerkin matrices and
+prolongators, and the aggregates.  Floating point: each operator within a
+tolerance derived from the solve tolerances it runs at (stated per test);
+the control u of the FP64 path within 1e-10 and of the mixed path within
+1e-8 (relative, 2-norm).
+"""
+import numpy as np
+import pytest
+
+from oracle.oracle import Oracle
+from paper_2001_11533_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+TIGHT = dict(inner_tol=1e-13, mass_tol=1e-13)
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def cuda(x):
+    torch = _torch()
+    return torch.from_numpy(np.ascontiguousarray(x, dtype=np.float64)).cuda()
+
+
+def host(t):
+    return t.detach().cpu().numpy()
+
+
+def rel(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+def _case(name):
+    if name == "sq33":
+        return W.tiny_fp64(), dict(max_levels=3, coarse_max=16)
+    if name == "lshape65":
+        return W.lshape_checkerboard(N=65), dict(coarse_max=32)
+    if name == "cube9":
+        return W.cube_grf(N=9, features=64), dict(coarse_max=16)
+    if name == "sq3":
+        return W.unit_square(3, beta=1e-2), dict()
+    raise KeyError(name)
+
+
+_CACHE = {}
+
+
+def pair(name, **extra):
+    """(workload, gpu Problem, Oracle) with the same options; cached per module."""
+    key = (name, tuple(sorted(extra.items())))
+    if key not in _CACHE:
+        from paper_2001_11533_gb300 import amgh
+        w, opts = _case(name)
+        opts = dict(opts, **extra)
+        prob = amgh.Problem.from_workload(w).amg_setup(**opts)
+        o_opts = {k: v for k, v in opts.items() if k in ("max_levels", "hessian_levels", "theta",
+                                                         "coarse_max", "smoother")}
+        if "smooth_degree" in opts:
+            o_opts["degree"] = opts["smooth_degree"]
+        if "smooth_prolongator" in opts:
+            o_opts["smooth_prolongator"] = opts["smooth_prolongator"]
+        orc = Oracle(w, **o_opts)
+        _CACHE[key] = (w, prob, orc)
+    return _CACHE[key]
+
+
+CASES = ["sq33", "lshape65", "cube9"]
+
+
+@pytest.mark.parametrize("name", CASES)
+def test_assembly_bit_exact(name):
+    w, prob, orc = pair(name)
+    for which in ("Kfull", "Mfull"):
+        g = prob.matrix(which)
+        o = orc.matrix(which)
+        for a, b in zip(g[:3], o[:3]):
+            assert np.array_equal(a, b), which
+
+
+@pytest.mark.parametrize("name", CASES)
+def test_hierarchy_bit_exact(name):
+    w, prob, orc = pair(name)
+    gs, os_ = prob.query_sizes(), orc.sizes()
+    for k in ("m", "n", "Ls", "Lc", "ell", "state", "control"):
+        assert gs[k] == os_[k], k
+    for l in range(gs["Ls"]):
+        for which in ["A", "My"] + (["S"] if l + 1 < gs["Ls"] else []):
+            g, o = prob.matrix(which, l), orc.matrix(which, l)
+            assert g[3] == o[3]
+            for a, b in zip(g[:3], o[:3]):
+                assert np.array_equal(a, b), (which, l)
+        if l + 1 < gs["Ls"]:
+            ga, gn = prob.aggregates(0, l)
+            oa, on = orc.aggregates(0, l)
+            assert gn == on and np.array_equal(ga, oa), ("state aggregates", l)
+    for l in range(gs["Lc"]):
+        for which in ["KN", "Mu"] + (["P"] if l + 1 < gs["Lc"] else []):
+            g, o = prob.matrix(which, l), orc.matrix(which, l)
+            for a, b in zip(g[:3], o[:3]):
+                assert np.array_equal(a, b), (which, l)
+        if l + 1 < gs["Lc"]:
+            ga, gn = prob.aggregates(1, l)
+            oa, on = orc.aggregates(1, l)
+            assert gn == on and np.array_equal(ga, oa), ("control aggregates", l)
+    for l in range(min(gs["Ls"], gs["Lc"])):
+        g, o = prob.matrix("Myu", l), orc.matrix("Myu", l)
+        for a, b in zip(g[:3], o[:3]):
+            assert np.array_equal(a, b), ("Myu", l)
+
+
+@pytest.mark.parametrize("name", CASES)
+def test_vcycle(name):
+    """One V-cycle is a fixed linear map: only rounding order differs (FMA,
+    reciprocal diagonal, explicit coarse inverse) -> 1e-11 relative."""
+    w, prob, orc = pair(name)
+    rng = np.random.default_rng(11)
+    for l in range(prob.sizes["Ls"]):
+        b = rng.standard_normal(prob.sizes["state"][l])
+        assert rel(host(prob.vcycle(l, cuda(b))), orc.vcycle(l, b)) <= 1e-11, l
+
+
+@pytest.mark.parametrize("name", CASES)
+def test_state_solve(name):
+    """A y = f to 1e-13 on both sides: both residuals <= 1e-13 ||f||, so the
+    difference is bounded by the conditioning; 1e-9 relative is asserted and the
+    GPU residual itself must meet the tolerance."""
+    w, prob, orc = pair(name)
+    A = orc.scipy("A", 0)
+    f = np.random.default_rng(12).standard_normal(prob.sizes["m"])
+    y, it = prob.state_solve_level(0, cuda(f), 1e-13)
+    y = host(y)
+    yo, _ = orc.state_solve(f, tol=1e-13)
+    assert np.linalg.norm(A @ y - f) <= 2e-13 * np.linalg.norm(f)
+    assert rel(y, yo) <= 1e-9
+
+
+@pytest.mark.parametrize("name", CASES)
+def test_mass_solve(name):
+    w, prob, orc = pair(name)
+    prob.set_solve_opts(**TIGHT)
+    orc.set_tols(1e-13, 1e-13)
+    for l in range(prob.sizes["Lc"]):
+        b = np.random.default_rng(13 + l).standard_normal(prob.sizes["control"][l])
+        x, _ = prob.mass_solve(l, cuda(b))
+        xo, _ = orc.mass_solve(b, level=l)
+        assert rel(host(x), xo) <= 1e-11, l
+
+
+@pytest.mark.parametrize("name", CASES)
+def test_hessian_apply(name):
+    """H u with inner solves to 1e-13 on both sides: relative 1e-10."""
+    w, prob, orc = pair(name)
+    prob.set_solve_opts(**TIGHT)
+    orc.set_tols(1e-13, 1e-13)
+    U = np.random.default_rng(14).standard_normal((3, prob.sizes["n"]))
+    for u in U:
+        assert rel(host(prob.hessian_apply(cuda(u))), orc.hessian(u)) <= 1e-10
+    for l in range(1, prob.sizes["ell"]):
+        v = np.random.default_rng(15 + l).standard_normal(prob.sizes["control"][l])
+        assert rel(host(prob.hessian_apply_level(l, cuda(v))), orc.hessian(v, level=l)) <= 1e-10, l
+    assert rel(host(prob.rhs()), orc.rhs()) <= 1e-10
+
+
+@pytest.mark.parametrize("name", CASES)
+def test_precond_apply(name):
+    """Q_0 r (Algorithm MLAS) with inner and mass solves to 1e-13: relative 1e-9."""
+    w, prob, orc = pair(name)
+    prob.set_solve_opts(**TIGHT)
+    orc.set_tols(1e-13, 1e-13)
+    r = np.random.default_rng(16).standard_normal(prob.sizes["n"])
+    assert rel(host(prob.precond_apply(cuda(r))), orc.precond(r)) <= 1e-9
+    for l in range(prob.sizes["ell"] - 1):
+        b = np.random.default_rng(17 + l).standard_normal(prob.sizes["control"][l])
+        assert rel(host(prob.precond_apply_level(1, l, cuda(b))), orc.R(b, level=l)) <= 1e-9, l
+        assert rel(host(prob.precond_apply_level(0, l, cuda(b))), orc.precond(b, level=l)) <= 1e-9, l
+
+
+@pytest.mark.parametrize("name", CASES)
+def test_solve_fp64(name):
+    """The control of the FP64 path matches the oracle to 1e-10 (outer 1e-12)."""
+    w, prob, orc = pair(name)
+    orc.set_tols(1e-13, 1e-13)
+    u, y, info = prob.solve(tol=1e-12, **TIGHT)
+    uo, yo, io = orc.solve(precond=1, tol=1e-12)
+    assert rel(host(u), uo) <= 1e-10, (info, io)
+    assert rel(host(y), yo) <= 1e-10
+    assert info["final_relres"] <= 1e-11
+    assert abs(info["outer_iters"] - io["outer_iters"]) <= 1
+
+
+@pytest.mark.parametrize("name", CASES)
+def test_solve_mixed(name):
+    """FP32 V-cycles / inner CG with FP64 refinement: control within 1e-8."""
+    w, prob, orc = pair(name, precision=1)
+    orc.set_tols(1e-13, 1e-13)
+    u, y, info = prob.solve(tol=1e-11, inner_tol=1e-12, mass_tol=1e-12)
+    uo, yo, io = orc.solve(precond=1, tol=1e-12)
+    assert rel(host(u), uo) <= 1e-8, info
+    assert rel(host(y), yo) <= 1e-8
+    assert info["refinements"] > 0
+
+
+def test_objective_and_gradient():
+    w, prob, orc = pair("lshape65")
+    prob.set_solve_opts(**TIGHT)
+    orc.set_tols(1e-13, 1e-13)
+    u = np.random.default_rng(18).standard_normal(prob.sizes["n"])
+    y, J = prob.state_solve(cuda(u))
+    g = prob.gradient(cuda(u), y)
+    Jo, yo, go = orc.objective(u)
+    assert abs(J - Jo) <= 1e-11 * abs(Jo)
+    assert rel(host(y), yo) <= 1e-10
+    assert rel(host(g), go) <= 1e-10
+
+
+def test_unpreconditioned_and_two_grid():
+    w, prob, orc = pair("sq33")
+    orc.set_tols(1e-13, 1e-13)
+    u, _, info = prob.solve(tol=1e-11, precond=0, **TIGHT)
+    uo, _, io = orc.solve(precond=0, tol=1e-11)
+    assert rel(host(u), uo) <= 1e-9
+    assert abs(info["outer_iters"] - io["outer_iters"]) <= 1
+    w2, prob2, orc2 = pair("sq33", hessian_levels=2)
+    orc2.set_tols(1e-13, 1e-13)
+    u2, _, i2 = prob2.solve(tol=1e-12, **TIGHT)
+    uo2, _, _ = orc2.solve(precond=1, tol=1e-12)
+    assert rel(host(u2), uo2) <= 1e-10
+
+
+@pytest.mark.parametrize("extra", [dict(smoother=0, smooth_degree=2), dict(smooth_prolongator=0),
+                                   dict(smooth_degree=3), dict(max_levels=1, coarse_max=1)])
+def test_options_parity(extra):
+    w, prob, orc = pair("sq33", **extra)
+    orc.set_tols(1e-13, 1e-13)
+    rp = prob.query_sizes()
+    assert rp["state"] == orc.sizes()["state"]
+    u, _, info = prob.solve(tol=1e-12, **TIGHT)
+    uo, _, _ = orc.solve(precond=1, tol=1e-12)
+    assert rel(host(u), uo) <= 1e-10, extra
+
+
+def test_tiny_one_interior_vertex():
+    w, prob, orc = pair("sq3")
+    assert prob.sizes["m"] == 1 and prob.sizes["n"] == 9
+    orc.set_tols(1e-13, 1e-13)
+    u, y, info = prob.solve(tol=1e-12, **TIGHT)
+    uo, yo, _ = orc.solve(precond=1, tol=1e-12)
+    assert rel(host(u), uo) <= 1e-10
+
+
+def test_deterministic_rerun():
+    from paper_2001_11533_gb300 import amgh
+    w, opts = _case("lshape65")
+    a = amgh.Problem.from_workload(w).amg_setup(**opts)
+    b = amgh.Problem.from_workload(w).amg_setup(**opts)
+    ua, _, _ = a.solve(tol=1e-10)
+    ub, _, _ = b.solve(tol=1e-10)
+    assert np.array_equal(host(ua), host(ub))
+
+
+def test_host_entry_point_matches_device():
+    w, prob, orc = pair("sq33")
+    ud, yd, _ = prob.solve(tol=1e-10)
+    uh, yh, info = prob.solve_host(tol=1e-10)
+    assert np.array_equal(host(ud), uh)
+    assert np.array_equal(host(yd), yh)
+
+
+def test_warm_start():
+    w, prob, orc = pair("sq33")
+    u, _, _ = prob.solve(tol=1e-12, **TIGHT)
+    u2, _, info = prob.solve(u0=u, tol=1e-10, **TIGHT)
+    assert info["outer_iters"] <= 1
+    assert rel(host(u2), host(u)) <= 1e-10
+
+
+# ---------------------------------------------------------------- error paths
+def test_errors_reported():
+    import torch
+    from paper_2001_11533_gb300 import amgh
+    w = W.unit_square(9)
+    with pytest.raises(amgh.AmghError) as e:
+        amgh.Problem(2, w.coords, w.elements, w.dirichlet, w.kappa, 0.0, w.y_d)
+    assert e.value.code == -1
+    bad = w.elements.copy()
+    bad[3, 1] = w.n_vertices + 5
+    with pytest.raises(amgh.AmghError) as e:
+        amgh.Problem(2, w.coords, bad, w.dirichlet, w.kappa, 1e-2, w.y_d)
+    assert e.value.code == -1
+    rep = w.elements.copy()
+    rep[0, 1] = rep[0, 0]
+    with pytest.raises(amgh.AmghError) as e:
+        amgh.Problem(2, w.coords, rep, w.dirichlet, w.kappa, 1e-2, w.y_d)
+    assert e.value.code == -1
+    p = amgh.Problem(2, w.coords, w.elements, w.dirichlet, w.kappa, 1e-2, w.y_d)
+    with pytest.raises(amgh.AmghError) as e:
+        p.sizes = {"n": 81, "m": 49}
+        p.hessian_apply(torch.zeros(81, dtype=torch.float64, device="cuda"))
+    assert e.value.code == -2
+    with pytest.raises(amgh.AmghError) as e:
+        p.amg_setup(max_levels=0)
+    assert e.value.code == -1
+
+
+def test_indefinite_multilevel_reported():
+    """beta = 1e-4 with a 1-dof coarsest level: W is indefinite (Sec. 3.2 caveat)."""
+    from paper_2001_11533_gb300 import amgh
+    w = W.unit_square(9, beta=1e-4, y_d="sin")
+    p = amgh.Problem.from_workload(w).amg_setup(max_levels=3, coarse_max=4)
+    with pytest.raises(amgh.AmghError) as e:
+        p.solve(tol=1e-13, **TIGHT)
+    assert e.value.code == -6
+
+
+def test_not_converged_and_nan():
+    from paper_2001_11533_gb300 import amgh
+    w = W.tiny_fp64()
+    p = amgh.Problem.from_workload(w).amg_setup(max_levels=3, coarse_max=16)
+    u, y, info = p.solve(tol=1e-12, max_iter=1, raise_on_error=False)
+    assert info["status"] == -5 and info["outer_iters"] == 1
+    yd = w.y_d.copy()
+    yd[500] = np.nan
+    p.set_yd(cuda(yd))
+    with pytest.raises(amgh.AmghError) as e:
+        p.solve(tol=1e-8)
+    assert e.value.code == -7
+
+
+# ---------------------------------------------------------------- full size
+@pytest.mark.slow
+def test_full_size_lshape_1025():
+    """The bench workload (1025^2 L-shape, 784,385 states): bit-exact level-0
+    aggregates of both hierarchies and level-1 Galerkin matrix, H u within 1e-9
+    of the oracle, and the mixed-precision solve reaching 1e-8."""
+    from paper_2001_11533_gb300 import amgh
+    w = W.lshape_checkerboard()
+    prob = amgh.Problem.from_workload(w).amg_setup()
+    orc = Oracle(w)
+    assert prob.sizes["state"] == orc.sizes()["state"]
+    for hier in (0, 1):
+        ga, gn = prob.aggregates(hier, 0)
+        oa, on = orc.aggregates(hier, 0)
+        assert gn == on and np.array_equal(ga, oa)
+    g, o = prob.matrix("A", 1), orc.matrix("A", 1)
+    for a, b in zip(g[:3], o[:3]):
+        assert np.array_equal(a, b)
+    prob.set_solve_opts(inner_tol=1e-12, mass_tol=1e-12)
+    orc.set_tols(1e-12, 1e-12)
+    u = np.random.default_rng(19).standard_normal(prob.sizes["n"])
+    assert rel(host(prob.hessian_apply(cuda(u))), orc.hessian(u)) <= 1e-9
+    pm = amgh.Problem.from_workload(w).amg_setup(precision=1)
+    _, _, info = pm.solve(tol=1e-8)
+    assert info["final_relres"] <= 1.5e-8
