@@ -336,6 +336,7 @@ __global__ void k_prol(int n, const int *__restrict__ rp, const int *__restrict_
         if (!found) {
             if (c >= MAXROW) {
                 atomicOr(bad, 1);
+                if (!prp) cnt[i] = 0;
                 return;
             }
             for (int t = c; t > pos; t--) {
@@ -408,17 +409,20 @@ int amg_prolongator(amgh_problem *p, Arena &ar, const DevCsr &a, const int *agg,
     memcpy(&rho, &hb, sizeof(double));
     if (!(rho > 0.0)) return AMGH_ERR_NUMERIC;
     double omega = 4.0 / (3.0 * rho);
-    k_prol<<<nb, 128, 0, s>>>(n, a.rp, a.ci, a.v, agg, omega, nullptr, cnt, nullptr, nullptr, bad);
+    k_prol<<<ceil_div(n, 128), 128, 0, s>>>(n, a.rp, a.ci, a.v, agg, omega, nullptr, cnt, nullptr, nullptr, bad);
     LAUNCH_CHECK();
+    int hbad = 0;
+    CU(cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
+    if (hbad) return AMGH_ERR_INVALID_ARG;
     TRY(ar.alloc(&S.rp, n + 1));
     int nnz = 0;
     TRY(exclusive_scan<int>(cnt, S.rp, n, s, &nnz));
     S.nnz = nnz;
     TRY(ar.alloc(&S.ci, nnz));
     TRY(ar.alloc(&S.v, nnz));
-    k_prol<<<nb, 128, 0, s>>>(n, a.rp, a.ci, a.v, agg, omega, S.rp, cnt, S.ci, S.v, bad);
+    k_prol<<<ceil_div(n, 128), 128, 0, s>>>(n, a.rp, a.ci, a.v, agg, omega, S.rp, cnt, S.ci, S.v, bad);
     LAUNCH_CHECK();
-    int hbad = 0;
     CU(cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
     CU(cudaStreamSynchronize(s));
     return hbad ? AMGH_ERR_INVALID_ARG : AMGH_OK;
