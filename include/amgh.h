@@ -73,7 +73,9 @@ typedef struct {
  *  smoother        0 = l1-Jacobi, 1 = Chebyshev on D_l1^-1 A over [1/30, 1]
  *  smooth_degree   Jacobi sweeps or Chebyshev degree (1..16)
  *  precision       0 = FP64 everywhere; 1 = FP32 V-cycles, smoothers and
- *                  inner CG with FP64 iterative refinement of every PDE solve
+ *                  inner CG with FP64 iterative refinement of every PDE solve;
+ *                  2 = FP64 CG for every PDE solve preconditioned by FP32
+ *                  V-cycles (FP32 smoothers, transfers and coarse solve)
  *  smooth_prolongator 1 = S = (I - omega D^-1 A) S_hat, 0 = S_hat */
 typedef struct {
     int max_levels;
@@ -235,7 +237,8 @@ int amgh_get_matrix(const amgh_problem *p, int which, int level, int32_t *rowptr
 int amgh_get_counters(const amgh_problem *p, amgh_solve_info *info);
 int amgh_reset_counters(amgh_problem *p);
 
-/* Kernel timing for roofline reporting: when enabled, every launch of the
+/* Kernel timing for roofline reporting: when enabled, CG iterations are
+ * launched kernel by kernel instead of as CUDA graphs, and every launch of the
  * fine-level (level 0) SpMV-class kernels is bracketed by CUDA events on the
  * problem's stream.  amgh_kernel_stats returns the number of timed launches,
  * their summed duration in ms, and their summed algorithmic bytes

@@ -94,6 +94,7 @@ static int create_impl(const amgh_mesh *mesh, const double *kappa, double beta, 
     amgh_amg_opts_default(&p->aopts);
     amgh_solve_opts_default(&p->sopts);
     CU(cudaHostAlloc((void **)&p->h_scal, sizeof(CgScal), cudaHostAllocDefault));
+    CU(cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking));
     int d1 = p->dim + 1;
     Arena &ar = p->arena;
     TRY(ar.alloc(&p->coords, p->nv * p->dim));
@@ -161,6 +162,7 @@ extern "C" int amgh_set_solve_opts(amgh_problem *p, const amgh_solve_opts *o)
 // ------------------------------------------------------------------ setup
 static void reset_hierarchy(amgh_problem *p)
 {
+    solver_free_graphs(p);
     p->harena.free_all();
     for (int l = 0; l < AMGH_MAXL; l++) {
         p->sl[l] = StateLevel();
@@ -322,7 +324,7 @@ extern "C" int amgh_amg_setup(amgh_problem *p, const amgh_amg_opts *opts)
     else amgh_amg_opts_default(&o);
     if (o.max_levels < 1 || o.max_levels > AMGH_MAXL || o.smooth_degree < 1 || o.smooth_degree > 16 ||
         o.coarse_max < 1 || !(o.theta >= 0.0) || (o.smoother != 0 && o.smoother != 1) ||
-        (o.precision != 0 && o.precision != 1) || o.hessian_levels < 0)
+        o.precision < 0 || o.precision > 2 || o.hessian_levels < 0)
         return AMGH_ERR_INVALID_ARG;
     double t0 = now_s();
     reset_hierarchy(p);
@@ -637,8 +639,10 @@ extern "C" void amgh_problem_destroy(amgh_problem *p)
     else cudaDeviceSynchronize();
     for (auto e : p->timer.ev) cudaEventDestroy(e);
     for (auto e : p->timer.pool) cudaEventDestroy(e);
+    solver_free_graphs(p);
     p->harena.free_all();
     p->arena.free_all();
     if (p->h_scal) cudaFreeHost(p->h_scal);
+    if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
     delete p;
 }

@@ -29,6 +29,7 @@
 
 // count of kernels launched by this library (reported to callers)
 void amgh_count_launch(int n = 1);
+void amgh_set_capturing(int on);
 #define LAUNCH_CHECK()                         \
     do {                                       \
         amgh_count_launch();                   \
@@ -122,6 +123,14 @@ struct CgScal {
 enum { CG_RUNNING = 0, CG_CONVERGED = 1, CG_INDEFINITE = 2, CG_NUMERIC = 3, CG_MAXIT = 4 };
 
 // ------------------------------------------------------------------ hierarchy
+// CUDA graphs of one CG iteration (and of the CG start after the first
+// residual), captured once per level and precision mode, replayed per
+// iteration; `nodes` is the kernel count of one replay.
+struct CgGraph {
+    cudaGraphExec_t start = nullptr, iter = nullptr;
+    int nodes_start = 0, nodes_iter = 0;
+};
+
 struct StateLevel {
     DevCsr A, My, S, St; // S: rows m_l, cols m_{l+1}; St = S^T
     double *invd = nullptr;   // 1 / l1 row sums
@@ -137,6 +146,7 @@ struct StateLevel {
     double *ry; // refinement residual (FP64)
     CgScal *scal = nullptr;  // FP64 CG loop scalars
     CgScal *scal32 = nullptr; // FP32 inner CG loop scalars
+    CgGraph graph[3];         // 0: FP64 CG, 1: FP32 inner CG, 2: FP64 CG + FP32 V-cycle
     CgScal *rscal = nullptr;  // refinement loop scalars
     RedSlot red;
 };
@@ -149,6 +159,7 @@ struct CtrlLevel {
     // mass CG work
     double *mx, *mr, *mz, *mp, *mq;
     CgScal *mscal = nullptr;
+    CgGraph mgraph;
     // MLAS work
     double *bc, *qc, *wc, *w1, *ta, *tb, *hu, *rq, *du; // n_l each (bc, qc, wc: coarse side of R_{l-1})
     // Hessian work (state-sized at this level, and control-sized)
@@ -176,6 +187,8 @@ struct amgh_problem {
     double beta = 0.0;
     int m = 0, n = 0;
     cudaStream_t stream = 0;
+    cudaStream_t cap_stream = 0; // private stream used only to capture graphs
+    int capturing = 0;
     Arena arena;
     // inputs on device
     double *coords = nullptr, *kappa = nullptr, *yd_state = nullptr;
@@ -209,6 +222,7 @@ struct amgh_problem {
     double t_setup = 0.0;
     KernelTimer timer;
     int chunk_hint[AMGH_MAXL];
+    int chunk_hint32[AMGH_MAXL];
     int mchunk_hint[AMGH_MAXL];
 };
 
@@ -292,6 +306,7 @@ int dense_coarse_hessian(amgh_problem *p, int c, const double *ainv, double *hin
 
 // ------------------------------------------------------------------ solver.cu
 int solver_alloc(amgh_problem *p);
+void solver_free_graphs(amgh_problem *p);
 int vcycle_run(amgh_problem *p, int l0, int prec32, const void *b, void *x, const int *skip);
 int state_solve(amgh_problem *p, int l, const double *f, double *y, double tol, int64_t *iters);
 int mass_solve(amgh_problem *p, int l, const double *b, double *x, int64_t *iters);

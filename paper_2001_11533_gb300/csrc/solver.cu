@@ -88,6 +88,7 @@ int solver_alloc(amgh_problem *p)
         CU(cudaMemset(S.rscal, 0, sizeof(CgScal)));
         TRY(red_alloc(ar, S.red, m));
         p->chunk_hint[l] = 8;
+        p->chunk_hint32[l] = 8;
     }
     for (int l = 0; l < p->Lc; l++) {
         CtrlLevel &C = p->cl[l];
@@ -191,48 +192,182 @@ int vcycle_run(amgh_problem *p, int l0, int prec32, const void *b, void *x, cons
     return vcyc<double>(p, l0, (const double *)b, (double *)x, skip);
 }
 
+// ------------------------------------------------------------------ graphs
+// One CG iteration (SpMV + p.q, update + r.r, the whole V-cycle, r.z, p update)
+// is captured once per level and precision mode on a private stream and then
+// replayed with cudaGraphLaunch; all its buffers and scalars are level-owned,
+// and every kernel returns at once when the loop's `done` flag is set, so the
+// host can replay a whole chunk of iterations before reading the flag back.
+template <typename F>
+static int capture(amgh_problem *p, F body, cudaGraphExec_t *exec, int *nodes)
+{
+    cudaStream_t orig = p->stream;
+    p->stream = p->cap_stream;
+    p->capturing = 1;
+    amgh_set_capturing(1);
+    cudaGraph_t g = nullptr;
+    int st = AMGH_OK;
+    if (cudaStreamBeginCapture(p->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) st = AMGH_ERR_CUDA;
+    else {
+        st = body();
+        if (cudaStreamEndCapture(p->cap_stream, &g) != cudaSuccess && st == AMGH_OK) st = AMGH_ERR_CUDA;
+    }
+    p->stream = orig;
+    p->capturing = 0;
+    amgh_set_capturing(0);
+    if (st != AMGH_OK) {
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        return st;
+    }
+    size_t n = 0;
+    cudaGraphGetNodes(g, nullptr, &n);
+    cudaError_t e = cudaGraphInstantiate(exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return AMGH_ERR_CUDA;
+    *nodes = (int)n;
+    return AMGH_OK;
+}
+
+static int replay(amgh_problem *p, cudaGraphExec_t ex, int nodes)
+{
+    CU(cudaGraphLaunch(ex, p->stream));
+    amgh_count_launch(nodes);
+    return AMGH_OK;
+}
+
+static void free_graph(CgGraph &g)
+{
+    if (g.start) cudaGraphExecDestroy(g.start);
+    if (g.iter) cudaGraphExecDestroy(g.iter);
+    g = CgGraph();
+}
+
+void solver_free_graphs(amgh_problem *p)
+{
+    for (int l = 0; l < AMGH_MAXL; l++) {
+        for (int m = 0; m < 3; m++) free_graph(p->sl[l].graph[m]);
+        free_graph(p->cl[l].mgraph);
+    }
+}
+
+// kernel timing needs one event pair per launch, so it runs without graphs
+static bool use_graphs(amgh_problem *p) { return !p->timer.enabled; }
+
 // ------------------------------------------------------------------ AMG-CG
-// PCG for A_l x = f (x, r, z, p, q of type T), preconditioned by V_l
-template <typename T>
-static int pcg_amg(amgh_problem *p, int l, const T *f, T *x, T *r, T *z, T *pv, T *q, CgScal *sc, double tol,
-                   int maxit, int64_t *iters)
+__global__ void k_d2f(int n, const double *__restrict__ a, float *__restrict__ b, const int *skip)
+{
+    if (skip && *skip) return;
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) b[i] = (float)a[i];
+}
+
+__global__ void k_f2d(int n, const float *__restrict__ a, double *__restrict__ b, const int *skip)
+{
+    if (skip && *skip) return;
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) b[i] = (double)a[i];
+}
+
+// z = V_l r with an FP32 V-cycle for FP64 vectors (precision mode 2)
+static int vprec32(amgh_problem *p, int l, const double *r, double *z, const int *skip)
 {
     StateLevel &S = p->sl[l];
     int n = S.A.rows;
-    const int *skip = &sc->done;
-    TRY(cg_start<T>(p, S.red, n, f, x, r, sc, tol, maxit, 1));
-    TRY(vcyc<T>(p, l, r, z, skip));
-    TRY(cg_rz_first<T>(p, S.red, n, r, z, pv, sc));
-    int chunk = p->chunk_hint[l] > 0 ? p->chunk_hint[l] : 4;
+    k_d2f<<<ceil_div(n, 256), 256, 0, p->stream>>>(n, r, S.fb, skip);
+    LAUNCH_CHECK();
+    TRY(vcyc<float>(p, l, S.fb, S.gz, skip));
+    k_f2d<<<ceil_div(n, 256), 256, 0, p->stream>>>(n, S.gz, z, skip);
+    LAUNCH_CHECK();
+    return AMGH_OK;
+}
+
+// mode 0: FP64 CG + FP64 V-cycle; 1: FP32 CG + FP32 V-cycle; 2: FP64 CG + FP32 V-cycle
+static int cg_body_start(amgh_problem *p, int l, int mode)
+{
+    StateLevel &S = p->sl[l];
+    int n = S.A.rows;
+    if (mode == 1) {
+        TRY(vcyc<float>(p, l, S.gr, S.gz, &S.scal32->done));
+        return cg_rz_first<float>(p, S.red, n, S.gr, S.gz, S.gp, S.scal32);
+    }
+    if (mode == 0) TRY(vcyc<double>(p, l, S.cr, S.cz, &S.scal->done));
+    else TRY(vprec32(p, l, S.cr, S.cz, &S.scal->done));
+    return cg_rz_first<double>(p, S.red, n, S.cr, S.cz, S.cp, S.scal);
+}
+
+static int cg_body_iter(amgh_problem *p, int l, int mode)
+{
+    StateLevel &S = p->sl[l];
+    int n = S.A.rows;
+    if (mode == 1) {
+        TRY(cg_spmv_pq<float>(p, S.red, S.A, S.gp, S.gq, S.scal32, l == 0));
+        TRY(cg_update<float>(p, S.red, n, S.gx, S.gr, S.gp, S.gq, S.scal32));
+        TRY(vcyc<float>(p, l, S.gr, S.gz, &S.scal32->done));
+        return cg_rz_next<float>(p, S.red, n, S.gr, S.gz, S.gp, S.scal32);
+    }
+    TRY(cg_spmv_pq<double>(p, S.red, S.A, S.cp, S.cq, S.scal, l == 0));
+    TRY(cg_update<double>(p, S.red, n, S.cx, S.cr, S.cp, S.cq, S.scal));
+    if (mode == 0) TRY(vcyc<double>(p, l, S.cr, S.cz, &S.scal->done));
+    else TRY(vprec32(p, l, S.cr, S.cz, &S.scal->done));
+    return cg_rz_next<double>(p, S.red, n, S.cr, S.cz, S.cp, S.scal);
+}
+
+// PCG for A_l x = f preconditioned by V_l; the solution is left in S.cx (FP64
+// modes) or S.gx (mode 1)
+static int pcg_run(amgh_problem *p, int l, int mode, const void *f, double tol, int maxit, int64_t *iters)
+{
+    StateLevel &S = p->sl[l];
+    int n = S.A.rows;
+    CgScal *sc = mode == 1 ? S.scal32 : S.scal;
+    if (mode == 1) TRY(cg_start<float>(p, S.red, n, (const float *)f, S.gx, S.gr, sc, tol, maxit, 1));
+    else TRY(cg_start<double>(p, S.red, n, (const double *)f, S.cx, S.cr, sc, tol, maxit, 1));
+    CgGraph &g = S.graph[mode];
+    bool gr = use_graphs(p);
+    if (gr && !g.iter) {
+        TRY(capture(p, [&] { return cg_body_start(p, l, mode); }, &g.start, &g.nodes_start));
+        TRY(capture(p, [&] { return cg_body_iter(p, l, mode); }, &g.iter, &g.nodes_iter));
+    }
+    if (gr) TRY(replay(p, g.start, g.nodes_start));
+    else TRY(cg_body_start(p, l, mode));
+    int *hint = mode == 1 ? &p->chunk_hint32[l] : &p->chunk_hint[l];
+    // first chunk: most of the previous solve's count (replays past convergence are no-ops)
+    int chunk = *hint > 1 ? (*hint * 7) / 8 : 1;
     int enq = 0;
     CgScal h;
     for (;;) {
         for (int c = 0; c < chunk; c++) {
-            TRY(cg_spmv_pq<T>(p, S.red, S.A, pv, q, sc, l == 0));
-            TRY(cg_update<T>(p, S.red, n, x, r, pv, q, sc));
-            TRY(vcyc<T>(p, l, r, z, skip));
-            TRY(cg_rz_next<T>(p, S.red, n, r, z, pv, sc));
+            if (gr) TRY(replay(p, g.iter, g.nodes_iter));
+            else TRY(cg_body_iter(p, l, mode));
         }
         enq += chunk;
         TRY(read_scal(p, sc, &h));
         if (h.done || enq > maxit + 2) break;
-        chunk = h.iters / 4 > 1 ? h.iters / 4 : 1;
+        chunk = h.iters / 8 > 1 ? h.iters / 8 : 1;
     }
-    if (h.iters > 0) p->chunk_hint[l] = h.iters;
+    if (h.iters > 0) *hint = h.iters;
     if (iters) *iters = h.iters;
     p->c_inner += h.iters;
     if (!h.done) return AMGH_ERR_NOT_CONVERGED;
     return cg_status(h);
 }
 
-// A_l y = f to relative residual tol (FP64 CG, or FP32 CG inside FP64 refinement)
+// A_l y = f to relative residual tol: FP64 CG with an FP64 (precision 0) or
+// FP32 (precision 2) V-cycle, or FP32 CG inside FP64 iterative refinement
+// (precision 1)
 int state_solve(amgh_problem *p, int l, const double *f, double *y, double tol, int64_t *iters)
 {
     StateLevel &S = p->sl[l];
-    int maxit = p->sopts.inner_max_iter;
-    if (!p->aopts.precision) return pcg_amg<double>(p, l, f, y, S.cr, S.cz, S.cp, S.cq, S.scal, tol, maxit, iters);
-    // mixed: r = f - A y in FP64, FP32 PCG on A e = r / ||r||, y += ||r|| e
     int n = S.A.rows;
+    int maxit = p->sopts.inner_max_iter;
+    int prec = p->aopts.precision;
+    if (prec != 1) {
+        int st = pcg_run(p, l, prec == 2 ? 2 : 0, f, tol, maxit, iters);
+        k_copy<double><<<ceil_div(n, 256), 256, 0, p->stream>>>(n, S.cx, y, nullptr);
+        LAUNCH_CHECK();
+        return st;
+    }
+    // r = f - A y in FP64, FP32 PCG on A e = r / ||r||, y += ||r|| e
     TRY(ref_start(p, S.red, n, f, y, S.ry, S.rscal, tol, 50));
     CgScal h;
     TRY(read_scal(p, S.rscal, &h));
@@ -241,7 +376,7 @@ int state_solve(amgh_problem *p, int l, const double *f, double *y, double tol, 
     while (!h.done) {
         TRY(ref_to32(p, S.red, n, S.ry, S.gq, S.rscal));
         int64_t it = 0;
-        int st = pcg_amg<float>(p, l, S.gq, S.gx, S.gr, S.gz, S.gp, S.gq, S.scal32, inner, maxit, &it);
+        int st = pcg_run(p, l, 1, S.gq, inner, maxit, &it);
         it_total += it;
         // FP32 CG stops at its own accuracy floor; refinement continues from there
         if (st != AMGH_OK && st != AMGH_ERR_NOT_CONVERGED) return st;
@@ -258,21 +393,30 @@ int mass_solve(amgh_problem *p, int l, const double *b, double *x, int64_t *iter
 {
     CtrlLevel &C = p->cl[l];
     int n = C.Mu.rows;
-    TRY(mass_start(p, C.red, n, b, x, C.mr, C.mz, C.mp, C.mu_invdiag, C.mscal, p->sopts.mass_tol,
+    TRY(mass_start(p, C.red, n, b, C.mx, C.mr, C.mz, C.mp, C.mu_invdiag, C.mscal, p->sopts.mass_tol,
                    p->sopts.mass_max_iter));
-    int chunk = p->mchunk_hint[l] > 0 ? p->mchunk_hint[l] : 4;
+    bool gr = use_graphs(p);
+    CgGraph &g = C.mgraph;
+    auto body = [&] { return mass_iter(p, C.red, C.Mu, C.mx, C.mr, C.mz, C.mp, C.mq, C.mu_invdiag, C.mscal); };
+    if (gr && !g.iter) TRY(capture(p, body, &g.iter, &g.nodes_iter));
+    int chunk = p->mchunk_hint[l] > 1 ? (p->mchunk_hint[l] * 7) / 8 : 1;
     int enq = 0;
     CgScal h;
     for (;;) {
-        for (int c = 0; c < chunk; c++) TRY(mass_iter(p, C.red, C.Mu, x, C.mr, C.mz, C.mp, C.mq, C.mu_invdiag, C.mscal));
+        for (int c = 0; c < chunk; c++) {
+            if (gr) TRY(replay(p, g.iter, g.nodes_iter));
+            else TRY(body());
+        }
         enq += chunk;
         TRY(read_scal(p, C.mscal, &h));
         if (h.done || enq > p->sopts.mass_max_iter + 2) break;
-        chunk = h.iters / 4 > 1 ? h.iters / 4 : 1;
+        chunk = h.iters / 8 > 1 ? h.iters / 8 : 1;
     }
     if (h.iters > 0) p->mchunk_hint[l] = h.iters;
     if (iters) *iters = h.iters;
     p->c_mass += h.iters;
+    k_copy<double><<<ceil_div(n, 256), 256, 0, p->stream>>>(n, C.mx, x, nullptr);
+    LAUNCH_CHECK();
     if (!h.done) return AMGH_ERR_NOT_CONVERGED;
     return cg_status(h);
 }

@@ -6,7 +6,13 @@
 #include "util.cuh"
 
 static std::atomic<long long> g_launches{0};
-void amgh_count_launch(int n) { g_launches += n; }
+static thread_local int g_capturing = 0;
+// launches recorded while a graph is being captured are counted per replay instead
+void amgh_count_launch(int n)
+{
+    if (!g_capturing) g_launches += n;
+}
+void amgh_set_capturing(int on) { g_capturing = on; }
 extern "C" int64_t amgh_launch_count(void) { return (int64_t)g_launches.load(); }
 
 void Arena::release(void *q)
@@ -138,7 +144,7 @@ static cudaEvent_t pool_get(KernelTimer &t)
 
 void timer_begin(amgh_problem *p, int timed)
 {
-    if (!timed || !p->timer.enabled) return;
+    if (!timed || !p->timer.enabled || p->capturing) return;
     cudaEvent_t a = pool_get(p->timer);
     cudaEventRecord(a, p->stream);
     p->timer.ev.push_back(a);
@@ -146,7 +152,7 @@ void timer_begin(amgh_problem *p, int timed)
 
 void timer_end(amgh_problem *p, int timed, double bytes)
 {
-    if (!timed || !p->timer.enabled) return;
+    if (!timed || !p->timer.enabled || p->capturing) return;
     cudaEvent_t b = pool_get(p->timer);
     cudaEventRecord(b, p->stream);
     p->timer.ev.push_back(b);
