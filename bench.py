@@ -44,6 +44,8 @@ def parse():
     ap.add_argument("--impl", default="amgh", choices=["amgh", "reference"])
     ap.add_argument("--N", type=int, default=1025, help="L-shape grid size (bench workload: 1025)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--single-step", action="store_true",
+                    help="run one untimed step of the first form (for profilers) and print its counters")
     ap.add_argument("--forms", default="mixed,fp64,refine",
                     help="mixed = FP64 CG + FP32 V-cycles; fp64; refine = FP32 CG in FP64 refinement")
     return ap.parse_args()
@@ -300,9 +302,27 @@ def run_reference(args, rank, world):
 
 
 # ------------------------------------------------------------------------- main
+def single_step(args):
+    """One step of the first form, untimed, for profilers (ncu launch lists)."""
+    import torch
+
+    from paper_2001_11533_gb300 import _build, amgh, workloads
+    _build.build()
+    w = workloads.lshape_checkerboard(N=args.N)
+    prob = amgh.Problem.from_workload(w)
+    prob.amg_setup(precision=PRECISION[args.forms.split(",")[0]])
+    u, y, info = prob.solve(tol=1e-8)
+    torch.cuda.synchronize()
+    print(json.dumps({"info": info, "levels": prob.level_counters(), "sizes": prob.sizes,
+                      "launches": amgh.launch_count()}))
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
+    if args.single_step:
+        single_step(args)
+        return
     if args.impl == "reference":
         run_reference(args, rank, world)
         return

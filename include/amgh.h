@@ -235,6 +235,11 @@ int amgh_get_matrix(const amgh_problem *p, int which, int level, int32_t *rowptr
 
 /* Counters since the last reset (fields as amgh_solve_info). */
 int amgh_get_counters(const amgh_problem *p, amgh_solve_info *info);
+
+/* CG iterations since the last reset per level (32 int64 slots each, either
+ * may be NULL): inner_host[l] = state/adjoint AMG-CG iterations on level l,
+ * mass_host[l] = mass-matrix CG iterations on control level l. */
+int amgh_get_level_counters(const amgh_problem *p, int64_t *inner_host, int64_t *mass_host);
 int amgh_reset_counters(amgh_problem *p);
 
 /* Kernel timing for roofline reporting: when enabled, CG iterations are

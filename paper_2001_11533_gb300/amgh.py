@@ -81,6 +81,7 @@ _SIGS = {
     "amgh_get_matrix": ([_P, _I, _I, _P, _P, _P], _I),
     "amgh_get_counters": ([_P, _P], _I),
     "amgh_reset_counters": ([_P], _I),
+    "amgh_get_level_counters": ([_P, _P, _P], _I),
     "amgh_kernel_timing": ([_P, _I], _I),
     "amgh_kernel_stats": ([_P, _P, _P, _P], _I),
     "amgh_launch_count": ([], _I64),
@@ -332,6 +333,12 @@ class Problem:
         info = amgh_solve_info()
         check(lib().amgh_get_counters(self.h, C.byref(info)), "amgh_get_counters")
         return info.as_dict()
+
+    def level_counters(self):
+        a = np.zeros(32, dtype=np.int64)
+        b = np.zeros(32, dtype=np.int64)
+        check(lib().amgh_get_level_counters(self.h, _ptr(a), _ptr(b)), "amgh_get_level_counters")
+        return {"inner": a[:self.sizes["Ls"]].tolist(), "mass": b[:self.sizes["Lc"]].tolist()}
 
     def reset_counters(self):
         check(lib().amgh_reset_counters(self.h), "amgh_reset_counters")

@@ -8,6 +8,8 @@
 #include "internal.cuh"
 #include "util.cuh"
 
+static void zero_counters(amgh_problem *p);
+
 static double now_s()
 {
     using namespace std::chrono;
@@ -125,6 +127,7 @@ extern "C" int amgh_problem_create(const amgh_mesh *mesh, const double *kappa, d
     if (!(beta > 0.0) || isinf(beta)) return AMGH_ERR_INVALID_ARG;
     amgh_problem *p = new (std::nothrow) amgh_problem();
     if (!p) return AMGH_ERR_OOM;
+    zero_counters(p);
     int st = create_impl(mesh, kappa, beta, y_d, y_d_on_device, p);
     if (st) {
         amgh_problem_destroy(p);
@@ -391,7 +394,7 @@ extern "C" int amgh_solve(amgh_problem *p, const double *u0, double *u, double *
     else amgh_solve_opts_default(&o);
     if (!(o.tol > 0.0) || o.max_iter < 1 || o.ncols != 1) return AMGH_ERR_INVALID_ARG;
     TRY(amgh_set_solve_opts(p, &o));
-    p->c_inner = p->c_mass = p->c_happ = p->c_refine = 0;
+    zero_counters(p);
     amgh_solve_info loc;
     memset(&loc, 0, sizeof(loc));
     int st = outer_solve(p, u0, u, &o, &loc);
@@ -604,10 +607,26 @@ extern "C" int amgh_get_counters(const amgh_problem *p, amgh_solve_info *info)
     return AMGH_OK;
 }
 
+static void zero_counters(amgh_problem *p)
+{
+    p->c_inner = p->c_mass = p->c_happ = p->c_refine = 0;
+    for (int l = 0; l < AMGH_MAXL; l++) p->c_inner_lvl[l] = p->c_mass_lvl[l] = 0;
+}
+
 extern "C" int amgh_reset_counters(amgh_problem *p)
 {
     if (!p) return AMGH_ERR_INVALID_ARG;
-    p->c_inner = p->c_mass = p->c_happ = p->c_refine = 0;
+    zero_counters(p);
+    return AMGH_OK;
+}
+
+extern "C" int amgh_get_level_counters(const amgh_problem *p, int64_t *inner, int64_t *mass)
+{
+    if (!p) return AMGH_ERR_INVALID_ARG;
+    for (int l = 0; l < AMGH_MAXL; l++) {
+        if (inner) inner[l] = p->c_inner_lvl[l];
+        if (mass) mass[l] = p->c_mass_lvl[l];
+    }
     return AMGH_OK;
 }
 

@@ -67,6 +67,7 @@ __device__ void cg_finalize(int mode, const double *t, CgScal *sc, double *out)
         }
         if (mode == F_MASS_START && !sc->done) {
             sc->rz = t[1];
+            sc->beta = 0.0;
             if (!(t[1] > 0.0)) {
                 sc->status = bad(t[1]) ? CG_NUMERIC : CG_INDEFINITE;
                 sc->done = 1;
@@ -76,6 +77,7 @@ __device__ void cg_finalize(int mode, const double *t, CgScal *sc, double *out)
     }
     case F_RZ_FIRST:
         sc->rz = t[0];
+        sc->beta = 0.0;
         if (!(t[0] > 0.0)) {
             sc->status = bad(t[0]) ? CG_NUMERIC : CG_INDEFINITE;
             sc->done = 1;
@@ -184,10 +186,10 @@ __global__ void k_cg_start(int n, const T *__restrict__ f, T *__restrict__ x, T 
     if (reduce_last_block<1>(v, partials, ticket, tot)) cg_finalize(mode, tot, sc, nullptr);
 }
 
-// mass CG start: x = 0, r = f, z = invd r, p = z; reduce f.f and r.z
+// mass CG start: x = 0, r = f, z = invd r; reduce f.f and r.z (beta = 0)
 __global__ void k_mass_start(int n, const double *__restrict__ f, double *__restrict__ x, double *__restrict__ r,
-                             double *__restrict__ z, double *__restrict__ pv, const double *__restrict__ invd,
-                             CgScal *sc, double *partials, unsigned *ticket)
+                             double *__restrict__ z, const double *__restrict__ invd, CgScal *sc, double *partials,
+                             unsigned *ticket)
 {
     double v[2] = {0.0, 0.0}, tot[2];
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
@@ -196,11 +198,67 @@ __global__ void k_mass_start(int n, const double *__restrict__ f, double *__rest
         r[i] = fi;
         x[i] = 0.0;
         z[i] = zi;
-        pv[i] = zi;
         v[0] += fi * fi;
         v[1] += fi * zi;
     }
     if (reduce_last_block<2>(v, partials, ticket, tot)) cg_finalize(F_MASS_START, tot, sc, nullptr);
+}
+
+// inner CG r.z without touching p (the p update is fused into the next SpMV)
+template <typename T>
+__global__ void k_rz_only(int n, const T *__restrict__ r, const T *__restrict__ z, CgScal *sc, int mode,
+                          double *partials, unsigned *ticket)
+{
+    SKIP_DONE();
+    double v[1] = {0.0}, tot[1];
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        v[0] += (double)r[i] * (double)z[i];
+    if (reduce_last_block<1>(v, partials, ticket, tot)) cg_finalize(mode, tot, sc, nullptr);
+}
+
+// z64 = z32 and r.z (FP32 V-cycle inside FP64 CG)
+__global__ void k_f2d_rz(int n, const float *__restrict__ z32, double *__restrict__ z, const double *__restrict__ r,
+                         CgScal *sc, int mode, double *partials, unsigned *ticket)
+{
+    SKIP_DONE();
+    double v[1] = {0.0}, tot[1];
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        double zi = (double)z32[i];
+        z[i] = zi;
+        v[0] += r[i] * zi;
+    }
+    if (reduce_last_block<1>(v, partials, ticket, tot)) cg_finalize(mode, tot, sc, nullptr);
+}
+
+// p_out = z + beta p_in (p_out = z when beta = 0) and q = A p_out, reduce p.q -> alpha
+template <typename T>
+__global__ void k_spmv_pq_xpay(int rows, const int *__restrict__ slp, const int *__restrict__ sci,
+                               const T *__restrict__ sv, const T *__restrict__ z, const T *__restrict__ pin,
+                               T *__restrict__ pout, T *__restrict__ q, CgScal *sc, double *partials,
+                               unsigned *ticket)
+{
+    SKIP_DONE();
+    T b = (T)sc->beta;
+    bool first = sc->beta == 0.0;
+    double v[1] = {0.0}, tot[1];
+    int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r < rows) {
+        int s = r >> 5, lane = r & 31;
+        T acc = (T)0;
+        if (first) {
+            for (int k = slp[s] + lane; k < slp[s + 1]; k += 32) acc += sv[k] * __ldg(&z[sci[k]]);
+        } else {
+            for (int k = slp[s] + lane; k < slp[s + 1]; k += 32) {
+                int c = sci[k];
+                acc += sv[k] * (__ldg(&z[c]) + b * __ldg(&pin[c]));
+            }
+        }
+        T pr = first ? z[r] : z[r] + b * pin[r];
+        pout[r] = pr;
+        q[r] = acc;
+        v[0] = (double)pr * (double)acc;
+    }
+    if (reduce_last_block<1>(v, partials, ticket, tot)) cg_finalize(F_PQ, tot, sc, nullptr);
 }
 
 // rz = r.z and p = z (first iteration) or beta from rz (later)
@@ -227,29 +285,11 @@ __global__ void k_xpay(int n, const T *__restrict__ z, T *__restrict__ pv, const
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) pv[i] = z[i] + b * pv[i];
 }
 
-// q = A p (SELL-32), reduce p.q -> alpha
-template <typename T>
-__global__ void k_spmv_pq(int rows, const int *__restrict__ slp, const int *__restrict__ sci,
-                          const T *__restrict__ sv, const T *__restrict__ pv, T *__restrict__ q, CgScal *sc,
-                          double *partials, unsigned *ticket)
-{
-    SKIP_DONE();
-    double v[1] = {0.0}, tot[1];
-    int r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r < rows) {
-        int s = r >> 5, lane = r & 31;
-        T acc = (T)0;
-        for (int k = slp[s] + lane; k < slp[s + 1]; k += 32) acc += sv[k] * __ldg(&pv[sci[k]]);
-        q[r] = acc;
-        v[0] = (double)pv[r] * (double)acc;
-    }
-    if (reduce_last_block<1>(v, partials, ticket, tot)) cg_finalize(F_PQ, tot, sc, nullptr);
-}
-
-// x += alpha p, r -= alpha q, reduce r.r -> stop test
+// x += alpha p, r -= alpha q (and r32 = r when given), reduce r.r -> stop test
 template <typename T>
 __global__ void k_update(int n, T *__restrict__ x, T *__restrict__ r, const T *__restrict__ pv,
-                         const T *__restrict__ q, CgScal *sc, double *partials, unsigned *ticket)
+                         const T *__restrict__ q, CgScal *sc, float *__restrict__ r32, double *partials,
+                         unsigned *ticket)
 {
     SKIP_DONE();
     T a = (T)sc->alpha;
@@ -258,6 +298,7 @@ __global__ void k_update(int n, T *__restrict__ x, T *__restrict__ r, const T *_
         x[i] = x[i] + a * pv[i];
         T ri = r[i] - a * q[i];
         r[i] = ri;
+        if (r32) r32[i] = (float)ri;
         v[0] += (double)ri * (double)ri;
     }
     if (reduce_last_block<1>(v, partials, ticket, tot)) cg_finalize(F_RR, tot, sc, nullptr);
@@ -372,73 +413,81 @@ int cg_start(amgh_problem *p, RedSlot &red, int n, const T *f, T *x, T *r, CgSca
 }
 
 template <typename T>
-int cg_rz_first(amgh_problem *p, RedSlot &red, int n, const T *r, const T *z, T *pv, CgScal *sc)
+int cg_rz_first(amgh_problem *p, RedSlot &red, int n, const T *r, const T *z, CgScal *sc)
 {
-    k_rz<T><<<vec_blocks(n), TPB, 0, p->stream>>>(n, r, z, pv, sc, 1, red.partials, red.ticket);
+    k_rz_only<T><<<vec_blocks(n), TPB, 0, p->stream>>>(n, r, z, sc, F_RZ_FIRST, red.partials, red.ticket);
     LAUNCH_CHECK();
     return AMGH_OK;
 }
 
 template <typename T>
-int cg_spmv_pq(amgh_problem *p, RedSlot &red, const DevCsr &a, const T *pv, T *q, CgScal *sc, int timed)
+int cg_spmv_pq_xpay(amgh_problem *p, RedSlot &red, const DevCsr &a, const T *z, const T *pin, T *pout, T *q,
+                    CgScal *sc, int timed)
 {
     const T *sv;
     if (sizeof(T) == 8) sv = (const T *)a.sl_v;
     else sv = (const T *)a.sl_v32;
     timer_begin(p, timed);
-    k_spmv_pq<T><<<ceil_div(a.rows, TPB), TPB, 0, p->stream>>>(a.rows, a.sl_ptr, a.sl_ci, sv, pv, q, sc,
-                                                               red.partials, red.ticket);
+    k_spmv_pq_xpay<T><<<ceil_div(a.rows, TPB), TPB, 0, p->stream>>>(a.rows, a.sl_ptr, a.sl_ci, sv, z, pin, pout, q,
+                                                                    sc, red.partials, red.ticket);
     LAUNCH_CHECK();
+    // matrix + gathers of z and p_in + writes of p_out and q
     timer_end(p, timed,
-              (double)a.nnz * (sizeof(T) + 4) + 4.0 * (a.rows + 1) + (double)sizeof(T) * (a.rows + a.cols));
+              (double)a.nnz * (sizeof(T) + 4) + 4.0 * (a.rows + 1) + (double)sizeof(T) * (2.0 * a.cols + 2.0 * a.rows));
     return AMGH_OK;
 }
 
 template <typename T>
-int cg_update(amgh_problem *p, RedSlot &red, int n, T *x, T *r, const T *pv, const T *q, CgScal *sc)
+int cg_update(amgh_problem *p, RedSlot &red, int n, T *x, T *r, const T *pv, const T *q, CgScal *sc, float *r32)
 {
-    k_update<T><<<vec_blocks(n), TPB, 0, p->stream>>>(n, x, r, pv, q, sc, red.partials, red.ticket);
+    k_update<T><<<vec_blocks(n), TPB, 0, p->stream>>>(n, x, r, pv, q, sc, r32, red.partials, red.ticket);
     LAUNCH_CHECK();
     return AMGH_OK;
 }
 
 template <typename T>
-int cg_rz_next(amgh_problem *p, RedSlot &red, int n, const T *r, const T *z, T *pv, CgScal *sc)
+int cg_rz_next(amgh_problem *p, RedSlot &red, int n, const T *r, const T *z, CgScal *sc)
 {
-    k_rz<T><<<vec_blocks(n), TPB, 0, p->stream>>>(n, r, z, pv, sc, 0, red.partials, red.ticket);
+    k_rz_only<T><<<vec_blocks(n), TPB, 0, p->stream>>>(n, r, z, sc, F_RZ_NEXT, red.partials, red.ticket);
     LAUNCH_CHECK();
-    k_xpay<T><<<vec_blocks(n), TPB, 0, p->stream>>>(n, z, pv, sc);
+    return AMGH_OK;
+}
+
+int cg_f2d_rz(amgh_problem *p, RedSlot &red, int n, const float *z32, double *z, const double *r, CgScal *sc,
+              int first)
+{
+    k_f2d_rz<<<vec_blocks(n), TPB, 0, p->stream>>>(n, z32, z, r, sc, first ? F_RZ_FIRST : F_RZ_NEXT, red.partials,
+                                                    red.ticket);
     LAUNCH_CHECK();
     return AMGH_OK;
 }
 
 #define INST(T)                                                                                              \
     template int cg_start<T>(amgh_problem *, RedSlot &, int, const T *, T *, T *, CgScal *, double, int, int); \
-    template int cg_rz_first<T>(amgh_problem *, RedSlot &, int, const T *, const T *, T *, CgScal *);         \
-    template int cg_spmv_pq<T>(amgh_problem *, RedSlot &, const DevCsr &, const T *, T *, CgScal *, int);     \
-    template int cg_update<T>(amgh_problem *, RedSlot &, int, T *, T *, const T *, const T *, CgScal *);      \
-    template int cg_rz_next<T>(amgh_problem *, RedSlot &, int, const T *, const T *, T *, CgScal *);
+    template int cg_rz_first<T>(amgh_problem *, RedSlot &, int, const T *, const T *, CgScal *);              \
+    template int cg_spmv_pq_xpay<T>(amgh_problem *, RedSlot &, const DevCsr &, const T *, const T *, T *, T *,  \
+                                    CgScal *, int);                                                          \
+    template int cg_update<T>(amgh_problem *, RedSlot &, int, T *, T *, const T *, const T *, CgScal *, float *); \
+    template int cg_rz_next<T>(amgh_problem *, RedSlot &, int, const T *, const T *, CgScal *);
 INST(double)
 INST(float)
 
 // mass CG pieces
 int mass_start(amgh_problem *p, RedSlot &red, int n, const double *f, double *x, double *r, double *z,
-               double *pv, const double *invd, CgScal *sc, double tol, int maxit)
+               const double *invd, CgScal *sc, double tol, int maxit)
 {
     TRY(set_scal(p, sc, tol, maxit));
-    k_mass_start<<<vec_blocks(n), TPB, 0, p->stream>>>(n, f, x, r, z, pv, invd, sc, red.partials, red.ticket);
+    k_mass_start<<<vec_blocks(n), TPB, 0, p->stream>>>(n, f, x, r, z, invd, sc, red.partials, red.ticket);
     LAUNCH_CHECK();
     return AMGH_OK;
 }
 
-int mass_iter(amgh_problem *p, RedSlot &red, const DevCsr &M, double *x, double *r, double *z, double *pv,
-              double *q, const double *invd, CgScal *sc)
+int mass_iter(amgh_problem *p, RedSlot &red, const DevCsr &M, double *x, double *r, double *z, const double *pin,
+              double *pout, double *q, const double *invd, CgScal *sc)
 {
     int n = M.rows;
-    TRY(cg_spmv_pq<double>(p, red, M, pv, q, sc, 0));
-    k_mass_update<<<vec_blocks(n), TPB, 0, p->stream>>>(n, x, r, z, pv, q, invd, sc, red.partials, red.ticket);
-    LAUNCH_CHECK();
-    k_xpay<double><<<vec_blocks(n), TPB, 0, p->stream>>>(n, z, pv, sc);
+    TRY(cg_spmv_pq_xpay<double>(p, red, M, z, pin, pout, q, sc, 0));
+    k_mass_update<<<vec_blocks(n), TPB, 0, p->stream>>>(n, x, r, z, pout, q, invd, sc, red.partials, red.ticket);
     LAUNCH_CHECK();
     return AMGH_OK;
 }

@@ -127,8 +127,8 @@ enum { CG_RUNNING = 0, CG_CONVERGED = 1, CG_INDEFINITE = 2, CG_NUMERIC = 3, CG_M
 // residual), captured once per level and precision mode, replayed per
 // iteration; `nodes` is the kernel count of one replay.
 struct CgGraph {
-    cudaGraphExec_t start = nullptr, iter = nullptr;
-    int nodes_start = 0, nodes_iter = 0;
+    cudaGraphExec_t start = nullptr, iter[2] = {nullptr, nullptr}; // iter[k]: p ping-pong parity k
+    int nodes_start = 0, nodes_iter[2] = {0, 0};
 };
 
 struct StateLevel {
@@ -141,8 +141,8 @@ struct StateLevel {
     double *vb, *vx, *vx2, *vd, *vr;
     float *fb, *fx, *fx2, *fd, *fr;
     // CG work at this level (FP64): x r z p q; FP32 inner CG: same
-    double *cx, *cr, *cz, *cp, *cq;
-    float *gx, *gr, *gz, *gp, *gq;
+    double *cx, *cr, *cz, *cp, *cq, *cp2; // cp/cp2: search direction ping-pong
+    float *gx, *gr, *gz, *gp, *gq, *gp2;
     double *ry; // refinement residual (FP64)
     CgScal *scal = nullptr;  // FP64 CG loop scalars
     CgScal *scal32 = nullptr; // FP32 inner CG loop scalars
@@ -157,7 +157,7 @@ struct CtrlLevel {
     int *agg = nullptr;
     int nagg = 0;
     // mass CG work
-    double *mx, *mr, *mz, *mp, *mq;
+    double *mx, *mr, *mz, *mp, *mq, *mp2;
     CgScal *mscal = nullptr;
     CgGraph mgraph;
     // MLAS work
@@ -219,6 +219,7 @@ struct amgh_problem {
     CgScal *h_scal = nullptr; // pinned
     // counters
     int64_t c_inner = 0, c_mass = 0, c_happ = 0, c_refine = 0;
+    int64_t c_inner_lvl[AMGH_MAXL], c_mass_lvl[AMGH_MAXL];
     double t_setup = 0.0;
     KernelTimer timer;
     int chunk_hint[AMGH_MAXL];
@@ -250,6 +251,9 @@ int residual(amgh_problem *p, const DevCsr &a, const T *b, const T *x, T *r, con
 template <typename T>
 int spmv_t(amgh_problem *p, const DevCsr &a, const T *x, T *y, const int *skip, int timed);
 template <typename T>
+int restrict_first(amgh_problem *p, const DevCsr &st, const T *r, T *bc, const T *invd_c, T *d_c, T *x_c,
+                   double c0, const int *skip);
+template <typename T>
 int prolong_add(amgh_problem *p, const DevCsr &s, const T *e, T *x, const int *skip);
 template <typename T>
 int dense_gemv(amgh_problem *p, int n, const double *inv, const T *b, T *x, const int *skip);
@@ -261,15 +265,17 @@ template <typename T>
 int cg_start(amgh_problem *p, RedSlot &red, int n, const T *f, T *x, T *r, CgScal *sc,
              double tol, int maxit, int zero_x);
 template <typename T>
-int cg_rz_first(amgh_problem *p, RedSlot &red, int n, const T *r, const T *z, T *pv, CgScal *sc);
+int cg_rz_first(amgh_problem *p, RedSlot &red, int n, const T *r, const T *z, CgScal *sc);
 template <typename T>
-int cg_spmv_pq(amgh_problem *p, RedSlot &red, const DevCsr &a, const T *pv, T *q, CgScal *sc, int timed);
+int cg_spmv_pq_xpay(amgh_problem *p, RedSlot &red, const DevCsr &a, const T *z, const T *pin, T *pout, T *q,
+                    CgScal *sc, int timed);
 template <typename T>
-int cg_update(amgh_problem *p, RedSlot &red, int n, T *x, T *r, const T *pv, const T *q, CgScal *sc);
+int cg_update(amgh_problem *p, RedSlot &red, int n, T *x, T *r, const T *pv, const T *q, CgScal *sc,
+              float *r32 = nullptr);
 template <typename T>
-int cg_rz_next(amgh_problem *p, RedSlot &red, int n, const T *r, const T *z, T *pv, CgScal *sc);
-int cg_jacobi(amgh_problem *p, int n, const double *invd, const double *r, double *z, const int *skip);
-int cg_pq_mass(amgh_problem *p, RedSlot &red, const DevCsr &a, const double *pv, double *q, CgScal *sc);
+int cg_rz_next(amgh_problem *p, RedSlot &red, int n, const T *r, const T *z, CgScal *sc);
+int cg_f2d_rz(amgh_problem *p, RedSlot &red, int n, const float *z32, double *z, const double *r, CgScal *sc,
+              int first);
 // refinement loop pieces
 int ref_start(amgh_problem *p, RedSlot &red, int n, const double *f, double *y, double *r,
               CgScal *rs, double tol, int maxit);

@@ -19,10 +19,10 @@
 #include "util.cuh"
 
 // pieces from blas.cu without a template
-int mass_start(amgh_problem *p, RedSlot &red, int n, const double *f, double *x, double *r, double *z, double *pv,
+int mass_start(amgh_problem *p, RedSlot &red, int n, const double *f, double *x, double *r, double *z,
                const double *invd, CgScal *sc, double tol, int maxit);
-int mass_iter(amgh_problem *p, RedSlot &red, const DevCsr &M, double *x, double *r, double *z, double *pv,
-              double *q, const double *invd, CgScal *sc);
+int mass_iter(amgh_problem *p, RedSlot &red, const DevCsr &M, double *x, double *r, double *z, const double *pin,
+              double *pout, double *q, const double *invd, CgScal *sc);
 int outer_pq(amgh_problem *p, RedSlot &red, int n, const double *pv, const double *q, CgScal *sc);
 int outer_rz(amgh_problem *p, RedSlot &red, int n, const double *r, const double *z, double *pv, CgScal *sc,
              int first);
@@ -74,6 +74,8 @@ int solver_alloc(amgh_problem *p)
         TRY(ar.alloc(&S.cz, m));
         TRY(ar.alloc(&S.cp, m));
         TRY(ar.alloc(&S.cq, m));
+        TRY(ar.alloc(&S.cp2, m));
+        TRY(ar.alloc(&S.gp2, m));
         TRY(ar.alloc(&S.gx, m));
         TRY(ar.alloc(&S.gr, m));
         TRY(ar.alloc(&S.gz, m));
@@ -94,7 +96,7 @@ int solver_alloc(amgh_problem *p)
         CtrlLevel &C = p->cl[l];
         int n = C.Mu.rows;
         int m = l < p->Ls ? p->sl[l].A.rows : 1;
-        double **vn[] = {&C.mx, &C.mr, &C.mz, &C.mp, &C.mq, &C.bc, &C.qc, &C.wc,
+        double **vn[] = {&C.mx, &C.mr, &C.mz, &C.mp, &C.mq, &C.mp2, &C.bc, &C.qc, &C.wc,
                          &C.w1, &C.ta, &C.tb, &C.hu, &C.rq, &C.du};
         for (double **q : vn) TRY(ar.alloc(q, n));
         double **vm[] = {&C.t1, &C.ys, &C.t2, &C.ps};
@@ -145,9 +147,11 @@ __global__ void k_copy(int n, const T *__restrict__ a, T *__restrict__ b, const 
     if (i < n) b[i] = a[i];
 }
 
-// x = V_l b from x = 0; x and b must not alias level-l internal buffers
+// x = V_l b from x = 0; x and b must not alias level-l internal buffers.
+// preinit: the caller already wrote the first smoother step (d and the
+// level's alternate x buffer) while restricting.
 template <typename T>
-static int vcyc(amgh_problem *p, int l, const T *b, T *x, const int *skip)
+static int vcyc(amgh_problem *p, int l, const T *b, T *x, const int *skip, int preinit = 0)
 {
     StateLevel &S = p->sl[l];
     int n = S.A.rows;
@@ -158,7 +162,7 @@ static int vcyc(amgh_problem *p, int l, const T *b, T *x, const int *skip)
     const T *invd = VBuf<T>::invd(S);
     T *cur = tmp, *nxt = x;
     // pre-smoothing from zero
-    TRY(cheb_first<T>(p, n, invd, b, d, cur, p->cr[0], skip));
+    if (!preinit) TRY(cheb_first<T>(p, n, invd, b, d, cur, p->cr[0], skip));
     for (int s = 1; s < p->nsteps; s++) {
         TRY(cheb_step<T>(p, S.A, invd, b, cur, d, nxt, p->cd[s], p->cr[s], skip, timed));
         T *t = cur;
@@ -169,8 +173,13 @@ static int vcyc(amgh_problem *p, int l, const T *b, T *x, const int *skip)
     TRY(residual<T>(p, S.A, b, cur, r, skip, timed));
     StateLevel &Sc = p->sl[l + 1];
     T *bc = VBuf<T>::b(Sc), *xc = VBuf<T>::x(Sc);
-    TRY(spmv_t<T>(p, S.St, r, bc, skip, 0));
-    TRY(vcyc<T>(p, l + 1, bc, xc, skip));
+    if (l + 1 < p->Ls - 1) {
+        TRY(restrict_first<T>(p, S.St, r, bc, VBuf<T>::invd(Sc), VBuf<T>::d(Sc), VBuf<T>::x2(Sc), p->cr[0], skip));
+        TRY(vcyc<T>(p, l + 1, bc, xc, skip, 1));
+    } else {
+        TRY(spmv_t<T>(p, S.St, r, bc, skip, 0));
+        TRY(vcyc<T>(p, l + 1, bc, xc, skip));
+    }
     TRY(prolong_add<T>(p, S.S, xc, cur, skip));
     // post-smoothing with the same polynomial
     for (int s = 0; s < p->nsteps; s++) {
@@ -239,7 +248,8 @@ static int replay(amgh_problem *p, cudaGraphExec_t ex, int nodes)
 static void free_graph(CgGraph &g)
 {
     if (g.start) cudaGraphExecDestroy(g.start);
-    if (g.iter) cudaGraphExecDestroy(g.iter);
+    for (int k = 0; k < 2; k++)
+        if (g.iter[k]) cudaGraphExecDestroy(g.iter[k]);
     g = CgGraph();
 }
 
@@ -269,48 +279,50 @@ __global__ void k_f2d(int n, const float *__restrict__ a, double *__restrict__ b
     if (i < n) b[i] = (double)a[i];
 }
 
-// z = V_l r with an FP32 V-cycle for FP64 vectors (precision mode 2)
-static int vprec32(amgh_problem *p, int l, const double *r, double *z, const int *skip)
-{
-    StateLevel &S = p->sl[l];
-    int n = S.A.rows;
-    k_d2f<<<ceil_div(n, 256), 256, 0, p->stream>>>(n, r, S.fb, skip);
-    LAUNCH_CHECK();
-    TRY(vcyc<float>(p, l, S.fb, S.gz, skip));
-    k_f2d<<<ceil_div(n, 256), 256, 0, p->stream>>>(n, S.gz, z, skip);
-    LAUNCH_CHECK();
-    return AMGH_OK;
-}
-
-// mode 0: FP64 CG + FP64 V-cycle; 1: FP32 CG + FP32 V-cycle; 2: FP64 CG + FP32 V-cycle
+// mode 0: FP64 CG + FP64 V-cycle; 1: FP32 CG + FP32 V-cycle; 2: FP64 CG + FP32
+// V-cycle (the update also writes the FP32 copy of r that the V-cycle reads,
+// and one kernel converts z back and forms r.z).
 static int cg_body_start(amgh_problem *p, int l, int mode)
 {
     StateLevel &S = p->sl[l];
     int n = S.A.rows;
     if (mode == 1) {
         TRY(vcyc<float>(p, l, S.gr, S.gz, &S.scal32->done));
-        return cg_rz_first<float>(p, S.red, n, S.gr, S.gz, S.gp, S.scal32);
+        return cg_rz_first<float>(p, S.red, n, S.gr, S.gz, S.scal32);
     }
-    if (mode == 0) TRY(vcyc<double>(p, l, S.cr, S.cz, &S.scal->done));
-    else TRY(vprec32(p, l, S.cr, S.cz, &S.scal->done));
-    return cg_rz_first<double>(p, S.red, n, S.cr, S.cz, S.cp, S.scal);
+    if (mode == 0) {
+        TRY(vcyc<double>(p, l, S.cr, S.cz, &S.scal->done));
+        return cg_rz_first<double>(p, S.red, n, S.cr, S.cz, S.scal);
+    }
+    k_d2f<<<ceil_div(n, 256), 256, 0, p->stream>>>(n, S.cr, S.fb, &S.scal->done);
+    LAUNCH_CHECK();
+    TRY(vcyc<float>(p, l, S.fb, S.gz, &S.scal->done));
+    return cg_f2d_rz(p, S.red, n, S.gz, S.cz, S.cr, S.scal, 1);
 }
 
-static int cg_body_iter(amgh_problem *p, int l, int mode)
+// one iteration; parity selects which search-direction buffer is read and
+// which is written by the fused p = z + beta p / q = A p kernel
+static int cg_body_iter(amgh_problem *p, int l, int mode, int parity)
 {
     StateLevel &S = p->sl[l];
     int n = S.A.rows;
     if (mode == 1) {
-        TRY(cg_spmv_pq<float>(p, S.red, S.A, S.gp, S.gq, S.scal32, l == 0));
-        TRY(cg_update<float>(p, S.red, n, S.gx, S.gr, S.gp, S.gq, S.scal32));
+        float *pin = parity ? S.gp2 : S.gp, *pout = parity ? S.gp : S.gp2;
+        TRY(cg_spmv_pq_xpay<float>(p, S.red, S.A, S.gz, pin, pout, S.gq, S.scal32, l == 0));
+        TRY(cg_update<float>(p, S.red, n, S.gx, S.gr, pout, S.gq, S.scal32));
         TRY(vcyc<float>(p, l, S.gr, S.gz, &S.scal32->done));
-        return cg_rz_next<float>(p, S.red, n, S.gr, S.gz, S.gp, S.scal32);
+        return cg_rz_next<float>(p, S.red, n, S.gr, S.gz, S.scal32);
     }
-    TRY(cg_spmv_pq<double>(p, S.red, S.A, S.cp, S.cq, S.scal, l == 0));
-    TRY(cg_update<double>(p, S.red, n, S.cx, S.cr, S.cp, S.cq, S.scal));
-    if (mode == 0) TRY(vcyc<double>(p, l, S.cr, S.cz, &S.scal->done));
-    else TRY(vprec32(p, l, S.cr, S.cz, &S.scal->done));
-    return cg_rz_next<double>(p, S.red, n, S.cr, S.cz, S.cp, S.scal);
+    double *pin = parity ? S.cp2 : S.cp, *pout = parity ? S.cp : S.cp2;
+    TRY(cg_spmv_pq_xpay<double>(p, S.red, S.A, S.cz, pin, pout, S.cq, S.scal, l == 0));
+    if (mode == 0) {
+        TRY(cg_update<double>(p, S.red, n, S.cx, S.cr, pout, S.cq, S.scal));
+        TRY(vcyc<double>(p, l, S.cr, S.cz, &S.scal->done));
+        return cg_rz_next<double>(p, S.red, n, S.cr, S.cz, S.scal);
+    }
+    TRY(cg_update<double>(p, S.red, n, S.cx, S.cr, pout, S.cq, S.scal, S.fb));
+    TRY(vcyc<float>(p, l, S.fb, S.gz, &S.scal->done));
+    return cg_f2d_rz(p, S.red, n, S.gz, S.cz, S.cr, S.scal, 0);
 }
 
 // PCG for A_l x = f preconditioned by V_l; the solution is left in S.cx (FP64
@@ -324,9 +336,10 @@ static int pcg_run(amgh_problem *p, int l, int mode, const void *f, double tol, 
     else TRY(cg_start<double>(p, S.red, n, (const double *)f, S.cx, S.cr, sc, tol, maxit, 1));
     CgGraph &g = S.graph[mode];
     bool gr = use_graphs(p);
-    if (gr && !g.iter) {
+    if (gr && !g.iter[0]) {
         TRY(capture(p, [&] { return cg_body_start(p, l, mode); }, &g.start, &g.nodes_start));
-        TRY(capture(p, [&] { return cg_body_iter(p, l, mode); }, &g.iter, &g.nodes_iter));
+        for (int k = 0; k < 2; k++)
+            TRY(capture(p, [&] { return cg_body_iter(p, l, mode, k); }, &g.iter[k], &g.nodes_iter[k]));
     }
     if (gr) TRY(replay(p, g.start, g.nodes_start));
     else TRY(cg_body_start(p, l, mode));
@@ -337,14 +350,16 @@ static int pcg_run(amgh_problem *p, int l, int mode, const void *f, double tol, 
     CgScal h;
     for (;;) {
         for (int c = 0; c < chunk; c++) {
-            if (gr) TRY(replay(p, g.iter, g.nodes_iter));
-            else TRY(cg_body_iter(p, l, mode));
+            int k = (enq + c) & 1;
+            if (gr) TRY(replay(p, g.iter[k], g.nodes_iter[k]));
+            else TRY(cg_body_iter(p, l, mode, k));
         }
         enq += chunk;
         TRY(read_scal(p, sc, &h));
         if (h.done || enq > maxit + 2) break;
         chunk = h.iters / 8 > 1 ? h.iters / 8 : 1;
     }
+    p->c_inner_lvl[l] += h.iters;
     if (h.iters > 0) *hint = h.iters;
     if (iters) *iters = h.iters;
     p->c_inner += h.iters;
@@ -393,25 +408,31 @@ int mass_solve(amgh_problem *p, int l, const double *b, double *x, int64_t *iter
 {
     CtrlLevel &C = p->cl[l];
     int n = C.Mu.rows;
-    TRY(mass_start(p, C.red, n, b, C.mx, C.mr, C.mz, C.mp, C.mu_invdiag, C.mscal, p->sopts.mass_tol,
+    TRY(mass_start(p, C.red, n, b, C.mx, C.mr, C.mz, C.mu_invdiag, C.mscal, p->sopts.mass_tol,
                    p->sopts.mass_max_iter));
     bool gr = use_graphs(p);
     CgGraph &g = C.mgraph;
-    auto body = [&] { return mass_iter(p, C.red, C.Mu, C.mx, C.mr, C.mz, C.mp, C.mq, C.mu_invdiag, C.mscal); };
-    if (gr && !g.iter) TRY(capture(p, body, &g.iter, &g.nodes_iter));
+    auto body = [&](int k) {
+        double *pin = k ? C.mp2 : C.mp, *pout = k ? C.mp : C.mp2;
+        return mass_iter(p, C.red, C.Mu, C.mx, C.mr, C.mz, pin, pout, C.mq, C.mu_invdiag, C.mscal);
+    };
+    if (gr && !g.iter[0])
+        for (int k = 0; k < 2; k++) TRY(capture(p, [&] { return body(k); }, &g.iter[k], &g.nodes_iter[k]));
     int chunk = p->mchunk_hint[l] > 1 ? (p->mchunk_hint[l] * 7) / 8 : 1;
     int enq = 0;
     CgScal h;
     for (;;) {
         for (int c = 0; c < chunk; c++) {
-            if (gr) TRY(replay(p, g.iter, g.nodes_iter));
-            else TRY(body());
+            int k = (enq + c) & 1;
+            if (gr) TRY(replay(p, g.iter[k], g.nodes_iter[k]));
+            else TRY(body(k));
         }
         enq += chunk;
         TRY(read_scal(p, C.mscal, &h));
         if (h.done || enq > p->sopts.mass_max_iter + 2) break;
         chunk = h.iters / 8 > 1 ? h.iters / 8 : 1;
     }
+    p->c_mass_lvl[l] += h.iters;
     if (h.iters > 0) p->mchunk_hint[l] = h.iters;
     if (iters) *iters = h.iters;
     p->c_mass += h.iters;

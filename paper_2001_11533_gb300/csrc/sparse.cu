@@ -159,13 +159,6 @@ int csr_transpose(Arena &ar, const DevCsr &a, DevCsr &t, cudaStream_t s)
 
 // ------------------------------------------------------------------ SpMV family
 template <typename T>
-__device__ __forceinline__ const T *sell_vals(const DevCsr &a);
-template <>
-__device__ __forceinline__ const double *sell_vals<double>(const DevCsr &a) { return a.sl_v; }
-template <>
-__device__ __forceinline__ const float *sell_vals<float>(const DevCsr &a) { return a.sl_v32; }
-
-template <typename T>
 static inline const T *h_sell_vals(const DevCsr &a);
 template <>
 inline const double *h_sell_vals<double>(const DevCsr &a) { return a.sl_v; }
@@ -252,6 +245,24 @@ __global__ void k_residual(int rows, const int *__restrict__ slp, const int *__r
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= rows) return;
     r[i] = b[i] - sell_row<T>(i, slp, sci, sv, x);
+}
+
+// restriction b_c = S^T r fused with the first smoother step of the coarse
+// level from zero: d_c = x_c = c0 D_c^-1 b_c
+template <typename T>
+__global__ void k_restrict_first(int rows, const int *__restrict__ slp, const int *__restrict__ sci,
+                                 const T *__restrict__ sv, const T *__restrict__ r, T *__restrict__ bc,
+                                 const T *__restrict__ invd, T *__restrict__ d, T *__restrict__ x, T c0,
+                                 const int *__restrict__ skip)
+{
+    SKIP_RETURN();
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= rows) return;
+    T b = sell_row<T>(i, slp, sci, sv, r);
+    bc[i] = b;
+    T v = c0 * (b * invd[i]);
+    d[i] = v;
+    x[i] = v;
 }
 
 template <typename T>
@@ -356,6 +367,18 @@ int residual(amgh_problem *p, const DevCsr &a, const T *b, const T *x, T *r, con
 }
 
 template <typename T>
+int restrict_first(amgh_problem *p, const DevCsr &st, const T *r, T *bc, const T *invd_c, T *d_c, T *x_c,
+                   double c0, const int *skip)
+{
+    if (st.rows == 0) return AMGH_OK;
+    k_restrict_first<T><<<ceil_div(st.rows, TPB), TPB, 0, p->stream>>>(st.rows, st.sl_ptr, st.sl_ci,
+                                                                       h_sell_vals<T>(st), r, bc, invd_c, d_c, x_c,
+                                                                       (T)c0, skip);
+    LAUNCH_CHECK();
+    return AMGH_OK;
+}
+
+template <typename T>
 int prolong_add(amgh_problem *p, const DevCsr &s, const T *e, T *x, const int *skip)
 {
     if (s.rows == 0) return AMGH_OK;
@@ -380,6 +403,8 @@ int dense_gemv(amgh_problem *p, int n, const double *inv, const T *b, T *x, cons
                               double, double, const int *, int);                                      \
     template int residual<T>(amgh_problem *, const DevCsr &, const T *, const T *, T *, const int *, int); \
     template int prolong_add<T>(amgh_problem *, const DevCsr &, const T *, T *, const int *);            \
+    template int restrict_first<T>(amgh_problem *, const DevCsr &, const T *, T *, const T *, T *, T *, double, \
+                                   const int *);                                                         \
     template int dense_gemv<T>(amgh_problem *, int, const double *, const T *, T *, const int *);
 INST(double)
 INST(float)
