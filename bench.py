@@ -44,6 +44,8 @@ def parse():
     ap.add_argument("--impl", default="amgh", choices=["amgh", "reference"])
     ap.add_argument("--N", type=int, default=1025, help="L-shape grid size (bench workload: 1025)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--hessian-levels", type=int, default=4,
+                    help="levels of the Hessian preconditioner (fewer than the AMG levels, as in Sec. 5.6)")
     ap.add_argument("--single-step", action="store_true",
                     help="run one untimed step of the first form (for profilers) and print its counters")
     ap.add_argument("--forms", default="mixed,fp64,refine",
@@ -149,7 +151,7 @@ def run_amgh(args, rank, world, local):
             prob = amgh.Problem(w.dim, *pinned_np[:4], w.beta, pinned_np[4], on_device=False)
         else:
             prob = amgh.Problem(w.dim, dev[0], dev[1], dev[2], dev[3], w.beta, dev[4], on_device=True)
-        prob.amg_setup(precision=precision)
+        prob.amg_setup(precision=precision, hessian_levels=args.hessian_levels)
         if timing:
             prob.kernel_timing(True)
         if e2e:
@@ -256,10 +258,10 @@ def roofline_from(res):
 
 
 # ------------------------------------------------------------------------- oracle (CPU)
-def oracle_apply_rate(w, budget_s, applies=None):
+def oracle_apply_rate(w, budget_s, applies=None, hessian_levels=0):
     """Time the FP64 oracle's Hessian apply on the host (setup untimed)."""
     from oracle.oracle import Oracle
-    orc = Oracle(w)
+    orc = Oracle(w, hessian_levels=hessian_levels)
     u = np.random.default_rng(0).standard_normal(w.n_vertices)
     n, t = 0, 0.0
     while (applies is None and (t < budget_s or n == 0)) or (applies is not None and n < applies):
@@ -278,7 +280,7 @@ def run_reference(args, rank, world):
     orc_mod.build()
     w = workloads.lshape_checkerboard(N=args.N)
     from oracle.oracle import Oracle
-    orc = Oracle(w)
+    orc = Oracle(w, hessian_levels=args.hessian_levels)
     u = np.random.default_rng(0).standard_normal(w.n_vertices)
     for _ in range(min(args.warmup, 1)):
         orc.hessian(u)
@@ -310,7 +312,7 @@ def single_step(args):
     _build.build()
     w = workloads.lshape_checkerboard(N=args.N)
     prob = amgh.Problem.from_workload(w)
-    prob.amg_setup(precision=PRECISION[args.forms.split(",")[0]])
+    prob.amg_setup(precision=PRECISION[args.forms.split(",")[0]], hessian_levels=args.hessian_levels)
     u, y, info = prob.solve(tol=1e-8)
     torch.cuda.synchronize()
     print(json.dumps({"info": info, "levels": prob.level_counters(), "sizes": prob.sizes,
@@ -339,6 +341,7 @@ def main():
         "data": "synthetic",
         "config": {"workload": f"lshape{args.N}_checkerboard", "m": w.n_interior, "n": w.n_vertices,
                    "beta": w.beta, "kappa": "8x8 checkerboard {1,1e4}", "tol": 1e-8,
+                   "hessian_levels": args.hessian_levels,
                    "precision": forms[0], "parallelism": "replicas" if world > 1 else "single",
                    "l2": "256 MB buffer written between timed steps",
                    "step": "assembly + AMG setup + rhs + outer CG to 1e-8 + true residual"},
@@ -354,7 +357,7 @@ def main():
     if "refine" in results and "fp64" in results:
         line["speedup_refine_vs_fp64"] = results["refine"]["value"] / results["fp64"]["value"]
     if world == 1 and not args.no_cpu_baseline:
-        n, t = oracle_apply_rate(w, budget_s=15.0)
+        n, t = oracle_apply_rate(w, budget_s=15.0, hessian_levels=args.hessian_levels)
         line["cpu_baseline"] = {"value": n / t, "unit": UNIT, "cores": 1, "kind": "oracle",
                                 "sample": f"{n} Hessian applies of the FP64 oracle on the same workload "
                                           f"({t:.1f} s, setup untimed)"}

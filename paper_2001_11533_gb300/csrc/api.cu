@@ -274,11 +274,11 @@ static int setup_impl(amgh_problem *p)
     // SELL copies of the operators applied in the solve phase, smoother and mass diagonals
     for (int l = 0; l < p->Ls; l++) {
         StateLevel &S = p->sl[l];
-        TRY(csr_to_sell(ar, S.A, 1, s));
-        TRY(csr_to_sell(ar, S.My, 1, s));
+        TRY(prepare_operator(ar, S.A, s));
+        TRY(prepare_operator(ar, S.My, s));
         if (l + 1 < p->Ls) {
-            TRY(csr_to_sell(ar, S.S, 1, s));
-            TRY(csr_to_sell(ar, S.St, 1, s));
+            TRY(prepare_operator(ar, S.S, s));
+            TRY(prepare_operator(ar, S.St, s));
         }
         TRY(ar.alloc(&S.invd, S.A.rows));
         TRY(ar.alloc(&S.invd32, S.A.rows));
@@ -286,14 +286,14 @@ static int setup_impl(amgh_problem *p)
     }
     for (int l = 0; l < p->Lc; l++) {
         CtrlLevel &C = p->cl[l];
-        TRY(csr_to_sell(ar, C.Mu, 1, s));
+        TRY(prepare_operator(ar, C.Mu, s));
         if (l + 1 < p->Lc) {
-            TRY(csr_to_sell(ar, C.P, 1, s));
-            TRY(csr_to_sell(ar, C.Pt, 1, s));
+            TRY(prepare_operator(ar, C.P, s));
+            TRY(prepare_operator(ar, C.Pt, s));
         }
         if (l < lmin) {
-            TRY(csr_to_sell(ar, C.Myu, 1, s));
-            TRY(csr_to_sell(ar, C.Myut, 1, s));
+            TRY(prepare_operator(ar, C.Myu, s));
+            TRY(prepare_operator(ar, C.Myut, s));
         }
         TRY(ar.alloc(&C.mu_invdiag, C.Mu.rows));
         TRY(diag_inv(p, C.Mu, C.mu_invdiag));

@@ -1,16 +1,26 @@
 // blas.cu -- conjugate-gradient building blocks with device-resident scalars.
 //
-// Every CG loop keeps its scalars (r.z, p.q, alpha, beta, ||r||^2, the
-// stopping threshold, an iteration count and a `done` flag) in a CgScal in
-// device memory.  Each kernel below fuses a vector update with the next
-// inner product; its reduction is two-stage and deterministic (block
-// partials summed in fixed order by the last block to finish), and that last
-// block also computes the new alpha / beta or the stopping decision.  Every
-// kernel returns at once when `done` is set, so the host can enqueue several
+// Every CG loop keeps its scalars (r.z, alpha, beta, ||r||^2, the stopping
+// threshold, an iteration count and a `done` flag) in a CgScal in device
+// memory.  Each kernel below fuses a vector update with the next inner
+// product; its reduction is two-stage and deterministic (block partials
+// summed in fixed order by the last block to finish), and that last block
+// also computes the new alpha / beta or the stopping decision.  Every kernel
+// returns at once when `done` is set, so the host can enqueue several
 // iterations ahead and only read the flag back now and then.
+//
+// The inner (state and mass) solves use the single-reduction form of
+// preconditioned CG (Chronopoulos & Gear, J. Comput. Appl. Math. 25, 1989):
+// with z = M r and s = A z computed together,
+//   gamma = (r, z), delta = (z, s), beta = gamma / gamma_old,
+//   alpha = gamma / (delta - beta gamma / alpha_old),
+//   p = z + beta p, q = s + beta q, x += alpha p, r -= alpha q,
+// which equals standard PCG in exact arithmetic and needs one SpMV (one
+// gather of z) and one reduction point per iteration.
 #include <math.h>
 
 #include "internal.cuh"
+#include "spmv.cuh"
 #include "util.cuh"
 
 static const int TPB = 256;
@@ -23,7 +33,8 @@ static inline int vec_blocks(int64_t n)
 
 int red_alloc(Arena &ar, RedSlot &slot, int capacity_rows)
 {
-    int cap = ceil_div(capacity_rows > 0 ? capacity_rows : 1, TPB) + 8;
+    // SpMV-class kernels launch up to 32 threads per row
+    int cap = ceil_div((int64_t)(capacity_rows > 0 ? capacity_rows : 1) * 32, TPB) + 8;
     slot.capacity = cap;
     TRY(ar.alloc(&slot.partials, (int64_t)cap * 2));
     TRY(ar.alloc(&slot.ticket, 1));
@@ -42,6 +53,7 @@ enum {
     F_REF_START,     // t0 = f.f -> scale, thr
     F_REF_UPDATE,    // t0 = r.r -> refinement stop test, scale
     F_STORE,         // t0 -> *out
+    F_CG2,           // t0 = (r,z), t1 = (z,Az) -> alpha, beta (single-reduction CG)
 };
 
 __device__ __forceinline__ bool bad(double x) { return !(x == x) || isinf(x); }
@@ -165,6 +177,32 @@ __device__ void cg_finalize(int mode, const double *t, CgScal *sc, double *out)
     case F_STORE:
         *out = t[0];
         break;
+    case F_CG2: {
+        double g = t[0], d = t[1];
+        if (!(g > 0.0) || !(d > 0.0)) {
+            sc->status = (bad(g) || bad(d)) ? CG_NUMERIC : CG_INDEFINITE;
+            sc->done = 1;
+            break;
+        }
+        double beta = 0.0, alpha;
+        if (sc->k1 == 0) {
+            alpha = g / d;
+        } else {
+            beta = g / sc->rz;
+            double den = d - beta * g / sc->alpha;
+            if (!(den > 0.0)) {
+                sc->status = bad(den) ? CG_NUMERIC : CG_INDEFINITE;
+                sc->done = 1;
+                break;
+            }
+            alpha = g / den;
+        }
+        sc->rz = g;
+        sc->alpha = alpha;
+        sc->beta = beta;
+        sc->k1 += 1;
+        break;
+    }
     }
 }
 
@@ -186,79 +224,67 @@ __global__ void k_cg_start(int n, const T *__restrict__ f, T *__restrict__ x, T 
     if (reduce_last_block<1>(v, partials, ticket, tot)) cg_finalize(mode, tot, sc, nullptr);
 }
 
-// mass CG start: x = 0, r = f, z = invd r; reduce f.f and r.z (beta = 0)
+// mass CG start: x = 0, r = f, z = invd r; reduce f.f
 __global__ void k_mass_start(int n, const double *__restrict__ f, double *__restrict__ x, double *__restrict__ r,
                              double *__restrict__ z, const double *__restrict__ invd, CgScal *sc, double *partials,
                              unsigned *ticket)
 {
-    double v[2] = {0.0, 0.0}, tot[2];
+    double v[1] = {0.0}, tot[1];
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         double fi = f[i];
-        double zi = invd[i] * fi;
         r[i] = fi;
         x[i] = 0.0;
-        z[i] = zi;
+        z[i] = invd[i] * fi;
         v[0] += fi * fi;
-        v[1] += fi * zi;
     }
-    if (reduce_last_block<2>(v, partials, ticket, tot)) cg_finalize(F_MASS_START, tot, sc, nullptr);
+    if (reduce_last_block<1>(v, partials, ticket, tot)) cg_finalize(F_START, tot, sc, nullptr);
 }
 
-// inner CG r.z without touching p (the p update is fused into the next SpMV)
-template <typename T>
-__global__ void k_rz_only(int n, const T *__restrict__ r, const T *__restrict__ z, CgScal *sc, int mode,
-                          double *partials, unsigned *ticket)
+// K1: s = A z, reduce (r, z) and (z, s) -> alpha, beta.  z may be FP32 (the
+// output of an FP32 V-cycle) while A, r and s are FP64.
+template <typename T, typename Z, int TPR>
+__global__ void k_cg2_spmv(MatView<T> A, const Z *__restrict__ z, const T *__restrict__ r, T *__restrict__ s,
+                           CgScal *sc, double *partials, unsigned *ticket)
 {
     SKIP_DONE();
-    double v[1] = {0.0}, tot[1];
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-        v[0] += (double)r[i] * (double)z[i];
-    if (reduce_last_block<1>(v, partials, ticket, tot)) cg_finalize(mode, tot, sc, nullptr);
-}
-
-// z64 = z32 and r.z (FP32 V-cycle inside FP64 CG)
-__global__ void k_f2d_rz(int n, const float *__restrict__ z32, double *__restrict__ z, const double *__restrict__ r,
-                         CgScal *sc, int mode, double *partials, unsigned *ticket)
-{
-    SKIP_DONE();
-    double v[1] = {0.0}, tot[1];
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        double zi = (double)z32[i];
-        z[i] = zi;
-        v[0] += r[i] * zi;
+    int row = my_row<TPR>();
+    T v = row_sum<T, TPR>(A, row, [&](int c) { return (T)__ldg(&z[c]); });
+    double a[2] = {0.0, 0.0}, tot[2];
+    if (row < A.rows && row_leader<TPR>()) {
+        s[row] = v;
+        double zr = (double)z[row];
+        a[0] = (double)r[row] * zr;
+        a[1] = zr * (double)v;
     }
-    if (reduce_last_block<1>(v, partials, ticket, tot)) cg_finalize(mode, tot, sc, nullptr);
+    if (reduce_last_block<2>(a, partials, ticket, tot)) cg_finalize(F_CG2, tot, sc, nullptr);
 }
 
-// p_out = z + beta p_in (p_out = z when beta = 0) and q = A p_out, reduce p.q -> alpha
-template <typename T>
-__global__ void k_spmv_pq_xpay(int rows, const int *__restrict__ slp, const int *__restrict__ sci,
-                               const T *__restrict__ sv, const T *__restrict__ z, const T *__restrict__ pin,
-                               T *__restrict__ pout, T *__restrict__ q, CgScal *sc, double *partials,
-                               unsigned *ticket)
+// K2: p = z + beta p, q = s + beta q, x += alpha p, r -= alpha q, reduce r.r;
+// optionally r32 = r (input of an FP32 V-cycle) or, for the Jacobi-
+// preconditioned mass CG, z = invd r for the next K1.
+template <typename T, typename Z>
+__global__ void k_cg2_update(int n, Z *__restrict__ z, const T *__restrict__ s, T *__restrict__ pv,
+                             T *__restrict__ q, T *__restrict__ x, T *__restrict__ r, float *__restrict__ r32,
+                             const double *__restrict__ invd, CgScal *sc, double *partials, unsigned *ticket)
 {
     SKIP_DONE();
-    T b = (T)sc->beta;
+    T a = (T)sc->alpha, b = (T)sc->beta;
     bool first = sc->beta == 0.0;
     double v[1] = {0.0}, tot[1];
-    int r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r < rows) {
-        int s = r >> 5, lane = r & 31;
-        T acc = (T)0;
-        if (first) {
-            for (int k = slp[s] + lane; k < slp[s + 1]; k += 32) acc += sv[k] * __ldg(&z[sci[k]]);
-        } else {
-            for (int k = slp[s] + lane; k < slp[s + 1]; k += 32) {
-                int c = sci[k];
-                acc += sv[k] * (__ldg(&z[c]) + b * __ldg(&pin[c]));
-            }
-        }
-        T pr = first ? z[r] : z[r] + b * pin[r];
-        pout[r] = pr;
-        q[r] = acc;
-        v[0] = (double)pr * (double)acc;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        T zi = (T)z[i];
+        T pi = first ? zi : zi + b * pv[i];
+        T qi = first ? s[i] : s[i] + b * q[i];
+        pv[i] = pi;
+        q[i] = qi;
+        x[i] = x[i] + a * pi;
+        T ri = r[i] - a * qi;
+        r[i] = ri;
+        if (r32) r32[i] = (float)ri;
+        if (invd) z[i] = (Z)(invd[i] * (double)ri);
+        v[0] += (double)ri * (double)ri;
     }
-    if (reduce_last_block<1>(v, partials, ticket, tot)) cg_finalize(F_PQ, tot, sc, nullptr);
+    if (reduce_last_block<1>(v, partials, ticket, tot)) cg_finalize(F_RR, tot, sc, nullptr);
 }
 
 // rz = r.z and p = z (first iteration) or beta from rz (later)
@@ -285,43 +311,20 @@ __global__ void k_xpay(int n, const T *__restrict__ z, T *__restrict__ pv, const
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) pv[i] = z[i] + b * pv[i];
 }
 
-// x += alpha p, r -= alpha q (and r32 = r when given), reduce r.r -> stop test
-template <typename T>
-__global__ void k_update(int n, T *__restrict__ x, T *__restrict__ r, const T *__restrict__ pv,
-                         const T *__restrict__ q, CgScal *sc, float *__restrict__ r32, double *partials,
-                         unsigned *ticket)
-{
-    SKIP_DONE();
-    T a = (T)sc->alpha;
-    double v[1] = {0.0}, tot[1];
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        x[i] = x[i] + a * pv[i];
-        T ri = r[i] - a * q[i];
-        r[i] = ri;
-        if (r32) r32[i] = (float)ri;
-        v[0] += (double)ri * (double)ri;
-    }
-    if (reduce_last_block<1>(v, partials, ticket, tot)) cg_finalize(F_RR, tot, sc, nullptr);
-}
-
-// mass CG: x += alpha p, r -= alpha q, z = invd r; reduce r.r, r.z
-__global__ void k_mass_update(int n, double *__restrict__ x, double *__restrict__ r, double *__restrict__ z,
-                              const double *__restrict__ pv, const double *__restrict__ q,
-                              const double *__restrict__ invd, CgScal *sc, double *partials, unsigned *ticket)
+// outer CG: x += alpha p, r -= alpha q, reduce r.r -> stop test
+__global__ void k_update(int n, double *__restrict__ x, double *__restrict__ r, const double *__restrict__ pv,
+                         const double *__restrict__ q, CgScal *sc, double *partials, unsigned *ticket)
 {
     SKIP_DONE();
     double a = sc->alpha;
-    double v[2] = {0.0, 0.0}, tot[2];
+    double v[1] = {0.0}, tot[1];
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         x[i] = x[i] + a * pv[i];
         double ri = r[i] - a * q[i];
         r[i] = ri;
-        double zi = invd[i] * ri;
-        z[i] = zi;
         v[0] += ri * ri;
-        v[1] += ri * zi;
     }
-    if (reduce_last_block<2>(v, partials, ticket, tot)) cg_finalize(F_MASS_UPDATE, tot, sc, nullptr);
+    if (reduce_last_block<1>(v, partials, ticket, tot)) cg_finalize(F_RR, tot, sc, nullptr);
 }
 
 // generic dot with finaliser (outer CG: p.Hp; r.z)
@@ -353,21 +356,18 @@ __global__ void k_ref_add(int n, double *__restrict__ y, const float *__restrict
 }
 
 // refinement: r = f - A y (FP64), reduce r.r -> stop test
-__global__ void k_ref_resid(int rows, const int *__restrict__ slp, const int *__restrict__ sci,
-                            const double *__restrict__ sv, const double *__restrict__ f,
-                            const double *__restrict__ y, double *__restrict__ r, CgScal *rs, double *partials,
-                            unsigned *ticket)
+template <typename T, int TPR>
+__global__ void k_ref_resid(MatView<T> A, const T *__restrict__ f, const T *__restrict__ y, T *__restrict__ r,
+                            CgScal *rs, double *partials, unsigned *ticket)
 {
     if (rs->done) return;
+    int i = my_row<TPR>();
+    T ay = row_sum<T, TPR>(A, i, [&](int c) { return __ldg(&y[c]); });
     double v[1] = {0.0}, tot[1];
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < rows) {
-        int s = i >> 5, lane = i & 31;
-        double acc = 0.0;
-        for (int k = slp[s] + lane; k < slp[s + 1]; k += 32) acc += sv[k] * __ldg(&y[sci[k]]);
-        double ri = f[i] - acc;
+    if (i < A.rows && row_leader<TPR>()) {
+        T ri = f[i] - ay;
         r[i] = ri;
-        v[0] = ri * ri;
+        v[0] = (double)ri * (double)ri;
     }
     if (reduce_last_block<1>(v, partials, ticket, tot)) cg_finalize(F_REF_UPDATE, tot, rs, nullptr);
 }
@@ -378,6 +378,8 @@ __global__ void k_set_scal(CgScal *sc, double tol2, int maxit)
     sc->maxit = maxit;
     sc->done = 0;
     sc->iters = 0;
+    sc->k1 = 0;
+    sc->beta = 0.0;
     sc->status = CG_RUNNING;
 }
 
@@ -401,76 +403,71 @@ static int set_scal(amgh_problem *p, CgScal *sc, double tol, int maxit)
     return AMGH_OK;
 }
 
+// single-reduction CG pieces (templated on the vector type T and the type Z of z)
+template <typename T, typename Z>
+int cg2_spmv(amgh_problem *p, RedSlot &red, const DevCsr &a, const Z *z, const T *r, T *s, CgScal *sc, int timed)
+{
+    MatView<T> A = view<T>(a);
+    timer_begin(p, timed);
+    switch (A.tpr) {
+    case 2: k_cg2_spmv<T, Z, 2><<<rows_grid(A.rows, 2), TPB, 0, p->stream>>>(A, z, r, s, sc, red.partials, red.ticket); break;
+    case 4: k_cg2_spmv<T, Z, 4><<<rows_grid(A.rows, 4), TPB, 0, p->stream>>>(A, z, r, s, sc, red.partials, red.ticket); break;
+    case 8: k_cg2_spmv<T, Z, 8><<<rows_grid(A.rows, 8), TPB, 0, p->stream>>>(A, z, r, s, sc, red.partials, red.ticket); break;
+    case 16: k_cg2_spmv<T, Z, 16><<<rows_grid(A.rows, 16), TPB, 0, p->stream>>>(A, z, r, s, sc, red.partials, red.ticket); break;
+    case 32: k_cg2_spmv<T, Z, 32><<<rows_grid(A.rows, 32), TPB, 0, p->stream>>>(A, z, r, s, sc, red.partials, red.ticket); break;
+    default: k_cg2_spmv<T, Z, 1><<<rows_grid(A.rows, 1), TPB, 0, p->stream>>>(A, z, r, s, sc, red.partials, red.ticket); break;
+    }
+    LAUNCH_CHECK();
+    // matrix + gather of z + reads of r, z + write of s
+    timer_end(p, timed, spmv_bytes(a, sizeof(T)) - (double)sizeof(T) * a.cols + (double)sizeof(Z) * a.cols +
+                            (double)(sizeof(T) + sizeof(Z)) * a.rows);
+    return AMGH_OK;
+}
+
+template <typename T, typename Z>
+int cg2_update(amgh_problem *p, RedSlot &red, int n, Z *z, const T *s, T *pv, T *q, T *x, T *r, float *r32,
+               const double *invd, CgScal *sc)
+{
+    k_cg2_update<T, Z><<<vec_blocks(n), TPB, 0, p->stream>>>(n, z, s, pv, q, x, r, r32, invd, sc, red.partials,
+                                                             red.ticket);
+    LAUNCH_CHECK();
+    return AMGH_OK;
+}
+
+template int cg2_spmv<double, double>(amgh_problem *, RedSlot &, const DevCsr &, const double *, const double *,
+                                      double *, CgScal *, int);
+template int cg2_spmv<double, float>(amgh_problem *, RedSlot &, const DevCsr &, const float *, const double *,
+                                     double *, CgScal *, int);
+template int cg2_spmv<float, float>(amgh_problem *, RedSlot &, const DevCsr &, const float *, const float *, float *,
+                                    CgScal *, int);
+template int cg2_update<double, double>(amgh_problem *, RedSlot &, int, double *, const double *, double *, double *,
+                                        double *, double *, float *, const double *, CgScal *);
+template int cg2_update<double, float>(amgh_problem *, RedSlot &, int, float *, const double *, double *, double *,
+                                       double *, double *, float *, const double *, CgScal *);
+template int cg2_update<float, float>(amgh_problem *, RedSlot &, int, float *, const float *, float *, float *,
+                                      float *, float *, float *, const double *, CgScal *);
+
 template <typename T>
 int cg_start(amgh_problem *p, RedSlot &red, int n, const T *f, T *x, T *r, CgScal *sc, double tol, int maxit,
              int zero_x)
 {
     TRY(set_scal(p, sc, tol, maxit));
-    k_cg_start<T><<<vec_blocks(n), TPB, 0, p->stream>>>(n, f, x, r, sc, zero_x, red.partials, red.ticket,
-                                                        F_START);
+    k_cg_start<T><<<vec_blocks(n), TPB, 0, p->stream>>>(n, f, x, r, sc, zero_x, red.partials, red.ticket, F_START);
     LAUNCH_CHECK();
     return AMGH_OK;
 }
+template int cg_start<double>(amgh_problem *, RedSlot &, int, const double *, double *, double *, CgScal *, double,
+                              int, int);
+template int cg_start<float>(amgh_problem *, RedSlot &, int, const float *, float *, float *, CgScal *, double, int,
+                             int);
 
-template <typename T>
-int cg_rz_first(amgh_problem *p, RedSlot &red, int n, const T *r, const T *z, CgScal *sc)
+int cg_update_outer(amgh_problem *p, RedSlot &red, int n, double *x, double *r, const double *pv, const double *q,
+                    CgScal *sc)
 {
-    k_rz_only<T><<<vec_blocks(n), TPB, 0, p->stream>>>(n, r, z, sc, F_RZ_FIRST, red.partials, red.ticket);
+    k_update<<<vec_blocks(n), TPB, 0, p->stream>>>(n, x, r, pv, q, sc, red.partials, red.ticket);
     LAUNCH_CHECK();
     return AMGH_OK;
 }
-
-template <typename T>
-int cg_spmv_pq_xpay(amgh_problem *p, RedSlot &red, const DevCsr &a, const T *z, const T *pin, T *pout, T *q,
-                    CgScal *sc, int timed)
-{
-    const T *sv;
-    if (sizeof(T) == 8) sv = (const T *)a.sl_v;
-    else sv = (const T *)a.sl_v32;
-    timer_begin(p, timed);
-    k_spmv_pq_xpay<T><<<ceil_div(a.rows, TPB), TPB, 0, p->stream>>>(a.rows, a.sl_ptr, a.sl_ci, sv, z, pin, pout, q,
-                                                                    sc, red.partials, red.ticket);
-    LAUNCH_CHECK();
-    // matrix + gathers of z and p_in + writes of p_out and q
-    timer_end(p, timed,
-              (double)a.nnz * (sizeof(T) + 4) + 4.0 * (a.rows + 1) + (double)sizeof(T) * (2.0 * a.cols + 2.0 * a.rows));
-    return AMGH_OK;
-}
-
-template <typename T>
-int cg_update(amgh_problem *p, RedSlot &red, int n, T *x, T *r, const T *pv, const T *q, CgScal *sc, float *r32)
-{
-    k_update<T><<<vec_blocks(n), TPB, 0, p->stream>>>(n, x, r, pv, q, sc, r32, red.partials, red.ticket);
-    LAUNCH_CHECK();
-    return AMGH_OK;
-}
-
-template <typename T>
-int cg_rz_next(amgh_problem *p, RedSlot &red, int n, const T *r, const T *z, CgScal *sc)
-{
-    k_rz_only<T><<<vec_blocks(n), TPB, 0, p->stream>>>(n, r, z, sc, F_RZ_NEXT, red.partials, red.ticket);
-    LAUNCH_CHECK();
-    return AMGH_OK;
-}
-
-int cg_f2d_rz(amgh_problem *p, RedSlot &red, int n, const float *z32, double *z, const double *r, CgScal *sc,
-              int first)
-{
-    k_f2d_rz<<<vec_blocks(n), TPB, 0, p->stream>>>(n, z32, z, r, sc, first ? F_RZ_FIRST : F_RZ_NEXT, red.partials,
-                                                    red.ticket);
-    LAUNCH_CHECK();
-    return AMGH_OK;
-}
-
-#define INST(T)                                                                                              \
-    template int cg_start<T>(amgh_problem *, RedSlot &, int, const T *, T *, T *, CgScal *, double, int, int); \
-    template int cg_rz_first<T>(amgh_problem *, RedSlot &, int, const T *, const T *, CgScal *);              \
-    template int cg_spmv_pq_xpay<T>(amgh_problem *, RedSlot &, const DevCsr &, const T *, const T *, T *, T *,  \
-                                    CgScal *, int);                                                          \
-    template int cg_update<T>(amgh_problem *, RedSlot &, int, T *, T *, const T *, const T *, CgScal *, float *); \
-    template int cg_rz_next<T>(amgh_problem *, RedSlot &, int, const T *, const T *, CgScal *);
-INST(double)
-INST(float)
 
 // mass CG pieces
 int mass_start(amgh_problem *p, RedSlot &red, int n, const double *f, double *x, double *r, double *z,
@@ -478,16 +475,6 @@ int mass_start(amgh_problem *p, RedSlot &red, int n, const double *f, double *x,
 {
     TRY(set_scal(p, sc, tol, maxit));
     k_mass_start<<<vec_blocks(n), TPB, 0, p->stream>>>(n, f, x, r, z, invd, sc, red.partials, red.ticket);
-    LAUNCH_CHECK();
-    return AMGH_OK;
-}
-
-int mass_iter(amgh_problem *p, RedSlot &red, const DevCsr &M, double *x, double *r, double *z, const double *pin,
-              double *pout, double *q, const double *invd, CgScal *sc)
-{
-    int n = M.rows;
-    TRY(cg_spmv_pq_xpay<double>(p, red, M, z, pin, pout, q, sc, 0));
-    k_mass_update<<<vec_blocks(n), TPB, 0, p->stream>>>(n, x, r, z, pout, q, invd, sc, red.partials, red.ticket);
     LAUNCH_CHECK();
     return AMGH_OK;
 }
@@ -548,8 +535,15 @@ int ref_update(amgh_problem *p, RedSlot &red, const DevCsr &a, const double *f, 
     int n = a.rows;
     k_ref_add<<<vec_blocks(n), TPB, 0, p->stream>>>(n, y, e32, rs);
     LAUNCH_CHECK();
-    k_ref_resid<<<ceil_div(n, TPB), TPB, 0, p->stream>>>(n, a.sl_ptr, a.sl_ci, a.sl_v, f, y, r, rs, red.partials,
-                                                          red.ticket);
+    MatView<double> A = view<double>(a);
+    switch (A.tpr) {
+    case 2: k_ref_resid<double, 2><<<rows_grid(n, 2), TPB, 0, p->stream>>>(A, f, y, r, rs, red.partials, red.ticket); break;
+    case 4: k_ref_resid<double, 4><<<rows_grid(n, 4), TPB, 0, p->stream>>>(A, f, y, r, rs, red.partials, red.ticket); break;
+    case 8: k_ref_resid<double, 8><<<rows_grid(n, 8), TPB, 0, p->stream>>>(A, f, y, r, rs, red.partials, red.ticket); break;
+    case 16: k_ref_resid<double, 16><<<rows_grid(n, 16), TPB, 0, p->stream>>>(A, f, y, r, rs, red.partials, red.ticket); break;
+    case 32: k_ref_resid<double, 32><<<rows_grid(n, 32), TPB, 0, p->stream>>>(A, f, y, r, rs, red.partials, red.ticket); break;
+    default: k_ref_resid<double, 1><<<rows_grid(n, 1), TPB, 0, p->stream>>>(A, f, y, r, rs, red.partials, red.ticket); break;
+    }
     LAUNCH_CHECK();
     return AMGH_OK;
 }

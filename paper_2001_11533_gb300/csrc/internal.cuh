@@ -94,6 +94,10 @@ struct DevCsr {
     int rows = 0, cols = 0, nnz = 0;
     int *rp = nullptr, *ci = nullptr;
     double *v = nullptr;
+    // how the solve phase applies it: tpr = 1 -> SELL-32 below; tpr > 1 -> CSR
+    // with tpr lanes per row and the FP32 copy v32
+    int tpr = 1;
+    float *v32 = nullptr;
     // SELL-32
     int nslices = 0, sell_nnz = 0;
     int *sl_ptr = nullptr, *sl_ci = nullptr;
@@ -117,7 +121,8 @@ struct CgScal {
     double scale;                             // refinement: ||r||
     int done, iters, status, maxit;
     int total_iters;
-    int pad[3];
+    int k1; // single-reduction CG: number of alpha/beta updates so far
+    int pad[2];
 };
 
 enum { CG_RUNNING = 0, CG_CONVERGED = 1, CG_INDEFINITE = 2, CG_NUMERIC = 3, CG_MAXIT = 4 };
@@ -127,8 +132,8 @@ enum { CG_RUNNING = 0, CG_CONVERGED = 1, CG_INDEFINITE = 2, CG_NUMERIC = 3, CG_M
 // residual), captured once per level and precision mode, replayed per
 // iteration; `nodes` is the kernel count of one replay.
 struct CgGraph {
-    cudaGraphExec_t start = nullptr, iter[2] = {nullptr, nullptr}; // iter[k]: p ping-pong parity k
-    int nodes_start = 0, nodes_iter[2] = {0, 0};
+    cudaGraphExec_t start = nullptr, iter = nullptr;
+    int nodes_start = 0, nodes_iter = 0;
 };
 
 struct StateLevel {
@@ -141,8 +146,8 @@ struct StateLevel {
     double *vb, *vx, *vx2, *vd, *vr;
     float *fb, *fx, *fx2, *fd, *fr;
     // CG work at this level (FP64): x r z p q; FP32 inner CG: same
-    double *cx, *cr, *cz, *cp, *cq, *cp2; // cp/cp2: search direction ping-pong
-    float *gx, *gr, *gz, *gp, *gq, *gp2;
+    double *cx, *cr, *cz, *cp, *cq, *cs; // x r z p q and s = A z
+    float *gx, *gr, *gz, *gp, *gq, *gs;
     double *ry; // refinement residual (FP64)
     CgScal *scal = nullptr;  // FP64 CG loop scalars
     CgScal *scal32 = nullptr; // FP32 inner CG loop scalars
@@ -157,7 +162,7 @@ struct CtrlLevel {
     int *agg = nullptr;
     int nagg = 0;
     // mass CG work
-    double *mx, *mr, *mz, *mp, *mq, *mp2;
+    double *mx, *mr, *mz, *mp, *mq, *ms;
     CgScal *mscal = nullptr;
     CgGraph mgraph;
     // MLAS work
@@ -229,6 +234,8 @@ struct amgh_problem {
 
 // ------------------------------------------------------------------ sparse.cu
 int csr_to_sell(Arena &ar, DevCsr &a, int want32, cudaStream_t s);
+// pick SELL-32 or lanes-per-row CSR from the mean row length and build it
+int prepare_operator(Arena &ar, DevCsr &a, cudaStream_t s, int force_tpr = 0);
 int csr_transpose(Arena &ar, const DevCsr &a, DevCsr &t, cudaStream_t s);
 // y = A x (FP64 or FP32 SELL)
 int spmv(amgh_problem *p, const DevCsr &a, const double *x, double *y, const int *skip, int timed);
@@ -236,6 +243,8 @@ int spmv32(amgh_problem *p, const DevCsr &a, const float *x, float *y, const int
 // y = A1 x1 + c * A2 x2 (same row count)
 int spmv2(amgh_problem *p, const DevCsr &a1, const double *x1, const DevCsr &a2, const double *x2,
           double c, double *y, const int *skip);
+int vec_axpby_spmv(amgh_problem *p, const DevCsr &a, const double *x, double c, double *y, const int *skip);
+double spmv_bytes(const DevCsr &a, int value_bytes);
 
 template <typename T>
 struct VT;
@@ -264,19 +273,13 @@ int red_alloc(Arena &ar, RedSlot &slot, int capacity);
 template <typename T>
 int cg_start(amgh_problem *p, RedSlot &red, int n, const T *f, T *x, T *r, CgScal *sc,
              double tol, int maxit, int zero_x);
-template <typename T>
-int cg_rz_first(amgh_problem *p, RedSlot &red, int n, const T *r, const T *z, CgScal *sc);
-template <typename T>
-int cg_spmv_pq_xpay(amgh_problem *p, RedSlot &red, const DevCsr &a, const T *z, const T *pin, T *pout, T *q,
-                    CgScal *sc, int timed);
-template <typename T>
-int cg_update(amgh_problem *p, RedSlot &red, int n, T *x, T *r, const T *pv, const T *q, CgScal *sc,
-              float *r32 = nullptr);
-template <typename T>
-int cg_rz_next(amgh_problem *p, RedSlot &red, int n, const T *r, const T *z, CgScal *sc);
-int cg_f2d_rz(amgh_problem *p, RedSlot &red, int n, const float *z32, double *z, const double *r, CgScal *sc,
-              int first);
-// refinement loop pieces
+template <typename T, typename Z>
+int cg2_spmv(amgh_problem *p, RedSlot &red, const DevCsr &a, const Z *z, const T *r, T *s, CgScal *sc, int timed);
+template <typename T, typename Z>
+int cg2_update(amgh_problem *p, RedSlot &red, int n, Z *z, const T *s, T *pv, T *q, T *x, T *r, float *r32,
+               const double *invd, CgScal *sc);
+int cg_update_outer(amgh_problem *p, RedSlot &red, int n, double *x, double *r, const double *pv, const double *q,
+                    CgScal *sc);
 int ref_start(amgh_problem *p, RedSlot &red, int n, const double *f, double *y, double *r,
               CgScal *rs, double tol, int maxit);
 int ref_to32(amgh_problem *p, RedSlot &red, int n, const double *r, float *r32, CgScal *rs);

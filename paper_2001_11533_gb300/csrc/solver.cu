@@ -21,8 +21,6 @@
 // pieces from blas.cu without a template
 int mass_start(amgh_problem *p, RedSlot &red, int n, const double *f, double *x, double *r, double *z,
                const double *invd, CgScal *sc, double tol, int maxit);
-int mass_iter(amgh_problem *p, RedSlot &red, const DevCsr &M, double *x, double *r, double *z, const double *pin,
-              double *pout, double *q, const double *invd, CgScal *sc);
 int outer_pq(amgh_problem *p, RedSlot &red, int n, const double *pv, const double *q, CgScal *sc);
 int outer_rz(amgh_problem *p, RedSlot &red, int n, const double *r, const double *z, double *pv, CgScal *sc,
              int first);
@@ -74,8 +72,8 @@ int solver_alloc(amgh_problem *p)
         TRY(ar.alloc(&S.cz, m));
         TRY(ar.alloc(&S.cp, m));
         TRY(ar.alloc(&S.cq, m));
-        TRY(ar.alloc(&S.cp2, m));
-        TRY(ar.alloc(&S.gp2, m));
+        TRY(ar.alloc(&S.cs, m));
+        TRY(ar.alloc(&S.gs, m));
         TRY(ar.alloc(&S.gx, m));
         TRY(ar.alloc(&S.gr, m));
         TRY(ar.alloc(&S.gz, m));
@@ -96,7 +94,7 @@ int solver_alloc(amgh_problem *p)
         CtrlLevel &C = p->cl[l];
         int n = C.Mu.rows;
         int m = l < p->Ls ? p->sl[l].A.rows : 1;
-        double **vn[] = {&C.mx, &C.mr, &C.mz, &C.mp, &C.mq, &C.mp2, &C.bc, &C.qc, &C.wc,
+        double **vn[] = {&C.mx, &C.mr, &C.mz, &C.mp, &C.mq, &C.ms, &C.bc, &C.qc, &C.wc,
                          &C.w1, &C.ta, &C.tb, &C.hu, &C.rq, &C.du};
         for (double **q : vn) TRY(ar.alloc(q, n));
         double **vm[] = {&C.t1, &C.ys, &C.t2, &C.ps};
@@ -248,8 +246,7 @@ static int replay(amgh_problem *p, cudaGraphExec_t ex, int nodes)
 static void free_graph(CgGraph &g)
 {
     if (g.start) cudaGraphExecDestroy(g.start);
-    for (int k = 0; k < 2; k++)
-        if (g.iter[k]) cudaGraphExecDestroy(g.iter[k]);
+    if (g.iter) cudaGraphExecDestroy(g.iter);
     g = CgGraph();
 }
 
@@ -281,48 +278,37 @@ __global__ void k_f2d(int n, const float *__restrict__ a, double *__restrict__ b
 
 // mode 0: FP64 CG + FP64 V-cycle; 1: FP32 CG + FP32 V-cycle; 2: FP64 CG + FP32
 // V-cycle (the update also writes the FP32 copy of r that the V-cycle reads,
-// and one kernel converts z back and forms r.z).
+// and the SpMV gathers the FP32 z directly).
+// start: z = V r;  iteration: s = A z (+ dots), p/q/x/r update, z = V r.
 static int cg_body_start(amgh_problem *p, int l, int mode)
 {
     StateLevel &S = p->sl[l];
     int n = S.A.rows;
-    if (mode == 1) {
-        TRY(vcyc<float>(p, l, S.gr, S.gz, &S.scal32->done));
-        return cg_rz_first<float>(p, S.red, n, S.gr, S.gz, S.scal32);
-    }
-    if (mode == 0) {
-        TRY(vcyc<double>(p, l, S.cr, S.cz, &S.scal->done));
-        return cg_rz_first<double>(p, S.red, n, S.cr, S.cz, S.scal);
-    }
+    if (mode == 1) return vcyc<float>(p, l, S.gr, S.gz, &S.scal32->done);
+    if (mode == 0) return vcyc<double>(p, l, S.cr, S.cz, &S.scal->done);
     k_d2f<<<ceil_div(n, 256), 256, 0, p->stream>>>(n, S.cr, S.fb, &S.scal->done);
     LAUNCH_CHECK();
-    TRY(vcyc<float>(p, l, S.fb, S.gz, &S.scal->done));
-    return cg_f2d_rz(p, S.red, n, S.gz, S.cz, S.cr, S.scal, 1);
+    return vcyc<float>(p, l, S.fb, S.gz, &S.scal->done);
 }
 
-// one iteration; parity selects which search-direction buffer is read and
-// which is written by the fused p = z + beta p / q = A p kernel
-static int cg_body_iter(amgh_problem *p, int l, int mode, int parity)
+static int cg_body_iter(amgh_problem *p, int l, int mode)
 {
     StateLevel &S = p->sl[l];
     int n = S.A.rows;
+    int timed = (l == 0);
     if (mode == 1) {
-        float *pin = parity ? S.gp2 : S.gp, *pout = parity ? S.gp : S.gp2;
-        TRY(cg_spmv_pq_xpay<float>(p, S.red, S.A, S.gz, pin, pout, S.gq, S.scal32, l == 0));
-        TRY(cg_update<float>(p, S.red, n, S.gx, S.gr, pout, S.gq, S.scal32));
-        TRY(vcyc<float>(p, l, S.gr, S.gz, &S.scal32->done));
-        return cg_rz_next<float>(p, S.red, n, S.gr, S.gz, S.scal32);
+        TRY((cg2_spmv<float, float>(p, S.red, S.A, S.gz, S.gr, S.gs, S.scal32, timed)));
+        TRY((cg2_update<float, float>(p, S.red, n, S.gz, S.gs, S.gp, S.gq, S.gx, S.gr, nullptr, nullptr, S.scal32)));
+        return vcyc<float>(p, l, S.gr, S.gz, &S.scal32->done);
     }
-    double *pin = parity ? S.cp2 : S.cp, *pout = parity ? S.cp : S.cp2;
-    TRY(cg_spmv_pq_xpay<double>(p, S.red, S.A, S.cz, pin, pout, S.cq, S.scal, l == 0));
     if (mode == 0) {
-        TRY(cg_update<double>(p, S.red, n, S.cx, S.cr, pout, S.cq, S.scal));
-        TRY(vcyc<double>(p, l, S.cr, S.cz, &S.scal->done));
-        return cg_rz_next<double>(p, S.red, n, S.cr, S.cz, S.scal);
+        TRY((cg2_spmv<double, double>(p, S.red, S.A, S.cz, S.cr, S.cs, S.scal, timed)));
+        TRY((cg2_update<double, double>(p, S.red, n, S.cz, S.cs, S.cp, S.cq, S.cx, S.cr, nullptr, nullptr, S.scal)));
+        return vcyc<double>(p, l, S.cr, S.cz, &S.scal->done);
     }
-    TRY(cg_update<double>(p, S.red, n, S.cx, S.cr, pout, S.cq, S.scal, S.fb));
-    TRY(vcyc<float>(p, l, S.fb, S.gz, &S.scal->done));
-    return cg_f2d_rz(p, S.red, n, S.gz, S.cz, S.cr, S.scal, 0);
+    TRY((cg2_spmv<double, float>(p, S.red, S.A, S.gz, S.cr, S.cs, S.scal, timed)));
+    TRY((cg2_update<double, float>(p, S.red, n, S.gz, S.cs, S.cp, S.cq, S.cx, S.cr, S.fb, nullptr, S.scal)));
+    return vcyc<float>(p, l, S.fb, S.gz, &S.scal->done);
 }
 
 // PCG for A_l x = f preconditioned by V_l; the solution is left in S.cx (FP64
@@ -336,10 +322,9 @@ static int pcg_run(amgh_problem *p, int l, int mode, const void *f, double tol, 
     else TRY(cg_start<double>(p, S.red, n, (const double *)f, S.cx, S.cr, sc, tol, maxit, 1));
     CgGraph &g = S.graph[mode];
     bool gr = use_graphs(p);
-    if (gr && !g.iter[0]) {
+    if (gr && !g.iter) {
         TRY(capture(p, [&] { return cg_body_start(p, l, mode); }, &g.start, &g.nodes_start));
-        for (int k = 0; k < 2; k++)
-            TRY(capture(p, [&] { return cg_body_iter(p, l, mode, k); }, &g.iter[k], &g.nodes_iter[k]));
+        TRY(capture(p, [&] { return cg_body_iter(p, l, mode); }, &g.iter, &g.nodes_iter));
     }
     if (gr) TRY(replay(p, g.start, g.nodes_start));
     else TRY(cg_body_start(p, l, mode));
@@ -350,9 +335,8 @@ static int pcg_run(amgh_problem *p, int l, int mode, const void *f, double tol, 
     CgScal h;
     for (;;) {
         for (int c = 0; c < chunk; c++) {
-            int k = (enq + c) & 1;
-            if (gr) TRY(replay(p, g.iter[k], g.nodes_iter[k]));
-            else TRY(cg_body_iter(p, l, mode, k));
+            if (gr) TRY(replay(p, g.iter, g.nodes_iter));
+            else TRY(cg_body_iter(p, l, mode));
         }
         enq += chunk;
         TRY(read_scal(p, sc, &h));
@@ -412,20 +396,19 @@ int mass_solve(amgh_problem *p, int l, const double *b, double *x, int64_t *iter
                    p->sopts.mass_max_iter));
     bool gr = use_graphs(p);
     CgGraph &g = C.mgraph;
-    auto body = [&](int k) {
-        double *pin = k ? C.mp2 : C.mp, *pout = k ? C.mp : C.mp2;
-        return mass_iter(p, C.red, C.Mu, C.mx, C.mr, C.mz, pin, pout, C.mq, C.mu_invdiag, C.mscal);
+    auto body = [&]() {
+        TRY((cg2_spmv<double, double>(p, C.red, C.Mu, C.mz, C.mr, C.ms, C.mscal, 0)));
+        return cg2_update<double, double>(p, C.red, n, C.mz, C.ms, C.mp, C.mq, C.mx, C.mr, nullptr, C.mu_invdiag,
+                                          C.mscal);
     };
-    if (gr && !g.iter[0])
-        for (int k = 0; k < 2; k++) TRY(capture(p, [&] { return body(k); }, &g.iter[k], &g.nodes_iter[k]));
+    if (gr && !g.iter) TRY(capture(p, body, &g.iter, &g.nodes_iter));
     int chunk = p->mchunk_hint[l] > 1 ? (p->mchunk_hint[l] * 7) / 8 : 1;
     int enq = 0;
     CgScal h;
     for (;;) {
         for (int c = 0; c < chunk; c++) {
-            int k = (enq + c) & 1;
-            if (gr) TRY(replay(p, g.iter[k], g.nodes_iter[k]));
-            else TRY(body(k));
+            if (gr) TRY(replay(p, g.iter, g.nodes_iter));
+            else TRY(body());
         }
         enq += chunk;
         TRY(read_scal(p, C.mscal, &h));
@@ -540,8 +523,6 @@ int outer_solve(amgh_problem *p, const double *u0, double *u, const amgh_solve_o
         f = p->ou;
     }
     CgScal *sc = p->oscal;
-    const int *skip = &sc->done;
-    (void)skip;
     TRY(cg_start<double>(p, p->ored, n, f, u, r, sc, tol, o->max_iter, 1));
     CgScal h;
     TRY(read_scal(p, sc, &h));
@@ -556,7 +537,7 @@ int outer_solve(amgh_problem *p, const double *u0, double *u, const amgh_solve_o
             if (h.done) break;
             TRY(hessian_level(p, 0, pv, q));
             TRY(outer_pq(p, p->ored, n, pv, q, sc));
-            TRY(cg_update<double>(p, p->ored, n, u, r, pv, q, sc));
+            TRY(cg_update_outer(p, p->ored, n, u, r, pv, q, sc));
             TRY(read_scal(p, sc, &h));
             if (h.done) break;
             if (o->precond) TRY(mlas_Q(p, 0, r, z));

@@ -10,6 +10,7 @@
 // and gathers x through the read-only cache.  Entries keep the CSR order, so
 // padding (value 0, column = the row's last column) only adds exact zeros.
 #include "internal.cuh"
+#include "spmv.cuh"
 #include "util.cuh"
 
 // ------------------------------------------------------------------ conversion
@@ -157,76 +158,80 @@ int csr_transpose(Arena &ar, const DevCsr &a, DevCsr &t, cudaStream_t s)
     return AMGH_OK;
 }
 
-// ------------------------------------------------------------------ SpMV family
-template <typename T>
-static inline const T *h_sell_vals(const DevCsr &a);
-template <>
-inline const double *h_sell_vals<double>(const DevCsr &a) { return a.sl_v; }
-template <>
-inline const float *h_sell_vals<float>(const DevCsr &a) { return a.sl_v32; }
-
-// row dot product of SELL row r with x
-template <typename T>
-__device__ __forceinline__ T sell_row(int r, const int *__restrict__ slp, const int *__restrict__ sci,
-                                      const T *__restrict__ sv, const T *__restrict__ x)
+// ------------------------------------------------------------------ operator layout
+__global__ void k_to_f32(int64_t n, const double *__restrict__ a, float *__restrict__ b)
 {
-    int s = r >> 5, lane = r & 31;
-    int beg = slp[s] + lane, end = slp[s + 1];
-    T acc = (T)0;
-    for (int k = beg; k < end; k += 32) acc += sv[k] * __ldg(&x[sci[k]]);
-    return acc;
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) b[i] = (float)a[i];
 }
 
+int prepare_operator(Arena &ar, DevCsr &a, cudaStream_t s, int force_tpr)
+{
+    double avg = a.rows > 0 ? (double)a.nnz / a.rows : 0.0;
+    int tpr = 1;
+    if (force_tpr > 0) tpr = force_tpr;
+    else if (avg > 96.0) tpr = 32;
+    else if (avg > 48.0) tpr = 16;
+    else if (avg > 24.0) tpr = 8;
+    else if (avg > 12.0) tpr = 4;
+    a.tpr = tpr;
+    if (tpr == 1) return csr_to_sell(ar, a, 1, s);
+    TRY(ar.alloc(&a.v32, a.nnz));
+    if (a.nnz > 0) {
+        k_to_f32<<<ceil_div(a.nnz, 256), 256, 0, s>>>(a.nnz, a.v, a.v32);
+        LAUNCH_CHECK();
+    }
+    CU(cudaStreamSynchronize(s));
+    return AMGH_OK;
+}
+
+// ------------------------------------------------------------------ SpMV family
 #define SKIP_RETURN() \
     if (skip && *skip) return
 
-template <typename T>
-__global__ void k_spmv(int rows, const int *__restrict__ slp, const int *__restrict__ sci,
-                       const T *__restrict__ sv, const T *__restrict__ x, T *__restrict__ y,
-                       const int *__restrict__ skip)
+template <typename T, int TPR>
+__global__ void k_spmv(MatView<T> A, const T *__restrict__ x, T *__restrict__ y, const int *__restrict__ skip)
 {
     SKIP_RETURN();
-    int r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= rows) return;
-    y[r] = sell_row<T>(r, slp, sci, sv, x);
+    int r = my_row<TPR>();
+    T v = row_sum<T, TPR>(A, r, [&](int c) { return __ldg(&x[c]); });
+    if (r < A.rows && row_leader<TPR>()) y[r] = v;
 }
 
 // y = A1 x1 + c A2 x2
-__global__ void k_spmv2(int rows, const int *__restrict__ slp1, const int *__restrict__ sci1,
-                        const double *__restrict__ sv1, const double *__restrict__ x1,
-                        const int *__restrict__ slp2, const int *__restrict__ sci2,
-                        const double *__restrict__ sv2, const double *__restrict__ x2, double c,
-                        double *__restrict__ y, const int *__restrict__ skip)
+template <typename T, int TPR>
+__global__ void k_spmv2(MatView<T> A1, const T *__restrict__ x1, MatView<T> A2, const T *__restrict__ x2, T c,
+                        T *__restrict__ y, const int *__restrict__ skip)
 {
     SKIP_RETURN();
-    int r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= rows) return;
-    double a = sell_row<double>(r, slp1, sci1, sv1, x1);
-    double b = sell_row<double>(r, slp2, sci2, sv2, x2);
-    y[r] = a + c * b;
+    int r = my_row<TPR>();
+    T a = row_sum<T, TPR>(A1, r, [&](int j) { return __ldg(&x1[j]); });
+    // A2 may use another layout; it is read row-wise by the group leader's lanes
+    T b = row_sum<T, TPR>(A2, r, [&](int j) { return __ldg(&x2[j]); });
+    if (r < A1.rows && row_leader<TPR>()) y[r] = a + c * b;
 }
 
 // smoother step: d = cd d + cr D^-1 (b - A x); xn = x + d
-template <typename T>
-__global__ void k_cheb_step(int rows, const int *__restrict__ slp, const int *__restrict__ sci,
-                            const T *__restrict__ sv, const T *__restrict__ invd, const T *__restrict__ b,
+template <typename T, int TPR>
+__global__ void k_cheb_step(MatView<T> A, const T *__restrict__ invd, const T *__restrict__ b,
                             const T *__restrict__ x, T *__restrict__ d, T *__restrict__ xn, T cdv, T crv,
                             const int *__restrict__ skip)
 {
     SKIP_RETURN();
-    int r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= rows) return;
-    T ax = sell_row<T>(r, slp, sci, sv, x);
-    T res = (b[r] - ax) * invd[r];
-    T dn = cdv * d[r] + crv * res;
-    d[r] = dn;
-    xn[r] = x[r] + dn;
+    int r = my_row<TPR>();
+    T ax = row_sum<T, TPR>(A, r, [&](int c) { return __ldg(&x[c]); });
+    if (r < A.rows && row_leader<TPR>()) {
+        T res = (b[r] - ax) * invd[r];
+        T dn = cdv * d[r] + crv * res;
+        d[r] = dn;
+        xn[r] = x[r] + dn;
+    }
 }
 
 // first smoother step from x = 0: d = c D^-1 b; x = d
 template <typename T>
-__global__ void k_cheb_first(int n, const T *__restrict__ invd, const T *__restrict__ b,
-                             T *__restrict__ d, T *__restrict__ x, T c, const int *__restrict__ skip)
+__global__ void k_cheb_first(int n, const T *__restrict__ invd, const T *__restrict__ b, T *__restrict__ d,
+                             T *__restrict__ x, T c, const int *__restrict__ skip)
 {
     SKIP_RETURN();
     int r = blockIdx.x * blockDim.x + threadIdx.x;
@@ -236,50 +241,48 @@ __global__ void k_cheb_first(int n, const T *__restrict__ invd, const T *__restr
     x[r] = v;
 }
 
-template <typename T>
-__global__ void k_residual(int rows, const int *__restrict__ slp, const int *__restrict__ sci,
-                           const T *__restrict__ sv, const T *__restrict__ b, const T *__restrict__ x,
-                           T *__restrict__ r, const int *__restrict__ skip)
+template <typename T, int TPR>
+__global__ void k_residual(MatView<T> A, const T *__restrict__ b, const T *__restrict__ x, T *__restrict__ res,
+                           const int *__restrict__ skip)
 {
     SKIP_RETURN();
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= rows) return;
-    r[i] = b[i] - sell_row<T>(i, slp, sci, sv, x);
+    int r = my_row<TPR>();
+    T ax = row_sum<T, TPR>(A, r, [&](int c) { return __ldg(&x[c]); });
+    if (r < A.rows && row_leader<TPR>()) res[r] = b[r] - ax;
 }
 
 // restriction b_c = S^T r fused with the first smoother step of the coarse
 // level from zero: d_c = x_c = c0 D_c^-1 b_c
-template <typename T>
-__global__ void k_restrict_first(int rows, const int *__restrict__ slp, const int *__restrict__ sci,
-                                 const T *__restrict__ sv, const T *__restrict__ r, T *__restrict__ bc,
+template <typename T, int TPR>
+__global__ void k_restrict_first(MatView<T> St, const T *__restrict__ r, T *__restrict__ bc,
                                  const T *__restrict__ invd, T *__restrict__ d, T *__restrict__ x, T c0,
                                  const int *__restrict__ skip)
 {
     SKIP_RETURN();
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= rows) return;
-    T b = sell_row<T>(i, slp, sci, sv, r);
-    bc[i] = b;
-    T v = c0 * (b * invd[i]);
-    d[i] = v;
-    x[i] = v;
+    int i = my_row<TPR>();
+    T b = row_sum<T, TPR>(St, i, [&](int c) { return __ldg(&r[c]); });
+    if (i < St.rows && row_leader<TPR>()) {
+        bc[i] = b;
+        T v = c0 * (b * invd[i]);
+        d[i] = v;
+        x[i] = v;
+    }
 }
 
-template <typename T>
-__global__ void k_prolong_add(int rows, const int *__restrict__ slp, const int *__restrict__ sci,
-                              const T *__restrict__ sv, const T *__restrict__ e, T *__restrict__ x,
+template <typename T, int TPR>
+__global__ void k_prolong_add(MatView<T> S, const T *__restrict__ e, T *__restrict__ x,
                               const int *__restrict__ skip)
 {
     SKIP_RETURN();
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= rows) return;
-    x[i] = x[i] + sell_row<T>(i, slp, sci, sv, e);
+    int i = my_row<TPR>();
+    T v = row_sum<T, TPR>(S, i, [&](int c) { return __ldg(&e[c]); });
+    if (i < S.rows && row_leader<TPR>()) x[i] = x[i] + v;
 }
 
 // x = inv b, one warp per row of the dense explicit inverse
 template <typename T>
-__global__ void k_dense_gemv(int n, const double *__restrict__ inv, const T *__restrict__ b,
-                             T *__restrict__ x, const int *__restrict__ skip)
+__global__ void k_dense_gemv(int n, const double *__restrict__ inv, const T *__restrict__ b, T *__restrict__ x,
+                             const int *__restrict__ skip)
 {
     SKIP_RETURN();
     int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
@@ -293,7 +296,7 @@ __global__ void k_dense_gemv(int n, const double *__restrict__ inv, const T *__r
 
 static const int TPB = 256;
 
-static double spmv_bytes(const DevCsr &a, int vb)
+double spmv_bytes(const DevCsr &a, int vb)
 {
     return (double)a.nnz * (vb + 4) + 4.0 * (a.rows + 1) + (double)vb * (a.rows + a.cols);
 }
@@ -303,8 +306,8 @@ int spmv_t(amgh_problem *p, const DevCsr &a, const T *x, T *y, const int *skip, 
 {
     if (a.rows == 0) return AMGH_OK;
     timer_begin(p, timed);
-    k_spmv<T><<<ceil_div(a.rows, TPB), TPB, 0, p->stream>>>(a.rows, a.sl_ptr, a.sl_ci, h_sell_vals<T>(a), x,
-                                                            y, skip);
+    MatView<T> A = view<T>(a);
+    LAUNCH_TPR(k_spmv, T, A.tpr, A.rows, p->stream, A, x, y, skip);
     LAUNCH_CHECK();
     timer_end(p, timed, spmv_bytes(a, sizeof(T)));
     return AMGH_OK;
@@ -321,12 +324,38 @@ int spmv32(amgh_problem *p, const DevCsr &a, const float *x, float *y, const int
     return spmv_t<float>(p, a, x, y, skip, timed);
 }
 
-int spmv2(amgh_problem *p, const DevCsr &a1, const double *x1, const DevCsr &a2, const double *x2,
-          double c, double *y, const int *skip)
+int spmv2(amgh_problem *p, const DevCsr &a1, const double *x1, const DevCsr &a2, const double *x2, double c,
+          double *y, const int *skip)
 {
     if (a1.rows == 0) return AMGH_OK;
-    k_spmv2<<<ceil_div(a1.rows, TPB), TPB, 0, p->stream>>>(a1.rows, a1.sl_ptr, a1.sl_ci, a1.sl_v, x1,
-                                                           a2.sl_ptr, a2.sl_ci, a2.sl_v, x2, c, y, skip);
+    // both operands use the layout of a1 (a2 is re-viewed with a1's lane count)
+    MatView<double> A1 = view<double>(a1), A2 = view<double>(a2);
+    if (A1.tpr != A2.tpr) {
+        // mixed layouts: two passes through y
+        TRY(spmv_t<double>(p, a2, x2, y, skip, 0));
+        TRY(vec_axpby_spmv(p, a1, x1, c, y, skip));
+        return AMGH_OK;
+    }
+    LAUNCH_TPR(k_spmv2, double, A1.tpr, A1.rows, p->stream, A1, x1, A2, x2, c, y, skip);
+    LAUNCH_CHECK();
+    return AMGH_OK;
+}
+
+// y = A x + c y  (used when the two operands of spmv2 have different layouts)
+template <typename T, int TPR>
+__global__ void k_spmv_axpy(MatView<T> A, const T *__restrict__ x, T c, T *__restrict__ y,
+                            const int *__restrict__ skip)
+{
+    SKIP_RETURN();
+    int r = my_row<TPR>();
+    T v = row_sum<T, TPR>(A, r, [&](int j) { return __ldg(&x[j]); });
+    if (r < A.rows && row_leader<TPR>()) y[r] = v + c * y[r];
+}
+
+int vec_axpby_spmv(amgh_problem *p, const DevCsr &a, const double *x, double c, double *y, const int *skip)
+{
+    MatView<double> A = view<double>(a);
+    LAUNCH_TPR(k_spmv_axpy, double, A.tpr, A.rows, p->stream, A, x, c, y, skip);
     LAUNCH_CHECK();
     return AMGH_OK;
 }
@@ -341,13 +370,13 @@ int cheb_first(amgh_problem *p, int n, const T *invd, const T *b, T *d, T *x, do
 }
 
 template <typename T>
-int cheb_step(amgh_problem *p, const DevCsr &a, const T *invd, const T *b, const T *x, T *d, T *xn,
-              double cdv, double crv, const int *skip, int timed)
+int cheb_step(amgh_problem *p, const DevCsr &a, const T *invd, const T *b, const T *x, T *d, T *xn, double cdv,
+              double crv, const int *skip, int timed)
 {
     if (a.rows == 0) return AMGH_OK;
     timer_begin(p, timed);
-    k_cheb_step<T><<<ceil_div(a.rows, TPB), TPB, 0, p->stream>>>(a.rows, a.sl_ptr, a.sl_ci, h_sell_vals<T>(a),
-                                                                 invd, b, x, d, xn, (T)cdv, (T)crv, skip);
+    MatView<T> A = view<T>(a);
+    LAUNCH_TPR(k_cheb_step, T, A.tpr, A.rows, p->stream, A, invd, b, x, d, xn, (T)cdv, (T)crv, skip);
     LAUNCH_CHECK();
     // algorithmic bytes: matrix + x gather + b, invd, d (read+write), xn
     timer_end(p, timed, spmv_bytes(a, sizeof(T)) + 4.0 * sizeof(T) * a.rows);
@@ -359,8 +388,8 @@ int residual(amgh_problem *p, const DevCsr &a, const T *b, const T *x, T *r, con
 {
     if (a.rows == 0) return AMGH_OK;
     timer_begin(p, timed);
-    k_residual<T><<<ceil_div(a.rows, TPB), TPB, 0, p->stream>>>(a.rows, a.sl_ptr, a.sl_ci, h_sell_vals<T>(a), b,
-                                                                x, r, skip);
+    MatView<T> A = view<T>(a);
+    LAUNCH_TPR(k_residual, T, A.tpr, A.rows, p->stream, A, b, x, r, skip);
     LAUNCH_CHECK();
     timer_end(p, timed, spmv_bytes(a, sizeof(T)) + sizeof(T) * (double)a.rows);
     return AMGH_OK;
@@ -371,9 +400,8 @@ int restrict_first(amgh_problem *p, const DevCsr &st, const T *r, T *bc, const T
                    double c0, const int *skip)
 {
     if (st.rows == 0) return AMGH_OK;
-    k_restrict_first<T><<<ceil_div(st.rows, TPB), TPB, 0, p->stream>>>(st.rows, st.sl_ptr, st.sl_ci,
-                                                                       h_sell_vals<T>(st), r, bc, invd_c, d_c, x_c,
-                                                                       (T)c0, skip);
+    MatView<T> A = view<T>(st);
+    LAUNCH_TPR(k_restrict_first, T, A.tpr, A.rows, p->stream, A, r, bc, invd_c, d_c, x_c, (T)c0, skip);
     LAUNCH_CHECK();
     return AMGH_OK;
 }
@@ -382,8 +410,8 @@ template <typename T>
 int prolong_add(amgh_problem *p, const DevCsr &s, const T *e, T *x, const int *skip)
 {
     if (s.rows == 0) return AMGH_OK;
-    k_prolong_add<T><<<ceil_div(s.rows, TPB), TPB, 0, p->stream>>>(s.rows, s.sl_ptr, s.sl_ci, h_sell_vals<T>(s), e,
-                                                                   x, skip);
+    MatView<T> A = view<T>(s);
+    LAUNCH_TPR(k_prolong_add, T, A.tpr, A.rows, p->stream, A, e, x, skip);
     LAUNCH_CHECK();
     return AMGH_OK;
 }
@@ -397,14 +425,14 @@ int dense_gemv(amgh_problem *p, int n, const double *inv, const T *b, T *x, cons
     return AMGH_OK;
 }
 
-#define INST(T)                                                                                       \
-    template int cheb_first<T>(amgh_problem *, int, const T *, const T *, T *, T *, double, const int *); \
-    template int cheb_step<T>(amgh_problem *, const DevCsr &, const T *, const T *, const T *, T *, T *,  \
-                              double, double, const int *, int);                                      \
-    template int residual<T>(amgh_problem *, const DevCsr &, const T *, const T *, T *, const int *, int); \
-    template int prolong_add<T>(amgh_problem *, const DevCsr &, const T *, T *, const int *);            \
+#define INST(T)                                                                                              \
+    template int cheb_first<T>(amgh_problem *, int, const T *, const T *, T *, T *, double, const int *);        \
+    template int cheb_step<T>(amgh_problem *, const DevCsr &, const T *, const T *, const T *, T *, T *, double, \
+                              double, const int *, int);                                                    \
+    template int residual<T>(amgh_problem *, const DevCsr &, const T *, const T *, T *, const int *, int);       \
+    template int prolong_add<T>(amgh_problem *, const DevCsr &, const T *, T *, const int *);                  \
     template int restrict_first<T>(amgh_problem *, const DevCsr &, const T *, T *, const T *, T *, T *, double, \
-                                   const int *);                                                         \
+                                   const int *);                                                            \
     template int dense_gemv<T>(amgh_problem *, int, const double *, const T *, T *, const int *);
 INST(double)
 INST(float)
