@@ -429,8 +429,15 @@ int amg_prolongator(amgh_problem *p, Arena &ar, const DevCsr &a, const int *agg,
 }
 
 // ------------------------------------------------------------------ SpGEMM
+// Candidate count of row i: u_i = sum over A's row i of the lengths of the
+// B rows it selects.  Rows with u_i <= WARP_TS / 2 are handled by one warp
+// with its hash table in shared memory; longer rows by one thread with a
+// table of 2^ceil(log2(2 u_i)) slots in global memory.
+#define WARP_TS 2048
+#define WARPS_PER_BLOCK 2
+
 __global__ void k_gemm_ub(int n, const int *__restrict__ arp, const int *__restrict__ aci,
-                          const int *__restrict__ brp, long long *__restrict__ ub)
+                          const int *__restrict__ brp, long long *__restrict__ ub, int *__restrict__ small)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -439,23 +446,24 @@ __global__ void k_gemm_ub(int n, const int *__restrict__ arp, const int *__restr
         int j = aci[k];
         u += brp[j + 1] - brp[j];
     }
-    // hash table of the row: power of two >= 2u (at least 2)
+    int sm = u <= WARP_TS / 2;
+    small[i] = sm;
     long long t = 2;
     while (t < 2 * u) t <<= 1;
-    ub[i] = u > 0 ? t : 0;
+    ub[i] = (u > 0 && !sm) ? t : 0;
 }
 
 __device__ __forceinline__ unsigned hslot(int key, unsigned mask) { return ((unsigned)key * 2654435761u) & mask; }
 
-// accumulate row i into its hash table in canonical order; count uniques
+// global-table path: accumulate row i in canonical order; count uniques
 __global__ void k_gemm_hash(int n, const int *__restrict__ arp, const int *__restrict__ aci,
                             const double *__restrict__ av, const int *__restrict__ brp,
                             const int *__restrict__ bci, const double *__restrict__ bv,
-                            const long long *__restrict__ toff, int *__restrict__ tkey, double *__restrict__ tval,
-                            int *__restrict__ cnt)
+                            const long long *__restrict__ toff, const int *__restrict__ small, int *__restrict__ tkey,
+                            double *__restrict__ tval, int *__restrict__ cnt)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
+    if (i >= n || small[i]) return;
     long long base = toff[i];
     unsigned size = (unsigned)(toff[i + 1] - base);
     int c = 0;
@@ -491,12 +499,12 @@ __global__ void k_gemm_hash(int n, const int *__restrict__ arp, const int *__res
     cnt[i] = c;
 }
 
-__global__ void k_gemm_out(int n, const long long *__restrict__ toff, const int *__restrict__ tkey,
-                           const double *__restrict__ tval, const int *__restrict__ crp, int *__restrict__ cci,
-                           double *__restrict__ cv)
+__global__ void k_gemm_out(int n, const long long *__restrict__ toff, const int *__restrict__ small,
+                           const int *__restrict__ tkey, const double *__restrict__ tval, const int *__restrict__ crp,
+                           int *__restrict__ cci, double *__restrict__ cv)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
+    if (i >= n || small[i]) return;
     long long base = toff[i];
     unsigned size = (unsigned)(toff[i + 1] - base);
     int b = crp[i], c = 0;
@@ -516,27 +524,112 @@ __global__ void k_gemm_out(int n, const long long *__restrict__ toff, const int 
     }
 }
 
+// shared-memory path: one warp per row.  Candidates are taken 32 at a time in
+// canonical order; lanes holding the same column form a group
+// (__match_any_sync) whose lowest lane finds / inserts the slot and adds the
+// group's products in lane order -- so every entry receives its products in
+// exactly the sequential order.  phase 0 counts, phase 1 writes the sorted row.
+__global__ void k_gemm_warp(int n, const int *__restrict__ arp, const int *__restrict__ aci,
+                            const double *__restrict__ av, const int *__restrict__ brp,
+                            const int *__restrict__ bci, const double *__restrict__ bv,
+                            const int *__restrict__ small, int phase, int *__restrict__ cnt,
+                            const int *__restrict__ crp, int *__restrict__ cci, double *__restrict__ cv)
+{
+    extern __shared__ unsigned char smem_raw[];
+    int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int *keys = (int *)smem_raw + w * WARP_TS;
+    double *vals = (double *)((int *)smem_raw + WARPS_PER_BLOCK * WARP_TS) + w * WARP_TS;
+    double *stage = (double *)((int *)smem_raw + WARPS_PER_BLOCK * WARP_TS) + WARPS_PER_BLOCK * WARP_TS + w * 32;
+    int i = blockIdx.x * WARPS_PER_BLOCK + w;
+    if (i >= n || !small[i]) return; // warp-uniform
+    const unsigned mask = WARP_TS - 1;
+    for (int t = lane; t < WARP_TS; t += 32) keys[t] = -1;
+    __syncwarp();
+    for (int k = arp[i]; k < arp[i + 1]; k++) {
+        int j = aci[k];
+        double aij = av[k];
+        int qb = brp[j], qe = brp[j + 1];
+        for (int q0 = qb; q0 < qe; q0 += 32) {
+            int q = q0 + lane;
+            bool valid = q < qe;
+            int J = valid ? bci[q] : -1;
+            double prod = valid ? __dmul_rn(aij, bv[q]) : 0.0;
+            unsigned grp = __match_any_sync(0xffffffffu, J);
+            stage[lane] = prod;
+            __syncwarp();
+            if (valid && lane == __ffs(grp) - 1) {
+                unsigned h = hslot(J, mask);
+                for (;;) {
+                    int old = atomicCAS(&keys[h], -1, J);
+                    if (old == -1) {
+                        vals[h] = 0.0;
+                        break;
+                    }
+                    if (old == J) break;
+                    h = (h + 1) & mask;
+                }
+                double acc = vals[h];
+                for (unsigned m = grp; m; m &= m - 1) acc = __dadd_rn(acc, stage[__ffs(m) - 1]);
+                vals[h] = acc;
+            }
+            __syncwarp();
+        }
+    }
+    if (phase == 0) {
+        int c = 0;
+        for (int t = lane; t < WARP_TS; t += 32) c += keys[t] >= 0;
+        for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+        if (lane == 0) cnt[i] = c;
+        return;
+    }
+    // rank of each key among the row's keys = its position in the sorted row
+    int base = crp[i];
+    for (int t = lane; t < WARP_TS; t += 32) {
+        int key = keys[t];
+        if (key < 0) continue;
+        int rank = 0;
+        for (int u = 0; u < WARP_TS; u++) {
+            int o = keys[u];
+            rank += (o >= 0) & (o < key);
+        }
+        cci[base + rank] = key;
+        cv[base + rank] = vals[t];
+    }
+}
+
+static size_t warp_smem() { return (size_t)WARPS_PER_BLOCK * WARP_TS * (sizeof(int) + sizeof(double)) +
+                                  (size_t)WARPS_PER_BLOCK * 32 * sizeof(double); }
+
 int spgemm(amgh_problem *p, Arena &ar, const DevCsr &a, const DevCsr &b, DevCsr &c)
 {
     cudaStream_t s = p->stream;
     int n = a.rows;
     c.rows = n;
     c.cols = b.cols;
+    static bool attr_set = false;
+    if (!attr_set) {
+        CU(cudaFuncSetAttribute(k_gemm_warp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)warp_smem()));
+        attr_set = true;
+    }
     Scratch sc;
     long long *ub = nullptr, *toff = nullptr;
-    int *cnt = nullptr, *tkey = nullptr;
+    int *cnt = nullptr, *tkey = nullptr, *small = nullptr;
     double *tval = nullptr;
     TRY(sc.alloc(&ub, n + 1));
     TRY(sc.alloc(&toff, n + 1));
     TRY(sc.alloc(&cnt, n + 1));
-    int nb = ceil_div(n, 128);
-    k_gemm_ub<<<nb, 128, 0, s>>>(n, a.rp, a.ci, b.rp, ub);
+    TRY(sc.alloc(&small, n + 1));
+    int nb = ceil_div(n, 128), nw = ceil_div(n, WARPS_PER_BLOCK);
+    k_gemm_ub<<<nb, 128, 0, s>>>(n, a.rp, a.ci, b.rp, ub, small);
     LAUNCH_CHECK();
     long long tot = 0;
     TRY(exclusive_scan<long long>(ub, toff, n, s, &tot));
     TRY(sc.alloc(&tkey, tot));
     TRY(sc.alloc(&tval, tot));
-    k_gemm_hash<<<nb, 128, 0, s>>>(n, a.rp, a.ci, a.v, b.rp, b.ci, b.v, toff, tkey, tval, cnt);
+    k_gemm_hash<<<nb, 128, 0, s>>>(n, a.rp, a.ci, a.v, b.rp, b.ci, b.v, toff, small, tkey, tval, cnt);
+    LAUNCH_CHECK();
+    k_gemm_warp<<<nw, 32 * WARPS_PER_BLOCK, warp_smem(), s>>>(n, a.rp, a.ci, a.v, b.rp, b.ci, b.v, small, 0, cnt,
+                                                              nullptr, nullptr, nullptr);
     LAUNCH_CHECK();
     TRY(ar.alloc(&c.rp, n + 1));
     int nnz = 0;
@@ -544,7 +637,10 @@ int spgemm(amgh_problem *p, Arena &ar, const DevCsr &a, const DevCsr &b, DevCsr 
     c.nnz = nnz;
     TRY(ar.alloc(&c.ci, nnz));
     TRY(ar.alloc(&c.v, nnz));
-    k_gemm_out<<<nb, 128, 0, s>>>(n, toff, tkey, tval, c.rp, c.ci, c.v);
+    k_gemm_out<<<nb, 128, 0, s>>>(n, toff, small, tkey, tval, c.rp, c.ci, c.v);
+    LAUNCH_CHECK();
+    k_gemm_warp<<<nw, 32 * WARPS_PER_BLOCK, warp_smem(), s>>>(n, a.rp, a.ci, a.v, b.rp, b.ci, b.v, small, 1,
+                                                              nullptr, c.rp, c.ci, c.v);
     LAUNCH_CHECK();
     CU(cudaStreamSynchronize(s));
     return AMGH_OK;

@@ -4,9 +4,9 @@
 //   * the dense coarsest Hessian H_c = M_yu^T A_c^-1 M_y A_c^-1 M_yu + beta M_u
 //     on Hessian level l-1 and its explicit inverse -- the exact coarsest
 //     inverse G_{l-1}^-1 assumed by the theory (Sec. 3.2).
-// Both inverses come from a right-looking Cholesky factorisation
-// (INDEFINITE if a pivot is not positive) and two triangular solves per
-// column.
+// Both inverses come from a right-looking Cholesky factorisation A = L L^T
+// (INDEFINITE if a pivot is not positive), the triangular inverse W = L^-1
+// computed column by column (one block per column) and A^-1 = W^T W.
 #include <math.h>
 
 #include "internal.cuh"
@@ -57,52 +57,24 @@ __global__ void k_chol_update(int n, int j, double *__restrict__ g)
     g[(int64_t)i * n + k] -= g[(int64_t)i * n + j] * g[(int64_t)k * n + j];
 }
 
-// inverse column c: solve L y = e_c, then L^T x = y
-__global__ void k_chol_inv(int n, const double *__restrict__ L, double *__restrict__ inv, double *__restrict__ work)
+// column k of W = L^-1 (one block per column): w_k = 1 / l_kk and, for i > k,
+// w_i = -(sum_{k <= j < i} l_ij w_j) / l_ii, the column kept in shared memory
+__global__ void k_trinv(int n, const double *__restrict__ L, double *__restrict__ W)
 {
-    int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= n) return;
-    double *y = work + (int64_t)c * n;
-    for (int i = 0; i < n; i++) {
-        double s = (i == c) ? 1.0 : 0.0;
-        if (i > c)
-            for (int k = c; k < i; k++) s -= L[(int64_t)i * n + k] * y[k];
-        else if (i < c)
-            s = 0.0;
-        y[i] = s / L[(int64_t)i * n + i];
+    extern __shared__ double w[];
+    __shared__ double sh32[32];
+    int k = blockIdx.x;
+    if (threadIdx.x == 0) w[k] = 1.0 / L[(int64_t)k * n + k];
+    __syncthreads();
+    for (int i = k + 1; i < n; i++) {
+        const double *row = L + (int64_t)i * n;
+        double s = 0.0;
+        for (int j = k + threadIdx.x; j < i; j += blockDim.x) s += row[j] * w[j];
+        s = block_sum(s, sh32);
+        if (threadIdx.x == 0) w[i] = -s / row[i];
+        __syncthreads();
     }
-    for (int i = n - 1; i >= 0; i--) {
-        double s = y[i];
-        for (int k = i + 1; k < n; k++) s -= L[(int64_t)k * n + i] * y[k];
-        y[i] = s / L[(int64_t)i * n + i];
-    }
-    for (int i = 0; i < n; i++) inv[(int64_t)i * n + c] = y[i];
-}
-
-int dense_spd_inverse(amgh_problem *p, double *g, int n, double *inv, int *info_dev)
-{
-    cudaStream_t s = p->stream;
-    CU(cudaMemsetAsync(info_dev, 0, sizeof(int), s));
-    for (int j = 0; j < n; j++) {
-        k_chol_col<<<1, 256, 0, s>>>(n, j, g, info_dev);
-        LAUNCH_CHECK();
-        int64_t m = n - j - 1;
-        if (m > 0) {
-            k_chol_update<<<ceil_div(m * m, 256), 256, 0, s>>>(n, j, g);
-            LAUNCH_CHECK();
-        }
-    }
-    int info = 0;
-    CU(cudaMemcpyAsync(&info, info_dev, sizeof(int), cudaMemcpyDeviceToHost, s));
-    CU(cudaStreamSynchronize(s));
-    if (info) return AMGH_ERR_INDEFINITE;
-    Scratch sc;
-    double *work = nullptr;
-    TRY(sc.alloc(&work, (int64_t)n * n));
-    k_chol_inv<<<ceil_div(n, 64), 64, 0, s>>>(n, g, inv, work);
-    LAUNCH_CHECK();
-    CU(cudaStreamSynchronize(s));
-    return AMGH_OK;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) W[(int64_t)i * n + k] = i >= k ? w[i] : 0.0;
 }
 
 // C = op(A) B (+ beta D), all row-major; transA: A is k x m and used as A^T
@@ -138,6 +110,34 @@ static int gemm(amgh_problem *p, int m, int n, int k, const double *A, int trans
     dim3 blk(TILE, TILE), grd(ceil_div(n, TILE), ceil_div(m, TILE));
     k_gemm<<<grd, blk, 0, p->stream>>>(m, n, k, A, transA, B, beta, D, C);
     LAUNCH_CHECK();
+    return AMGH_OK;
+}
+
+int dense_spd_inverse(amgh_problem *p, double *g, int n, double *inv, int *info_dev)
+{
+    cudaStream_t s = p->stream;
+    CU(cudaMemsetAsync(info_dev, 0, sizeof(int), s));
+    for (int j = 0; j < n; j++) {
+        k_chol_col<<<1, 256, 0, s>>>(n, j, g, info_dev);
+        LAUNCH_CHECK();
+        int64_t m = n - j - 1;
+        if (m > 0) {
+            k_chol_update<<<ceil_div(m * m, 256), 256, 0, s>>>(n, j, g);
+            LAUNCH_CHECK();
+        }
+    }
+    int info = 0;
+    CU(cudaMemcpyAsync(&info, info_dev, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
+    if (info) return AMGH_ERR_INDEFINITE;
+    // A^-1 = L^-T L^-1 = W^T W
+    Scratch sc;
+    double *W = nullptr;
+    TRY(sc.alloc(&W, (int64_t)n * n));
+    k_trinv<<<n, 256, sizeof(double) * n, s>>>(n, g, W);
+    LAUNCH_CHECK();
+    TRY(gemm(p, n, n, n, W, 1, W, 0.0, nullptr, inv));
+    CU(cudaStreamSynchronize(s));
     return AMGH_OK;
 }
 
