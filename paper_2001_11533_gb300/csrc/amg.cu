@@ -430,14 +430,18 @@ int amg_prolongator(amgh_problem *p, Arena &ar, const DevCsr &a, const int *agg,
 
 // ------------------------------------------------------------------ SpGEMM
 // Candidate count of row i: u_i = sum over A's row i of the lengths of the
-// B rows it selects.  Rows with u_i <= WARP_TS / 2 are handled by one warp
-// with its hash table in shared memory; longer rows by one thread with a
-// table of 2^ceil(log2(2 u_i)) slots in global memory.
-#define WARP_TS 2048
-#define WARPS_PER_BLOCK 2
+// B rows it selects.  On matrices with few rows (coarse levels, where one
+// thread per row cannot fill the GPU and each row is long) rows with
+// u_i <= WARP_TS / 2 are handled by one warp with its hash table in shared
+// memory; all other rows by one thread with a table of 2^ceil(log2(2 u_i))
+// slots in global memory.
+#define WARP_TS 1024
+#define WARPS_PER_BLOCK 4
+#define WARP_PATH_MAX_ROWS 65536
 
 __global__ void k_gemm_ub(int n, const int *__restrict__ arp, const int *__restrict__ aci,
-                          const int *__restrict__ brp, long long *__restrict__ ub, int *__restrict__ small)
+                          const int *__restrict__ brp, long long *__restrict__ ub, int *__restrict__ small,
+                          int use_warp)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -446,7 +450,7 @@ __global__ void k_gemm_ub(int n, const int *__restrict__ arp, const int *__restr
         int j = aci[k];
         u += brp[j + 1] - brp[j];
     }
-    int sm = u <= WARP_TS / 2;
+    int sm = use_warp && u <= WARP_TS / 2;
     small[i] = sm;
     long long t = 2;
     while (t < 2 * u) t <<= 1;
@@ -542,8 +546,17 @@ __global__ void k_gemm_warp(int n, const int *__restrict__ arp, const int *__res
     double *stage = (double *)((int *)smem_raw + WARPS_PER_BLOCK * WARP_TS) + WARPS_PER_BLOCK * WARP_TS + w * 32;
     int i = blockIdx.x * WARPS_PER_BLOCK + w;
     if (i >= n || !small[i]) return; // warp-uniform
-    const unsigned mask = WARP_TS - 1;
-    for (int t = lane; t < WARP_TS; t += 32) keys[t] = -1;
+    // table of 2^ceil(log2(2u)) slots (u = candidate count of the row)
+    int u = 0;
+    for (int k = arp[i] + lane; k < arp[i + 1]; k += 32) {
+        int j = aci[k];
+        u += brp[j + 1] - brp[j];
+    }
+    for (int o = 16; o > 0; o >>= 1) u += __shfl_xor_sync(0xffffffffu, u, o);
+    unsigned ts = 2;
+    while ((int)ts < 2 * u) ts <<= 1;
+    const unsigned mask = ts - 1;
+    for (unsigned t = lane; t < ts; t += 32) keys[t] = -1;
     __syncwarp();
     for (int k = arp[i]; k < arp[i + 1]; k++) {
         int j = aci[k];
@@ -575,23 +588,32 @@ __global__ void k_gemm_warp(int n, const int *__restrict__ arp, const int *__res
             __syncwarp();
         }
     }
+    // compact the occupied slots to the front of the table (keys and values)
+    int c = 0;
+    for (unsigned t0 = 0; t0 < ts; t0 += 32) {
+        unsigned t = t0 + lane;
+        int key = t < ts ? keys[t] : -1;
+        double val = t < ts ? vals[t] : 0.0;
+        unsigned occ = __ballot_sync(0xffffffffu, key >= 0);
+        __syncwarp();
+        if (key >= 0) {
+            int pos = c + __popc(occ & ((1u << lane) - 1));
+            keys[pos] = key; // pos <= t: never overwrites an unread slot
+            vals[pos] = val;
+        }
+        c += __popc(occ);
+        __syncwarp();
+    }
     if (phase == 0) {
-        int c = 0;
-        for (int t = lane; t < WARP_TS; t += 32) c += keys[t] >= 0;
-        for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
         if (lane == 0) cnt[i] = c;
         return;
     }
     // rank of each key among the row's keys = its position in the sorted row
     int base = crp[i];
-    for (int t = lane; t < WARP_TS; t += 32) {
+    for (int t = lane; t < c; t += 32) {
         int key = keys[t];
-        if (key < 0) continue;
         int rank = 0;
-        for (int u = 0; u < WARP_TS; u++) {
-            int o = keys[u];
-            rank += (o >= 0) & (o < key);
-        }
+        for (int v = 0; v < c; v++) rank += keys[v] < key;
         cci[base + rank] = key;
         cv[base + rank] = vals[t];
     }
@@ -620,7 +642,7 @@ int spgemm(amgh_problem *p, Arena &ar, const DevCsr &a, const DevCsr &b, DevCsr 
     TRY(sc.alloc(&cnt, n + 1));
     TRY(sc.alloc(&small, n + 1));
     int nb = ceil_div(n, 128), nw = ceil_div(n, WARPS_PER_BLOCK);
-    k_gemm_ub<<<nb, 128, 0, s>>>(n, a.rp, a.ci, b.rp, ub, small);
+    k_gemm_ub<<<nb, 128, 0, s>>>(n, a.rp, a.ci, b.rp, ub, small, n <= WARP_PATH_MAX_ROWS);
     LAUNCH_CHECK();
     long long tot = 0;
     TRY(exclusive_scan<long long>(ub, toff, n, s, &tot));
