@@ -195,6 +195,11 @@ int amgh_state_solve(amgh_problem *p, const double *u_dev, double *y_dev, double
  * amgh_state_solve.  u_dev, g_dev n doubles; y_dev m doubles. */
 int amgh_gradient(amgh_problem *p, const double *u_dev, const double *y_dev, double *g_dev);
 
+/* Adjoint of the solution operator K = A^-1 M_yu (Sec. 2, Eq. solutionopdef):
+ * g = K^T w = M_yu^T A^-T w for a state-space vector w (m doubles, device);
+ * g_dev: n doubles, device.  This is the backward pass of the state solve. */
+int amgh_state_adjoint(amgh_problem *p, const double *w_dev, double *g_dev);
+
 /* Level-wise building blocks (for tests and diagnostics).
  * amgh_vcycle: x = V_l b, one symmetric V-cycle on A_l from x = 0.
  * amgh_state_solve_level: A_l y = f by AMG-CG to rel. tolerance tol.

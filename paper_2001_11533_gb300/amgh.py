@@ -70,6 +70,7 @@ _SIGS = {
     "amgh_solve_host": ([_P, _P, _P, _P, _P, _P], _I),
     "amgh_state_solve": ([_P, _P, _P, _P], _I),
     "amgh_gradient": ([_P, _P, _P, _P], _I),
+    "amgh_state_adjoint": ([_P, _P, _P], _I),
     "amgh_vcycle": ([_P, _I, _P, _P], _I),
     "amgh_state_solve_level": ([_P, _I, _P, _P, _D, _P], _I),
     "amgh_mass_solve": ([_P, _I, _P, _P, _P], _I),
@@ -277,6 +278,17 @@ class Problem:
         g = self._new(self.sizes["n"])
         check(lib().amgh_gradient(self.h, _ptr(u), _ptr(y), _ptr(g)), "amgh_gradient")
         return g
+
+    def state_adjoint(self, w):
+        g = self._new(self.sizes["n"])
+        check(lib().amgh_state_adjoint(self.h, _ptr(w), _ptr(g)), "amgh_state_adjoint")
+        return g
+
+    def state_only(self, u):
+        """y = A^-1 M_yu u without evaluating J."""
+        y = self._new(self.sizes["m"])
+        check(lib().amgh_state_solve(self.h, _ptr(u), _ptr(y), None), "amgh_state_solve")
+        return y
 
     # -- level-wise pieces
     def vcycle(self, level, b):

@@ -478,6 +478,17 @@ extern "C" int amgh_gradient(amgh_problem *p, const double *u, const double *y, 
     return sync_stream(p);
 }
 
+extern "C" int amgh_state_adjoint(amgh_problem *p, const double *w, double *g)
+{
+    NEED_SETUP(p);
+    if (!w || !g) return AMGH_ERR_INVALID_ARG;
+    CtrlLevel &C = p->cl[0];
+    // A is symmetric, so A^-T w is one more AMG-CG solve
+    TRY(state_solve(p, 0, w, C.ps, p->sopts.inner_tol, nullptr));
+    TRY(spmv(p, C.Myut, C.ps, g, nullptr, 0));
+    return sync_stream(p);
+}
+
 // ------------------------------------------------------------------ level-wise
 extern "C" int amgh_vcycle(amgh_problem *p, int level, const double *b, double *x)
 {

@@ -111,6 +111,14 @@ def grid3d_kuhn(N: int):
     return coords, elems.astype(np.int32)
 
 
+def cube_boundary(N: int) -> np.ndarray:
+    """Boundary flags of the N^3 structured grid (same set as boundary_vertices)."""
+    i = np.arange(N)
+    on = (i == 0) | (i == N - 1)
+    K, J, I = np.meshgrid(on, on, on, indexing="ij")
+    return (K | J | I).ravel().astype(np.uint8)
+
+
 def boundary_vertices(elements: np.ndarray, n: int) -> np.ndarray:
     """Flag vertices on a facet that belongs to exactly one element."""
     d1 = elements.shape[1]
@@ -258,8 +266,7 @@ def cube_grf(N: int = 129, cfg: int = 2, features: int = 1024, corr: float = 0.1
     beta = 1e-5; y_d from 8 Gaussian bumps of width 0.1 (stream 3).
     """
     coords, elems = grid3d_kuhn(N)
-    n = coords.shape[0]
-    dirichlet = boundary_vertices(elems, n)
+    dirichlet = cube_boundary(N)
     rng = _rng(cfg, 4)
     omega = rng.normal(0.0, 1.0 / corr, size=(features, 3))
     phase = rng.uniform(0.0, 2.0 * np.pi, size=features)
@@ -308,8 +315,7 @@ def cube_slabs(N: int = 257, cfg: int = 4) -> Workload:
     beta = 1e-6; y_d from 32 Gaussian bumps of width 0.05 (stream 9).
     """
     coords, elems = grid3d_kuhn(N)
-    n = coords.shape[0]
-    dirichlet = boundary_vertices(elems, n)
+    dirichlet = cube_boundary(N)
     bnd = np.sort(np.arange(1, 10) / 10.0 + _rng(cfg, 8).uniform(-0.02, 0.02, size=9))
     z = centroids(coords, elems)[:, 2]
     slab = np.searchsorted(bnd, z)

@@ -1,0 +1,87 @@
+"""Differentiation pattern: torch.autograd.Function over the C ABI.
+
+The reduced cost J(u) is quadratic, so its central difference equals the
+directional derivative up to rounding of J itself; the adjoint gradient is
+also compared with the FP64 oracle's, and the state solve's backward with the
+adjoint identity <ybar, K u> = <K^T ybar, u> (Sec. 2).
+"""
+import numpy as np
+import pytest
+
+from oracle.oracle import Oracle
+from paper_2001_11533_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+TIGHT = dict(inner_tol=1e-13, mass_tol=1e-13)
+
+
+def _cuda(x):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(x, dtype=np.float64)).cuda()
+
+
+def _problem(w, **opts):
+    from paper_2001_11533_gb300 import amgh
+    p = amgh.Problem.from_workload(w).amg_setup(**opts)
+    p.set_solve_opts(**TIGHT)
+    return p
+
+
+def test_gradient_matches_oracle_3d():
+    import torch
+    from paper_2001_11533_gb300.autograd import reduced_cost
+    w = W.cube_grf(N=9, features=64)
+    prob = _problem(w, coarse_max=16)
+    orc = Oracle(w, coarse_max=16, inner_tol=1e-13)
+    u0 = np.random.default_rng(31).standard_normal(w.n_vertices)
+    u = _cuda(u0).requires_grad_(True)
+    J = reduced_cost(u, prob)
+    J.backward()
+    Jo, _, go = orc.objective(u0)
+    assert abs(J.item() - Jo) <= 1e-11 * abs(Jo)
+    g = u.grad.cpu().numpy()
+    assert np.linalg.norm(g - go) <= 1e-10 * np.linalg.norm(go)
+
+
+def test_state_solve_backward_is_adjoint():
+    import torch
+    from paper_2001_11533_gb300.autograd import state_solve
+    w = W.lshape_checkerboard(N=65)
+    prob = _problem(w, coarse_max=32)
+    rng = np.random.default_rng(32)
+    u = _cuda(rng.standard_normal(w.n_vertices)).requires_grad_(True)
+    ybar = _cuda(rng.standard_normal(w.n_interior))
+    y = state_solve(u, prob)
+    (y * ybar).sum().backward()
+    lhs = float((ybar * y.detach()).sum())
+    rhs = float((u.grad * u.detach()).sum())
+    assert abs(lhs - rhs) <= 1e-11 * max(abs(lhs), 1e-30)
+
+
+@pytest.mark.slow
+def test_central_differences_full_cube_129():
+    """129^3 Kuhn cube, kappa = exp(GRF), beta = 1e-5: 20 seeded directions, step
+    1e-6.  J is quadratic, so |fd - g.d| is bounded by the rounding and solve error
+    of J divided by the step."""
+    import torch
+    from paper_2001_11533_gb300.autograd import reduced_cost
+    w = W.cube_grf(N=129, features=64)
+    prob = _problem(w, precision=2)
+    n = w.n_vertices
+    u = _cuda(W.random_vectors(n, 1, 2, 6)[0]).requires_grad_(True)
+    J = reduced_cost(u, prob)
+    J.backward()
+    g = u.grad.detach()
+    D = W.random_vectors(n, 20, 2, 5)
+    h = 1e-6
+    worst = 0.0
+    for d in D:
+        d = _cuda(d / np.linalg.norm(d))
+        with torch.no_grad():
+            jp = reduced_cost(u.detach() + h * d, prob).item()
+            jm = reduced_cost(u.detach() - h * d, prob).item()
+        fd = (jp - jm) / (2 * h)
+        gd = float((g * d).sum())
+        bound = 1e-6 * abs(gd) + 1e-12 * abs(J.item()) / h
+        worst = max(worst, abs(fd - gd) / bound)
+    assert worst <= 1.0, worst
