@@ -44,6 +44,8 @@ def parse():
     ap.add_argument("--impl", default="amgh", choices=["amgh", "reference"])
     ap.add_argument("--N", type=int, default=1025, help="L-shape grid size (bench workload: 1025)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--coarse-max", type=int, default=256, help="AMG stops at or below this many rows")
+    ap.add_argument("--degree", type=int, default=2, help="Chebyshev smoother degree")
     ap.add_argument("--hessian-levels", type=int, default=4,
                     help="levels of the Hessian preconditioner (fewer than the AMG levels, as in Sec. 5.6)")
     ap.add_argument("--single-step", action="store_true",
@@ -151,7 +153,8 @@ def run_amgh(args, rank, world, local):
             prob = amgh.Problem(w.dim, *pinned_np[:4], w.beta, pinned_np[4], on_device=False)
         else:
             prob = amgh.Problem(w.dim, dev[0], dev[1], dev[2], dev[3], w.beta, dev[4], on_device=True)
-        prob.amg_setup(precision=precision, hessian_levels=args.hessian_levels)
+        prob.amg_setup(precision=precision, hessian_levels=args.hessian_levels, coarse_max=args.coarse_max,
+                       smooth_degree=args.degree)
         if timing:
             prob.kernel_timing(True)
         if e2e:
@@ -258,10 +261,10 @@ def roofline_from(res):
 
 
 # ------------------------------------------------------------------------- oracle (CPU)
-def oracle_apply_rate(w, budget_s, applies=None, hessian_levels=0):
+def oracle_apply_rate(w, budget_s, args, applies=None):
     """Time the FP64 oracle's Hessian apply on the host (setup untimed)."""
     from oracle.oracle import Oracle
-    orc = Oracle(w, hessian_levels=hessian_levels)
+    orc = Oracle(w, hessian_levels=args.hessian_levels, coarse_max=args.coarse_max, degree=args.degree)
     u = np.random.default_rng(0).standard_normal(w.n_vertices)
     n, t = 0, 0.0
     while (applies is None and (t < budget_s or n == 0)) or (applies is not None and n < applies):
@@ -280,7 +283,7 @@ def run_reference(args, rank, world):
     orc_mod.build()
     w = workloads.lshape_checkerboard(N=args.N)
     from oracle.oracle import Oracle
-    orc = Oracle(w, hessian_levels=args.hessian_levels)
+    orc = Oracle(w, hessian_levels=args.hessian_levels, coarse_max=args.coarse_max, degree=args.degree)
     u = np.random.default_rng(0).standard_normal(w.n_vertices)
     for _ in range(min(args.warmup, 1)):
         orc.hessian(u)
@@ -312,7 +315,8 @@ def single_step(args):
     _build.build()
     w = workloads.lshape_checkerboard(N=args.N)
     prob = amgh.Problem.from_workload(w)
-    prob.amg_setup(precision=PRECISION[args.forms.split(",")[0]], hessian_levels=args.hessian_levels)
+    prob.amg_setup(precision=PRECISION[args.forms.split(",")[0]], hessian_levels=args.hessian_levels,
+                   coarse_max=args.coarse_max, smooth_degree=args.degree)
     u, y, info = prob.solve(tol=1e-8)
     torch.cuda.synchronize()
     print(json.dumps({"info": info, "levels": prob.level_counters(), "sizes": prob.sizes,
@@ -341,7 +345,8 @@ def main():
         "data": "synthetic",
         "config": {"workload": f"lshape{args.N}_checkerboard", "m": w.n_interior, "n": w.n_vertices,
                    "beta": w.beta, "kappa": "8x8 checkerboard {1,1e4}", "tol": 1e-8,
-                   "hessian_levels": args.hessian_levels,
+                   "hessian_levels": args.hessian_levels, "coarse_max": args.coarse_max,
+                   "chebyshev_degree": args.degree,
                    "precision": forms[0], "parallelism": "replicas" if world > 1 else "single",
                    "l2": "256 MB buffer written between timed steps",
                    "step": "assembly + AMG setup + rhs + outer CG to 1e-8 + true residual"},
@@ -357,7 +362,7 @@ def main():
     if "refine" in results and "fp64" in results:
         line["speedup_refine_vs_fp64"] = results["refine"]["value"] / results["fp64"]["value"]
     if world == 1 and not args.no_cpu_baseline:
-        n, t = oracle_apply_rate(w, budget_s=15.0, hessian_levels=args.hessian_levels)
+        n, t = oracle_apply_rate(w, 15.0, args)
         line["cpu_baseline"] = {"value": n / t, "unit": UNIT, "cores": 1, "kind": "oracle",
                                 "sample": f"{n} Hessian applies of the FP64 oracle on the same workload "
                                           f"({t:.1f} s, setup untimed)"}
