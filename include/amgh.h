@@ -256,6 +256,28 @@ int amgh_reset_counters(amgh_problem *p);
 int amgh_kernel_timing(amgh_problem *p, int enable);
 int amgh_kernel_stats(amgh_problem *p, int64_t *launches, double *ms, double *bytes);
 
+/* Aggregation of a caller's matrix that allocates no device memory.  The
+ * paper has no counterpart: this is a service for callers that cannot call
+ * cudaMalloc (a framework's caching allocator owns the memory budget, a hard
+ * memory cap, or a latency-critical path that must not allocate or implicitly
+ * synchronise).  It returns exactly the level-0 aggregates amgh_amg_setup
+ * computes for a matrix with this CSR (strength threshold theta): the
+ * distance-2 independent set by splitmix64 priority and phases 1-3.
+ *   n              rows, 1 .. 32768 (more: AMGH_ERR_INVALID_ARG)
+ *   rowptr_dev, col_dev, val_dev   CSR of a symmetric matrix with sorted
+ *                  columns, on the current device; at most 262144 entries
+ *                  (more: AMGH_ERR_INVALID_ARG)
+ *   stream         cudaStream_t to run on (NULL = legacy default stream)
+ *   agg_dev        n int32 outputs (device); *nagg_host = number of aggregates
+ * Scratch comes from one fixed buffer inside the library (about 5 MB per
+ * device that loads it, held until the process exits).  The first call on a
+ * device looks up that buffer's device address (make it before any CUDA graph
+ * capture).  All calls share the buffer: calls that overlap on the GPU race,
+ * so the caller must serialise them.  The call synchronises `stream`. */
+int amgh_aggregate_noalloc(int n, const int32_t *rowptr_dev, const int32_t *col_dev,
+                           const double *val_dev, double theta, void *stream, int32_t *agg_dev,
+                           int32_t *nagg_host);
+
 /* Number of kernels this library launched since load (all problems). */
 int64_t amgh_launch_count(void);
 

@@ -86,6 +86,7 @@ _SIGS = {
     "amgh_kernel_timing": ([_P, _I], _I),
     "amgh_kernel_stats": ([_P, _P, _P, _P], _I),
     "amgh_launch_count": ([], _I64),
+    "amgh_aggregate_noalloc": ([_I, _P, _P, _P, _D, _P, _P, _P], _I),
     "amgh_problem_destroy": ([_P], None),
     "amgh_status_string": ([_I], C.c_char_p),
 }
@@ -128,6 +129,17 @@ def _ptr(t):
 
 def launch_count() -> int:
     return int(lib().amgh_launch_count())
+
+
+def aggregate_noalloc(rowptr, col, val, theta, agg_out, stream=None):
+    """amgh_aggregate_noalloc on CUDA tensors (int32 rowptr/col, float64 val);
+    writes agg_out (int32, n) and returns the number of aggregates."""
+    n = int(rowptr.numel()) - 1
+    nagg = C.c_int32()
+    check(lib().amgh_aggregate_noalloc(n, _ptr(rowptr), _ptr(col), _ptr(val), float(theta),
+                                       C.c_void_p(stream) if stream else None, _ptr(agg_out),
+                                       C.byref(nagg)), "amgh_aggregate_noalloc")
+    return nagg.value
 
 
 def amg_opts(**kw) -> amgh_amg_opts:
