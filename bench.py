@@ -10,9 +10,9 @@ second of step time (whole job over all ranks); the time to 1e-8 is
 reported beside it.  Three precision forms are timed: "mixed" (FP64 CG for
 every PDE solve preconditioned by FP32 V-cycles; the headline), "fp64", and
 "refine" (FP32 CG and V-cycles inside FP64 iterative refinement).  Kernel
-durations for the roofline come from an instrumented pass of the same step
-right after the timed region (CUDA events per fine-level launch, which needs
-direct launches instead of CUDA graphs).
+durations for the roofline (the level-0 Chebyshev smoother step) come from
+an instrumented pass of the same step right after the timed region (CUDA
+events per launch, which needs direct launches instead of CUDA graphs).
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl amgh|reference]
 """
@@ -44,10 +44,11 @@ def parse():
     ap.add_argument("--impl", default="amgh", choices=["amgh", "reference"])
     ap.add_argument("--N", type=int, default=1025, help="L-shape grid size (bench workload: 1025)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--coarse-max", type=int, default=256, help="AMG stops at or below this many rows")
+    ap.add_argument("--coarse-max", type=int, default=1000,
+                    help="AMG stops at or below this many rows (1000: 4 levels, 784k..847 on the L-shape)")
     ap.add_argument("--degree", type=int, default=2, help="Chebyshev smoother degree")
-    ap.add_argument("--hessian-levels", type=int, default=4,
-                    help="levels of the Hessian preconditioner (fewer than the AMG levels, as in Sec. 5.6)")
+    ap.add_argument("--hessian-levels", type=int, default=0,
+                    help="levels of the Hessian preconditioner (0 = all AMG levels, as in Sec. 5.3)")
     ap.add_argument("--single-step", action="store_true",
                     help="run one untimed step of the first form (for profilers) and print its counters")
     ap.add_argument("--forms", default="mixed,fp64,refine",
@@ -256,7 +257,7 @@ def roofline_from(res):
     achieved = ks["bytes"] / (ks["ms"] / 1000.0) / 1e9
     return {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
             "frac": round(achieved / peak, 4), "traffic": None, "peak_source": src,
-            "kernel": "fine-level SELL-32 SpMV-class kernels (smoother step, residual, CG p.Ap)",
+            "kernel": "k_cheb_step on level 0 (Chebyshev smoother step fused with its residual, SELL-32)",
             "launches": ks["launches"], "avg_us": round(1000.0 * ks["ms"] / ks["launches"], 2)}
 
 

@@ -249,10 +249,11 @@ int amgh_reset_counters(amgh_problem *p);
 
 /* Kernel timing for roofline reporting: when enabled, CG iterations are
  * launched kernel by kernel instead of as CUDA graphs, and every launch of the
- * fine-level (level 0) SpMV-class kernels is bracketed by CUDA events on the
- * problem's stream.  amgh_kernel_stats returns the number of timed launches,
- * their summed duration in ms, and their summed algorithmic bytes
- * (nnz*(value+4) + 4*(rows+1) + value*(rows+cols) per SpMV). */
+ * level-0 Chebyshev smoother step (SpMV fused with the smoother update) is
+ * bracketed by CUDA events on the problem's stream.  amgh_kernel_stats
+ * returns the number of timed launches, their summed duration in ms, and
+ * their summed algorithmic bytes (nnz*(v+4) + 4*(rows+1) + v*(rows+cols) +
+ * 4*v*rows per launch, v = value bytes). */
 int amgh_kernel_timing(amgh_problem *p, int enable);
 int amgh_kernel_stats(amgh_problem *p, int64_t *launches, double *ms, double *bytes);
 

