@@ -245,6 +245,21 @@ def run_amgh(args, rank, world, local):
     return w, results, e2e
 
 
+def captured_traffic():
+    """DRAM bytes per launch of the level-0 smoother step from the committed ncu
+    summary, or None if the kernel source changed since that capture."""
+    import hashlib
+    try:
+        txt = open(os.path.join(ROOT, "profiles", "k_cheb_step_level0_lshape1025.md")).read()
+        want = txt.split("source_sha256:")[1].split()[0]
+        traffic = float(txt.split("traffic_bytes_per_launch:")[1].split()[0])
+        src = b"".join(open(os.path.join(ROOT, "paper_2001_11533_gb300", "csrc", f), "rb").read()
+                       for f in ("sparse.cu", "spmv.cuh"))
+        return traffic if hashlib.sha256(src).hexdigest() == want else None
+    except Exception:
+        return None
+
+
 def roofline_from(res):
     ks = res["kstats"]
     peaks = measured_peaks()
@@ -256,7 +271,7 @@ def roofline_from(res):
         return None
     achieved = ks["bytes"] / (ks["ms"] / 1000.0) / 1e9
     return {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-            "frac": round(achieved / peak, 4), "traffic": None, "peak_source": src,
+            "frac": round(achieved / peak, 4), "traffic": captured_traffic(), "peak_source": src,
             "kernel": "k_cheb_step on level 0 (Chebyshev smoother step fused with its residual, SELL-32)",
             "launches": ks["launches"], "avg_us": round(1000.0 * ks["ms"] / ks["launches"], 2)}
 
