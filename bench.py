@@ -47,6 +47,9 @@ def parse():
     ap.add_argument("--coarse-max", type=int, default=1000,
                     help="AMG stops at or below this many rows (1000: 4 levels, 784k..847 on the L-shape)")
     ap.add_argument("--degree", type=int, default=2, help="Chebyshev smoother degree")
+    ap.add_argument("--inner-tol", type=float, default=1e-10, help="state/adjoint solves of the outer H applies")
+    ap.add_argument("--precond-tol", type=float, default=1e-8,
+                    help="coarse-Hessian solves and mass solves inside the preconditioner (Sec. 5.2: 1e-8)")
     ap.add_argument("--hessian-levels", type=int, default=0,
                     help="levels of the Hessian preconditioner (0 = all AMG levels, as in Sec. 5.3)")
     ap.add_argument("--single-step", action="store_true",
@@ -158,10 +161,11 @@ def run_amgh(args, rank, world, local):
                        smooth_degree=args.degree)
         if timing:
             prob.kernel_timing(True)
+        tols = dict(tol=1e-8, inner_tol=args.inner_tol, mass_tol=args.precond_tol, precond_tol=args.precond_tol)
         if e2e:
-            u, y, info = prob.solve_host(tol=1e-8)
+            u, y, info = prob.solve_host(**tols)
         else:
-            u, y, info = prob.solve(tol=1e-8)
+            u, y, info = prob.solve(**tols)
         ks = prob.kernel_stats() if timing else None
         sizes = prob.sizes
         prob.close()
@@ -280,7 +284,8 @@ def roofline_from(res):
 def oracle_apply_rate(w, budget_s, args, applies=None):
     """Time the FP64 oracle's Hessian apply on the host (setup untimed)."""
     from oracle.oracle import Oracle
-    orc = Oracle(w, hessian_levels=args.hessian_levels, coarse_max=args.coarse_max, degree=args.degree)
+    orc = Oracle(w, hessian_levels=args.hessian_levels, coarse_max=args.coarse_max, degree=args.degree,
+                 inner_tol=args.inner_tol)
     u = np.random.default_rng(0).standard_normal(w.n_vertices)
     n, t = 0, 0.0
     while (applies is None and (t < budget_s or n == 0)) or (applies is not None and n < applies):
@@ -333,7 +338,8 @@ def single_step(args):
     prob = amgh.Problem.from_workload(w)
     prob.amg_setup(precision=PRECISION[args.forms.split(",")[0]], hessian_levels=args.hessian_levels,
                    coarse_max=args.coarse_max, smooth_degree=args.degree)
-    u, y, info = prob.solve(tol=1e-8)
+    u, y, info = prob.solve(tol=1e-8, inner_tol=args.inner_tol, mass_tol=args.precond_tol,
+                            precond_tol=args.precond_tol)
     torch.cuda.synchronize()
     print(json.dumps({"info": info, "levels": prob.level_counters(), "sizes": prob.sizes,
                       "launches": amgh.launch_count()}))
@@ -362,7 +368,8 @@ def main():
         "config": {"workload": f"lshape{args.N}_checkerboard", "m": w.n_interior, "n": w.n_vertices,
                    "beta": w.beta, "kappa": "8x8 checkerboard {1,1e4}", "tol": 1e-8,
                    "hessian_levels": args.hessian_levels, "coarse_max": args.coarse_max,
-                   "chebyshev_degree": args.degree,
+                   "chebyshev_degree": args.degree, "inner_tol": args.inner_tol,
+                   "precond_and_mass_tol": args.precond_tol,
                    "precision": forms[0], "parallelism": "replicas" if world > 1 else "single",
                    "l2": "256 MB buffer written between timed steps",
                    "step": "assembly + AMG setup + rhs + outer CG to 1e-8 + true residual"},

@@ -95,7 +95,10 @@ typedef struct {
  *  mass_tol     relative residual of every mass solve M_{u,j} x = b
  *  precond      0 = none (identity), 1 = multilevel / two-grid (Q_0)
  *  ncols        columns solved together (1 in this version)
- *  inner_max_iter, mass_max_iter   caps of the inner CG loops */
+ *  inner_max_iter, mass_max_iter   caps of the inner CG loops
+ *  precond_tol  relative residual of the state/adjoint solves of the coarse
+ *               Hessians H_j, j >= 1, which occur only inside the
+ *               preconditioner (0 = inner_tol; Sec. 5.2 uses 1e-8) */
 typedef struct {
     double tol;
     int max_iter;
@@ -105,6 +108,7 @@ typedef struct {
     int ncols;
     int inner_max_iter;
     int mass_max_iter;
+    double precond_tol;
 } amgh_solve_opts;
 
 /* Counters of the last amgh_solve (or since amgh_reset_counters). */
@@ -122,7 +126,8 @@ typedef struct {
 
 /* Defaults: max_levels 25, hessian_levels 0, theta 0.08, coarse_max 256,
  * Chebyshev degree 2, precision 0, smoothed prolongator; tol 1e-8,
- * max_iter 200, inner/mass tol 1e-10, precond 1, ncols 1, caps 1000. */
+ * max_iter 200, inner/mass tol 1e-10, precond 1, ncols 1, caps 1000,
+ * precond_tol 0 (= inner_tol). */
 void amgh_amg_opts_default(amgh_amg_opts *opts);
 void amgh_solve_opts_default(amgh_solve_opts *opts);
 
@@ -154,8 +159,8 @@ int amgh_set_stream(amgh_problem *p, void *cuda_stream);
 int amgh_amg_setup(amgh_problem *p, const amgh_amg_opts *opts);
 
 /* Set the tolerances used by amgh_hessian_apply / amgh_precond_apply /
- * amgh_rhs / amgh_state_solve / amgh_gradient (inner_tol, mass_tol and the
- * caps; other fields ignored). */
+ * amgh_rhs / amgh_state_solve / amgh_gradient (inner_tol, mass_tol,
+ * precond_tol and the caps; other fields ignored). */
 int amgh_set_solve_opts(amgh_problem *p, const amgh_solve_opts *opts);
 
 /* Hu = H u on the finest level (Eq. firstorderpractice): one forward and one

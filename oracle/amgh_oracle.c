@@ -85,6 +85,7 @@ typedef struct {
     double cd[16], cr[16];
     /* solve parameters used by the preconditioner */
     double inner_tol, mass_tol;
+    double pc_inner_tol; /* inner solves of the coarse Hessians inside the preconditioner */
     int inner_maxit, mass_maxit;
     long inner_iters, mass_iters, happlies;
 } orc_t;
@@ -933,10 +934,13 @@ static int hessian(orc_t *o, int l, const double *v, double *hv)
     double *w = xcalloc((size_t)n, sizeof(double));
     if (!t1 || !y || !t2 || !p || !w) return ORC_OOM;
     int st;
+    /* level 0: the operator of the outer CG; levels >= 1 occur only inside
+     * the preconditioner (Algorithm MLAS) and use the preconditioner tolerance */
+    double tol = l == 0 ? o->inner_tol : o->pc_inner_tol;
     spmv(&o->Myu[l], v, t1);
-    if ((st = state_solve(o, l, t1, y, o->inner_tol))) goto done;
+    if ((st = state_solve(o, l, t1, y, tol))) goto done;
     spmv(&o->My[l], y, t2);
-    if ((st = state_solve(o, l, t2, p, o->inner_tol))) goto done;
+    if ((st = state_solve(o, l, t2, p, tol))) goto done;
     spmv(&o->Myut[l], p, hv);
     spmv(&o->Mu[l], v, w);
     for (int i = 0; i < n; i++) hv[i] = hv[i] + o->beta * w[i];
@@ -1215,6 +1219,7 @@ int orc_setup(void *h, int max_levels, int hessian_levels, double theta, int coa
     if (hessian_levels > 0 && hessian_levels < o->ell) o->ell = hessian_levels;
     o->inner_tol = 1e-10;
     o->mass_tol = 1e-10;
+    o->pc_inner_tol = 1e-10;
     o->inner_maxit = 1000;
     o->mass_maxit = 1000;
     if ((st = build_coarse_hessian(o))) return st;
@@ -1226,9 +1231,17 @@ int orc_set_tols(void *h, double inner_tol, double mass_tol, int inner_maxit, in
 {
     orc_t *o = h;
     o->inner_tol = inner_tol;
+    o->pc_inner_tol = inner_tol;
     o->mass_tol = mass_tol;
     o->inner_maxit = inner_maxit;
     o->mass_maxit = mass_maxit;
+    return ORC_OK;
+}
+
+int orc_set_precond_tol(void *h, double pc_inner_tol)
+{
+    orc_t *o = h;
+    o->pc_inner_tol = pc_inner_tol;
     return ORC_OK;
 }
 

@@ -57,6 +57,7 @@ def lib():
                 "orc_set_yd": [P, P],
                 "orc_setup": [P, I, I, D, I, I, I, I],
                 "orc_set_tols": [P, D, D, I, I],
+                "orc_set_precond_tol": [P, D],
                 "orc_sizes": [P, P, P, P, P, P, P, P],
                 "orc_matrix_info": [P, I, I, P, P, P],
                 "orc_matrix_copy": [P, I, I, P, P, P],
@@ -154,6 +155,10 @@ class Oracle:
 
     def set_tols(self, inner_tol, mass_tol, inner_maxit=1000, mass_maxit=1000):
         _check(lib().orc_set_tols(self.h, inner_tol, mass_tol, inner_maxit, mass_maxit), "tols")
+
+    def set_precond_tol(self, pc_inner_tol):
+        """Tolerance of the coarse-level state solves inside the preconditioner."""
+        _check(lib().orc_set_precond_tol(self.h, pc_inner_tol), "set_precond_tol")
 
     def set_yd(self, yd):
         self._yd = np.ascontiguousarray(yd, dtype=np.float64)

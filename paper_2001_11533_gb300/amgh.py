@@ -42,7 +42,7 @@ class amgh_amg_opts(C.Structure):
 class amgh_solve_opts(C.Structure):
     _fields_ = [("tol", C.c_double), ("max_iter", C.c_int), ("inner_tol", C.c_double),
                 ("mass_tol", C.c_double), ("precond", C.c_int), ("ncols", C.c_int),
-                ("inner_max_iter", C.c_int), ("mass_max_iter", C.c_int)]
+                ("inner_max_iter", C.c_int), ("mass_max_iter", C.c_int), ("precond_tol", C.c_double)]
 
 
 class amgh_solve_info(C.Structure):

@@ -40,6 +40,7 @@ extern "C" void amgh_solve_opts_default(amgh_solve_opts *o)
     o->ncols = 1;
     o->inner_max_iter = 1000;
     o->mass_max_iter = 1000;
+    o->precond_tol = 0.0;
 }
 
 extern "C" const char *amgh_status_string(int s)
@@ -95,6 +96,7 @@ static int create_impl(const amgh_mesh *mesh, const double *kappa, double beta, 
     p->beta = beta;
     amgh_amg_opts_default(&p->aopts);
     amgh_solve_opts_default(&p->sopts);
+    p->sopts.precond_tol = p->sopts.inner_tol;
     CU(cudaHostAlloc((void **)&p->h_scal, sizeof(CgScal), cudaHostAllocDefault));
     CU(cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking));
     int d1 = p->dim + 1;
@@ -153,9 +155,11 @@ extern "C" int amgh_set_stream(amgh_problem *p, void *stream)
 extern "C" int amgh_set_solve_opts(amgh_problem *p, const amgh_solve_opts *o)
 {
     if (!p || !o) return AMGH_ERR_INVALID_ARG;
-    if (!(o->inner_tol > 0.0) || !(o->mass_tol > 0.0) || o->inner_max_iter < 1 || o->mass_max_iter < 1)
+    if (!(o->inner_tol > 0.0) || !(o->mass_tol > 0.0) || o->inner_max_iter < 1 || o->mass_max_iter < 1 ||
+        !(o->precond_tol >= 0.0))
         return AMGH_ERR_INVALID_ARG;
     p->sopts.inner_tol = o->inner_tol;
+    p->sopts.precond_tol = o->precond_tol > 0.0 ? o->precond_tol : o->inner_tol;
     p->sopts.mass_tol = o->mass_tol;
     p->sopts.inner_max_iter = o->inner_max_iter;
     p->sopts.mass_max_iter = o->mass_max_iter;
@@ -275,6 +279,7 @@ static int setup_impl(amgh_problem *p)
     for (int l = 0; l < p->Ls; l++) {
         StateLevel &S = p->sl[l];
         TRY(prepare_operator(ar, S.A, s));
+        TRY(build_lo_parts(ar, S.A, s));
         TRY(prepare_operator(ar, S.My, s));
         if (l + 1 < p->Ls) {
             TRY(prepare_operator(ar, S.S, s));
@@ -287,6 +292,7 @@ static int setup_impl(amgh_problem *p)
     for (int l = 0; l < p->Lc; l++) {
         CtrlLevel &C = p->cl[l];
         TRY(prepare_operator(ar, C.Mu, s));
+        TRY(build_lo_parts(ar, C.Mu, s));
         if (l + 1 < p->Lc) {
             TRY(prepare_operator(ar, C.P, s));
             TRY(prepare_operator(ar, C.Pt, s));

@@ -259,6 +259,26 @@ __global__ void k_cg2_spmv(MatView<T> A, const Z *__restrict__ z, const T *__res
     if (reduce_last_block<2>(a, partials, ticket, tot)) cg_finalize(F_CG2, tot, sc, nullptr);
 }
 
+// K1 with the products on the FP32 pipe: s = (A_hi + A_lo) z accumulated in
+// double-float (about 2^-48 relative), converted to FP64 per row
+template <typename Z, int TPR>
+__global__ void k_cg2_spmv_df(MatView<float> A, const float *__restrict__ lo, const Z *__restrict__ z,
+                              const double *__restrict__ r, double *__restrict__ s, CgScal *sc, double *partials,
+                              unsigned *ticket)
+{
+    SKIP_DONE();
+    int row = my_row<TPR>();
+    double v = row_sum_df<Z, TPR>(A, lo, row, z);
+    double a[2] = {0.0, 0.0}, tot[2];
+    if (row < A.rows && row_leader<TPR>()) {
+        s[row] = v;
+        double zr = (double)z[row];
+        a[0] = r[row] * zr;
+        a[1] = zr * v;
+    }
+    if (reduce_last_block<2>(a, partials, ticket, tot)) cg_finalize(F_CG2, tot, sc, nullptr);
+}
+
 // K2: p = z + beta p, q = s + beta q, x += alpha p, r -= alpha q, reduce r.r;
 // optionally r32 = r (input of an FP32 V-cycle) or, for the Jacobi-
 // preconditioned mass CG, z = invd r for the next K1.
@@ -404,9 +424,31 @@ static int set_scal(amgh_problem *p, CgScal *sc, double tol, int maxit)
 }
 
 // single-reduction CG pieces (templated on the vector type T and the type Z of z)
+template <typename Z>
+static int cg2_spmv_df(amgh_problem *p, RedSlot &red, const DevCsr &a, const Z *z, const double *r, double *s,
+                       CgScal *sc)
+{
+    MatView<float> A = view<float>(a);
+    const float *lo = a.lo32;
+    switch (A.tpr) {
+    case 2: k_cg2_spmv_df<Z, 2><<<rows_grid(A.rows, 2), TPB, 0, p->stream>>>(A, lo, z, r, s, sc, red.partials, red.ticket); break;
+    case 4: k_cg2_spmv_df<Z, 4><<<rows_grid(A.rows, 4), TPB, 0, p->stream>>>(A, lo, z, r, s, sc, red.partials, red.ticket); break;
+    case 8: k_cg2_spmv_df<Z, 8><<<rows_grid(A.rows, 8), TPB, 0, p->stream>>>(A, lo, z, r, s, sc, red.partials, red.ticket); break;
+    case 16: k_cg2_spmv_df<Z, 16><<<rows_grid(A.rows, 16), TPB, 0, p->stream>>>(A, lo, z, r, s, sc, red.partials, red.ticket); break;
+    case 32: k_cg2_spmv_df<Z, 32><<<rows_grid(A.rows, 32), TPB, 0, p->stream>>>(A, lo, z, r, s, sc, red.partials, red.ticket); break;
+    default: k_cg2_spmv_df<Z, 1><<<rows_grid(A.rows, 1), TPB, 0, p->stream>>>(A, lo, z, r, s, sc, red.partials, red.ticket); break;
+    }
+    LAUNCH_CHECK();
+    return AMGH_OK;
+}
+
 template <typename T, typename Z>
 int cg2_spmv(amgh_problem *p, RedSlot &red, const DevCsr &a, const Z *z, const T *r, T *s, CgScal *sc, int timed)
 {
+    // FP64 CG operator applied to an FP32 z with the hi/lo split available:
+    // products on the FP32 pipe
+    if (sizeof(T) == 8 && sizeof(Z) == 4 && a.lo32 && p->df_spmv)
+        return cg2_spmv_df<Z>(p, red, a, z, (const double *)r, (double *)s, sc);
     MatView<T> A = view<T>(a);
     timer_begin(p, timed);
     switch (A.tpr) {

@@ -98,6 +98,9 @@ struct DevCsr {
     // with tpr lanes per row and the FP32 copy v32
     int tpr = 1;
     float *v32 = nullptr;
+    // low FP32 parts, v - (double)(float)v, in the same layout as the solve-phase
+    // values (SELL or CSR): with the FP32 values they carry ~48 bits of v
+    float *lo32 = nullptr;
     // SELL-32
     int nslices = 0, sell_nnz = 0;
     int *sl_ptr = nullptr, *sl_ci = nullptr;
@@ -193,6 +196,7 @@ struct amgh_problem {
     int m = 0, n = 0;
     cudaStream_t stream = 0;
     cudaStream_t cap_stream = 0; // private stream used only to capture graphs
+    int df_spmv = 1;             // FP64 CG SpMVs as double-float on the FP32 pipe
     int capturing = 0;
     Arena arena;
     // inputs on device
@@ -236,6 +240,8 @@ struct amgh_problem {
 int csr_to_sell(Arena &ar, DevCsr &a, int want32, cudaStream_t s);
 // pick SELL-32 or lanes-per-row CSR from the mean row length and build it
 int prepare_operator(Arena &ar, DevCsr &a, cudaStream_t s, int force_tpr = 0);
+// build a.lo32 (after prepare_operator)
+int build_lo_parts(Arena &ar, DevCsr &a, cudaStream_t s);
 int csr_transpose(Arena &ar, const DevCsr &a, DevCsr &t, cudaStream_t s);
 // y = A x (FP64 or FP32 SELL)
 int spmv(amgh_problem *p, const DevCsr &a, const double *x, double *y, const int *skip, int timed);

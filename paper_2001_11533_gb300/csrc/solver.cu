@@ -430,7 +430,9 @@ int hessian_level(amgh_problem *p, int l, const double *v, double *hv)
 {
     StateLevel &S = p->sl[l];
     CtrlLevel &C = p->cl[l];
-    double tol = p->sopts.inner_tol;
+    // level 0 is the outer CG's operator; levels >= 1 occur only inside the
+    // preconditioner (Algorithm MLAS) and use the preconditioner tolerance
+    double tol = l == 0 ? p->sopts.inner_tol : p->sopts.precond_tol;
     TRY(spmv(p, C.Myu, v, C.t1, nullptr, 0));
     TRY(state_solve(p, l, C.t1, C.ys, tol, nullptr));
     TRY(spmv(p, S.My, C.ys, C.t2, nullptr, 0));

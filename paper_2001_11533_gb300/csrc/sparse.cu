@@ -185,6 +185,27 @@ int prepare_operator(Arena &ar, DevCsr &a, cudaStream_t s, int force_tpr)
     return AMGH_OK;
 }
 
+__global__ void k_lo_parts(int64_t n, const double *__restrict__ v, const float *__restrict__ hi,
+                           float *__restrict__ lo)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) lo[i] = (float)(v[i] - (double)hi[i]);
+}
+
+int build_lo_parts(Arena &ar, DevCsr &a, cudaStream_t s)
+{
+    int64_t n = a.tpr <= 1 ? a.sell_nnz : a.nnz;
+    const double *v = a.tpr <= 1 ? a.sl_v : a.v;
+    const float *hi = a.tpr <= 1 ? a.sl_v32 : a.v32;
+    TRY(ar.alloc(&a.lo32, n));
+    if (n > 0) {
+        k_lo_parts<<<ceil_div(n, 256), 256, 0, s>>>(n, v, hi, a.lo32);
+        LAUNCH_CHECK();
+    }
+    CU(cudaStreamSynchronize(s));
+    return AMGH_OK;
+}
+
 // ------------------------------------------------------------------ SpMV family
 #define SKIP_RETURN() \
     if (skip && *skip) return

@@ -209,6 +209,22 @@ def test_solve_mixed(name, precision):
     assert (info["refinements"] > 0) == (precision == 1)
 
 
+def test_loose_preconditioner_tolerance():
+    """Solves inside the preconditioner at the paper's 1e-8 (Sec. 5.2) only change
+    the path: with tight outer Hessian applies the control still matches to 1e-10."""
+    w, prob, orc = pair("lshape65")
+    orc.set_tols(1e-13, 1e-13)
+    u, y, info = prob.solve(tol=1e-12, inner_tol=1e-13, mass_tol=1e-8, precond_tol=1e-8)
+    uo, yo, io = orc.solve(precond=1, tol=1e-12)
+    assert rel(host(u), uo) <= 1e-10, info
+    orc2 = Oracle(w, coarse_max=32, inner_tol=1e-13, mass_tol=1e-8)
+    orc2.set_precond_tol(1e-8)
+    r = np.random.default_rng(21).standard_normal(prob.sizes["n"])
+    prob.set_solve_opts(inner_tol=1e-13, mass_tol=1e-8, precond_tol=1e-8)
+    z, zo = host(prob.precond_apply(cuda(r))), orc2.precond(r)
+    assert rel(z, zo) <= 1e-6   # both sides solve to 1e-8 inside Q_0
+
+
 def test_objective_and_gradient():
     w, prob, orc = pair("lshape65")
     prob.set_solve_opts(**TIGHT)
