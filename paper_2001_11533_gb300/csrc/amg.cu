@@ -473,9 +473,8 @@ __global__ void k_gemm_hash(int n, const int *__restrict__ arp, const int *__res
     int c = 0;
     if (size > 0) {
         unsigned mask = size - 1;
-        int *key = tkey + base;
+        int *key = tkey + base; // all slots set to -1 by the caller
         double *val = tval + base;
-        for (unsigned t = 0; t < size; t++) key[t] = -1;
         for (int k = arp[i]; k < arp[i + 1]; k++) {
             int j = aci[k];
             double aij = av[k];
@@ -648,6 +647,7 @@ int spgemm(amgh_problem *p, Arena &ar, const DevCsr &a, const DevCsr &b, DevCsr 
     TRY(exclusive_scan<long long>(ub, toff, n, s, &tot));
     TRY(sc.alloc(&tkey, tot));
     TRY(sc.alloc(&tval, tot));
+    if (tot > 0) CU(cudaMemsetAsync(tkey, 0xff, sizeof(int) * (size_t)tot, s));
     k_gemm_hash<<<nb, 128, 0, s>>>(n, a.rp, a.ci, a.v, b.rp, b.ci, b.v, toff, small, tkey, tval, cnt);
     LAUNCH_CHECK();
     k_gemm_warp<<<nw, 32 * WARPS_PER_BLOCK, warp_smem(), s>>>(n, a.rp, a.ci, a.v, b.rp, b.ci, b.v, small, 0, cnt,

@@ -142,6 +142,7 @@ extern "C" int amgh_problem_create(const amgh_mesh *mesh, const double *kappa, d
 extern "C" int amgh_set_yd(amgh_problem *p, const double *y_d, int on_device)
 {
     if (!p || !y_d) return AMGH_ERR_INVALID_ARG;
+    StreamScope ss_(p->stream);
     return load_yd(p, y_d, on_device);
 }
 
@@ -336,6 +337,7 @@ extern "C" int amgh_amg_setup(amgh_problem *p, const amgh_amg_opts *opts)
         o.precision < 0 || o.precision > 2 || o.hessian_levels < 0)
         return AMGH_ERR_INVALID_ARG;
     double t0 = now_s();
+    StreamScope ss_(p->stream);
     reset_hierarchy(p);
     p->aopts = o;
     int st = setup_impl(p);
@@ -358,6 +360,7 @@ extern "C" int amgh_amg_setup(amgh_problem *p, const amgh_amg_opts *opts)
 extern "C" int amgh_hessian_apply(amgh_problem *p, const double *u, double *hu, int ncols)
 {
     NEED_SETUP(p);
+    StreamScope ss_(p->stream);
     if (!u || !hu || ncols < 1) return AMGH_ERR_INVALID_ARG;
     for (int c = 0; c < ncols; c++) TRY(hessian_level(p, 0, u + (int64_t)c * p->n, hu + (int64_t)c * p->n));
     TRY(timer_collect(p));
@@ -367,6 +370,7 @@ extern "C" int amgh_hessian_apply(amgh_problem *p, const double *u, double *hu, 
 extern "C" int amgh_precond_apply(amgh_problem *p, const double *r, double *z, int ncols)
 {
     NEED_SETUP(p);
+    StreamScope ss_(p->stream);
     if (!r || !z || ncols < 1) return AMGH_ERR_INVALID_ARG;
     for (int c = 0; c < ncols; c++) TRY(mlas_Q(p, 0, r + (int64_t)c * p->n, z + (int64_t)c * p->n));
     TRY(timer_collect(p));
@@ -376,6 +380,7 @@ extern "C" int amgh_precond_apply(amgh_problem *p, const double *r, double *z, i
 extern "C" int amgh_rhs(amgh_problem *p, double *b)
 {
     NEED_SETUP(p);
+    StreamScope ss_(p->stream);
     if (!b) return AMGH_ERR_INVALID_ARG;
     TRY(rhs_apply(p, b));
     return sync_stream(p);
@@ -394,6 +399,7 @@ extern "C" int amgh_solve(amgh_problem *p, const double *u0, double *u, double *
                           amgh_solve_info *info)
 {
     NEED_SETUP(p);
+    StreamScope ss_(p->stream);
     if (!u) return AMGH_ERR_INVALID_ARG;
     amgh_solve_opts o;
     if (opts) o = *opts;
@@ -423,6 +429,7 @@ extern "C" int amgh_solve_host(amgh_problem *p, const double *u0_host, double *u
                                const amgh_solve_opts *opts, amgh_solve_info *info)
 {
     NEED_SETUP(p);
+    StreamScope ss_(p->stream);
     if (!u_host) return AMGH_ERR_INVALID_ARG;
     Scratch sc;
     double *u0 = nullptr, *u = nullptr, *y = nullptr;
@@ -448,6 +455,7 @@ __global__ void k_sub(int n, const double *__restrict__ a, const double *__restr
 extern "C" int amgh_state_solve(amgh_problem *p, const double *u, double *y, double *J)
 {
     NEED_SETUP(p);
+    StreamScope ss_(p->stream);
     if (!u || !y) return AMGH_ERR_INVALID_ARG;
     CtrlLevel &C = p->cl[0];
     StateLevel &S = p->sl[0];
@@ -472,6 +480,7 @@ extern "C" int amgh_state_solve(amgh_problem *p, const double *u, double *y, dou
 extern "C" int amgh_gradient(amgh_problem *p, const double *u, const double *y, double *g)
 {
     NEED_SETUP(p);
+    StreamScope ss_(p->stream);
     if (!u || !y || !g) return AMGH_ERR_INVALID_ARG;
     CtrlLevel &C = p->cl[0];
     StateLevel &S = p->sl[0];
@@ -487,6 +496,7 @@ extern "C" int amgh_gradient(amgh_problem *p, const double *u, const double *y, 
 extern "C" int amgh_state_adjoint(amgh_problem *p, const double *w, double *g)
 {
     NEED_SETUP(p);
+    StreamScope ss_(p->stream);
     if (!w || !g) return AMGH_ERR_INVALID_ARG;
     CtrlLevel &C = p->cl[0];
     // A is symmetric, so A^-T w is one more AMG-CG solve
@@ -499,6 +509,7 @@ extern "C" int amgh_state_adjoint(amgh_problem *p, const double *w, double *g)
 extern "C" int amgh_vcycle(amgh_problem *p, int level, const double *b, double *x)
 {
     NEED_SETUP(p);
+    StreamScope ss_(p->stream);
     if (level < 0 || level >= p->Ls || !b || !x) return AMGH_ERR_INVALID_ARG;
     TRY(vcycle_run(p, level, 0, b, x, nullptr));
     return sync_stream(p);
@@ -508,6 +519,7 @@ extern "C" int amgh_state_solve_level(amgh_problem *p, int level, const double *
                                       int64_t *iters)
 {
     NEED_SETUP(p);
+    StreamScope ss_(p->stream);
     if (level < 0 || level >= p->Ls || !f || !y || !(tol > 0.0)) return AMGH_ERR_INVALID_ARG;
     TRY(state_solve(p, level, f, y, tol, iters));
     return sync_stream(p);
@@ -516,6 +528,7 @@ extern "C" int amgh_state_solve_level(amgh_problem *p, int level, const double *
 extern "C" int amgh_mass_solve(amgh_problem *p, int level, const double *b, double *x, int64_t *iters)
 {
     NEED_SETUP(p);
+    StreamScope ss_(p->stream);
     if (level < 0 || level >= p->Lc || !b || !x) return AMGH_ERR_INVALID_ARG;
     TRY(mass_solve(p, level, b, x, iters));
     return sync_stream(p);
@@ -524,6 +537,7 @@ extern "C" int amgh_mass_solve(amgh_problem *p, int level, const double *b, doub
 extern "C" int amgh_hessian_apply_level(amgh_problem *p, int level, const double *v, double *hv)
 {
     NEED_SETUP(p);
+    StreamScope ss_(p->stream);
     if (level < 0 || level >= p->ell || !v || !hv) return AMGH_ERR_INVALID_ARG;
     TRY(hessian_level(p, level, v, hv));
     return sync_stream(p);
@@ -532,6 +546,7 @@ extern "C" int amgh_hessian_apply_level(amgh_problem *p, int level, const double
 extern "C" int amgh_precond_apply_level(amgh_problem *p, int which, int level, const double *b, double *z)
 {
     NEED_SETUP(p);
+    StreamScope ss_(p->stream);
     if (level < 0 || level >= p->ell || !b || !z) return AMGH_ERR_INVALID_ARG;
     if (which == 0) TRY(mlas_Q(p, level, b, z));
     else {
@@ -671,6 +686,7 @@ extern "C" int amgh_kernel_stats(amgh_problem *p, int64_t *launches, double *ms,
 extern "C" void amgh_problem_destroy(amgh_problem *p)
 {
     if (!p) return;
+    StreamScope ss_(p->stream);
     if (p->stream) cudaStreamSynchronize(p->stream);
     else cudaDeviceSynchronize();
     for (auto e : p->timer.ev) cudaEventDestroy(e);
@@ -678,6 +694,8 @@ extern "C" void amgh_problem_destroy(amgh_problem *p)
     solver_free_graphs(p);
     p->harena.free_all();
     p->arena.free_all();
+    if (p->stream) cudaStreamSynchronize(p->stream);
+    else cudaDeviceSynchronize();
     if (p->h_scal) cudaFreeHost(p->h_scal);
     if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
     delete p;

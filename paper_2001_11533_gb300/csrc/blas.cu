@@ -38,7 +38,7 @@ int red_alloc(Arena &ar, RedSlot &slot, int capacity_rows)
     slot.capacity = cap;
     TRY(ar.alloc(&slot.partials, (int64_t)cap * 2));
     TRY(ar.alloc(&slot.ticket, 1));
-    CU(cudaMemset(slot.ticket, 0, sizeof(unsigned)));
+    CU(cudaMemsetAsync(slot.ticket, 0, sizeof(unsigned), g_alloc_stream));
     return AMGH_OK;
 }
 

@@ -29,52 +29,107 @@ int dense_from_csr(amgh_problem *p, const DevCsr &a, double *g)
     return AMGH_OK;
 }
 
-// column j: pivot and scaling (one block)
-__global__ void k_chol_col(int n, int j, double *__restrict__ g, int *__restrict__ info)
+// Blocked right-looking Cholesky with NB-wide panels (lower triangle, row-major):
+// for each panel k: factor the NB x NB diagonal block in shared memory, solve
+// the panel below it (L_ik L_kk^T = A_ik, one thread per row), and subtract
+// L_ik L_jk^T from the trailing lower triangle.
+#define NB 32
+
+__global__ void k_potrf_diag(int n, int k0, double *__restrict__ g, int *__restrict__ info)
 {
-    __shared__ double ljj;
-    if (threadIdx.x == 0) {
-        double s = g[(int64_t)j * n + j];
-        if (!(s > 0.0)) {
-            *info = j + 1;
-            s = 1.0;
+    __shared__ double a[NB][NB + 1];
+    int nb = min(NB, n - k0);
+    int t = threadIdx.x;
+    for (int e = t; e < nb * nb; e += blockDim.x) a[e / nb][e % nb] = g[(int64_t)(k0 + e / nb) * n + k0 + e % nb];
+    __syncthreads();
+    for (int j = 0; j < nb; j++) {
+        if (t == 0) {
+            double d = a[j][j];
+            if (!(d > 0.0)) {
+                atomicCAS(info, 0, k0 + j + 1);
+                d = 1.0;
+            }
+            a[j][j] = sqrt(d);
         }
-        ljj = sqrt(s);
-        g[(int64_t)j * n + j] = ljj;
+        __syncthreads();
+        double ljj = a[j][j];
+        for (int i = j + 1 + t; i < nb; i += blockDim.x) a[i][j] /= ljj;
+        __syncthreads();
+        for (int e = t; e < (nb - j - 1) * (nb - j - 1); e += blockDim.x) {
+            int i = j + 1 + e / (nb - j - 1), c = j + 1 + e % (nb - j - 1);
+            if (c <= i) a[i][c] -= a[i][j] * a[c][j];
+        }
+        __syncthreads();
+    }
+    for (int e = t; e < nb * nb; e += blockDim.x) {
+        int i = e / nb, c = e % nb;
+        g[(int64_t)(k0 + i) * n + k0 + c] = c <= i ? a[i][c] : 0.0;
+    }
+}
+
+// rows i >= k0 + NB: solve x L_kk^T = g[i, k0:k0+nb] (forward substitution)
+__global__ void k_trsm_panel(int n, int k0, double *__restrict__ g)
+{
+    __shared__ double l[NB][NB + 1];
+    int nb = min(NB, n - k0);
+    for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) l[e / nb][e % nb] = g[(int64_t)(k0 + e / nb) * n + k0 + e % nb];
+    __syncthreads();
+    int i = k0 + nb + blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double x[NB];
+    double *row = g + (int64_t)i * n + k0;
+    for (int c = 0; c < nb; c++) {
+        double s = row[c];
+        for (int q = 0; q < c; q++) s -= x[q] * l[c][q];
+        x[c] = s / l[c][c];
+    }
+    for (int c = 0; c < nb; c++) row[c] = x[c];
+}
+
+// trailing update g[i][j] -= sum_c L[i][k0+c] L[j][k0+c] for k0+nb <= j <= i (16x16 tiles)
+__global__ void k_syrk_update(int n, int k0, double *__restrict__ g)
+{
+    __shared__ double Ai[16][NB + 1], Aj[16][NB + 1];
+    int nb = min(NB, n - k0);
+    int base = k0 + nb;
+    int ti = blockIdx.y * 16, tj = blockIdx.x * 16;
+    if (tj > ti) return; // upper tiles untouched (block-uniform)
+    int t = threadIdx.y * 16 + threadIdx.x;
+    for (int e = t; e < 16 * nb; e += 256) {
+        int r = e / nb, c = e % nb;
+        int gi = base + ti + r, gj = base + tj + r;
+        Ai[r][c] = gi < n ? g[(int64_t)gi * n + k0 + c] : 0.0;
+        Aj[r][c] = gj < n ? g[(int64_t)gj * n + k0 + c] : 0.0;
     }
     __syncthreads();
-    for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) g[(int64_t)i * n + j] /= ljj;
+    int i = base + ti + threadIdx.y, j = base + tj + threadIdx.x;
+    if (i >= n || j > i) return;
+    double s = 0.0;
+    for (int c = 0; c < nb; c++) s += Ai[threadIdx.y][c] * Aj[threadIdx.x][c];
+    g[(int64_t)i * n + j] -= s;
 }
 
-// trailing update of the lower triangle: g_ik -= l_ij l_kj for j < k <= i
-__global__ void k_chol_update(int n, int j, double *__restrict__ g)
-{
-    int64_t m = n - j - 1;
-    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= m * m) return;
-    int i = j + 1 + (int)(t / m), k = j + 1 + (int)(t % m);
-    if (k > i) return;
-    g[(int64_t)i * n + k] -= g[(int64_t)i * n + j] * g[(int64_t)k * n + j];
-}
-
-// column k of W = L^-1 (one block per column): w_k = 1 / l_kk and, for i > k,
-// w_i = -(sum_{k <= j < i} l_ij w_j) / l_ii, the column kept in shared memory
+// column k of W = L^-1 (one warp per column): w_k = 1 / l_kk and, for i > k,
+// w_i = -(sum_{k <= j < i} l_ij w_j) / l_ii; the column is kept in shared memory
+#define TRINV_WARPS 4
 __global__ void k_trinv(int n, const double *__restrict__ L, double *__restrict__ W)
 {
-    extern __shared__ double w[];
-    __shared__ double sh32[32];
-    int k = blockIdx.x;
-    if (threadIdx.x == 0) w[k] = 1.0 / L[(int64_t)k * n + k];
-    __syncthreads();
+    extern __shared__ double wsh[];
+    int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int k = blockIdx.x * TRINV_WARPS + warp;
+    if (k >= n) return; // warp-uniform
+    double *w = wsh + (int64_t)warp * n;
+    if (lane == 0) w[k] = 1.0 / L[(int64_t)k * n + k];
+    __syncwarp();
     for (int i = k + 1; i < n; i++) {
         const double *row = L + (int64_t)i * n;
         double s = 0.0;
-        for (int j = k + threadIdx.x; j < i; j += blockDim.x) s += row[j] * w[j];
-        s = block_sum(s, sh32);
-        if (threadIdx.x == 0) w[i] = -s / row[i];
-        __syncthreads();
+        for (int j = k + lane; j < i; j += 32) s += row[j] * w[j];
+        s = warp_sum(s);
+        if (lane == 0) w[i] = -s / row[i];
+        __syncwarp();
     }
-    for (int i = threadIdx.x; i < n; i += blockDim.x) W[(int64_t)i * n + k] = i >= k ? w[i] : 0.0;
+    for (int i = lane; i < n; i += 32) W[(int64_t)i * n + k] = i >= k ? w[i] : 0.0;
 }
 
 // C = op(A) B (+ beta D), all row-major; transA: A is k x m and used as A^T
@@ -117,12 +172,15 @@ int dense_spd_inverse(amgh_problem *p, double *g, int n, double *inv, int *info_
 {
     cudaStream_t s = p->stream;
     CU(cudaMemsetAsync(info_dev, 0, sizeof(int), s));
-    for (int j = 0; j < n; j++) {
-        k_chol_col<<<1, 256, 0, s>>>(n, j, g, info_dev);
+    for (int k0 = 0; k0 < n; k0 += NB) {
+        k_potrf_diag<<<1, 256, 0, s>>>(n, k0, g, info_dev);
         LAUNCH_CHECK();
-        int64_t m = n - j - 1;
-        if (m > 0) {
-            k_chol_update<<<ceil_div(m * m, 256), 256, 0, s>>>(n, j, g);
+        int rest = n - k0 - NB;
+        if (rest > 0) {
+            k_trsm_panel<<<ceil_div(rest, 128), 128, 0, s>>>(n, k0, g);
+            LAUNCH_CHECK();
+            int tiles = ceil_div(rest, 16);
+            k_syrk_update<<<dim3(tiles, tiles), dim3(16, 16), 0, s>>>(n, k0, g);
             LAUNCH_CHECK();
         }
     }
@@ -134,7 +192,9 @@ int dense_spd_inverse(amgh_problem *p, double *g, int n, double *inv, int *info_
     Scratch sc;
     double *W = nullptr;
     TRY(sc.alloc(&W, (int64_t)n * n));
-    k_trinv<<<n, 256, sizeof(double) * n, s>>>(n, g, W);
+    size_t shm = sizeof(double) * (size_t)n * TRINV_WARPS;
+    if (shm > 48 * 1024) CU(cudaFuncSetAttribute(k_trinv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+    k_trinv<<<ceil_div(n, TRINV_WARPS), 32 * TRINV_WARPS, shm, s>>>(n, g, W);
     LAUNCH_CHECK();
     TRY(gemm(p, n, n, n, W, 1, W, 0.0, nullptr, inv));
     CU(cudaStreamSynchronize(s));

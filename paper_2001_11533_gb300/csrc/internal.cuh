@@ -40,6 +40,21 @@ void amgh_set_capturing(int on);
 static inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
 
 // ------------------------------------------------------------------ memory
+// Device memory comes from one stream-ordered pool per device owned by the
+// library (cudaMallocFromPoolAsync): allocations and frees are ordered on the
+// problem's stream, never synchronise the device, and freed blocks stay in the
+// pool for the next problem.  g_alloc_stream is the stream the calling thread
+// is working on (set by every entry point through StreamScope).
+extern thread_local cudaStream_t g_alloc_stream;
+int pool_alloc(void **p, size_t bytes);
+void pool_free(void *p);
+
+struct StreamScope {
+    cudaStream_t prev;
+    explicit StreamScope(cudaStream_t s) : prev(g_alloc_stream) { g_alloc_stream = s; }
+    ~StreamScope() { g_alloc_stream = prev; }
+};
+
 // Every device allocation of a problem goes through an Arena so destroy frees all.
 struct Arena {
     std::vector<void *> ptrs;
@@ -49,20 +64,17 @@ struct Arena {
         *p = nullptr;
         if (count <= 0) count = 1;
         void *q = nullptr;
-        cudaError_t e = cudaMalloc(&q, (size_t)count * sizeof(T));
-        if (e != cudaSuccess) {
-            cudaGetLastError();
-            return e == cudaErrorMemoryAllocation ? AMGH_ERR_OOM : AMGH_ERR_CUDA;
-        }
+        int st = pool_alloc(&q, (size_t)count * sizeof(T));
+        if (st) return st;
         ptrs.push_back(q);
         *p = (T *)q;
-        return AMGH_OK;
+        return 0;
     }
     void release(void *q);
     void free_all();
 };
 
-// Temporary device allocations released at scope exit.
+// Temporary device allocations released (stream-ordered) at scope exit.
 struct Scratch {
     std::vector<void *> ptrs;
     template <typename T>
@@ -71,18 +83,15 @@ struct Scratch {
         *p = nullptr;
         if (count <= 0) count = 1;
         void *q = nullptr;
-        cudaError_t e = cudaMalloc(&q, (size_t)count * sizeof(T));
-        if (e != cudaSuccess) {
-            cudaGetLastError();
-            return e == cudaErrorMemoryAllocation ? AMGH_ERR_OOM : AMGH_ERR_CUDA;
-        }
+        int st = pool_alloc(&q, (size_t)count * sizeof(T));
+        if (st) return st;
         ptrs.push_back(q);
         *p = (T *)q;
-        return AMGH_OK;
+        return 0;
     }
     ~Scratch()
     {
-        for (void *q : ptrs) cudaFree(q);
+        for (void *q : ptrs) pool_free(q);
     }
 };
 

@@ -83,9 +83,9 @@ int solver_alloc(amgh_problem *p)
         TRY(ar.alloc(&S.scal, 1));
         TRY(ar.alloc(&S.scal32, 1));
         TRY(ar.alloc(&S.rscal, 1));
-        CU(cudaMemset(S.scal, 0, sizeof(CgScal)));
-        CU(cudaMemset(S.scal32, 0, sizeof(CgScal)));
-        CU(cudaMemset(S.rscal, 0, sizeof(CgScal)));
+        CU(cudaMemsetAsync(S.scal, 0, sizeof(CgScal), g_alloc_stream));
+        CU(cudaMemsetAsync(S.scal32, 0, sizeof(CgScal), g_alloc_stream));
+        CU(cudaMemsetAsync(S.rscal, 0, sizeof(CgScal), g_alloc_stream));
         TRY(red_alloc(ar, S.red, m));
         p->chunk_hint[l] = 8;
         p->chunk_hint32[l] = 8;
@@ -100,7 +100,7 @@ int solver_alloc(amgh_problem *p)
         double **vm[] = {&C.t1, &C.ys, &C.t2, &C.ps};
         for (double **q : vm) TRY(ar.alloc(q, m));
         TRY(ar.alloc(&C.mscal, 1));
-        CU(cudaMemset(C.mscal, 0, sizeof(CgScal)));
+        CU(cudaMemsetAsync(C.mscal, 0, sizeof(CgScal), g_alloc_stream));
         int cap = n > m ? n : m;
         TRY(red_alloc(ar, C.red, cap));
         p->mchunk_hint[l] = 8;
@@ -109,7 +109,7 @@ int solver_alloc(amgh_problem *p)
     double **vo[] = {&p->ou, &p->or_, &p->oz, &p->op, &p->oq, &p->ob};
     for (double **q : vo) TRY(ar.alloc(q, n));
     TRY(ar.alloc(&p->oscal, 1));
-    CU(cudaMemset(p->oscal, 0, sizeof(CgScal)));
+    CU(cudaMemsetAsync(p->oscal, 0, sizeof(CgScal), g_alloc_stream));
     TRY(red_alloc(ar, p->ored, n > p->m ? n : p->m));
     TRY(ar.alloc(&p->dscratch, 4));
     return AMGH_OK;

@@ -1,6 +1,7 @@
 // util.cu -- arena, launch counting, scans and kernel timing shared by the
 // amgh translation units.
 #include <atomic>
+#include <mutex>
 
 #include "internal.cuh"
 #include "util.cuh"
@@ -15,11 +16,54 @@ void amgh_count_launch(int n)
 void amgh_set_capturing(int on) { g_capturing = on; }
 extern "C" int64_t amgh_launch_count(void) { return (int64_t)g_launches.load(); }
 
+// ------------------------------------------------------------------ memory pool
+thread_local cudaStream_t g_alloc_stream = 0;
+
+static cudaMemPool_t device_pool()
+{
+    static std::mutex mu;
+    static cudaMemPool_t pools[64] = {nullptr};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+    std::lock_guard<std::mutex> lock(mu);
+    if (!pools[dev]) {
+        cudaMemPoolProps props = {};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaMemPool_t pool = nullptr;
+        if (cudaMemPoolCreate(&pool, &props) != cudaSuccess) return nullptr;
+        // keep freed memory in the pool (no release at synchronisation points)
+        uint64_t keep = ~0ull;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        pools[dev] = pool;
+    }
+    return pools[dev];
+}
+
+int pool_alloc(void **p, size_t bytes)
+{
+    cudaMemPool_t pool = device_pool();
+    if (!pool) return AMGH_ERR_CUDA;
+    cudaError_t e = cudaMallocFromPoolAsync(p, bytes, pool, g_alloc_stream);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return e == cudaErrorMemoryAllocation ? AMGH_ERR_OOM : AMGH_ERR_CUDA;
+    }
+    return AMGH_OK;
+}
+
+void pool_free(void *p)
+{
+    if (p) cudaFreeAsync(p, g_alloc_stream);
+}
+
 void Arena::release(void *q)
 {
     for (auto &x : ptrs)
         if (x == q) {
-            cudaFree(q);
+            pool_free(q);
             x = nullptr;
         }
 }
@@ -27,7 +71,7 @@ void Arena::release(void *q)
 void Arena::free_all()
 {
     for (void *q : ptrs)
-        if (q) cudaFree(q);
+        if (q) pool_free(q);
     ptrs.clear();
 }
 
@@ -117,10 +161,8 @@ int exclusive_scan(const T *in, T *out, int64_t n, cudaStream_t s, T *total_host
     if (total_host) {
         CU(cudaMemcpyAsync(total_host, tot, sizeof(T), cudaMemcpyDeviceToHost, s));
         CU(cudaStreamSynchronize(s));
-    } else {
-        CU(cudaStreamSynchronize(s)); // Scratch frees bsum/tot at return
     }
-    return AMGH_OK;
+    return AMGH_OK; // bsum / tot are freed in stream order
 }
 
 template int exclusive_scan<int>(const int *, int *, int64_t, cudaStream_t, int *);
