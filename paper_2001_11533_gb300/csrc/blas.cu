@@ -54,6 +54,7 @@ enum {
     F_REF_UPDATE,    // t0 = r.r -> refinement stop test, scale
     F_STORE,         // t0 -> *out
     F_CG2,           // t0 = (r,z), t1 = (z,Az) -> alpha, beta (single-reduction CG)
+    F_SCALE,         // t0 = f.f -> scale = power of two nearest 1 / ||f||
 };
 
 __device__ __forceinline__ bool bad(double x) { return !(x == x) || isinf(x); }
@@ -177,6 +178,11 @@ __device__ void cg_finalize(int mode, const double *t, CgScal *sc, double *out)
     case F_STORE:
         *out = t[0];
         break;
+    case F_SCALE: {
+        double nrm = sqrt(t[0]);
+        sc->scale = (nrm > 0.0 && !bad(nrm)) ? exp2(-rint(log2(nrm))) : 1.0;
+        break;
+    }
     case F_CG2: {
         double g = t[0], d = t[1];
         if (!(g > 0.0) || !(d > 0.0)) {
@@ -201,6 +207,10 @@ __device__ void cg_finalize(int mode, const double *t, CgScal *sc, double *out)
         sc->alpha = alpha;
         sc->beta = beta;
         sc->k1 += 1;
+        sc->ahi = (float)alpha;
+        sc->alo = (float)(alpha - (double)sc->ahi);
+        sc->bhi = (float)beta;
+        sc->blo = (float)(beta - (double)sc->bhi);
         break;
     }
     }
@@ -602,6 +612,210 @@ int vec_fill(amgh_problem *p, int n, double v, double *x)
 {
     if (n == 0) return AMGH_OK;
     k_fill<<<vec_blocks(n), TPB, 0, p->stream>>>(n, v, x);
+    LAUNCH_CHECK();
+    return AMGH_OK;
+}
+
+// ------------------------------------------------------------------ double-float CG
+// Inner CG of precision mode 2 with every vector (x, r, p, q, s) held as
+// double-float: the FP64-sized buffer of n doubles is used as two FP32 arrays,
+// hi = [0, n) and lo = [n, 2n).  All per-element arithmetic stays on the FP32
+// pipe; the FP32 V-cycle reads r's hi half directly.  Reductions sum in
+// double-float inside each warp and in FP64 only across warps and blocks.
+
+template <int NV>
+__device__ bool reduce_df_last_block(const DF (&val)[NV], double *partials, unsigned *ticket, double (&tot)[NV])
+{
+    __shared__ double shw[NV][32];
+    __shared__ bool is_last;
+    int nb = gridDim.x, w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int q = 0; q < NV; q++) {
+        DF s = df_warp_sum(val[q]);
+        if (l == 0) shw[q][w] = df_to_double(s);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int q = 0; q < NV; q++) {
+            double t = 0.0;
+            for (int k = 0; k < nw; k++) t += shw[q][k];
+            partials[q * nb + blockIdx.x] = t;
+        }
+        __threadfence();
+        unsigned tk = atomicAdd(ticket, 1u);
+        is_last = (tk == (unsigned)nb - 1);
+    }
+    __syncthreads();
+    if (!is_last) return false;
+    __threadfence();
+#pragma unroll
+    for (int q = 0; q < NV; q++) {
+        double s = 0.0;
+        for (int b = threadIdx.x; b < nb; b += blockDim.x) s += ((volatile double *)partials)[q * nb + b];
+        s = warp_sum(s);
+        if (l == 0) shw[q][w] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int q = 0; q < NV; q++) {
+            double t = 0.0;
+            for (int k = 0; k < nw; k++) t += shw[q][k];
+            tot[q] = t;
+        }
+        *ticket = 0u;
+    }
+    return threadIdx.x == 0;
+}
+
+// ||f||^2 -> sc->scale, the power of two nearest 1 / ||f||.  The double-float
+// CG solves for the scaled right side (an exact scaling) so that its FP32
+// halves stay far from the FP32 exponent limits whatever the size of f.
+__global__ void k_df_norm(int n, const double *__restrict__ f, CgScal *sc, double *partials, unsigned *ticket)
+{
+    double v[1] = {0.0}, tot[1];
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) v[0] += f[i] * f[i];
+    if (reduce_last_block<1>(v, partials, ticket, tot)) cg_finalize(F_SCALE, tot, sc, nullptr);
+}
+
+// r = scale f (split into hi/lo), x = 0, reduce (scale f).(scale f)
+__global__ void k_df_start(int n, const double *__restrict__ f, float *__restrict__ xh, float *__restrict__ xl,
+                           float *__restrict__ rh, float *__restrict__ rl, CgScal *sc, double *partials,
+                           unsigned *ticket)
+{
+    DF acc = {0.f, 0.f}, tot_df[1];
+    double tot[1];
+    double scale = sc->scale;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        DF fi = df_from_double(scale * f[i]);
+        rh[i] = fi.hi;
+        rl[i] = fi.lo;
+        xh[i] = 0.f;
+        xl[i] = 0.f;
+        acc = df_add2(acc, df_mul2(fi, fi));
+    }
+    tot_df[0] = acc;
+    if (reduce_df_last_block<1>(tot_df, partials, ticket, tot)) cg_finalize(F_START, tot, sc, nullptr);
+}
+
+// K1: s = A z (FP32 z), reduce (r, z) and (z, s) -> alpha, beta
+template <int TPR>
+__global__ void k_df_spmv(MatView<float> A, const float *__restrict__ lo, const float *__restrict__ z,
+                          const float *__restrict__ rh, const float *__restrict__ rl, float *__restrict__ sh,
+                          float *__restrict__ sl, CgScal *sc, double *partials, unsigned *ticket)
+{
+    SKIP_DONE();
+    int row = my_row<TPR>();
+    DF v = row_sum_dfv<float, TPR>(A, lo, row, z);
+    DF a[2] = {{0.f, 0.f}, {0.f, 0.f}};
+    double tot[2];
+    if (row < A.rows && row_leader<TPR>()) {
+        sh[row] = v.hi;
+        sl[row] = v.lo;
+        float zr = z[row];
+        a[0] = df_mulf(DF{rh[row], rl[row]}, zr);
+        a[1] = df_mulf(v, zr);
+    }
+    if (reduce_df_last_block<2>(a, partials, ticket, tot)) cg_finalize(F_CG2, tot, sc, nullptr);
+}
+
+// K2: p = z + beta p, q = s + beta q, x += alpha p, r -= alpha q, reduce r.r
+__global__ void k_df_update(int n, const float *__restrict__ z, const float *__restrict__ sh,
+                            const float *__restrict__ sl, float *__restrict__ ph, float *__restrict__ pl,
+                            float *__restrict__ qh, float *__restrict__ ql, float *__restrict__ xh,
+                            float *__restrict__ xl, float *__restrict__ rh, float *__restrict__ rl, CgScal *sc,
+                            double *partials, unsigned *ticket)
+{
+    SKIP_DONE();
+    DF al = {sc->ahi, sc->alo}, be = {sc->bhi, sc->blo};
+    DF nal = {-al.hi, -al.lo};
+    bool first = sc->beta == 0.0;
+    DF acc = {0.f, 0.f}, tot_df[1];
+    double tot[1];
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        DF zi = {z[i], 0.f};
+        DF si = {sh[i], sl[i]};
+        DF pi = first ? zi : df_add2(zi, df_mul2(be, DF{ph[i], pl[i]}));
+        DF qi = first ? si : df_add2(si, df_mul2(be, DF{qh[i], ql[i]}));
+        DF xi = df_add2(DF{xh[i], xl[i]}, df_mul2(al, pi));
+        DF ri = df_add2(DF{rh[i], rl[i]}, df_mul2(nal, qi));
+        ph[i] = pi.hi;
+        pl[i] = pi.lo;
+        qh[i] = qi.hi;
+        ql[i] = qi.lo;
+        xh[i] = xi.hi;
+        xl[i] = xi.lo;
+        rh[i] = ri.hi;
+        rl[i] = ri.lo;
+        acc = df_add2(acc, df_mul2(ri, ri));
+    }
+    tot_df[0] = acc;
+    if (reduce_df_last_block<1>(tot_df, partials, ticket, tot)) cg_finalize(F_RR, tot, sc, nullptr);
+}
+
+// y = x / scale (exact: scale is a power of two)
+__global__ void k_df_to_double(int n, const float *__restrict__ xh, const float *__restrict__ xl,
+                               const CgScal *sc, double *__restrict__ y)
+{
+    double inv = 1.0 / sc->scale;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        y[i] = ((double)xh[i] + (double)xl[i]) * inv;
+}
+
+static inline float *hi_of(double *b) { return (float *)b; }
+static inline float *lo_of(double *b, int n) { return (float *)b + n; }
+static inline const float *hi_of(const double *b) { return (const float *)b; }
+static inline const float *lo_of(const double *b, int n) { return (const float *)b + n; }
+
+int dfcg_start(amgh_problem *p, RedSlot &red, int n, const double *f, double *x, double *r, CgScal *sc, double tol,
+               int maxit)
+{
+    TRY(set_scal(p, sc, tol, maxit));
+    k_df_norm<<<vec_blocks(n), TPB, 0, p->stream>>>(n, f, sc, red.partials, red.ticket);
+    LAUNCH_CHECK();
+    k_df_start<<<vec_blocks(n), TPB, 0, p->stream>>>(n, f, hi_of(x), lo_of(x, n), hi_of(r), lo_of(r, n), sc,
+                                                    red.partials, red.ticket);
+    LAUNCH_CHECK();
+    return AMGH_OK;
+}
+
+int dfcg_spmv(amgh_problem *p, RedSlot &red, const DevCsr &a, const float *z, const double *r, double *s,
+              CgScal *sc, int timed)
+{
+    (void)timed;
+    MatView<float> A = view<float>(a);
+    int n = a.rows;
+    const float *lo = a.lo32;
+#define DFSPMV(TPR)                                                                                            \
+    k_df_spmv<TPR><<<rows_grid(n, TPR), TPB, 0, p->stream>>>(A, lo, z, hi_of(r), lo_of(r, n), hi_of(s),        \
+                                                             lo_of(s, n), sc, red.partials, red.ticket)
+    switch (A.tpr) {
+    case 2: DFSPMV(2); break;
+    case 4: DFSPMV(4); break;
+    case 8: DFSPMV(8); break;
+    case 16: DFSPMV(16); break;
+    case 32: DFSPMV(32); break;
+    default: DFSPMV(1); break;
+    }
+#undef DFSPMV
+    LAUNCH_CHECK();
+    return AMGH_OK;
+}
+
+int dfcg_update(amgh_problem *p, RedSlot &red, int n, const float *z, const double *s, double *pv, double *q,
+                double *x, double *r, CgScal *sc)
+{
+    k_df_update<<<vec_blocks(n), TPB, 0, p->stream>>>(n, z, hi_of(s), lo_of(s, n), hi_of(pv), lo_of(pv, n),
+                                                     hi_of(q), lo_of(q, n), hi_of(x), lo_of(x, n), hi_of(r),
+                                                     lo_of(r, n), sc, red.partials, red.ticket);
+    LAUNCH_CHECK();
+    return AMGH_OK;
+}
+
+int df_to_double(amgh_problem *p, int n, const double *x, const CgScal *sc, double *y)
+{
+    k_df_to_double<<<vec_blocks(n), TPB, 0, p->stream>>>(n, hi_of(x), lo_of(x, n), sc, y);
     LAUNCH_CHECK();
     return AMGH_OK;
 }

@@ -134,6 +134,7 @@ struct CgScal {
     int done, iters, status, maxit;
     int total_iters;
     int k1; // single-reduction CG: number of alpha/beta updates so far
+    float ahi, alo, bhi, blo; // alpha and beta as double-float (double-float CG)
     int pad[2];
 };
 
@@ -295,6 +296,14 @@ int cg2_update(amgh_problem *p, RedSlot &red, int n, Z *z, const T *s, T *pv, T 
                const double *invd, CgScal *sc);
 int cg_update_outer(amgh_problem *p, RedSlot &red, int n, double *x, double *r, const double *pv, const double *q,
                     CgScal *sc);
+// double-float CG (vectors stored as hi / lo FP32 halves of an FP64-sized buffer)
+int dfcg_start(amgh_problem *p, RedSlot &red, int n, const double *f, double *x, double *r, CgScal *sc, double tol,
+               int maxit);
+int dfcg_spmv(amgh_problem *p, RedSlot &red, const DevCsr &a, const float *z, const double *r, double *s,
+              CgScal *sc, int timed);
+int dfcg_update(amgh_problem *p, RedSlot &red, int n, const float *z, const double *s, double *pv, double *q,
+                double *x, double *r, CgScal *sc);
+int df_to_double(amgh_problem *p, int n, const double *x, const CgScal *sc, double *y);
 int ref_start(amgh_problem *p, RedSlot &red, int n, const double *f, double *y, double *r,
               CgScal *rs, double tol, int maxit);
 int ref_to32(amgh_problem *p, RedSlot &red, int n, const double *r, float *r32, CgScal *rs);

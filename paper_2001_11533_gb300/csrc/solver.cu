@@ -283,12 +283,10 @@ __global__ void k_f2d(int n, const float *__restrict__ a, double *__restrict__ b
 static int cg_body_start(amgh_problem *p, int l, int mode)
 {
     StateLevel &S = p->sl[l];
-    int n = S.A.rows;
     if (mode == 1) return vcyc<float>(p, l, S.gr, S.gz, &S.scal32->done);
     if (mode == 0) return vcyc<double>(p, l, S.cr, S.cz, &S.scal->done);
-    k_d2f<<<ceil_div(n, 256), 256, 0, p->stream>>>(n, S.cr, S.fb, &S.scal->done);
-    LAUNCH_CHECK();
-    return vcyc<float>(p, l, S.fb, S.gz, &S.scal->done);
+    // double-float CG: the V-cycle reads the hi half of r
+    return vcyc<float>(p, l, (const float *)S.cr, S.gz, &S.scal->done);
 }
 
 static int cg_body_iter(amgh_problem *p, int l, int mode)
@@ -306,9 +304,9 @@ static int cg_body_iter(amgh_problem *p, int l, int mode)
         TRY((cg2_update<double, double>(p, S.red, n, S.cz, S.cs, S.cp, S.cq, S.cx, S.cr, nullptr, nullptr, S.scal)));
         return vcyc<double>(p, l, S.cr, S.cz, &S.scal->done);
     }
-    TRY((cg2_spmv<double, float>(p, S.red, S.A, S.gz, S.cr, S.cs, S.scal, timed)));
-    TRY((cg2_update<double, float>(p, S.red, n, S.gz, S.cs, S.cp, S.cq, S.cx, S.cr, S.fb, nullptr, S.scal)));
-    return vcyc<float>(p, l, S.fb, S.gz, &S.scal->done);
+    TRY(dfcg_spmv(p, S.red, S.A, S.gz, S.cr, S.cs, S.scal, timed));
+    TRY(dfcg_update(p, S.red, n, S.gz, S.cs, S.cp, S.cq, S.cx, S.cr, S.scal));
+    return vcyc<float>(p, l, (const float *)S.cr, S.gz, &S.scal->done);
 }
 
 // PCG for A_l x = f preconditioned by V_l; the solution is left in S.cx (FP64
@@ -319,6 +317,7 @@ static int pcg_run(amgh_problem *p, int l, int mode, const void *f, double tol, 
     int n = S.A.rows;
     CgScal *sc = mode == 1 ? S.scal32 : S.scal;
     if (mode == 1) TRY(cg_start<float>(p, S.red, n, (const float *)f, S.gx, S.gr, sc, tol, maxit, 1));
+    else if (mode == 2) TRY(dfcg_start(p, S.red, n, (const double *)f, S.cx, S.cr, sc, tol, maxit));
     else TRY(cg_start<double>(p, S.red, n, (const double *)f, S.cx, S.cr, sc, tol, maxit, 1));
     CgGraph &g = S.graph[mode];
     bool gr = use_graphs(p);
@@ -362,8 +361,11 @@ int state_solve(amgh_problem *p, int l, const double *f, double *y, double tol, 
     int prec = p->aopts.precision;
     if (prec != 1) {
         int st = pcg_run(p, l, prec == 2 ? 2 : 0, f, tol, maxit, iters);
-        k_copy<double><<<ceil_div(n, 256), 256, 0, p->stream>>>(n, S.cx, y, nullptr);
-        LAUNCH_CHECK();
+        if (prec == 2) TRY(df_to_double(p, n, S.cx, S.scal, y));
+        else {
+            k_copy<double><<<ceil_div(n, 256), 256, 0, p->stream>>>(n, S.cx, y, nullptr);
+            LAUNCH_CHECK();
+        }
         return st;
     }
     // r = f - A y in FP64, FP32 PCG on A e = r / ||r||, y += ||r|| e

@@ -10,6 +10,7 @@
 #pragma once
 
 #include "internal.cuh"
+#include "df.cuh"
 
 template <typename T>
 struct MatView {
@@ -73,45 +74,7 @@ __device__ __forceinline__ T row_sum(const MatView<T> &m, int row, F xf)
     return acc;
 }
 
-// ---- double-float (FP32 pair) accumulation: sums carried as hi + lo with
-// Knuth's error-free two-sum, products split exactly with fmaf.  Used to form
-// FP64-accurate (about 2^-48 relative) matrix-vector products on the FP32 pipe.
-struct DF {
-    float hi, lo;
-};
-
-__device__ __forceinline__ void df_add(DF &a, float b)
-{
-    float s = a.hi + b;
-    float bb = s - a.hi;
-    float err = (a.hi - (s - bb)) + (b - bb);
-    a.hi = s;
-    a.lo += err;
-}
-
-__device__ __forceinline__ void df_merge(DF &a, const DF &b)
-{
-    df_add(a, b.hi);
-    a.lo += b.lo;
-}
-
-// a_hi*z exactly as p + e, plus the small terms; all added into acc
-__device__ __forceinline__ void df_fma(DF &acc, float ahi, float alo, float z)
-{
-    float p = ahi * z;
-    float e = fmaf(ahi, z, -p);
-    df_add(acc, p);
-    acc.lo += e + alo * z;
-}
-
-__device__ __forceinline__ void df_fma2(DF &acc, float ahi, float alo, float zhi, float zlo)
-{
-    float p = ahi * zhi;
-    float e = fmaf(ahi, zhi, -p);
-    df_add(acc, p);
-    acc.lo += e + (ahi * zlo + alo * zhi);
-}
-
+// a z added to acc, a = ahi + alo (FP32 parts of an FP64 value)
 template <typename Z>
 __device__ __forceinline__ void df_term(DF &acc, float ahi, float alo, Z z);
 template <>
@@ -124,7 +87,37 @@ __device__ __forceinline__ void df_term<double>(DF &acc, float ahi, float alo, d
     df_fma2(acc, ahi, alo, zhi, zlo);
 }
 
-// sum_j a_rj z_j in double-float; every lane of the group returns the value
+// sum_j a_rj z_j in double-float (normalised); every lane of the group returns it
+template <typename Z, int TPR>
+__device__ __forceinline__ DF row_sum_dfv(const MatView<float> &m, const float *__restrict__ lo, int row,
+                                          const Z *__restrict__ z)
+{
+    DF acc = {0.f, 0.f};
+    if (TPR == 1) {
+        if (row < m.rows) {
+            int s = row >> 5, lane = row & 31;
+            int end = m.ptr[s + 1];
+#pragma unroll 4
+            for (int k = m.ptr[s] + lane; k < end; k += 32) df_term<Z>(acc, m.v[k], lo[k], __ldg(&z[m.ci[k]]));
+        }
+    } else {
+        int lane = threadIdx.x & (TPR - 1);
+        if (row < m.rows) {
+            int end = m.ptr[row + 1];
+#pragma unroll 4
+            for (int k = m.ptr[row] + lane; k < end; k += TPR) df_term<Z>(acc, m.v[k], lo[k], __ldg(&z[m.ci[k]]));
+        }
+#pragma unroll
+        for (int o = TPR / 2; o > 0; o >>= 1) {
+            DF other = {__shfl_xor_sync(0xffffffffu, acc.hi, o, TPR), __shfl_xor_sync(0xffffffffu, acc.lo, o, TPR)};
+            df_merge(acc, other);
+        }
+    }
+    DF r;
+    quick_two_sum(acc.hi, acc.lo, r.hi, r.lo);
+    return r;
+}
+
 template <typename Z, int TPR>
 __device__ __forceinline__ double row_sum_df(const MatView<float> &m, const float *__restrict__ lo, int row,
                                              const Z *__restrict__ z)
