@@ -76,7 +76,12 @@ typedef struct {
  *                  inner CG with FP64 iterative refinement of every PDE solve;
  *                  2 = FP64 CG for every PDE solve preconditioned by FP32
  *                  V-cycles (FP32 smoothers, transfers and coarse solve)
- *  smooth_prolongator 1 = S = (I - omega D^-1 A) S_hat, 0 = S_hat */
+ *  smooth_prolongator 1 = S = (I - omega D^-1 A) S_hat, 0 = S_hat
+ *  coarse_solve    Q_{l-1} on the coarsest Hessian level: 0 = exact, the
+ *                  dense inverse of H_{l-1} (the assumption of Sec. 3-4;
+ *                  needs at most 4096 control dofs there); 1 = unpreconditioned
+ *                  CG on H_{l-1} to the relative residual coarse_tol of the
+ *                  solve options (Sec. 5.2 uses 1e-4) */
 typedef struct {
     int max_levels;
     int hessian_levels;
@@ -86,6 +91,7 @@ typedef struct {
     int smooth_degree;
     int precision;
     int smooth_prolongator;
+    int coarse_solve;
 } amgh_amg_opts;
 
 /* Solve options (Sec. 5.2-5.3).
@@ -98,7 +104,19 @@ typedef struct {
  *  inner_max_iter, mass_max_iter   caps of the inner CG loops
  *  precond_tol  relative residual of the state/adjoint solves of the coarse
  *               Hessians H_j, j >= 1, which occur only inside the
- *               preconditioner (0 = inner_tol; Sec. 5.2 uses 1e-8) */
+ *               preconditioner (0 = inner_tol; Sec. 5.2 uses 1e-8)
+ *  coarse_tol, coarse_max_iter   stopping rule of the coarsest-level CG
+ *               (coarse_solve = 1); reaching the cap is not an error, the
+ *               iterate is used as it stands
+ *  level_fallback  1 = when the outer CG finds the preconditioner indefinite
+ *               (possible for small beta, Sec. 3.2; the experiments of
+ *               Sec. 5.5-5.6 cut levels for this reason), drop the
+ *               coarsest Hessian level and restart from u = 0, down to two
+ *               levels (always positive definite); info->fallbacks and
+ *               info->hessian_levels record it.  The reduction persists for
+ *               later solves of this problem until amgh_amg_setup.  With
+ *               coarse_solve = 0 a level whose dense H_{l-1} would exceed
+ *               4096 dofs ends the fallback with AMGH_ERR_INDEFINITE. */
 typedef struct {
     double tol;
     int max_iter;
@@ -109,6 +127,9 @@ typedef struct {
     int inner_max_iter;
     int mass_max_iter;
     double precond_tol;
+    double coarse_tol;
+    int coarse_max_iter;
+    int level_fallback;
 } amgh_solve_opts;
 
 /* Counters of the last amgh_solve (or since amgh_reset_counters). */
@@ -122,12 +143,16 @@ typedef struct {
     double final_relres;     /* ||b - H u|| / ||b|| recomputed at the end */
     double t_setup_s;
     double t_solve_s;
+    int hessian_levels;      /* levels l of the preconditioner at the end */
+    int fallbacks;           /* levels dropped by level_fallback */
+    int64_t coarse_iters;    /* coarsest-level CG iterations (coarse_solve = 1) */
 } amgh_solve_info;
 
 /* Defaults: max_levels 25, hessian_levels 0, theta 0.08, coarse_max 256,
- * Chebyshev degree 2, precision 0, smoothed prolongator; tol 1e-8,
- * max_iter 200, inner/mass tol 1e-10, precond 1, ncols 1, caps 1000,
- * precond_tol 0 (= inner_tol). */
+ * Chebyshev degree 2, precision 0, smoothed prolongator, coarse_solve 0;
+ * tol 1e-8, max_iter 200, inner/mass tol 1e-10, precond 1, ncols 1, caps
+ * 1000, precond_tol 0 (= inner_tol), coarse_tol 1e-4, coarse_max_iter 1000,
+ * level_fallback 0. */
 void amgh_amg_opts_default(amgh_amg_opts *opts);
 void amgh_solve_opts_default(amgh_solve_opts *opts);
 
@@ -261,6 +286,33 @@ int amgh_reset_counters(amgh_problem *p);
  * 4*v*rows per launch, v = value bytes). */
 int amgh_kernel_timing(amgh_problem *p, int enable);
 int amgh_kernel_stats(amgh_problem *p, int64_t *launches, double *ms, double *bytes);
+
+/* Batched solves of many independent problems (the batching pattern: many
+ * desired states, many meshes of uneven size).  The batch runtime gives every
+ * problem its own non-blocking CUDA stream and host worker thread; each worker
+ * runs the whole hot path of its problem (AMG setup if not yet done, then
+ * one outer CG per desired state, each with the captured CUDA graphs of that
+ * problem), so the small, latency-bound problems overlap on the GPU.
+ *   probs      nprob problems created by amgh_problem_create on the current
+ *              device; the batch borrows them (caller keeps ownership and must
+ *              not use them from another thread until amgh_batch_destroy)
+ *   amg        options for problems whose hierarchy is not set up (NULL =
+ *              defaults); amgh_batch_setup builds all hierarchies concurrently
+ * amgh_batch_solve:
+ *   yd_dev[p]  device array of ncols[p] desired states of problem p, each of
+ *              n_vertices(p) doubles, column-major
+ *   u_dev[p]   device array of ncols[p] controls of problem p (n(p) doubles each)
+ *   opts       solve options shared by all problems (NULL = defaults)
+ *   info       nprob entries (may be NULL): counters summed over the
+ *              problem's columns, status = first error of the problem
+ * Returns AMGH_OK if every solve converged, else the first error in problem
+ * order.  The call returns after all work has completed. */
+typedef struct amgh_batch amgh_batch;
+int amgh_batch_create(amgh_problem *const *probs, int nprob, amgh_batch **out);
+int amgh_batch_setup(amgh_batch *b, const amgh_amg_opts *amg);
+int amgh_batch_solve(amgh_batch *b, const double *const *yd_dev, const int *ncols, double *const *u_dev,
+                     const amgh_solve_opts *opts, amgh_solve_info *info);
+void amgh_batch_destroy(amgh_batch *b);
 
 /* Aggregation of a caller's matrix that allocates no device memory.  The
  * paper has no counterpart: this is a service for callers that cannot call

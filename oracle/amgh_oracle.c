@@ -88,6 +88,10 @@ typedef struct {
     double pc_inner_tol; /* inner solves of the coarse Hessians inside the preconditioner */
     int inner_maxit, mass_maxit;
     long inner_iters, mass_iters, happlies;
+    /* coarsest Hessian level: 0 = dense Cholesky of H_{ell-1}, 1 = plain CG */
+    int coarse_solve, coarse_maxit;
+    double coarse_tol;
+    long coarse_iters;
 } orc_t;
 
 /* ------------------------------------------------------------------ utils */
@@ -985,11 +989,27 @@ done:
     return st;
 }
 
-/* Algorithm MLAS (Sec. 3.2), M_u-scaled: Q_j approximates H_j^-1 */
+static int op_H(orc_t *o, int l, const double *x, double *y) { return hessian(o, l, x, y); }
+static int prec_none(orc_t *o, int l, const double *x, double *y)
+{
+    memcpy(y, x, sizeof(double) * (size_t)o->Mu[l].rows);
+    return ORC_OK;
+}
+
+/* Algorithm MLAS (Sec. 3.2), M_u-scaled: Q_j approximates H_j^-1.  On the
+ * coarsest level Q is H^-1 itself (dense Cholesky, the assumption of the
+ * analysis), or unpreconditioned CG on H to a loose tolerance as in the
+ * implementation of Sec. 5.2 (the iterate at the cap is used as it stands). */
 static int mlas_Q(orc_t *o, int j, const double *b, double *u)
 {
     int n = o->Mu[j].rows;
     if (j == o->ell - 1) {
+        if (o->coarse_solve == 1) {
+            long it = 0;
+            int st = pcg(o, j, n, op_H, prec_none, b, u, o->coarse_tol, o->coarse_maxit, &it, NULL);
+            o->coarse_iters += it;
+            return st == ORC_NOT_CONVERGED ? ORC_OK : st;
+        }
         chol_solve(o->Hc_chol, n, b, u);
         return ORC_OK;
     }
@@ -1235,6 +1255,18 @@ int orc_set_tols(void *h, double inner_tol, double mass_tol, int inner_maxit, in
     o->mass_tol = mass_tol;
     o->inner_maxit = inner_maxit;
     o->mass_maxit = mass_maxit;
+    return ORC_OK;
+}
+
+int orc_set_coarse_solve(void *h, int mode, double tol, int maxit, long *iters)
+{
+    orc_t *o = h;
+    if ((mode != 0 && mode != 1) || !(tol > 0.0) || maxit < 1) return ORC_INVALID;
+    o->coarse_solve = mode;
+    o->coarse_tol = tol;
+    o->coarse_maxit = maxit;
+    if (iters) *iters = o->coarse_iters;
+    o->coarse_iters = 0;
     return ORC_OK;
 }
 

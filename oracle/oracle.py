@@ -58,6 +58,7 @@ def lib():
                 "orc_setup": [P, I, I, D, I, I, I, I],
                 "orc_set_tols": [P, D, D, I, I],
                 "orc_set_precond_tol": [P, D],
+                "orc_set_coarse_solve": [P, I, D, I, P],
                 "orc_sizes": [P, P, P, P, P, P, P, P],
                 "orc_matrix_info": [P, I, I, P, P, P],
                 "orc_matrix_copy": [P, I, I, P, P, P],
@@ -159,6 +160,14 @@ class Oracle:
     def set_precond_tol(self, pc_inner_tol):
         """Tolerance of the coarse-level state solves inside the preconditioner."""
         _check(lib().orc_set_precond_tol(self.h, pc_inner_tol), "set_precond_tol")
+
+    def set_coarse_solve(self, mode, tol=1e-4, maxit=1000):
+        """Coarsest Hessian level: 0 = dense Cholesky, 1 = plain CG to `tol`
+        (Sec. 5.2).  Returns the coarse CG iterations since the last call."""
+        it = C.c_long()
+        _check(lib().orc_set_coarse_solve(self.h, mode, float(tol), int(maxit), C.byref(it)),
+               "set_coarse_solve")
+        return it.value
 
     def set_yd(self, yd):
         self._yd = np.ascontiguousarray(yd, dtype=np.float64)

@@ -36,19 +36,21 @@ class amgh_mesh(C.Structure):
 class amgh_amg_opts(C.Structure):
     _fields_ = [("max_levels", C.c_int), ("hessian_levels", C.c_int), ("theta", C.c_double),
                 ("coarse_max", C.c_int), ("smoother", C.c_int), ("smooth_degree", C.c_int),
-                ("precision", C.c_int), ("smooth_prolongator", C.c_int)]
+                ("precision", C.c_int), ("smooth_prolongator", C.c_int), ("coarse_solve", C.c_int)]
 
 
 class amgh_solve_opts(C.Structure):
     _fields_ = [("tol", C.c_double), ("max_iter", C.c_int), ("inner_tol", C.c_double),
                 ("mass_tol", C.c_double), ("precond", C.c_int), ("ncols", C.c_int),
-                ("inner_max_iter", C.c_int), ("mass_max_iter", C.c_int), ("precond_tol", C.c_double)]
+                ("inner_max_iter", C.c_int), ("mass_max_iter", C.c_int), ("precond_tol", C.c_double),
+                ("coarse_tol", C.c_double), ("coarse_max_iter", C.c_int), ("level_fallback", C.c_int)]
 
 
 class amgh_solve_info(C.Structure):
     _fields_ = [("status", C.c_int), ("outer_iters", C.c_int), ("hessian_applies", C.c_int64),
                 ("inner_iters", C.c_int64), ("mass_iters", C.c_int64), ("refinements", C.c_int64),
-                ("final_relres", C.c_double), ("t_setup_s", C.c_double), ("t_solve_s", C.c_double)]
+                ("final_relres", C.c_double), ("t_setup_s", C.c_double), ("t_solve_s", C.c_double),
+                ("hessian_levels", C.c_int), ("fallbacks", C.c_int), ("coarse_iters", C.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -87,6 +89,10 @@ _SIGS = {
     "amgh_kernel_stats": ([_P, _P, _P, _P], _I),
     "amgh_launch_count": ([], _I64),
     "amgh_aggregate_noalloc": ([_I, _P, _P, _P, _D, _P, _P, _P], _I),
+    "amgh_batch_create": ([_P, _I, _P], _I),
+    "amgh_batch_setup": ([_P, _P], _I),
+    "amgh_batch_solve": ([_P, _P, _P, _P, _P, _P], _I),
+    "amgh_batch_destroy": ([_P], None),
     "amgh_problem_destroy": ([_P], None),
     "amgh_status_string": ([_I], C.c_char_p),
 }
@@ -142,20 +148,25 @@ def aggregate_noalloc(rowptr, col, val, theta, agg_out, stream=None):
     return nagg.value
 
 
+def _fill(o, kw):
+    names = {k for k, _ in o._fields_}
+    for k, v in kw.items():
+        if k not in names:
+            raise TypeError(f"{type(o).__name__} has no field {k!r}")
+        setattr(o, k, v)
+    return o
+
+
 def amg_opts(**kw) -> amgh_amg_opts:
     o = amgh_amg_opts()
     lib().amgh_amg_opts_default(C.byref(o))
-    for k, v in kw.items():
-        setattr(o, k, v)
-    return o
+    return _fill(o, kw)
 
 
 def solve_opts(**kw) -> amgh_solve_opts:
     o = amgh_solve_opts()
     lib().amgh_solve_opts_default(C.byref(o))
-    for k, v in kw.items():
-        setattr(o, k, v)
-    return o
+    return _fill(o, kw)
 
 
 class Problem:
@@ -374,3 +385,49 @@ class Problem:
         n, ms, b = C.c_int64(), C.c_double(), C.c_double()
         check(lib().amgh_kernel_stats(self.h, C.byref(n), C.byref(ms), C.byref(b)), "amgh_kernel_stats")
         return {"launches": n.value, "ms": ms.value, "bytes": b.value}
+
+
+class Batch:
+    """Many independent problems solved concurrently (amgh_batch_*): one CUDA
+    stream and one native worker thread per problem."""
+
+    def __init__(self, problems):
+        self.problems = list(problems)
+        arr = (C.c_void_p * len(self.problems))(*[p.h.value for p in self.problems])
+        h = C.c_void_p()
+        check(lib().amgh_batch_create(arr, len(self.problems), C.byref(h)), "amgh_batch_create")
+        self.h = h
+
+    def setup(self, **kw):
+        o = amg_opts(**kw)
+        check(lib().amgh_batch_setup(self.h, C.byref(o)), "amgh_batch_setup")
+        for p in self.problems:
+            p.sizes = p.query_sizes()
+        return self
+
+    def solve(self, yds, raise_on_error=True, **kw):
+        """yds[p]: CUDA float64 tensor (ncols, n_vertices) of desired states;
+        returns a list of (ncols, n) controls and the per-problem counters."""
+        import torch
+        np_ = len(self.problems)
+        yds = [y.contiguous() for y in yds]
+        us = [torch.empty_like(y) for y in yds]
+        ycols = (C.c_int * np_)(*[int(y.shape[0]) for y in yds])
+        yptr = (C.c_void_p * np_)(*[y.data_ptr() for y in yds])
+        uptr = (C.c_void_p * np_)(*[u.data_ptr() for u in us])
+        infos = (amgh_solve_info * np_)()
+        o = solve_opts(**kw)
+        # the batch runs on its own streams: inputs and outputs must be ready
+        torch.cuda.current_stream().synchronize()
+        st = lib().amgh_batch_solve(self.h, yptr, ycols, uptr, C.byref(o), infos)
+        if raise_on_error:
+            check(st, "amgh_batch_solve")
+        return us, [i.as_dict() for i in infos], st
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().amgh_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        self.close()

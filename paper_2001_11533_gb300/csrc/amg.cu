@@ -627,11 +627,8 @@ int spgemm(amgh_problem *p, Arena &ar, const DevCsr &a, const DevCsr &b, DevCsr 
     int n = a.rows;
     c.rows = n;
     c.cols = b.cols;
-    static bool attr_set = false;
-    if (!attr_set) {
-        CU(cudaFuncSetAttribute(k_gemm_warp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)warp_smem()));
-        attr_set = true;
-    }
+    // the attribute is per function and device; setting it again is harmless
+    CU(cudaFuncSetAttribute(k_gemm_warp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)warp_smem()));
     Scratch sc;
     long long *ub = nullptr, *toff = nullptr;
     int *cnt = nullptr, *tkey = nullptr, *small = nullptr;

@@ -27,6 +27,7 @@ extern "C" void amgh_amg_opts_default(amgh_amg_opts *o)
     o->smooth_degree = 2;
     o->precision = 0;
     o->smooth_prolongator = 1;
+    o->coarse_solve = 0;
 }
 
 extern "C" void amgh_solve_opts_default(amgh_solve_opts *o)
@@ -41,6 +42,9 @@ extern "C" void amgh_solve_opts_default(amgh_solve_opts *o)
     o->inner_max_iter = 1000;
     o->mass_max_iter = 1000;
     o->precond_tol = 0.0;
+    o->coarse_tol = 1e-4;
+    o->coarse_max_iter = 1000;
+    o->level_fallback = 0;
 }
 
 extern "C" const char *amgh_status_string(int s)
@@ -157,13 +161,15 @@ extern "C" int amgh_set_solve_opts(amgh_problem *p, const amgh_solve_opts *o)
 {
     if (!p || !o) return AMGH_ERR_INVALID_ARG;
     if (!(o->inner_tol > 0.0) || !(o->mass_tol > 0.0) || o->inner_max_iter < 1 || o->mass_max_iter < 1 ||
-        !(o->precond_tol >= 0.0))
+        !(o->precond_tol >= 0.0) || !(o->coarse_tol > 0.0) || o->coarse_max_iter < 1)
         return AMGH_ERR_INVALID_ARG;
     p->sopts.inner_tol = o->inner_tol;
     p->sopts.precond_tol = o->precond_tol > 0.0 ? o->precond_tol : o->inner_tol;
     p->sopts.mass_tol = o->mass_tol;
     p->sopts.inner_max_iter = o->inner_max_iter;
     p->sopts.mass_max_iter = o->mass_max_iter;
+    p->sopts.coarse_tol = o->coarse_tol;
+    p->sopts.coarse_max_iter = o->coarse_max_iter;
     return AMGH_OK;
 }
 
@@ -221,6 +227,30 @@ static int dense_inverse_of(amgh_problem *p, const DevCsr &a, Dense &out)
     out.n = n;
     TRY(dense_from_csr(p, a, g));
     return dense_spd_inverse(p, g, n, out.inv, info);
+}
+
+// Make level ell-1 the coarsest level of the Hessian preconditioner: with the
+// exact coarse solve, H_{ell-1} is formed densely (Eq. firstorderpractice on
+// that level) and inverted.  Memory of an earlier coarse level stays in the
+// arena until the next setup.
+static int coarse_hessian_setup(amgh_problem *p, int ell)
+{
+    int c = ell - 1;
+    p->Hcoarse = Dense();
+    if (p->aopts.coarse_solve == 0) {
+        if (p->cl[c].Mu.rows > AMGH_DENSE_MAX) return AMGH_ERR_INVALID_ARG;
+        const double *ainv = p->Acoarse.inv;
+        if (c != p->Ls - 1) {
+            TRY(dense_inverse_of(p, p->sl[c].A, p->Aell));
+            ainv = p->Aell.inv;
+        }
+        int nc = p->cl[c].Mu.rows;
+        TRY(p->harena.alloc(&p->Hcoarse.inv, (int64_t)nc * nc));
+        p->Hcoarse.n = nc;
+        TRY(dense_coarse_hessian(p, c, ainv, p->Hcoarse.inv));
+    }
+    p->ell = ell;
+    return AMGH_OK;
 }
 
 static int setup_impl(amgh_problem *p)
@@ -305,21 +335,11 @@ static int setup_impl(amgh_problem *p)
         TRY(ar.alloc(&C.mu_invdiag, C.Mu.rows));
         TRY(diag_inv(p, C.Mu, C.mu_invdiag));
     }
-    // exact coarsest solves
+    // exact coarsest state solve, then the coarsest Hessian level
     TRY(dense_inverse_of(p, p->sl[p->Ls - 1].A, p->Acoarse));
-    p->ell = lmin;
-    if (o.hessian_levels > 0 && o.hessian_levels < p->ell) p->ell = o.hessian_levels;
-    int c = p->ell - 1;
-    const double *ainv = p->Acoarse.inv;
-    if (c != p->Ls - 1) {
-        TRY(dense_inverse_of(p, p->sl[c].A, p->Aell));
-        ainv = p->Aell.inv;
-    }
-    if (p->cl[c].Mu.rows > AMGH_DENSE_MAX) return AMGH_ERR_INVALID_ARG;
-    int nc = p->cl[c].Mu.rows;
-    TRY(ar.alloc(&p->Hcoarse.inv, (int64_t)nc * nc));
-    p->Hcoarse.n = nc;
-    TRY(dense_coarse_hessian(p, c, ainv, p->Hcoarse.inv));
+    int ell = lmin;
+    if (o.hessian_levels > 0 && o.hessian_levels < ell) ell = o.hessian_levels;
+    TRY(coarse_hessian_setup(p, ell));
     smoother_coeffs(p);
     TRY(solver_alloc(p));
     CU(cudaStreamSynchronize(s));
@@ -334,7 +354,7 @@ extern "C" int amgh_amg_setup(amgh_problem *p, const amgh_amg_opts *opts)
     else amgh_amg_opts_default(&o);
     if (o.max_levels < 1 || o.max_levels > AMGH_MAXL || o.smooth_degree < 1 || o.smooth_degree > 16 ||
         o.coarse_max < 1 || !(o.theta >= 0.0) || (o.smoother != 0 && o.smoother != 1) ||
-        o.precision < 0 || o.precision > 2 || o.hessian_levels < 0)
+        o.precision < 0 || o.precision > 2 || o.hessian_levels < 0 || (o.coarse_solve != 0 && o.coarse_solve != 1))
         return AMGH_ERR_INVALID_ARG;
     double t0 = now_s();
     StreamScope ss_(p->stream);
@@ -393,6 +413,8 @@ static void fill_info(amgh_problem *p, amgh_solve_info *info)
     info->mass_iters = p->c_mass;
     info->refinements = p->c_refine;
     info->t_setup_s = p->t_setup;
+    info->hessian_levels = p->ell;
+    info->coarse_iters = p->c_coarse;
 }
 
 extern "C" int amgh_solve(amgh_problem *p, const double *u0, double *u, double *y, const amgh_solve_opts *opts,
@@ -410,6 +432,18 @@ extern "C" int amgh_solve(amgh_problem *p, const double *u0, double *u, double *
     amgh_solve_info loc;
     memset(&loc, 0, sizeof(loc));
     int st = outer_solve(p, u0, u, &o, &loc);
+    int fallbacks = 0;
+    // an indefinite multilevel preconditioner: one Hessian level fewer, restart
+    while (st == AMGH_ERR_INDEFINITE && o.level_fallback && o.precond && p->ell > 2) {
+        if (p->aopts.coarse_solve == 0 && p->cl[p->ell - 2].Mu.rows > AMGH_DENSE_MAX) break;
+        int s2 = coarse_hessian_setup(p, p->ell - 1);
+        if (s2) {
+            st = s2;
+            break;
+        }
+        fallbacks++;
+        st = outer_solve(p, u0, u, &o, &loc);
+    }
     if (st == AMGH_OK && y) {
         CtrlLevel &C = p->cl[0];
         int s2 = spmv(p, C.Myu, u, C.t1, nullptr, 0);
@@ -418,6 +452,7 @@ extern "C" int amgh_solve(amgh_problem *p, const double *u0, double *u, double *
     }
     fill_info(p, &loc);
     loc.status = st;
+    loc.fallbacks = fallbacks;
     if (info) *info = loc;
     int st2 = timer_collect(p);
     if (st == AMGH_OK) st = st2;
@@ -631,17 +666,13 @@ extern "C" int amgh_get_counters(const amgh_problem *p, amgh_solve_info *info)
 {
     if (!p || !info) return AMGH_ERR_INVALID_ARG;
     memset(info, 0, sizeof(*info));
-    info->hessian_applies = p->c_happ;
-    info->inner_iters = p->c_inner;
-    info->mass_iters = p->c_mass;
-    info->refinements = p->c_refine;
-    info->t_setup_s = p->t_setup;
+    fill_info((amgh_problem *)p, info);
     return AMGH_OK;
 }
 
 static void zero_counters(amgh_problem *p)
 {
-    p->c_inner = p->c_mass = p->c_happ = p->c_refine = 0;
+    p->c_inner = p->c_mass = p->c_happ = p->c_refine = p->c_coarse = 0;
     for (int l = 0; l < AMGH_MAXL; l++) p->c_inner_lvl[l] = p->c_mass_lvl[l] = 0;
 }
 

@@ -237,7 +237,7 @@ struct amgh_problem {
     // host mirrors
     CgScal *h_scal = nullptr; // pinned
     // counters
-    int64_t c_inner = 0, c_mass = 0, c_happ = 0, c_refine = 0;
+    int64_t c_inner = 0, c_mass = 0, c_happ = 0, c_refine = 0, c_coarse = 0;
     int64_t c_inner_lvl[AMGH_MAXL], c_mass_lvl[AMGH_MAXL];
     double t_setup = 0.0;
     KernelTimer timer;

@@ -467,11 +467,54 @@ int mlas_R(amgh_problem *p, int j, const double *b, double *out)
     return AMGH_OK;
 }
 
+static int dot_host(amgh_problem *p, RedSlot &red, int n, const double *x, const double *y, double *out);
+
+// Q_{ell-1} b by unpreconditioned CG on H_{ell-1} from u = 0 (Sec. 5.2),
+// stopping at ||r_k|| <= coarse_tol ||b|| on the recursively updated
+// residual; the iterate at the iteration cap is used as it stands.
+static int coarse_cg(amgh_problem *p, int j, const double *b, double *u)
+{
+    CtrlLevel &C = p->cl[j];
+    int n = C.Mu.rows;
+    double *r = C.rq, *pv = C.du, *q = C.hu;
+    CU(cudaMemsetAsync(u, 0, sizeof(double) * n, p->stream));
+    CU(cudaMemcpyAsync(r, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, p->stream));
+    CU(cudaMemcpyAsync(pv, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, p->stream));
+    double ff = 0.0;
+    TRY(dot_host(p, C.red, n, b, b, &ff));
+    if (!(ff == ff)) return AMGH_ERR_NUMERIC;
+    if (ff == 0.0) return AMGH_OK;
+    double nf = sqrt(ff), rz = ff;
+    double tol = p->sopts.coarse_tol;
+    for (int k = 1; k <= p->sopts.coarse_max_iter; k++) {
+        TRY(hessian_level(p, j, pv, q));
+        p->c_coarse += 1;
+        double pq = 0.0;
+        TRY(dot_host(p, C.red, n, pv, q, &pq));
+        if (!(pq > 0.0)) return pq == pq ? AMGH_ERR_INDEFINITE : AMGH_ERR_NUMERIC;
+        double alpha = rz / pq;
+        TRY(vec_axpby(p, n, 1.0, u, alpha, pv, u));
+        TRY(vec_axpby(p, n, 1.0, r, -alpha, q, r));
+        double rr = 0.0;
+        TRY(dot_host(p, C.red, n, r, r, &rr));
+        if (!(rr == rr)) return AMGH_ERR_NUMERIC;
+        if (sqrt(rr) <= tol * nf) break;
+        if (!(rr > 0.0)) return AMGH_ERR_INDEFINITE;
+        double beta = rr / rz;
+        rz = rr;
+        TRY(vec_axpby(p, n, 1.0, r, beta, pv, pv));
+    }
+    return AMGH_OK;
+}
+
 int mlas_Q(amgh_problem *p, int j, const double *b, double *u)
 {
     CtrlLevel &C = p->cl[j];
     int n = C.Mu.rows;
-    if (j == p->ell - 1) return dense_gemv<double>(p, n, p->Hcoarse.inv, b, u, nullptr);
+    if (j == p->ell - 1) {
+        if (p->aopts.coarse_solve == 1) return coarse_cg(p, j, b, u);
+        return dense_gemv<double>(p, n, p->Hcoarse.inv, b, u, nullptr);
+    }
     TRY(mlas_R(p, j, b, u));
     if (j == 0) return AMGH_OK;
     TRY(hessian_level(p, j, u, C.hu));

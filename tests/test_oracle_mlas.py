@@ -85,3 +85,39 @@ def test_mlas_matches_closed_formula():
         bj = rng.standard_normal(L[j]["Mu"].shape[0])
         assert np.linalg.norm(o.precond(bj, level=j) - Q[j] @ bj) <= 1e-9 * np.linalg.norm(Q[j] @ bj)
         assert np.linalg.norm(o.R(bj, level=j) - Rs[j] @ bj) <= 1e-9 * np.linalg.norm(Rs[j] @ bj)
+
+
+def test_coarsest_cg_solves_the_coarse_hessian():
+    """Coarsest level by plain CG (Sec. 5.2): the residual meets the coarse
+    tolerance against a dense numpy H_{ell-1}; a tight tolerance gives H^-1 b."""
+    o = _case(17, 1e-2, 3)
+    o.set_precond_tol(1e-14)
+    ell = o.sizes()["ell"]
+    assert ell == 3
+    H = _levels(o, ell)[ell - 1]["H"]
+    b = np.random.default_rng(5).standard_normal(H.shape[0])
+    o.set_coarse_solve(1, tol=1e-4)
+    x = o.precond(b, level=ell - 1)
+    its = o.set_coarse_solve(1, tol=1e-4)
+    assert its >= 2
+    assert np.linalg.norm(b - H @ x) <= 1.0001e-4 * np.linalg.norm(b)
+    o.set_coarse_solve(1, tol=1e-13)
+    x = o.precond(b, level=ell - 1)
+    xd = np.linalg.solve(H, b)
+    assert np.abs(x - xd).max() <= 1e-10 * np.abs(xd).max()
+    # and the whole W-cycle then equals the one with the dense coarse inverse
+    r = np.random.default_rng(6).standard_normal(o.n)
+    z_cg = o.precond(r)
+    o.set_coarse_solve(0)
+    z_dense = o.precond(r)
+    assert np.abs(z_cg - z_dense).max() <= 1e-9 * np.abs(z_dense).max()
+
+
+def test_solution_does_not_depend_on_the_coarse_solve():
+    w = W.unit_square(33, beta=1e-3, jitter=0.2, cfg=121)
+    o = Oracle(w, coarse_max=16, inner_tol=1e-13, mass_tol=1e-13)
+    assert o.sizes()["ell"] >= 3
+    u_dense, _, _ = o.solve(tol=1e-11)
+    o.set_coarse_solve(1, tol=1e-4)
+    u_cg, _, info = o.solve(tol=1e-11)
+    assert np.abs(u_cg - u_dense).max() <= 1e-8 * np.abs(u_dense).max()
