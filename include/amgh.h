@@ -81,7 +81,8 @@ typedef struct {
  *                  dense inverse of H_{l-1} (the assumption of Sec. 3-4;
  *                  needs at most 4096 control dofs there); 1 = unpreconditioned
  *                  CG on H_{l-1} to the relative residual coarse_tol of the
- *                  solve options (Sec. 5.2 uses 1e-4) */
+ *                  solve options (Sec. 5.2 uses 1e-4); 2 = the dense inverse
+ *                  where H_{l-1} has at most 4096 dofs, else CG */
 typedef struct {
     int max_levels;
     int hessian_levels;
@@ -116,7 +117,8 @@ typedef struct {
  *               info->hessian_levels record it.  The reduction persists for
  *               later solves of this problem until amgh_amg_setup.  With
  *               coarse_solve = 0 a level whose dense H_{l-1} would exceed
- *               4096 dofs ends the fallback with AMGH_ERR_INDEFINITE. */
+ *               4096 dofs ends the fallback with AMGH_ERR_INDEFINITE; with
+ *               coarse_solve = 2 that level is solved by CG instead. */
 typedef struct {
     double tol;
     int max_iter;
@@ -155,6 +157,18 @@ typedef struct {
  * level_fallback 0. */
 void amgh_amg_opts_default(amgh_amg_opts *opts);
 void amgh_solve_opts_default(amgh_solve_opts *opts);
+
+/* A second handle on a set-up problem: the same assembled matrices, AMG
+ * hierarchies and dense coarse inverses, with its own work space, desired
+ * state (a copy of the parent's), graphs, counters and stream (initially
+ * the parent's; give it another with amgh_set_stream).  Solves and applies
+ * on different handles may run at the same time on different streams and
+ * host threads.  The parent must outlive its shared handles and must not be
+ * set up again while they exist; amgh_amg_setup on a shared handle returns
+ * AMGH_ERR_INVALID_ARG.  A level fallback on one handle does not change the
+ * others.  Sharing a shared handle shares its parent.  Release with
+ * amgh_problem_destroy. */
+int amgh_problem_share(amgh_problem *parent, amgh_problem **out);
 
 /* Copy the mesh, per-element kappa (Eq. bilform), beta > 0 and the nodal
  * desired state y_d (n_vertices doubles; on the device iff y_d_on_device) to
@@ -288,28 +302,36 @@ int amgh_kernel_timing(amgh_problem *p, int enable);
 int amgh_kernel_stats(amgh_problem *p, int64_t *launches, double *ms, double *bytes);
 
 /* Batched solves of many independent problems (the batching pattern: many
- * desired states, many meshes of uneven size).  The batch runtime gives every
- * problem its own non-blocking CUDA stream and host worker thread; each worker
- * runs the whole hot path of its problem (AMG setup if not yet done, then
- * one outer CG per desired state, each with the captured CUDA graphs of that
- * problem), so the small, latency-bound problems overlap on the GPU.
- *   probs      nprob problems created by amgh_problem_create on the current
- *              device; the batch borrows them (caller keeps ownership and must
- *              not use them from another thread until amgh_batch_destroy)
+ * desired states, many meshes of uneven size).  Every (problem, desired
+ * state) pair is an independent outer CG.  The batch runtime gives each
+ * problem up to `workers` solve slots (default: one per desired state):
+ * the problem itself and handles from amgh_problem_share, each with its own
+ * non-blocking CUDA stream and host thread, taking every workers-th desired
+ * state of that problem; the small, latency-bound coarse-level work of many
+ * solves then overlaps on the GPU.  Results are identical to solving each
+ * desired state alone on the problem.
+ *   probs      nprob distinct problems created by amgh_problem_create on the
+ *              current device; the batch borrows them (the caller keeps
+ *              ownership and must not use them, nor set them up again, until
+ *              amgh_batch_destroy)
  *   amg        options for problems whose hierarchy is not set up (NULL =
  *              defaults); amgh_batch_setup builds all hierarchies concurrently
+ * amgh_batch_set_workers: slots per problem (0 = one per desired state).
  * amgh_batch_solve:
  *   yd_dev[p]  device array of ncols[p] desired states of problem p, each of
  *              n_vertices(p) doubles, column-major
  *   u_dev[p]   device array of ncols[p] controls of problem p (n(p) doubles each)
  *   opts       solve options shared by all problems (NULL = defaults)
  *   info       nprob entries (may be NULL): counters summed over the
- *              problem's columns, status = first error of the problem
+ *              problem's desired states, t_solve_s the longest slot,
+ *              status = the problem's first error
  * Returns AMGH_OK if every solve converged, else the first error in problem
- * order.  The call returns after all work has completed. */
+ * order; a failing problem does not stop the others.  The call returns
+ * after all work has completed. */
 typedef struct amgh_batch amgh_batch;
 int amgh_batch_create(amgh_problem *const *probs, int nprob, amgh_batch **out);
 int amgh_batch_setup(amgh_batch *b, const amgh_amg_opts *amg);
+int amgh_batch_set_workers(amgh_batch *b, int workers);
 int amgh_batch_solve(amgh_batch *b, const double *const *yd_dev, const int *ncols, double *const *u_dev,
                      const amgh_solve_opts *opts, amgh_solve_info *info);
 void amgh_batch_destroy(amgh_batch *b);

@@ -88,7 +88,8 @@ typedef struct {
     double pc_inner_tol; /* inner solves of the coarse Hessians inside the preconditioner */
     int inner_maxit, mass_maxit;
     long inner_iters, mass_iters, happlies;
-    /* coarsest Hessian level: 0 = dense Cholesky of H_{ell-1}, 1 = plain CG */
+    /* coarsest Hessian level: 0 = dense Cholesky of H_{ell-1}, 1 = plain CG,
+     * 2 = dense up to 4096 control dofs there, else CG */
     int coarse_solve, coarse_maxit;
     double coarse_tol;
     long coarse_iters;
@@ -1004,7 +1005,7 @@ static int mlas_Q(orc_t *o, int j, const double *b, double *u)
 {
     int n = o->Mu[j].rows;
     if (j == o->ell - 1) {
-        if (o->coarse_solve == 1) {
+        if (o->coarse_solve == 1 || (o->coarse_solve == 2 && n > 4096)) {
             long it = 0;
             int st = pcg(o, j, n, op_H, prec_none, b, u, o->coarse_tol, o->coarse_maxit, &it, NULL);
             o->coarse_iters += it;
@@ -1261,7 +1262,7 @@ int orc_set_tols(void *h, double inner_tol, double mass_tol, int inner_maxit, in
 int orc_set_coarse_solve(void *h, int mode, double tol, int maxit, long *iters)
 {
     orc_t *o = h;
-    if ((mode != 0 && mode != 1) || !(tol > 0.0) || maxit < 1) return ORC_INVALID;
+    if (mode < 0 || mode > 2 || !(tol > 0.0) || maxit < 1) return ORC_INVALID;
     o->coarse_solve = mode;
     o->coarse_tol = tol;
     o->coarse_maxit = maxit;

@@ -91,6 +91,8 @@ _SIGS = {
     "amgh_aggregate_noalloc": ([_I, _P, _P, _P, _D, _P, _P, _P], _I),
     "amgh_batch_create": ([_P, _I, _P], _I),
     "amgh_batch_setup": ([_P, _P], _I),
+    "amgh_batch_set_workers": ([_P, _I], _I),
+    "amgh_problem_share": ([_P, _P], _I),
     "amgh_batch_solve": ([_P, _P, _P, _P, _P, _P], _I),
     "amgh_batch_destroy": ([_P], None),
     "amgh_problem_destroy": ([_P], None),
@@ -222,6 +224,17 @@ class Problem:
             self.h = None
 
     # -- setup and options
+    def share(self, stream=None):
+        """A second handle on this problem's matrices and hierarchies with its
+        own work space (amgh_problem_share); keeps this problem alive."""
+        h = C.c_void_p()
+        check(lib().amgh_problem_share(self.h, C.byref(h)), "amgh_problem_share")
+        q = Problem.__new__(Problem)
+        q.h, q.beta, q.dim, q.sizes, q._parent = h, self.beta, self.dim, dict(self.sizes), self
+        if stream is not None:
+            q.set_stream(stream)
+        return q
+
     def amg_setup(self, **kw):
         o = amg_opts(**kw)
         check(lib().amgh_amg_setup(self.h, C.byref(o)), "amgh_amg_setup")
@@ -388,15 +401,17 @@ class Problem:
 
 
 class Batch:
-    """Many independent problems solved concurrently (amgh_batch_*): one CUDA
-    stream and one native worker thread per problem."""
+    """Many independent problems, several desired states each, solved
+    concurrently (amgh_batch_*): per problem up to `workers` slots (0 = one per
+    desired state), each with its own CUDA stream and native host thread."""
 
-    def __init__(self, problems):
+    def __init__(self, problems, workers=0):
         self.problems = list(problems)
         arr = (C.c_void_p * len(self.problems))(*[p.h.value for p in self.problems])
         h = C.c_void_p()
         check(lib().amgh_batch_create(arr, len(self.problems), C.byref(h)), "amgh_batch_create")
         self.h = h
+        check(lib().amgh_batch_set_workers(self.h, int(workers)), "amgh_batch_set_workers")
 
     def setup(self, **kw):
         o = amg_opts(**kw)

@@ -143,6 +143,80 @@ extern "C" int amgh_problem_create(const amgh_mesh *mesh, const double *kappa, d
     return AMGH_OK;
 }
 
+extern "C" int amgh_problem_share(amgh_problem *parent, amgh_problem **out)
+{
+    if (!out) return AMGH_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!parent) return AMGH_ERR_INVALID_ARG;
+    if (!parent->setup_done) return AMGH_ERR_NOT_SETUP;
+    if (parent->parent) parent = (amgh_problem *)parent->parent;
+    amgh_problem *p = new (std::nothrow) amgh_problem();
+    if (!p) return AMGH_ERR_OOM;
+    zero_counters(p);
+    p->parent = parent;
+    p->dim = parent->dim;
+    p->nv = parent->nv;
+    p->ne = parent->ne;
+    p->beta = parent->beta;
+    p->m = parent->m;
+    p->n = parent->n;
+    p->stream = parent->stream;
+    p->df_spmv = parent->df_spmv;
+    p->coords = parent->coords;
+    p->kappa = parent->kappa;
+    p->elems = parent->elems;
+    p->dir = parent->dir;
+    p->state_of_vertex = parent->state_of_vertex;
+    p->vertex_of_state = parent->vertex_of_state;
+    p->Kfull = parent->Kfull;
+    p->Mfull = parent->Mfull;
+    p->aopts = parent->aopts;
+    p->sopts = parent->sopts;
+    p->Ls = parent->Ls;
+    p->Lc = parent->Lc;
+    p->ell = parent->ell;
+    p->coarse_cg = parent->coarse_cg;
+    for (int l = 0; l < AMGH_MAXL; l++) {
+        p->sl[l] = parent->sl[l];
+        p->cl[l] = parent->cl[l];
+        for (CgGraph &g : p->sl[l].graph) g = CgGraph();
+        p->cl[l].mgraph = CgGraph();
+        p->chunk_hint[l] = parent->chunk_hint[l];
+        p->chunk_hint32[l] = parent->chunk_hint32[l];
+        p->mchunk_hint[l] = parent->mchunk_hint[l];
+    }
+    p->Acoarse = parent->Acoarse;
+    p->Aell = parent->Aell;
+    p->Hcoarse = parent->Hcoarse;
+    p->nsteps = parent->nsteps;
+    for (int k = 0; k < 16; k++) {
+        p->cd[k] = parent->cd[k];
+        p->cr[k] = parent->cr[k];
+    }
+    p->t_setup = parent->t_setup;
+    int st = AMGH_OK;
+    {
+        StreamScope ss_(p->stream);
+        if (cudaHostAlloc((void **)&p->h_scal, sizeof(CgScal), cudaHostAllocDefault) != cudaSuccess ||
+            cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
+            st = AMGH_ERR_CUDA;
+        if (!st) st = p->arena.alloc(&p->yd_state, p->m);
+        if (!st && p->m > 0 &&
+            cudaMemcpyAsync(p->yd_state, parent->yd_state, sizeof(double) * p->m, cudaMemcpyDeviceToDevice,
+                            p->stream) != cudaSuccess)
+            st = AMGH_ERR_CUDA;
+        if (!st) st = solver_alloc(p);
+        if (!st && cudaStreamSynchronize(p->stream) != cudaSuccess) st = AMGH_ERR_CUDA;
+    }
+    if (st) {
+        amgh_problem_destroy(p);
+        return st;
+    }
+    p->setup_done = 1;
+    *out = p;
+    return AMGH_OK;
+}
+
 extern "C" int amgh_set_yd(amgh_problem *p, const double *y_d, int on_device)
 {
     if (!p || !y_d) return AMGH_ERR_INVALID_ARG;
@@ -237,7 +311,10 @@ static int coarse_hessian_setup(amgh_problem *p, int ell)
 {
     int c = ell - 1;
     p->Hcoarse = Dense();
-    if (p->aopts.coarse_solve == 0) {
+    int mode = p->aopts.coarse_solve;
+    if (mode == 2) mode = p->cl[c].Mu.rows <= AMGH_DENSE_MAX ? 0 : 1;
+    p->coarse_cg = mode == 1;
+    if (mode == 0) {
         if (p->cl[c].Mu.rows > AMGH_DENSE_MAX) return AMGH_ERR_INVALID_ARG;
         const double *ainv = p->Acoarse.inv;
         if (c != p->Ls - 1) {
@@ -348,13 +425,13 @@ static int setup_impl(amgh_problem *p)
 
 extern "C" int amgh_amg_setup(amgh_problem *p, const amgh_amg_opts *opts)
 {
-    if (!p) return AMGH_ERR_INVALID_ARG;
+    if (!p || p->parent) return AMGH_ERR_INVALID_ARG;
     amgh_amg_opts o;
     if (opts) o = *opts;
     else amgh_amg_opts_default(&o);
     if (o.max_levels < 1 || o.max_levels > AMGH_MAXL || o.smooth_degree < 1 || o.smooth_degree > 16 ||
         o.coarse_max < 1 || !(o.theta >= 0.0) || (o.smoother != 0 && o.smoother != 1) ||
-        o.precision < 0 || o.precision > 2 || o.hessian_levels < 0 || (o.coarse_solve != 0 && o.coarse_solve != 1))
+        o.precision < 0 || o.precision > 2 || o.hessian_levels < 0 || o.coarse_solve < 0 || o.coarse_solve > 2)
         return AMGH_ERR_INVALID_ARG;
     double t0 = now_s();
     StreamScope ss_(p->stream);
@@ -729,5 +806,6 @@ extern "C" void amgh_problem_destroy(amgh_problem *p)
     else cudaDeviceSynchronize();
     if (p->h_scal) cudaFreeHost(p->h_scal);
     if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
+    if (p->wait_ev) cudaEventDestroy(p->wait_ev);
     delete p;
 }

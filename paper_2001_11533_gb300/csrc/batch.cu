@@ -1,5 +1,14 @@
-// batch.cu -- native batch runtime: many independent control problems solved
-// concurrently (one stream and one host worker thread per problem).
+// batch.cu -- native batch runtime: many independent control problems, each
+// with several desired states, solved concurrently.
+//
+// Every (problem, desired state) pair is an independent outer CG.  The batch
+// gives each problem up to `workers` solve slots: slot 0 is the problem
+// itself, the others are handles from amgh_problem_share (same matrices and
+// hierarchies, own work space and graphs).  Each slot has its own
+// non-blocking stream and host thread and takes the columns c = s, s + w,
+// ... of its problem, so the small, latency-bound coarse-level work of many
+// solves overlaps on the GPU.  Host threads wait on blocking-sync events, so
+// more threads than cores do not spin against each other.
 #include <string.h>
 
 #include <new>
@@ -8,61 +17,117 @@
 
 #include "internal.cuh"
 
+struct BatchSlot {
+    amgh_problem *h = nullptr; // the problem (slot 0) or a shared handle
+    cudaStream_t stream = 0;
+    bool owned = false; // shared handle made by the batch
+};
+
 struct amgh_batch {
     std::vector<amgh_problem *> probs;
-    std::vector<cudaStream_t> streams;
     std::vector<void *> old_streams;
+    std::vector<std::vector<BatchSlot>> slots; // [problem][slot]
+    int workers = 0;                           // slots per problem (0 = one per column)
     int device = 0;
 };
+
+static void slot_release(BatchSlot &s)
+{
+    if (s.stream) cudaStreamSynchronize(s.stream);
+    if (s.owned) amgh_problem_destroy(s.h);
+    if (s.stream) cudaStreamDestroy(s.stream);
+    s = BatchSlot();
+}
+
+static int make_slot(amgh_problem *p, bool share, BatchSlot &out)
+{
+    BatchSlot s;
+    if (cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking) != cudaSuccess) return AMGH_ERR_CUDA;
+    if (share) {
+        int st = amgh_problem_share(p, &s.h);
+        if (st) {
+            cudaStreamDestroy(s.stream);
+            return st;
+        }
+        s.owned = true;
+    } else {
+        s.h = p;
+    }
+    amgh_set_stream(s.h, s.stream);
+    if (!s.h->wait_ev && cudaEventCreateWithFlags(&s.h->wait_ev, cudaEventBlockingSync | cudaEventDisableTiming) !=
+                             cudaSuccess) {
+        slot_release(s);
+        return AMGH_ERR_CUDA;
+    }
+    out = s;
+    return AMGH_OK;
+}
+
+// run fn(i) for i in [0, count) on count threads (device made current there)
+template <typename F>
+static void run_all(amgh_batch *b, int count, F fn)
+{
+    std::vector<std::thread> th;
+    th.reserve(count);
+    for (int i = 0; i < count; i++)
+        th.emplace_back([b, i, &fn] {
+            cudaSetDevice(b->device);
+            fn(i);
+        });
+    for (auto &t : th) t.join();
+}
 
 extern "C" int amgh_batch_create(amgh_problem *const *probs, int nprob, amgh_batch **out)
 {
     if (!out || !probs || nprob <= 0) return AMGH_ERR_INVALID_ARG;
     *out = nullptr;
     for (int i = 0; i < nprob; i++)
-        if (!probs[i]) return AMGH_ERR_INVALID_ARG;
+        if (!probs[i] || probs[i]->parent) return AMGH_ERR_INVALID_ARG;
     amgh_batch *b = new (std::nothrow) amgh_batch();
     if (!b) return AMGH_ERR_OOM;
     if (cudaGetDevice(&b->device) != cudaSuccess) {
         delete b;
         return AMGH_ERR_CUDA;
     }
+    b->slots.resize(nprob);
     for (int i = 0; i < nprob; i++) {
-        cudaStream_t s = 0;
-        if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
-            amgh_batch_destroy(b);
-            return AMGH_ERR_CUDA;
-        }
         b->probs.push_back(probs[i]);
-        b->streams.push_back(s);
         b->old_streams.push_back((void *)probs[i]->stream);
-        // work already queued on the old stream must finish before the new one runs
+        // work already queued on the caller's stream must finish first
         cudaStreamSynchronize(probs[i]->stream);
-        amgh_set_stream(probs[i], s);
+        BatchSlot s;
+        int st = make_slot(probs[i], false, s);
+        if (st) {
+            amgh_batch_destroy(b);
+            return st;
+        }
+        b->slots[i].push_back(s);
     }
     *out = b;
     return AMGH_OK;
 }
 
-// run fn(i) for every problem on its own thread (device made current there)
-template <typename F>
-static void run_all(amgh_batch *b, F fn)
+extern "C" int amgh_batch_set_workers(amgh_batch *b, int workers)
 {
-    std::vector<std::thread> th;
-    th.reserve(b->probs.size());
-    for (size_t i = 0; i < b->probs.size(); i++)
-        th.emplace_back([b, i, &fn] {
-            cudaSetDevice(b->device);
-            fn((int)i);
-        });
-    for (auto &t : th) t.join();
+    if (!b || workers < 0) return AMGH_ERR_INVALID_ARG;
+    b->workers = workers;
+    return AMGH_OK;
 }
 
 extern "C" int amgh_batch_setup(amgh_batch *b, const amgh_amg_opts *amg)
 {
     if (!b) return AMGH_ERR_INVALID_ARG;
-    std::vector<int> st(b->probs.size(), AMGH_OK);
-    run_all(b, [&](int i) {
+    int np = (int)b->probs.size();
+    // shared handles hold the old hierarchy: drop them before a new setup
+    for (int i = 0; i < np; i++) {
+        auto &v = b->slots[i];
+        while (!b->probs[i]->setup_done && v.size() > 1) {
+            slot_release(v.back());
+            v.pop_back();
+        }
+    }
+    std::vector<int> st(np, AMGH_OK);
+    run_all(b, np, [&](int i) {
         if (!b->probs[i]->setup_done) st[i] = amgh_amg_setup(b->probs[i], amg);
     });
     for (int s : st)
@@ -74,51 +139,101 @@ extern "C" int amgh_batch_solve(amgh_batch *b, const double *const *yd, const in
                                 const amgh_solve_opts *opts, amgh_solve_info *info)
 {
     if (!b || !yd || !ncols || !u) return AMGH_ERR_INVALID_ARG;
-    size_t np = b->probs.size();
-    for (size_t i = 0; i < np; i++)
+    int np = (int)b->probs.size();
+    for (int i = 0; i < np; i++)
         if (ncols[i] < 0 || (ncols[i] > 0 && (!yd[i] || !u[i]))) return AMGH_ERR_INVALID_ARG;
-    std::vector<int> st(np, AMGH_OK);
-    std::vector<amgh_solve_info> acc(np);
-    run_all(b, [&](int i) {
-        amgh_problem *p = b->probs[i];
-        amgh_solve_info &a = acc[i];
-        memset(&a, 0, sizeof(a));
-        if (!p->setup_done) {
-            st[i] = amgh_amg_setup(p, nullptr);
-            if (st[i]) return;
+    // hierarchies first (concurrently), then the slots each problem needs
+    std::vector<int> pst(np, AMGH_OK);
+    run_all(b, np, [&](int i) {
+        if (!b->probs[i]->setup_done) pst[i] = amgh_amg_setup(b->probs[i], nullptr);
+    });
+    struct Work {
+        int prob, slot, nslot;
+    };
+    std::vector<Work> work;
+    for (int i = 0; i < np; i++) {
+        if (pst[i] || ncols[i] == 0) continue;
+        int want = b->workers > 0 && b->workers < ncols[i] ? b->workers : ncols[i];
+        auto &v = b->slots[i];
+        while ((int)v.size() < want) {
+            BatchSlot s;
+            int st = make_slot(b->probs[i], true, s);
+            if (st) break; // fewer slots: the columns are shared among those made
+            v.push_back(s);
         }
-        for (int c = 0; c < ncols[i]; c++) {
-            int s = amgh_set_yd(p, yd[i] + (int64_t)c * p->nv, 1);
+        int ns = want < (int)v.size() ? want : (int)v.size();
+        for (int k = 0; k < ns; k++) work.push_back({i, k, ns});
+    }
+    std::vector<amgh_solve_info> acc(work.size());
+    std::vector<int> wst(work.size(), AMGH_OK);
+    run_all(b, (int)work.size(), [&](int wi) {
+        const Work &w = work[wi];
+        amgh_problem *p = b->slots[w.prob][w.slot].h;
+        amgh_solve_info &a = acc[wi];
+        memset(&a, 0, sizeof(a));
+        for (int c = w.slot; c < ncols[w.prob]; c += w.nslot) {
+            int s = amgh_set_yd(p, yd[w.prob] + (int64_t)c * p->nv, 1);
             amgh_solve_info one;
             memset(&one, 0, sizeof(one));
-            if (s == AMGH_OK) s = amgh_solve(p, nullptr, u[i] + (int64_t)c * p->n, nullptr, opts, &one);
+            if (s == AMGH_OK) s = amgh_solve(p, nullptr, u[w.prob] + (int64_t)c * p->n, nullptr, opts, &one);
             a.outer_iters += one.outer_iters;
             a.hessian_applies += one.hessian_applies;
             a.inner_iters += one.inner_iters;
             a.mass_iters += one.mass_iters;
             a.refinements += one.refinements;
+            a.coarse_iters += one.coarse_iters;
+            a.fallbacks += one.fallbacks;
             a.t_solve_s += one.t_solve_s;
             a.final_relres = one.final_relres > a.final_relres ? one.final_relres : a.final_relres;
-            a.t_setup_s = one.t_setup_s;
-            if (s != AMGH_OK && st[i] == AMGH_OK) st[i] = s;
+            a.hessian_levels = one.hessian_levels;
+            if (s != AMGH_OK && wst[wi] == AMGH_OK) wst[wi] = s;
         }
-        a.status = st[i];
     });
+    // per problem: counters summed over its slots, status = its first error
+    std::vector<amgh_solve_info> out(np);
+    for (int i = 0; i < np; i++) {
+        memset(&out[i], 0, sizeof(out[i]));
+        out[i].status = pst[i];
+        out[i].t_setup_s = b->probs[i]->t_setup;
+    }
+    for (size_t wi = 0; wi < work.size(); wi++) {
+        amgh_solve_info &o = out[work[wi].prob];
+        const amgh_solve_info &a = acc[wi];
+        o.outer_iters += a.outer_iters;
+        o.hessian_applies += a.hessian_applies;
+        o.inner_iters += a.inner_iters;
+        o.mass_iters += a.mass_iters;
+        o.refinements += a.refinements;
+        o.coarse_iters += a.coarse_iters;
+        o.fallbacks += a.fallbacks;
+        o.t_solve_s = a.t_solve_s > o.t_solve_s ? a.t_solve_s : o.t_solve_s;
+        o.final_relres = a.final_relres > o.final_relres ? a.final_relres : o.final_relres;
+        if (work[wi].slot == 0 || a.hessian_levels < o.hessian_levels) o.hessian_levels = a.hessian_levels;
+        if (wst[wi] != AMGH_OK && o.status == AMGH_OK) o.status = wst[wi];
+    }
     if (info)
-        for (size_t i = 0; i < np; i++) info[i] = acc[i];
-    for (int s : st)
-        if (s != AMGH_OK) return s;
+        for (int i = 0; i < np; i++) info[i] = out[i];
+    for (int i = 0; i < np; i++)
+        if (out[i].status != AMGH_OK) return out[i].status;
     return AMGH_OK;
 }
 
 extern "C" void amgh_batch_destroy(amgh_batch *b)
 {
     if (!b) return;
-    for (size_t i = 0; i < b->probs.size(); i++) {
-        cudaStreamSynchronize(b->streams[i]);
-        amgh_set_stream(b->probs[i], b->old_streams[i]);
+    for (size_t i = 0; i < b->slots.size(); i++) {
+        auto &v = b->slots[i];
+        for (size_t k = v.size(); k-- > 0;) {
+            BatchSlot &s = v[k];
+            if (!s.owned && s.h) {
+                cudaStreamSynchronize(s.stream);
+                amgh_set_stream(s.h, b->old_streams[i]);
+                if (s.h->wait_ev) cudaEventDestroy(s.h->wait_ev);
+                s.h->wait_ev = nullptr;
+                s.h = nullptr;
+            }
+            slot_release(s);
+        }
     }
-    for (cudaStream_t s : b->streams)
-        if (s) cudaStreamDestroy(s);
     delete b;
 }

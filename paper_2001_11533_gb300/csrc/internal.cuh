@@ -200,6 +200,11 @@ struct KernelTimer {
 };
 
 struct amgh_problem {
+    // set on a handle made by amgh_problem_share: matrices, hierarchies and
+    // dense coarse inverses belong to the parent; this handle owns only its
+    // work space, desired state, streams, graphs and counters
+    const amgh_problem *parent = nullptr;
+    cudaEvent_t wait_ev = nullptr; // blocking-sync event for host waits (else spin)
     int dim = 0;
     int64_t nv = 0, ne = 0;
     double beta = 0.0;
@@ -221,6 +226,7 @@ struct amgh_problem {
     amgh_solve_opts sopts;
     int setup_done = 0;
     int Ls = 0, Lc = 0, ell = 0;
+    int coarse_cg = 0; // Q_{ell-1} by CG on H_{ell-1} (else the dense inverse)
     StateLevel sl[AMGH_MAXL];
     CtrlLevel cl[AMGH_MAXL];
     Dense Acoarse;  // inverse of A[Ls-1]

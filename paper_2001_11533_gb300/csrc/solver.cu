@@ -25,8 +25,15 @@ int outer_pq(amgh_problem *p, RedSlot &red, int n, const double *pv, const doubl
 int outer_rz(amgh_problem *p, RedSlot &red, int n, const double *r, const double *z, double *pv, CgScal *sc,
              int first);
 
+// Wait for the problem's stream: a spin in cudaStreamSynchronize, or a sleep
+// on a blocking-sync event when many host threads share few cores.
 int sync_stream(amgh_problem *p)
 {
+    if (p->wait_ev) {
+        CU(cudaEventRecord(p->wait_ev, p->stream));
+        CU(cudaEventSynchronize(p->wait_ev));
+        return AMGH_OK;
+    }
     CU(cudaStreamSynchronize(p->stream));
     return AMGH_OK;
 }
@@ -34,7 +41,7 @@ int sync_stream(amgh_problem *p)
 static int read_scal(amgh_problem *p, const CgScal *sc, CgScal *out)
 {
     CU(cudaMemcpyAsync(p->h_scal, sc, sizeof(CgScal), cudaMemcpyDeviceToHost, p->stream));
-    CU(cudaStreamSynchronize(p->stream));
+    TRY(sync_stream(p));
     *out = *p->h_scal;
     return AMGH_OK;
 }
@@ -512,7 +519,7 @@ int mlas_Q(amgh_problem *p, int j, const double *b, double *u)
     CtrlLevel &C = p->cl[j];
     int n = C.Mu.rows;
     if (j == p->ell - 1) {
-        if (p->aopts.coarse_solve == 1) return coarse_cg(p, j, b, u);
+        if (p->coarse_cg) return coarse_cg(p, j, b, u);
         return dense_gemv<double>(p, n, p->Hcoarse.inv, b, u, nullptr);
     }
     TRY(mlas_R(p, j, b, u));
@@ -546,7 +553,7 @@ static int dot_host(amgh_problem *p, RedSlot &red, int n, const double *x, const
 {
     TRY(vec_dot(p, red, n, x, y, p->dscratch));
     CU(cudaMemcpyAsync(out, p->dscratch, sizeof(double), cudaMemcpyDeviceToHost, p->stream));
-    CU(cudaStreamSynchronize(p->stream));
+    TRY(sync_stream(p));
     return AMGH_OK;
 }
 

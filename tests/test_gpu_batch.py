@@ -36,6 +36,44 @@ def test_batch_equals_single_problem_solves():
             assert np.array_equal(uc.cpu().numpy(), u[c].cpu().numpy())
 
 
+def test_workers_do_not_change_results():
+    from paper_2001_11533_gb300 import amgh
+    ws = _small_batch()[:2]
+    res = []
+    for workers in (0, 1, 2):
+        probs = [amgh.Problem.from_workload(w) for w in ws]
+        batch = amgh.Batch(probs, workers=workers).setup(coarse_max=600)
+        us, infos, st = batch.solve([_cuda(w.y_d) for w in ws], tol=1e-10)
+        batch.close()
+        assert st == 0
+        res.append([u.cpu().numpy() for u in us])
+    for r in res[1:]:
+        for a, b in zip(res[0], r):
+            assert np.array_equal(a, b)
+
+
+def test_shared_handle():
+    from paper_2001_11533_gb300 import amgh
+    w = _small_batch()[0]
+    p = amgh.Problem.from_workload(w)
+    with pytest.raises(amgh.AmghError):
+        p.share()                                   # not set up yet
+    p.amg_setup(coarse_max=600)
+    q = p.share()
+    with pytest.raises(amgh.AmghError):
+        q.amg_setup()                               # hierarchy belongs to p
+    for h in (p, q):
+        h.set_yd(_cuda(w.y_d[1]))
+    up, _, ip = p.solve(tol=1e-10)
+    uq, _, iq = q.solve(tol=1e-10)
+    assert np.array_equal(up.cpu().numpy(), uq.cpu().numpy())
+    assert ip["outer_iters"] == iq["outer_iters"]
+    q.close()
+    # the parent is untouched by its shared handle's life
+    up2, _, _ = p.solve(tol=1e-10)
+    assert np.array_equal(up.cpu().numpy(), up2.cpu().numpy())
+
+
 def test_batch_isolates_a_failing_problem():
     from paper_2001_11533_gb300 import amgh
     ws = _small_batch()
