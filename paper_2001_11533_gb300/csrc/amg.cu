@@ -439,9 +439,12 @@ int amg_prolongator(amgh_problem *p, Arena &ar, const DevCsr &a, const int *agg,
 #define WARPS_PER_BLOCK 4
 #define WARP_PATH_MAX_ROWS 65536
 
+// path of row i: 0 = one thread with a global hash table, 1 = one warp with a
+// shared hash table (u <= WARP_TS / 2), 2 = one block with a dense shared
+// accumulator over all columns (long rows of products with few columns)
 __global__ void k_gemm_ub(int n, const int *__restrict__ arp, const int *__restrict__ aci,
                           const int *__restrict__ brp, long long *__restrict__ ub, int *__restrict__ small,
-                          int use_warp)
+                          int *__restrict__ big, int use_warp, int use_dense)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -450,11 +453,87 @@ __global__ void k_gemm_ub(int n, const int *__restrict__ arp, const int *__restr
         int j = aci[k];
         u += brp[j + 1] - brp[j];
     }
-    int sm = use_warp && u <= WARP_TS / 2;
-    small[i] = sm;
+    int path = use_warp && u <= WARP_TS / 2 ? 1 : (use_dense && u > WARP_TS / 2 ? 2 : 0);
+    small[i] = path;
+    big[i] = path == 2;
     long long t = 2;
     while (t < 2 * u) t <<= 1;
-    ub[i] = (u > 0 && !sm) ? t : 0;
+    ub[i] = (u > 0 && path == 0) ? t : 0;
+}
+
+__global__ void k_list(int n, const int *__restrict__ flag, const int *__restrict__ pos, int *__restrict__ list)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n && flag[i]) list[pos[i]] = i;
+}
+
+// dense-accumulator path: one block per listed row.  The row's products are
+// taken one entry a_ik at a time (a barrier between entries) with the
+// entries of row k of B spread over the threads; every column J occurs once
+// in a row of B, so each accumulator receives its products in exactly the
+// sequential order.  phase 0 counts the row's columns, phase 1 writes them
+// in ascending order.
+#define DENSE_ROW_TPB 256
+#define DENSE_ROW_MAX_COLS 16384
+__global__ void __launch_bounds__(DENSE_ROW_TPB) k_gemm_dense(int nlist, const int *__restrict__ list, int cols,
+                                                              const int *__restrict__ arp, const int *__restrict__ aci,
+                                                              const double *__restrict__ av,
+                                                              const int *__restrict__ brp,
+                                                              const int *__restrict__ bci,
+                                                              const double *__restrict__ bv, int phase,
+                                                              int *__restrict__ cnt, const int *__restrict__ crp,
+                                                              int *__restrict__ cci, double *__restrict__ cv)
+{
+    extern __shared__ unsigned char smem_raw[];
+    __shared__ int wsum[DENSE_ROW_TPB / 32];
+    double *acc = (double *)smem_raw;
+    unsigned char *seen = smem_raw + (size_t)cols * sizeof(double);
+    int i = list[blockIdx.x];
+    int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    for (int J = t; J < cols; J += DENSE_ROW_TPB) {
+        acc[J] = 0.0;
+        seen[J] = 0;
+    }
+    __syncthreads();
+    for (int k = arp[i]; k < arp[i + 1]; k++) {
+        int j = aci[k];
+        double aij = av[k];
+        for (int q = brp[j] + t; q < brp[j + 1]; q += DENSE_ROW_TPB) {
+            int J = bci[q];
+            acc[J] = __dadd_rn(acc[J], __dmul_rn(aij, bv[q]));
+            seen[J] = 1;
+        }
+        __syncthreads();
+    }
+    // each thread owns a contiguous run of columns; a block scan of the runs'
+    // counts gives every column its position in the sorted row
+    int per = (cols + DENSE_ROW_TPB - 1) / DENSE_ROW_TPB;
+    int beg = t * per, end = min(beg + per, cols);
+    int c = 0;
+    for (int J = beg; J < end; J++) c += seen[J];
+    int incl = c;
+    for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) wsum[w] = incl;
+    __syncthreads();
+    int before = 0, total = 0;
+    for (int q = 0; q < DENSE_ROW_TPB / 32; q++) {
+        if (q < w) before += wsum[q];
+        total += wsum[q];
+    }
+    if (phase == 0) {
+        if (t == 0) cnt[i] = total;
+        return;
+    }
+    int pos = crp[i] + before + incl - c;
+    for (int J = beg; J < end; J++)
+        if (seen[J]) {
+            cci[pos] = J;
+            cv[pos] = acc[J];
+            pos++;
+        }
 }
 
 __device__ __forceinline__ unsigned hslot(int key, unsigned mask) { return ((unsigned)key * 2654435761u) & mask; }
@@ -544,7 +623,7 @@ __global__ void k_gemm_warp(int n, const int *__restrict__ arp, const int *__res
     double *vals = (double *)((int *)smem_raw + WARPS_PER_BLOCK * WARP_TS) + w * WARP_TS;
     double *stage = (double *)((int *)smem_raw + WARPS_PER_BLOCK * WARP_TS) + WARPS_PER_BLOCK * WARP_TS + w * 32;
     int i = blockIdx.x * WARPS_PER_BLOCK + w;
-    if (i >= n || !small[i]) return; // warp-uniform
+    if (i >= n || small[i] != 1) return; // warp-uniform
     // table of 2^ceil(log2(2u)) slots (u = candidate count of the row)
     int u = 0;
     for (int k = arp[i] + lane; k < arp[i + 1]; k += 32) {
@@ -631,15 +710,28 @@ int spgemm(amgh_problem *p, Arena &ar, const DevCsr &a, const DevCsr &b, DevCsr 
     CU(cudaFuncSetAttribute(k_gemm_warp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)warp_smem()));
     Scratch sc;
     long long *ub = nullptr, *toff = nullptr;
-    int *cnt = nullptr, *tkey = nullptr, *small = nullptr;
+    int *cnt = nullptr, *tkey = nullptr, *small = nullptr, *big = nullptr, *bpos = nullptr, *blist = nullptr;
     double *tval = nullptr;
     TRY(sc.alloc(&ub, n + 1));
     TRY(sc.alloc(&toff, n + 1));
     TRY(sc.alloc(&cnt, n + 1));
     TRY(sc.alloc(&small, n + 1));
+    TRY(sc.alloc(&big, n + 1));
+    TRY(sc.alloc(&bpos, n + 1));
     int nb = ceil_div(n, 128), nw = ceil_div(n, WARPS_PER_BLOCK);
-    k_gemm_ub<<<nb, 128, 0, s>>>(n, a.rp, a.ci, b.rp, ub, small, n <= WARP_PATH_MAX_ROWS);
+    int use_dense = b.cols <= DENSE_ROW_MAX_COLS;
+    size_t dsmem = (size_t)b.cols * (sizeof(double) + 1);
+    if (use_dense && dsmem > 48 * 1024)
+        CU(cudaFuncSetAttribute(k_gemm_dense, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsmem));
+    k_gemm_ub<<<nb, 128, 0, s>>>(n, a.rp, a.ci, b.rp, ub, small, big, n <= WARP_PATH_MAX_ROWS, use_dense);
     LAUNCH_CHECK();
+    int nbig = 0;
+    TRY(exclusive_scan<int>(big, bpos, n, s, &nbig));
+    if (nbig > 0) {
+        TRY(sc.alloc(&blist, nbig));
+        k_list<<<ceil_div(n, 256), 256, 0, s>>>(n, big, bpos, blist);
+        LAUNCH_CHECK();
+    }
     long long tot = 0;
     TRY(exclusive_scan<long long>(ub, toff, n, s, &tot));
     TRY(sc.alloc(&tkey, tot));
@@ -650,6 +742,11 @@ int spgemm(amgh_problem *p, Arena &ar, const DevCsr &a, const DevCsr &b, DevCsr 
     k_gemm_warp<<<nw, 32 * WARPS_PER_BLOCK, warp_smem(), s>>>(n, a.rp, a.ci, a.v, b.rp, b.ci, b.v, small, 0, cnt,
                                                               nullptr, nullptr, nullptr);
     LAUNCH_CHECK();
+    if (nbig > 0) {
+        k_gemm_dense<<<nbig, DENSE_ROW_TPB, dsmem, s>>>(nbig, blist, b.cols, a.rp, a.ci, a.v, b.rp, b.ci, b.v, 0,
+                                                          cnt, nullptr, nullptr, nullptr);
+        LAUNCH_CHECK();
+    }
     TRY(ar.alloc(&c.rp, n + 1));
     int nnz = 0;
     TRY(exclusive_scan<int>(cnt, c.rp, n, s, &nnz));
@@ -661,6 +758,11 @@ int spgemm(amgh_problem *p, Arena &ar, const DevCsr &a, const DevCsr &b, DevCsr 
     k_gemm_warp<<<nw, 32 * WARPS_PER_BLOCK, warp_smem(), s>>>(n, a.rp, a.ci, a.v, b.rp, b.ci, b.v, small, 1,
                                                               nullptr, c.rp, c.ci, c.v);
     LAUNCH_CHECK();
+    if (nbig > 0) {
+        k_gemm_dense<<<nbig, DENSE_ROW_TPB, dsmem, s>>>(nbig, blist, b.cols, a.rp, a.ci, a.v, b.rp, b.ci, b.v, 1,
+                                                          nullptr, c.rp, c.ci, c.v);
+        LAUNCH_CHECK();
+    }
     CU(cudaStreamSynchronize(s));
     return AMGH_OK;
 }

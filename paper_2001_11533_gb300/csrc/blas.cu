@@ -620,27 +620,31 @@ int vec_fill(amgh_problem *p, int n, double v, double *x)
 // Inner CG of precision mode 2 with every vector (x, r, p, q, s) held as
 // double-float: the FP64-sized buffer of n doubles is used as two FP32 arrays,
 // hi = [0, n) and lo = [n, 2n).  All per-element arithmetic stays on the FP32
-// pipe; the FP32 V-cycle reads r's hi half directly.  Reductions sum in
-// double-float inside each warp and in FP64 only across warps and blocks.
+// pipe; the FP32 V-cycle reads r's hi half directly.  Reductions stay in
+// double-float across lanes, warps and blocks; only the final sums become FP64
+// for the CG scalars.
 
 template <int NV>
 __device__ bool reduce_df_last_block(const DF (&val)[NV], double *partials, unsigned *ticket, double (&tot)[NV])
 {
-    __shared__ double shw[NV][32];
+    // the partial sums stay double-float (two FP32 halves in each 8-byte
+    // slot): on GB300 every FP64 instruction costs ~64 FP32 issue slots
+    __shared__ DF shw[NV][32];
     __shared__ bool is_last;
+    float2 *part = reinterpret_cast<float2 *>(partials);
     int nb = gridDim.x, w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
 #pragma unroll
     for (int q = 0; q < NV; q++) {
         DF s = df_warp_sum(val[q]);
-        if (l == 0) shw[q][w] = df_to_double(s);
+        if (l == 0) shw[q][w] = s;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
 #pragma unroll
         for (int q = 0; q < NV; q++) {
-            double t = 0.0;
-            for (int k = 0; k < nw; k++) t += shw[q][k];
-            partials[q * nb + blockIdx.x] = t;
+            DF t = shw[q][0];
+            for (int k = 1; k < nw; k++) t = df_add2(t, shw[q][k]);
+            part[q * nb + blockIdx.x] = make_float2(t.hi, t.lo);
         }
         __threadfence();
         unsigned tk = atomicAdd(ticket, 1u);
@@ -651,18 +655,21 @@ __device__ bool reduce_df_last_block(const DF (&val)[NV], double *partials, unsi
     __threadfence();
 #pragma unroll
     for (int q = 0; q < NV; q++) {
-        double s = 0.0;
-        for (int b = threadIdx.x; b < nb; b += blockDim.x) s += ((volatile double *)partials)[q * nb + b];
-        s = warp_sum(s);
+        DF s = {0.f, 0.f};
+        for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+            float2 v = __ldcg(&part[q * nb + b]); // L2: written by other blocks
+            s = df_add2(s, DF{v.x, v.y});
+        }
+        s = df_warp_sum(s);
         if (l == 0) shw[q][w] = s;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
 #pragma unroll
         for (int q = 0; q < NV; q++) {
-            double t = 0.0;
-            for (int k = 0; k < nw; k++) t += shw[q][k];
-            tot[q] = t;
+            DF t = shw[q][0];
+            for (int k = 1; k < nw; k++) t = df_add2(t, shw[q][k]);
+            tot[q] = df_to_double(t);
         }
         *ticket = 0u;
     }
@@ -707,14 +714,20 @@ __global__ void k_df_spmv(MatView<float> A, const float *__restrict__ lo, const 
 {
     SKIP_DONE();
     int row = my_row<TPR>();
+    bool lead = row < A.rows && row_leader<TPR>();
+    float zr = 0.f, rhr = 0.f, rlr = 0.f;
+    if (lead) {
+        zr = z[row];
+        rhr = rh[row];
+        rlr = rl[row];
+    }
     DF v = row_sum_dfv<float, TPR>(A, lo, row, z);
     DF a[2] = {{0.f, 0.f}, {0.f, 0.f}};
     double tot[2];
-    if (row < A.rows && row_leader<TPR>()) {
+    if (lead) {
         sh[row] = v.hi;
         sl[row] = v.lo;
-        float zr = z[row];
-        a[0] = df_mulf(DF{rh[row], rl[row]}, zr);
+        a[0] = df_mulf(DF{rhr, rlr}, zr);
         a[1] = df_mulf(v, zr);
     }
     if (reduce_df_last_block<2>(a, partials, ticket, tot)) cg_finalize(F_CG2, tot, sc, nullptr);

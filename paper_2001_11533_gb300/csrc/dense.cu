@@ -168,6 +168,58 @@ static int gemm(amgh_problem *p, int m, int n, int k, const double *A, int trans
     return AMGH_OK;
 }
 
+// C = W^T W for lower-triangular W (so C is symmetric): upper tiles only, the
+// sum over k starting where both columns of W can be non-zero; then mirrored
+__global__ void k_wtw_upper(int n, const double *__restrict__ W, double *__restrict__ C)
+{
+    __shared__ double As[TILE][TILE + 1], Bs[TILE][TILE + 1];
+    if (blockIdx.y > blockIdx.x) return; // block-uniform: lower tiles come from the mirror
+    int row = blockIdx.y * TILE + threadIdx.y, col = blockIdx.x * TILE + threadIdx.x;
+    double acc = 0.0;
+    // W[k][row] = 0 for k < row and W[k][col] = 0 for k < col
+    for (int k0 = blockIdx.x * TILE; k0 < n; k0 += TILE) {
+        int ka = k0 + threadIdx.x, kb = k0 + threadIdx.y;
+        As[threadIdx.y][threadIdx.x] = row < n && ka < n ? W[(int64_t)ka * n + row] : 0.0;
+        Bs[threadIdx.y][threadIdx.x] = kb < n && col < n ? W[(int64_t)kb * n + col] : 0.0;
+        __syncthreads();
+#pragma unroll
+        for (int t = 0; t < TILE; t++) acc += As[threadIdx.y][t] * Bs[t][threadIdx.x];
+        __syncthreads();
+    }
+    if (row < n && col < n && col >= row) C[(int64_t)row * n + col] = acc;
+}
+
+__global__ void k_mirror_lower(int n, double *__restrict__ C)
+{
+    int i = blockIdx.y * blockDim.y + threadIdx.y, j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n && j < i) C[(int64_t)i * n + j] = C[(int64_t)j * n + i];
+}
+
+// C = S op(D): S sparse (CSR, rows x inner), D dense row-major with leading
+// dimension ld; transD = 0: D is inner x cols, 1: D is cols x inner (used as D^T)
+__global__ void k_csr_dense(int rows, int cols, const int *__restrict__ rp, const int *__restrict__ ci,
+                            const double *__restrict__ v, const double *__restrict__ D, int ld, int transD,
+                            double *__restrict__ C)
+{
+    int j = blockIdx.x * blockDim.x + threadIdx.x, i = blockIdx.y;
+    if (j >= cols) return;
+    double acc = 0.0;
+    for (int k = rp[i]; k < rp[i + 1]; k++) {
+        int l = ci[k];
+        acc += v[k] * (transD ? D[(int64_t)j * ld + l] : D[(int64_t)l * ld + j]);
+    }
+    C[(int64_t)i * cols + j] = acc;
+}
+
+static int csr_dense(amgh_problem *p, const DevCsr &a, const double *D, int ld, int cols, int transD, double *C)
+{
+    if (a.rows == 0 || cols == 0) return AMGH_OK;
+    k_csr_dense<<<dim3(ceil_div(cols, 128), a.rows), 128, 0, p->stream>>>(a.rows, cols, a.rp, a.ci, a.v, D, ld,
+                                                                          transD, C);
+    LAUNCH_CHECK();
+    return AMGH_OK;
+}
+
 int dense_spd_inverse(amgh_problem *p, double *g, int n, double *inv, int *info_dev)
 {
     cudaStream_t s = p->stream;
@@ -196,34 +248,34 @@ int dense_spd_inverse(amgh_problem *p, double *g, int n, double *inv, int *info_
     if (shm > 48 * 1024) CU(cudaFuncSetAttribute(k_trinv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
     k_trinv<<<ceil_div(n, TRINV_WARPS), 32 * TRINV_WARPS, shm, s>>>(n, g, W);
     LAUNCH_CHECK();
-    TRY(gemm(p, n, n, n, W, 1, W, 0.0, nullptr, inv));
+    int tiles = ceil_div(n, TILE);
+    k_wtw_upper<<<dim3(tiles, tiles), dim3(TILE, TILE), 0, s>>>(n, W, inv);
+    LAUNCH_CHECK();
+    k_mirror_lower<<<dim3(tiles, tiles), dim3(TILE, TILE), 0, s>>>(n, inv);
+    LAUNCH_CHECK();
     CU(cudaStreamSynchronize(s));
     return AMGH_OK;
 }
 
-// H_c on Hessian level c and its inverse (hinv, n_c x n_c)
+// H_c on Hessian level c and its inverse (hinv, n_c x n_c).  With W =
+// M_yu^T A_c^-1 (sparse times dense) and U = M_y W^T (sparse times dense),
+// H_c = W U + beta M_u: one dense product instead of four.
 int dense_coarse_hessian(amgh_problem *p, int c, const double *ainv, double *hinv)
 {
     StateLevel &S = p->sl[c];
     CtrlLevel &C = p->cl[c];
     int m = S.A.rows, n = C.Mu.rows;
     Scratch sc;
-    double *Myu, *My, *Mu, *X, *Y, *Z, *H;
+    double *W, *U, *Mu, *H;
     int *info;
-    TRY(sc.alloc(&Myu, (int64_t)m * n));
-    TRY(sc.alloc(&My, (int64_t)m * m));
+    TRY(sc.alloc(&W, (int64_t)n * m));
+    TRY(sc.alloc(&U, (int64_t)m * n));
     TRY(sc.alloc(&Mu, (int64_t)n * n));
-    TRY(sc.alloc(&X, (int64_t)m * n));
-    TRY(sc.alloc(&Y, (int64_t)m * n));
-    TRY(sc.alloc(&Z, (int64_t)m * n));
     TRY(sc.alloc(&H, (int64_t)n * n));
     TRY(sc.alloc(&info, 1));
-    TRY(dense_from_csr(p, C.Myu, Myu));
-    TRY(dense_from_csr(p, S.My, My));
     TRY(dense_from_csr(p, C.Mu, Mu));
-    TRY(gemm(p, m, n, m, ainv, 0, Myu, 0.0, nullptr, X));        // X = A^-1 M_yu
-    TRY(gemm(p, m, n, m, My, 0, X, 0.0, nullptr, Y));            // Y = M_y X
-    TRY(gemm(p, m, n, m, ainv, 0, Y, 0.0, nullptr, Z));          // Z = A^-1 Y
-    TRY(gemm(p, n, n, m, Myu, 1, Z, p->beta, Mu, H));            // H = M_yu^T Z + beta M_u
+    TRY(csr_dense(p, C.Myut, ainv, m, m, 0, W)); // W = M_yu^T A^-1   (n x m)
+    TRY(csr_dense(p, S.My, W, m, n, 1, U));      // U = M_y W^T       (m x n)
+    TRY(gemm(p, n, n, m, W, 0, U, p->beta, Mu, H)); // H = W U + beta M_u
     return dense_spd_inverse(p, H, n, hinv, info);
 }

@@ -110,6 +110,10 @@ struct DevCsr {
     // low FP32 parts, v - (double)(float)v, in the same layout as the solve-phase
     // values (SELL or CSR): with the FP32 values they carry ~48 bits of v
     float *lo32 = nullptr;
+    // most entries one lane of the applying kernels visits in a row (SELL:
+    // the widest slice; CSR: ceil(longest row / tpr)); rows up to
+    // ROW_UNROLL per lane are read with every load issued up front
+    int wmax = 1 << 30;
     // SELL-32
     int nslices = 0, sell_nnz = 0;
     int *sl_ptr = nullptr, *sl_ci = nullptr;

@@ -165,6 +165,30 @@ __global__ void k_to_f32(int64_t n, const double *__restrict__ a, float *__restr
     if (i < n) b[i] = (float)a[i];
 }
 
+__global__ void k_row_max(int rows, const int *__restrict__ rp, int *__restrict__ out)
+{
+    int r = blockIdx.x * blockDim.x + threadIdx.x;
+    int len = r < rows ? rp[r + 1] - rp[r] : 0;
+    for (int o = 16; o > 0; o >>= 1) len = max(len, __shfl_xor_sync(0xffffffffu, len, o));
+    if ((threadIdx.x & 31) == 0 && len > 0) atomicMax(out, len);
+}
+
+// longest row of a (host value; setup only)
+static int max_row_length(const DevCsr &a, cudaStream_t s, int *out)
+{
+    *out = 0;
+    if (a.rows == 0) return AMGH_OK;
+    Scratch sc;
+    int *d = nullptr;
+    TRY(sc.alloc(&d, 1));
+    CU(cudaMemsetAsync(d, 0, sizeof(int), s));
+    k_row_max<<<ceil_div(a.rows, 256), 256, 0, s>>>(a.rows, a.rp, d);
+    LAUNCH_CHECK();
+    CU(cudaMemcpyAsync(out, d, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
+    return AMGH_OK;
+}
+
 int prepare_operator(Arena &ar, DevCsr &a, cudaStream_t s, int force_tpr)
 {
     double avg = a.rows > 0 ? (double)a.nnz / a.rows : 0.0;
@@ -175,6 +199,10 @@ int prepare_operator(Arena &ar, DevCsr &a, cudaStream_t s, int force_tpr)
     else if (avg > 24.0) tpr = 8;
     else if (avg > 12.0) tpr = 4;
     a.tpr = tpr;
+    int longest = 0;
+    TRY(max_row_length(a, s, &longest));
+    // SELL pads every row of a slice to the slice's longest row
+    a.wmax = tpr == 1 ? longest : ceil_div(longest, tpr);
     if (tpr == 1) return csr_to_sell(ar, a, 1, s);
     TRY(ar.alloc(&a.v32, a.nnz));
     if (a.nnz > 0) {
@@ -240,12 +268,21 @@ __global__ void k_cheb_step(MatView<T> A, const T *__restrict__ invd, const T *_
 {
     SKIP_RETURN();
     int r = my_row<TPR>();
+    bool lead = r < A.rows && row_leader<TPR>();
+    // row-local operands first, so their loads overlap the row's
+    T br = 0, ir = 0, dr = 0, xr = 0;
+    if (lead) {
+        br = b[r];
+        ir = invd[r];
+        dr = d[r];
+        xr = x[r];
+    }
     T ax = row_sum<T, TPR>(A, r, [&](int c) { return __ldg(&x[c]); });
-    if (r < A.rows && row_leader<TPR>()) {
-        T res = (b[r] - ax) * invd[r];
-        T dn = cdv * d[r] + crv * res;
+    if (lead) {
+        T res = (br - ax) * ir;
+        T dn = cdv * dr + crv * res;
         d[r] = dn;
-        xn[r] = x[r] + dn;
+        xn[r] = xr + dn;
     }
 }
 
@@ -268,8 +305,10 @@ __global__ void k_residual(MatView<T> A, const T *__restrict__ b, const T *__res
 {
     SKIP_RETURN();
     int r = my_row<TPR>();
+    bool lead = r < A.rows && row_leader<TPR>();
+    T br = lead ? b[r] : (T)0;
     T ax = row_sum<T, TPR>(A, r, [&](int c) { return __ldg(&x[c]); });
-    if (r < A.rows && row_leader<TPR>()) res[r] = b[r] - ax;
+    if (lead) res[r] = br - ax;
 }
 
 // restriction b_c = S^T r fused with the first smoother step of the coarse

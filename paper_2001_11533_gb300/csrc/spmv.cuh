@@ -15,6 +15,7 @@
 template <typename T>
 struct MatView {
     int rows, cols, tpr;
+    int wmax;       // most entries one lane visits in a row (DevCsr::wmax)
     const int *ptr; // SELL slice pointers (tpr = 1) or CSR row pointers
     const int *ci;
     const T *v;
@@ -25,14 +26,35 @@ inline MatView<T> view(const DevCsr &a);
 template <>
 inline MatView<double> view<double>(const DevCsr &a)
 {
-    if (a.tpr <= 1) return {a.rows, a.cols, 1, a.sl_ptr, a.sl_ci, a.sl_v};
-    return {a.rows, a.cols, a.tpr, a.rp, a.ci, a.v};
+    if (a.tpr <= 1) return {a.rows, a.cols, 1, a.wmax, a.sl_ptr, a.sl_ci, a.sl_v};
+    return {a.rows, a.cols, a.tpr, a.wmax, a.rp, a.ci, a.v};
 }
 template <>
 inline MatView<float> view<float>(const DevCsr &a)
 {
-    if (a.tpr <= 1) return {a.rows, a.cols, 1, a.sl_ptr, a.sl_ci, a.sl_v32};
-    return {a.rows, a.cols, a.tpr, a.rp, a.ci, a.v32};
+    if (a.tpr <= 1) return {a.rows, a.cols, 1, a.wmax, a.sl_ptr, a.sl_ci, a.sl_v32};
+    return {a.rows, a.cols, a.tpr, a.wmax, a.rp, a.ci, a.v32};
+}
+
+// Rows of at most ROW_UNROLL entries per lane are read with all their value
+// and index loads issued first, then all gathers, then the sum in the same
+// order as the loop (so the result does not depend on the path): two memory
+// round trips per row instead of one per group of four entries.
+#define ROW_UNROLL 8
+
+// entry range of this lane in `row` (SELL: stride 32 inside the slice; CSR:
+// stride STEP = TPR inside the row)
+template <typename T, int TPR>
+__device__ __forceinline__ void lane_range(const MatView<T> &m, int row, int &k, int &end)
+{
+    if (TPR == 1) {
+        int s = row >> 5;
+        k = m.ptr[s] + (row & 31);
+        end = m.ptr[s + 1];
+    } else {
+        k = m.ptr[row] + (int)(threadIdx.x & (TPR - 1));
+        end = m.ptr[row + 1];
+    }
 }
 
 // row owned by this thread (tpr = 1) or lane group
@@ -53,21 +75,32 @@ __device__ __forceinline__ bool row_leader()
 template <typename T, int TPR, typename F>
 __device__ __forceinline__ T row_sum(const MatView<T> &m, int row, F xf)
 {
+    constexpr int STEP = TPR == 1 ? 32 : TPR;
     T acc = (T)0;
-    if (TPR == 1) {
-        if (row < m.rows) {
-            int s = row >> 5, lane = row & 31;
-            int end = m.ptr[s + 1];
+    if (row < m.rows) {
+        int k, end;
+        lane_range<T, TPR>(m, row, k, end);
+        if (m.wmax <= ROW_UNROLL) {
+            T vv[ROW_UNROLL];
+            int cc[ROW_UNROLL];
+#pragma unroll
+            for (int j = 0; j < ROW_UNROLL; j++) {
+                bool ok = k + STEP * j < end;
+                vv[j] = ok ? m.v[k + STEP * j] : (T)0;
+                cc[j] = ok ? m.ci[k + STEP * j] : 0;
+            }
+            T xv[ROW_UNROLL];
+#pragma unroll
+            for (int j = 0; j < ROW_UNROLL; j++) xv[j] = k + STEP * j < end ? xf(cc[j]) : (T)0;
+#pragma unroll
+            for (int j = 0; j < ROW_UNROLL; j++)
+                if (k + STEP * j < end) acc += vv[j] * xv[j];
+        } else {
 #pragma unroll 4
-            for (int k = m.ptr[s] + lane; k < end; k += 32) acc += m.v[k] * xf(m.ci[k]);
+            for (; k < end; k += STEP) acc += m.v[k] * xf(m.ci[k]);
         }
-    } else {
-        int lane = threadIdx.x & (TPR - 1);
-        if (row < m.rows) {
-            int end = m.ptr[row + 1];
-#pragma unroll 4
-            for (int k = m.ptr[row] + lane; k < end; k += TPR) acc += m.v[k] * xf(m.ci[k]);
-        }
+    }
+    if (TPR > 1) {
 #pragma unroll
         for (int o = TPR / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o, TPR);
     }
@@ -87,32 +120,54 @@ __device__ __forceinline__ void df_term<double>(DF &acc, float ahi, float alo, d
     df_fma2(acc, ahi, alo, zhi, zlo);
 }
 
-// sum_j a_rj z_j in double-float (normalised); every lane of the group returns it
+// sum_j a_rj z_j in double-float, not normalised; every lane of the group
+// returns it
 template <typename Z, int TPR>
-__device__ __forceinline__ DF row_sum_dfv(const MatView<float> &m, const float *__restrict__ lo, int row,
-                                          const Z *__restrict__ z)
+__device__ __forceinline__ DF row_sum_df_acc(const MatView<float> &m, const float *__restrict__ lo, int row,
+                                             const Z *__restrict__ z)
 {
+    constexpr int STEP = TPR == 1 ? 32 : TPR;
     DF acc = {0.f, 0.f};
-    if (TPR == 1) {
-        if (row < m.rows) {
-            int s = row >> 5, lane = row & 31;
-            int end = m.ptr[s + 1];
+    if (row < m.rows) {
+        int k, end;
+        lane_range<float, TPR>(m, row, k, end);
+        if (m.wmax <= ROW_UNROLL) {
+            float vh[ROW_UNROLL], vl[ROW_UNROLL];
+            int cc[ROW_UNROLL];
+#pragma unroll
+            for (int j = 0; j < ROW_UNROLL; j++) {
+                bool ok = k + STEP * j < end;
+                vh[j] = ok ? m.v[k + STEP * j] : 0.f;
+                vl[j] = ok ? lo[k + STEP * j] : 0.f;
+                cc[j] = ok ? m.ci[k + STEP * j] : 0;
+            }
+            Z zv[ROW_UNROLL];
+#pragma unroll
+            for (int j = 0; j < ROW_UNROLL; j++) zv[j] = k + STEP * j < end ? __ldg(&z[cc[j]]) : (Z)0;
+#pragma unroll
+            for (int j = 0; j < ROW_UNROLL; j++)
+                if (k + STEP * j < end) df_term<Z>(acc, vh[j], vl[j], zv[j]);
+        } else {
 #pragma unroll 4
-            for (int k = m.ptr[s] + lane; k < end; k += 32) df_term<Z>(acc, m.v[k], lo[k], __ldg(&z[m.ci[k]]));
+            for (; k < end; k += STEP) df_term<Z>(acc, m.v[k], lo[k], __ldg(&z[m.ci[k]]));
         }
-    } else {
-        int lane = threadIdx.x & (TPR - 1);
-        if (row < m.rows) {
-            int end = m.ptr[row + 1];
-#pragma unroll 4
-            for (int k = m.ptr[row] + lane; k < end; k += TPR) df_term<Z>(acc, m.v[k], lo[k], __ldg(&z[m.ci[k]]));
-        }
+    }
+    if (TPR > 1) {
 #pragma unroll
         for (int o = TPR / 2; o > 0; o >>= 1) {
             DF other = {__shfl_xor_sync(0xffffffffu, acc.hi, o, TPR), __shfl_xor_sync(0xffffffffu, acc.lo, o, TPR)};
             df_merge(acc, other);
         }
     }
+    return acc;
+}
+
+// sum_j a_rj z_j in double-float (normalised)
+template <typename Z, int TPR>
+__device__ __forceinline__ DF row_sum_dfv(const MatView<float> &m, const float *__restrict__ lo, int row,
+                                          const Z *__restrict__ z)
+{
+    DF acc = row_sum_df_acc<Z, TPR>(m, lo, row, z);
     DF r;
     quick_two_sum(acc.hi, acc.lo, r.hi, r.lo);
     return r;
@@ -122,27 +177,7 @@ template <typename Z, int TPR>
 __device__ __forceinline__ double row_sum_df(const MatView<float> &m, const float *__restrict__ lo, int row,
                                              const Z *__restrict__ z)
 {
-    DF acc = {0.f, 0.f};
-    if (TPR == 1) {
-        if (row < m.rows) {
-            int s = row >> 5, lane = row & 31;
-            int end = m.ptr[s + 1];
-#pragma unroll 4
-            for (int k = m.ptr[s] + lane; k < end; k += 32) df_term<Z>(acc, m.v[k], lo[k], __ldg(&z[m.ci[k]]));
-        }
-    } else {
-        int lane = threadIdx.x & (TPR - 1);
-        if (row < m.rows) {
-            int end = m.ptr[row + 1];
-#pragma unroll 4
-            for (int k = m.ptr[row] + lane; k < end; k += TPR) df_term<Z>(acc, m.v[k], lo[k], __ldg(&z[m.ci[k]]));
-        }
-#pragma unroll
-        for (int o = TPR / 2; o > 0; o >>= 1) {
-            DF other = {__shfl_xor_sync(0xffffffffu, acc.hi, o, TPR), __shfl_xor_sync(0xffffffffu, acc.lo, o, TPR)};
-            df_merge(acc, other);
-        }
-    }
+    DF acc = row_sum_df_acc<Z, TPR>(m, lo, row, z);
     return (double)acc.hi + (double)acc.lo;
 }
 
