@@ -82,7 +82,13 @@ typedef struct {
  *                  needs at most 4096 control dofs there); 1 = unpreconditioned
  *                  CG on H_{l-1} to the relative residual coarse_tol of the
  *                  solve options (Sec. 5.2 uses 1e-4); 2 = the dense inverse
- *                  where H_{l-1} has at most 4096 dofs, else CG */
+ *                  where H_{l-1} has at most 4096 dofs, else CG
+ *  fuse_coarse     1 = FP32 V-cycles run their levels of at most 32768 rows
+ *                  (down to the dense coarsest solve) as one launch on a
+ *                  thread-block cluster; same result to the bit as 0 =
+ *                  one launch per smoother step and transfer (the default:
+ *                  on GB300 one cluster of 16 SMs is slower than the
+ *                  whole-GPU kernels for a 9,585-row level) */
 typedef struct {
     int max_levels;
     int hessian_levels;
@@ -93,6 +99,7 @@ typedef struct {
     int precision;
     int smooth_prolongator;
     int coarse_solve;
+    int fuse_coarse;
 } amgh_amg_opts;
 
 /* Solve options (Sec. 5.2-5.3).
@@ -151,7 +158,7 @@ typedef struct {
 } amgh_solve_info;
 
 /* Defaults: max_levels 25, hessian_levels 0, theta 0.08, coarse_max 256,
- * Chebyshev degree 2, precision 0, smoothed prolongator, coarse_solve 0;
+ * Chebyshev degree 2, precision 0, smoothed prolongator, coarse_solve 0, fuse_coarse 0;
  * tol 1e-8, max_iter 200, inner/mass tol 1e-10, precond 1, ncols 1, caps
  * 1000, precond_tol 0 (= inner_tol), coarse_tol 1e-4, coarse_max_iter 1000,
  * level_fallback 0. */

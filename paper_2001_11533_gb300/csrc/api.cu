@@ -28,6 +28,7 @@ extern "C" void amgh_amg_opts_default(amgh_amg_opts *o)
     o->precision = 0;
     o->smooth_prolongator = 1;
     o->coarse_solve = 0;
+    o->fuse_coarse = 0;
 }
 
 extern "C" void amgh_solve_opts_default(amgh_solve_opts *o)
@@ -206,6 +207,7 @@ extern "C" int amgh_problem_share(amgh_problem *parent, amgh_problem **out)
                             p->stream) != cudaSuccess)
             st = AMGH_ERR_CUDA;
         if (!st) st = solver_alloc(p);
+        if (!st) st = fused_setup(p); // its own table: it names this handle's vectors
         if (!st && cudaStreamSynchronize(p->stream) != cudaSuccess) st = AMGH_ERR_CUDA;
     }
     if (st) {
@@ -411,14 +413,18 @@ static int setup_impl(amgh_problem *p)
         }
         TRY(ar.alloc(&C.mu_invdiag, C.Mu.rows));
         TRY(diag_inv(p, C.Mu, C.mu_invdiag));
+        TRY(ar.alloc(&C.mu_invdiag32, C.Mu.rows));
+        TRY(to_f32(p, C.mu_invdiag, C.Mu.rows, C.mu_invdiag32));
     }
     // exact coarsest state solve, then the coarsest Hessian level
     TRY(dense_inverse_of(p, p->sl[p->Ls - 1].A, p->Acoarse));
+    TRY(dense_make32(p, p->harena, p->Acoarse));
     int ell = lmin;
     if (o.hessian_levels > 0 && o.hessian_levels < ell) ell = o.hessian_levels;
     TRY(coarse_hessian_setup(p, ell));
     smoother_coeffs(p);
     TRY(solver_alloc(p));
+    TRY(fused_setup(p));
     CU(cudaStreamSynchronize(s));
     return AMGH_OK;
 }
@@ -431,7 +437,7 @@ extern "C" int amgh_amg_setup(amgh_problem *p, const amgh_amg_opts *opts)
     else amgh_amg_opts_default(&o);
     if (o.max_levels < 1 || o.max_levels > AMGH_MAXL || o.smooth_degree < 1 || o.smooth_degree > 16 ||
         o.coarse_max < 1 || !(o.theta >= 0.0) || (o.smoother != 0 && o.smoother != 1) ||
-        o.precision < 0 || o.precision > 2 || o.hessian_levels < 0 || o.coarse_solve < 0 || o.coarse_solve > 2)
+        o.precision < 0 || o.precision > 2 || o.hessian_levels < 0 || o.coarse_solve < 0 || o.coarse_solve > 2 || (o.fuse_coarse != 0 && o.fuse_coarse != 1))
         return AMGH_ERR_INVALID_ARG;
     double t0 = now_s();
     StreamScope ss_(p->stream);

@@ -734,11 +734,14 @@ __global__ void k_df_spmv(MatView<float> A, const float *__restrict__ lo, const 
 }
 
 // K2: p = z + beta p, q = s + beta q, x += alpha p, r -= alpha q, reduce r.r
-__global__ void k_df_update(int n, const float *__restrict__ z, const float *__restrict__ sh,
-                            const float *__restrict__ sl, float *__restrict__ ph, float *__restrict__ pl,
-                            float *__restrict__ qh, float *__restrict__ ql, float *__restrict__ xh,
-                            float *__restrict__ xl, float *__restrict__ rh, float *__restrict__ rl, CgScal *sc,
-                            double *partials, unsigned *ticket)
+// With invd32 the preconditioner is Jacobi and the new z = D^-1 r (FP32, from
+// r's hi half) is written over z in the same pass (element i is read before it
+// is written, by the same thread).
+__global__ void k_df_update(int n, const float *z, const float *__restrict__ sh, const float *__restrict__ sl,
+                            float *__restrict__ ph, float *__restrict__ pl, float *__restrict__ qh,
+                            float *__restrict__ ql, float *__restrict__ xh, float *__restrict__ xl,
+                            float *__restrict__ rh, float *__restrict__ rl, const float *__restrict__ invd32,
+                            float *znew, CgScal *sc, double *partials, unsigned *ticket)
 {
     SKIP_DONE();
     DF al = {sc->ahi, sc->alo}, be = {sc->bhi, sc->blo};
@@ -761,6 +764,7 @@ __global__ void k_df_update(int n, const float *__restrict__ z, const float *__r
         xl[i] = xi.lo;
         rh[i] = ri.hi;
         rl[i] = ri.lo;
+        if (invd32) znew[i] = ri.hi * invd32[i];
         acc = df_add2(acc, df_mul2(ri, ri));
     }
     tot_df[0] = acc;
@@ -817,11 +821,25 @@ int dfcg_spmv(amgh_problem *p, RedSlot &red, const DevCsr &a, const float *z, co
 }
 
 int dfcg_update(amgh_problem *p, RedSlot &red, int n, const float *z, const double *s, double *pv, double *q,
-                double *x, double *r, CgScal *sc)
+                double *x, double *r, CgScal *sc, const float *invd32)
 {
     k_df_update<<<vec_blocks(n), TPB, 0, p->stream>>>(n, z, hi_of(s), lo_of(s, n), hi_of(pv), lo_of(pv, n),
                                                      hi_of(q), lo_of(q, n), hi_of(x), lo_of(x, n), hi_of(r),
-                                                     lo_of(r, n), sc, red.partials, red.ticket);
+                                                     lo_of(r, n), invd32, (float *)z, sc, red.partials, red.ticket);
+    LAUNCH_CHECK();
+    return AMGH_OK;
+}
+
+// z = D^-1 r from r's hi half (Jacobi start of the double-float mass CG)
+__global__ void k_df_jacobi(int n, const float *__restrict__ rh, const float *__restrict__ invd32,
+                            float *__restrict__ z)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) z[i] = rh[i] * invd32[i];
+}
+
+int dfcg_jacobi(amgh_problem *p, int n, const double *r, const float *invd32, float *z)
+{
+    k_df_jacobi<<<vec_blocks(n), TPB, 0, p->stream>>>(n, hi_of(r), invd32, z);
     LAUNCH_CHECK();
     return AMGH_OK;
 }

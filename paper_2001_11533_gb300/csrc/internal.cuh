@@ -176,6 +176,7 @@ struct StateLevel {
 struct CtrlLevel {
     DevCsr KN, Mu, P, Pt, Myu, Myut; // Myu: m_l x n_l (cross), Myut its transpose
     double *mu_invdiag = nullptr;
+    float *mu_invdiag32 = nullptr;
     int *agg = nullptr;
     int nagg = 0;
     // mass CG work
@@ -192,6 +193,8 @@ struct CtrlLevel {
 struct Dense {
     int n = 0;
     double *inv = nullptr; // explicit inverse (n x n, row-major)
+    float *inv32 = nullptr; // FP32 copy for FP32 V-cycles, rows padded to ld32 (a multiple of 4)
+    int ld32 = 0;
 };
 
 struct KernelTimer {
@@ -231,6 +234,9 @@ struct amgh_problem {
     int setup_done = 0;
     int Ls = 0, Lc = 0, ell = 0;
     int coarse_cg = 0; // Q_{ell-1} by CG on H_{ell-1} (else the dense inverse)
+    // fused coarse end of the FP32 V-cycle (fused.cu): first fused level or -1
+    int fuse_c0 = -1, fuse_cluster = 0;
+    void *fuse_table = nullptr;
     StateLevel sl[AMGH_MAXL];
     CtrlLevel cl[AMGH_MAXL];
     Dense Acoarse;  // inverse of A[Ls-1]
@@ -260,6 +266,8 @@ struct amgh_problem {
 int csr_to_sell(Arena &ar, DevCsr &a, int want32, cudaStream_t s);
 // pick SELL-32 or lanes-per-row CSR from the mean row length and build it
 int prepare_operator(Arena &ar, DevCsr &a, cudaStream_t s, int force_tpr = 0);
+// b = (float)a
+int to_f32(amgh_problem *p, const double *a, int64_t n, float *b);
 // build a.lo32 (after prepare_operator)
 int build_lo_parts(Arena &ar, DevCsr &a, cudaStream_t s);
 int csr_transpose(Arena &ar, const DevCsr &a, DevCsr &t, cudaStream_t s);
@@ -292,6 +300,13 @@ template <typename T>
 int prolong_add(amgh_problem *p, const DevCsr &s, const T *e, T *x, const int *skip);
 template <typename T>
 int dense_gemv(amgh_problem *p, int n, const double *inv, const T *b, T *x, const int *skip);
+// fused.cu: table and cluster size of the fused coarse V-cycle; one launch of it
+int fused_setup(amgh_problem *p);
+int fused_vcycle(amgh_problem *p, const float *b, float *x, int preinit, const int *skip);
+// x = inv b with the FP32 copy (rows padded to ld, 16-byte aligned)
+int dense_gemv32(amgh_problem *p, int n, int ld, const float *inv32, const float *b, float *x, const int *skip);
+// FP32 copy of a dense inverse with rows padded to a multiple of 4
+int dense_make32(amgh_problem *p, Arena &ar, Dense &d);
 
 // ------------------------------------------------------------------ blas.cu
 int red_alloc(Arena &ar, RedSlot &slot, int capacity);
@@ -312,7 +327,9 @@ int dfcg_start(amgh_problem *p, RedSlot &red, int n, const double *f, double *x,
 int dfcg_spmv(amgh_problem *p, RedSlot &red, const DevCsr &a, const float *z, const double *r, double *s,
               CgScal *sc, int timed);
 int dfcg_update(amgh_problem *p, RedSlot &red, int n, const float *z, const double *s, double *pv, double *q,
-                double *x, double *r, CgScal *sc);
+                double *x, double *r, CgScal *sc, const float *invd32 = nullptr);
+// z = D^-1 r (FP32) from the hi half of a double-float r
+int dfcg_jacobi(amgh_problem *p, int n, const double *r, const float *invd32, float *z);
 int df_to_double(amgh_problem *p, int n, const double *x, const CgScal *sc, double *y);
 int ref_start(amgh_problem *p, RedSlot &red, int n, const double *f, double *y, double *r,
               CgScal *rs, double tol, int maxit);

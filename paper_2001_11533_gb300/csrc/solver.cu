@@ -160,7 +160,13 @@ static int vcyc(amgh_problem *p, int l, const T *b, T *x, const int *skip, int p
 {
     StateLevel &S = p->sl[l];
     int n = S.A.rows;
-    if (l == p->Ls - 1) return dense_gemv<T>(p, n, p->Acoarse.inv, b, x, skip);
+    if (sizeof(T) == sizeof(float) && l == p->fuse_c0)
+        return fused_vcycle(p, (const float *)b, (float *)x, preinit, skip);
+    if (l == p->Ls - 1) {
+        if (sizeof(T) == sizeof(float))
+            return dense_gemv32(p, n, p->Acoarse.ld32, p->Acoarse.inv32, (const float *)b, (float *)x, skip);
+        return dense_gemv<T>(p, n, p->Acoarse.inv, b, x, skip);
+    }
     int timed = (l == 0);
     T *tmp = (x == VBuf<T>::x(S)) ? VBuf<T>::x2(S) : VBuf<T>::x(S);
     T *d = VBuf<T>::d(S), *r = VBuf<T>::r(S);
@@ -401,11 +407,23 @@ int mass_solve(amgh_problem *p, int l, const double *b, double *x, int64_t *iter
 {
     CtrlLevel &C = p->cl[l];
     int n = C.Mu.rows;
-    TRY(mass_start(p, C.red, n, b, C.mx, C.mr, C.mz, C.mu_invdiag, C.mscal, p->sopts.mass_tol,
-                   p->sopts.mass_max_iter));
+    // precision 2: the mass CG in double-float too, Jacobi from FP32 copies
+    bool df = p->aopts.precision == 2;
+    if (df) {
+        TRY(dfcg_start(p, C.red, n, b, C.mx, C.mr, C.mscal, p->sopts.mass_tol, p->sopts.mass_max_iter));
+        TRY(dfcg_jacobi(p, n, C.mr, C.mu_invdiag32, (float *)C.mz));
+    } else {
+        TRY(mass_start(p, C.red, n, b, C.mx, C.mr, C.mz, C.mu_invdiag, C.mscal, p->sopts.mass_tol,
+                       p->sopts.mass_max_iter));
+    }
     bool gr = use_graphs(p);
     CgGraph &g = C.mgraph;
     auto body = [&]() {
+        if (df) {
+            TRY(dfcg_spmv(p, C.red, C.Mu, (const float *)C.mz, C.mr, C.ms, C.mscal, 0));
+            return dfcg_update(p, C.red, n, (const float *)C.mz, C.ms, C.mp, C.mq, C.mx, C.mr, C.mscal,
+                               C.mu_invdiag32);
+        }
         TRY((cg2_spmv<double, double>(p, C.red, C.Mu, C.mz, C.mr, C.ms, C.mscal, 0)));
         return cg2_update<double, double>(p, C.red, n, C.mz, C.ms, C.mp, C.mq, C.mx, C.mr, nullptr, C.mu_invdiag,
                                           C.mscal);
@@ -428,8 +446,12 @@ int mass_solve(amgh_problem *p, int l, const double *b, double *x, int64_t *iter
     if (h.iters > 0) p->mchunk_hint[l] = h.iters;
     if (iters) *iters = h.iters;
     p->c_mass += h.iters;
-    k_copy<double><<<ceil_div(n, 256), 256, 0, p->stream>>>(n, C.mx, x, nullptr);
-    LAUNCH_CHECK();
+    if (df) {
+        TRY(df_to_double(p, n, C.mx, C.mscal, x));
+    } else {
+        k_copy<double><<<ceil_div(n, 256), 256, 0, p->stream>>>(n, C.mx, x, nullptr);
+        LAUNCH_CHECK();
+    }
     if (!h.done) return AMGH_ERR_NOT_CONVERGED;
     return cg_status(h);
 }

@@ -165,6 +165,14 @@ __global__ void k_to_f32(int64_t n, const double *__restrict__ a, float *__restr
     if (i < n) b[i] = (float)a[i];
 }
 
+int to_f32(amgh_problem *p, const double *a, int64_t n, float *b)
+{
+    if (n <= 0) return AMGH_OK;
+    k_to_f32<<<ceil_div(n, 256), 256, 0, p->stream>>>(n, a, b);
+    LAUNCH_CHECK();
+    return AMGH_OK;
+}
+
 __global__ void k_row_max(int rows, const int *__restrict__ rp, int *__restrict__ out)
 {
     int r = blockIdx.x * blockDim.x + threadIdx.x;
@@ -279,10 +287,10 @@ __global__ void k_cheb_step(MatView<T> A, const T *__restrict__ invd, const T *_
     }
     T ax = row_sum<T, TPR>(A, r, [&](int c) { return __ldg(&x[c]); });
     if (lead) {
-        T res = (br - ax) * ir;
-        T dn = cdv * dr + crv * res;
+        T dn, xv;
+        cheb_point(br, ax, ir, dr, xr, cdv, crv, dn, xv);
         d[r] = dn;
-        xn[r] = xr + dn;
+        xn[r] = xv;
     }
 }
 
@@ -294,7 +302,7 @@ __global__ void k_cheb_first(int n, const T *__restrict__ invd, const T *__restr
     SKIP_RETURN();
     int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= n) return;
-    T v = c * (b[r] * invd[r]);
+    T v = cheb_first_point(b[r], invd[r], c);
     d[r] = v;
     x[r] = v;
 }
@@ -308,7 +316,7 @@ __global__ void k_residual(MatView<T> A, const T *__restrict__ b, const T *__res
     bool lead = r < A.rows && row_leader<TPR>();
     T br = lead ? b[r] : (T)0;
     T ax = row_sum<T, TPR>(A, r, [&](int c) { return __ldg(&x[c]); });
-    if (lead) res[r] = br - ax;
+    if (lead) res[r] = rsub(br, ax);
 }
 
 // restriction b_c = S^T r fused with the first smoother step of the coarse
@@ -323,7 +331,7 @@ __global__ void k_restrict_first(MatView<T> St, const T *__restrict__ r, T *__re
     T b = row_sum<T, TPR>(St, i, [&](int c) { return __ldg(&r[c]); });
     if (i < St.rows && row_leader<TPR>()) {
         bc[i] = b;
-        T v = c0 * (b * invd[i]);
+        T v = cheb_first_point(b, invd[i], c0);
         d[i] = v;
         x[i] = v;
     }
@@ -336,7 +344,7 @@ __global__ void k_prolong_add(MatView<T> S, const T *__restrict__ e, T *__restri
     SKIP_RETURN();
     int i = my_row<TPR>();
     T v = row_sum<T, TPR>(S, i, [&](int c) { return __ldg(&e[c]); });
-    if (i < S.rows && row_leader<TPR>()) x[i] = x[i] + v;
+    if (i < S.rows && row_leader<TPR>()) x[i] = radd(x[i], v);
 }
 
 // x = inv b, one warp per row of the dense explicit inverse
@@ -354,7 +362,49 @@ __global__ void k_dense_gemv(int n, const double *__restrict__ inv, const T *__r
     if (lane == 0) x[warp] = (T)acc;
 }
 
+// FP32 copy, one warp per row, 16-byte loads of the padded row and (VEC) of
+// b (the last partial group of four read element by element)
+template <bool VEC>
+__global__ void k_dense_gemv32(int n, int ld, const float *__restrict__ inv, const float *__restrict__ b,
+                               float *__restrict__ x, const int *__restrict__ skip)
+{
+    SKIP_RETURN();
+    int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (warp >= n) return;
+    float acc = dense_row32<VEC>(inv, ld, warp, n, b, lane);
+    if (lane == 0) x[warp] = acc;
+}
+
+__global__ void k_pad32(int n, int ld, const double *__restrict__ inv, float *__restrict__ out)
+{
+    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (int64_t)n * ld) return;
+    int i = (int)(e / ld), j = (int)(e % ld);
+    out[e] = j < n ? (float)inv[(int64_t)i * n + j] : 0.f;
+}
+
 static const int TPB = 256;
+
+int dense_gemv32(amgh_problem *p, int n, int ld, const float *inv32, const float *b, float *x, const int *skip)
+{
+    if (n == 0) return AMGH_OK;
+    int g = ceil_div((int64_t)n * 32, TPB);
+    if (((uintptr_t)b & 15) == 0) k_dense_gemv32<true><<<g, TPB, 0, p->stream>>>(n, ld, inv32, b, x, skip);
+    else k_dense_gemv32<false><<<g, TPB, 0, p->stream>>>(n, ld, inv32, b, x, skip);
+    LAUNCH_CHECK();
+    return AMGH_OK;
+}
+
+int dense_make32(amgh_problem *p, Arena &ar, Dense &d)
+{
+    if (d.n == 0) return AMGH_OK;
+    d.ld32 = (d.n + 3) & ~3;
+    TRY(ar.alloc(&d.inv32, (int64_t)d.n * d.ld32));
+    if ((uintptr_t)d.inv32 & 15) return AMGH_ERR_CUDA; // pool blocks are 256-byte aligned
+    k_pad32<<<ceil_div((int64_t)d.n * d.ld32, TPB), TPB, 0, p->stream>>>(d.n, d.ld32, d.inv, d.inv32);
+    LAUNCH_CHECK();
+    return AMGH_OK;
+}
 
 double spmv_bytes(const DevCsr &a, int vb)
 {

@@ -181,6 +181,57 @@ __device__ __forceinline__ double row_sum_df(const MatView<float> &m, const floa
     return (double)acc.hi + (double)acc.lo;
 }
 
+// ---- point-wise V-cycle arithmetic with explicit rounding, shared by the
+// level-by-level kernels and the fused coarse cycle so both give the same bits
+__device__ __forceinline__ float rmul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double rmul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float radd(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double radd(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float rsub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ double rsub(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ float rfma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double rfma(double a, double b, double c) { return __fma_rn(a, b, c); }
+
+// Chebyshev step at one row: d' = c_d d + c_r D^-1 (b - A x), x' = x + d'
+template <typename T>
+__device__ __forceinline__ void cheb_point(T br, T ax, T ir, T dr, T xr, T cdv, T crv, T &dn, T &xn)
+{
+    T res = rmul(rsub(br, ax), ir);
+    dn = rfma(cdv, dr, rmul(crv, res));
+    xn = radd(xr, dn);
+}
+
+// first step from zero: c D^-1 b
+template <typename T>
+__device__ __forceinline__ T cheb_first_point(T br, T ir, T c)
+{
+    return rmul(c, rmul(br, ir));
+}
+
+// one row of a dense FP32 inverse (rows padded to ld, 16-byte aligned) times
+// b; the whole warp returns the sum
+template <bool VEC>
+__device__ __forceinline__ float dense_row32(const float *__restrict__ inv, int ld, int row, int n, const float *b,
+                                             int lane)
+{
+    const float4 *r4 = reinterpret_cast<const float4 *>(inv + (int64_t)row * ld);
+    int full = n >> 2;
+    float a0 = 0.f, a1 = 0.f;
+    for (int k = lane; k < full; k += 32) {
+        float4 r = r4[k], v;
+        if (VEC) v = __ldcg(reinterpret_cast<const float4 *>(b) + k);
+        else v = make_float4(__ldcg(b + 4 * k), __ldcg(b + 4 * k + 1), __ldcg(b + 4 * k + 2), __ldcg(b + 4 * k + 3));
+        a0 = fmaf(r.x, v.x, a0);
+        a1 = fmaf(r.y, v.y, a1);
+        a0 = fmaf(r.z, v.z, a0);
+        a1 = fmaf(r.w, v.w, a1);
+    }
+    for (int k = (full << 2) + lane; k < n; k += 32) a0 = fmaf(inv[(int64_t)row * ld + k], __ldcg(b + k), a0);
+    float acc = a0 + a1;
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    return acc;
+}
+
 inline int rows_grid(int rows, int tpr, int tpb = 256) { return ceil_div((int64_t)rows * (tpr < 1 ? 1 : tpr), tpb); }
 
 // run KERNEL<T, TPR><<<grid, 256, 0, stream>>>(args...) with TPR = m.tpr
