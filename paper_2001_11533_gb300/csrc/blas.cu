@@ -224,6 +224,7 @@ template <typename T>
 __global__ void k_cg_start(int n, const T *__restrict__ f, T *__restrict__ x, T *__restrict__ r, CgScal *sc,
                            int zero_x, double *partials, unsigned *ticket, int mode)
 {
+    pdl_enter();
     double v[1] = {0.0}, tot[1];
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         T fi = f[i];
@@ -239,6 +240,7 @@ __global__ void k_mass_start(int n, const double *__restrict__ f, double *__rest
                              double *__restrict__ z, const double *__restrict__ invd, CgScal *sc, double *partials,
                              unsigned *ticket)
 {
+    pdl_enter();
     double v[1] = {0.0}, tot[1];
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         double fi = f[i];
@@ -256,6 +258,7 @@ template <typename T, typename Z, int TPR>
 __global__ void k_cg2_spmv(MatView<T> A, const Z *__restrict__ z, const T *__restrict__ r, T *__restrict__ s,
                            CgScal *sc, double *partials, unsigned *ticket)
 {
+    pdl_enter();
     SKIP_DONE();
     int row = my_row<TPR>();
     T v = row_sum<T, TPR>(A, row, [&](int c) { return (T)__ldg(&z[c]); });
@@ -276,6 +279,7 @@ __global__ void k_cg2_spmv_df(MatView<float> A, const float *__restrict__ lo, co
                               const double *__restrict__ r, double *__restrict__ s, CgScal *sc, double *partials,
                               unsigned *ticket)
 {
+    pdl_enter();
     SKIP_DONE();
     int row = my_row<TPR>();
     double v = row_sum_df<Z, TPR>(A, lo, row, z);
@@ -297,6 +301,7 @@ __global__ void k_cg2_update(int n, Z *__restrict__ z, const T *__restrict__ s, 
                              T *__restrict__ q, T *__restrict__ x, T *__restrict__ r, float *__restrict__ r32,
                              const double *__restrict__ invd, CgScal *sc, double *partials, unsigned *ticket)
 {
+    pdl_enter();
     SKIP_DONE();
     T a = (T)sc->alpha, b = (T)sc->beta;
     bool first = sc->beta == 0.0;
@@ -322,6 +327,7 @@ template <typename T>
 __global__ void k_rz(int n, const T *__restrict__ r, const T *__restrict__ z, T *__restrict__ pv, CgScal *sc,
                      int first, double *partials, unsigned *ticket)
 {
+    pdl_enter();
     SKIP_DONE();
     double v[1] = {0.0}, tot[1];
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
@@ -336,6 +342,7 @@ __global__ void k_rz(int n, const T *__restrict__ r, const T *__restrict__ z, T 
 template <typename T>
 __global__ void k_xpay(int n, const T *__restrict__ z, T *__restrict__ pv, const CgScal *sc)
 {
+    pdl_enter();
     SKIP_DONE();
     T b = (T)sc->beta;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) pv[i] = z[i] + b * pv[i];
@@ -345,6 +352,7 @@ __global__ void k_xpay(int n, const T *__restrict__ z, T *__restrict__ pv, const
 __global__ void k_update(int n, double *__restrict__ x, double *__restrict__ r, const double *__restrict__ pv,
                          const double *__restrict__ q, CgScal *sc, double *partials, unsigned *ticket)
 {
+    pdl_enter();
     SKIP_DONE();
     double a = sc->alpha;
     double v[1] = {0.0}, tot[1];
@@ -361,6 +369,7 @@ __global__ void k_update(int n, double *__restrict__ x, double *__restrict__ r, 
 __global__ void k_dot(int n, const double *__restrict__ x, const double *__restrict__ y, CgScal *sc, int mode,
                       double *out, double *partials, unsigned *ticket)
 {
+    pdl_enter();
     if (sc && mode != F_STORE && sc->done) return;
     double v[1] = {0.0}, tot[1];
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) v[0] += x[i] * y[i];
@@ -370,6 +379,7 @@ __global__ void k_dot(int n, const double *__restrict__ x, const double *__restr
 // refinement: r32 = r / scale
 __global__ void k_ref_to32(int n, const double *__restrict__ r, float *__restrict__ r32, const CgScal *rs)
 {
+    pdl_enter();
     if (rs->done) return;
     double inv = 1.0 / rs->scale;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
@@ -379,6 +389,7 @@ __global__ void k_ref_to32(int n, const double *__restrict__ r, float *__restric
 // refinement: y += scale * e
 __global__ void k_ref_add(int n, double *__restrict__ y, const float *__restrict__ e, const CgScal *rs)
 {
+    pdl_enter();
     if (rs->done) return;
     double s = rs->scale;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
@@ -390,6 +401,7 @@ template <typename T, int TPR>
 __global__ void k_ref_resid(MatView<T> A, const T *__restrict__ f, const T *__restrict__ y, T *__restrict__ r,
                             CgScal *rs, double *partials, unsigned *ticket)
 {
+    pdl_enter();
     if (rs->done) return;
     int i = my_row<TPR>();
     T ay = row_sum<T, TPR>(A, i, [&](int c) { return __ldg(&y[c]); });
@@ -404,6 +416,7 @@ __global__ void k_ref_resid(MatView<T> A, const T *__restrict__ f, const T *__re
 
 __global__ void k_set_scal(CgScal *sc, double tol2, int maxit)
 {
+    pdl_enter();
     sc->thr = tol2;
     sc->maxit = maxit;
     sc->done = 0;
@@ -416,19 +429,21 @@ __global__ void k_set_scal(CgScal *sc, double tol2, int maxit)
 __global__ void k_axpby(int n, double a, const double *__restrict__ x, double b, const double *__restrict__ y,
                         double *__restrict__ out)
 {
+    pdl_enter();
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
         out[i] = a * x[i] + b * (y ? y[i] : 0.0);
 }
 
 __global__ void k_fill(int n, double v, double *__restrict__ x)
 {
+    pdl_enter();
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) x[i] = v;
 }
 
 // ------------------------------------------------------------------ host side
 static int set_scal(amgh_problem *p, CgScal *sc, double tol, int maxit)
 {
-    k_set_scal<<<1, 1, 0, p->stream>>>(sc, tol * tol, maxit);
+    pdl_launch(k_set_scal, dim3(1), dim3(1), 0, p->stream, sc, tol * tol, maxit);
     LAUNCH_CHECK();
     return AMGH_OK;
 }
@@ -441,12 +456,12 @@ static int cg2_spmv_df(amgh_problem *p, RedSlot &red, const DevCsr &a, const Z *
     MatView<float> A = view<float>(a);
     const float *lo = a.lo32;
     switch (A.tpr) {
-    case 2: k_cg2_spmv_df<Z, 2><<<rows_grid(A.rows, 2), TPB, 0, p->stream>>>(A, lo, z, r, s, sc, red.partials, red.ticket); break;
-    case 4: k_cg2_spmv_df<Z, 4><<<rows_grid(A.rows, 4), TPB, 0, p->stream>>>(A, lo, z, r, s, sc, red.partials, red.ticket); break;
-    case 8: k_cg2_spmv_df<Z, 8><<<rows_grid(A.rows, 8), TPB, 0, p->stream>>>(A, lo, z, r, s, sc, red.partials, red.ticket); break;
-    case 16: k_cg2_spmv_df<Z, 16><<<rows_grid(A.rows, 16), TPB, 0, p->stream>>>(A, lo, z, r, s, sc, red.partials, red.ticket); break;
-    case 32: k_cg2_spmv_df<Z, 32><<<rows_grid(A.rows, 32), TPB, 0, p->stream>>>(A, lo, z, r, s, sc, red.partials, red.ticket); break;
-    default: k_cg2_spmv_df<Z, 1><<<rows_grid(A.rows, 1), TPB, 0, p->stream>>>(A, lo, z, r, s, sc, red.partials, red.ticket); break;
+    case 2: pdl_launch(k_cg2_spmv_df<Z, 2>, dim3(rows_grid(A.rows, 2)), dim3(TPB), 0, p->stream, A, lo, z, r, s, sc, red.partials, red.ticket); break;
+    case 4: pdl_launch(k_cg2_spmv_df<Z, 4>, dim3(rows_grid(A.rows, 4)), dim3(TPB), 0, p->stream, A, lo, z, r, s, sc, red.partials, red.ticket); break;
+    case 8: pdl_launch(k_cg2_spmv_df<Z, 8>, dim3(rows_grid(A.rows, 8)), dim3(TPB), 0, p->stream, A, lo, z, r, s, sc, red.partials, red.ticket); break;
+    case 16: pdl_launch(k_cg2_spmv_df<Z, 16>, dim3(rows_grid(A.rows, 16)), dim3(TPB), 0, p->stream, A, lo, z, r, s, sc, red.partials, red.ticket); break;
+    case 32: pdl_launch(k_cg2_spmv_df<Z, 32>, dim3(rows_grid(A.rows, 32)), dim3(TPB), 0, p->stream, A, lo, z, r, s, sc, red.partials, red.ticket); break;
+    default: pdl_launch(k_cg2_spmv_df<Z, 1>, dim3(rows_grid(A.rows, 1)), dim3(TPB), 0, p->stream, A, lo, z, r, s, sc, red.partials, red.ticket); break;
     }
     LAUNCH_CHECK();
     return AMGH_OK;
@@ -462,12 +477,12 @@ int cg2_spmv(amgh_problem *p, RedSlot &red, const DevCsr &a, const Z *z, const T
     MatView<T> A = view<T>(a);
     timer_begin(p, timed);
     switch (A.tpr) {
-    case 2: k_cg2_spmv<T, Z, 2><<<rows_grid(A.rows, 2), TPB, 0, p->stream>>>(A, z, r, s, sc, red.partials, red.ticket); break;
-    case 4: k_cg2_spmv<T, Z, 4><<<rows_grid(A.rows, 4), TPB, 0, p->stream>>>(A, z, r, s, sc, red.partials, red.ticket); break;
-    case 8: k_cg2_spmv<T, Z, 8><<<rows_grid(A.rows, 8), TPB, 0, p->stream>>>(A, z, r, s, sc, red.partials, red.ticket); break;
-    case 16: k_cg2_spmv<T, Z, 16><<<rows_grid(A.rows, 16), TPB, 0, p->stream>>>(A, z, r, s, sc, red.partials, red.ticket); break;
-    case 32: k_cg2_spmv<T, Z, 32><<<rows_grid(A.rows, 32), TPB, 0, p->stream>>>(A, z, r, s, sc, red.partials, red.ticket); break;
-    default: k_cg2_spmv<T, Z, 1><<<rows_grid(A.rows, 1), TPB, 0, p->stream>>>(A, z, r, s, sc, red.partials, red.ticket); break;
+    case 2: pdl_launch(k_cg2_spmv<T, Z, 2>, dim3(rows_grid(A.rows, 2)), dim3(TPB), 0, p->stream, A, z, r, s, sc, red.partials, red.ticket); break;
+    case 4: pdl_launch(k_cg2_spmv<T, Z, 4>, dim3(rows_grid(A.rows, 4)), dim3(TPB), 0, p->stream, A, z, r, s, sc, red.partials, red.ticket); break;
+    case 8: pdl_launch(k_cg2_spmv<T, Z, 8>, dim3(rows_grid(A.rows, 8)), dim3(TPB), 0, p->stream, A, z, r, s, sc, red.partials, red.ticket); break;
+    case 16: pdl_launch(k_cg2_spmv<T, Z, 16>, dim3(rows_grid(A.rows, 16)), dim3(TPB), 0, p->stream, A, z, r, s, sc, red.partials, red.ticket); break;
+    case 32: pdl_launch(k_cg2_spmv<T, Z, 32>, dim3(rows_grid(A.rows, 32)), dim3(TPB), 0, p->stream, A, z, r, s, sc, red.partials, red.ticket); break;
+    default: pdl_launch(k_cg2_spmv<T, Z, 1>, dim3(rows_grid(A.rows, 1)), dim3(TPB), 0, p->stream, A, z, r, s, sc, red.partials, red.ticket); break;
     }
     LAUNCH_CHECK();
     // matrix + gather of z + reads of r, z + write of s
@@ -480,7 +495,7 @@ template <typename T, typename Z>
 int cg2_update(amgh_problem *p, RedSlot &red, int n, Z *z, const T *s, T *pv, T *q, T *x, T *r, float *r32,
                const double *invd, CgScal *sc)
 {
-    k_cg2_update<T, Z><<<vec_blocks(n), TPB, 0, p->stream>>>(n, z, s, pv, q, x, r, r32, invd, sc, red.partials,
+    pdl_launch(k_cg2_update<T, Z>, dim3(vec_blocks(n)), dim3(TPB), 0, p->stream, n, z, s, pv, q, x, r, r32, invd, sc, red.partials,
                                                              red.ticket);
     LAUNCH_CHECK();
     return AMGH_OK;
@@ -504,7 +519,7 @@ int cg_start(amgh_problem *p, RedSlot &red, int n, const T *f, T *x, T *r, CgSca
              int zero_x)
 {
     TRY(set_scal(p, sc, tol, maxit));
-    k_cg_start<T><<<vec_blocks(n), TPB, 0, p->stream>>>(n, f, x, r, sc, zero_x, red.partials, red.ticket, F_START);
+    pdl_launch(k_cg_start<T>, dim3(vec_blocks(n)), dim3(TPB), 0, p->stream, n, f, x, r, sc, zero_x, red.partials, red.ticket, F_START);
     LAUNCH_CHECK();
     return AMGH_OK;
 }
@@ -516,7 +531,7 @@ template int cg_start<float>(amgh_problem *, RedSlot &, int, const float *, floa
 int cg_update_outer(amgh_problem *p, RedSlot &red, int n, double *x, double *r, const double *pv, const double *q,
                     CgScal *sc)
 {
-    k_update<<<vec_blocks(n), TPB, 0, p->stream>>>(n, x, r, pv, q, sc, red.partials, red.ticket);
+    pdl_launch(k_update, dim3(vec_blocks(n)), dim3(TPB), 0, p->stream, n, x, r, pv, q, sc, red.partials, red.ticket);
     LAUNCH_CHECK();
     return AMGH_OK;
 }
@@ -526,7 +541,7 @@ int mass_start(amgh_problem *p, RedSlot &red, int n, const double *f, double *x,
                const double *invd, CgScal *sc, double tol, int maxit)
 {
     TRY(set_scal(p, sc, tol, maxit));
-    k_mass_start<<<vec_blocks(n), TPB, 0, p->stream>>>(n, f, x, r, z, invd, sc, red.partials, red.ticket);
+    pdl_launch(k_mass_start, dim3(vec_blocks(n)), dim3(TPB), 0, p->stream, n, f, x, r, z, invd, sc, red.partials, red.ticket);
     LAUNCH_CHECK();
     return AMGH_OK;
 }
@@ -534,7 +549,7 @@ int mass_start(amgh_problem *p, RedSlot &red, int n, const double *f, double *x,
 // outer CG pieces (operator applied by the host between them)
 int outer_dot(amgh_problem *p, RedSlot &red, int n, const double *x, const double *y, CgScal *sc, int mode)
 {
-    k_dot<<<vec_blocks(n), TPB, 0, p->stream>>>(n, x, y, sc, mode, nullptr, red.partials, red.ticket);
+    pdl_launch(k_dot, dim3(vec_blocks(n)), dim3(TPB), 0, p->stream, n, x, y, sc, mode, nullptr, red.partials, red.ticket);
     LAUNCH_CHECK();
     return AMGH_OK;
 }
@@ -547,10 +562,10 @@ int outer_pq(amgh_problem *p, RedSlot &red, int n, const double *pv, const doubl
 int outer_rz(amgh_problem *p, RedSlot &red, int n, const double *r, const double *z, double *pv, CgScal *sc,
              int first)
 {
-    k_rz<double><<<vec_blocks(n), TPB, 0, p->stream>>>(n, r, z, pv, sc, first, red.partials, red.ticket);
+    pdl_launch(k_rz<double>, dim3(vec_blocks(n)), dim3(TPB), 0, p->stream, n, r, z, pv, sc, first, red.partials, red.ticket);
     LAUNCH_CHECK();
     if (!first) {
-        k_xpay<double><<<vec_blocks(n), TPB, 0, p->stream>>>(n, z, pv, sc);
+        pdl_launch(k_xpay<double>, dim3(vec_blocks(n)), dim3(TPB), 0, p->stream, n, z, pv, sc);
         LAUNCH_CHECK();
     }
     return AMGH_OK;
@@ -558,7 +573,7 @@ int outer_rz(amgh_problem *p, RedSlot &red, int n, const double *r, const double
 
 int vec_dot(amgh_problem *p, RedSlot &red, int n, const double *x, const double *y, double *out_dev)
 {
-    k_dot<<<vec_blocks(n), TPB, 0, p->stream>>>(n, x, y, nullptr, F_STORE, out_dev, red.partials, red.ticket);
+    pdl_launch(k_dot, dim3(vec_blocks(n)), dim3(TPB), 0, p->stream, n, x, y, nullptr, F_STORE, out_dev, red.partials, red.ticket);
     LAUNCH_CHECK();
     return AMGH_OK;
 }
@@ -568,7 +583,7 @@ int ref_start(amgh_problem *p, RedSlot &red, int n, const double *f, double *y, 
               int maxit)
 {
     TRY(set_scal(p, rs, tol, maxit));
-    k_cg_start<double><<<vec_blocks(n), TPB, 0, p->stream>>>(n, f, y, r, rs, 1, red.partials, red.ticket,
+    pdl_launch(k_cg_start<double>, dim3(vec_blocks(n)), dim3(TPB), 0, p->stream, n, f, y, r, rs, 1, red.partials, red.ticket,
                                                              F_REF_START);
     LAUNCH_CHECK();
     return AMGH_OK;
@@ -576,7 +591,7 @@ int ref_start(amgh_problem *p, RedSlot &red, int n, const double *f, double *y, 
 
 int ref_to32(amgh_problem *p, RedSlot & /*red*/, int n, const double *r, float *r32, CgScal *rs)
 {
-    k_ref_to32<<<vec_blocks(n), TPB, 0, p->stream>>>(n, r, r32, rs);
+    pdl_launch(k_ref_to32, dim3(vec_blocks(n)), dim3(TPB), 0, p->stream, n, r, r32, rs);
     LAUNCH_CHECK();
     return AMGH_OK;
 }
@@ -585,16 +600,16 @@ int ref_update(amgh_problem *p, RedSlot &red, const DevCsr &a, const double *f, 
                double *r, CgScal *rs)
 {
     int n = a.rows;
-    k_ref_add<<<vec_blocks(n), TPB, 0, p->stream>>>(n, y, e32, rs);
+    pdl_launch(k_ref_add, dim3(vec_blocks(n)), dim3(TPB), 0, p->stream, n, y, e32, rs);
     LAUNCH_CHECK();
     MatView<double> A = view<double>(a);
     switch (A.tpr) {
-    case 2: k_ref_resid<double, 2><<<rows_grid(n, 2), TPB, 0, p->stream>>>(A, f, y, r, rs, red.partials, red.ticket); break;
-    case 4: k_ref_resid<double, 4><<<rows_grid(n, 4), TPB, 0, p->stream>>>(A, f, y, r, rs, red.partials, red.ticket); break;
-    case 8: k_ref_resid<double, 8><<<rows_grid(n, 8), TPB, 0, p->stream>>>(A, f, y, r, rs, red.partials, red.ticket); break;
-    case 16: k_ref_resid<double, 16><<<rows_grid(n, 16), TPB, 0, p->stream>>>(A, f, y, r, rs, red.partials, red.ticket); break;
-    case 32: k_ref_resid<double, 32><<<rows_grid(n, 32), TPB, 0, p->stream>>>(A, f, y, r, rs, red.partials, red.ticket); break;
-    default: k_ref_resid<double, 1><<<rows_grid(n, 1), TPB, 0, p->stream>>>(A, f, y, r, rs, red.partials, red.ticket); break;
+    case 2: pdl_launch(k_ref_resid<double, 2>, dim3(rows_grid(n, 2)), dim3(TPB), 0, p->stream, A, f, y, r, rs, red.partials, red.ticket); break;
+    case 4: pdl_launch(k_ref_resid<double, 4>, dim3(rows_grid(n, 4)), dim3(TPB), 0, p->stream, A, f, y, r, rs, red.partials, red.ticket); break;
+    case 8: pdl_launch(k_ref_resid<double, 8>, dim3(rows_grid(n, 8)), dim3(TPB), 0, p->stream, A, f, y, r, rs, red.partials, red.ticket); break;
+    case 16: pdl_launch(k_ref_resid<double, 16>, dim3(rows_grid(n, 16)), dim3(TPB), 0, p->stream, A, f, y, r, rs, red.partials, red.ticket); break;
+    case 32: pdl_launch(k_ref_resid<double, 32>, dim3(rows_grid(n, 32)), dim3(TPB), 0, p->stream, A, f, y, r, rs, red.partials, red.ticket); break;
+    default: pdl_launch(k_ref_resid<double, 1>, dim3(rows_grid(n, 1)), dim3(TPB), 0, p->stream, A, f, y, r, rs, red.partials, red.ticket); break;
     }
     LAUNCH_CHECK();
     return AMGH_OK;
@@ -603,7 +618,7 @@ int ref_update(amgh_problem *p, RedSlot &red, const DevCsr &a, const double *f, 
 int vec_axpby(amgh_problem *p, int n, double a, const double *x, double b, const double *y, double *out)
 {
     if (n == 0) return AMGH_OK;
-    k_axpby<<<vec_blocks(n), TPB, 0, p->stream>>>(n, a, x, b, y, out);
+    pdl_launch(k_axpby, dim3(vec_blocks(n)), dim3(TPB), 0, p->stream, n, a, x, b, y, out);
     LAUNCH_CHECK();
     return AMGH_OK;
 }
@@ -611,7 +626,7 @@ int vec_axpby(amgh_problem *p, int n, double a, const double *x, double b, const
 int vec_fill(amgh_problem *p, int n, double v, double *x)
 {
     if (n == 0) return AMGH_OK;
-    k_fill<<<vec_blocks(n), TPB, 0, p->stream>>>(n, v, x);
+    pdl_launch(k_fill, dim3(vec_blocks(n)), dim3(TPB), 0, p->stream, n, v, x);
     LAUNCH_CHECK();
     return AMGH_OK;
 }
@@ -681,6 +696,7 @@ __device__ bool reduce_df_last_block(const DF (&val)[NV], double *partials, unsi
 // halves stay far from the FP32 exponent limits whatever the size of f.
 __global__ void k_df_norm(int n, const double *__restrict__ f, CgScal *sc, double *partials, unsigned *ticket)
 {
+    pdl_enter();
     double v[1] = {0.0}, tot[1];
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) v[0] += f[i] * f[i];
     if (reduce_last_block<1>(v, partials, ticket, tot)) cg_finalize(F_SCALE, tot, sc, nullptr);
@@ -691,6 +707,7 @@ __global__ void k_df_start(int n, const double *__restrict__ f, float *__restric
                            float *__restrict__ rh, float *__restrict__ rl, CgScal *sc, double *partials,
                            unsigned *ticket)
 {
+    pdl_enter();
     DF acc = {0.f, 0.f}, tot_df[1];
     double tot[1];
     double scale = sc->scale;
@@ -712,6 +729,7 @@ __global__ void k_df_spmv(MatView<float> A, const float *__restrict__ lo, const 
                           const float *__restrict__ rh, const float *__restrict__ rl, float *__restrict__ sh,
                           float *__restrict__ sl, CgScal *sc, double *partials, unsigned *ticket)
 {
+    pdl_enter();
     SKIP_DONE();
     int row = my_row<TPR>();
     bool lead = row < A.rows && row_leader<TPR>();
@@ -743,6 +761,7 @@ __global__ void k_df_update(int n, const float *z, const float *__restrict__ sh,
                             float *__restrict__ rh, float *__restrict__ rl, const float *__restrict__ invd32,
                             float *znew, CgScal *sc, double *partials, unsigned *ticket)
 {
+    pdl_enter();
     SKIP_DONE();
     DF al = {sc->ahi, sc->alo}, be = {sc->bhi, sc->blo};
     DF nal = {-al.hi, -al.lo};
@@ -775,6 +794,7 @@ __global__ void k_df_update(int n, const float *z, const float *__restrict__ sh,
 __global__ void k_df_to_double(int n, const float *__restrict__ xh, const float *__restrict__ xl,
                                const CgScal *sc, double *__restrict__ y)
 {
+    pdl_enter();
     double inv = 1.0 / sc->scale;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
         y[i] = ((double)xh[i] + (double)xl[i]) * inv;
@@ -789,9 +809,9 @@ int dfcg_start(amgh_problem *p, RedSlot &red, int n, const double *f, double *x,
                int maxit)
 {
     TRY(set_scal(p, sc, tol, maxit));
-    k_df_norm<<<vec_blocks(n), TPB, 0, p->stream>>>(n, f, sc, red.partials, red.ticket);
+    pdl_launch(k_df_norm, dim3(vec_blocks(n)), dim3(TPB), 0, p->stream, n, f, sc, red.partials, red.ticket);
     LAUNCH_CHECK();
-    k_df_start<<<vec_blocks(n), TPB, 0, p->stream>>>(n, f, hi_of(x), lo_of(x, n), hi_of(r), lo_of(r, n), sc,
+    pdl_launch(k_df_start, dim3(vec_blocks(n)), dim3(TPB), 0, p->stream, n, f, hi_of(x), lo_of(x, n), hi_of(r), lo_of(r, n), sc,
                                                     red.partials, red.ticket);
     LAUNCH_CHECK();
     return AMGH_OK;
@@ -805,7 +825,7 @@ int dfcg_spmv(amgh_problem *p, RedSlot &red, const DevCsr &a, const float *z, co
     int n = a.rows;
     const float *lo = a.lo32;
 #define DFSPMV(TPR)                                                                                            \
-    k_df_spmv<TPR><<<rows_grid(n, TPR), TPB, 0, p->stream>>>(A, lo, z, hi_of(r), lo_of(r, n), hi_of(s),        \
+    pdl_launch(k_df_spmv<TPR>, dim3(rows_grid(n, TPR)), dim3(TPB), 0, p->stream, A, lo, z, hi_of(r), lo_of(r, n), hi_of(s),        \
                                                              lo_of(s, n), sc, red.partials, red.ticket)
     switch (A.tpr) {
     case 2: DFSPMV(2); break;
@@ -823,7 +843,7 @@ int dfcg_spmv(amgh_problem *p, RedSlot &red, const DevCsr &a, const float *z, co
 int dfcg_update(amgh_problem *p, RedSlot &red, int n, const float *z, const double *s, double *pv, double *q,
                 double *x, double *r, CgScal *sc, const float *invd32)
 {
-    k_df_update<<<vec_blocks(n), TPB, 0, p->stream>>>(n, z, hi_of(s), lo_of(s, n), hi_of(pv), lo_of(pv, n),
+    pdl_launch(k_df_update, dim3(vec_blocks(n)), dim3(TPB), 0, p->stream, n, z, hi_of(s), lo_of(s, n), hi_of(pv), lo_of(pv, n),
                                                      hi_of(q), lo_of(q, n), hi_of(x), lo_of(x, n), hi_of(r),
                                                      lo_of(r, n), invd32, (float *)z, sc, red.partials, red.ticket);
     LAUNCH_CHECK();
@@ -834,19 +854,20 @@ int dfcg_update(amgh_problem *p, RedSlot &red, int n, const float *z, const doub
 __global__ void k_df_jacobi(int n, const float *__restrict__ rh, const float *__restrict__ invd32,
                             float *__restrict__ z)
 {
+    pdl_enter();
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) z[i] = rh[i] * invd32[i];
 }
 
 int dfcg_jacobi(amgh_problem *p, int n, const double *r, const float *invd32, float *z)
 {
-    k_df_jacobi<<<vec_blocks(n), TPB, 0, p->stream>>>(n, hi_of(r), invd32, z);
+    pdl_launch(k_df_jacobi, dim3(vec_blocks(n)), dim3(TPB), 0, p->stream, n, hi_of(r), invd32, z);
     LAUNCH_CHECK();
     return AMGH_OK;
 }
 
 int df_to_double(amgh_problem *p, int n, const double *x, const CgScal *sc, double *y)
 {
-    k_df_to_double<<<vec_blocks(n), TPB, 0, p->stream>>>(n, hi_of(x), lo_of(x, n), sc, y);
+    pdl_launch(k_df_to_double, dim3(vec_blocks(n)), dim3(TPB), 0, p->stream, n, hi_of(x), lo_of(x, n), sc, y);
     LAUNCH_CHECK();
     return AMGH_OK;
 }

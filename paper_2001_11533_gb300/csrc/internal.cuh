@@ -2,6 +2,8 @@
 // translation units of the amgh library (sm_103a).
 #pragma once
 
+#include <utility>
+
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -30,6 +32,39 @@
 // count of kernels launched by this library (reported to callers)
 void amgh_count_launch(int n = 1);
 void amgh_set_capturing(int on);
+// Programmatic dependent launch.  Solve-phase kernels are launched with
+// pdl_launch, which lets a kernel be scheduled while its predecessor in the
+// stream (or CUDA graph) is still running; every such kernel calls
+// pdl_enter() first, which waits until the predecessor has completed and its
+// writes are visible, and -- for grids that fit comfortably in one wave --
+// lets its own successor be scheduled right away, so launch latency overlaps
+// the kernel instead of following it.  Without the launch attribute the wait
+// returns at once.
+#define PDL_EARLY_BLOCKS 608
+__device__ __forceinline__ void pdl_enter()
+{
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    if (gridDim.x * gridDim.y * gridDim.z <= PDL_EARLY_BLOCKS) asm volatile("griddepcontrol.launch_dependents;" :::);
+}
+
+template <typename... KArgs, typename... Args>
+inline void pdl_launch(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t stream,
+                       Args &&...args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    // a failed launch is reported by cudaGetLastError in LAUNCH_CHECK
+    (void)cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
+
 #define LAUNCH_CHECK()                         \
     do {                                       \
         amgh_count_launch();                   \

@@ -147,6 +147,7 @@ struct VBuf<float> {
 template <typename T>
 __global__ void k_copy(int n, const T *__restrict__ a, T *__restrict__ b, const int *skip)
 {
+    pdl_enter();
     if (skip && *skip) return;
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) b[i] = a[i];
@@ -200,7 +201,7 @@ static int vcyc(amgh_problem *p, int l, const T *b, T *x, const int *skip, int p
         nxt = t;
     }
     if (cur != x) {
-        k_copy<T><<<ceil_div(n, 256), 256, 0, p->stream>>>(n, cur, x, skip);
+        pdl_launch(k_copy<T>, dim3(ceil_div(n, 256)), dim3(256), 0, p->stream, n, cur, x, skip);
         LAUNCH_CHECK();
     }
     return AMGH_OK;
@@ -376,7 +377,7 @@ int state_solve(amgh_problem *p, int l, const double *f, double *y, double tol, 
         int st = pcg_run(p, l, prec == 2 ? 2 : 0, f, tol, maxit, iters);
         if (prec == 2) TRY(df_to_double(p, n, S.cx, S.scal, y));
         else {
-            k_copy<double><<<ceil_div(n, 256), 256, 0, p->stream>>>(n, S.cx, y, nullptr);
+            pdl_launch(k_copy<double>, dim3(ceil_div(n, 256)), dim3(256), 0, p->stream, n, S.cx, y, nullptr);
             LAUNCH_CHECK();
         }
         return st;
@@ -449,7 +450,7 @@ int mass_solve(amgh_problem *p, int l, const double *b, double *x, int64_t *iter
     if (df) {
         TRY(df_to_double(p, n, C.mx, C.mscal, x));
     } else {
-        k_copy<double><<<ceil_div(n, 256), 256, 0, p->stream>>>(n, C.mx, x, nullptr);
+        pdl_launch(k_copy<double>, dim3(ceil_div(n, 256)), dim3(256), 0, p->stream, n, C.mx, x, nullptr);
         LAUNCH_CHECK();
     }
     if (!h.done) return AMGH_ERR_NOT_CONVERGED;
@@ -477,6 +478,7 @@ int hessian_level(amgh_problem *p, int l, const double *v, double *hv)
 __global__ void k_r_combine(int n, const double *__restrict__ ta, const double *__restrict__ w1,
                             const double *__restrict__ tb, double beta, double *__restrict__ out)
 {
+    pdl_enter();
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) out[i] = ta[i] + (w1[i] - tb[i]) / beta;
 }
@@ -491,7 +493,7 @@ int mlas_R(amgh_problem *p, int j, const double *b, double *out)
     TRY(mass_solve(p, j + 1, Cc.bc, Cc.wc, nullptr));
     TRY(spmv(p, C.P, Cc.qc, C.ta, nullptr, 0));
     TRY(spmv(p, C.P, Cc.wc, C.tb, nullptr, 0));
-    k_r_combine<<<ceil_div(n, 256), 256, 0, p->stream>>>(n, C.ta, C.w1, C.tb, p->beta, out);
+    pdl_launch(k_r_combine, dim3(ceil_div(n, 256)), dim3(256), 0, p->stream, n, C.ta, C.w1, C.tb, p->beta, out);
     LAUNCH_CHECK();
     return AMGH_OK;
 }

@@ -249,6 +249,7 @@ int build_lo_parts(Arena &ar, DevCsr &a, cudaStream_t s)
 template <typename T, int TPR>
 __global__ void k_spmv(MatView<T> A, const T *__restrict__ x, T *__restrict__ y, const int *__restrict__ skip)
 {
+    pdl_enter();
     SKIP_RETURN();
     int r = my_row<TPR>();
     T v = row_sum<T, TPR>(A, r, [&](int c) { return __ldg(&x[c]); });
@@ -260,6 +261,7 @@ template <typename T, int TPR>
 __global__ void k_spmv2(MatView<T> A1, const T *__restrict__ x1, MatView<T> A2, const T *__restrict__ x2, T c,
                         T *__restrict__ y, const int *__restrict__ skip)
 {
+    pdl_enter();
     SKIP_RETURN();
     int r = my_row<TPR>();
     T a = row_sum<T, TPR>(A1, r, [&](int j) { return __ldg(&x1[j]); });
@@ -274,6 +276,7 @@ __global__ void k_cheb_step(MatView<T> A, const T *__restrict__ invd, const T *_
                             const T *__restrict__ x, T *__restrict__ d, T *__restrict__ xn, T cdv, T crv,
                             const int *__restrict__ skip)
 {
+    pdl_enter();
     SKIP_RETURN();
     int r = my_row<TPR>();
     bool lead = r < A.rows && row_leader<TPR>();
@@ -299,6 +302,7 @@ template <typename T>
 __global__ void k_cheb_first(int n, const T *__restrict__ invd, const T *__restrict__ b, T *__restrict__ d,
                              T *__restrict__ x, T c, const int *__restrict__ skip)
 {
+    pdl_enter();
     SKIP_RETURN();
     int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= n) return;
@@ -311,6 +315,7 @@ template <typename T, int TPR>
 __global__ void k_residual(MatView<T> A, const T *__restrict__ b, const T *__restrict__ x, T *__restrict__ res,
                            const int *__restrict__ skip)
 {
+    pdl_enter();
     SKIP_RETURN();
     int r = my_row<TPR>();
     bool lead = r < A.rows && row_leader<TPR>();
@@ -326,6 +331,7 @@ __global__ void k_restrict_first(MatView<T> St, const T *__restrict__ r, T *__re
                                  const T *__restrict__ invd, T *__restrict__ d, T *__restrict__ x, T c0,
                                  const int *__restrict__ skip)
 {
+    pdl_enter();
     SKIP_RETURN();
     int i = my_row<TPR>();
     T b = row_sum<T, TPR>(St, i, [&](int c) { return __ldg(&r[c]); });
@@ -341,6 +347,7 @@ template <typename T, int TPR>
 __global__ void k_prolong_add(MatView<T> S, const T *__restrict__ e, T *__restrict__ x,
                               const int *__restrict__ skip)
 {
+    pdl_enter();
     SKIP_RETURN();
     int i = my_row<TPR>();
     T v = row_sum<T, TPR>(S, i, [&](int c) { return __ldg(&e[c]); });
@@ -352,6 +359,7 @@ template <typename T>
 __global__ void k_dense_gemv(int n, const double *__restrict__ inv, const T *__restrict__ b, T *__restrict__ x,
                              const int *__restrict__ skip)
 {
+    pdl_enter();
     SKIP_RETURN();
     int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     if (warp >= n) return;
@@ -368,6 +376,7 @@ template <bool VEC>
 __global__ void k_dense_gemv32(int n, int ld, const float *__restrict__ inv, const float *__restrict__ b,
                                float *__restrict__ x, const int *__restrict__ skip)
 {
+    pdl_enter();
     SKIP_RETURN();
     int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     if (warp >= n) return;
@@ -389,8 +398,8 @@ int dense_gemv32(amgh_problem *p, int n, int ld, const float *inv32, const float
 {
     if (n == 0) return AMGH_OK;
     int g = ceil_div((int64_t)n * 32, TPB);
-    if (((uintptr_t)b & 15) == 0) k_dense_gemv32<true><<<g, TPB, 0, p->stream>>>(n, ld, inv32, b, x, skip);
-    else k_dense_gemv32<false><<<g, TPB, 0, p->stream>>>(n, ld, inv32, b, x, skip);
+    if (((uintptr_t)b & 15) == 0) pdl_launch(k_dense_gemv32<true>, dim3(g), dim3(TPB), 0, p->stream, n, ld, inv32, b, x, skip);
+    else pdl_launch(k_dense_gemv32<false>, dim3(g), dim3(TPB), 0, p->stream, n, ld, inv32, b, x, skip);
     LAUNCH_CHECK();
     return AMGH_OK;
 }
@@ -456,6 +465,7 @@ template <typename T, int TPR>
 __global__ void k_spmv_axpy(MatView<T> A, const T *__restrict__ x, T c, T *__restrict__ y,
                             const int *__restrict__ skip)
 {
+    pdl_enter();
     SKIP_RETURN();
     int r = my_row<TPR>();
     T v = row_sum<T, TPR>(A, r, [&](int j) { return __ldg(&x[j]); });
@@ -474,7 +484,7 @@ template <typename T>
 int cheb_first(amgh_problem *p, int n, const T *invd, const T *b, T *d, T *x, double c, const int *skip)
 {
     if (n == 0) return AMGH_OK;
-    k_cheb_first<T><<<ceil_div(n, TPB), TPB, 0, p->stream>>>(n, invd, b, d, x, (T)c, skip);
+    pdl_launch(k_cheb_first<T>, dim3(ceil_div(n, TPB)), dim3(TPB), 0, p->stream, n, invd, b, d, x, (T)c, skip);
     LAUNCH_CHECK();
     return AMGH_OK;
 }
@@ -530,7 +540,7 @@ template <typename T>
 int dense_gemv(amgh_problem *p, int n, const double *inv, const T *b, T *x, const int *skip)
 {
     if (n == 0) return AMGH_OK;
-    k_dense_gemv<T><<<ceil_div((int64_t)n * 32, TPB), TPB, 0, p->stream>>>(n, inv, b, x, skip);
+    pdl_launch(k_dense_gemv<T>, dim3(ceil_div((int64_t)n * 32, TPB)), dim3(TPB), 0, p->stream, n, inv, b, x, skip);
     LAUNCH_CHECK();
     return AMGH_OK;
 }

@@ -234,16 +234,16 @@ __device__ __forceinline__ float dense_row32(const float *__restrict__ inv, int 
 
 inline int rows_grid(int rows, int tpr, int tpb = 256) { return ceil_div((int64_t)rows * (tpr < 1 ? 1 : tpr), tpb); }
 
-// run KERNEL<T, TPR><<<grid, 256, 0, stream>>>(args...) with TPR = m.tpr
+// launch KERNEL<T, TPR> (grid of 256-thread blocks, programmatic dependent launch) with TPR = m.tpr
 #define LAUNCH_TPR(KERNEL, T, tpr, rows, stream, ...)                                                     \
     do {                                                                                                  \
         int g_ = rows_grid(rows, tpr);                                                                    \
         switch (tpr) {                                                                                    \
-        case 2: KERNEL<T, 2><<<g_, 256, 0, stream>>>(__VA_ARGS__); break;                                 \
-        case 4: KERNEL<T, 4><<<g_, 256, 0, stream>>>(__VA_ARGS__); break;                                 \
-        case 8: KERNEL<T, 8><<<g_, 256, 0, stream>>>(__VA_ARGS__); break;                                 \
-        case 16: KERNEL<T, 16><<<g_, 256, 0, stream>>>(__VA_ARGS__); break;                               \
-        case 32: KERNEL<T, 32><<<g_, 256, 0, stream>>>(__VA_ARGS__); break;                               \
-        default: KERNEL<T, 1><<<g_, 256, 0, stream>>>(__VA_ARGS__); break;                                \
+        case 2: pdl_launch(KERNEL<T, 2>, dim3(g_), dim3(256), 0, stream, __VA_ARGS__); break;                                 \
+        case 4: pdl_launch(KERNEL<T, 4>, dim3(g_), dim3(256), 0, stream, __VA_ARGS__); break;                                 \
+        case 8: pdl_launch(KERNEL<T, 8>, dim3(g_), dim3(256), 0, stream, __VA_ARGS__); break;                                 \
+        case 16: pdl_launch(KERNEL<T, 16>, dim3(g_), dim3(256), 0, stream, __VA_ARGS__); break;                               \
+        case 32: pdl_launch(KERNEL<T, 32>, dim3(g_), dim3(256), 0, stream, __VA_ARGS__); break;                               \
+        default: pdl_launch(KERNEL<T, 1>, dim3(g_), dim3(256), 0, stream, __VA_ARGS__); break;                                \
         }                                                                                                 \
     } while (0)
