@@ -658,7 +658,7 @@ __device__ bool reduce_df_last_block(const DF (&val)[NV], double *partials, unsi
 #pragma unroll
         for (int q = 0; q < NV; q++) {
             DF t = shw[q][0];
-            for (int k = 1; k < nw; k++) t = df_add2(t, shw[q][k]);
+            for (int k = 1; k < nw; k++) t = df_add_fast(t, shw[q][k]);
             part[q * nb + blockIdx.x] = make_float2(t.hi, t.lo);
         }
         __threadfence();
@@ -673,7 +673,7 @@ __device__ bool reduce_df_last_block(const DF (&val)[NV], double *partials, unsi
         DF s = {0.f, 0.f};
         for (int b = threadIdx.x; b < nb; b += blockDim.x) {
             float2 v = __ldcg(&part[q * nb + b]); // L2: written by other blocks
-            s = df_add2(s, DF{v.x, v.y});
+            s = df_add_fast(s, DF{v.x, v.y});
         }
         s = df_warp_sum(s);
         if (l == 0) shw[q][w] = s;
@@ -683,7 +683,7 @@ __device__ bool reduce_df_last_block(const DF (&val)[NV], double *partials, unsi
 #pragma unroll
         for (int q = 0; q < NV; q++) {
             DF t = shw[q][0];
-            for (int k = 1; k < nw; k++) t = df_add2(t, shw[q][k]);
+            for (int k = 1; k < nw; k++) t = df_add_fast(t, shw[q][k]);
             tot[q] = df_to_double(t);
         }
         *ticket = 0u;
@@ -717,7 +717,7 @@ __global__ void k_df_start(int n, const double *__restrict__ f, float *__restric
         rl[i] = fi.lo;
         xh[i] = 0.f;
         xl[i] = 0.f;
-        acc = df_add2(acc, df_mul2(fi, fi));
+        acc = df_add_fast(acc, df_mul2(fi, fi));
     }
     tot_df[0] = acc;
     if (reduce_df_last_block<1>(tot_df, partials, ticket, tot)) cg_finalize(F_START, tot, sc, nullptr);
@@ -784,7 +784,7 @@ __global__ void k_df_update(int n, const float *z, const float *__restrict__ sh,
         rh[i] = ri.hi;
         rl[i] = ri.lo;
         if (invd32) znew[i] = ri.hi * invd32[i];
-        acc = df_add2(acc, df_mul2(ri, ri));
+        acc = df_add_fast(acc, df_mul2(ri, ri)); // squares: no cancellation
     }
     tot_df[0] = acc;
     if (reduce_df_last_block<1>(tot_df, partials, ticket, tot)) cg_finalize(F_RR, tot, sc, nullptr);

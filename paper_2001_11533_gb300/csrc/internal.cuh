@@ -149,8 +149,9 @@ struct DevCsr {
     // the widest slice; CSR: ceil(longest row / tpr)); rows up to
     // ROW_UNROLL per lane are read with every load issued up front
     int wmax = 1 << 30;
-    // SELL-32
-    int nslices = 0, sell_nnz = 0;
+    // SELL-32; ellw > 0: every slice has this width (slice s starts at
+    // 32 * ellw * s, so kernels need not load the slice pointers)
+    int nslices = 0, sell_nnz = 0, ellw = 0;
     int *sl_ptr = nullptr, *sl_ci = nullptr;
     double *sl_v = nullptr;
     float *sl_v32 = nullptr;

@@ -55,6 +55,12 @@ __global__ void k_sell_fill(int rows, const int *__restrict__ rp, const int *__r
     }
 }
 
+__global__ void k_fill_int(int n, int v, int *__restrict__ x)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) x[i] = v;
+}
+
 int csr_to_sell(Arena &ar, DevCsr &a, int /*want32*/, cudaStream_t s)
 {
     a.nslices = ceil_div(a.rows, 32);
@@ -69,6 +75,17 @@ int csr_to_sell(Arena &ar, DevCsr &a, int /*want32*/, cudaStream_t s)
     }
     int total = 0;
     TRY(exclusive_scan<int>(w, a.sl_ptr, ns, s, &total));
+    // one width for all slices when that pads by at most 5 %: the kernels
+    // then compute where a slice starts instead of loading it
+    a.ellw = 0;
+    int widest = a.wmax < (1 << 30) ? a.wmax : 0;
+    if (ns > 0 && widest > 0 && (int64_t)32 * widest * ns <= (int64_t)total + total / 20 &&
+        (int64_t)32 * widest * ns < (1ll << 31)) {
+        k_fill_int<<<ceil_div(ns, 256), 256, 0, s>>>(ns, 32 * widest, w);
+        LAUNCH_CHECK();
+        TRY(exclusive_scan<int>(w, a.sl_ptr, ns, s, &total));
+        a.ellw = widest;
+    }
     a.sell_nnz = total;
     TRY(ar.alloc(&a.sl_ci, total));
     TRY(ar.alloc(&a.sl_v, total));

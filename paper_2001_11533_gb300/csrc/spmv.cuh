@@ -16,6 +16,7 @@ template <typename T>
 struct MatView {
     int rows, cols, tpr;
     int wmax;       // most entries one lane visits in a row (DevCsr::wmax)
+    int ellw;       // SELL with one width for all slices (DevCsr::ellw), else 0
     const int *ptr; // SELL slice pointers (tpr = 1) or CSR row pointers
     const int *ci;
     const T *v;
@@ -26,14 +27,14 @@ inline MatView<T> view(const DevCsr &a);
 template <>
 inline MatView<double> view<double>(const DevCsr &a)
 {
-    if (a.tpr <= 1) return {a.rows, a.cols, 1, a.wmax, a.sl_ptr, a.sl_ci, a.sl_v};
-    return {a.rows, a.cols, a.tpr, a.wmax, a.rp, a.ci, a.v};
+    if (a.tpr <= 1) return {a.rows, a.cols, 1, a.wmax, a.ellw, a.sl_ptr, a.sl_ci, a.sl_v};
+    return {a.rows, a.cols, a.tpr, a.wmax, 0, a.rp, a.ci, a.v};
 }
 template <>
 inline MatView<float> view<float>(const DevCsr &a)
 {
-    if (a.tpr <= 1) return {a.rows, a.cols, 1, a.wmax, a.sl_ptr, a.sl_ci, a.sl_v32};
-    return {a.rows, a.cols, a.tpr, a.wmax, a.rp, a.ci, a.v32};
+    if (a.tpr <= 1) return {a.rows, a.cols, 1, a.wmax, a.ellw, a.sl_ptr, a.sl_ci, a.sl_v32};
+    return {a.rows, a.cols, a.tpr, a.wmax, 0, a.rp, a.ci, a.v32};
 }
 
 // Rows of at most ROW_UNROLL entries per lane are read with all their value
@@ -49,8 +50,14 @@ __device__ __forceinline__ void lane_range(const MatView<T> &m, int row, int &k,
 {
     if (TPR == 1) {
         int s = row >> 5;
-        k = m.ptr[s] + (row & 31);
-        end = m.ptr[s + 1];
+        if (m.ellw > 0) {
+            int base = s * 32 * m.ellw;
+            k = base + (row & 31);
+            end = base + 32 * m.ellw;
+        } else {
+            k = m.ptr[s] + (row & 31);
+            end = m.ptr[s + 1];
+        }
     } else {
         k = m.ptr[row] + (int)(threadIdx.x & (TPR - 1));
         end = m.ptr[row + 1];
