@@ -19,6 +19,8 @@
 // gather of z) and one reduction point per iteration.
 #include <math.h>
 
+#include <algorithm>
+
 #include "internal.cuh"
 #include "spmv.cuh"
 #include "util.cuh"
@@ -654,16 +656,18 @@ __device__ bool reduce_df_last_block(const DF (&val)[NV], double *partials, unsi
         if (l == 0) shw[q][w] = s;
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (w == 0) {
 #pragma unroll
         for (int q = 0; q < NV; q++) {
-            DF t = shw[q][0];
-            for (int k = 1; k < nw; k++) t = df_add_fast(t, shw[q][k]);
-            part[q * nb + blockIdx.x] = make_float2(t.hi, t.lo);
+            DF t = l < nw ? shw[q][l] : DF{0.f, 0.f};
+            t = df_warp_sum(t);
+            if (l == 0) part[q * nb + blockIdx.x] = make_float2(t.hi, t.lo);
         }
-        __threadfence();
-        unsigned tk = atomicAdd(ticket, 1u);
-        is_last = (tk == (unsigned)nb - 1);
+        if (l == 0) {
+            __threadfence();
+            unsigned tk = atomicAdd(ticket, 1u);
+            is_last = (tk == (unsigned)nb - 1);
+        }
     }
     __syncthreads();
     if (!is_last) return false;
@@ -679,14 +683,14 @@ __device__ bool reduce_df_last_block(const DF (&val)[NV], double *partials, unsi
         if (l == 0) shw[q][w] = s;
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (w == 0) {
 #pragma unroll
         for (int q = 0; q < NV; q++) {
-            DF t = shw[q][0];
-            for (int k = 1; k < nw; k++) t = df_add_fast(t, shw[q][k]);
+            DF t = l < nw ? shw[q][l] : DF{0.f, 0.f};
+            t = df_warp_sum(t);
             tot[q] = df_to_double(t);
         }
-        *ticket = 0u;
+        if (l == 0) *ticket = 0u;
     }
     return threadIdx.x == 0;
 }
@@ -731,22 +735,27 @@ __global__ void k_df_spmv(MatView<float> A, const float *__restrict__ lo, const 
 {
     pdl_enter();
     SKIP_DONE();
-    int row = my_row<TPR>();
-    bool lead = row < A.rows && row_leader<TPR>();
-    float zr = 0.f, rhr = 0.f, rlr = 0.f;
-    if (lead) {
-        zr = z[row];
-        rhr = rh[row];
-        rlr = rl[row];
-    }
-    DF v = row_sum_dfv<float, TPR>(A, lo, row, z);
+    // a grid that fits on the GPU at once walks the rows, so each block pays
+    // its reduction tail once for several rows per thread
     DF a[2] = {{0.f, 0.f}, {0.f, 0.f}};
     double tot[2];
-    if (lead) {
-        sh[row] = v.hi;
-        sl[row] = v.lo;
-        a[0] = df_mulf(DF{rhr, rlr}, zr);
-        a[1] = df_mulf(v, zr);
+    const int stride = gridDim.x * blockDim.x, slots = A.rows * TPR;
+    for (int base = blockIdx.x * blockDim.x; base < slots; base += stride) {
+        int row = (base + (int)threadIdx.x) / TPR;
+        bool lead = row < A.rows && row_leader<TPR>();
+        float zr = 0.f, rhr = 0.f, rlr = 0.f;
+        if (lead) {
+            zr = z[row];
+            rhr = rh[row];
+            rlr = rl[row];
+        }
+        DF v = row_sum_dfv<float, TPR>(A, lo, row, z);
+        if (lead) {
+            sh[row] = v.hi;
+            sl[row] = v.lo;
+            a[0] = df_add_fast(a[0], df_mulf(DF{rhr, rlr}, zr));
+            a[1] = df_add_fast(a[1], df_mulf(v, zr));
+        }
     }
     if (reduce_df_last_block<2>(a, partials, ticket, tot)) cg_finalize(F_CG2, tot, sc, nullptr);
 }
@@ -811,7 +820,7 @@ int dfcg_start(amgh_problem *p, RedSlot &red, int n, const double *f, double *x,
     TRY(set_scal(p, sc, tol, maxit));
     pdl_launch(k_df_norm, dim3(vec_blocks(n)), dim3(TPB), 0, p->stream, n, f, sc, red.partials, red.ticket);
     LAUNCH_CHECK();
-    pdl_launch(k_df_start, dim3(vec_blocks(n)), dim3(TPB), 0, p->stream, n, f, hi_of(x), lo_of(x, n), hi_of(r), lo_of(r, n), sc,
+    pdl_launch(k_df_start, dim3(std::min(vec_blocks(n), resident_grid((const void *)k_df_start, TPB))), dim3(TPB), 0, p->stream, n, f, hi_of(x), lo_of(x, n), hi_of(r), lo_of(r, n), sc,
                                                     red.partials, red.ticket);
     LAUNCH_CHECK();
     return AMGH_OK;
@@ -825,8 +834,9 @@ int dfcg_spmv(amgh_problem *p, RedSlot &red, const DevCsr &a, const float *z, co
     int n = a.rows;
     const float *lo = a.lo32;
 #define DFSPMV(TPR)                                                                                            \
-    pdl_launch(k_df_spmv<TPR>, dim3(rows_grid(n, TPR)), dim3(TPB), 0, p->stream, A, lo, z, hi_of(r), lo_of(r, n), hi_of(s),        \
-                                                             lo_of(s, n), sc, red.partials, red.ticket)
+    pdl_launch(k_df_spmv<TPR>,                                                                                 \
+               dim3(std::min(rows_grid(n, TPR), resident_grid((const void *)k_df_spmv<TPR>, TPB))), dim3(TPB), \
+               0, p->stream, A, lo, z, hi_of(r), lo_of(r, n), hi_of(s), lo_of(s, n), sc, red.partials, red.ticket)
     switch (A.tpr) {
     case 2: DFSPMV(2); break;
     case 4: DFSPMV(4); break;
@@ -843,7 +853,7 @@ int dfcg_spmv(amgh_problem *p, RedSlot &red, const DevCsr &a, const float *z, co
 int dfcg_update(amgh_problem *p, RedSlot &red, int n, const float *z, const double *s, double *pv, double *q,
                 double *x, double *r, CgScal *sc, const float *invd32)
 {
-    pdl_launch(k_df_update, dim3(vec_blocks(n)), dim3(TPB), 0, p->stream, n, z, hi_of(s), lo_of(s, n), hi_of(pv), lo_of(pv, n),
+    pdl_launch(k_df_update, dim3(std::min(vec_blocks(n), resident_grid((const void *)k_df_update, TPB))), dim3(TPB), 0, p->stream, n, z, hi_of(s), lo_of(s, n), hi_of(pv), lo_of(pv, n),
                                                      hi_of(q), lo_of(q, n), hi_of(x), lo_of(x, n), hi_of(r),
                                                      lo_of(r, n), invd32, (float *)z, sc, red.partials, red.ticket);
     LAUNCH_CHECK();
@@ -860,14 +870,14 @@ __global__ void k_df_jacobi(int n, const float *__restrict__ rh, const float *__
 
 int dfcg_jacobi(amgh_problem *p, int n, const double *r, const float *invd32, float *z)
 {
-    pdl_launch(k_df_jacobi, dim3(vec_blocks(n)), dim3(TPB), 0, p->stream, n, hi_of(r), invd32, z);
+    pdl_launch(k_df_jacobi, dim3(std::min(vec_blocks(n), resident_grid((const void *)k_df_jacobi, TPB))), dim3(TPB), 0, p->stream, n, hi_of(r), invd32, z);
     LAUNCH_CHECK();
     return AMGH_OK;
 }
 
 int df_to_double(amgh_problem *p, int n, const double *x, const CgScal *sc, double *y)
 {
-    pdl_launch(k_df_to_double, dim3(vec_blocks(n)), dim3(TPB), 0, p->stream, n, hi_of(x), lo_of(x, n), sc, y);
+    pdl_launch(k_df_to_double, dim3(std::min(vec_blocks(n), resident_grid((const void *)k_df_to_double, TPB))), dim3(TPB), 0, p->stream, n, hi_of(x), lo_of(x, n), sc, y);
     LAUNCH_CHECK();
     return AMGH_OK;
 }

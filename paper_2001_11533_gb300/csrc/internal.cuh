@@ -31,6 +31,8 @@
 
 // count of kernels launched by this library (reported to callers)
 void amgh_count_launch(int n = 1);
+// blocks of `block` threads of `kernel` resident on the current device at once
+int resident_grid(const void *kernel, int block);
 void amgh_set_capturing(int on);
 // Programmatic dependent launch.  Solve-phase kernels are launched with
 // pdl_launch, which lets a kernel be scheduled while its predecessor in the

@@ -14,6 +14,31 @@ void amgh_count_launch(int n)
     if (!g_capturing) g_launches += n;
 }
 void amgh_set_capturing(int on) { g_capturing = on; }
+
+// blocks of `block` threads of `kernel` that fit on the current device at once
+// (occupancy x SM count), cached per kernel and device
+int resident_grid(const void *kernel, int block)
+{
+    static std::mutex mu;
+    static std::vector<std::pair<std::pair<const void *, int>, int>> cache;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 1 << 30;
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        for (auto &e : cache)
+            if (e.first.first == kernel && e.first.second == dev) return e.second;
+    }
+    int per_sm = 0, sms = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, block, 0) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || per_sm < 1) {
+        cudaGetLastError();
+        return 1 << 30;
+    }
+    int g = per_sm * sms;
+    std::lock_guard<std::mutex> lock(mu);
+    cache.push_back({{kernel, dev}, g});
+    return g;
+}
 extern "C" int64_t amgh_launch_count(void) { return (int64_t)g_launches.load(); }
 
 // ------------------------------------------------------------------ memory pool
