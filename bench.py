@@ -57,6 +57,8 @@ def parse():
                     help="levels of the Hessian preconditioner (0 = all AMG levels, as in Sec. 5.3)")
     ap.add_argument("--single-step", action="store_true",
                     help="run one untimed step of the first form (for profilers) and print its counters")
+    ap.add_argument("--autotune", type=int, default=0,
+                    help="time the SpMV layouts of every operator at setup (remembered per matrix shape)")
     ap.add_argument("--no-batch", action="store_true",
                     help="skip the batched workload (16 squares, 128 desired states)")
     ap.add_argument("--batch-steps", type=int, default=2)
@@ -164,7 +166,7 @@ def run_amgh(args, rank, world, local):
         else:
             prob = amgh.Problem(w.dim, dev[0], dev[1], dev[2], dev[3], w.beta, dev[4], on_device=True)
         prob.amg_setup(precision=precision, hessian_levels=args.hessian_levels, coarse_max=args.coarse_max,
-                       smooth_degree=args.degree)
+                       smooth_degree=args.degree, autotune=args.autotune)
         if timing:
             prob.kernel_timing(True)
         tols = dict(tol=1e-8, inner_tol=args.inner_tol, mass_tol=args.precond_tol, precond_tol=args.precond_tol)
@@ -272,7 +274,8 @@ def run_batch(args, rank, world, local):
         probs = [amgh.Problem.from_workload(w) for w in ws]
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        batch = amgh.Batch(probs).setup(coarse_max=1000, precision=PRECISION[form], coarse_solve=2)
+        batch = amgh.Batch(probs).setup(coarse_max=1000, precision=PRECISION[form], coarse_solve=2,
+                                        autotune=args.autotune)
         t_setup = time.perf_counter() - t0
         sopts = dict(tol=1e-8, inner_tol=args.inner_tol, mass_tol=args.precond_tol,
                      precond_tol=args.precond_tol, level_fallback=1)
@@ -394,7 +397,7 @@ def single_step(args):
     w = workloads.lshape_checkerboard(N=args.N)
     prob = amgh.Problem.from_workload(w)
     prob.amg_setup(precision=PRECISION[args.forms.split(",")[0]], hessian_levels=args.hessian_levels,
-                   coarse_max=args.coarse_max, smooth_degree=args.degree)
+                   coarse_max=args.coarse_max, smooth_degree=args.degree, autotune=args.autotune)
     u, y, info = prob.solve(tol=1e-8, inner_tol=args.inner_tol, mass_tol=args.precond_tol,
                             precond_tol=args.precond_tol)
     torch.cuda.synchronize()
@@ -427,6 +430,7 @@ def main():
                    "beta": w.beta, "kappa": "8x8 checkerboard {1,1e4}", "tol": 1e-8,
                    "hessian_levels": args.hessian_levels, "coarse_max": args.coarse_max,
                    "chebyshev_degree": args.degree, "inner_tol": args.inner_tol,
+                   "autotune": args.autotune,
                    "precond_and_mass_tol": args.precond_tol,
                    "precision": forms[0], "parallelism": "replicas" if world > 1 else "single",
                    "l2": "256 MB buffer written between timed steps",

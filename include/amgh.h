@@ -88,7 +88,17 @@ typedef struct {
  *                  thread-block cluster; same result to the bit as 0 =
  *                  one launch per smoother step and transfer (the default:
  *                  on GB300 one cluster of 16 SMs is slower than the
- *                  whole-GPU kernels for a 9,585-row level) */
+ *                  whole-GPU kernels for a 9,585-row level)
+ *  autotune        1 = for every state matrix A_l of at least 4096 rows,
+ *                  time four back-to-back FP32 Chebyshev steps in each layout
+ *                  (SELL-32, or 2..32 lanes per CSR row; L2 flushed first
+ *                  for matrices above 32 MB) on this GPU and keep the
+ *                  fastest; the choice is remembered per matrix shape for
+ *                  the process.  Layouts sum
+ *                  a row in different orders, so results may differ in the
+ *                  last bits from the default heuristic (0: by mean row
+ *                  length), which is reproducible across processes.  On the
+ *                  1025^2 L-shape the heuristic's layouts were as fast */
 typedef struct {
     int max_levels;
     int hessian_levels;
@@ -100,6 +110,7 @@ typedef struct {
     int smooth_prolongator;
     int coarse_solve;
     int fuse_coarse;
+    int autotune;
 } amgh_amg_opts;
 
 /* Solve options (Sec. 5.2-5.3).
@@ -158,7 +169,8 @@ typedef struct {
 } amgh_solve_info;
 
 /* Defaults: max_levels 25, hessian_levels 0, theta 0.08, coarse_max 256,
- * Chebyshev degree 2, precision 0, smoothed prolongator, coarse_solve 0, fuse_coarse 0;
+ * Chebyshev degree 2, precision 0, smoothed prolongator, coarse_solve 0, fuse_coarse 0,
+ * autotune 0;
  * tol 1e-8, max_iter 200, inner/mass tol 1e-10, precond 1, ncols 1, caps
  * 1000, precond_tol 0 (= inner_tol), coarse_tol 1e-4, coarse_max_iter 1000,
  * level_fallback 0. */

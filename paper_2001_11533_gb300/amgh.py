@@ -37,7 +37,7 @@ class amgh_amg_opts(C.Structure):
     _fields_ = [("max_levels", C.c_int), ("hessian_levels", C.c_int), ("theta", C.c_double),
                 ("coarse_max", C.c_int), ("smoother", C.c_int), ("smooth_degree", C.c_int),
                 ("precision", C.c_int), ("smooth_prolongator", C.c_int), ("coarse_solve", C.c_int),
-                ("fuse_coarse", C.c_int)]
+                ("fuse_coarse", C.c_int), ("autotune", C.c_int)]
 
 
 class amgh_solve_opts(C.Structure):

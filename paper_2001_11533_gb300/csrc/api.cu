@@ -29,6 +29,7 @@ extern "C" void amgh_amg_opts_default(amgh_amg_opts *o)
     o->smooth_prolongator = 1;
     o->coarse_solve = 0;
     o->fuse_coarse = 0;
+    o->autotune = 0;
 }
 
 extern "C" void amgh_solve_opts_default(amgh_solve_opts *o)
@@ -388,7 +389,7 @@ static int setup_impl(amgh_problem *p)
     // SELL copies of the operators applied in the solve phase, smoother and mass diagonals
     for (int l = 0; l < p->Ls; l++) {
         StateLevel &S = p->sl[l];
-        TRY(prepare_operator(ar, S.A, s));
+        TRY(prepare_tuned(p, ar, S.A, 1));
         TRY(build_lo_parts(ar, S.A, s));
         TRY(prepare_operator(ar, S.My, s));
         if (l + 1 < p->Ls) {
@@ -437,7 +438,8 @@ extern "C" int amgh_amg_setup(amgh_problem *p, const amgh_amg_opts *opts)
     else amgh_amg_opts_default(&o);
     if (o.max_levels < 1 || o.max_levels > AMGH_MAXL || o.smooth_degree < 1 || o.smooth_degree > 16 ||
         o.coarse_max < 1 || !(o.theta >= 0.0) || (o.smoother != 0 && o.smoother != 1) ||
-        o.precision < 0 || o.precision > 2 || o.hessian_levels < 0 || o.coarse_solve < 0 || o.coarse_solve > 2 || (o.fuse_coarse != 0 && o.fuse_coarse != 1))
+        o.precision < 0 || o.precision > 2 || o.hessian_levels < 0 || o.coarse_solve < 0 || o.coarse_solve > 2 || (o.fuse_coarse != 0 && o.fuse_coarse != 1) ||
+        (o.autotune != 0 && o.autotune != 1))
         return AMGH_ERR_INVALID_ARG;
     double t0 = now_s();
     StreamScope ss_(p->stream);

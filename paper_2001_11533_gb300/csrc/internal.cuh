@@ -304,6 +304,9 @@ struct amgh_problem {
 int csr_to_sell(Arena &ar, DevCsr &a, int want32, cudaStream_t s);
 // pick SELL-32 or lanes-per-row CSR from the mean row length and build it
 int prepare_operator(Arena &ar, DevCsr &a, cudaStream_t s, int force_tpr = 0);
+// prepare_operator; for a state matrix A with aopts.autotune set, the layout
+// is the one whose Chebyshev step timed fastest on this GPU
+int prepare_tuned(amgh_problem *p, Arena &ar, DevCsr &a, int is_state_matrix);
 // b = (float)a
 int to_f32(amgh_problem *p, const double *a, int64_t n, float *b);
 // build a.lo32 (after prepare_operator)

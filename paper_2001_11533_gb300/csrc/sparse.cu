@@ -9,6 +9,8 @@
 // consecutive values and 32 consecutive column indices per step (coalesced),
 // and gathers x through the read-only cache.  Entries keep the CSR order, so
 // padding (value 0, column = the row's last column) only adds exact zeros.
+#include <mutex>
+
 #include "internal.cuh"
 #include "spmv.cuh"
 #include "util.cuh"
@@ -435,6 +437,120 @@ int dense_make32(amgh_problem *p, Arena &ar, Dense &d)
 double spmv_bytes(const DevCsr &a, int vb)
 {
     return (double)a.nnz * (vb + 4) + 4.0 * (a.rows + 1) + (double)vb * (a.rows + a.cols);
+}
+
+// ------------------------------------------------------------------ autotuning
+// Rows per lane group (tpr: 1 = SELL-32, else lanes per CSR row) of a state
+// matrix A picked by timing what the V-cycle does with it: four back-to-back
+// FP32 Chebyshev steps (so launch overlap between kernels is part of the
+// measurement), after writing a buffer larger than L2 when the matrix itself
+// would not stay in L2.  The choice is remembered for matrices of the same
+// shape (rows, columns, entries, longest row) for the rest of the process.
+__global__ void k_fill_f32(int n, float v, float *__restrict__ x)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) x[i] = v;
+}
+
+struct TuneKey {
+    int rows, cols, nnz, longest, dev;
+    bool operator==(const TuneKey &o) const
+    {
+        return rows == o.rows && cols == o.cols && nnz == o.nnz && longest == o.longest && dev == o.dev;
+    }
+};
+
+#define TUNE_COLD_BYTES (32ll << 20)
+#define TUNE_FLUSH_BYTES (256ll << 20)
+
+static int tune_tpr(amgh_problem *p, const DevCsr &a, int *best)
+{
+    static std::mutex mu;
+    static std::vector<std::pair<TuneKey, int>> cache;
+    cudaStream_t s = p->stream;
+    int longest = 0, dev = 0;
+    TRY(max_row_length(a, s, &longest));
+    CU(cudaGetDevice(&dev));
+    TuneKey key = {a.rows, a.cols, a.nnz, longest, dev};
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        for (auto &e : cache)
+            if (e.first == key) {
+                *best = e.second;
+                return AMGH_OK;
+            }
+    }
+    int n = a.rows;
+    bool cold = (int64_t)a.nnz * 8 > TUNE_COLD_BYTES;
+    Scratch sc;
+    float *x = nullptr, *xn = nullptr, *d = nullptr, *b = nullptr, *invd = nullptr;
+    unsigned char *flush = nullptr;
+    TRY(sc.alloc(&x, n));
+    TRY(sc.alloc(&xn, n));
+    TRY(sc.alloc(&d, n));
+    TRY(sc.alloc(&b, n));
+    TRY(sc.alloc(&invd, n));
+    if (cold) TRY(sc.alloc(&flush, TUNE_FLUSH_BYTES));
+    for (float *v : {x, xn, d, b, invd}) {
+        k_fill_f32<<<ceil_div(n, 256), 256, 0, s>>>(n, 0.5f, v);
+        LAUNCH_CHECK();
+    }
+    double mean = (double)a.nnz / n;
+    cudaEvent_t e0, e1;
+    CU(cudaEventCreate(&e0));
+    CU(cudaEventCreate(&e1));
+    float best_ms = 1e30f;
+    int pick = 0, st = AMGH_OK;
+    for (int c : {1, 2, 4, 8, 16, 32}) {
+        if (c > 1 && c > 2 * mean) break;
+        DevCsr t;
+        t.rows = a.rows;
+        t.cols = a.cols;
+        t.nnz = a.nnz;
+        t.rp = a.rp;
+        t.ci = a.ci;
+        t.v = a.v;
+        Arena tar;
+        st = prepare_operator(tar, t, s, c);
+        float total = 0.f;
+        for (int rep = 0; rep < 3 && st == AMGH_OK; rep++) {
+            if (cold) CU(cudaMemsetAsync(flush, rep, TUNE_FLUSH_BYTES, s));
+            MatView<float> V = view<float>(t);
+            cudaEventRecord(e0, s);
+            for (int k = 0; k < 4; k++)
+                LAUNCH_TPR(k_cheb_step, float, c, n, s, V, (const float *)invd, (const float *)b,
+                           (const float *)(k & 1 ? xn : x), d, k & 1 ? x : xn, 0.5f, 0.5f, (const int *)nullptr);
+            cudaEventRecord(e1, s);
+            float ms = 0.f;
+            if (cudaEventSynchronize(e1) != cudaSuccess || cudaGetLastError() != cudaSuccess ||
+                cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess)
+                st = AMGH_ERR_CUDA;
+            if (rep > 0) total += ms; // the first repetition warms the caches of a small matrix
+        }
+        if (st == AMGH_OK && total < best_ms) {
+            best_ms = total;
+            pick = c;
+        }
+        cudaStreamSynchronize(s);
+        tar.free_all();
+        if (st) break;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st) return st;
+    *best = pick;
+    std::lock_guard<std::mutex> lock(mu);
+    cache.push_back({key, pick});
+    return AMGH_OK;
+}
+
+#define TUNE_MIN_ROWS 4096
+
+int prepare_tuned(amgh_problem *p, Arena &ar, DevCsr &a, int is_state_matrix)
+{
+    int tpr = 0;
+    if (p->aopts.autotune && is_state_matrix && a.rows >= TUNE_MIN_ROWS && a.nnz > 0) TRY(tune_tpr(p, a, &tpr));
+    return prepare_operator(ar, a, p->stream, tpr);
 }
 
 template <typename T>
