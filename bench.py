@@ -318,7 +318,7 @@ def captured_traffic():
         want = txt.split("source_sha256:")[1].split()[0]
         traffic = float(txt.split("traffic_bytes_per_launch:")[1].split()[0])
         src = b"".join(open(os.path.join(ROOT, "paper_2001_11533_gb300", "csrc", f), "rb").read()
-                       for f in ("sparse.cu", "spmv.cuh"))
+                       for f in ("sparse.cu", "spmv.cuh", "internal.cuh"))
         return traffic if hashlib.sha256(src).hexdigest() == want else None
     except Exception:
         return None
