@@ -45,7 +45,10 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="amgh", choices=["amgh", "reference"])
-    ap.add_argument("--N", type=int, default=1025, help="L-shape grid size (bench workload: 1025)")
+    ap.add_argument("--workload", default="lshape", choices=["lshape", "cube"],
+                    help="lshape: 1025^2 L-shape, checkerboard kappa (the headline workload); cube: 257^3 Kuhn "
+                         "cube, 10 slabs of kappa in {1, 1e6}, beta 1e-6")
+    ap.add_argument("--N", type=int, default=None, help="grid size (default 1025 for lshape, 257 for cube)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--coarse-max", type=int, default=1000,
                     help="AMG stops at or below this many rows (1000: 4 levels, 784k..847 on the L-shape)")
@@ -65,6 +68,31 @@ def parse():
     ap.add_argument("--forms", default="mixed,fp64,refine",
                     help="mixed = FP64 CG + FP32 V-cycles; fp64; refine = FP32 CG in FP64 refinement")
     return ap.parse_args()
+
+
+def make_workload(args):
+    """(workload, config name, kappa description, extra setup options, extra solve options)."""
+    from paper_2001_11533_gb300 import workloads
+    if args.workload == "cube":
+        N = args.N or 257
+        w = workloads.cube_slabs(N=N)
+        # beta = 1e-6 with a 1e6 contrast: drop Hessian levels if the W-cycle turns indefinite,
+        # and solve a coarsest Hessian level too large for the dense inverse by CG
+        return (w, f"cube{N}_slabs", "10 jittered slabs {1,1e6}", dict(coarse_solve=2),
+                dict(level_fallback=1))
+    N = args.N or 1025
+    return w_lshape(N), f"lshape{N}_checkerboard", "8x8 checkerboard {1,1e4}", {}, {}
+
+
+def workload_names(args):
+    if args.workload == "cube":
+        return f"cube{args.N or 257}_slabs", "10 jittered slabs {1,1e6}"
+    return f"lshape{args.N or 1025}_checkerboard", "8x8 checkerboard {1,1e4}"
+
+
+def w_lshape(N):
+    from paper_2001_11533_gb300 import workloads
+    return workloads.lshape_checkerboard(N=N)
 
 
 def dist_env():
@@ -145,7 +173,7 @@ def run_amgh(args, rank, world, local):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    w = workloads.lshape_checkerboard(N=args.N)
+    w, _, _, xsetup, xsolve = make_workload(args)
     host = [np.ascontiguousarray(w.coords, np.float64), np.ascontiguousarray(w.elements, np.int32),
             np.ascontiguousarray(w.dirichlet, np.uint8), np.ascontiguousarray(w.kappa, np.float64),
             np.ascontiguousarray(w.y_d, np.float64)]
@@ -166,10 +194,11 @@ def run_amgh(args, rank, world, local):
         else:
             prob = amgh.Problem(w.dim, dev[0], dev[1], dev[2], dev[3], w.beta, dev[4], on_device=True)
         prob.amg_setup(precision=precision, hessian_levels=args.hessian_levels, coarse_max=args.coarse_max,
-                       smooth_degree=args.degree, autotune=args.autotune)
+                       smooth_degree=args.degree, autotune=args.autotune, **xsetup)
         if timing:
             prob.kernel_timing(True)
-        tols = dict(tol=1e-8, inner_tol=args.inner_tol, mass_tol=args.precond_tol, precond_tol=args.precond_tol)
+        tols = dict(tol=1e-8, inner_tol=args.inner_tol, mass_tol=args.precond_tol, precond_tol=args.precond_tol,
+                    **xsolve)
         if e2e:
             u, y, info = prob.solve_host(**tols)
         else:
@@ -309,10 +338,13 @@ def run_batch(args, rank, world, local):
     return out
 
 
-def captured_traffic():
+def captured_traffic(args):
     """DRAM bytes per launch of the level-0 smoother step from the committed ncu
-    summary, or None if the kernel source changed since that capture."""
+    summary, or None if the kernel source changed since that capture (or the
+    workload is not the captured one)."""
     import hashlib
+    if args.workload != "lshape" or (args.N or 1025) != 1025:
+        return None
     try:
         txt = open(os.path.join(ROOT, "profiles", "k_cheb_step_level0_lshape1025.md")).read()
         want = txt.split("source_sha256:")[1].split()[0]
@@ -324,7 +356,7 @@ def captured_traffic():
         return None
 
 
-def roofline_from(res):
+def roofline_from(res, args):
     ks = res["kstats"]
     peaks = measured_peaks()
     if peaks and peaks.get("hbm_gbs"):
@@ -335,7 +367,7 @@ def roofline_from(res):
         return None
     achieved = ks["bytes"] / (ks["ms"] / 1000.0) / 1e9
     return {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-            "frac": round(achieved / peak, 4), "traffic": captured_traffic(), "peak_source": src,
+            "frac": round(achieved / peak, 4), "traffic": captured_traffic(args), "peak_source": src,
             "kernel": "k_cheb_step on level 0 (Chebyshev smoother step fused with its residual, SELL-32)",
             "launches": ks["launches"], "avg_us": round(1000.0 * ks["ms"] / ks["launches"], 2)}
 
@@ -362,7 +394,7 @@ def run_reference(args, rank, world):
     from oracle import oracle as orc_mod
     from paper_2001_11533_gb300 import workloads
     orc_mod.build()
-    w = workloads.lshape_checkerboard(N=args.N)
+    w, wname, _, _, _ = make_workload(args)
     from oracle.oracle import Oracle
     orc = Oracle(w, hessian_levels=args.hessian_levels, coarse_max=args.coarse_max, degree=args.degree)
     u = np.random.default_rng(0).standard_normal(w.n_vertices)
@@ -379,7 +411,7 @@ def run_reference(args, rank, world):
             "steps": args.steps, "warmup": min(args.warmup, 1), "ms_per_step": 1000.0 * tot / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": f"lshape{args.N}_checkerboard", "m": w.n_interior, "n": w.n_vertices,
+            "config": {"workload": wname, "m": w.n_interior, "n": w.n_vertices,
                        "beta": w.beta, "step": "one fine-level Hessian apply of the FP64 CPU oracle"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": f"{args.steps} Hessian applies (2 AMG-CG solves to 1e-10 each)"},
@@ -394,12 +426,12 @@ def single_step(args):
 
     from paper_2001_11533_gb300 import _build, amgh, workloads
     _build.build()
-    w = workloads.lshape_checkerboard(N=args.N)
+    w, _, _, xsetup, xsolve = make_workload(args)
     prob = amgh.Problem.from_workload(w)
     prob.amg_setup(precision=PRECISION[args.forms.split(",")[0]], hessian_levels=args.hessian_levels,
-                   coarse_max=args.coarse_max, smooth_degree=args.degree, autotune=args.autotune)
+                   coarse_max=args.coarse_max, smooth_degree=args.degree, autotune=args.autotune, **xsetup)
     u, y, info = prob.solve(tol=1e-8, inner_tol=args.inner_tol, mass_tol=args.precond_tol,
-                            precond_tol=args.precond_tol)
+                            precond_tol=args.precond_tol, **xsolve)
     torch.cuda.synchronize()
     print(json.dumps({"info": info, "levels": prob.level_counters(), "sizes": prob.sizes,
                       "launches": amgh.launch_count()}))
@@ -415,6 +447,7 @@ def main():
         run_reference(args, rank, world)
         return
     w, results, e2e = run_amgh(args, rank, world, local)
+    wname, kdesc = workload_names(args)
     batch = None if args.no_batch else run_batch(args, rank, world, local)
     if rank != 0:
         return
@@ -426,8 +459,8 @@ def main():
         "scaling": "weak", "vs_baseline": None,
         "dtype": "f64" if forms[0] == "fp64" else "f32+f64",
         "data": "synthetic",
-        "config": {"workload": f"lshape{args.N}_checkerboard", "m": w.n_interior, "n": w.n_vertices,
-                   "beta": w.beta, "kappa": "8x8 checkerboard {1,1e4}", "tol": 1e-8,
+        "config": {"workload": wname, "m": w.n_interior, "n": w.n_vertices,
+                   "beta": w.beta, "kappa": kdesc, "tol": 1e-8,
                    "hessian_levels": args.hessian_levels, "coarse_max": args.coarse_max,
                    "chebyshev_degree": args.degree, "inner_tol": args.inner_tol,
                    "autotune": args.autotune,
@@ -438,7 +471,7 @@ def main():
         "time_to_1e-8_s": head["ms_per_step"] / 1000.0,
         "gpu_launches": head["gpu_launches"],
         "clocks": head["clocks"],
-        "roofline": roofline_from(head),
+        "roofline": roofline_from(head, args),
         "e2e": e2e,
         "forms": {f: {k: v for k, v in r.items() if k not in ("kstats", "clocks")} for f, r in results.items()},
     }
@@ -448,7 +481,7 @@ def main():
         line["speedup_mixed_vs_fp64"] = results["mixed"]["value"] / results["fp64"]["value"]
     if "refine" in results and "fp64" in results:
         line["speedup_refine_vs_fp64"] = results["refine"]["value"] / results["fp64"]["value"]
-    if world == 1 and not args.no_cpu_baseline:
+    if world == 1 and not args.no_cpu_baseline and args.workload == "lshape":
         n, t = oracle_apply_rate(w, 15.0, args)
         line["cpu_baseline"] = {"value": n / t, "unit": UNIT, "cores": 1, "kind": "oracle",
                                 "sample": f"{n} Hessian applies of the FP64 oracle on the same workload "

@@ -92,23 +92,24 @@ def grid2d(N: int):
 def grid3d_kuhn(N: int):
     """N^3 vertex grid on [0,1]^3 split into 6 (N-1)^3 Kuhn tetrahedra."""
     h = 1.0 / (N - 1)
-    i = np.arange(N, dtype=np.int64)
+    i = np.arange(N, dtype=np.float64) * h
     K, J, I = np.meshgrid(i, i, i, indexing="ij")  # I fastest
-    coords = np.stack([I.ravel() * h, J.ravel() * h, K.ravel() * h], axis=1).astype(np.float64)
-    c = np.arange(N - 1, dtype=np.int64)
+    coords = np.stack([I.ravel(), J.ravel(), K.ravel()], axis=1)
+    del K, J, I
+    it = np.int64 if N ** 3 >= 2 ** 31 else np.int32
+    c = np.arange(N - 1, dtype=it)
     CK, CJ, CI = np.meshgrid(c, c, c, indexing="ij")
     base = (CI + N * CJ + N * N * CK).ravel()
+    del CK, CJ, CI
     step = {0: 1, 1: N, 2: N * N}
-    tets = []
-    for perm in itertools.permutations((0, 1, 2)):
+    elems = np.empty((base.size, 6, 4), dtype=np.int32)  # cube-major, 6 per cube
+    for t, perm in enumerate(itertools.permutations((0, 1, 2))):
         a, b, _ = perm
-        v0 = base
-        v1 = base + step[a]
-        v2 = v1 + step[b]
-        v3 = base + 1 + N + N * N
-        tets.append(np.stack([v0, v1, v2, v3], axis=1))
-    elems = np.stack(tets, axis=1).reshape(-1, 4)  # cube-major, 6 per cube
-    return coords, elems.astype(np.int32)
+        elems[:, t, 0] = base
+        elems[:, t, 1] = base + step[a]
+        elems[:, t, 2] = base + step[a] + step[b]
+        elems[:, t, 3] = base + 1 + N + N * N
+    return coords, elems.reshape(-1, 4)
 
 
 def cube_boundary(N: int) -> np.ndarray:
@@ -166,7 +167,12 @@ def jitter_interior(coords, dirichlet, h, frac, rng):
 
 
 def centroids(coords, elems):
-    return coords[elems].mean(axis=1)
+    """Element centroids, one vertex gather at a time (no (ne, d+1, d) temporary)."""
+    out = coords[elems[:, 0]].copy()
+    for k in range(1, elems.shape[1]):
+        out += coords[elems[:, k]]
+    out /= elems.shape[1]
+    return out
 
 
 def gaussian_bumps(x, centres, amps, width):

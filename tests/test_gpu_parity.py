@@ -390,3 +390,28 @@ def test_full_size_lshape_1025():
     pm = amgh.Problem.from_workload(w).amg_setup(precision=1)
     _, _, info = pm.solve(tol=1e-8)
     assert info["final_relres"] <= 1.5e-8
+
+
+@pytest.mark.slow
+def test_full_size_cube257_slabs():
+    """The large 3D case (257^3 Kuhn cube, 16.6M states, kappa in {1, 1e6} on
+    10 slabs, beta = 1e-6) at full size, checked by properties that hold at any
+    size: at least five AMG levels, both precision forms reach 1e-8 on the true
+    residual and agree with each other, and H is symmetric."""
+    from paper_2001_11533_gb300 import amgh
+    w = W.cube_slabs(N=257)
+    res = {}
+    for prec in (2, 0):
+        p = amgh.Problem.from_workload(w).amg_setup(precision=prec, coarse_solve=2, coarse_max=1000)
+        assert p.sizes["Ls"] >= 5
+        u, _, info = p.solve(tol=1e-8, precond_tol=1e-8, mass_tol=1e-8, level_fallback=1, want_y=False)
+        assert info["final_relres"] <= 1.5e-8
+        res[prec] = host(u)
+        if prec == 0:
+            rng = np.random.default_rng(23)
+            a, b = rng.standard_normal((2, w.n_vertices))
+            p.set_solve_opts(inner_tol=1e-12, mass_tol=1e-12)
+            ha, hb = host(p.hessian_apply(cuda(a))), host(p.hessian_apply(cuda(b)))
+            assert abs(a @ hb - b @ ha) <= 1e-8 * np.linalg.norm(a) * np.linalg.norm(hb)
+        p.close()
+    assert rel(res[2], res[0]) <= 1e-6
