@@ -382,6 +382,10 @@ int64_t amgh_launch_count(void);
 
 void amgh_problem_destroy(amgh_problem *p);
 const char *amgh_status_string(int status);
+/* The last CUDA error met inside the library by any host thread (name, code
+ * and source location), or "" if none; for diagnosing AMGH_ERR_CUDA.  The
+ * string is valid until the calling thread's next call of this function. */
+const char *amgh_last_error(void);
 
 #ifdef __cplusplus
 }

@@ -98,6 +98,7 @@ _SIGS = {
     "amgh_batch_destroy": ([_P], None),
     "amgh_problem_destroy": ([_P], None),
     "amgh_status_string": ([_I], C.c_char_p),
+    "amgh_last_error": ([], C.c_char_p),
 }
 _lib = None
 
@@ -124,6 +125,8 @@ def lib():
 
 def check(code: int, what: str):
     if code != OK:
+        if code == -3:  # CUDA: say which call failed and where
+            what = f"{what} [{lib().amgh_last_error().decode()}]"
         raise AmghError(code, what)
 
 

@@ -20,6 +20,8 @@
 //              A_ij * B_jJ (rounded products, added in that order), so the
 //              Galerkin matrices -- and the strength tests of the next level
 //              -- are the same bits on every run.
+#include <stdio.h>
+
 #include "internal.cuh"
 #include "util.cuh"
 
@@ -439,12 +441,26 @@ int amg_prolongator(amgh_problem *p, Arena &ar, const DevCsr &a, const int *agg,
 #define WARPS_PER_BLOCK 4
 #define WARP_PATH_MAX_ROWS 65536
 
-// path of row i: 0 = one thread with a global hash table, 1 = one warp with a
-// shared hash table (u <= WARP_TS / 2), 2 = one block with a dense shared
-// accumulator over all columns (long rows of products with few columns)
+// path of row i (u = its candidate products): 0 = one thread with a global
+// hash table, 1 = one warp with a shared hash table (u <= WARP_TS / 2), 2 =
+// one block with a dense shared accumulator over all columns (u > WARP_TS / 2,
+// few columns), 3 = one block with a shared hash table (u > WARP_TS / 2, many
+// columns, few rows).  Small products (n <= WARP_PATH_MAX_ROWS) use the shared
+// paths throughout.  In large products a thread per row with a global table
+// wins while the tables stay small; rows with 64 < u <= WARP_TS / 2 are marked
+// 4 here and go to the warp path only if all such tables together would exceed
+// GLOBAL_TABLE_MAX_BYTES (the 3D fine levels).
+#define BLOCK_HASH_MAX_U 8192
+#define GLOBAL_TABLE_MAX_BYTES (8ll << 30)
+
+// set when a row reaches a SpGEMM path whose table it would overflow; the
+// row is skipped and the host reports an error
+__device__ int g_spgemm_bad = 0;
+
 __global__ void k_gemm_ub(int n, const int *__restrict__ arp, const int *__restrict__ aci,
-                          const int *__restrict__ brp, long long *__restrict__ ub, int *__restrict__ small,
-                          int *__restrict__ big, int use_warp, int use_dense)
+                          const int *__restrict__ brp, long long *__restrict__ ub, int *__restrict__ path_of,
+                          int small_n, int use_dense, int *__restrict__ umax3,
+                          unsigned long long *__restrict__ slots4)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -453,12 +469,31 @@ __global__ void k_gemm_ub(int n, const int *__restrict__ arp, const int *__restr
         int j = aci[k];
         u += brp[j + 1] - brp[j];
     }
-    int path = use_warp && u <= WARP_TS / 2 ? 1 : (use_dense && u > WARP_TS / 2 ? 2 : 0);
-    small[i] = path;
-    big[i] = path == 2;
     long long t = 2;
     while (t < 2 * u) t <<= 1;
-    ub[i] = (u > 0 && path == 0) ? t : 0;
+    int path = 0;
+    if (u <= WARP_TS / 2) path = small_n ? 1 : (u > 64 ? 4 : 0);
+    else if (use_dense) path = 2;
+    else if (small_n && u <= BLOCK_HASH_MAX_U) path = 3;
+    path_of[i] = path;
+    if (path == 3) atomicMax(umax3, (int)u);
+    if (path == 4) atomicAdd(slots4, (unsigned long long)t);
+    ub[i] = (u > 0 && (path == 0 || path == 4)) ? t : 0;
+}
+
+// settle the rows marked 4: warp path (no global table) or thread path
+__global__ void k_gemm_settle(int n, int to_warp, int *__restrict__ path_of, long long *__restrict__ ub)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n || path_of[i] != 4) return;
+    path_of[i] = to_warp ? 1 : 0;
+    if (to_warp) ub[i] = 0;
+}
+
+__global__ void k_is_path(int n, const int *__restrict__ path_of, int want, int *__restrict__ flag)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) flag[i] = path_of[i] == want;
 }
 
 __global__ void k_list(int n, const int *__restrict__ flag, const int *__restrict__ pos, int *__restrict__ list)
@@ -614,7 +649,7 @@ __global__ void k_gemm_out(int n, const long long *__restrict__ toff, const int 
 __global__ void k_gemm_warp(int n, const int *__restrict__ arp, const int *__restrict__ aci,
                             const double *__restrict__ av, const int *__restrict__ brp,
                             const int *__restrict__ bci, const double *__restrict__ bv,
-                            const int *__restrict__ small, int phase, int *__restrict__ cnt,
+                            const int *__restrict__ list, int phase, int *__restrict__ cnt,
                             const int *__restrict__ crp, int *__restrict__ cci, double *__restrict__ cv)
 {
     extern __shared__ unsigned char smem_raw[];
@@ -622,8 +657,9 @@ __global__ void k_gemm_warp(int n, const int *__restrict__ arp, const int *__res
     int *keys = (int *)smem_raw + w * WARP_TS;
     double *vals = (double *)((int *)smem_raw + WARPS_PER_BLOCK * WARP_TS) + w * WARP_TS;
     double *stage = (double *)((int *)smem_raw + WARPS_PER_BLOCK * WARP_TS) + WARPS_PER_BLOCK * WARP_TS + w * 32;
-    int i = blockIdx.x * WARPS_PER_BLOCK + w;
-    if (i >= n || small[i] != 1) return; // warp-uniform
+    int li = blockIdx.x * WARPS_PER_BLOCK + w;
+    if (li >= n) return; // warp-uniform; n = number of listed rows
+    int i = list[li];
     // table of 2^ceil(log2(2u)) slots (u = candidate count of the row)
     int u = 0;
     for (int k = arp[i] + lane; k < arp[i + 1]; k += 32) {
@@ -633,6 +669,10 @@ __global__ void k_gemm_warp(int n, const int *__restrict__ arp, const int *__res
     for (int o = 16; o > 0; o >>= 1) u += __shfl_xor_sync(0xffffffffu, u, o);
     unsigned ts = 2;
     while ((int)ts < 2 * u) ts <<= 1;
+    if (ts > WARP_TS) { // warp-uniform
+        if (lane == 0) atomicExch(&g_spgemm_bad, 1);
+        return;
+    }
     const unsigned mask = ts - 1;
     for (unsigned t = lane; t < ts; t += 32) keys[t] = -1;
     __syncwarp();
@@ -697,6 +737,122 @@ __global__ void k_gemm_warp(int n, const int *__restrict__ arp, const int *__res
     }
 }
 
+// block shared-hash path: one block per listed row, the row's products taken
+// one entry a_ik at a time (a barrier between entries) with row k of B spread
+// over the threads -- each column occurs once in a row of B, so every entry
+// receives its products in the sequential order.  Then the occupied slots are
+// compacted to the front of the table (chunk by chunk: all reads of a chunk
+// before its writes, which only land on slots already read) and sorted by
+// column (bitonic network over the next power of two), phase 0 counting and
+// phase 1 writing the row.
+#define BH_TPB 256
+__global__ void __launch_bounds__(BH_TPB) k_gemm_bhash(int nlist, const int *__restrict__ list, int ts,
+                                                       const int *__restrict__ arp, const int *__restrict__ aci,
+                                                       const double *__restrict__ av, const int *__restrict__ brp,
+                                                       const int *__restrict__ bci, const double *__restrict__ bv,
+                                                       int phase, int *__restrict__ cnt, const int *__restrict__ crp,
+                                                       int *__restrict__ cci, double *__restrict__ cv)
+{
+    extern __shared__ unsigned char smem_raw[];
+    __shared__ int wcount[BH_TPB / 32];
+    double *vals = (double *)smem_raw;
+    int *keys = (int *)(vals + ts);
+    const unsigned mask = (unsigned)ts - 1;
+    int i = list[blockIdx.x];
+    int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    if (t == 0) {
+        long long u = 0;
+        for (int k = arp[i]; k < arp[i + 1]; k++) u += brp[aci[k] + 1] - brp[aci[k]];
+        wcount[0] = 2 * u <= ts;
+    }
+    __syncthreads();
+    if (!wcount[0]) { // block-uniform
+        if (t == 0) atomicExch(&g_spgemm_bad, 1);
+        return;
+    }
+    __syncthreads();
+    for (int q = t; q < ts; q += BH_TPB) keys[q] = -1;
+    __syncthreads();
+    for (int k = arp[i]; k < arp[i + 1]; k++) {
+        int j = aci[k];
+        double aij = av[k];
+        for (int q = brp[j] + t; q < brp[j + 1]; q += BH_TPB) {
+            int J = bci[q];
+            double prod = __dmul_rn(aij, bv[q]);
+            unsigned h = hslot(J, mask);
+            for (;;) {
+                int old = atomicCAS(&keys[h], -1, J);
+                if (old == -1) {
+                    vals[h] = __dadd_rn(0.0, prod);
+                    break;
+                }
+                if (old == J) {
+                    vals[h] = __dadd_rn(vals[h], prod);
+                    break;
+                }
+                h = (h + 1) & mask;
+            }
+        }
+        __syncthreads();
+    }
+    // compact occupied slots to the front, one chunk of BH_TPB slots at a time
+    int c = 0;
+    for (int base = 0; base < ts; base += BH_TPB) {
+        int slot = base + t;
+        int key = keys[slot];
+        double val = vals[slot];
+        bool occ = key >= 0;
+        unsigned bal = __ballot_sync(0xffffffffu, occ);
+        if (lane == 0) wcount[w] = __popc(bal);
+        __syncthreads();
+        int before = 0, chunk = 0;
+        for (int q = 0; q < BH_TPB / 32; q++) {
+            if (q < w) before += wcount[q];
+            chunk += wcount[q];
+        }
+        int pos = c + before + __popc(bal & ((1u << lane) - 1));
+        __syncthreads(); // every read of this chunk is done
+        if (occ) {
+            keys[pos] = key;
+            vals[pos] = val;
+        }
+        c += chunk;
+        __syncthreads();
+    }
+    if (phase == 0) {
+        if (t == 0) cnt[i] = c;
+        return;
+    }
+    // bitonic sort of the c entries by column (padding sorts last)
+    int P = 1;
+    while (P < c) P <<= 1;
+    for (int q = c + t; q < P; q += BH_TPB) keys[q] = 0x7fffffff;
+    __syncthreads();
+    for (int kk = 2; kk <= P; kk <<= 1)
+        for (int jj = kk >> 1; jj > 0; jj >>= 1) {
+            for (int a = t; a < P; a += BH_TPB) {
+                int b = a ^ jj;
+                if (b > a) {
+                    bool up = (a & kk) == 0;
+                    int ka = keys[a], kb = keys[b];
+                    if ((ka > kb) == up) {
+                        keys[a] = kb;
+                        keys[b] = ka;
+                        double tv = vals[a];
+                        vals[a] = vals[b];
+                        vals[b] = tv;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    int base = crp[i];
+    for (int q = t; q < c; q += BH_TPB) {
+        cci[base + q] = keys[q];
+        cv[base + q] = vals[q];
+    }
+}
+
 static size_t warp_smem() { return (size_t)WARPS_PER_BLOCK * WARP_TS * (sizeof(int) + sizeof(double)) +
                                   (size_t)WARPS_PER_BLOCK * 32 * sizeof(double); }
 
@@ -710,58 +866,106 @@ int spgemm(amgh_problem *p, Arena &ar, const DevCsr &a, const DevCsr &b, DevCsr 
     CU(cudaFuncSetAttribute(k_gemm_warp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)warp_smem()));
     Scratch sc;
     long long *ub = nullptr, *toff = nullptr;
-    int *cnt = nullptr, *tkey = nullptr, *small = nullptr, *big = nullptr, *bpos = nullptr, *blist = nullptr;
+    int *cnt = nullptr, *tkey = nullptr, *path = nullptr, *flag = nullptr, *pos = nullptr, *umax = nullptr;
+    unsigned long long *slots4 = nullptr;
     double *tval = nullptr;
     TRY(sc.alloc(&ub, n + 1));
     TRY(sc.alloc(&toff, n + 1));
     TRY(sc.alloc(&cnt, n + 1));
-    TRY(sc.alloc(&small, n + 1));
-    TRY(sc.alloc(&big, n + 1));
-    TRY(sc.alloc(&bpos, n + 1));
-    int nb = ceil_div(n, 128), nw = ceil_div(n, WARPS_PER_BLOCK);
+    TRY(sc.alloc(&path, n + 1));
+    TRY(sc.alloc(&flag, n + 1));
+    TRY(sc.alloc(&pos, n + 1));
+    TRY(sc.alloc(&umax, 1));
+    TRY(sc.alloc(&slots4, 1));
+    int nb = ceil_div(n, 128);
     int use_dense = b.cols <= DENSE_ROW_MAX_COLS;
     size_t dsmem = (size_t)b.cols * (sizeof(double) + 1);
-    if (use_dense && dsmem > 48 * 1024)
-        CU(cudaFuncSetAttribute(k_gemm_dense, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsmem));
-    k_gemm_ub<<<nb, 128, 0, s>>>(n, a.rp, a.ci, b.rp, ub, small, big, n <= WARP_PATH_MAX_ROWS, use_dense);
+    // The dynamic shared memory limit is per function, and setups may run on
+    // several host threads at once: raise it once to the most any launch of
+    // the kernel can use (the 48 KB default counts static memory too).
+    CU(cudaFuncSetAttribute(k_gemm_dense, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                            (int)((size_t)DENSE_ROW_MAX_COLS * (sizeof(double) + 1))));
+    CU(cudaFuncSetAttribute(k_gemm_bhash, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                            (int)((size_t)2 * BLOCK_HASH_MAX_U * (sizeof(double) + sizeof(int)))));
+    CU(cudaMemsetAsync(umax, 0, sizeof(int), s));
+    CU(cudaMemsetAsync(slots4, 0, sizeof(unsigned long long), s));
+    k_gemm_ub<<<nb, 128, 0, s>>>(n, a.rp, a.ci, b.rp, ub, path, n <= WARP_PATH_MAX_ROWS, use_dense, umax, slots4);
     LAUNCH_CHECK();
-    int nbig = 0;
-    TRY(exclusive_scan<int>(big, bpos, n, s, &nbig));
-    if (nbig > 0) {
-        TRY(sc.alloc(&blist, nbig));
-        k_list<<<ceil_div(n, 256), 256, 0, s>>>(n, big, bpos, blist);
+    {
+        unsigned long long sl = 0;
+        CU(cudaMemcpyAsync(&sl, slots4, sizeof(sl), cudaMemcpyDeviceToHost, s));
+        CU(cudaStreamSynchronize(s));
+        int to_warp = (long long)sl * (long long)(sizeof(int) + sizeof(double)) > GLOBAL_TABLE_MAX_BYTES;
+        k_gemm_settle<<<ceil_div(n, 256), 256, 0, s>>>(n, to_warp, path, ub);
         LAUNCH_CHECK();
+    }
+    // row lists of the warp (1), dense (2) and block-hash (3) paths
+    int nlist[4] = {0, 0, 0, 0};
+    int *list[4] = {nullptr, nullptr, nullptr, nullptr};
+    for (int q = 1; q <= 3; q++) {
+        k_is_path<<<ceil_div(n, 256), 256, 0, s>>>(n, path, q, flag);
+        LAUNCH_CHECK();
+        TRY(exclusive_scan<int>(flag, pos, n, s, &nlist[q]));
+        if (nlist[q] > 0) {
+            TRY(sc.alloc(&list[q], nlist[q]));
+            k_list<<<ceil_div(n, 256), 256, 0, s>>>(n, flag, pos, list[q]);
+            LAUNCH_CHECK();
+        }
+    }
+    int ts3 = 0;
+    size_t bsmem = 0;
+    if (nlist[3] > 0) {
+        int um = 0;
+        CU(cudaMemcpyAsync(&um, umax, sizeof(int), cudaMemcpyDeviceToHost, s));
+        CU(cudaStreamSynchronize(s));
+        ts3 = BH_TPB;
+        while (ts3 < 2 * um) ts3 <<= 1;
+        bsmem = (size_t)ts3 * (sizeof(double) + sizeof(int));
     }
     long long tot = 0;
     TRY(exclusive_scan<long long>(ub, toff, n, s, &tot));
     TRY(sc.alloc(&tkey, tot));
     TRY(sc.alloc(&tval, tot));
     if (tot > 0) CU(cudaMemsetAsync(tkey, 0xff, sizeof(int) * (size_t)tot, s));
-    k_gemm_hash<<<nb, 128, 0, s>>>(n, a.rp, a.ci, a.v, b.rp, b.ci, b.v, toff, small, tkey, tval, cnt);
+    k_gemm_hash<<<nb, 128, 0, s>>>(n, a.rp, a.ci, a.v, b.rp, b.ci, b.v, toff, path, tkey, tval, cnt);
     LAUNCH_CHECK();
-    k_gemm_warp<<<nw, 32 * WARPS_PER_BLOCK, warp_smem(), s>>>(n, a.rp, a.ci, a.v, b.rp, b.ci, b.v, small, 0, cnt,
-                                                              nullptr, nullptr, nullptr);
-    LAUNCH_CHECK();
-    if (nbig > 0) {
-        k_gemm_dense<<<nbig, DENSE_ROW_TPB, dsmem, s>>>(nbig, blist, b.cols, a.rp, a.ci, a.v, b.rp, b.ci, b.v, 0,
-                                                          cnt, nullptr, nullptr, nullptr);
-        LAUNCH_CHECK();
-    }
+    auto launch_lists = [&](int phase, int *cnt_, const int *crp, int *cci, double *cv) -> int {
+        if (nlist[1] > 0) {
+            k_gemm_warp<<<ceil_div(nlist[1], WARPS_PER_BLOCK), 32 * WARPS_PER_BLOCK, warp_smem(), s>>>(
+                nlist[1], a.rp, a.ci, a.v, b.rp, b.ci, b.v, list[1], phase, cnt_, crp, cci, cv);
+            LAUNCH_CHECK();
+        }
+        if (nlist[2] > 0) {
+            k_gemm_dense<<<nlist[2], DENSE_ROW_TPB, dsmem, s>>>(nlist[2], list[2], b.cols, a.rp, a.ci, a.v, b.rp,
+                                                                 b.ci, b.v, phase, cnt_, crp, cci, cv);
+            LAUNCH_CHECK();
+        }
+        if (nlist[3] > 0) {
+            k_gemm_bhash<<<nlist[3], BH_TPB, bsmem, s>>>(nlist[3], list[3], ts3, a.rp, a.ci, a.v, b.rp, b.ci, b.v,
+                                                          phase, cnt_, crp, cci, cv);
+            LAUNCH_CHECK();
+        }
+        return AMGH_OK;
+    };
+    TRY(launch_lists(0, cnt, nullptr, nullptr, nullptr));
     TRY(ar.alloc(&c.rp, n + 1));
     int nnz = 0;
     TRY(exclusive_scan<int>(cnt, c.rp, n, s, &nnz));
     c.nnz = nnz;
     TRY(ar.alloc(&c.ci, nnz));
     TRY(ar.alloc(&c.v, nnz));
-    k_gemm_out<<<nb, 128, 0, s>>>(n, toff, small, tkey, tval, c.rp, c.ci, c.v);
+    k_gemm_out<<<nb, 128, 0, s>>>(n, toff, path, tkey, tval, c.rp, c.ci, c.v);
     LAUNCH_CHECK();
-    k_gemm_warp<<<nw, 32 * WARPS_PER_BLOCK, warp_smem(), s>>>(n, a.rp, a.ci, a.v, b.rp, b.ci, b.v, small, 1,
-                                                              nullptr, c.rp, c.ci, c.v);
-    LAUNCH_CHECK();
-    if (nbig > 0) {
-        k_gemm_dense<<<nbig, DENSE_ROW_TPB, dsmem, s>>>(nbig, blist, b.cols, a.rp, a.ci, a.v, b.rp, b.ci, b.v, 1,
-                                                          nullptr, c.rp, c.ci, c.v);
-        LAUNCH_CHECK();
+    TRY(launch_lists(1, nullptr, c.rp, c.ci, c.v));
+    int bad = 0;
+    CU(cudaMemcpyFromSymbolAsync(&bad, g_spgemm_bad, sizeof(int), 0, cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
+    if (bad) {
+        int zero = 0;
+        CU(cudaMemcpyToSymbolAsync(g_spgemm_bad, &zero, sizeof(int), 0, cudaMemcpyHostToDevice, s));
+        CU(cudaStreamSynchronize(s));
+        amgh_note_error(0, __FILE__, __LINE__);
+        return AMGH_ERR_CUDA;
     }
     CU(cudaStreamSynchronize(s));
     return AMGH_OK;

@@ -245,7 +245,10 @@ int dense_spd_inverse(amgh_problem *p, double *g, int n, double *inv, int *info_
     double *W = nullptr;
     TRY(sc.alloc(&W, (int64_t)n * n));
     size_t shm = sizeof(double) * (size_t)n * TRINV_WARPS;
-    if (shm > 48 * 1024) CU(cudaFuncSetAttribute(k_trinv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+    // per-function limit, set to the largest case (n <= AMGH_DENSE_MAX) so that
+    // setups on several host threads never lower it under one another
+    CU(cudaFuncSetAttribute(k_trinv, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                            (int)(sizeof(double) * (size_t)AMGH_DENSE_MAX * TRINV_WARPS)));
     k_trinv<<<ceil_div(n, TRINV_WARPS), 32 * TRINV_WARPS, shm, s>>>(n, g, W);
     LAUNCH_CHECK();
     int tiles = ceil_div(n, TILE);

@@ -16,10 +16,14 @@
 #define AMGH_SELL_C 32
 
 // ------------------------------------------------------------------ errors
+// record the CUDA error (code, file, line) for amgh_last_error
+void amgh_note_error(int code, const char *file, int line);
+void amgh_note_msg(const char *msg);
 #define CU(call)                                                               \
     do {                                                                       \
         cudaError_t e_ = (call);                                               \
         if (e_ != cudaSuccess) {                                               \
+            amgh_note_error((int)e_, __FILE__, __LINE__);                      \
             return e_ == cudaErrorMemoryAllocation ? AMGH_ERR_OOM : AMGH_ERR_CUDA; \
         }                                                                      \
     } while (0)
@@ -67,11 +71,14 @@ inline void pdl_launch(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t s
     (void)cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
 }
 
-#define LAUNCH_CHECK()                         \
-    do {                                       \
-        amgh_count_launch();                   \
-        cudaError_t e_ = cudaGetLastError();   \
-        if (e_ != cudaSuccess) return AMGH_ERR_CUDA; \
+#define LAUNCH_CHECK()                                   \
+    do {                                                 \
+        amgh_count_launch();                             \
+        cudaError_t e_ = cudaGetLastError();             \
+        if (e_ != cudaSuccess) {                         \
+            amgh_note_error((int)e_, __FILE__, __LINE__); \
+            return AMGH_ERR_CUDA;                        \
+        }                                                \
     } while (0)
 
 static inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }

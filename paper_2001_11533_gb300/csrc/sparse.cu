@@ -126,12 +126,60 @@ __global__ void k_transpose_fill(int rows, const int *__restrict__ rp, const int
     }
 }
 
-// sort every row of (ci, v) by column (insertion sort; rows are short)
+// Sort every row of (ci, v) by column: rows of at most 32 entries (or more
+// than SORT_WARP_MAX) by one thread with insertion sort, the others by one
+// warp with a bitonic network in shared memory.  Columns within a row are
+// distinct, so the result does not depend on the order of equal keys.
+#define SORT_WARP_MAX 1024
+#define SORT_WARPS 4
+__global__ void k_sort_rows_warp(int rows, const int *__restrict__ rp, int *__restrict__ ci, double *__restrict__ v)
+{
+    __shared__ int ks[SORT_WARPS][SORT_WARP_MAX];
+    __shared__ double vs[SORT_WARPS][SORT_WARP_MAX];
+    int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int r = blockIdx.x * SORT_WARPS + w;
+    if (r >= rows) return; // warp-uniform
+    int b = rp[r], L = rp[r + 1] - b;
+    if (L <= 32 || L > SORT_WARP_MAX) return;
+    int P = 64;
+    while (P < L) P <<= 1;
+    int *key = ks[w];
+    double *val = vs[w];
+    for (int q = lane; q < P; q += 32) {
+        key[q] = q < L ? ci[b + q] : 0x7fffffff;
+        val[q] = q < L ? v[b + q] : 0.0;
+    }
+    __syncwarp();
+    for (int kk = 2; kk <= P; kk <<= 1)
+        for (int jj = kk >> 1; jj > 0; jj >>= 1) {
+            for (int a = lane; a < P; a += 32) {
+                int c = a ^ jj;
+                if (c > a) {
+                    bool up = (a & kk) == 0;
+                    int ka = key[a], kc = key[c];
+                    if ((ka > kc) == up) {
+                        key[a] = kc;
+                        key[c] = ka;
+                        double t = val[a];
+                        val[a] = val[c];
+                        val[c] = t;
+                    }
+                }
+            }
+            __syncwarp();
+        }
+    for (int q = lane; q < L; q += 32) {
+        ci[b + q] = key[q];
+        v[b + q] = val[q];
+    }
+}
+
 __global__ void k_sort_rows(int rows, const int *__restrict__ rp, int *__restrict__ ci, double *__restrict__ v)
 {
     int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= rows) return;
     int b = rp[r], e = rp[r + 1];
+    if (e - b > 32 && e - b <= SORT_WARP_MAX) return; // the warp kernel's rows
     for (int k = b + 1; k < e; k++) {
         int c = ci[k];
         double x = v[k];
@@ -171,6 +219,8 @@ int csr_transpose(Arena &ar, const DevCsr &a, DevCsr &t, cudaStream_t s)
     }
     if (t.rows > 0) {
         k_sort_rows<<<ceil_div(t.rows, 128), 128, 0, s>>>(t.rows, t.rp, t.ci, t.v);
+        LAUNCH_CHECK();
+        k_sort_rows_warp<<<ceil_div(t.rows, SORT_WARPS), 32 * SORT_WARPS, 0, s>>>(t.rows, t.rp, t.ci, t.v);
         LAUNCH_CHECK();
     }
     CU(cudaStreamSynchronize(s));

@@ -1,5 +1,8 @@
 // util.cu -- arena, launch counting, scans and kernel timing shared by the
 // amgh translation units.
+#include <stdio.h>
+#include <string.h>
+
 #include <atomic>
 #include <mutex>
 
@@ -14,6 +17,31 @@ void amgh_count_launch(int n)
     if (!g_capturing) g_launches += n;
 }
 void amgh_set_capturing(int on) { g_capturing = on; }
+
+static std::mutex g_err_mu;
+static char g_last_error[256] = "";
+static thread_local char g_err_copy[256];
+
+void amgh_note_error(int code, const char *file, int line)
+{
+    const char *base = strrchr(file, '/');
+    std::lock_guard<std::mutex> lock(g_err_mu);
+    snprintf(g_last_error, sizeof(g_last_error), "%s (%d) at %s:%d", cudaGetErrorName((cudaError_t)code), code,
+             base ? base + 1 : file, line);
+}
+
+void amgh_note_msg(const char *msg)
+{
+    std::lock_guard<std::mutex> lock(g_err_mu);
+    snprintf(g_last_error, sizeof(g_last_error), "%s", msg);
+}
+
+extern "C" const char *amgh_last_error(void)
+{
+    std::lock_guard<std::mutex> lock(g_err_mu);
+    memcpy(g_err_copy, g_last_error, sizeof(g_err_copy));
+    return g_err_copy;
+}
 
 // blocks of `block` threads of `kernel` that fit on the current device at once
 // (occupancy x SM count), cached per kernel and device
