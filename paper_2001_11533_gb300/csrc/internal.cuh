@@ -164,6 +164,9 @@ struct DevCsr {
     int *sl_ptr = nullptr, *sl_ci = nullptr;
     double *sl_v = nullptr;
     float *sl_v32 = nullptr;
+    // uniform-width SELL only: column - row as int16 when every entry fits
+    // (2 instead of 4 bytes of index per stored entry)
+    short *sl_ci16 = nullptr;
 };
 
 // ------------------------------------------------------------------ reductions

@@ -63,6 +63,25 @@ __global__ void k_fill_int(int n, int v, int *__restrict__ x)
     if (i < n) x[i] = v;
 }
 
+// column - row of every stored entry of a uniform-width SELL matrix as int16;
+// *bad set if some entry of a real row does not fit (padding rows store 0)
+__global__ void k_sell_delta(int rows, int nslices, int w, const int *__restrict__ sci, short *__restrict__ d16,
+                             int *__restrict__ bad)
+{
+    int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= nslices * 32) return;
+    int64_t base = (int64_t)(r >> 5) * 32 * w + (r & 31);
+    for (int j = 0; j < w; j++) {
+        int64_t k = base + 32 * j;
+        int d = r < rows ? sci[k] - r : 0;
+        if (d < -32768 || d > 32767) {
+            atomicOr(bad, 1);
+            d = 0;
+        }
+        d16[k] = (short)d;
+    }
+}
+
 int csr_to_sell(Arena &ar, DevCsr &a, int /*want32*/, cudaStream_t s)
 {
     a.nslices = ceil_div(a.rows, 32);
@@ -89,6 +108,7 @@ int csr_to_sell(Arena &ar, DevCsr &a, int /*want32*/, cudaStream_t s)
         a.ellw = widest;
     }
     a.sell_nnz = total;
+    a.sl_ci16 = nullptr;
     TRY(ar.alloc(&a.sl_ci, total));
     TRY(ar.alloc(&a.sl_v, total));
     TRY(ar.alloc(&a.sl_v32, total));
@@ -96,6 +116,20 @@ int csr_to_sell(Arena &ar, DevCsr &a, int /*want32*/, cudaStream_t s)
         k_sell_fill<<<ceil_div(ns * 32, 256), 256, 0, s>>>(a.rows, a.rp, a.ci, a.v, a.sl_ptr, a.sl_ci,
                                                           a.sl_v, a.sl_v32, ns);
         LAUNCH_CHECK();
+    }
+    // int16 column offsets for uniform-width SELL when every entry fits
+    if (a.ellw > 0 && ns > 0) {
+        int *bad = nullptr;
+        short *d16 = nullptr;
+        TRY(sc.alloc(&bad, 1));
+        TRY(ar.alloc(&d16, total));
+        CU(cudaMemsetAsync(bad, 0, sizeof(int), s));
+        k_sell_delta<<<ceil_div(ns * 32, 256), 256, 0, s>>>(a.rows, ns, a.ellw, a.sl_ci, d16, bad);
+        LAUNCH_CHECK();
+        int hb = 0;
+        CU(cudaMemcpyAsync(&hb, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
+        CU(cudaStreamSynchronize(s));
+        if (!hb) a.sl_ci16 = d16;
     }
     CU(cudaStreamSynchronize(s));
     return AMGH_OK;
@@ -486,6 +520,9 @@ int dense_make32(amgh_problem *p, Arena &ar, Dense &d)
 
 double spmv_bytes(const DevCsr &a, int vb)
 {
+    // index bytes per entry and slice / row pointers as the kernels read them
+    if (a.tpr <= 1 && a.ellw > 0)
+        return (double)a.nnz * (vb + (a.sl_ci16 ? 2 : 4)) + (double)vb * (a.rows + a.cols);
     return (double)a.nnz * (vb + 4) + 4.0 * (a.rows + 1) + (double)vb * (a.rows + a.cols);
 }
 

@@ -20,6 +20,7 @@ struct MatView {
     const int *ptr; // SELL slice pointers (tpr = 1) or CSR row pointers
     const int *ci;
     const T *v;
+    const short *d16; // SELL: column - row as int16 (DevCsr::sl_ci16), else null
 };
 
 template <typename T>
@@ -27,14 +28,14 @@ inline MatView<T> view(const DevCsr &a);
 template <>
 inline MatView<double> view<double>(const DevCsr &a)
 {
-    if (a.tpr <= 1) return {a.rows, a.cols, 1, a.wmax, a.ellw, a.sl_ptr, a.sl_ci, a.sl_v};
-    return {a.rows, a.cols, a.tpr, a.wmax, 0, a.rp, a.ci, a.v};
+    if (a.tpr <= 1) return {a.rows, a.cols, 1, a.wmax, a.ellw, a.sl_ptr, a.sl_ci, a.sl_v, a.sl_ci16};
+    return {a.rows, a.cols, a.tpr, a.wmax, 0, a.rp, a.ci, a.v, nullptr};
 }
 template <>
 inline MatView<float> view<float>(const DevCsr &a)
 {
-    if (a.tpr <= 1) return {a.rows, a.cols, 1, a.wmax, a.ellw, a.sl_ptr, a.sl_ci, a.sl_v32};
-    return {a.rows, a.cols, a.tpr, a.wmax, 0, a.rp, a.ci, a.v32};
+    if (a.tpr <= 1) return {a.rows, a.cols, 1, a.wmax, a.ellw, a.sl_ptr, a.sl_ci, a.sl_v32, a.sl_ci16};
+    return {a.rows, a.cols, a.tpr, a.wmax, 0, a.rp, a.ci, a.v32, nullptr};
 }
 
 // Rows of at most ROW_UNROLL entries per lane are read with all their value
@@ -42,6 +43,13 @@ inline MatView<float> view<float>(const DevCsr &a)
 // order as the loop (so the result does not depend on the path): two memory
 // round trips per row instead of one per group of four entries.
 #define ROW_UNROLL 8
+
+// column of stored entry k of `row`
+template <typename T>
+__device__ __forceinline__ int col_of(const MatView<T> &m, int row, int k)
+{
+    return m.d16 ? row + (int)m.d16[k] : m.ci[k];
+}
 
 // entry range of this lane in `row` (SELL: stride 32 inside the slice; CSR:
 // stride STEP = TPR inside the row)
@@ -94,7 +102,7 @@ __device__ __forceinline__ T row_sum(const MatView<T> &m, int row, F xf)
             for (int j = 0; j < ROW_UNROLL; j++) {
                 bool ok = k + STEP * j < end;
                 vv[j] = ok ? m.v[k + STEP * j] : (T)0;
-                cc[j] = ok ? m.ci[k + STEP * j] : 0;
+                cc[j] = ok ? col_of(m, row, k + STEP * j) : 0;
             }
             T xv[ROW_UNROLL];
 #pragma unroll
@@ -104,7 +112,7 @@ __device__ __forceinline__ T row_sum(const MatView<T> &m, int row, F xf)
                 if (k + STEP * j < end) acc += vv[j] * xv[j];
         } else {
 #pragma unroll 4
-            for (; k < end; k += STEP) acc += m.v[k] * xf(m.ci[k]);
+            for (; k < end; k += STEP) acc += m.v[k] * xf(col_of(m, row, k));
         }
     }
     if (TPR > 1) {
@@ -146,7 +154,7 @@ __device__ __forceinline__ DF row_sum_df_acc(const MatView<float> &m, const floa
                 bool ok = k + STEP * j < end;
                 vh[j] = ok ? m.v[k + STEP * j] : 0.f;
                 vl[j] = ok ? lo[k + STEP * j] : 0.f;
-                cc[j] = ok ? m.ci[k + STEP * j] : 0;
+                cc[j] = ok ? col_of(m, row, k + STEP * j) : 0;
             }
             Z zv[ROW_UNROLL];
 #pragma unroll
@@ -156,7 +164,7 @@ __device__ __forceinline__ DF row_sum_df_acc(const MatView<float> &m, const floa
                 if (k + STEP * j < end) df_term<Z>(acc, vh[j], vl[j], zv[j]);
         } else {
 #pragma unroll 4
-            for (; k < end; k += STEP) df_term<Z>(acc, m.v[k], lo[k], __ldg(&z[m.ci[k]]));
+            for (; k < end; k += STEP) df_term<Z>(acc, m.v[k], lo[k], __ldg(&z[col_of(m, row, k)]));
         }
     }
     if (TPR > 1) {
