@@ -194,8 +194,10 @@ int amgh_problem_share(amgh_problem *parent, amgh_problem **out);
  * the device and assemble A, M_y, M_u, M_yu (Sec. 2) there.  Element
  * contributions are summed in ascending element order without fused
  * multiply-add, so the matrices are bit-identical on every run.
- * Errors: INVALID_ARG (dim not 2/3, sizes <= 0, beta <= 0, vertex id out of
- * range, degenerate element), OOM, CUDA.  *out is NULL on error. */
+ * Errors: INVALID_ARG (dim not 2/3, sizes <= 0, n_vertices or
+ * n_elements*(dim+1) >= 2^31, beta <= 0 or infinite, vertex id out of range,
+ * degenerate element, no vertex off the Dirichlet boundary), OOM, CUDA.
+ * *out is NULL on error. */
 int amgh_problem_create(const amgh_mesh *mesh, const double *kappa, double beta,
                         const double *y_d, int y_d_on_device, amgh_problem **out);
 

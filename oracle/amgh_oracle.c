@@ -1116,6 +1116,8 @@ static void free_hierarchy(orc_t *o)
 
 /* ------------------------------------------------------------ public API */
 
+void orc_destroy(void *h);
+
 int orc_create(int dim, long nv, const double *coords, long ne, const int *elems,
                const unsigned char *dirichlet, const double *kappa, double beta, const double *yd,
                void **out)
@@ -1141,6 +1143,10 @@ int orc_create(int dim, long nv, const double *coords, long ne, const int *elems
     o->state_of_vertex = malloc(sizeof(int) * (size_t)nv);
     int m = 0;
     for (long v = 0; v < nv; v++) o->state_of_vertex[v] = dirichlet[v] ? -1 : m++;
+    if (m == 0) { /* no vertex off the Dirichlet boundary: empty state space (Sec. 2) */
+        orc_destroy(o);
+        return ORC_INVALID;
+    }
     o->m = m;
     o->n = (int)nv;
     o->yd_state = xcalloc((size_t)m, sizeof(double));

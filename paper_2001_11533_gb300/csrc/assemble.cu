@@ -315,6 +315,9 @@ int assemble_full(amgh_problem *p)
     LAUNCH_CHECK();
     int m = 0;
     TRY(exclusive_scan<int>(flag, rank, nv, s, &m));
+    // every vertex on the Dirichlet boundary: the state space is empty and the
+    // problem of Sec. 2 degenerates (y = 0 for every control)
+    if (m == 0) return AMGH_ERR_INVALID_ARG;
     p->m = m;
     p->n = nv;
     TRY(p->arena.alloc(&p->state_of_vertex, nv));

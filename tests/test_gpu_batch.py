@@ -52,6 +52,20 @@ def test_workers_do_not_change_results():
             assert np.array_equal(a, b)
 
 
+def test_batch_with_an_empty_column_set():
+    """A problem with no desired states is skipped; the others solve."""
+    from paper_2001_11533_gb300 import amgh
+    import torch
+    ws = _small_batch()[:2]
+    probs = [amgh.Problem.from_workload(w) for w in ws]
+    batch = amgh.Batch(probs).setup(coarse_max=600)
+    yds = [_cuda(ws[0].y_d), torch.empty((0, ws[1].n_vertices), dtype=torch.float64, device="cuda")]
+    us, infos, st = batch.solve(yds, tol=1e-10)
+    batch.close()
+    assert st == 0 and infos[1]["outer_iters"] == 0 and us[1].shape[0] == 0
+    assert infos[0]["outer_iters"] > 0
+
+
 def test_shared_handle():
     from paper_2001_11533_gb300 import amgh
     w = _small_batch()[0]

@@ -331,6 +331,10 @@ def test_errors_reported():
     with pytest.raises(amgh.AmghError) as e:
         amgh.Problem(2, w.coords, rep, w.dirichlet, w.kappa, 1e-2, w.y_d)
     assert e.value.code == -1
+    w2 = W.unit_square(2)                     # every vertex on the Dirichlet boundary
+    with pytest.raises(amgh.AmghError) as e:
+        amgh.Problem(2, w2.coords, w2.elements, w2.dirichlet, w2.kappa, 1e-2, w2.y_d)
+    assert e.value.code == -1
     p = amgh.Problem(2, w.coords, w.elements, w.dirichlet, w.kappa, 1e-2, w.y_d)
     with pytest.raises(amgh.AmghError) as e:
         p.sizes = {"n": 81, "m": 49}

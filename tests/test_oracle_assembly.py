@@ -119,3 +119,14 @@ def test_state_restriction():
     assert np.array_equal(o.scipy("Myu").toarray(), M[st, :])
     assert np.array_equal(o.scipy("Mu").toarray(), M)
     assert np.array_equal(o.scipy("KN").toarray(), K)
+
+
+def test_all_dirichlet_mesh_rejected():
+    """A mesh whose every vertex lies on the Dirichlet boundary has no state
+    space (y = 0 for every control), so the problem of Sec. 2 is rejected."""
+    import pytest
+    from oracle.oracle import Oracle, OracleError
+    w = W.unit_square(2)
+    assert w.n_interior == 0
+    with pytest.raises(OracleError):
+        Oracle(w)
