@@ -542,6 +542,7 @@ extern "C" int amgh_solve(amgh_problem *p, const double *u0, double *u, double *
     int st2 = timer_collect(p);
     if (st == AMGH_OK) st = st2;
     if (st == AMGH_OK) st = sync_stream(p);
+    if (st == AMGH_OK) st = bulk_timeout_check(p->stream);
     return st;
 }
 

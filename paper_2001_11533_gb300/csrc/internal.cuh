@@ -317,6 +317,8 @@ int prepare_operator(Arena &ar, DevCsr &a, cudaStream_t s, int force_tpr = 0);
 // prepare_operator; for a state matrix A with aopts.autotune set, the layout
 // is the one whose Chebyshev step timed fastest on this GPU
 int prepare_tuned(amgh_problem *p, Arena &ar, DevCsr &a, int is_state_matrix);
+// AMGH_ERR_TIMEOUT (and the flag cleared) if a staged copy timed out
+int bulk_timeout_check(cudaStream_t s);
 // b = (float)a
 int to_f32(amgh_problem *p, const double *a, int64_t n, float *b);
 // build a.lo32 (after prepare_operator)

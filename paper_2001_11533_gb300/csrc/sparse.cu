@@ -13,6 +13,7 @@
 
 #include "internal.cuh"
 #include "spmv.cuh"
+#include "bulk.cuh"
 #include "util.cuh"
 
 // ------------------------------------------------------------------ conversion
@@ -414,6 +415,78 @@ __global__ void k_cheb_first(int n, const T *__restrict__ invd, const T *__restr
     x[r] = v;
 }
 
+// ------------------------------------------------------------------ staged ELL smoother
+// Level-0 Chebyshev step on a uniform-width SELL matrix (FP32 values, int16
+// offsets or int32 columns): each block's 8 slices of the matrix are one
+// contiguous range, brought into shared memory by the copy engine in one
+// transaction while the threads load their rows' b, D^-1, d and x; then
+// each thread gathers x at its row's columns.  Same sum order as row_sum, so
+// the same bits as the register-loading kernel.  A copy that has not landed
+// after the poll limit sets g_bulk_timeout and the block computes nothing.
+#define ELL_SLICES 8
+#define ELL_MAX_W 16
+#define BULK_POLLS (1 << 16)
+__device__ int g_bulk_timeout = 0;
+
+template <bool D16>
+__global__ void __launch_bounds__(32 * ELL_SLICES)
+    k_cheb_step_ell(int rows, int nslices, int W, const float *__restrict__ v, const void *__restrict__ cols,
+                    const float *__restrict__ invd, const float *__restrict__ b, const float *__restrict__ x,
+                    float *__restrict__ d, float *__restrict__ xn, float cdv, float crv, const int *__restrict__ skip)
+{
+    pdl_enter();
+    if (skip && *skip) return;
+    extern __shared__ __align__(16) unsigned char ell_sm[];
+    __shared__ __align__(8) uint64_t bar;
+    const int s0 = blockIdx.x * ELL_SLICES;
+    const int ns = min(ELL_SLICES, nslices - s0);
+    const int64_t first = (int64_t)s0 * 32 * W;
+    const uint32_t nent = (uint32_t)ns * 32 * W;
+    float *sv = (float *)ell_sm;
+    unsigned char *sc = ell_sm + (size_t)ELL_SLICES * 32 * W * sizeof(float);
+    const uint32_t ib = D16 ? 2 : 4;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        mbar_expect_tx(&bar, nent * (4 + ib));
+        bulk_g2s(sv, v + first, nent * 4, &bar);
+        bulk_g2s(sc, (const unsigned char *)cols + first * ib, nent * ib, &bar);
+    }
+    const int row = s0 * 32 + (int)threadIdx.x;
+    const bool ok = row < rows;
+    float br = 0.f, ir = 0.f, dr = 0.f, xr = 0.f;
+    if (ok) {
+        br = b[row];
+        ir = invd[row];
+        dr = d[row];
+        xr = x[row];
+    }
+    __syncthreads(); // the barrier is initialised before anyone polls it
+    if (!mbar_wait(&bar, 0, BULK_POLLS)) {
+        if (threadIdx.x == 0) atomicExch(&g_bulk_timeout, 1);
+        mbar_wait(&bar, 0, BULK_POLLS); // let the copies into this block's memory finish
+        return;
+    }
+    if (!ok) return;
+    const int base = ((int)threadIdx.x >> 5) * 32 * W + ((int)threadIdx.x & 31);
+    float xv[ELL_MAX_W];
+#pragma unroll
+    for (int j = 0; j < ELL_MAX_W; j++) {
+        if (j < W) {
+            int k = base + 32 * j;
+            int c = D16 ? row + (int)((const short *)sc)[k] : ((const int *)sc)[k];
+            xv[j] = __ldg(&x[c]);
+        }
+    }
+    float ax = 0.f;
+#pragma unroll
+    for (int j = 0; j < ELL_MAX_W; j++)
+        if (j < W) ax += sv[base + 32 * j] * xv[j];
+    float dn, xv2;
+    cheb_point(br, ax, ir, dr, xr, cdv, crv, dn, xv2);
+    d[row] = dn;
+    xn[row] = xv2;
+}
+
 template <typename T, int TPR>
 __global__ void k_residual(MatView<T> A, const T *__restrict__ b, const T *__restrict__ x, T *__restrict__ res,
                            const int *__restrict__ skip)
@@ -663,6 +736,19 @@ int spmv32(amgh_problem *p, const DevCsr &a, const float *x, float *y, const int
     return spmv_t<float>(p, a, x, y, skip, timed);
 }
 
+// nonzero once a staged copy has timed out (then cleared)
+int bulk_timeout_check(cudaStream_t s)
+{
+    int h = 0;
+    CU(cudaMemcpyFromSymbolAsync(&h, g_bulk_timeout, sizeof(int), 0, cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
+    if (!h) return AMGH_OK;
+    int zero = 0;
+    CU(cudaMemcpyToSymbolAsync(g_bulk_timeout, &zero, sizeof(int), 0, cudaMemcpyHostToDevice, s));
+    CU(cudaStreamSynchronize(s));
+    return AMGH_ERR_TIMEOUT;
+}
+
 int spmv2(amgh_problem *p, const DevCsr &a1, const double *x1, const DevCsr &a2, const double *x2, double c,
           double *y, const int *skip)
 {
@@ -716,7 +802,22 @@ int cheb_step(amgh_problem *p, const DevCsr &a, const T *invd, const T *b, const
     if (a.rows == 0) return AMGH_OK;
     timer_begin(p, timed);
     MatView<T> A = view<T>(a);
-    LAUNCH_TPR(k_cheb_step, T, A.tpr, A.rows, p->stream, A, invd, b, x, d, xn, (T)cdv, (T)crv, skip);
+    const void *ellcols = a.sl_ci16 ? (const void *)a.sl_ci16 : (const void *)a.sl_ci;
+    if (sizeof(T) == sizeof(float) && a.tpr <= 1 && a.ellw > 0 && a.ellw <= ELL_MAX_W &&
+        ((uintptr_t)a.sl_v32 & 15) == 0 && ((uintptr_t)ellcols & 15) == 0) {
+        size_t smem = (size_t)ELL_SLICES * 32 * a.ellw * (sizeof(float) + (a.sl_ci16 ? 2 : 4));
+        dim3 g(ceil_div(a.nslices, ELL_SLICES)), blk(32 * ELL_SLICES);
+        const float *fi = (const float *)invd, *fb = (const float *)b, *fx = (const float *)x;
+        float *fd = (float *)d, *fxn = (float *)xn;
+        if (a.sl_ci16)
+            pdl_launch(k_cheb_step_ell<true>, g, blk, smem, p->stream, a.rows, a.nslices, a.ellw, a.sl_v32,
+                       (const void *)a.sl_ci16, fi, fb, fx, fd, fxn, (float)cdv, (float)crv, skip);
+        else
+            pdl_launch(k_cheb_step_ell<false>, g, blk, smem, p->stream, a.rows, a.nslices, a.ellw, a.sl_v32,
+                       (const void *)a.sl_ci, fi, fb, fx, fd, fxn, (float)cdv, (float)crv, skip);
+    } else {
+        LAUNCH_TPR(k_cheb_step, T, A.tpr, A.rows, p->stream, A, invd, b, x, d, xn, (T)cdv, (T)crv, skip);
+    }
     LAUNCH_CHECK();
     // algorithmic bytes: matrix + x gather + b, invd, d (read+write), xn
     timer_end(p, timed, spmv_bytes(a, sizeof(T)) + 4.0 * sizeof(T) * a.rows);
