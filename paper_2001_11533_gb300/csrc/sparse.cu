@@ -309,7 +309,7 @@ int prepare_operator(Arena &ar, DevCsr &a, cudaStream_t s, int force_tpr)
     else if (avg > 96.0) tpr = 32;
     else if (avg > 48.0) tpr = 16;
     else if (avg > 24.0) tpr = 8;
-    else if (avg > 12.0) tpr = 4;
+    else if (avg > 16.0) tpr = 4;
     a.tpr = tpr;
     int longest = 0;
     TRY(max_row_length(a, s, &longest));
@@ -420,8 +420,8 @@ __global__ void k_cheb_first(int n, const T *__restrict__ invd, const T *__restr
 // offsets or int32 columns): each block's 8 slices of the matrix are one
 // contiguous range, brought into shared memory by the copy engine in one
 // transaction while the threads load their rows' b, D^-1, d and x; then
-// each thread gathers x at its row's columns.  Same sum order as row_sum, so
-// the same bits as the register-loading kernel.  A copy that has not landed
+// each thread gathers x at its row's columns, summing in the same order as
+// row_sum in the register-loading kernel.  A copy that has not landed
 // after the poll limit sets g_bulk_timeout and the block computes nothing.
 #define ELL_SLICES 8
 #define ELL_MAX_W 16
