@@ -431,35 +431,62 @@ int amg_prolongator(amgh_problem *p, Arena &ar, const DevCsr &a, const int *agg,
 }
 
 // ------------------------------------------------------------------ SpGEMM
+// C = A B for CSR matrices, every entry summed in the canonical order (A's
+// row entries ascending, then B's row entries ascending; first product added
+// to 0.0).  NV = 2 multiplies two pairs of matrices that share their patterns
+// (A1, A2 with one pattern, B1, B2 with one pattern) in one pass, so the
+// hashing is paid once for C1 = A1 B1 and C2 = A2 B2 (A and M_y, K_N and M_u
+// in the Galerkin products).
+//
 // Candidate count of row i: u_i = sum over A's row i of the lengths of the
-// B rows it selects.  On matrices with few rows (coarse levels, where one
-// thread per row cannot fill the GPU and each row is long) rows with
-// u_i <= WARP_TS / 2 are handled by one warp with its hash table in shared
-// memory; all other rows by one thread with a table of 2^ceil(log2(2 u_i))
-// slots in global memory.
+// B rows it selects.  Path of row i: 0 = one thread with a global hash table
+// of 2^ceil(log2(2 u_i)) slots, 1 = one warp with a shared hash table
+// (u_i <= WARP_TS / 2), 2 = one block with a dense shared accumulator over all
+// columns (u_i > WARP_TS / 2, few columns), 3 = one block with a shared hash
+// table (u_i > WARP_TS / 2, many columns, few rows).  Products with few rows
+// (n <= WARP_PATH_MAX_ROWS) use the shared paths throughout.  In large
+// products a thread per row with a global table wins while the tables stay
+// small; rows with 64 < u_i <= WARP_TS / 2 are marked 4 and go to the warp
+// path only if all such tables together would exceed GLOBAL_TABLE_MAX_BYTES
+// (the 3D fine levels).
 #define WARP_TS 1024
 #define WARPS_PER_BLOCK 4
 #define WARP_PATH_MAX_ROWS 65536
-
-// path of row i (u = its candidate products): 0 = one thread with a global
-// hash table, 1 = one warp with a shared hash table (u <= WARP_TS / 2), 2 =
-// one block with a dense shared accumulator over all columns (u > WARP_TS / 2,
-// few columns), 3 = one block with a shared hash table (u > WARP_TS / 2, many
-// columns, few rows).  Small products (n <= WARP_PATH_MAX_ROWS) use the shared
-// paths throughout.  In large products a thread per row with a global table
-// wins while the tables stay small; rows with 64 < u <= WARP_TS / 2 are marked
-// 4 here and go to the warp path only if all such tables together would exceed
-// GLOBAL_TABLE_MAX_BYTES (the 3D fine levels).
-#define BLOCK_HASH_MAX_U 8192
 #define GLOBAL_TABLE_MAX_BYTES (8ll << 30)
+#define DENSE_ROW_TPB 256
+#define BH_TPB 256
+
+template <int NV>
+struct GemmVals {
+    const double *a[NV];
+    const double *b[NV];
+};
+
+template <int NV>
+struct GemmOut {
+    double *v[NV];
+};
+
+template <int NV>
+struct Limits;
+template <>
+struct Limits<1> {
+    static constexpr int dense_cols = 16384, bhash_u = 8192;
+};
+template <>
+struct Limits<2> {
+    static constexpr int dense_cols = 12288, bhash_u = 4096;
+};
 
 // set when a row reaches a SpGEMM path whose table it would overflow; the
 // row is skipped and the host reports an error
 __device__ int g_spgemm_bad = 0;
 
+__device__ __forceinline__ unsigned hslot(int key, unsigned mask) { return ((unsigned)key * 2654435761u) & mask; }
+
 __global__ void k_gemm_ub(int n, const int *__restrict__ arp, const int *__restrict__ aci,
                           const int *__restrict__ brp, long long *__restrict__ ub, int *__restrict__ path_of,
-                          int small_n, int use_dense, int *__restrict__ umax3,
+                          int small_n, int use_dense, int bhash_u, int *__restrict__ umax3,
                           unsigned long long *__restrict__ slots4)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -474,7 +501,7 @@ __global__ void k_gemm_ub(int n, const int *__restrict__ arp, const int *__restr
     int path = 0;
     if (u <= WARP_TS / 2) path = small_n ? 1 : (u > 64 ? 4 : 0);
     else if (use_dense) path = 2;
-    else if (small_n && u <= BLOCK_HASH_MAX_U) path = 3;
+    else if (small_n && u <= bhash_u) path = 3;
     path_of[i] = path;
     if (path == 3) atomicMax(umax3, (int)u);
     if (path == 4) atomicAdd(slots4, (unsigned long long)t);
@@ -502,40 +529,229 @@ __global__ void k_list(int n, const int *__restrict__ flag, const int *__restric
     if (i < n && flag[i]) list[pos[i]] = i;
 }
 
-// dense-accumulator path: one block per listed row.  The row's products are
-// taken one entry a_ik at a time (a barrier between entries) with the
-// entries of row k of B spread over the threads; every column J occurs once
-// in a row of B, so each accumulator receives its products in exactly the
-// sequential order.  phase 0 counts the row's columns, phase 1 writes them
-// in ascending order.
-#define DENSE_ROW_TPB 256
-#define DENSE_ROW_MAX_COLS 16384
-__global__ void __launch_bounds__(DENSE_ROW_TPB) k_gemm_dense(int nlist, const int *__restrict__ list, int cols,
-                                                              const int *__restrict__ arp, const int *__restrict__ aci,
-                                                              const double *__restrict__ av,
-                                                              const int *__restrict__ brp,
-                                                              const int *__restrict__ bci,
-                                                              const double *__restrict__ bv, int phase,
-                                                              int *__restrict__ cnt, const int *__restrict__ crp,
-                                                              int *__restrict__ cci, double *__restrict__ cv)
+// path 0: accumulate row i in canonical order in its global table; count uniques
+template <int NV>
+__global__ void k_gemm_hash(int n, const int *__restrict__ arp, const int *__restrict__ aci, GemmVals<NV> V,
+                            const int *__restrict__ brp, const int *__restrict__ bci,
+                            const long long *__restrict__ toff, const int *__restrict__ path_of,
+                            int *__restrict__ tkey, GemmOut<NV> T, int *__restrict__ cnt)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n || path_of[i]) return;
+    long long base = toff[i];
+    unsigned size = (unsigned)(toff[i + 1] - base);
+    int c = 0;
+    if (size > 0) {
+        unsigned mask = size - 1;
+        int *key = tkey + base; // all slots set to -1 by the caller
+        for (int k = arp[i]; k < arp[i + 1]; k++) {
+            int j = aci[k];
+            double aij[NV];
+#pragma unroll
+            for (int q = 0; q < NV; q++) aij[q] = V.a[q][k];
+            for (int e = brp[j]; e < brp[j + 1]; e++) {
+                int J = bci[e];
+                unsigned h = hslot(J, mask);
+                for (;;) {
+                    int kk = key[h];
+                    if (kk == J) {
+#pragma unroll
+                        for (int q = 0; q < NV; q++)
+                            T.v[q][base + h] = __dadd_rn(T.v[q][base + h], __dmul_rn(aij[q], V.b[q][e]));
+                        break;
+                    }
+                    if (kk < 0) {
+                        key[h] = J;
+#pragma unroll
+                        for (int q = 0; q < NV; q++) T.v[q][base + h] = __dadd_rn(0.0, __dmul_rn(aij[q], V.b[q][e]));
+                        c++;
+                        break;
+                    }
+                    h = (h + 1) & mask;
+                }
+            }
+        }
+    }
+    cnt[i] = c;
+}
+
+// path 0 output: the table's entries in ascending column order
+template <int NV>
+__global__ void k_gemm_out(int n, const long long *__restrict__ toff, const int *__restrict__ path_of,
+                           const int *__restrict__ tkey, GemmOut<NV> T, const int *__restrict__ crp,
+                           int *__restrict__ cci, GemmOut<NV> C)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n || path_of[i]) return;
+    long long base = toff[i];
+    unsigned size = (unsigned)(toff[i + 1] - base);
+    int b = crp[i], c = 0;
+    for (unsigned t = 0; t < size; t++) {
+        int key = tkey[base + t];
+        if (key < 0) continue;
+        int j = b + c - 1;
+        while (j >= b && cci[j] > key) {
+            cci[j + 1] = cci[j];
+#pragma unroll
+            for (int q = 0; q < NV; q++) C.v[q][j + 1] = C.v[q][j];
+            j--;
+        }
+        cci[j + 1] = key;
+#pragma unroll
+        for (int q = 0; q < NV; q++) C.v[q][j + 1] = T.v[q][base + t];
+        c++;
+    }
+}
+
+// path 1: one warp per listed row.  Candidates are taken 32 at a time in
+// canonical order; lanes holding the same column form a group
+// (__match_any_sync) whose lowest lane finds / inserts the slot and adds the
+// group's products in lane order -- so every entry receives its products in
+// exactly the sequential order.  phase 0 counts, phase 1 writes the sorted row.
+template <int NV>
+__host__ __device__ constexpr size_t warp_smem_bytes()
+{
+    return (size_t)WARPS_PER_BLOCK * WARP_TS * (sizeof(int) + NV * sizeof(double)) +
+           (size_t)WARPS_PER_BLOCK * 32 * NV * sizeof(double);
+}
+
+template <int NV>
+__global__ void k_gemm_warp(int n, const int *__restrict__ arp, const int *__restrict__ aci, GemmVals<NV> V,
+                            const int *__restrict__ brp, const int *__restrict__ bci, const int *__restrict__ list,
+                            int phase, int *__restrict__ cnt, const int *__restrict__ crp, int *__restrict__ cci,
+                            GemmOut<NV> C)
+{
+    extern __shared__ unsigned char smem_raw[];
+    int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int *keys = (int *)smem_raw + w * WARP_TS;
+    double *vbase = (double *)((int *)smem_raw + WARPS_PER_BLOCK * WARP_TS);
+    double *vals = vbase + (size_t)w * NV * WARP_TS; // [NV][WARP_TS]
+    double *stage = vbase + (size_t)WARPS_PER_BLOCK * NV * WARP_TS + (size_t)w * NV * 32; // [NV][32]
+    int li = blockIdx.x * WARPS_PER_BLOCK + w;
+    if (li >= n) return; // warp-uniform; n = number of listed rows
+    int i = list[li];
+    // table of 2^ceil(log2(2u)) slots (u = candidate count of the row)
+    int u = 0;
+    for (int k = arp[i] + lane; k < arp[i + 1]; k += 32) {
+        int j = aci[k];
+        u += brp[j + 1] - brp[j];
+    }
+    for (int o = 16; o > 0; o >>= 1) u += __shfl_xor_sync(0xffffffffu, u, o);
+    unsigned ts = 2;
+    while ((int)ts < 2 * u) ts <<= 1;
+    if (ts > WARP_TS) { // warp-uniform
+        if (lane == 0) atomicExch(&g_spgemm_bad, 1);
+        return;
+    }
+    const unsigned mask = ts - 1;
+    for (unsigned t = lane; t < ts; t += 32) keys[t] = -1;
+    __syncwarp();
+    for (int k = arp[i]; k < arp[i + 1]; k++) {
+        int j = aci[k];
+        double aij[NV];
+#pragma unroll
+        for (int q = 0; q < NV; q++) aij[q] = V.a[q][k];
+        int qb = brp[j], qe = brp[j + 1];
+        for (int q0 = qb; q0 < qe; q0 += 32) {
+            int e = q0 + lane;
+            bool valid = e < qe;
+            int J = valid ? bci[e] : -1;
+#pragma unroll
+            for (int q = 0; q < NV; q++) stage[q * 32 + lane] = valid ? __dmul_rn(aij[q], V.b[q][e]) : 0.0;
+            unsigned grp = __match_any_sync(0xffffffffu, J);
+            __syncwarp();
+            if (valid && lane == __ffs(grp) - 1) {
+                unsigned h = hslot(J, mask);
+                bool fresh = false;
+                for (;;) {
+                    int old = atomicCAS(&keys[h], -1, J);
+                    if (old == -1) {
+                        fresh = true;
+                        break;
+                    }
+                    if (old == J) break;
+                    h = (h + 1) & mask;
+                }
+#pragma unroll
+                for (int q = 0; q < NV; q++) {
+                    double acc = fresh ? 0.0 : vals[q * WARP_TS + h];
+                    for (unsigned m = grp; m; m &= m - 1) acc = __dadd_rn(acc, stage[q * 32 + __ffs(m) - 1]);
+                    vals[q * WARP_TS + h] = acc;
+                }
+            }
+            __syncwarp();
+        }
+    }
+    // compact the occupied slots to the front of the table
+    int c = 0;
+    for (unsigned t0 = 0; t0 < ts; t0 += 32) {
+        unsigned t = t0 + lane;
+        int key = t < ts ? keys[t] : -1;
+        double val[NV];
+#pragma unroll
+        for (int q = 0; q < NV; q++) val[q] = t < ts ? vals[q * WARP_TS + t] : 0.0;
+        unsigned occ = __ballot_sync(0xffffffffu, key >= 0);
+        __syncwarp();
+        if (key >= 0) {
+            int pos = c + __popc(occ & ((1u << lane) - 1));
+            keys[pos] = key; // pos <= t: never overwrites an unread slot
+#pragma unroll
+            for (int q = 0; q < NV; q++) vals[q * WARP_TS + pos] = val[q];
+        }
+        c += __popc(occ);
+        __syncwarp();
+    }
+    if (phase == 0) {
+        if (lane == 0) cnt[i] = c;
+        return;
+    }
+    // rank of each key among the row's keys = its position in the sorted row
+    int base = crp[i];
+    for (int t = lane; t < c; t += 32) {
+        int key = keys[t];
+        int rank = 0;
+        for (int v = 0; v < c; v++) rank += keys[v] < key;
+        cci[base + rank] = key;
+#pragma unroll
+        for (int q = 0; q < NV; q++) C.v[q][base + rank] = vals[q * WARP_TS + t];
+    }
+}
+
+// path 2: one block per listed row with a dense shared accumulator over all
+// columns.  The row's products are taken one entry a_ik at a time (a barrier
+// between entries) with row k of B spread over the threads; every column
+// occurs once in a row of B, so each accumulator receives its products in the
+// sequential order.  phase 0 counts the row's columns, phase 1 writes them in
+// ascending order.
+template <int NV>
+__global__ void __launch_bounds__(DENSE_ROW_TPB)
+    k_gemm_dense(int nlist, const int *__restrict__ list, int cols, const int *__restrict__ arp,
+                 const int *__restrict__ aci, GemmVals<NV> V, const int *__restrict__ brp,
+                 const int *__restrict__ bci, int phase, int *__restrict__ cnt, const int *__restrict__ crp,
+                 int *__restrict__ cci, GemmOut<NV> C)
 {
     extern __shared__ unsigned char smem_raw[];
     __shared__ int wsum[DENSE_ROW_TPB / 32];
-    double *acc = (double *)smem_raw;
-    unsigned char *seen = smem_raw + (size_t)cols * sizeof(double);
+    double *acc = (double *)smem_raw; // [NV][cols]
+    unsigned char *seen = smem_raw + (size_t)NV * cols * sizeof(double);
     int i = list[blockIdx.x];
     int t = threadIdx.x, lane = t & 31, w = t >> 5;
     for (int J = t; J < cols; J += DENSE_ROW_TPB) {
-        acc[J] = 0.0;
+#pragma unroll
+        for (int q = 0; q < NV; q++) acc[(size_t)q * cols + J] = 0.0;
         seen[J] = 0;
     }
     __syncthreads();
     for (int k = arp[i]; k < arp[i + 1]; k++) {
         int j = aci[k];
-        double aij = av[k];
-        for (int q = brp[j] + t; q < brp[j + 1]; q += DENSE_ROW_TPB) {
-            int J = bci[q];
-            acc[J] = __dadd_rn(acc[J], __dmul_rn(aij, bv[q]));
+        double aij[NV];
+#pragma unroll
+        for (int q = 0; q < NV; q++) aij[q] = V.a[q][k];
+        for (int e = brp[j] + t; e < brp[j + 1]; e += DENSE_ROW_TPB) {
+            int J = bci[e];
+#pragma unroll
+            for (int q = 0; q < NV; q++)
+                acc[(size_t)q * cols + J] = __dadd_rn(acc[(size_t)q * cols + J], __dmul_rn(aij[q], V.b[q][e]));
             seen[J] = 1;
         }
         __syncthreads();
@@ -566,197 +782,28 @@ __global__ void __launch_bounds__(DENSE_ROW_TPB) k_gemm_dense(int nlist, const i
     for (int J = beg; J < end; J++)
         if (seen[J]) {
             cci[pos] = J;
-            cv[pos] = acc[J];
+#pragma unroll
+            for (int q = 0; q < NV; q++) C.v[q][pos] = acc[(size_t)q * cols + J];
             pos++;
         }
 }
 
-__device__ __forceinline__ unsigned hslot(int key, unsigned mask) { return ((unsigned)key * 2654435761u) & mask; }
-
-// global-table path: accumulate row i in canonical order; count uniques
-__global__ void k_gemm_hash(int n, const int *__restrict__ arp, const int *__restrict__ aci,
-                            const double *__restrict__ av, const int *__restrict__ brp,
-                            const int *__restrict__ bci, const double *__restrict__ bv,
-                            const long long *__restrict__ toff, const int *__restrict__ small, int *__restrict__ tkey,
-                            double *__restrict__ tval, int *__restrict__ cnt)
-{
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n || small[i]) return;
-    long long base = toff[i];
-    unsigned size = (unsigned)(toff[i + 1] - base);
-    int c = 0;
-    if (size > 0) {
-        unsigned mask = size - 1;
-        int *key = tkey + base; // all slots set to -1 by the caller
-        double *val = tval + base;
-        for (int k = arp[i]; k < arp[i + 1]; k++) {
-            int j = aci[k];
-            double aij = av[k];
-            for (int q = brp[j]; q < brp[j + 1]; q++) {
-                int J = bci[q];
-                double prod = __dmul_rn(aij, bv[q]);
-                unsigned h = hslot(J, mask);
-                for (;;) {
-                    int kk = key[h];
-                    if (kk == J) {
-                        val[h] = __dadd_rn(val[h], prod);
-                        break;
-                    }
-                    if (kk < 0) {
-                        key[h] = J;
-                        val[h] = __dadd_rn(0.0, prod);
-                        c++;
-                        break;
-                    }
-                    h = (h + 1) & mask;
-                }
-            }
-        }
-    }
-    cnt[i] = c;
-}
-
-__global__ void k_gemm_out(int n, const long long *__restrict__ toff, const int *__restrict__ small,
-                           const int *__restrict__ tkey, const double *__restrict__ tval, const int *__restrict__ crp,
-                           int *__restrict__ cci, double *__restrict__ cv)
-{
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n || small[i]) return;
-    long long base = toff[i];
-    unsigned size = (unsigned)(toff[i + 1] - base);
-    int b = crp[i], c = 0;
-    for (unsigned t = 0; t < size; t++) {
-        int key = tkey[base + t];
-        if (key < 0) continue;
-        double x = tval[base + t];
-        int j = b + c - 1;
-        while (j >= b && cci[j] > key) {
-            cci[j + 1] = cci[j];
-            cv[j + 1] = cv[j];
-            j--;
-        }
-        cci[j + 1] = key;
-        cv[j + 1] = x;
-        c++;
-    }
-}
-
-// shared-memory path: one warp per row.  Candidates are taken 32 at a time in
-// canonical order; lanes holding the same column form a group
-// (__match_any_sync) whose lowest lane finds / inserts the slot and adds the
-// group's products in lane order -- so every entry receives its products in
-// exactly the sequential order.  phase 0 counts, phase 1 writes the sorted row.
-__global__ void k_gemm_warp(int n, const int *__restrict__ arp, const int *__restrict__ aci,
-                            const double *__restrict__ av, const int *__restrict__ brp,
-                            const int *__restrict__ bci, const double *__restrict__ bv,
-                            const int *__restrict__ list, int phase, int *__restrict__ cnt,
-                            const int *__restrict__ crp, int *__restrict__ cci, double *__restrict__ cv)
-{
-    extern __shared__ unsigned char smem_raw[];
-    int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    int *keys = (int *)smem_raw + w * WARP_TS;
-    double *vals = (double *)((int *)smem_raw + WARPS_PER_BLOCK * WARP_TS) + w * WARP_TS;
-    double *stage = (double *)((int *)smem_raw + WARPS_PER_BLOCK * WARP_TS) + WARPS_PER_BLOCK * WARP_TS + w * 32;
-    int li = blockIdx.x * WARPS_PER_BLOCK + w;
-    if (li >= n) return; // warp-uniform; n = number of listed rows
-    int i = list[li];
-    // table of 2^ceil(log2(2u)) slots (u = candidate count of the row)
-    int u = 0;
-    for (int k = arp[i] + lane; k < arp[i + 1]; k += 32) {
-        int j = aci[k];
-        u += brp[j + 1] - brp[j];
-    }
-    for (int o = 16; o > 0; o >>= 1) u += __shfl_xor_sync(0xffffffffu, u, o);
-    unsigned ts = 2;
-    while ((int)ts < 2 * u) ts <<= 1;
-    if (ts > WARP_TS) { // warp-uniform
-        if (lane == 0) atomicExch(&g_spgemm_bad, 1);
-        return;
-    }
-    const unsigned mask = ts - 1;
-    for (unsigned t = lane; t < ts; t += 32) keys[t] = -1;
-    __syncwarp();
-    for (int k = arp[i]; k < arp[i + 1]; k++) {
-        int j = aci[k];
-        double aij = av[k];
-        int qb = brp[j], qe = brp[j + 1];
-        for (int q0 = qb; q0 < qe; q0 += 32) {
-            int q = q0 + lane;
-            bool valid = q < qe;
-            int J = valid ? bci[q] : -1;
-            double prod = valid ? __dmul_rn(aij, bv[q]) : 0.0;
-            unsigned grp = __match_any_sync(0xffffffffu, J);
-            stage[lane] = prod;
-            __syncwarp();
-            if (valid && lane == __ffs(grp) - 1) {
-                unsigned h = hslot(J, mask);
-                for (;;) {
-                    int old = atomicCAS(&keys[h], -1, J);
-                    if (old == -1) {
-                        vals[h] = 0.0;
-                        break;
-                    }
-                    if (old == J) break;
-                    h = (h + 1) & mask;
-                }
-                double acc = vals[h];
-                for (unsigned m = grp; m; m &= m - 1) acc = __dadd_rn(acc, stage[__ffs(m) - 1]);
-                vals[h] = acc;
-            }
-            __syncwarp();
-        }
-    }
-    // compact the occupied slots to the front of the table (keys and values)
-    int c = 0;
-    for (unsigned t0 = 0; t0 < ts; t0 += 32) {
-        unsigned t = t0 + lane;
-        int key = t < ts ? keys[t] : -1;
-        double val = t < ts ? vals[t] : 0.0;
-        unsigned occ = __ballot_sync(0xffffffffu, key >= 0);
-        __syncwarp();
-        if (key >= 0) {
-            int pos = c + __popc(occ & ((1u << lane) - 1));
-            keys[pos] = key; // pos <= t: never overwrites an unread slot
-            vals[pos] = val;
-        }
-        c += __popc(occ);
-        __syncwarp();
-    }
-    if (phase == 0) {
-        if (lane == 0) cnt[i] = c;
-        return;
-    }
-    // rank of each key among the row's keys = its position in the sorted row
-    int base = crp[i];
-    for (int t = lane; t < c; t += 32) {
-        int key = keys[t];
-        int rank = 0;
-        for (int v = 0; v < c; v++) rank += keys[v] < key;
-        cci[base + rank] = key;
-        cv[base + rank] = vals[t];
-    }
-}
-
-// block shared-hash path: one block per listed row, the row's products taken
-// one entry a_ik at a time (a barrier between entries) with row k of B spread
-// over the threads -- each column occurs once in a row of B, so every entry
-// receives its products in the sequential order.  Then the occupied slots are
-// compacted to the front of the table (chunk by chunk: all reads of a chunk
-// before its writes, which only land on slots already read) and sorted by
-// column (bitonic network over the next power of two), phase 0 counting and
-// phase 1 writing the row.
-#define BH_TPB 256
-__global__ void __launch_bounds__(BH_TPB) k_gemm_bhash(int nlist, const int *__restrict__ list, int ts,
-                                                       const int *__restrict__ arp, const int *__restrict__ aci,
-                                                       const double *__restrict__ av, const int *__restrict__ brp,
-                                                       const int *__restrict__ bci, const double *__restrict__ bv,
-                                                       int phase, int *__restrict__ cnt, const int *__restrict__ crp,
-                                                       int *__restrict__ cci, double *__restrict__ cv)
+// path 3: one block per listed row with a shared hash table of ts slots; the
+// products are taken as in path 2, then the occupied slots are compacted to
+// the front (chunk by chunk: all reads of a chunk before its writes, which
+// only land on slots already read) and sorted by column (bitonic network over
+// the next power of two).  phase 0 counts, phase 1 writes the row.
+template <int NV>
+__global__ void __launch_bounds__(BH_TPB)
+    k_gemm_bhash(int nlist, const int *__restrict__ list, int ts, const int *__restrict__ arp,
+                 const int *__restrict__ aci, GemmVals<NV> V, const int *__restrict__ brp,
+                 const int *__restrict__ bci, int phase, int *__restrict__ cnt, const int *__restrict__ crp,
+                 int *__restrict__ cci, GemmOut<NV> C)
 {
     extern __shared__ unsigned char smem_raw[];
     __shared__ int wcount[BH_TPB / 32];
-    double *vals = (double *)smem_raw;
-    int *keys = (int *)(vals + ts);
+    double *vals = (double *)smem_raw; // [NV][ts]
+    int *keys = (int *)(vals + (size_t)NV * ts);
     const unsigned mask = (unsigned)ts - 1;
     int i = list[blockIdx.x];
     int t = threadIdx.x, lane = t & 31, w = t >> 5;
@@ -775,19 +822,20 @@ __global__ void __launch_bounds__(BH_TPB) k_gemm_bhash(int nlist, const int *__r
     __syncthreads();
     for (int k = arp[i]; k < arp[i + 1]; k++) {
         int j = aci[k];
-        double aij = av[k];
-        for (int q = brp[j] + t; q < brp[j + 1]; q += BH_TPB) {
-            int J = bci[q];
-            double prod = __dmul_rn(aij, bv[q]);
+        double aij[NV];
+#pragma unroll
+        for (int q = 0; q < NV; q++) aij[q] = V.a[q][k];
+        for (int e = brp[j] + t; e < brp[j + 1]; e += BH_TPB) {
+            int J = bci[e];
             unsigned h = hslot(J, mask);
             for (;;) {
                 int old = atomicCAS(&keys[h], -1, J);
-                if (old == -1) {
-                    vals[h] = __dadd_rn(0.0, prod);
-                    break;
-                }
-                if (old == J) {
-                    vals[h] = __dadd_rn(vals[h], prod);
+                if (old == -1 || old == J) {
+#pragma unroll
+                    for (int q = 0; q < NV; q++) {
+                        double prev = old == -1 ? 0.0 : vals[(size_t)q * ts + h];
+                        vals[(size_t)q * ts + h] = __dadd_rn(prev, __dmul_rn(aij[q], V.b[q][e]));
+                    }
                     break;
                 }
                 h = (h + 1) & mask;
@@ -800,7 +848,9 @@ __global__ void __launch_bounds__(BH_TPB) k_gemm_bhash(int nlist, const int *__r
     for (int base = 0; base < ts; base += BH_TPB) {
         int slot = base + t;
         int key = keys[slot];
-        double val = vals[slot];
+        double val[NV];
+#pragma unroll
+        for (int q = 0; q < NV; q++) val[q] = vals[(size_t)q * ts + slot];
         bool occ = key >= 0;
         unsigned bal = __ballot_sync(0xffffffffu, occ);
         if (lane == 0) wcount[w] = __popc(bal);
@@ -814,7 +864,8 @@ __global__ void __launch_bounds__(BH_TPB) k_gemm_bhash(int nlist, const int *__r
         __syncthreads(); // every read of this chunk is done
         if (occ) {
             keys[pos] = key;
-            vals[pos] = val;
+#pragma unroll
+            for (int q = 0; q < NV; q++) vals[(size_t)q * ts + pos] = val[q];
         }
         c += chunk;
         __syncthreads();
@@ -838,9 +889,12 @@ __global__ void __launch_bounds__(BH_TPB) k_gemm_bhash(int nlist, const int *__r
                     if ((ka > kb) == up) {
                         keys[a] = kb;
                         keys[b] = ka;
-                        double tv = vals[a];
-                        vals[a] = vals[b];
-                        vals[b] = tv;
+#pragma unroll
+                        for (int q = 0; q < NV; q++) {
+                            double tv = vals[(size_t)q * ts + a];
+                            vals[(size_t)q * ts + a] = vals[(size_t)q * ts + b];
+                            vals[(size_t)q * ts + b] = tv;
+                        }
                     }
                 }
             }
@@ -849,26 +903,39 @@ __global__ void __launch_bounds__(BH_TPB) k_gemm_bhash(int nlist, const int *__r
     int base = crp[i];
     for (int q = t; q < c; q += BH_TPB) {
         cci[base + q] = keys[q];
-        cv[base + q] = vals[q];
+#pragma unroll
+        for (int r = 0; r < NV; r++) C.v[r][base + q] = vals[(size_t)r * ts + q];
     }
 }
 
-static size_t warp_smem() { return (size_t)WARPS_PER_BLOCK * WARP_TS * (sizeof(int) + sizeof(double)) +
-                                  (size_t)WARPS_PER_BLOCK * 32 * sizeof(double); }
-
-int spgemm(amgh_problem *p, Arena &ar, const DevCsr &a, const DevCsr &b, DevCsr &c)
+// C (pattern c, values cv[0..NV-1]) = A_q B_q for q < NV (patterns of a, b)
+template <int NV>
+static int spgemm_nv(amgh_problem *p, Arena &ar, const DevCsr &a, const double *const *av, const DevCsr &b,
+                     const double *const *bv, DevCsr &c, double **cv)
 {
     cudaStream_t s = p->stream;
     int n = a.rows;
     c.rows = n;
     c.cols = b.cols;
-    // the attribute is per function and device; setting it again is harmless
-    CU(cudaFuncSetAttribute(k_gemm_warp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)warp_smem()));
+    GemmVals<NV> V;
+    for (int q = 0; q < NV; q++) {
+        V.a[q] = av[q];
+        V.b[q] = bv[q];
+    }
+    // dynamic shared memory limits are per function and setups may run on
+    // several host threads: raise them once to the most any launch can use
+    // (the 48 KB default counts static memory too)
+    const int dense_cols = Limits<NV>::dense_cols, bhash_u = Limits<NV>::bhash_u;
+    CU(cudaFuncSetAttribute(k_gemm_warp<NV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                            (int)warp_smem_bytes<NV>()));
+    CU(cudaFuncSetAttribute(k_gemm_dense<NV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                            (int)((size_t)dense_cols * (NV * sizeof(double) + 1))));
+    CU(cudaFuncSetAttribute(k_gemm_bhash<NV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                            (int)((size_t)2 * bhash_u * (NV * sizeof(double) + sizeof(int)))));
     Scratch sc;
     long long *ub = nullptr, *toff = nullptr;
     int *cnt = nullptr, *tkey = nullptr, *path = nullptr, *flag = nullptr, *pos = nullptr, *umax = nullptr;
     unsigned long long *slots4 = nullptr;
-    double *tval = nullptr;
     TRY(sc.alloc(&ub, n + 1));
     TRY(sc.alloc(&toff, n + 1));
     TRY(sc.alloc(&cnt, n + 1));
@@ -878,24 +945,18 @@ int spgemm(amgh_problem *p, Arena &ar, const DevCsr &a, const DevCsr &b, DevCsr 
     TRY(sc.alloc(&umax, 1));
     TRY(sc.alloc(&slots4, 1));
     int nb = ceil_div(n, 128);
-    int use_dense = b.cols <= DENSE_ROW_MAX_COLS;
-    size_t dsmem = (size_t)b.cols * (sizeof(double) + 1);
-    // The dynamic shared memory limit is per function, and setups may run on
-    // several host threads at once: raise it once to the most any launch of
-    // the kernel can use (the 48 KB default counts static memory too).
-    CU(cudaFuncSetAttribute(k_gemm_dense, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                            (int)((size_t)DENSE_ROW_MAX_COLS * (sizeof(double) + 1))));
-    CU(cudaFuncSetAttribute(k_gemm_bhash, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                            (int)((size_t)2 * BLOCK_HASH_MAX_U * (sizeof(double) + sizeof(int)))));
+    int use_dense = b.cols <= dense_cols;
+    size_t dsmem = (size_t)b.cols * (NV * sizeof(double) + 1);
     CU(cudaMemsetAsync(umax, 0, sizeof(int), s));
     CU(cudaMemsetAsync(slots4, 0, sizeof(unsigned long long), s));
-    k_gemm_ub<<<nb, 128, 0, s>>>(n, a.rp, a.ci, b.rp, ub, path, n <= WARP_PATH_MAX_ROWS, use_dense, umax, slots4);
+    k_gemm_ub<<<nb, 128, 0, s>>>(n, a.rp, a.ci, b.rp, ub, path, n <= WARP_PATH_MAX_ROWS, use_dense, bhash_u, umax,
+                                  slots4);
     LAUNCH_CHECK();
     {
         unsigned long long sl = 0;
         CU(cudaMemcpyAsync(&sl, slots4, sizeof(sl), cudaMemcpyDeviceToHost, s));
         CU(cudaStreamSynchronize(s));
-        int to_warp = (long long)sl * (long long)(sizeof(int) + sizeof(double)) > GLOBAL_TABLE_MAX_BYTES;
+        int to_warp = (long long)sl * (long long)(sizeof(int) + NV * sizeof(double)) > GLOBAL_TABLE_MAX_BYTES;
         k_gemm_settle<<<ceil_div(n, 256), 256, 0, s>>>(n, to_warp, path, ub);
         LAUNCH_CHECK();
     }
@@ -920,43 +981,51 @@ int spgemm(amgh_problem *p, Arena &ar, const DevCsr &a, const DevCsr &b, DevCsr 
         CU(cudaStreamSynchronize(s));
         ts3 = BH_TPB;
         while (ts3 < 2 * um) ts3 <<= 1;
-        bsmem = (size_t)ts3 * (sizeof(double) + sizeof(int));
+        bsmem = (size_t)ts3 * (NV * sizeof(double) + sizeof(int));
     }
     long long tot = 0;
     TRY(exclusive_scan<long long>(ub, toff, n, s, &tot));
+    GemmOut<NV> T;
     TRY(sc.alloc(&tkey, tot));
-    TRY(sc.alloc(&tval, tot));
+    for (int q = 0; q < NV; q++) TRY(sc.alloc(&T.v[q], tot));
     if (tot > 0) CU(cudaMemsetAsync(tkey, 0xff, sizeof(int) * (size_t)tot, s));
-    k_gemm_hash<<<nb, 128, 0, s>>>(n, a.rp, a.ci, a.v, b.rp, b.ci, b.v, toff, path, tkey, tval, cnt);
+    k_gemm_hash<NV><<<nb, 128, 0, s>>>(n, a.rp, a.ci, V, b.rp, b.ci, toff, path, tkey, T, cnt);
     LAUNCH_CHECK();
-    auto launch_lists = [&](int phase, int *cnt_, const int *crp, int *cci, double *cv) -> int {
+    auto launch_lists = [&](int phase, int *cnt_, const int *crp, int *cci, GemmOut<NV> Cv) -> int {
         if (nlist[1] > 0) {
-            k_gemm_warp<<<ceil_div(nlist[1], WARPS_PER_BLOCK), 32 * WARPS_PER_BLOCK, warp_smem(), s>>>(
-                nlist[1], a.rp, a.ci, a.v, b.rp, b.ci, b.v, list[1], phase, cnt_, crp, cci, cv);
+            k_gemm_warp<NV><<<ceil_div(nlist[1], WARPS_PER_BLOCK), 32 * WARPS_PER_BLOCK, warp_smem_bytes<NV>(), s>>>(
+                nlist[1], a.rp, a.ci, V, b.rp, b.ci, list[1], phase, cnt_, crp, cci, Cv);
             LAUNCH_CHECK();
         }
         if (nlist[2] > 0) {
-            k_gemm_dense<<<nlist[2], DENSE_ROW_TPB, dsmem, s>>>(nlist[2], list[2], b.cols, a.rp, a.ci, a.v, b.rp,
-                                                                 b.ci, b.v, phase, cnt_, crp, cci, cv);
+            k_gemm_dense<NV><<<nlist[2], DENSE_ROW_TPB, dsmem, s>>>(nlist[2], list[2], b.cols, a.rp, a.ci, V,
+                                                                     b.rp, b.ci, phase, cnt_, crp, cci, Cv);
             LAUNCH_CHECK();
         }
         if (nlist[3] > 0) {
-            k_gemm_bhash<<<nlist[3], BH_TPB, bsmem, s>>>(nlist[3], list[3], ts3, a.rp, a.ci, a.v, b.rp, b.ci, b.v,
-                                                          phase, cnt_, crp, cci, cv);
+            k_gemm_bhash<NV><<<nlist[3], BH_TPB, bsmem, s>>>(nlist[3], list[3], ts3, a.rp, a.ci, V, b.rp, b.ci,
+                                                              phase, cnt_, crp, cci, Cv);
             LAUNCH_CHECK();
         }
         return AMGH_OK;
     };
-    TRY(launch_lists(0, cnt, nullptr, nullptr, nullptr));
+    GemmOut<NV> none;
+    for (int q = 0; q < NV; q++) none.v[q] = nullptr;
+    TRY(launch_lists(0, cnt, nullptr, nullptr, none));
     TRY(ar.alloc(&c.rp, n + 1));
     int nnz = 0;
     TRY(exclusive_scan<int>(cnt, c.rp, n, s, &nnz));
     c.nnz = nnz;
     TRY(ar.alloc(&c.ci, nnz));
-    TRY(ar.alloc(&c.v, nnz));
-    k_gemm_out<<<nb, 128, 0, s>>>(n, toff, path, tkey, tval, c.rp, c.ci, c.v);
+    GemmOut<NV> Cv;
+    for (int q = 0; q < NV; q++) {
+        TRY(ar.alloc(&cv[q], nnz));
+        Cv.v[q] = cv[q];
+    }
+    c.v = cv[0];
+    k_gemm_out<NV><<<nb, 128, 0, s>>>(n, toff, path, tkey, T, c.rp, c.ci, Cv);
     LAUNCH_CHECK();
-    TRY(launch_lists(1, nullptr, c.rp, c.ci, c.v));
+    TRY(launch_lists(1, nullptr, c.rp, c.ci, Cv));
     int bad = 0;
     CU(cudaMemcpyFromSymbolAsync(&bad, g_spgemm_bad, sizeof(int), 0, cudaMemcpyDeviceToHost, s));
     CU(cudaStreamSynchronize(s));
@@ -969,6 +1038,13 @@ int spgemm(amgh_problem *p, Arena &ar, const DevCsr &a, const DevCsr &b, DevCsr 
     }
     CU(cudaStreamSynchronize(s));
     return AMGH_OK;
+}
+
+int spgemm(amgh_problem *p, Arena &ar, const DevCsr &a, const DevCsr &b, DevCsr &c)
+{
+    const double *av[1] = {a.v}, *bv[1] = {b.v};
+    double *cv[1] = {nullptr};
+    return spgemm_nv<1>(p, ar, a, av, b, bv, c, cv);
 }
 
 // entries below the diagonal take the value of their mirror above it
@@ -1024,6 +1100,40 @@ int galerkin(amgh_problem *p, Arena &ar, const DevCsr &rt, const DevCsr &a, cons
     tmp.free_all();
     if (st) return st;
     if (symmetric) TRY(symmetrize_upper(p, c));
+    return AMGH_OK;
+}
+
+// c1 = rt a1 pm and c2 = rt a2 pm for a1, a2 with one sparsity pattern (A and
+// M_y, or K_N and M_u): both products share their hashing and the result's
+// pattern (c2 uses c1's row pointers and columns); both made exactly symmetric
+int galerkin_pair(amgh_problem *p, Arena &ar, const DevCsr &rt, const DevCsr &a1, const DevCsr &a2,
+                  const DevCsr &pm, DevCsr &c1, DevCsr &c2)
+{
+    if (a1.rows != a2.rows || a1.nnz != a2.nnz) return AMGH_ERR_INVALID_ARG;
+    Arena tmp;
+    DevCsr ap;
+    double *apv[2] = {nullptr, nullptr};
+    const double *av[2] = {a1.v, a2.v}, *pv[2] = {pm.v, pm.v};
+    int st = spgemm_nv<2>(p, tmp, a1, av, pm, pv, ap, apv);
+    if (st == AMGH_OK) {
+        const double *rv[2] = {rt.v, rt.v}, *bv[2] = {apv[0], apv[1]};
+        double *cv[2] = {nullptr, nullptr};
+        st = spgemm_nv<2>(p, ar, rt, rv, ap, bv, c1, cv);
+        if (st == AMGH_OK) {
+            c2 = DevCsr();
+            c2.rows = c1.rows;
+            c2.cols = c1.cols;
+            c2.nnz = c1.nnz;
+            c2.rp = c1.rp;
+            c2.ci = c1.ci;
+            c1.v = cv[0];
+            c2.v = cv[1];
+        }
+    }
+    tmp.free_all();
+    if (st) return st;
+    TRY(symmetrize_upper(p, c1));
+    TRY(symmetrize_upper(p, c2));
     return AMGH_OK;
 }
 

@@ -359,8 +359,7 @@ static int setup_impl(amgh_problem *p)
         S.nagg = nagg;
         TRY(amg_prolongator(p, ar, S.A, S.agg, nagg, o.smooth_prolongator, S.S));
         TRY(csr_transpose(ar, S.S, S.St, s));
-        TRY(galerkin(p, ar, S.St, S.A, S.S, 1, p->sl[l + 1].A));
-        TRY(galerkin(p, ar, S.St, S.My, S.S, 1, p->sl[l + 1].My));
+        TRY(galerkin_pair(p, ar, S.St, S.A, S.My, S.S, p->sl[l + 1].A, p->sl[l + 1].My));
         p->Ls = l + 2;
         th = th * 0.5;
     }
@@ -377,8 +376,7 @@ static int setup_impl(amgh_problem *p)
         C.nagg = nagg;
         TRY(amg_prolongator(p, ar, C.KN, C.agg, nagg, o.smooth_prolongator, C.P));
         TRY(csr_transpose(ar, C.P, C.Pt, s));
-        TRY(galerkin(p, ar, C.Pt, C.KN, C.P, 1, p->cl[l + 1].KN));
-        TRY(galerkin(p, ar, C.Pt, C.Mu, C.P, 1, p->cl[l + 1].Mu));
+        TRY(galerkin_pair(p, ar, C.Pt, C.KN, C.Mu, C.P, p->cl[l + 1].KN, p->cl[l + 1].Mu));
         p->Lc = l + 2;
         th = th * 0.5;
     }

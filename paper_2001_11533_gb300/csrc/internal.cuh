@@ -409,6 +409,10 @@ int spgemm(amgh_problem *p, Arena &ar, const DevCsr &a, const DevCsr &b, DevCsr 
 int symmetrize_upper(amgh_problem *p, DevCsr &c);
 int galerkin(amgh_problem *p, Arena &ar, const DevCsr &rt, const DevCsr &a, const DevCsr &pm,
              int symmetric, DevCsr &c);
+// the same Galerkin product for two matrices with one sparsity pattern, in one
+// pass (results share row pointers and columns)
+int galerkin_pair(amgh_problem *p, Arena &ar, const DevCsr &rt, const DevCsr &a1, const DevCsr &a2,
+                  const DevCsr &pm, DevCsr &c1, DevCsr &c2);
 int l1_invdiag(amgh_problem *p, const DevCsr &a, double *invd, float *invd32);
 int diag_inv(amgh_problem *p, const DevCsr &a, double *invd);
 
