@@ -304,15 +304,19 @@ static int max_row_length(const DevCsr &a, cudaStream_t s, int *out)
 int prepare_operator(Arena &ar, DevCsr &a, cudaStream_t s, int force_tpr)
 {
     double avg = a.rows > 0 ? (double)a.nnz / a.rows : 0.0;
+    int longest = 0;
+    TRY(max_row_length(a, s, &longest));
+    // SELL-32 for short rows, and for rows up to 16 long when every row has
+    // nearly the longest length (uniform-width SELL: the staged smoother);
+    // otherwise CSR with 4..32 lanes per row
+    bool uniform = (double)longest * a.rows <= 1.05 * a.nnz;
     int tpr = 1;
     if (force_tpr > 0) tpr = force_tpr;
     else if (avg > 96.0) tpr = 32;
     else if (avg > 48.0) tpr = 16;
     else if (avg > 24.0) tpr = 8;
-    else if (avg > 16.0) tpr = 4;
+    else if (avg > 16.0 || (avg > 12.0 && !uniform)) tpr = 4;
     a.tpr = tpr;
-    int longest = 0;
-    TRY(max_row_length(a, s, &longest));
     // SELL pads every row of a slice to the slice's longest row
     a.wmax = tpr == 1 ? longest : ceil_div(longest, tpr);
     if (tpr == 1) return csr_to_sell(ar, a, 1, s);
