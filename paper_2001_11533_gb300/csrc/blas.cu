@@ -768,7 +768,8 @@ __global__ void k_df_update(int n, const float *z, const float *__restrict__ sh,
                             float *__restrict__ ph, float *__restrict__ pl, float *__restrict__ qh,
                             float *__restrict__ ql, float *__restrict__ xh, float *__restrict__ xl,
                             float *__restrict__ rh, float *__restrict__ rl, const float *__restrict__ invd32,
-                            float *znew, CgScal *sc, double *partials, unsigned *ticket)
+                            float *znew, float *__restrict__ vd, float *__restrict__ vx, float c0, CgScal *sc,
+                            double *partials, unsigned *ticket)
 {
     pdl_enter();
     SKIP_DONE();
@@ -792,7 +793,14 @@ __global__ void k_df_update(int n, const float *z, const float *__restrict__ sh,
         xl[i] = xi.lo;
         rh[i] = ri.hi;
         rl[i] = ri.lo;
-        if (invd32) znew[i] = ri.hi * invd32[i];
+        if (vd) {
+            // the V-cycle's first smoother step from zero on the new residual
+            float v = cheb_first_point(ri.hi, invd32[i], c0);
+            vd[i] = v;
+            vx[i] = v;
+        } else if (invd32) {
+            znew[i] = ri.hi * invd32[i];
+        }
         acc = df_add_fast(acc, df_mul2(ri, ri)); // squares: no cancellation
     }
     tot_df[0] = acc;
@@ -851,11 +859,11 @@ int dfcg_spmv(amgh_problem *p, RedSlot &red, const DevCsr &a, const float *z, co
 }
 
 int dfcg_update(amgh_problem *p, RedSlot &red, int n, const float *z, const double *s, double *pv, double *q,
-                double *x, double *r, CgScal *sc, const float *invd32)
+                double *x, double *r, CgScal *sc, const float *invd32, float *vd, float *vx, double c0)
 {
     pdl_launch(k_df_update, dim3(std::min(vec_blocks(n), resident_grid((const void *)k_df_update, TPB))), dim3(TPB), 0, p->stream, n, z, hi_of(s), lo_of(s, n), hi_of(pv), lo_of(pv, n),
                                                      hi_of(q), lo_of(q, n), hi_of(x), lo_of(x, n), hi_of(r),
-                                                     lo_of(r, n), invd32, (float *)z, sc, red.partials, red.ticket);
+                                                     lo_of(r, n), invd32, (float *)z, vd, vx, (float)c0, sc, red.partials, red.ticket);
     LAUNCH_CHECK();
     return AMGH_OK;
 }

@@ -379,8 +379,11 @@ int dfcg_start(amgh_problem *p, RedSlot &red, int n, const double *f, double *x,
                int maxit);
 int dfcg_spmv(amgh_problem *p, RedSlot &red, const DevCsr &a, const float *z, const double *r, double *s,
               CgScal *sc, int timed);
+// invd32 alone: Jacobi, z = D^-1 r written over z; invd32 with vd, vx: the
+// V-cycle's first smoother step on the new r written to vd and vx
 int dfcg_update(amgh_problem *p, RedSlot &red, int n, const float *z, const double *s, double *pv, double *q,
-                double *x, double *r, CgScal *sc, const float *invd32 = nullptr);
+                double *x, double *r, CgScal *sc, const float *invd32 = nullptr, float *vd = nullptr,
+                float *vx = nullptr, double c0 = 0.0);
 // z = D^-1 r (FP32) from the hi half of a double-float r
 int dfcg_jacobi(amgh_problem *p, int n, const double *r, const float *invd32, float *z);
 int df_to_double(amgh_problem *p, int n, const double *x, const CgScal *sc, double *y);

@@ -319,6 +319,12 @@ static int cg_body_iter(amgh_problem *p, int l, int mode)
         return vcyc<double>(p, l, S.cr, S.cz, &S.scal->done);
     }
     TRY(dfcg_spmv(p, S.red, S.A, S.gz, S.cr, S.cs, S.scal, timed));
+    // on a smoothing level the update also takes the V-cycle's first step
+    // (d and the level's other x buffer from the new residual)
+    if (l < p->Ls - 1) {
+        TRY(dfcg_update(p, S.red, n, S.gz, S.cs, S.cp, S.cq, S.cx, S.cr, S.scal, S.invd32, S.fd, S.fx, p->cr[0]));
+        return vcyc<float>(p, l, (const float *)S.cr, S.gz, &S.scal->done, 1);
+    }
     TRY(dfcg_update(p, S.red, n, S.gz, S.cs, S.cp, S.cq, S.cx, S.cr, S.scal));
     return vcyc<float>(p, l, (const float *)S.cr, S.gz, &S.scal->done);
 }
