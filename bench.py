@@ -167,7 +167,7 @@ def measured_peaks():
 def run_amgh(args, rank, world, local):
     import torch
 
-    from paper_2001_11533_gb300 import _build, amgh, workloads
+    from paper_2001_11533_gb300 import _build, amgh, replicas, workloads
     _build.build()
     torch.cuda.set_device(local)
     if world > 1:
@@ -243,15 +243,7 @@ def run_amgh(args, rank, world, local):
                 kstats[key] += ks[key]
         t_total = sum(times) / 1000.0
         # max over ranks of the timed total, sum of work
-        if world > 1:
-            import torch.distributed as dist
-            tt = torch.tensor([t_total], device="cuda")
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            hh = torch.tensor([float(happ)], device="cuda")
-            dist.all_reduce(hh, op=dist.ReduceOp.SUM)
-            t_total, happ_all = float(tt.item()), float(hh.item())
-        else:
-            happ_all = float(happ)
+        (t_total,), (happ_all,) = replicas.combine([t_total], [happ], device="cuda")
         results[form] = {
             "value": happ_all / t_total,
             "ms_per_step": 1000.0 * t_total / args.steps,
@@ -295,8 +287,9 @@ def run_batch(args, rank, world, local):
     that captures the CUDA graphs)."""
     import torch
 
-    from paper_2001_11533_gb300 import amgh, workloads
-    ws = [w for i, w in enumerate(workloads.batch_squares()) if i % world == rank]
+    from paper_2001_11533_gb300 import amgh, replicas, workloads
+    every = workloads.batch_squares()
+    ws = [every[i] for i in replicas.deal(len(every), rank, world)]
     yds = [torch.from_numpy(np.ascontiguousarray(w.y_d)).cuda() for w in ws]
     out = {}
     for form in ("mixed", "fp64"):
@@ -319,13 +312,7 @@ def run_batch(args, rank, world, local):
             p.close()
         t = max(times)
         happ = sum(i["hessian_applies"] for i in infos)
-        if world > 1:
-            import torch.distributed as dist
-            v = torch.tensor([t, float(happ), t_setup], device="cuda", dtype=torch.float64)
-            vmax = v.clone()
-            dist.all_reduce(vmax, op=dist.ReduceOp.MAX)
-            dist.all_reduce(v, op=dist.ReduceOp.SUM)
-            t, happ, t_setup = float(vmax[0]), float(v[1]), float(vmax[2])
+        (t, t_setup), (happ,) = replicas.combine([t, t_setup], [happ], device="cuda")
         out[form] = {"time_to_1e-8_s": t, "hessian_matvecs_per_s": happ / t, "hessian_applies": happ,
                      "setup_s": t_setup,
                      "outer_iters": sum(i["outer_iters"] for i in infos),
