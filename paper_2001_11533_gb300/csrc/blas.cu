@@ -301,7 +301,8 @@ __global__ void k_cg2_spmv_df(MatView<float> A, const float *__restrict__ lo, co
 template <typename T, typename Z>
 __global__ void k_cg2_update(int n, Z *__restrict__ z, const T *__restrict__ s, T *__restrict__ pv,
                              T *__restrict__ q, T *__restrict__ x, T *__restrict__ r, float *__restrict__ r32,
-                             const double *__restrict__ invd, CgScal *sc, double *partials, unsigned *ticket)
+                             const double *__restrict__ invd, T *__restrict__ vd, T *__restrict__ vx,
+                             const T *__restrict__ vinvd, T c0, CgScal *sc, double *partials, unsigned *ticket)
 {
     pdl_enter();
     SKIP_DONE();
@@ -319,6 +320,11 @@ __global__ void k_cg2_update(int n, Z *__restrict__ z, const T *__restrict__ s, 
         r[i] = ri;
         if (r32) r32[i] = (float)ri;
         if (invd) z[i] = (Z)(invd[i] * (double)ri);
+        if (vd) { // the V-cycle's first smoother step on the new residual
+            T v0 = cheb_first_point(ri, vinvd[i], c0);
+            vd[i] = v0;
+            vx[i] = v0;
+        }
         v[0] += (double)ri * (double)ri;
     }
     if (reduce_last_block<1>(v, partials, ticket, tot)) cg_finalize(F_RR, tot, sc, nullptr);
@@ -495,10 +501,10 @@ int cg2_spmv(amgh_problem *p, RedSlot &red, const DevCsr &a, const Z *z, const T
 
 template <typename T, typename Z>
 int cg2_update(amgh_problem *p, RedSlot &red, int n, Z *z, const T *s, T *pv, T *q, T *x, T *r, float *r32,
-               const double *invd, CgScal *sc)
+               const double *invd, CgScal *sc, T *vd, T *vx, const T *vinvd, double c0)
 {
-    pdl_launch(k_cg2_update<T, Z>, dim3(vec_blocks(n)), dim3(TPB), 0, p->stream, n, z, s, pv, q, x, r, r32, invd, sc, red.partials,
-                                                             red.ticket);
+    pdl_launch(k_cg2_update<T, Z>, dim3(vec_blocks(n)), dim3(TPB), 0, p->stream, n, z, s, pv, q, x, r, r32, invd,
+               vd, vx, vinvd, (T)c0, sc, red.partials, red.ticket);
     LAUNCH_CHECK();
     return AMGH_OK;
 }
@@ -510,11 +516,14 @@ template int cg2_spmv<double, float>(amgh_problem *, RedSlot &, const DevCsr &, 
 template int cg2_spmv<float, float>(amgh_problem *, RedSlot &, const DevCsr &, const float *, const float *, float *,
                                     CgScal *, int);
 template int cg2_update<double, double>(amgh_problem *, RedSlot &, int, double *, const double *, double *, double *,
-                                        double *, double *, float *, const double *, CgScal *);
+                                        double *, double *, float *, const double *, CgScal *, double *, double *,
+                                        const double *, double);
 template int cg2_update<double, float>(amgh_problem *, RedSlot &, int, float *, const double *, double *, double *,
-                                       double *, double *, float *, const double *, CgScal *);
+                                       double *, double *, float *, const double *, CgScal *, double *, double *,
+                                       const double *, double);
 template int cg2_update<float, float>(amgh_problem *, RedSlot &, int, float *, const float *, float *, float *,
-                                      float *, float *, float *, const double *, CgScal *);
+                                      float *, float *, float *, const double *, CgScal *, float *, float *,
+                                      const float *, double);
 
 template <typename T>
 int cg_start(amgh_problem *p, RedSlot &red, int n, const T *f, T *x, T *r, CgScal *sc, double tol, int maxit,

@@ -371,7 +371,8 @@ template <typename T, typename Z>
 int cg2_spmv(amgh_problem *p, RedSlot &red, const DevCsr &a, const Z *z, const T *r, T *s, CgScal *sc, int timed);
 template <typename T, typename Z>
 int cg2_update(amgh_problem *p, RedSlot &red, int n, Z *z, const T *s, T *pv, T *q, T *x, T *r, float *r32,
-               const double *invd, CgScal *sc);
+               const double *invd, CgScal *sc, T *vd = nullptr, T *vx = nullptr, const T *vinvd = nullptr,
+               double c0 = 0.0);
 int cg_update_outer(amgh_problem *p, RedSlot &red, int n, double *x, double *r, const double *pv, const double *q,
                     CgScal *sc);
 // double-float CG (vectors stored as hi / lo FP32 halves of an FP64-sized buffer)

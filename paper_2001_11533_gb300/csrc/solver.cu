@@ -308,15 +308,20 @@ static int cg_body_iter(amgh_problem *p, int l, int mode)
     StateLevel &S = p->sl[l];
     int n = S.A.rows;
     int timed = 0; // kernel timing covers the level-0 smoother step only
+    // on a smoothing level the update also takes the V-cycle's first step
+    // (d and the level's other x buffer from the new residual)
+    const bool pre = l < p->Ls - 1;
     if (mode == 1) {
         TRY((cg2_spmv<float, float>(p, S.red, S.A, S.gz, S.gr, S.gs, S.scal32, timed)));
-        TRY((cg2_update<float, float>(p, S.red, n, S.gz, S.gs, S.gp, S.gq, S.gx, S.gr, nullptr, nullptr, S.scal32)));
-        return vcyc<float>(p, l, S.gr, S.gz, &S.scal32->done);
+        TRY((cg2_update<float, float>(p, S.red, n, S.gz, S.gs, S.gp, S.gq, S.gx, S.gr, nullptr, nullptr, S.scal32,
+                                      pre ? S.fd : nullptr, pre ? S.fx : nullptr, S.invd32, p->cr[0])));
+        return vcyc<float>(p, l, S.gr, S.gz, &S.scal32->done, pre ? 1 : 0);
     }
     if (mode == 0) {
         TRY((cg2_spmv<double, double>(p, S.red, S.A, S.cz, S.cr, S.cs, S.scal, timed)));
-        TRY((cg2_update<double, double>(p, S.red, n, S.cz, S.cs, S.cp, S.cq, S.cx, S.cr, nullptr, nullptr, S.scal)));
-        return vcyc<double>(p, l, S.cr, S.cz, &S.scal->done);
+        TRY((cg2_update<double, double>(p, S.red, n, S.cz, S.cs, S.cp, S.cq, S.cx, S.cr, nullptr, nullptr, S.scal,
+                                        pre ? S.vd : nullptr, pre ? S.vx : nullptr, S.invd, p->cr[0])));
+        return vcyc<double>(p, l, S.cr, S.cz, &S.scal->done, pre ? 1 : 0);
     }
     TRY(dfcg_spmv(p, S.red, S.A, S.gz, S.cr, S.cs, S.scal, timed));
     // on a smoothing level the update also takes the V-cycle's first step
