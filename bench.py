@@ -355,7 +355,7 @@ def roofline_from(res, args):
     achieved = ks["bytes"] / (ks["ms"] / 1000.0) / 1e9
     return {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
             "frac": round(achieved / peak, 4), "traffic": captured_traffic(args), "peak_source": src,
-            "kernel": "k_cheb_step on level 0 (Chebyshev smoother step fused with its residual, SELL-32)",
+            "kernel": "level-0 Chebyshev smoother step (k_cheb_step_ell: uniform-width SELL-32 staged into shared memory by bulk copies)",
             "launches": ks["launches"], "avg_us": round(1000.0 * ks["ms"] / ks["launches"], 2)}
 
 
