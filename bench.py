@@ -106,9 +106,12 @@ class ClockSampler:
     """nvidia-smi clocks / throttle reasons sampled every 200 ms while running."""
 
     def __init__(self, index):
+        import tempfile
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+        # raw samples go to a scratch file (BENCH_CLOCKS_DIR if set); the JSON line carries the summary
+        out_dir = os.environ.get("BENCH_CLOCKS_DIR") or tempfile.gettempdir()
+        self.path = os.path.join(out_dir, f"clocks_rank{index}.csv")
 
     def __enter__(self):
         os.makedirs(os.path.dirname(self.path), exist_ok=True)

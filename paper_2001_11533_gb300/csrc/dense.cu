@@ -1,12 +1,14 @@
 // dense.cu -- dense coarsest-level operators (at most 4096 rows):
 //   * the explicit inverse of the coarsest AMG matrix A_{L-1} (the exact
-//     coarse solve of the V-cycle), applied as one GEMV;
+//     coarse solve of the V-cycle), applied as one GEMV (an FP32 copy serves
+//     the FP32 V-cycles);
 //   * the dense coarsest Hessian H_c = M_yu^T A_c^-1 M_y A_c^-1 M_yu + beta M_u
 //     on Hessian level l-1 and its explicit inverse -- the exact coarsest
 //     inverse G_{l-1}^-1 assumed by the theory (Sec. 3.2).
-// Both inverses come from a right-looking Cholesky factorisation A = L L^T
-// (INDEFINITE if a pivot is not positive), the triangular inverse W = L^-1
-// computed column by column (one block per column) and A^-1 = W^T W.
+// Both inverses come from a blocked right-looking Cholesky factorisation
+// A = L L^T (INDEFINITE if a pivot is not positive), the triangular inverse
+// W = L^-1 computed column by column (one warp per column) and A^-1 = W^T W
+// (upper triangle only, then mirrored).  All FP64 on CUDA cores.
 #include <math.h>
 
 #include "internal.cuh"

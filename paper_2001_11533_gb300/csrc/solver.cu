@@ -1,7 +1,8 @@
 // solver.cu -- the solve layer of the hot path, orchestrated from the host:
 //   V-cycle (Sec. 5.2's AMG preconditioner for A, levels l..L-1),
-//   AMG-preconditioned CG for A_l y = f (Sec. 5.2, inner solves) in FP64, or
-//     FP32 CG/V-cycle wrapped in FP64 iterative refinement,
+//   AMG-preconditioned CG for A_l y = f (Sec. 5.2, inner solves) in FP64,
+//     in double-float with FP32 V-cycles (precision 2), or as FP32 CG and
+//     V-cycle wrapped in FP64 iterative refinement (precision 1),
 //   Jacobi-preconditioned CG for the mass solves M_{u,l} x = b (Sec. 5.2),
 //   H_l v = M_yu^T A^-1 M_y A^-1 M_yu v + beta M_u v (Eq. firstorderpractice),
 //   Algorithm MLAS in the M_u-scaled form (Sec. 3.2, Sec. 5.2):
