@@ -69,23 +69,27 @@ __global__ void k_potrf_diag(int n, int k0, double *__restrict__ g, int *__restr
     }
 }
 
-// rows i >= k0 + NB: solve x L_kk^T = g[i, k0:k0+nb] (forward substitution)
+// rows i >= k0 + NB: solve x L_kk^T = g[i, k0:k0+nb] by forward substitution,
+// one warp per row: lane c holds x_c's running value and subtracts
+// x_q l_cq for q = 0, 1, ... in order, x_q broadcast from lane q when final
+#define TRSM_WARPS 8
 __global__ void k_trsm_panel(int n, int k0, double *__restrict__ g)
 {
     __shared__ double l[NB][NB + 1];
     int nb = min(NB, n - k0);
     for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) l[e / nb][e % nb] = g[(int64_t)(k0 + e / nb) * n + k0 + e % nb];
     __syncthreads();
-    int i = k0 + nb + blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    double x[NB];
+    int lane = threadIdx.x & 31;
+    int i = k0 + nb + blockIdx.x * TRSM_WARPS + (threadIdx.x >> 5);
+    if (i >= n) return; // warp-uniform
     double *row = g + (int64_t)i * n + k0;
-    for (int c = 0; c < nb; c++) {
-        double s = row[c];
-        for (int q = 0; q < c; q++) s -= x[q] * l[c][q];
-        x[c] = s / l[c][c];
+    double sc = lane < nb ? row[lane] : 0.0;
+    for (int q = 0; q < nb; q++) {
+        double xq = __shfl_sync(0xffffffffu, sc / l[q][q], q); // final on lane q
+        if (lane == q) sc = xq;
+        if (lane > q && lane < nb) sc -= xq * l[lane][q];
     }
-    for (int c = 0; c < nb; c++) row[c] = x[c];
+    if (lane < nb) row[lane] = sc;
 }
 
 // trailing update g[i][j] -= sum_c L[i][k0+c] L[j][k0+c] for k0+nb <= j <= i (16x16 tiles)
@@ -231,7 +235,7 @@ int dense_spd_inverse(amgh_problem *p, double *g, int n, double *inv, int *info_
         LAUNCH_CHECK();
         int rest = n - k0 - NB;
         if (rest > 0) {
-            k_trsm_panel<<<ceil_div(rest, 128), 128, 0, s>>>(n, k0, g);
+            k_trsm_panel<<<ceil_div(rest, TRSM_WARPS), 32 * TRSM_WARPS, 0, s>>>(n, k0, g);
             LAUNCH_CHECK();
             int tiles = ceil_div(rest, 16);
             k_syrk_update<<<dim3(tiles, tiles), dim3(16, 16), 0, s>>>(n, k0, g);
