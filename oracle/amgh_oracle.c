@@ -21,8 +21,18 @@
  *   the multilevel preconditioner of Sec. 3.2 (Eq. twogridinmulti,
  *   twogridinmultiactual, Algorithm MLAS) in the M_u-scaled form of Sec. 5.2:
  *     R_j b = P_j Q_{j+1} P_j^T b + beta^-1 (M_{u,j}^-1 b - P_j M_{u,j+1}^-1 P_j^T b)
- *     Q_{l-1} = H_{l-1}^-1 (dense),  Q_j = 2R_j - R_j H_j R_j (0<j<l-1),  Q_0 = R_0
+ *     Q_{l-1} = H_{l-1}^-1 (dense inverse, or CG on H_{l-1} to a relative
+ *               tolerance, chosen by the coarse-solve mode; Sec. 5.5-5.6),
+ *     Q_j = 2R_j - R_j H_j R_j (0<j<l-1),  Q_0 = R_0
  *   outer CG on H u = b (Sec. 5.3).
+ *
+ * Pins (tests/test_oracle_*.py): assembly against exact integrals, an
+ * independent assembly and harmonic linear functions; aggregation against a
+ * greedy sequential MIS(2) and a golden 5x5 grid; Galerkin products and the
+ * prolongator against their definitions; the V-cycle by symmetry, positivity
+ * and contraction; H against the dense formula, a KKT direct solve and a
+ * closed form; MLAS against its closed two-grid formula and the coarse CG
+ * against a dense solve of H_{l-1}.
  */
 #include <math.h>
 #include <stdint.h>
