@@ -287,7 +287,9 @@ def run_batch(args, rank, world, local):
     one of the 128 outer CGs to 1e-8.  Problems are dealt round-robin to the
     ranks.  Setup is timed apart; a step is one batched solve of all desired
     states (host clock around the synchronous call, after a warm-up solve
-    that captures the CUDA graphs)."""
+    that captures the CUDA graphs), once with one concurrent solve slot per
+    desired state ("columns") and once with the block solver, all 8 desired
+    states of a problem advanced together ("block")."""
     import torch
 
     from paper_2001_11533_gb300 import amgh, replicas, workloads
@@ -304,25 +306,36 @@ def run_batch(args, rank, world, local):
         t_setup = time.perf_counter() - t0
         sopts = dict(tol=1e-8, inner_tol=args.inner_tol, mass_tol=args.precond_tol,
                      precond_tol=args.precond_tol, level_fallback=1)
-        batch.solve(yds, **sopts)
-        times, infos = [], None
-        for _ in range(args.batch_steps):
-            t0 = time.perf_counter()
-            _, infos, st = batch.solve(yds, **sopts)
-            times.append(time.perf_counter() - t0)
+        controls = {}
+        for mode in ("columns", "block"):
+            batch.set_block(mode == "block")
+            batch.solve(yds, **sopts)
+            times, infos = [], None
+            for _ in range(args.batch_steps):
+                t0 = time.perf_counter()
+                us, infos, st = batch.solve(yds, **sopts)
+                times.append(time.perf_counter() - t0)
+            controls[mode] = [u.cpu().numpy() for u in us]
+            t = max(times)
+            happ = sum(i["hessian_applies"] for i in infos)
+            (t, ts), (happ,) = replicas.combine([t, t_setup], [happ], device="cuda")
+            out[form if mode == "columns" else form + "_block"] = {
+                "time_to_1e-8_s": t, "hessian_matvecs_per_s": happ / t, "hessian_applies": happ,
+                "setup_s": ts, "status": int(st),
+                "outer_iters": sum(i["outer_iters"] for i in infos),
+                "fallbacks": sum(i["fallbacks"] for i in infos),
+                "max_final_relres": max(i["final_relres"] for i in infos),
+                "hessian_levels": [i["hessian_levels"] for i in infos]}
+        # both modes run the same method per desired state: controls agree to the tolerance
+        out[form + "_block"]["max_rel_diff_vs_columns"] = max(
+            float(np.linalg.norm(a[c] - b[c]) / max(np.linalg.norm(b[c]), 1e-300))
+            for a, b in zip(controls["block"], controls["columns"]) for c in range(a.shape[0]))
         batch.close()
         for p in probs:
             p.close()
-        t = max(times)
-        happ = sum(i["hessian_applies"] for i in infos)
-        (t, t_setup), (happ,) = replicas.combine([t, t_setup], [happ], device="cuda")
-        out[form] = {"time_to_1e-8_s": t, "hessian_matvecs_per_s": happ / t, "hessian_applies": happ,
-                     "setup_s": t_setup,
-                     "outer_iters": sum(i["outer_iters"] for i in infos),
-                     "fallbacks": sum(i["fallbacks"] for i in infos),
-                     "max_final_relres": max(i["final_relres"] for i in infos),
-                     "hessian_levels": [i["hessian_levels"] for i in infos]}
     out["speedup_mixed_vs_fp64"] = out["fp64"]["time_to_1e-8_s"] / out["mixed"]["time_to_1e-8_s"]
+    out["speedup_block_vs_columns_mixed"] = (out["mixed"]["time_to_1e-8_s"]
+                                             / out["mixed_block"]["time_to_1e-8_s"])
     out["workload"] = "16 squares 65^2..513^2, 8 desired states each (128 outer CGs to 1e-8)"
     out["timing"] = "host clock around the synchronous batched solve; max of steps"
     return out

@@ -119,7 +119,7 @@ typedef struct {
  *  inner_tol    relative residual of every state/adjoint solve A y = f
  *  mass_tol     relative residual of every mass solve M_{u,j} x = b
  *  precond      0 = none (identity), 1 = multilevel / two-grid (Q_0)
- *  ncols        columns solved together (1 in this version)
+ *  ncols        must be 1 (amgh_solve_block chooses its own block width)
  *  inner_max_iter, mass_max_iter   caps of the inner CG loops
  *  precond_tol  relative residual of the state/adjoint solves of the coarse
  *               Hessians H_j, j >= 1, which occur only inside the
@@ -225,13 +225,19 @@ int amgh_set_solve_opts(amgh_problem *p, const amgh_solve_opts *opts);
 
 /* Hu = H u on the finest level (Eq. firstorderpractice): one forward and one
  * adjoint AMG-CG solve (Sec. 5.2).  u_dev, Hu_dev: n*ncols doubles, device,
- * may not alias.  Errors: NOT_SETUP, INVALID_ARG, NOT_CONVERGED, INDEFINITE,
- * NUMERIC, CUDA. */
+ * column-major (column c at offset c*n), may not alias.  ncols > 1 runs the
+ * block solver: columns in blocks of K = 2, 4 or 8 (the smallest K >= ncols,
+ * at most 8), every sparse operator applied to the K columns of a block in
+ * one pass, each column with its own inner CG scalars and stopping test; the
+ * V-cycles are FP64 for precision 0 and FP32 otherwise.
+ * Errors: NOT_SETUP, INVALID_ARG, NOT_CONVERGED, INDEFINITE, NUMERIC, CUDA
+ * (for ncols > 1: the first failing column's error). */
 int amgh_hessian_apply(amgh_problem *p, const double *u_dev, double *Hu_dev, int ncols);
 
 /* z = Q_0 r, the multilevel Hessian preconditioner in M_u-scaled form
  * (Sec. 3.2 Algorithm MLAS with Eq. twogridinmulti/twogridinmultiactual and
- * the substitution of Sec. 5.2).  r_dev, z_dev: n*ncols doubles, device. */
+ * the substitution of Sec. 5.2).  r_dev, z_dev: n*ncols doubles, device,
+ * column-major; ncols > 1 runs the block solver as amgh_hessian_apply. */
 int amgh_precond_apply(amgh_problem *p, const double *r_dev, double *z_dev, int ncols);
 
 /* b = M_yu^T A^-1 M_y y_d (right side of Eq. firstorderpractice); b_dev: n
@@ -245,6 +251,30 @@ int amgh_rhs(amgh_problem *p, double *b_dev);
  * Errors: as amgh_hessian_apply, plus NOT_CONVERGED for the outer loop. */
 int amgh_solve(amgh_problem *p, const double *u0_dev, double *u_dev, double *y_dev,
                const amgh_solve_opts *opts, amgh_solve_info *info);
+
+/* Block solve of the batching pattern: ncols independent control problems on
+ * this mesh, one per desired state, each the outer CG of Sec. 5.3 from u = 0
+ * to ||b_c - H u_c|| <= opts->tol ||b_c||.  The columns run in blocks of
+ * K = 2, 4 or 8 (the smallest K >= ncols, at most 8; a short last block is
+ * padded with zero columns): every sparse operator of the outer, inner
+ * (state, adjoint, mass) and preconditioner (Algorithm MLAS) work is applied
+ * to the K columns of a block in one pass (SpMM), while every column keeps its
+ * own CG scalars and stopping tests, so each column is the single-column
+ * method.  A failing column (indefinite, non-finite, a cap reached) stops
+ * alone; the others continue.  V-cycles are FP64 for precision 0 and FP32
+ * otherwise; the problem's own desired state is not changed.
+ *   yd_dev   ncols desired states, n_vertices doubles each, column-major,
+ *            device
+ *   u_dev    ncols controls, n doubles each, column-major, device (output;
+ *            a failed column's entries are unspecified)
+ *   opts     as amgh_solve (NULL = defaults; ncols must be 1)
+ *   info     (may be NULL) counters summed over the columns (outer_iters,
+ *            hessian_applies, inner/mass/coarse iterations), final_relres
+ *            the largest over the converged columns, status as returned
+ * Returns AMGH_OK if every column converged, else the first failing
+ * column's error (with level_fallback: after the fallbacks). */
+int amgh_solve_block(amgh_problem *p, const double *yd_dev, int ncols, double *u_dev,
+                     const amgh_solve_opts *opts, amgh_solve_info *info);
 
 /* Same as amgh_solve with HOST buffers: copies u0 (NULL ok) to the device,
  * solves, copies u (and y if not NULL) back.  This is the end-to-end call. */
@@ -353,6 +383,11 @@ typedef struct amgh_batch amgh_batch;
 int amgh_batch_create(amgh_problem *const *probs, int nprob, amgh_batch **out);
 int amgh_batch_setup(amgh_batch *b, const amgh_amg_opts *amg);
 int amgh_batch_set_workers(amgh_batch *b, int workers);
+/* block = 1: every slot solves its desired states (a contiguous share of the
+ * problem's columns) with amgh_solve_block instead of one by one, and
+ * workers = 0 then means one slot per problem; block = 0 (default) restores
+ * the per-column solves.  Errors: INVALID_ARG. */
+int amgh_batch_set_block(amgh_batch *b, int block);
 int amgh_batch_solve(amgh_batch *b, const double *const *yd_dev, const int *ncols, double *const *u_dev,
                      const amgh_solve_opts *opts, amgh_solve_info *info);
 void amgh_batch_destroy(amgh_batch *b);

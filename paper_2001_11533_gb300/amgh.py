@@ -71,6 +71,7 @@ _SIGS = {
     "amgh_rhs": ([_P, _P], _I),
     "amgh_solve": ([_P, _P, _P, _P, _P, _P], _I),
     "amgh_solve_host": ([_P, _P, _P, _P, _P, _P], _I),
+    "amgh_solve_block": ([_P, _P, _I, _P, _P, _P], _I),
     "amgh_state_solve": ([_P, _P, _P, _P], _I),
     "amgh_gradient": ([_P, _P, _P, _P], _I),
     "amgh_state_adjoint": ([_P, _P, _P], _I),
@@ -93,6 +94,7 @@ _SIGS = {
     "amgh_batch_create": ([_P, _I, _P], _I),
     "amgh_batch_setup": ([_P, _P], _I),
     "amgh_batch_set_workers": ([_P, _I], _I),
+    "amgh_batch_set_block": ([_P, _I], _I),
     "amgh_problem_share": ([_P, _P], _I),
     "amgh_batch_solve": ([_P, _P, _P, _P, _P, _P], _I),
     "amgh_batch_destroy": ([_P], None),
@@ -141,6 +143,11 @@ def _ptr(t):
 
 def launch_count() -> int:
     return int(lib().amgh_launch_count())
+
+
+def torch_empty_like(v):
+    import torch
+    return torch.empty_like(v, dtype=torch.float64)
 
 
 def aggregate_noalloc(rowptr, col, val, theta, agg_out, stream=None):
@@ -272,16 +279,23 @@ class Problem:
         return torch.empty(k, dtype=torch.float64, device="cuda")
 
     # -- the hot path
+    @staticmethod
+    def _cols(v):
+        """(n,) or (k, n) contiguous tensor: k stacked vectors, column-major n x k."""
+        if not v.is_contiguous():
+            raise ValueError("vectors must be contiguous (k, n) or (n,) tensors")
+        return 1 if v.dim() == 1 else int(v.shape[0])
+
     def hessian_apply(self, u, out=None):
-        out = self._new(u.numel()) if out is None else out
-        ncols = 1 if u.dim() == 1 else u.shape[1]
-        check(lib().amgh_hessian_apply(self.h, _ptr(u), _ptr(out), ncols), "amgh_hessian_apply")
+        """H u for u of shape (n,) or (k, n); k > 1 runs the block solver."""
+        out = torch_empty_like(u) if out is None else out
+        check(lib().amgh_hessian_apply(self.h, _ptr(u), _ptr(out), self._cols(u)), "amgh_hessian_apply")
         return out
 
     def precond_apply(self, r, out=None):
-        out = self._new(r.numel()) if out is None else out
-        ncols = 1 if r.dim() == 1 else r.shape[1]
-        check(lib().amgh_precond_apply(self.h, _ptr(r), _ptr(out), ncols), "amgh_precond_apply")
+        """Q_0 r for r of shape (n,) or (k, n); k > 1 runs the block solver."""
+        out = torch_empty_like(r) if out is None else out
+        check(lib().amgh_precond_apply(self.h, _ptr(r), _ptr(out), self._cols(r)), "amgh_precond_apply")
         return out
 
     def rhs(self):
@@ -298,6 +312,20 @@ class Problem:
         if raise_on_error:
             check(st, "amgh_solve")
         return u, y, info.as_dict()
+
+    def solve_block(self, yds, raise_on_error=True, **kw):
+        """Controls for k desired states yds (CUDA float64, shape (k, n_vertices))
+        solved together by the block solver; returns ((k, n) controls, info, status)."""
+        import torch
+        yds = yds.contiguous()
+        k = int(yds.shape[0])
+        u = torch.empty((k, self.sizes["n"]), dtype=torch.float64, device=yds.device)
+        info = amgh_solve_info()
+        o = solve_opts(**kw)
+        st = lib().amgh_solve_block(self.h, _ptr(yds), k, _ptr(u), C.byref(o), C.byref(info))
+        if raise_on_error:
+            check(st, "amgh_solve_block")
+        return u, info.as_dict(), st
 
     def solve_host(self, u0=None, want_y=True, **kw):
         o = solve_opts(**kw)
@@ -407,15 +435,22 @@ class Problem:
 class Batch:
     """Many independent problems, several desired states each, solved
     concurrently (amgh_batch_*): per problem up to `workers` slots (0 = one per
-    desired state), each with its own CUDA stream and native host thread."""
+    desired state, or one per problem with block=True), each with its own CUDA
+    stream and native host thread; block=True solves a slot's desired states
+    together with the block solver."""
 
-    def __init__(self, problems, workers=0):
+    def __init__(self, problems, workers=0, block=False):
         self.problems = list(problems)
         arr = (C.c_void_p * len(self.problems))(*[p.h.value for p in self.problems])
         h = C.c_void_p()
         check(lib().amgh_batch_create(arr, len(self.problems), C.byref(h)), "amgh_batch_create")
         self.h = h
         check(lib().amgh_batch_set_workers(self.h, int(workers)), "amgh_batch_set_workers")
+        check(lib().amgh_batch_set_block(self.h, 1 if block else 0), "amgh_batch_set_block")
+
+    def set_block(self, block=True):
+        check(lib().amgh_batch_set_block(self.h, 1 if block else 0), "amgh_batch_set_block")
+        return self
 
     def setup(self, **kw):
         o = amg_opts(**kw)

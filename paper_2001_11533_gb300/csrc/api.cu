@@ -253,6 +253,7 @@ extern "C" int amgh_set_solve_opts(amgh_problem *p, const amgh_solve_opts *o)
 // ------------------------------------------------------------------ setup
 static void reset_hierarchy(amgh_problem *p)
 {
+    block_free(p);
     solver_free_graphs(p);
     p->harena.free_all();
     for (int l = 0; l < AMGH_MAXL; l++) {
@@ -465,7 +466,8 @@ extern "C" int amgh_hessian_apply(amgh_problem *p, const double *u, double *hu, 
     NEED_SETUP(p);
     StreamScope ss_(p->stream);
     if (!u || !hu || ncols < 1) return AMGH_ERR_INVALID_ARG;
-    for (int c = 0; c < ncols; c++) TRY(hessian_level(p, 0, u + (int64_t)c * p->n, hu + (int64_t)c * p->n));
+    if (ncols > 1) TRY(block_hessian_apply(p, u, hu, ncols));
+    else TRY(hessian_level(p, 0, u, hu));
     TRY(timer_collect(p));
     return sync_stream(p);
 }
@@ -475,7 +477,8 @@ extern "C" int amgh_precond_apply(amgh_problem *p, const double *r, double *z, i
     NEED_SETUP(p);
     StreamScope ss_(p->stream);
     if (!r || !z || ncols < 1) return AMGH_ERR_INVALID_ARG;
-    for (int c = 0; c < ncols; c++) TRY(mlas_Q(p, 0, r + (int64_t)c * p->n, z + (int64_t)c * p->n));
+    if (ncols > 1) TRY(block_precond_apply(p, r, z, ncols));
+    else TRY(mlas_Q(p, 0, r, z));
     TRY(timer_collect(p));
     return sync_stream(p);
 }
@@ -540,6 +543,47 @@ extern "C" int amgh_solve(amgh_problem *p, const double *u0, double *u, double *
     int st2 = timer_collect(p);
     if (st == AMGH_OK) st = st2;
     if (st == AMGH_OK) st = sync_stream(p);
+    if (st == AMGH_OK) st = bulk_timeout_check(p->stream);
+    return st;
+}
+
+extern "C" int amgh_solve_block(amgh_problem *p, const double *yd, int ncols, double *u,
+                                const amgh_solve_opts *opts, amgh_solve_info *info)
+{
+    NEED_SETUP(p);
+    StreamScope ss_(p->stream);
+    if (!yd || !u || ncols < 1) return AMGH_ERR_INVALID_ARG;
+    amgh_solve_opts o;
+    if (opts) o = *opts;
+    else amgh_solve_opts_default(&o);
+    if (!(o.tol > 0.0) || o.max_iter < 1 || o.ncols != 1) return AMGH_ERR_INVALID_ARG;
+    TRY(amgh_set_solve_opts(p, &o));
+    zero_counters(p);
+    double t0 = now_s();
+    amgh_solve_info loc;
+    memset(&loc, 0, sizeof(loc));
+    int st = block_solve(p, yd, ncols, u, o, &loc);
+    int fallbacks = 0;
+    // as amgh_solve: an indefinite preconditioner drops the coarsest Hessian
+    // level and the whole block restarts from u = 0
+    while (st == AMGH_ERR_INDEFINITE && o.level_fallback && o.precond && p->ell > 2) {
+        if (p->aopts.coarse_solve == 0 && p->cl[p->ell - 2].Mu.rows > AMGH_DENSE_MAX) break;
+        int s2 = coarse_hessian_setup(p, p->ell - 1);
+        if (s2) {
+            st = s2;
+            break;
+        }
+        fallbacks++;
+        memset(&loc, 0, sizeof(loc));
+        st = block_solve(p, yd, ncols, u, o, &loc);
+    }
+    fill_info(p, &loc);
+    loc.status = st;
+    loc.fallbacks = fallbacks;
+    loc.t_solve_s = now_s() - t0;
+    if (info) *info = loc;
+    int st2 = sync_stream(p);
+    if (st == AMGH_OK) st = st2;
     if (st == AMGH_OK) st = bulk_timeout_check(p->stream);
     return st;
 }
@@ -806,6 +850,7 @@ extern "C" void amgh_problem_destroy(amgh_problem *p)
     else cudaDeviceSynchronize();
     for (auto e : p->timer.ev) cudaEventDestroy(e);
     for (auto e : p->timer.pool) cudaEventDestroy(e);
+    block_free(p);
     solver_free_graphs(p);
     p->harena.free_all();
     p->arena.free_all();

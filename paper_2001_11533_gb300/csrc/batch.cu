@@ -7,7 +7,9 @@
 // hierarchies, own work space and graphs).  Each slot has its own
 // non-blocking stream and host thread and takes the columns c = s, s + w,
 // ... of its problem, so the small, latency-bound coarse-level work of many
-// solves overlaps on the GPU.  Host threads wait on blocking-sync events, so
+// solves overlaps on the GPU.  In block mode a slot instead takes a
+// contiguous share of its problem's columns and solves them with
+// amgh_solve_block (every operator applied to up to 8 columns per pass).  Host threads wait on blocking-sync events, so
 // more threads than cores do not spin against each other.
 #include <string.h>
 
@@ -28,6 +30,7 @@ struct amgh_batch {
     std::vector<void *> old_streams;
     std::vector<std::vector<BatchSlot>> slots; // [problem][slot]
     int workers = 0;                           // slots per problem (0 = one per column)
+    int block = 0;                             // 1: slots run amgh_solve_block
     int device = 0;
 };
 
@@ -114,6 +117,13 @@ extern "C" int amgh_batch_set_workers(amgh_batch *b, int workers)
     return AMGH_OK;
 }
 
+extern "C" int amgh_batch_set_block(amgh_batch *b, int block)
+{
+    if (!b || (block != 0 && block != 1)) return AMGH_ERR_INVALID_ARG;
+    b->block = block;
+    return AMGH_OK;
+}
+
 extern "C" int amgh_batch_setup(amgh_batch *b, const amgh_amg_opts *amg)
 {
     if (!b) return AMGH_ERR_INVALID_ARG;
@@ -154,6 +164,7 @@ extern "C" int amgh_batch_solve(amgh_batch *b, const double *const *yd, const in
     for (int i = 0; i < np; i++) {
         if (pst[i] || ncols[i] == 0) continue;
         int want = b->workers > 0 && b->workers < ncols[i] ? b->workers : ncols[i];
+        if (b->block && b->workers == 0) want = 1;
         auto &v = b->slots[i];
         while ((int)v.size() < want) {
             BatchSlot s;
@@ -171,11 +182,22 @@ extern "C" int amgh_batch_solve(amgh_batch *b, const double *const *yd, const in
         amgh_problem *p = b->slots[w.prob][w.slot].h;
         amgh_solve_info &a = acc[wi];
         memset(&a, 0, sizeof(a));
-        for (int c = w.slot; c < ncols[w.prob]; c += w.nslot) {
-            int s = amgh_set_yd(p, yd[w.prob] + (int64_t)c * p->nv, 1);
+        // block mode: one contiguous share of the columns per slot, one call
+        int nc = ncols[w.prob], share = (nc + w.nslot - 1) / w.nslot;
+        int c_lo = b->block ? w.slot * share : w.slot;
+        int c_hi = b->block ? (c_lo + share < nc ? c_lo + share : nc) : nc;
+        int step = b->block ? share : w.nslot;
+        for (int c = c_lo; c < c_hi; c += step) {
             amgh_solve_info one;
             memset(&one, 0, sizeof(one));
-            if (s == AMGH_OK) s = amgh_solve(p, nullptr, u[w.prob] + (int64_t)c * p->n, nullptr, opts, &one);
+            int s;
+            if (b->block) {
+                s = amgh_solve_block(p, yd[w.prob] + (int64_t)c * p->nv, c_hi - c, u[w.prob] + (int64_t)c * p->n,
+                                     opts, &one);
+            } else {
+                s = amgh_set_yd(p, yd[w.prob] + (int64_t)c * p->nv, 1);
+                if (s == AMGH_OK) s = amgh_solve(p, nullptr, u[w.prob] + (int64_t)c * p->n, nullptr, opts, &one);
+            }
             a.outer_iters += one.outer_iters;
             a.hessian_applies += one.hessian_applies;
             a.inner_iters += one.inner_iters;

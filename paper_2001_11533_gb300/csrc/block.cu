@@ -1,0 +1,1717 @@
+// block.cu -- block (multi-column) solves: many desired states of one control
+// problem, or many vectors of one operator, advanced together.
+//
+// K columns (K = 2, 4 or 8; a short last block is padded with zero columns)
+// are stored interleaved -- entry i of column c at i*K + c -- so every row of
+// a sparse operator is read once for all K columns and the K values gathered
+// per column index are one contiguous 4K- or 8K-byte load: SpMM instead of K
+// SpMVs, and one launch instead of K.
+//
+// Per column the method is the single-column one: the same single-reduction
+// PCG for the state and adjoint solves (AMG V-cycle preconditioner) and for
+// the mass solves (Jacobi), the same V-cycle, the multilevel preconditioner of
+// Algorithm MLAS (Sec. 3.2, in the M_u-scaled form of Sec. 5.2) and the outer
+// CG of Sec. 5.3.  Every column keeps its own CG scalars and stopping test; a
+// column that has stopped is not updated again, and every launch of an inner
+// CG loop returns at once when all its columns have stopped, so iterations
+// are replayed from CUDA graphs in chunks as in the single-column solver.  A
+// column that fails (indefinite, non-finite, cap reached) is marked failed and
+// dropped; the other columns carry on.
+//
+// Precision: precision 0 runs FP64 V-cycles and FP64 CG products, as the
+// single-column FP64 path; precisions 1 and 2 run FP32 V-cycles, and the CG
+// operator products A z and M z are accumulated in double-float on the FP32
+// pipe from A = A_hi + A_lo (the refinement form of precision 1 has no block
+// variant).  CG vectors are FP64 throughout, and the control-side operators
+// (M_yu, M_y, M_u, P and their transposes) are applied in FP64.
+#include <math.h>
+#include <string.h>
+
+#include <functional>
+
+#include "internal.cuh"
+#include "spmv.cuh"
+#include "util.cuh"
+
+#define KB AMGH_BLOCK_MAX
+
+static const int TPB = 256;
+
+static inline int vblocks(int64_t n)
+{
+    int nb = ceil_div(n > 0 ? n : 1, TPB);
+    return nb < 2432 ? nb : 2432; // 152 SMs x 16 blocks of 256 threads
+}
+
+// per-column CG scalars of one block loop
+struct BScal {
+    CgScal c[KB];
+    int all; // every column has stopped
+    int pad[3];
+};
+
+// ------------------------------------------------------------------ K-vectors
+// K consecutive values of one row; the base is 4K- or 8K-byte aligned (block
+// buffers come from the pool, 256-byte aligned, and rows are K values apart)
+template <int K>
+__device__ __forceinline__ void ldk(const float *p, float (&v)[K])
+{
+    if constexpr (K % 4 == 0) {
+#pragma unroll
+        for (int i = 0; i < K / 4; i++) {
+            float4 w = reinterpret_cast<const float4 *>(p)[i];
+            v[4 * i] = w.x;
+            v[4 * i + 1] = w.y;
+            v[4 * i + 2] = w.z;
+            v[4 * i + 3] = w.w;
+        }
+    } else if constexpr (K % 2 == 0) {
+#pragma unroll
+        for (int i = 0; i < K / 2; i++) {
+            float2 w = reinterpret_cast<const float2 *>(p)[i];
+            v[2 * i] = w.x;
+            v[2 * i + 1] = w.y;
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < K; i++) v[i] = p[i];
+    }
+}
+
+template <int K>
+__device__ __forceinline__ void ldk(const double *p, double (&v)[K])
+{
+    if constexpr (K % 2 == 0) {
+#pragma unroll
+        for (int i = 0; i < K / 2; i++) {
+            double2 w = reinterpret_cast<const double2 *>(p)[i];
+            v[2 * i] = w.x;
+            v[2 * i + 1] = w.y;
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < K; i++) v[i] = p[i];
+    }
+}
+
+// read-only gathers (the source is not written by the same kernel)
+template <int K>
+__device__ __forceinline__ void ldk_ro(const float *p, float (&v)[K])
+{
+    if constexpr (K % 4 == 0) {
+#pragma unroll
+        for (int i = 0; i < K / 4; i++) {
+            float4 w = __ldg(reinterpret_cast<const float4 *>(p) + i);
+            v[4 * i] = w.x;
+            v[4 * i + 1] = w.y;
+            v[4 * i + 2] = w.z;
+            v[4 * i + 3] = w.w;
+        }
+    } else if constexpr (K % 2 == 0) {
+#pragma unroll
+        for (int i = 0; i < K / 2; i++) {
+            float2 w = __ldg(reinterpret_cast<const float2 *>(p) + i);
+            v[2 * i] = w.x;
+            v[2 * i + 1] = w.y;
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < K; i++) v[i] = __ldg(p + i);
+    }
+}
+
+template <int K>
+__device__ __forceinline__ void ldk_ro(const double *p, double (&v)[K])
+{
+    if constexpr (K % 2 == 0) {
+#pragma unroll
+        for (int i = 0; i < K / 2; i++) {
+            double2 w = __ldg(reinterpret_cast<const double2 *>(p) + i);
+            v[2 * i] = w.x;
+            v[2 * i + 1] = w.y;
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < K; i++) v[i] = __ldg(p + i);
+    }
+}
+
+template <int K>
+__device__ __forceinline__ void stk(float *p, const float (&v)[K])
+{
+    if constexpr (K % 4 == 0) {
+#pragma unroll
+        for (int i = 0; i < K / 4; i++)
+            reinterpret_cast<float4 *>(p)[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+    } else if constexpr (K % 2 == 0) {
+#pragma unroll
+        for (int i = 0; i < K / 2; i++) reinterpret_cast<float2 *>(p)[i] = make_float2(v[2 * i], v[2 * i + 1]);
+    } else {
+#pragma unroll
+        for (int i = 0; i < K; i++) p[i] = v[i];
+    }
+}
+
+template <int K>
+__device__ __forceinline__ void stk(double *p, const double (&v)[K])
+{
+    if constexpr (K % 2 == 0) {
+#pragma unroll
+        for (int i = 0; i < K / 2; i++) reinterpret_cast<double2 *>(p)[i] = make_double2(v[2 * i], v[2 * i + 1]);
+    } else {
+#pragma unroll
+        for (int i = 0; i < K; i++) p[i] = v[i];
+    }
+}
+
+// Rows of at most ROW_UNROLL entries per lane: every value and index load is
+// issued first, then the gathers in chunks of U entries (U * K values held
+// at once), then the sums in entry order -- two or three memory round trips
+// per row instead of one per entry.  Longer rows take the plain loop.
+template <typename T, int K>
+struct Chunk {
+    static constexpr int U = (int)sizeof(T) * K <= 32 ? ROW_UNROLL : ROW_UNROLL / 2;
+};
+
+// row of A times K columns of x; every lane of the group returns the K sums
+template <typename T, int TPR, int K>
+__device__ __forceinline__ void row_sum_k(const MatView<T> &m, int row, const T *__restrict__ x, T (&acc)[K])
+{
+    constexpr int STEP = TPR == 1 ? 32 : TPR;
+    constexpr int U = Chunk<T, K>::U;
+#pragma unroll
+    for (int c = 0; c < K; c++) acc[c] = (T)0;
+    if (row < m.rows) {
+        int k, end;
+        lane_range<T, TPR>(m, row, k, end);
+        if (m.wmax <= ROW_UNROLL) {
+            T vv[ROW_UNROLL];
+            int cc[ROW_UNROLL];
+#pragma unroll
+            for (int j = 0; j < ROW_UNROLL; j++) {
+                bool ok = k + STEP * j < end;
+                vv[j] = ok ? m.v[k + STEP * j] : (T)0;
+                cc[j] = ok ? col_of(m, row, k + STEP * j) : -1;
+            }
+#pragma unroll
+            for (int j0 = 0; j0 < ROW_UNROLL; j0 += U) {
+                T xv[U][K];
+#pragma unroll
+                for (int j = 0; j < U; j++) {
+                    if (cc[j0 + j] >= 0) ldk_ro<K>(x + (int64_t)cc[j0 + j] * K, xv[j]);
+                    else {
+#pragma unroll
+                        for (int c = 0; c < K; c++) xv[j][c] = (T)0;
+                    }
+                }
+#pragma unroll
+                for (int j = 0; j < U; j++) {
+                    if (cc[j0 + j] < 0) continue;
+#pragma unroll
+                    for (int c = 0; c < K; c++) acc[c] = rfma(vv[j0 + j], xv[j][c], acc[c]);
+                }
+            }
+        } else {
+#pragma unroll 2
+            for (; k < end; k += STEP) {
+                T a = m.v[k];
+                T xv[K];
+                ldk_ro<K>(x + (int64_t)col_of(m, row, k) * K, xv);
+#pragma unroll
+                for (int c = 0; c < K; c++) acc[c] = rfma(a, xv[c], acc[c]);
+            }
+        }
+    }
+    if (TPR > 1) {
+#pragma unroll
+        for (int c = 0; c < K; c++) {
+#pragma unroll
+            for (int o = TPR / 2; o > 0; o >>= 1) acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], o, TPR);
+        }
+    }
+}
+
+// row of (A_hi + A_lo) times K columns of z, accumulated in double-float
+template <typename Z, int TPR, int K>
+__device__ __forceinline__ void row_sum_df_k(const MatView<float> &m, const float *__restrict__ lo, int row,
+                                             const Z *__restrict__ z, double (&out)[K])
+{
+    constexpr int STEP = TPR == 1 ? 32 : TPR;
+    constexpr int U = Chunk<Z, K>::U;
+    DF acc[K];
+#pragma unroll
+    for (int c = 0; c < K; c++) acc[c] = DF{0.f, 0.f};
+    if (row < m.rows) {
+        int k, end;
+        lane_range<float, TPR>(m, row, k, end);
+        if (m.wmax <= ROW_UNROLL) {
+            float vh[ROW_UNROLL], vl[ROW_UNROLL];
+            int cc[ROW_UNROLL];
+#pragma unroll
+            for (int j = 0; j < ROW_UNROLL; j++) {
+                bool ok = k + STEP * j < end;
+                vh[j] = ok ? m.v[k + STEP * j] : 0.f;
+                vl[j] = ok ? lo[k + STEP * j] : 0.f;
+                cc[j] = ok ? col_of(m, row, k + STEP * j) : -1;
+            }
+#pragma unroll
+            for (int j0 = 0; j0 < ROW_UNROLL; j0 += U) {
+                Z zv[U][K];
+#pragma unroll
+                for (int j = 0; j < U; j++) {
+                    if (cc[j0 + j] >= 0) ldk_ro<K>(z + (int64_t)cc[j0 + j] * K, zv[j]);
+                    else {
+#pragma unroll
+                        for (int c = 0; c < K; c++) zv[j][c] = (Z)0;
+                    }
+                }
+#pragma unroll
+                for (int j = 0; j < U; j++) {
+                    if (cc[j0 + j] < 0) continue;
+#pragma unroll
+                    for (int c = 0; c < K; c++) df_term<Z>(acc[c], vh[j0 + j], vl[j0 + j], zv[j][c]);
+                }
+            }
+        } else {
+#pragma unroll 2
+            for (; k < end; k += STEP) {
+                float ah = m.v[k], al = lo[k];
+                Z zv[K];
+                ldk_ro<K>(z + (int64_t)col_of(m, row, k) * K, zv);
+#pragma unroll
+                for (int c = 0; c < K; c++) df_term<Z>(acc[c], ah, al, zv[c]);
+            }
+        }
+    }
+    if (TPR > 1) {
+#pragma unroll
+        for (int c = 0; c < K; c++) {
+#pragma unroll
+            for (int o = TPR / 2; o > 0; o >>= 1) {
+                DF other = {__shfl_xor_sync(0xffffffffu, acc[c].hi, o, TPR),
+                            __shfl_xor_sync(0xffffffffu, acc[c].lo, o, TPR)};
+                df_merge(acc[c], other);
+            }
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < K; c++) out[c] = (double)acc[c].hi + (double)acc[c].lo;
+}
+
+// ------------------------------------------------------------------ finalisers
+__device__ __forceinline__ bool nonfinite(double x) { return !(x == x) || isinf(x); }
+
+template <int K>
+__device__ void bs_all(BScal *bs)
+{
+    int a = 1;
+#pragma unroll
+    for (int c = 0; c < K; c++) a &= bs->c[c].done != 0;
+    bs->all = a;
+}
+
+// f.f per column: stopping threshold tol^2 f.f; a zero column has converged
+template <int K>
+__device__ void fin_start(BScal *bs, const double (&t)[K], double tol2, int maxit)
+{
+    for (int c = 0; c < K; c++) {
+        CgScal &s = bs->c[c];
+        double ff = t[c];
+        s.ff = ff;
+        s.rr = ff;
+        s.thr = tol2 * ff;
+        s.maxit = maxit;
+        s.iters = 0;
+        s.k1 = 0;
+        s.alpha = 0.0;
+        s.beta = 0.0;
+        s.rz = 0.0;
+        s.status = CG_RUNNING;
+        s.done = 0;
+        // power of two nearest 1 / ||f||: the FP32 V-cycle sees r scaled by it
+        // (exact, and PCG is invariant under a scalar multiple of the
+        // preconditioner), which keeps tiny residuals inside FP32's range
+        double nrm = sqrt(ff);
+        s.scale = (nrm > 0.0 && !nonfinite(nrm)) ? exp2(-rint(log2(nrm))) : 1.0;
+        if (nonfinite(ff)) {
+            s.status = CG_NUMERIC;
+            s.done = 1;
+        } else if (ff == 0.0) {
+            s.status = CG_CONVERGED;
+            s.done = 1;
+        }
+    }
+    bs_all<K>(bs);
+}
+
+// single-reduction PCG: gamma = (r, z), delta = (z, A z) -> alpha, beta
+template <int K>
+__device__ void fin_cg2(BScal *bs, const double (&t)[2 * K])
+{
+    for (int c = 0; c < K; c++) {
+        CgScal &s = bs->c[c];
+        if (s.done) continue;
+        double g = t[c], d = t[K + c];
+        if (!(g > 0.0) || !(d > 0.0)) {
+            s.status = (nonfinite(g) || nonfinite(d)) ? CG_NUMERIC : CG_INDEFINITE;
+            s.done = 1;
+            continue;
+        }
+        double beta = 0.0, alpha;
+        if (s.k1 == 0) {
+            alpha = g / d;
+        } else {
+            beta = g / s.rz;
+            double den = d - beta * g / s.alpha;
+            if (!(den > 0.0)) {
+                s.status = nonfinite(den) ? CG_NUMERIC : CG_INDEFINITE;
+                s.done = 1;
+                continue;
+            }
+            alpha = g / den;
+        }
+        s.rz = g;
+        s.alpha = alpha;
+        s.beta = beta;
+        s.k1 += 1;
+    }
+    bs_all<K>(bs);
+}
+
+// r.r per column -> iteration count and stopping test
+template <int K>
+__device__ void fin_rr(BScal *bs, const double (&t)[K])
+{
+    for (int c = 0; c < K; c++) {
+        CgScal &s = bs->c[c];
+        if (s.done) continue;
+        double rr = t[c];
+        s.rr = rr;
+        s.iters += 1;
+        s.total_iters += 1;
+        if (nonfinite(rr)) {
+            s.status = CG_NUMERIC;
+            s.done = 1;
+        } else if (rr <= s.thr) {
+            s.status = CG_CONVERGED;
+            s.done = 1;
+        } else if (s.iters >= s.maxit) {
+            s.status = CG_MAXIT;
+            s.done = 1;
+        }
+    }
+    bs_all<K>(bs);
+}
+
+// ------------------------------------------------------------------ CG kernels
+// x = 0, r = f, optionally z = invd f (Jacobi); f.f per column
+template <int K>
+__global__ void kb_cg_start(int n, const double *__restrict__ f, double *__restrict__ x, double *__restrict__ r,
+                            double *__restrict__ z, const double *__restrict__ invd, BScal *bs, double tol2,
+                            int maxit, double *partials, unsigned *ticket)
+{
+    pdl_enter();
+    double v[K], tot[K];
+#pragma unroll
+    for (int c = 0; c < K; c++) v[c] = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        int64_t o = (int64_t)i * K;
+        double fv[K], zero[K];
+        ldk<K>(f + o, fv);
+#pragma unroll
+        for (int c = 0; c < K; c++) zero[c] = 0.0;
+        stk<K>(x + o, zero);
+        stk<K>(r + o, fv);
+        if (z) {
+            double iv = invd[i], zv[K];
+#pragma unroll
+            for (int c = 0; c < K; c++) zv[c] = iv * fv[c];
+            stk<K>(z + o, zv);
+        }
+#pragma unroll
+        for (int c = 0; c < K; c++) v[c] += fv[c] * fv[c];
+    }
+    if (reduce_last_block<K>(v, partials, ticket, tot)) fin_start<K>(bs, tot, tol2, maxit);
+}
+
+// r32 = (float)(scale_c r): input of the FP32 V-cycle
+template <int K>
+__global__ void kb_r32(int n, const double *__restrict__ r, float *__restrict__ r32, const BScal *bs)
+{
+    pdl_enter();
+    if (bs->all) return;
+    double sc[K];
+#pragma unroll
+    for (int c = 0; c < K; c++) sc[c] = bs->c[c].scale;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        int64_t o = (int64_t)i * K;
+        double rv[K];
+        float f[K];
+        ldk<K>(r + o, rv);
+#pragma unroll
+        for (int c = 0; c < K; c++) f[c] = (float)(rv[c] * sc[c]);
+        stk<K>(r32 + o, f);
+    }
+}
+
+// s = A z (double-float products), (r, z) and (z, s) per column -> alpha, beta
+template <typename Z, int TPR, int K>
+__global__ void kb_cg_spmv(MatView<float> A, const float *__restrict__ lo, const Z *__restrict__ z,
+                           const double *__restrict__ r, double *__restrict__ s, BScal *bs, double *partials,
+                           unsigned *ticket)
+{
+    pdl_enter();
+    if (bs->all) return;
+    int row = my_row<TPR>();
+    double sv[K];
+    row_sum_df_k<Z, TPR, K>(A, lo, row, z, sv);
+    double a[2 * K], tot[2 * K];
+#pragma unroll
+    for (int q = 0; q < 2 * K; q++) a[q] = 0.0;
+    if (row < A.rows && row_leader<TPR>()) {
+        int64_t o = (int64_t)row * K;
+        stk<K>(s + o, sv);
+        Z zr[K];
+        double rr[K];
+        ldk_ro<K>(z + o, zr);
+        ldk<K>(r + o, rr);
+#pragma unroll
+        for (int c = 0; c < K; c++) {
+            double zc = (double)zr[c];
+            a[c] = rr[c] * zc;
+            a[K + c] = zc * sv[c];
+        }
+    }
+    if (reduce_last_block<2 * K>(a, partials, ticket, tot)) fin_cg2<K>(bs, tot);
+}
+
+// the same with FP64 products (precision 0, as the single-column FP64 CG)
+template <int TPR, int K>
+__global__ void kb_cg_spmv64(MatView<double> A, const double *__restrict__ z, const double *__restrict__ r,
+                             double *__restrict__ s, BScal *bs, double *partials, unsigned *ticket)
+{
+    pdl_enter();
+    if (bs->all) return;
+    int row = my_row<TPR>();
+    double sv[K];
+    row_sum_k<double, TPR, K>(A, row, z, sv);
+    double a[2 * K], tot[2 * K];
+#pragma unroll
+    for (int q = 0; q < 2 * K; q++) a[q] = 0.0;
+    if (row < A.rows && row_leader<TPR>()) {
+        int64_t o = (int64_t)row * K;
+        stk<K>(s + o, sv);
+        double zr[K], rr[K];
+        ldk_ro<K>(z + o, zr);
+        ldk<K>(r + o, rr);
+#pragma unroll
+        for (int c = 0; c < K; c++) {
+            a[c] = rr[c] * zr[c];
+            a[K + c] = zr[c] * sv[c];
+        }
+    }
+    if (reduce_last_block<2 * K>(a, partials, ticket, tot)) fin_cg2<K>(bs, tot);
+}
+
+// p = z + beta p, q = s + beta q, x += alpha p, r -= alpha q per running
+// column; optionally r32 = (float)(scale_c r) or, for Jacobi, z = invd r; r.r
+// per column
+template <typename Z, int K>
+__global__ void kb_cg_update(int n, Z *z, const double *__restrict__ s, double *__restrict__ pv,
+                             double *__restrict__ q, double *__restrict__ x, double *__restrict__ r,
+                             float *__restrict__ r32, const double *__restrict__ invd, BScal *bs, double *partials,
+                             unsigned *ticket)
+{
+    pdl_enter();
+    if (bs->all) return;
+    double al[K], be[K], scl[K];
+    bool run[K], first[K];
+#pragma unroll
+    for (int c = 0; c < K; c++) {
+        const CgScal &sc = bs->c[c];
+        al[c] = sc.alpha;
+        be[c] = sc.beta;
+        scl[c] = sc.scale;
+        run[c] = !sc.done;
+        first[c] = sc.beta == 0.0;
+    }
+    double v[K], tot[K];
+#pragma unroll
+    for (int c = 0; c < K; c++) v[c] = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        int64_t o = (int64_t)i * K;
+        Z zv[K];
+        double sv[K], pp[K], qq[K], xx[K], rr[K];
+        ldk<K>(z + o, zv);
+        ldk<K>(s + o, sv);
+        ldk<K>(pv + o, pp);
+        ldk<K>(q + o, qq);
+        ldk<K>(x + o, xx);
+        ldk<K>(r + o, rr);
+#pragma unroll
+        for (int c = 0; c < K; c++) {
+            if (!run[c]) continue;
+            double zc = (double)zv[c];
+            double pc = first[c] ? zc : zc + be[c] * pp[c];
+            double qc = first[c] ? sv[c] : sv[c] + be[c] * qq[c];
+            pp[c] = pc;
+            qq[c] = qc;
+            xx[c] = xx[c] + al[c] * pc;
+            rr[c] = rr[c] - al[c] * qc;
+        }
+        stk<K>(pv + o, pp);
+        stk<K>(q + o, qq);
+        stk<K>(x + o, xx);
+        stk<K>(r + o, rr);
+        if (r32) {
+            float f[K];
+#pragma unroll
+            for (int c = 0; c < K; c++) f[c] = (float)(rr[c] * scl[c]);
+            stk<K>(r32 + o, f);
+        }
+        if (invd) {
+            double iv = invd[i];
+            Z zn[K];
+#pragma unroll
+            for (int c = 0; c < K; c++) zn[c] = (Z)(iv * rr[c]);
+            stk<K>(z + o, zn);
+        }
+#pragma unroll
+        for (int c = 0; c < K; c++) v[c] += rr[c] * rr[c];
+    }
+    if (reduce_last_block<K>(v, partials, ticket, tot)) fin_rr<K>(bs, tot);
+}
+
+// ------------------------------------------------------------------ V-cycle kernels
+// first smoother step from zero: d = x = c D^-1 b
+template <typename T, int K>
+__global__ void kb_cheb_first(int n, const T *__restrict__ invd, const T *__restrict__ b, T *__restrict__ d,
+                              T *__restrict__ x, T cf, const BScal *bs)
+{
+    pdl_enter();
+    if (bs && bs->all) return;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        int64_t o = (int64_t)i * K;
+        T bv[K], w[K];
+        ldk<K>(b + o, bv);
+        T ir = invd[i];
+#pragma unroll
+        for (int c = 0; c < K; c++) w[c] = cheb_first_point(bv[c], ir, cf);
+        stk<K>(d + o, w);
+        stk<K>(x + o, w);
+    }
+}
+
+// Chebyshev step: d' = c_d d + c_r D^-1 (b - A x), x' = x + d'
+template <typename T, int TPR, int K>
+__global__ void kb_cheb_step(MatView<T> A, const T *__restrict__ invd, const T *__restrict__ b,
+                             const T *__restrict__ x, T *__restrict__ d, T *__restrict__ xn, T cdv, T crv,
+                             const BScal *bs)
+{
+    pdl_enter();
+    if (bs && bs->all) return;
+    int row = my_row<TPR>();
+    T ax[K];
+    row_sum_k<T, TPR, K>(A, row, x, ax);
+    if (row < A.rows && row_leader<TPR>()) {
+        int64_t o = (int64_t)row * K;
+        T bv[K], dv[K], xv[K], dn[K], xo[K];
+        ldk<K>(b + o, bv);
+        ldk<K>(d + o, dv);
+        ldk<K>(x + o, xv);
+        T ir = invd[row];
+#pragma unroll
+        for (int c = 0; c < K; c++) cheb_point(bv[c], ax[c], ir, dv[c], xv[c], cdv, crv, dn[c], xo[c]);
+        stk<K>(d + o, dn);
+        stk<K>(xn + o, xo);
+    }
+}
+
+// r = b - A x
+template <typename T, int TPR, int K>
+__global__ void kb_residual(MatView<T> A, const T *__restrict__ b, const T *__restrict__ x, T *__restrict__ r,
+                            const BScal *bs)
+{
+    pdl_enter();
+    if (bs && bs->all) return;
+    int row = my_row<TPR>();
+    T ax[K];
+    row_sum_k<T, TPR, K>(A, row, x, ax);
+    if (row < A.rows && row_leader<TPR>()) {
+        int64_t o = (int64_t)row * K;
+        T bv[K], w[K];
+        ldk<K>(b + o, bv);
+#pragma unroll
+        for (int c = 0; c < K; c++) w[c] = rsub(bv[c], ax[c]);
+        stk<K>(r + o, w);
+    }
+}
+
+// y = A x (add = 0) or y += A x (add = 1): restriction and prolongation
+template <typename T, int TPR, int K>
+__global__ void kb_apply(MatView<T> A, const T *__restrict__ x, T *__restrict__ y, int add, const BScal *bs)
+{
+    pdl_enter();
+    if (bs && bs->all) return;
+    int row = my_row<TPR>();
+    T ax[K];
+    row_sum_k<T, TPR, K>(A, row, x, ax);
+    if (row < A.rows && row_leader<TPR>()) {
+        int64_t o = (int64_t)row * K;
+        if (add) {
+            T yv[K];
+            ldk<K>(y + o, yv);
+#pragma unroll
+            for (int c = 0; c < K; c++) ax[c] = radd(yv[c], ax[c]);
+        }
+        stk<K>(y + o, ax);
+    }
+}
+
+// x = inv b for a dense row-major inverse with leading dimension ld: one warp
+// per row
+template <typename T, int K>
+__global__ void kb_dense(int n, const T *__restrict__ inv, int ld, const T *__restrict__ b, T *__restrict__ x,
+                         const BScal *bs)
+{
+    pdl_enter();
+    if (bs && bs->all) return;
+    int row = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    int lane = threadIdx.x & 31;
+    if (row >= n) return; // whole warps
+    const T *a = inv + (int64_t)row * ld;
+    T acc[K];
+#pragma unroll
+    for (int c = 0; c < K; c++) acc[c] = (T)0;
+    for (int j = lane; j < n; j += 32) {
+        T aj = a[j], bv[K];
+        ldk_ro<K>(b + (int64_t)j * K, bv);
+#pragma unroll
+        for (int c = 0; c < K; c++) acc[c] = rfma(aj, bv[c], acc[c]);
+    }
+#pragma unroll
+    for (int c = 0; c < K; c++) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], o);
+    }
+    if (lane == 0) stk<K>(x + (int64_t)row * K, acc);
+}
+
+template <typename T>
+__global__ void kb_copy(int64_t nk, const T *__restrict__ a, T *__restrict__ b, const BScal *bs)
+{
+    pdl_enter();
+    if (bs && bs->all) return;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nk; i += (int64_t)gridDim.x * blockDim.x)
+        b[i] = a[i];
+}
+
+// ------------------------------------------------------------------ FP64 operators and vectors
+// y = alpha A x + beta y (beta = 0: y is not read)
+template <int TPR, int K>
+__global__ void kb_spmm(MatView<double> A, const double *__restrict__ x, double *__restrict__ y, double alpha,
+                        double beta)
+{
+    pdl_enter();
+    int row = my_row<TPR>();
+    double ax[K];
+    row_sum_k<double, TPR, K>(A, row, x, ax);
+    if (row < A.rows && row_leader<TPR>()) {
+        int64_t o = (int64_t)row * K;
+        double w[K];
+        if (beta != 0.0) {
+            double yv[K];
+            ldk<K>(y + o, yv);
+#pragma unroll
+            for (int c = 0; c < K; c++) w[c] = alpha * ax[c] + beta * yv[c];
+        } else {
+#pragma unroll
+            for (int c = 0; c < K; c++) w[c] = alpha * ax[c];
+        }
+        stk<K>(y + o, w);
+    }
+}
+
+struct Coef {
+    double a[KB], b[KB];
+};
+
+// out = a_c x + b_c y per column (y may be null)
+template <int K>
+__global__ void kb_axpby(int n, Coef cf, const double *__restrict__ x, const double *__restrict__ y, double *out)
+{
+    pdl_enter();
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        int64_t o = (int64_t)i * K;
+        double xv[K], w[K];
+        ldk<K>(x + o, xv);
+        if (y) {
+            double yv[K];
+            ldk<K>(y + o, yv);
+#pragma unroll
+            for (int c = 0; c < K; c++) w[c] = cf.a[c] * xv[c] + cf.b[c] * yv[c];
+        } else {
+#pragma unroll
+            for (int c = 0; c < K; c++) w[c] = cf.a[c] * xv[c];
+        }
+        stk<K>(out + o, w);
+    }
+}
+
+// out = ta + (w1 - tb) / beta (the two-grid combination of Eq.
+// twogridinmultiactual, all columns)
+__global__ void kb_rcomb(int64_t nk, const double *__restrict__ ta, const double *__restrict__ w1,
+                         const double *__restrict__ tb, double beta, double *__restrict__ out)
+{
+    pdl_enter();
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nk; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = ta[i] + (w1[i] - tb[i]) / beta;
+}
+
+// out[c] = (x_c, y_c)
+template <int K>
+__global__ void kb_dot(int n, const double *__restrict__ x, const double *__restrict__ y, double *out,
+                       double *partials, unsigned *ticket)
+{
+    pdl_enter();
+    double v[K], tot[K];
+#pragma unroll
+    for (int c = 0; c < K; c++) v[c] = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        int64_t o = (int64_t)i * K;
+        double xv[K], yv[K];
+        ldk<K>(x + o, xv);
+        ldk<K>(y + o, yv);
+#pragma unroll
+        for (int c = 0; c < K; c++) v[c] += xv[c] * yv[c];
+    }
+    if (reduce_last_block<K>(v, partials, ticket, tot)) {
+#pragma unroll
+        for (int c = 0; c < K; c++) out[c] = tot[c];
+    }
+}
+
+// column-major (leading dimension ld, nc columns) -> interleaved K columns,
+// padding columns zero
+template <int K>
+__global__ void kb_pack(int n, int nc, const double *__restrict__ src, int64_t ld, double *__restrict__ dst)
+{
+    pdl_enter();
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        double w[K];
+#pragma unroll
+        for (int c = 0; c < K; c++) w[c] = c < nc ? src[(int64_t)c * ld + i] : 0.0;
+        stk<K>(dst + (int64_t)i * K, w);
+    }
+}
+
+template <int K>
+__global__ void kb_unpack(int n, int nc, const double *__restrict__ src, double *__restrict__ dst, int64_t ld)
+{
+    pdl_enter();
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        double w[K];
+        ldk<K>(src + (int64_t)i * K, w);
+#pragma unroll
+        for (int c = 0; c < K; c++)
+            if (c < nc) dst[(int64_t)c * ld + i] = w[c];
+    }
+}
+
+// desired states at the state dofs: dst[s][c] = yd[c][vertex_of_state[s]]
+template <int K>
+__global__ void kb_gather_state(int m, int nc, const double *__restrict__ yd, int64_t nv,
+                                const int *__restrict__ vos, double *__restrict__ dst)
+{
+    pdl_enter();
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < m; s += gridDim.x * blockDim.x) {
+        int64_t v = vos[s];
+        double w[K];
+#pragma unroll
+        for (int c = 0; c < K; c++) w[c] = c < nc ? yd[(int64_t)c * nv + v] : 0.0;
+        stk<K>(dst + (int64_t)s * K, w);
+    }
+}
+
+// ------------------------------------------------------------------ work space
+struct BGraph {
+    cudaGraphExec_t start = nullptr, iter = nullptr;
+    int ns = 0, ni = 0;
+};
+
+struct BState {
+    double *x = nullptr, *r = nullptr, *pv = nullptr, *q = nullptr, *s = nullptr;
+    void *z = nullptr;     // V-cycle output (FP32 or FP64)
+    float *r32 = nullptr;  // FP32 copy of r (FP32 V-cycle input)
+    void *vb = nullptr, *vx = nullptr, *vx2 = nullptr, *vd = nullptr, *vr = nullptr;
+    BScal *bs = nullptr;
+    RedSlot red;
+    BGraph g;
+    int hint = 0;
+};
+
+struct BCtrl {
+    double *mx = nullptr, *mr = nullptr, *mz = nullptr, *mp = nullptr, *mq = nullptr, *ms = nullptr;
+    BScal *mbs = nullptr;
+    RedSlot red;
+    BGraph mg;
+    int mhint = 0;
+    double *bc = nullptr, *qc = nullptr, *wc = nullptr, *w1 = nullptr, *ta = nullptr, *tb = nullptr;
+    double *hu = nullptr, *rq = nullptr, *du = nullptr;
+    double *t1 = nullptr, *ys = nullptr, *t2 = nullptr, *ps = nullptr; // state-sized
+};
+
+struct BlockWork {
+    int K = 0, f32 = 1;
+    Arena ar;
+    BState sl[AMGH_MAXL];
+    BCtrl cl[AMGH_MAXL];
+    double *ob = nullptr, *ou = nullptr, *orr = nullptr, *oz = nullptr, *op = nullptr, *oq = nullptr;
+    double *oyd = nullptr, *dots = nullptr;
+    RedSlot ored;
+    BScal *h_bs = nullptr;
+    double *h_dots = nullptr;
+    int fail[KB]; // sticky per-column status of the current call
+};
+
+static void free_bgraph(BGraph &g)
+{
+    if (g.start) cudaGraphExecDestroy(g.start);
+    if (g.iter) cudaGraphExecDestroy(g.iter);
+    g = BGraph();
+}
+
+void block_free(amgh_problem *p)
+{
+    BlockWork *W = p->blk;
+    if (!W) return;
+    for (int l = 0; l < AMGH_MAXL; l++) {
+        free_bgraph(W->sl[l].g);
+        free_bgraph(W->cl[l].mg);
+    }
+    W->ar.free_all();
+    if (W->h_bs) cudaFreeHost(W->h_bs);
+    if (W->h_dots) cudaFreeHost(W->h_dots);
+    delete W;
+    p->blk = nullptr;
+}
+
+// partial sums of nv values for up to `blocks` blocks
+static int bred_alloc(Arena &ar, RedSlot &slot, int blocks, int nv)
+{
+    slot.capacity = blocks + 8;
+    TRY(ar.alloc(&slot.partials, (int64_t)slot.capacity * nv));
+    TRY(ar.alloc(&slot.ticket, 1));
+    CU(cudaMemsetAsync(slot.ticket, 0, sizeof(unsigned), g_alloc_stream));
+    return AMGH_OK;
+}
+
+static int red_blocks(const DevCsr &a)
+{
+    int g = rows_grid(a.rows, a.tpr < 1 ? 1 : a.tpr);
+    int v = vblocks(a.rows);
+    return g > v ? g : v;
+}
+
+static int block_alloc(amgh_problem *p, int K)
+{
+    int f32 = p->aopts.precision != 0;
+    if (p->blk && p->blk->K == K && p->blk->f32 == f32) return AMGH_OK;
+    block_free(p);
+    BlockWork *W = new (std::nothrow) BlockWork();
+    if (!W) return AMGH_ERR_OOM;
+    p->blk = W;
+    W->K = K;
+    W->f32 = f32;
+    Arena &ar = W->ar;
+    size_t vs = f32 ? sizeof(float) : sizeof(double);
+    for (int l = 0; l < p->Ls; l++) {
+        BState &B = W->sl[l];
+        int64_t n = (int64_t)p->sl[l].A.rows * K;
+        TRY(ar.alloc(&B.x, n));
+        TRY(ar.alloc(&B.r, n));
+        TRY(ar.alloc(&B.pv, n));
+        TRY(ar.alloc(&B.q, n));
+        TRY(ar.alloc(&B.s, n));
+        TRY(ar.alloc(&B.r32, f32 ? n : 1));
+        char *v = nullptr;
+        TRY(ar.alloc(&v, (int64_t)(6 * n * vs)));
+        void **dst[6] = {&B.z, &B.vb, &B.vx, &B.vx2, &B.vd, &B.vr};
+        for (int k = 0; k < 6; k++) *dst[k] = v + k * n * vs;
+        TRY(ar.alloc(&B.bs, 1));
+        CU(cudaMemsetAsync(B.bs, 0, sizeof(BScal), g_alloc_stream));
+        TRY(bred_alloc(ar, B.red, red_blocks(p->sl[l].A), 2 * K));
+    }
+    for (int l = 0; l < p->Lc; l++) {
+        BCtrl &D = W->cl[l];
+        int64_t n = (int64_t)p->cl[l].Mu.rows * K;
+        int64_t m = (int64_t)p->sl[l < p->Ls ? l : 0].A.rows * K;
+        double **vec[15] = {&D.mx, &D.mr, &D.mz, &D.mp, &D.mq, &D.ms, &D.bc, &D.qc,
+                            &D.wc, &D.w1, &D.ta, &D.tb, &D.hu, &D.rq, &D.du};
+        for (auto d : vec) TRY(ar.alloc(d, n));
+        if (l < p->Ls) {
+            TRY(ar.alloc(&D.t1, m));
+            TRY(ar.alloc(&D.ys, m));
+            TRY(ar.alloc(&D.t2, m));
+            TRY(ar.alloc(&D.ps, m));
+        }
+        TRY(ar.alloc(&D.mbs, 1));
+        CU(cudaMemsetAsync(D.mbs, 0, sizeof(BScal), g_alloc_stream));
+        TRY(bred_alloc(ar, D.red, red_blocks(p->cl[l].Mu), 2 * K));
+    }
+    int64_t n = (int64_t)p->n * K;
+    double **vec[6] = {&W->ob, &W->ou, &W->orr, &W->oz, &W->op, &W->oq};
+    for (auto d : vec) TRY(ar.alloc(d, n));
+    TRY(ar.alloc(&W->oyd, (int64_t)p->m * K));
+    TRY(ar.alloc(&W->dots, KB));
+    TRY(bred_alloc(ar, W->ored, vblocks(p->n > p->m ? p->n : p->m), K));
+    CU(cudaHostAlloc((void **)&W->h_bs, sizeof(BScal), cudaHostAllocDefault));
+    CU(cudaHostAlloc((void **)&W->h_dots, sizeof(double) * KB, cudaHostAllocDefault));
+    return AMGH_OK;
+}
+
+// ------------------------------------------------------------------ launch helpers
+template <int V>
+struct IntC {
+    static constexpr int value = V;
+};
+
+// f(IntC<tpr>) for the lane counts the operators use; false for any other
+template <typename F>
+static bool with_tpr(int tpr, F &&f)
+{
+    switch (tpr) {
+    case 1: f(IntC<1>()); return true;
+    case 2: f(IntC<2>()); return true;
+    case 4: f(IntC<4>()); return true;
+    case 8: f(IntC<8>()); return true;
+    case 16: f(IntC<16>()); return true;
+    case 32: f(IntC<32>()); return true;
+    }
+    return false;
+}
+
+template <typename T>
+static inline MatView<T> bview(const DevCsr &a)
+{
+    MatView<T> m = view<T>(a);
+    if (m.tpr < 1) m.tpr = 1;
+    return m;
+}
+
+static int read_bscal(amgh_problem *p, const BScal *dev, BScal *out)
+{
+    CU(cudaMemcpyAsync(p->blk->h_bs, dev, sizeof(BScal), cudaMemcpyDeviceToHost, p->stream));
+    TRY(sync_stream(p));
+    *out = *p->blk->h_bs;
+    return AMGH_OK;
+}
+
+static int col_status(const CgScal &s)
+{
+    if (!s.done) return AMGH_ERR_NOT_CONVERGED;
+    switch (s.status) {
+    case CG_CONVERGED: return AMGH_OK;
+    case CG_INDEFINITE: return AMGH_ERR_INDEFINITE;
+    case CG_NUMERIC: return AMGH_ERR_NUMERIC;
+    }
+    return AMGH_ERR_NOT_CONVERGED;
+}
+
+// keep the first failure of each column
+static void note_fail(BlockWork &W, int c, int st)
+{
+    if (st != AMGH_OK && W.fail[c] == AMGH_OK) W.fail[c] = st;
+}
+
+// ------------------------------------------------------------------ the block solver
+template <typename T, int K>
+struct Blk {
+    static int spmm(amgh_problem *p, const DevCsr &a, const double *x, double *y, double alpha, double beta)
+    {
+        MatView<double> A = bview<double>(a);
+        if (!with_tpr(A.tpr, [&](auto t) {
+                constexpr int TPR = decltype(t)::value;
+                pdl_launch(kb_spmm<TPR, K>, dim3(rows_grid(A.rows, TPR)), dim3(TPB), 0, p->stream, A, x, y, alpha,
+                           beta);
+            }))
+            return AMGH_ERR_INVALID_ARG;
+        LAUNCH_CHECK();
+        return AMGH_OK;
+    }
+
+    static int axpby(amgh_problem *p, int n, const Coef &cf, const double *x, const double *y, double *out)
+    {
+        pdl_launch(kb_axpby<K>, dim3(vblocks(n)), dim3(TPB), 0, p->stream, n, cf, x, y, out);
+        LAUNCH_CHECK();
+        return AMGH_OK;
+    }
+
+    static int copy(amgh_problem *p, int64_t nk, const double *a, double *b)
+    {
+        pdl_launch(kb_copy<double>, dim3(vblocks(nk)), dim3(TPB), 0, p->stream, nk, a, b, (const BScal *)nullptr);
+        LAUNCH_CHECK();
+        return AMGH_OK;
+    }
+
+    // (x_c, y_c) for every column, on the host
+    static int dots(amgh_problem *p, int n, const double *x, const double *y, double *out)
+    {
+        BlockWork &W = *p->blk;
+        pdl_launch(kb_dot<K>, dim3(vblocks(n)), dim3(TPB), 0, p->stream, n, x, y, W.dots, W.ored.partials,
+                   W.ored.ticket);
+        LAUNCH_CHECK();
+        CU(cudaMemcpyAsync(W.h_dots, W.dots, sizeof(double) * K, cudaMemcpyDeviceToHost, p->stream));
+        TRY(sync_stream(p));
+        for (int c = 0; c < K; c++) out[c] = W.h_dots[c];
+        return AMGH_OK;
+    }
+
+    // ---- V-cycle on level l (x = V_l b from zero), K columns
+    static int vcyc(amgh_problem *p, int l, const T *b, T *x, const BScal *bs)
+    {
+        BlockWork &W = *p->blk;
+        StateLevel &S = p->sl[l];
+        BState &B = W.sl[l];
+        int n = S.A.rows;
+        if (l == p->Ls - 1) {
+            const T *inv;
+            int ld;
+            if (sizeof(T) == sizeof(float)) {
+                inv = (const T *)p->Acoarse.inv32;
+                ld = p->Acoarse.ld32;
+            } else {
+                inv = (const T *)p->Acoarse.inv;
+                ld = n;
+            }
+            pdl_launch(kb_dense<T, K>, dim3(ceil_div((int64_t)n * 32, TPB)), dim3(TPB), 0, p->stream, n, inv, ld,
+                       b, x, bs);
+            LAUNCH_CHECK();
+            return AMGH_OK;
+        }
+        const T *invd = sizeof(T) == sizeof(float) ? (const T *)S.invd32 : (const T *)S.invd;
+        T *tmp = (x == (T *)B.vx) ? (T *)B.vx2 : (T *)B.vx;
+        T *d = (T *)B.vd, *r = (T *)B.vr;
+        T *cur = tmp, *nxt = x;
+        MatView<T> A = bview<T>(S.A);
+        pdl_launch(kb_cheb_first<T, K>, dim3(vblocks(n)), dim3(TPB), 0, p->stream, n, invd, b, d, cur,
+                   (T)p->cr[0], bs);
+        LAUNCH_CHECK();
+        auto step = [&](double cdv, double crv) -> int {
+            if (!with_tpr(A.tpr, [&](auto t) {
+                    constexpr int TPR = decltype(t)::value;
+                    pdl_launch(kb_cheb_step<T, TPR, K>, dim3(rows_grid(n, TPR)), dim3(TPB), 0, p->stream, A, invd,
+                               b, (const T *)cur, d, nxt, (T)cdv, (T)crv, bs);
+                }))
+                return AMGH_ERR_INVALID_ARG;
+            LAUNCH_CHECK();
+            T *t = cur;
+            cur = nxt;
+            nxt = t;
+            return AMGH_OK;
+        };
+        for (int s = 1; s < p->nsteps; s++) TRY(step(p->cd[s], p->cr[s]));
+        // coarse-grid correction
+        if (!with_tpr(A.tpr, [&](auto t) {
+                constexpr int TPR = decltype(t)::value;
+                pdl_launch(kb_residual<T, TPR, K>, dim3(rows_grid(n, TPR)), dim3(TPB), 0, p->stream, A, b,
+                           (const T *)cur, r, bs);
+            }))
+            return AMGH_ERR_INVALID_ARG;
+        LAUNCH_CHECK();
+        BState &Bc = W.sl[l + 1];
+        T *bc = (T *)Bc.vb, *xc = (T *)Bc.vx;
+        TRY(apply(p, S.St, r, bc, 0, bs));
+        TRY(vcyc(p, l + 1, bc, xc, bs));
+        TRY(apply(p, S.S, xc, cur, 1, bs));
+        for (int s = 0; s < p->nsteps; s++) TRY(step(s == 0 ? 0.0 : p->cd[s], p->cr[s]));
+        if (cur != x) {
+            pdl_launch(kb_copy<T>, dim3(vblocks((int64_t)n * K)), dim3(TPB), 0, p->stream, (int64_t)n * K,
+                       (const T *)cur, x, bs);
+            LAUNCH_CHECK();
+        }
+        return AMGH_OK;
+    }
+
+    static int apply(amgh_problem *p, const DevCsr &a, const T *x, T *y, int add, const BScal *bs)
+    {
+        MatView<T> A = bview<T>(a);
+        if (!with_tpr(A.tpr, [&](auto t) {
+                constexpr int TPR = decltype(t)::value;
+                pdl_launch(kb_apply<T, TPR, K>, dim3(rows_grid(A.rows, TPR)), dim3(TPB), 0, p->stream, A, x, y, add,
+                           bs);
+            }))
+            return AMGH_ERR_INVALID_ARG;
+        LAUNCH_CHECK();
+        return AMGH_OK;
+    }
+
+    // s = A z with (r, z), (z, s) -> alpha, beta: products in FP64 for
+    // precision 0, else in double-float from the FP32 parts of A
+    template <typename Z>
+    static int cg_spmv(amgh_problem *p, const DevCsr &a, const Z *z, const double *r, double *s, BScal *bs,
+                       RedSlot &red)
+    {
+        if constexpr (sizeof(Z) == sizeof(double)) {
+            if (!p->blk->f32) {
+                MatView<double> A = bview<double>(a);
+                if (!with_tpr(A.tpr, [&](auto t) {
+                        constexpr int TPR = decltype(t)::value;
+                        pdl_launch(kb_cg_spmv64<TPR, K>, dim3(rows_grid(A.rows, TPR)), dim3(TPB), 0, p->stream, A,
+                                   z, r, s, bs, red.partials, red.ticket);
+                    }))
+                    return AMGH_ERR_INVALID_ARG;
+                LAUNCH_CHECK();
+                return AMGH_OK;
+            }
+        }
+        MatView<float> A = bview<float>(a);
+        if (!a.lo32) return AMGH_ERR_INVALID_ARG;
+        if (!with_tpr(A.tpr, [&](auto t) {
+                constexpr int TPR = decltype(t)::value;
+                pdl_launch(kb_cg_spmv<Z, TPR, K>, dim3(rows_grid(A.rows, TPR)), dim3(TPB), 0, p->stream, A,
+                           (const float *)a.lo32, z, r, s, bs, red.partials, red.ticket);
+            }))
+            return AMGH_ERR_INVALID_ARG;
+        LAUNCH_CHECK();
+        return AMGH_OK;
+    }
+
+    // replay one inner CG loop (start body once, iteration body in chunks)
+    // until every column has stopped or the cap is passed
+    static int run_loop(amgh_problem *p, BGraph &g, const std::function<int()> &start,
+                        const std::function<int()> &iter, BScal *bs, int maxit, int *hint, BScal *out)
+    {
+        bool gr = graphs_enabled(p);
+        if (gr && !g.iter) {
+            if (start) TRY(graph_capture(p, start, &g.start, &g.ns));
+            TRY(graph_capture(p, iter, &g.iter, &g.ni));
+        }
+        if (start) {
+            if (gr) TRY(graph_replay(p, g.start, g.ns));
+            else TRY(start());
+        }
+        int chunk = *hint > 1 ? (*hint * 7) / 8 : 1;
+        int enq = 0;
+        BScal h;
+        for (;;) {
+            for (int c = 0; c < chunk; c++) {
+                if (gr) TRY(graph_replay(p, g.iter, g.ni));
+                else TRY(iter());
+            }
+            enq += chunk;
+            TRY(read_bscal(p, bs, &h));
+            if (h.all || enq > maxit + 2) break;
+            int most = 0;
+            for (int c = 0; c < K; c++) most = h.c[c].iters > most ? h.c[c].iters : most;
+            chunk = most / 8 > 1 ? most / 8 : 1;
+        }
+        int most = 0;
+        for (int c = 0; c < K; c++) most = h.c[c].iters > most ? h.c[c].iters : most;
+        if (most > 0) *hint = most;
+        *out = h;
+        return AMGH_OK;
+    }
+
+    // ---- A_l y = f to relative residual tol per column
+    static int state_solve(amgh_problem *p, int l, const double *f, double *y, double tol)
+    {
+        BlockWork &W = *p->blk;
+        StateLevel &S = p->sl[l];
+        BState &B = W.sl[l];
+        int n = S.A.rows;
+        int maxit = p->sopts.inner_max_iter;
+        const bool f32 = sizeof(T) == sizeof(float);
+        pdl_launch(kb_cg_start<K>, dim3(vblocks(n)), dim3(TPB), 0, p->stream, n, f, B.x, B.r, (double *)nullptr,
+                   (const double *)nullptr, B.bs, tol * tol, maxit, B.red.partials, B.red.ticket);
+        LAUNCH_CHECK();
+        const T *vin = f32 ? (const T *)B.r32 : (const T *)B.r;
+        T *z = (T *)B.z;
+        std::function<int()> start = [&]() {
+            if (f32) {
+                pdl_launch(kb_r32<K>, dim3(vblocks(n)), dim3(TPB), 0, p->stream, n, (const double *)B.r, B.r32,
+                           (const BScal *)B.bs);
+                LAUNCH_CHECK();
+            }
+            return vcyc(p, l, vin, z, B.bs);
+        };
+        std::function<int()> iter = [&]() {
+            TRY(cg_spmv<T>(p, S.A, z, B.r, B.s, B.bs, B.red));
+            pdl_launch(kb_cg_update<T, K>, dim3(vblocks(n)), dim3(TPB), 0, p->stream, n, z, (const double *)B.s,
+                       B.pv, B.q, B.x, B.r, f32 ? B.r32 : (float *)nullptr, (const double *)nullptr, B.bs,
+                       B.red.partials, B.red.ticket);
+            LAUNCH_CHECK();
+            return vcyc(p, l, vin, z, B.bs);
+        };
+        BScal h;
+        TRY(run_loop(p, B.g, start, iter, B.bs, maxit, &B.hint, &h));
+        for (int c = 0; c < K; c++) {
+            p->c_inner += h.c[c].iters;
+            p->c_inner_lvl[l] += h.c[c].iters;
+            note_fail(W, c, col_status(h.c[c]));
+        }
+        return copy(p, (int64_t)n * K, B.x, y);
+    }
+
+    // ---- M_{u,l} x = b (Jacobi-preconditioned CG) per column
+    static int mass_solve(amgh_problem *p, int l, const double *b, double *x)
+    {
+        BlockWork &W = *p->blk;
+        CtrlLevel &C = p->cl[l];
+        BCtrl &D = W.cl[l];
+        int n = C.Mu.rows;
+        int maxit = p->sopts.mass_max_iter;
+        double tol = p->sopts.mass_tol;
+        pdl_launch(kb_cg_start<K>, dim3(vblocks(n)), dim3(TPB), 0, p->stream, n, b, D.mx, D.mr, D.mz,
+                   (const double *)C.mu_invdiag, D.mbs, tol * tol, maxit, D.red.partials, D.red.ticket);
+        LAUNCH_CHECK();
+        std::function<int()> iter = [&]() {
+            TRY(cg_spmv<double>(p, C.Mu, D.mz, D.mr, D.ms, D.mbs, D.red));
+            pdl_launch(kb_cg_update<double, K>, dim3(vblocks(n)), dim3(TPB), 0, p->stream, n, D.mz,
+                       (const double *)D.ms, D.mp, D.mq, D.mx, D.mr, (float *)nullptr,
+                       (const double *)C.mu_invdiag, D.mbs, D.red.partials, D.red.ticket);
+            LAUNCH_CHECK();
+            return AMGH_OK;
+        };
+        BScal h;
+        TRY(run_loop(p, D.mg, std::function<int()>(), iter, D.mbs, maxit, &D.mhint, &h));
+        for (int c = 0; c < K; c++) {
+            p->c_mass += h.c[c].iters;
+            p->c_mass_lvl[l] += h.c[c].iters;
+            note_fail(W, c, col_status(h.c[c]));
+        }
+        return copy(p, (int64_t)n * K, D.mx, x);
+    }
+
+    // ---- H_l v (Eq. firstorderpractice on level l), K columns
+    static int hessian(amgh_problem *p, int l, const double *v, double *hv)
+    {
+        BlockWork &W = *p->blk;
+        StateLevel &S = p->sl[l];
+        CtrlLevel &C = p->cl[l];
+        BCtrl &D = W.cl[l];
+        double tol = l == 0 ? p->sopts.inner_tol : p->sopts.precond_tol;
+        TRY(spmm(p, C.Myu, v, D.t1, 1.0, 0.0));
+        TRY(state_solve(p, l, D.t1, D.ys, tol));
+        TRY(spmm(p, S.My, D.ys, D.t2, 1.0, 0.0));
+        TRY(state_solve(p, l, D.t2, D.ps, tol));
+        TRY(spmm(p, C.Myut, D.ps, hv, 1.0, 0.0));
+        TRY(spmm(p, C.Mu, v, hv, p->beta, 1.0));
+        return AMGH_OK;
+    }
+
+    // ---- R_j b (Eq. twogridinmultiactual in M-form)
+    static int mlas_R(amgh_problem *p, int j, const double *b, double *out)
+    {
+        BlockWork &W = *p->blk;
+        CtrlLevel &C = p->cl[j];
+        BCtrl &D = W.cl[j], &Dc = W.cl[j + 1];
+        int n = C.Mu.rows;
+        TRY(spmm(p, C.Pt, b, Dc.bc, 1.0, 0.0));
+        TRY(mlas_Q(p, j + 1, Dc.bc, Dc.qc));
+        TRY(mass_solve(p, j, b, D.w1));
+        TRY(mass_solve(p, j + 1, Dc.bc, Dc.wc));
+        TRY(spmm(p, C.P, Dc.qc, D.ta, 1.0, 0.0));
+        TRY(spmm(p, C.P, Dc.wc, D.tb, 1.0, 0.0));
+        int64_t nk = (int64_t)n * K;
+        pdl_launch(kb_rcomb, dim3(vblocks(nk)), dim3(TPB), 0, p->stream, nk, (const double *)D.ta,
+                   (const double *)D.w1, (const double *)D.tb, p->beta, out);
+        LAUNCH_CHECK();
+        return AMGH_OK;
+    }
+
+    // ---- Q_{ell-1} b by CG on H_{ell-1} from zero, per column, stopping at
+    // ||r_k|| <= coarse_tol ||b||; the iterate at the cap is used as it stands
+    static int coarse_cg(amgh_problem *p, int j, const double *b, double *u)
+    {
+        BlockWork &W = *p->blk;
+        BCtrl &D = W.cl[j];
+        int n = p->cl[j].Mu.rows;
+        double *r = D.rq, *pv = D.du, *q = D.hu;
+        CU(cudaMemsetAsync(u, 0, sizeof(double) * n * K, p->stream));
+        TRY(copy(p, (int64_t)n * K, b, r));
+        TRY(copy(p, (int64_t)n * K, b, pv));
+        double ff[K], rz[K], nf[K];
+        bool run[K];
+        TRY(dots(p, n, b, b, ff));
+        bool any = false;
+        for (int c = 0; c < K; c++) {
+            if (!(ff[c] == ff[c])) note_fail(W, c, AMGH_ERR_NUMERIC);
+            run[c] = ff[c] > 0.0 && W.fail[c] == AMGH_OK;
+            nf[c] = sqrt(ff[c]);
+            rz[c] = ff[c];
+            any = any || run[c];
+        }
+        Coef cf;
+        if (any) {
+            // columns that do not run get p = 0 (their inner solves then stop at once)
+            for (int c = 0; c < K; c++) {
+                cf.a[c] = run[c] ? 1.0 : 0.0;
+                cf.b[c] = 0.0;
+            }
+            TRY(axpby(p, n, cf, b, nullptr, pv));
+        }
+        double tol = p->sopts.coarse_tol;
+        for (int k = 1; any && k <= p->sopts.coarse_max_iter; k++) {
+            TRY(hessian(p, j, pv, q));
+            for (int c = 0; c < K; c++) {
+                if (run[c]) p->c_coarse += 1;
+                if (W.fail[c] != AMGH_OK) run[c] = false;
+            }
+            double pq[K], alpha[K];
+            TRY(dots(p, n, pv, q, pq));
+            for (int c = 0; c < K; c++) {
+                alpha[c] = 0.0;
+                if (!run[c]) continue;
+                if (!(pq[c] > 0.0)) {
+                    note_fail(W, c, pq[c] == pq[c] ? AMGH_ERR_INDEFINITE : AMGH_ERR_NUMERIC);
+                    run[c] = false;
+                    continue;
+                }
+                alpha[c] = rz[c] / pq[c];
+            }
+            for (int c = 0; c < K; c++) {
+                cf.a[c] = 1.0;
+                cf.b[c] = alpha[c];
+            }
+            TRY(axpby(p, n, cf, u, pv, u));
+            for (int c = 0; c < K; c++) cf.b[c] = -alpha[c];
+            TRY(axpby(p, n, cf, r, q, r));
+            double rr[K], beta[K];
+            TRY(dots(p, n, r, r, rr));
+            any = false;
+            for (int c = 0; c < K; c++) {
+                beta[c] = 0.0;
+                if (!run[c]) continue;
+                if (!(rr[c] == rr[c])) {
+                    note_fail(W, c, AMGH_ERR_NUMERIC);
+                    run[c] = false;
+                } else if (sqrt(rr[c]) <= tol * nf[c]) {
+                    run[c] = false;
+                } else if (!(rr[c] > 0.0)) {
+                    note_fail(W, c, AMGH_ERR_INDEFINITE);
+                    run[c] = false;
+                } else {
+                    beta[c] = rr[c] / rz[c];
+                    rz[c] = rr[c];
+                }
+                any = any || run[c];
+            }
+            for (int c = 0; c < K; c++) {
+                cf.a[c] = run[c] ? 1.0 : 0.0;
+                cf.b[c] = run[c] ? beta[c] : 0.0;
+            }
+            TRY(axpby(p, n, cf, r, pv, pv));
+        }
+        return AMGH_OK;
+    }
+
+    // ---- Q_j b (Algorithm MLAS)
+    static int mlas_Q(amgh_problem *p, int j, const double *b, double *u)
+    {
+        BlockWork &W = *p->blk;
+        CtrlLevel &C = p->cl[j];
+        BCtrl &D = W.cl[j];
+        int n = C.Mu.rows;
+        if (j == p->ell - 1) {
+            if (p->coarse_cg) return coarse_cg(p, j, b, u);
+            pdl_launch(kb_dense<double, K>, dim3(ceil_div((int64_t)n * 32, TPB)), dim3(TPB), 0, p->stream, n,
+                       (const double *)p->Hcoarse.inv, n, b, u, (const BScal *)nullptr);
+            LAUNCH_CHECK();
+            return AMGH_OK;
+        }
+        TRY(mlas_R(p, j, b, u));
+        if (j == 0) return AMGH_OK;
+        TRY(hessian(p, j, u, D.hu));
+        Coef cf;
+        for (int c = 0; c < K; c++) {
+            cf.a[c] = 1.0;
+            cf.b[c] = -1.0;
+        }
+        TRY(axpby(p, n, cf, b, D.hu, D.rq));
+        TRY(mlas_R(p, j, D.rq, D.du));
+        for (int c = 0; c < K; c++) cf.b[c] = 1.0;
+        TRY(axpby(p, n, cf, u, D.du, u));
+        return AMGH_OK;
+    }
+
+    // ---- outer CG on H u = b per column (Sec. 5.3); columns [nact, K) are
+    // padding.  u (block) receives the controls.
+    static int outer(amgh_problem *p, int nact, const amgh_solve_opts &o, double *u, double *relres, int *iters)
+    {
+        BlockWork &W = *p->blk;
+        int n = p->n;
+        double *b = W.ob, *r = W.orr, *z = W.oz, *pv = W.op, *q = W.oq;
+        // b = M_yu^T A^-1 M_y y_d per column
+        {
+            BCtrl &D0 = W.cl[0];
+            TRY(spmm(p, p->sl[0].My, W.oyd, D0.t2, 1.0, 0.0));
+            TRY(state_solve(p, 0, D0.t2, D0.ps, p->sopts.inner_tol));
+            TRY(spmm(p, p->cl[0].Myut, D0.ps, b, 1.0, 0.0));
+        }
+        double bb[K];
+        TRY(dots(p, n, b, b, bb));
+        bool run[K];
+        bool any = false;
+        Coef cf;
+        for (int c = 0; c < K; c++) {
+            iters[c] = 0;
+            relres[c] = 0.0;
+            if (c < nact && !(bb[c] == bb[c])) note_fail(W, c, AMGH_ERR_NUMERIC);
+            run[c] = c < nact && bb[c] > 0.0 && W.fail[c] == AMGH_OK;
+            any = any || run[c];
+            cf.a[c] = run[c] ? 1.0 : 0.0;
+            cf.b[c] = 0.0;
+        }
+        CU(cudaMemsetAsync(u, 0, sizeof(double) * n * K, p->stream));
+        // r = b on running columns, 0 elsewhere (stopped columns cost nothing below)
+        TRY(axpby(p, n, cf, b, nullptr, r));
+        double rz[K];
+        auto precond = [&]() -> int {
+            if (o.precond) return mlas_Q(p, 0, r, z);
+            return copy(p, (int64_t)n * K, r, z);
+        };
+        auto drop_failed = [&]() {
+            for (int c = 0; c < K; c++)
+                if (W.fail[c] != AMGH_OK) run[c] = false;
+        };
+        if (any) {
+            TRY(precond());
+            drop_failed();
+            TRY(dots(p, n, r, z, rz));
+            for (int c = 0; c < K; c++) {
+                if (run[c] && !(rz[c] > 0.0)) {
+                    note_fail(W, c, rz[c] == rz[c] ? AMGH_ERR_INDEFINITE : AMGH_ERR_NUMERIC);
+                    run[c] = false;
+                }
+                cf.a[c] = run[c] ? 1.0 : 0.0;
+            }
+            TRY(axpby(p, n, cf, z, nullptr, pv));
+        }
+        for (;;) {
+            any = false;
+            for (int c = 0; c < K; c++) any = any || run[c];
+            if (!any) break;
+            TRY(hessian(p, 0, pv, q));
+            for (int c = 0; c < K; c++)
+                if (run[c]) p->c_happ += 1;
+            drop_failed();
+            double pq[K], alpha[K];
+            TRY(dots(p, n, pv, q, pq));
+            for (int c = 0; c < K; c++) {
+                alpha[c] = 0.0;
+                if (!run[c]) continue;
+                if (!(pq[c] > 0.0)) {
+                    note_fail(W, c, pq[c] == pq[c] ? AMGH_ERR_INDEFINITE : AMGH_ERR_NUMERIC);
+                    run[c] = false;
+                    continue;
+                }
+                alpha[c] = rz[c] / pq[c];
+            }
+            for (int c = 0; c < K; c++) {
+                cf.a[c] = 1.0;
+                cf.b[c] = alpha[c];
+            }
+            TRY(axpby(p, n, cf, u, pv, u));
+            for (int c = 0; c < K; c++) cf.b[c] = -alpha[c];
+            TRY(axpby(p, n, cf, r, q, r));
+            double rr[K];
+            TRY(dots(p, n, r, r, rr));
+            bool stop[K];
+            for (int c = 0; c < K; c++) {
+                stop[c] = false;
+                if (!run[c]) continue;
+                iters[c] += 1;
+                if (!(rr[c] == rr[c])) {
+                    note_fail(W, c, AMGH_ERR_NUMERIC);
+                    stop[c] = true;
+                } else if (rr[c] <= o.tol * o.tol * bb[c]) {
+                    stop[c] = true;
+                } else if (iters[c] >= o.max_iter) {
+                    note_fail(W, c, AMGH_ERR_NOT_CONVERGED);
+                    stop[c] = true;
+                }
+            }
+            any = false;
+            for (int c = 0; c < K; c++) {
+                if (stop[c]) run[c] = false;
+                any = any || run[c];
+            }
+            if (!any) break;
+            // stopped columns: r = 0, so the preconditioner does no work for them
+            for (int c = 0; c < K; c++) {
+                cf.a[c] = run[c] ? 1.0 : 0.0;
+                cf.b[c] = 0.0;
+            }
+            TRY(axpby(p, n, cf, r, nullptr, r));
+            TRY(precond());
+            drop_failed();
+            double rzn[K], beta[K];
+            TRY(dots(p, n, r, z, rzn));
+            for (int c = 0; c < K; c++) {
+                beta[c] = 0.0;
+                if (!run[c]) continue;
+                if (!(rzn[c] > 0.0)) {
+                    note_fail(W, c, rzn[c] == rzn[c] ? AMGH_ERR_INDEFINITE : AMGH_ERR_NUMERIC);
+                    run[c] = false;
+                    continue;
+                }
+                beta[c] = rzn[c] / rz[c];
+                rz[c] = rzn[c];
+            }
+            for (int c = 0; c < K; c++) {
+                cf.a[c] = run[c] ? 1.0 : 0.0;
+                cf.b[c] = run[c] ? beta[c] : 0.0;
+            }
+            TRY(axpby(p, n, cf, z, pv, pv));
+        }
+        // true relative residual ||b - H u|| / ||b|| of every converged column
+        bool want = false;
+        for (int c = 0; c < K; c++) {
+            cf.a[c] = (c < nact && W.fail[c] == AMGH_OK) ? 1.0 : 0.0;
+            cf.b[c] = 0.0;
+            want = want || cf.a[c] != 0.0;
+        }
+        if (want) {
+            TRY(axpby(p, n, cf, u, nullptr, pv));
+            TRY(hessian(p, 0, pv, q));
+            for (int c = 0; c < K; c++)
+                if (cf.a[c] != 0.0) p->c_happ += 1;
+            for (int c = 0; c < K; c++) cf.b[c] = -cf.a[c];
+            TRY(axpby(p, n, cf, b, q, r));
+            double rr[K];
+            TRY(dots(p, n, r, r, rr));
+            for (int c = 0; c < K; c++)
+                if (cf.a[c] != 0.0) relres[c] = bb[c] > 0.0 ? sqrt(rr[c] / bb[c]) : 0.0;
+        }
+        return AMGH_OK;
+    }
+};
+
+// ------------------------------------------------------------------ entry points
+static int block_width(int ncols) { return ncols <= 2 ? 2 : ncols <= 4 ? 4 : 8; }
+
+template <int K>
+static int pack(amgh_problem *p, int n, int nc, const double *src, int64_t ld, double *dst)
+{
+    pdl_launch(kb_pack<K>, dim3(vblocks(n)), dim3(TPB), 0, p->stream, n, nc, src, ld, dst);
+    LAUNCH_CHECK();
+    return AMGH_OK;
+}
+
+template <int K>
+static int unpack(amgh_problem *p, int n, int nc, const double *src, double *dst, int64_t ld)
+{
+    pdl_launch(kb_unpack<K>, dim3(vblocks(n)), dim3(TPB), 0, p->stream, n, nc, src, dst, ld);
+    LAUNCH_CHECK();
+    return AMGH_OK;
+}
+
+// first failure over the columns, in column order
+static int first_fail(const BlockWork &W, int nc)
+{
+    for (int c = 0; c < nc; c++)
+        if (W.fail[c] != AMGH_OK) return W.fail[c];
+    return AMGH_OK;
+}
+
+enum { OP_HESSIAN = 0, OP_PRECOND = 1 };
+
+template <typename T, int K>
+static int apply_blocks(amgh_problem *p, int op, const double *in, double *out, int ncols)
+{
+    BlockWork &W = *p->blk;
+    int n = p->n;
+    for (int c0 = 0; c0 < ncols; c0 += K) {
+        int nc = ncols - c0 < K ? ncols - c0 : K;
+        for (int c = 0; c < KB; c++) W.fail[c] = AMGH_OK;
+        TRY(pack<K>(p, n, nc, in + (int64_t)c0 * n, n, W.orr));
+        if (op == OP_HESSIAN) {
+            TRY((Blk<T, K>::hessian(p, 0, W.orr, W.oq)));
+            p->c_happ += nc;
+        } else {
+            TRY((Blk<T, K>::mlas_Q(p, 0, W.orr, W.oq)));
+        }
+        TRY(unpack<K>(p, n, nc, W.oq, out + (int64_t)c0 * n, n));
+        TRY(first_fail(W, nc));
+    }
+    return AMGH_OK;
+}
+
+template <typename T, int K>
+static int solve_blocks(amgh_problem *p, const double *yd, int ncols, double *u, const amgh_solve_opts &o,
+                        amgh_solve_info *info, int *first_status)
+{
+    BlockWork &W = *p->blk;
+    int n = p->n, m = p->m;
+    for (int c0 = 0; c0 < ncols; c0 += K) {
+        int nc = ncols - c0 < K ? ncols - c0 : K;
+        for (int c = 0; c < KB; c++) W.fail[c] = AMGH_OK;
+        pdl_launch(kb_gather_state<K>, dim3(vblocks(m)), dim3(TPB), 0, p->stream, m, nc,
+                   yd + (int64_t)c0 * p->nv, (int64_t)p->nv, (const int *)p->vertex_of_state, W.oyd);
+        LAUNCH_CHECK();
+        double relres[K];
+        int it[K];
+        TRY((Blk<T, K>::outer(p, nc, o, W.ou, relres, it)));
+        TRY(unpack<K>(p, n, nc, W.ou, u + (int64_t)c0 * n, n));
+        for (int c = 0; c < nc; c++) {
+            info->outer_iters += it[c];
+            if (W.fail[c] == AMGH_OK && relres[c] > info->final_relres) info->final_relres = relres[c];
+        }
+        int st = first_fail(W, nc);
+        if (st != AMGH_OK && *first_status == AMGH_OK) *first_status = st;
+    }
+    return AMGH_OK;
+}
+
+template <typename T>
+static int dispatch_apply(amgh_problem *p, int K, int op, const double *in, double *out, int ncols)
+{
+    switch (K) {
+    case 2: return apply_blocks<T, 2>(p, op, in, out, ncols);
+    case 4: return apply_blocks<T, 4>(p, op, in, out, ncols);
+    default: return apply_blocks<T, 8>(p, op, in, out, ncols);
+    }
+}
+
+template <typename T>
+static int dispatch_solve(amgh_problem *p, int K, const double *yd, int ncols, double *u, const amgh_solve_opts &o,
+                          amgh_solve_info *info, int *first_status)
+{
+    switch (K) {
+    case 2: return solve_blocks<T, 2>(p, yd, ncols, u, o, info, first_status);
+    case 4: return solve_blocks<T, 4>(p, yd, ncols, u, o, info, first_status);
+    default: return solve_blocks<T, 8>(p, yd, ncols, u, o, info, first_status);
+    }
+}
+
+int block_apply(amgh_problem *p, int op, const double *in, double *out, int ncols)
+{
+    int K = block_width(ncols);
+    TRY(block_alloc(p, K));
+    if (p->blk->f32) return dispatch_apply<float>(p, K, op, in, out, ncols);
+    return dispatch_apply<double>(p, K, op, in, out, ncols);
+}
+
+int block_hessian_apply(amgh_problem *p, const double *u, double *hu, int ncols)
+{
+    return block_apply(p, OP_HESSIAN, u, hu, ncols);
+}
+
+int block_precond_apply(amgh_problem *p, const double *r, double *z, int ncols)
+{
+    return block_apply(p, OP_PRECOND, r, z, ncols);
+}
+
+int block_solve(amgh_problem *p, const double *yd, int ncols, double *u, const amgh_solve_opts &o,
+                amgh_solve_info *info)
+{
+    int K = block_width(ncols);
+    TRY(block_alloc(p, K));
+    int first = AMGH_OK;
+    int st;
+    if (p->blk->f32) st = dispatch_solve<float>(p, K, yd, ncols, u, o, info, &first);
+    else st = dispatch_solve<double>(p, K, yd, ncols, u, o, info, &first);
+    if (st != AMGH_OK) return st;
+    return first;
+}

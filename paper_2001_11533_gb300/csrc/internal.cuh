@@ -2,6 +2,7 @@
 // translation units of the amgh library (sm_103a).
 #pragma once
 
+#include <functional>
 #include <utility>
 
 #include <cuda_runtime.h>
@@ -14,6 +15,7 @@
 #define AMGH_MAXL 32
 #define AMGH_DENSE_MAX 4096
 #define AMGH_SELL_C 32
+#define AMGH_BLOCK_MAX 8 // widest column block of the block solver
 
 // ------------------------------------------------------------------ errors
 // record the CUDA error (code, file, line) for amgh_last_error
@@ -254,6 +256,8 @@ struct KernelTimer {
     std::vector<cudaEvent_t> pool;
 };
 
+struct BlockWork; // work space of the block solver (block.cu)
+
 struct amgh_problem {
     // set on a handle made by amgh_problem_share: matrices, hierarchies and
     // dense coarse inverses belong to the parent; this handle owns only its
@@ -308,6 +312,7 @@ struct amgh_problem {
     int chunk_hint[AMGH_MAXL];
     int chunk_hint32[AMGH_MAXL];
     int mchunk_hint[AMGH_MAXL];
+    BlockWork *blk = nullptr; // allocated by the first block call
 };
 
 // ------------------------------------------------------------------ sparse.cu
@@ -437,6 +442,21 @@ int mlas_R(amgh_problem *p, int j, const double *b, double *out);
 int rhs_apply(amgh_problem *p, double *b);
 int outer_solve(amgh_problem *p, const double *u0, double *u, const amgh_solve_opts *o, amgh_solve_info *info);
 int sync_stream(amgh_problem *p);
+// capture body() on the problem's private stream as a graph; replay it
+int graph_capture(amgh_problem *p, const std::function<int()> &body, cudaGraphExec_t *exec, int *nodes);
+int graph_replay(amgh_problem *p, cudaGraphExec_t exec, int nodes);
+bool graphs_enabled(amgh_problem *p);
+
+// ------------------------------------------------------------------ block.cu
+// K columns (K = 2, 4, 8) advanced together; the column-major inputs hold
+// ncols columns of n (or n_vertices) doubles
+void block_free(amgh_problem *p);
+int block_hessian_apply(amgh_problem *p, const double *u, double *hu, int ncols);
+int block_precond_apply(amgh_problem *p, const double *r, double *z, int ncols);
+// the first failing column's status; info accumulates outer_iters and the
+// largest final_relres of the converged columns
+int block_solve(amgh_problem *p, const double *yd, int ncols, double *u, const amgh_solve_opts &o,
+                amgh_solve_info *info);
 
 // timing of fine-level SpMV-class kernels
 void timer_begin(amgh_problem *p, int timed);

@@ -276,6 +276,15 @@ void solver_free_graphs(amgh_problem *p)
 // kernel timing needs one event pair per launch, so it runs without graphs
 static bool use_graphs(amgh_problem *p) { return !p->timer.enabled; }
 
+int graph_capture(amgh_problem *p, const std::function<int()> &body, cudaGraphExec_t *exec, int *nodes)
+{
+    return capture(p, body, exec, nodes);
+}
+
+int graph_replay(amgh_problem *p, cudaGraphExec_t exec, int nodes) { return replay(p, exec, nodes); }
+
+bool graphs_enabled(amgh_problem *p) { return use_graphs(p); }
+
 // ------------------------------------------------------------------ AMG-CG
 __global__ void k_d2f(int n, const double *__restrict__ a, float *__restrict__ b, const int *skip)
 {

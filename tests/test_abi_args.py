@@ -49,6 +49,10 @@ def test_null_arguments():
     assert L.amgh_amg_setup(None, None) == -1
     assert L.amgh_solve(None, None, None, None, None, None) == -1
     assert L.amgh_hessian_apply(None, None, None, 1) == -1
+    assert L.amgh_hessian_apply(None, None, None, 4) == -1
+    assert L.amgh_precond_apply(None, None, None, 4) == -1
+    assert L.amgh_solve_block(None, None, 3, None, None, None) == -1
+    assert L.amgh_batch_set_block(None, 1) == -1
     assert L.amgh_batch_create(None, 0, C.byref(h)) == -1
     assert L.amgh_problem_share(None, C.byref(h)) == -1
     assert L.amgh_aggregate_noalloc(0, None, None, None, 0.08, None, None, None) == -1
