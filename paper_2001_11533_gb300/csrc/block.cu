@@ -36,6 +36,7 @@
 #define KB AMGH_BLOCK_MAX
 
 static const int TPB = 256;
+#define TPB_K 256 // threads per block of every block kernel that reduces
 
 static inline int vblocks(int64_t n)
 {
@@ -298,6 +299,61 @@ __device__ __forceinline__ void row_sum_df_k(const MatView<float> &m, const floa
     for (int c = 0; c < K; c++) out[c] = (double)acc[c].hi + (double)acc[c].lo;
 }
 
+// ------------------------------------------------------------------ reductions
+// Two-stage deterministic sum of NV values per thread over the grid (blocks of
+// TPB threads).  Inside a block the values go through shared memory and warp
+// w sums values w, w + 8, ... (fewer FP64 adds than NV butterflies); block
+// partials ([NV][gridDim.x]) are summed in fixed order by the last block to
+// finish, which issues all NV loads of a pass together.  Returns true in
+// thread 0 of that block, with the sums in tot.
+template <int NV>
+__device__ bool reduce_k(const double (&val)[NV], double *partials, unsigned *ticket, double (&tot)[NV])
+{
+    __shared__ double sh[NV][TPB_K];
+    __shared__ double stot[NV];
+    __shared__ bool is_last;
+    const int t = threadIdx.x, w = t >> 5, l = t & 31, nb = gridDim.x;
+#pragma unroll
+    for (int q = 0; q < NV; q++) sh[q][t] = val[q];
+    __syncthreads();
+    for (int q = w; q < NV; q += TPB_K / 32) {
+        double s = 0.0;
+#pragma unroll
+        for (int j = l; j < TPB_K; j += 32) s += sh[q][j];
+        s = warp_sum(s);
+        if (l == 0) partials[q * nb + blockIdx.x] = s;
+    }
+    __threadfence();
+    __syncthreads();
+    if (t == 0) is_last = atomicAdd(ticket, 1u) == (unsigned)nb - 1;
+    __syncthreads();
+    if (!is_last) return false;
+    __threadfence();
+    double s[NV];
+#pragma unroll
+    for (int q = 0; q < NV; q++) s[q] = 0.0;
+    for (int b = t; b < nb; b += TPB_K) {
+#pragma unroll
+        for (int q = 0; q < NV; q++) s[q] += __ldcg(&partials[q * nb + b]);
+    }
+#pragma unroll
+    for (int q = 0; q < NV; q++) sh[q][t] = s[q];
+    __syncthreads();
+    for (int q = w; q < NV; q += TPB_K / 32) {
+        double u = 0.0;
+#pragma unroll
+        for (int j = l; j < TPB_K; j += 32) u += sh[q][j];
+        u = warp_sum(u);
+        if (l == 0) stot[q] = u;
+    }
+    __syncthreads();
+    if (t != 0) return false;
+#pragma unroll
+    for (int q = 0; q < NV; q++) tot[q] = stot[q];
+    *ticket = 0u;
+    return true;
+}
+
 // ------------------------------------------------------------------ finalisers
 __device__ __forceinline__ bool nonfinite(double x) { return !(x == x) || isinf(x); }
 
@@ -431,7 +487,7 @@ __global__ void kb_cg_start(int n, const double *__restrict__ f, double *__restr
 #pragma unroll
         for (int c = 0; c < K; c++) v[c] += fv[c] * fv[c];
     }
-    if (reduce_last_block<K>(v, partials, ticket, tot)) fin_start<K>(bs, tot, tol2, maxit);
+    if (reduce_k<K>(v, partials, ticket, tot)) fin_start<K>(bs, tot, tol2, maxit);
 }
 
 // r32 = (float)(scale_c r): input of the FP32 V-cycle
@@ -482,7 +538,7 @@ __global__ void kb_cg_spmv(MatView<float> A, const float *__restrict__ lo, const
             a[K + c] = zc * sv[c];
         }
     }
-    if (reduce_last_block<2 * K>(a, partials, ticket, tot)) fin_cg2<K>(bs, tot);
+    if (reduce_k<2 * K>(a, partials, ticket, tot)) fin_cg2<K>(bs, tot);
 }
 
 // the same with FP64 products (precision 0, as the single-column FP64 CG)
@@ -510,46 +566,57 @@ __global__ void kb_cg_spmv64(MatView<double> A, const double *__restrict__ z, co
             a[K + c] = zr[c] * sv[c];
         }
     }
-    if (reduce_last_block<2 * K>(a, partials, ticket, tot)) fin_cg2<K>(bs, tot);
+    if (reduce_k<2 * K>(a, partials, ticket, tot)) fin_cg2<K>(bs, tot);
 }
 
 // p = z + beta p, q = s + beta q, x += alpha p, r -= alpha q per running
 // column; optionally r32 = (float)(scale_c r) or, for Jacobi, z = invd r; r.r
-// per column
+// per column.  For K = 8 two threads share a row, four columns each.
 template <typename Z, int K>
 __global__ void kb_cg_update(int n, Z *z, const double *__restrict__ s, double *__restrict__ pv,
                              double *__restrict__ q, double *__restrict__ x, double *__restrict__ r,
                              float *__restrict__ r32, const double *__restrict__ invd, BScal *bs, double *partials,
                              unsigned *ticket)
 {
+    constexpr int H = K > 4 ? 2 : 1; // threads per row
+    constexpr int KH = K / H;        // columns per thread
     pdl_enter();
     if (bs->all) return;
-    double al[K], be[K], scl[K];
-    bool run[K], first[K];
+    double v[K], tot[K];
 #pragma unroll
-    for (int c = 0; c < K; c++) {
-        const CgScal &sc = bs->c[c];
+    for (int c = 0; c < K; c++) v[c] = 0.0;
+    const int64_t items = (int64_t)n * H;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    int64_t it0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    // the half a thread takes is fixed (stride is even), so are its scalars
+    const int h = H == 1 ? 0 : (int)(it0 & 1);
+    double al[KH], be[KH], scl[KH];
+    bool run[KH], first[KH];
+#pragma unroll
+    for (int c = 0; c < KH; c++) {
+        const CgScal &sc = bs->c[h * KH + c];
         al[c] = sc.alpha;
         be[c] = sc.beta;
         scl[c] = sc.scale;
         run[c] = !sc.done;
         first[c] = sc.beta == 0.0;
     }
-    double v[K], tot[K];
+    double vh[KH];
 #pragma unroll
-    for (int c = 0; c < K; c++) v[c] = 0.0;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        int64_t o = (int64_t)i * K;
-        Z zv[K];
-        double sv[K], pp[K], qq[K], xx[K], rr[K];
-        ldk<K>(z + o, zv);
-        ldk<K>(s + o, sv);
-        ldk<K>(pv + o, pp);
-        ldk<K>(q + o, qq);
-        ldk<K>(x + o, xx);
-        ldk<K>(r + o, rr);
+    for (int c = 0; c < KH; c++) vh[c] = 0.0;
+    for (int64_t it = it0; it < items; it += stride) {
+        int64_t i = it / H;
+        int64_t o = i * K + h * KH;
+        Z zv[KH];
+        double sv[KH], pp[KH], qq[KH], xx[KH], rr[KH];
+        ldk<KH>(z + o, zv);
+        ldk<KH>(s + o, sv);
+        ldk<KH>(pv + o, pp);
+        ldk<KH>(q + o, qq);
+        ldk<KH>(x + o, xx);
+        ldk<KH>(r + o, rr);
 #pragma unroll
-        for (int c = 0; c < K; c++) {
+        for (int c = 0; c < KH; c++) {
             if (!run[c]) continue;
             double zc = (double)zv[c];
             double pc = first[c] ? zc : zc + be[c] * pp[c];
@@ -559,27 +626,32 @@ __global__ void kb_cg_update(int n, Z *z, const double *__restrict__ s, double *
             xx[c] = xx[c] + al[c] * pc;
             rr[c] = rr[c] - al[c] * qc;
         }
-        stk<K>(pv + o, pp);
-        stk<K>(q + o, qq);
-        stk<K>(x + o, xx);
-        stk<K>(r + o, rr);
+        stk<KH>(pv + o, pp);
+        stk<KH>(q + o, qq);
+        stk<KH>(x + o, xx);
+        stk<KH>(r + o, rr);
         if (r32) {
-            float f[K];
+            float f[KH];
 #pragma unroll
-            for (int c = 0; c < K; c++) f[c] = (float)(rr[c] * scl[c]);
-            stk<K>(r32 + o, f);
+            for (int c = 0; c < KH; c++) f[c] = (float)(rr[c] * scl[c]);
+            stk<KH>(r32 + o, f);
         }
         if (invd) {
             double iv = invd[i];
-            Z zn[K];
+            Z zn[KH];
 #pragma unroll
-            for (int c = 0; c < K; c++) zn[c] = (Z)(iv * rr[c]);
-            stk<K>(z + o, zn);
+            for (int c = 0; c < KH; c++) zn[c] = (Z)(iv * rr[c]);
+            stk<KH>(z + o, zn);
         }
 #pragma unroll
-        for (int c = 0; c < K; c++) v[c] += rr[c] * rr[c];
+        for (int c = 0; c < KH; c++) vh[c] += rr[c] * rr[c];
     }
-    if (reduce_last_block<K>(v, partials, ticket, tot)) fin_rr<K>(bs, tot);
+#pragma unroll
+    for (int c = 0; c < KH; c++) {
+        if (H == 1 || h == 0) v[c] = vh[c];
+        else v[KH + c] = vh[c];
+    }
+    if (reduce_k<K>(v, partials, ticket, tot)) fin_rr<K>(bs, tot);
 }
 
 // ------------------------------------------------------------------ V-cycle kernels
@@ -785,7 +857,7 @@ __global__ void kb_dot(int n, const double *__restrict__ x, const double *__rest
 #pragma unroll
         for (int c = 0; c < K; c++) v[c] += xv[c] * yv[c];
     }
-    if (reduce_last_block<K>(v, partials, ticket, tot)) {
+    if (reduce_k<K>(v, partials, ticket, tot)) {
 #pragma unroll
         for (int c = 0; c < K; c++) out[c] = tot[c];
     }
@@ -906,11 +978,20 @@ static int bred_alloc(Arena &ar, RedSlot &slot, int blocks, int nv)
     return AMGH_OK;
 }
 
+// most blocks of a reducing launch on a's rows (the CG update runs up to two
+// threads per row)
 static int red_blocks(const DevCsr &a)
 {
     int g = rows_grid(a.rows, a.tpr < 1 ? 1 : a.tpr);
-    int v = vblocks(a.rows);
+    int v = vblocks(2 * (int64_t)a.rows);
     return g > v ? g : v;
+}
+
+// grid of kb_cg_update<., K>
+template <int K>
+static inline int update_blocks(int n)
+{
+    return vblocks((int64_t)n * (K > 4 ? 2 : 1));
 }
 
 static int block_alloc(amgh_problem *p, int K)
@@ -1237,7 +1318,7 @@ struct Blk {
         };
         std::function<int()> iter = [&]() {
             TRY(cg_spmv<T>(p, S.A, z, B.r, B.s, B.bs, B.red));
-            pdl_launch(kb_cg_update<T, K>, dim3(vblocks(n)), dim3(TPB), 0, p->stream, n, z, (const double *)B.s,
+            pdl_launch(kb_cg_update<T, K>, dim3(update_blocks<K>(n)), dim3(TPB), 0, p->stream, n, z, (const double *)B.s,
                        B.pv, B.q, B.x, B.r, f32 ? B.r32 : (float *)nullptr, (const double *)nullptr, B.bs,
                        B.red.partials, B.red.ticket);
             LAUNCH_CHECK();
@@ -1267,7 +1348,7 @@ struct Blk {
         LAUNCH_CHECK();
         std::function<int()> iter = [&]() {
             TRY(cg_spmv<double>(p, C.Mu, D.mz, D.mr, D.ms, D.mbs, D.red));
-            pdl_launch(kb_cg_update<double, K>, dim3(vblocks(n)), dim3(TPB), 0, p->stream, n, D.mz,
+            pdl_launch(kb_cg_update<double, K>, dim3(update_blocks<K>(n)), dim3(TPB), 0, p->stream, n, D.mz,
                        (const double *)D.ms, D.mp, D.mq, D.mx, D.mr, (float *)nullptr,
                        (const double *)C.mu_invdiag, D.mbs, D.red.partials, D.red.ticket);
             LAUNCH_CHECK();
