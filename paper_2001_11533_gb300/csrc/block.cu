@@ -994,6 +994,10 @@ static inline int update_blocks(int n)
     return vblocks((int64_t)n * (K > 4 ? 2 : 1));
 }
 
+static int block_alloc_into(amgh_problem *p, BlockWork *W, int K);
+
+// work space for blocks of K columns (kept while K and the V-cycle precision
+// stay the same); on failure nothing is left allocated
 static int block_alloc(amgh_problem *p, int K)
 {
     int f32 = p->aopts.precision != 0;
@@ -1002,8 +1006,19 @@ static int block_alloc(amgh_problem *p, int K)
     BlockWork *W = new (std::nothrow) BlockWork();
     if (!W) return AMGH_ERR_OOM;
     p->blk = W;
-    W->K = K;
     W->f32 = f32;
+    int st = block_alloc_into(p, W, K);
+    if (st != AMGH_OK) {
+        block_free(p);
+        return st;
+    }
+    W->K = K;
+    return AMGH_OK;
+}
+
+static int block_alloc_into(amgh_problem *p, BlockWork *W, int K)
+{
+    int f32 = W->f32;
     Arena &ar = W->ar;
     size_t vs = f32 ? sizeof(float) : sizeof(double);
     for (int l = 0; l < p->Ls; l++) {
