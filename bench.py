@@ -60,6 +60,9 @@ def parse():
                     help="levels of the Hessian preconditioner (0 = all AMG levels, as in Sec. 5.3)")
     ap.add_argument("--single-step", action="store_true",
                     help="run one untimed step of the first form (for profilers) and print its counters")
+    ap.add_argument("--block-apply", action="store_true",
+                    help="block solver against single-column solves on one 513^2 square with 8 desired "
+                         "states (prints its own JSON line)")
     ap.add_argument("--autotune", type=int, default=0,
                     help="time the SpMV layouts of every operator at setup (remembered per matrix shape)")
     ap.add_argument("--no-batch", action="store_true",
@@ -440,11 +443,64 @@ def single_step(args):
                       "launches": amgh.launch_count()}))
 
 
+def block_apply(args):
+    """The block solver against single-column work on one jittered 513^2 square
+    with 8 desired states (mixed form, the batch's tolerances): one block
+    Hessian apply of 8 columns against 8 single applies in a row, and one block
+    solve of the 8 desired states against 8 concurrent single-column slots and
+    against 8 single solves in a row.  Host clock around synchronous calls,
+    best of 3 after a warm-up that captures the graphs."""
+    import torch
+
+    from paper_2001_11533_gb300 import _build, amgh, workloads
+    _build.build()
+    w = workloads.batch_squares(sizes=(513,), per_size=1, rhs=8)[0]
+    Y = torch.from_numpy(np.ascontiguousarray(w.y_d)).cuda()
+    amg = dict(coarse_max=1000, precision=PRECISION["mixed"], coarse_solve=2)
+    sopts = dict(tol=1e-8, inner_tol=args.inner_tol, mass_tol=args.precond_tol,
+                 precond_tol=args.precond_tol, level_fallback=1)
+    prob = amgh.Problem.from_workload(w).amg_setup(**amg)
+
+    def best(fn, reps=3):
+        fn()
+        ts = []
+        for _ in range(reps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            fn()
+            torch.cuda.synchronize()
+            ts.append(time.perf_counter() - t0)
+        return min(ts)
+
+    U = torch.from_numpy(np.random.default_rng(1).standard_normal((8, prob.sizes["n"]))).cuda()
+    prob.set_solve_opts(inner_tol=args.inner_tol, mass_tol=args.precond_tol, precond_tol=args.precond_tol)
+    t_hb = best(lambda: prob.hessian_apply(U))
+    t_hs = best(lambda: [prob.hessian_apply(U[c]) for c in range(8)])
+    t_sb = best(lambda: prob.solve_block(Y, **sopts))
+
+    def singles():
+        for c in range(8):
+            prob.set_yd(Y[c])
+            prob.solve(want_y=False, **sopts)
+    t_ss = best(singles)
+    batch = amgh.Batch([amgh.Problem.from_workload(w)]).setup(**amg)
+    t_sc = best(lambda: batch.solve([Y], **sopts))
+    batch.close()
+    print(json.dumps({"block_apply": {
+        "workload": "jittered 513^2 square, 8 desired states, mixed form", "K": 8,
+        "hessian_apply_block_s": t_hb, "hessian_apply_8_single_s": t_hs,
+        "solve_block_s": t_sb, "solve_8_concurrent_slots_s": t_sc, "solve_8_single_s": t_ss,
+        "timing": "host clock around synchronous calls, best of 3 after a warm-up"}}), flush=True)
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
     if args.single_step:
         single_step(args)
+        return
+    if args.block_apply:
+        block_apply(args)
         return
     if args.impl == "reference":
         run_reference(args, rank, world)
