@@ -197,3 +197,23 @@ def test_batch_block_mode():
         assert st == 0 and np.array_equal(host(u), host(ub))
         for c in range(w.y_d.shape[0]):
             assert rel(host(u[c]), host(uc[c])) <= 1e-8
+
+
+def test_more_columns_than_one_block():
+    """10 columns run as a block of 8 and a padded block of 2 more: every
+    column still matches the oracle (H applies) and its own one-column block
+    solve bit for bit."""
+    w = _lshape()
+    prob = _problem(w, coarse_max=32, precision=2)
+    prob.set_solve_opts(**TIGHT)
+    orc = Oracle(w, coarse_max=32, inner_tol=1e-13, mass_tol=1e-13)
+    U = np.random.default_rng(33).standard_normal((10, prob.sizes["n"]))
+    HU = host(prob.hessian_apply(cuda(U)))
+    for c in (0, 7, 8, 9):
+        assert rel(HU[c], orc.hessian(U[c])) <= 1e-10, c
+    Y = _desired_states(w, 10)
+    u, info, st = prob.solve_block(cuda(Y), tol=1e-10)
+    assert st == 0 and info["outer_iters"] > 0
+    for c in (1, 8, 9):
+        u1, _, st = prob.solve_block(cuda(Y[c:c + 1]), tol=1e-10)
+        assert st == 0 and np.array_equal(host(u1[0]), host(u[c])), c
