@@ -47,3 +47,15 @@ def test_defaults_without_gpu(libpath):
     assert (o.max_levels, o.coarse_max, o.smooth_degree, o.theta) == (25, 256, 2, 0.08)
     s = amgh.solve_opts()
     assert (s.tol, s.inner_tol, s.precond) == (1e-8, 1e-10, 1)
+
+
+def test_stacked_vectors_are_column_major():
+    """A (k, n) contiguous tensor is k columns of n, i.e. the column-major
+    n x k block the C ABI expects; other layouts are refused."""
+    import torch
+    from paper_2001_11533_gb300 import amgh
+    cols = amgh.Problem._cols
+    assert cols(torch.zeros(7, dtype=torch.float64)) == 1
+    assert cols(torch.zeros(3, 7, dtype=torch.float64)) == 3
+    with pytest.raises(ValueError):
+        cols(torch.zeros(7, 3, dtype=torch.float64).t())
