@@ -29,8 +29,9 @@
  * Pins (tests/test_oracle_*.py): assembly against exact integrals, an
  * independent assembly and harmonic linear functions; aggregation against a
  * greedy sequential MIS(2) and a golden 5x5 grid; Galerkin products and the
- * prolongator against their definitions; the V-cycle by symmetry, positivity
- * and contraction; H against the dense formula, a KKT direct solve and a
+ * prolongator against their definitions; the smoother's error propagator
+ * against the closed-form Chebyshev residual polynomial (and (1-t)^k for
+ * l1-Jacobi) of D^-1 A; the V-cycle by symmetry, positivity and contraction; H against the dense formula, a KKT direct solve and a
  * closed form; MLAS against its closed two-grid formula and the coarse CG
  * against a dense solve of H_{l-1}.
  */
@@ -1369,6 +1370,21 @@ int orc_vcycle(void *h, int l, const double *b, double *x)
     orc_t *o = h;
     if (!o->setup_done || l < 0 || l >= o->Ls) return ORC_NOT_SETUP;
     return vcycle(o, l, b, x);
+}
+
+/* the level-l smoother alone: x <- x after the nsteps polynomial steps for
+ * A_l x = b (zero_init: start from x = 0, else from the x passed in) */
+int orc_smooth(void *h, int l, const double *b, double *x, int zero_init)
+{
+    orc_t *o = h;
+    if (!o->setup_done || l < 0 || l >= o->Ls) return ORC_NOT_SETUP;
+    int n = o->A[l].rows;
+    double *d = xcalloc((size_t)n, sizeof(double)), *r = xcalloc((size_t)n, sizeof(double));
+    if (!d || !r) return ORC_OOM;
+    smooth(o, l, b, x, zero_init, d, r);
+    free(d);
+    free(r);
+    return ORC_OK;
 }
 
 int orc_state_solve(void *h, int l, double tol, const double *f, double *y, long *iters)

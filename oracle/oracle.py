@@ -65,6 +65,7 @@ def lib():
                 "orc_aggregates": [P, I, I, P, P],
                 "orc_aggregate_csr": [I, P, P, P, D, P, P, P],
                 "orc_vcycle": [P, I, P, P],
+                "orc_smooth": [P, I, P, P, I],
                 "orc_state_solve": [P, I, D, P, P, P],
                 "orc_mass_solve": [P, I, P, P, P],
                 "orc_hessian": [P, I, P, P],
@@ -212,6 +213,13 @@ class Oracle:
         b = np.ascontiguousarray(b, dtype=np.float64)
         x = np.zeros_like(b)
         _check(lib().orc_vcycle(self.h, level, _p(b), _p(x)), "vcycle")
+        return x
+
+    def smooth(self, level, b, x0=None):
+        """The level's polynomial smoother alone for A_l x = b, from x0 (None: from zero)."""
+        b = np.ascontiguousarray(b, dtype=np.float64)
+        x = np.zeros_like(b) if x0 is None else np.array(x0, dtype=np.float64, copy=True)
+        _check(lib().orc_smooth(self.h, level, _p(b), _p(x), 1 if x0 is None else 0), "smooth")
         return x
 
     def state_solve(self, f, level=0, tol=1e-10):
