@@ -352,6 +352,23 @@ int amgh_reset_counters(amgh_problem *p);
 int amgh_kernel_timing(amgh_problem *p, int enable);
 int amgh_kernel_stats(amgh_problem *p, int64_t *launches, double *ms, double *bytes);
 
+/* Test hook for the bounded waits (no counterpart in the paper; process-wide,
+ * not for production use).
+ *   bulk_first_polls  poll limit of the level-0 staged smoother's wait for its
+ *                     bulk copies: -1 restores the default, 0 makes every
+ *                     block give up at once (its copies still drain under a
+ *                     separate, larger limit before the block exits).  A
+ *                     block that gives up computes nothing and raises a flag;
+ *                     every solve-phase call checks the flag after its work
+ *                     and then returns AMGH_ERR_TIMEOUT, whatever else
+ *                     happened: all values that call produced are invalid.
+ *   mis_round_cap     rounds the aggregation's distance-2 independent-set
+ *                     loop may take before amgh_amg_setup returns
+ *                     AMGH_ERR_TIMEOUT (-1: the default, n + 1 rounds, which
+ *                     always suffice).
+ * Errors: INVALID_ARG for values below -1, CUDA. */
+int amgh_debug_limits(int bulk_first_polls, int mis_round_cap);
+
 /* Batched solves of many independent problems (the batching pattern: many
  * desired states, many meshes of uneven size).  Every (problem, desired
  * state) pair is an independent outer CG.  The batch runtime gives each
@@ -401,8 +418,9 @@ void amgh_batch_destroy(amgh_batch *b);
  * distance-2 independent set by splitmix64 priority and phases 1-3.
  *   n              rows, 1 .. 32768 (more: AMGH_ERR_INVALID_ARG)
  *   rowptr_dev, col_dev, val_dev   CSR of a symmetric matrix with sorted
- *                  columns, on the current device; at most 262144 entries
- *                  (more: AMGH_ERR_INVALID_ARG)
+ *                  columns, on the current device; rowptr_dev[0] must be 0
+ *                  and rowptr_dev[n] at most 262144 (else AMGH_ERR_INVALID_ARG,
+ *                  before any kernel runs)
  *   stream         cudaStream_t to run on (NULL = legacy default stream)
  *   agg_dev        n int32 outputs (device); *nagg_host = number of aggregates
  * Scratch comes from one fixed buffer inside the library (about 5 MB per

@@ -89,6 +89,7 @@ _SIGS = {
     "amgh_get_level_counters": ([_P, _P, _P], _I),
     "amgh_kernel_timing": ([_P, _I], _I),
     "amgh_kernel_stats": ([_P, _P, _P, _P], _I),
+    "amgh_debug_limits": ([_I, _I], _I),
     "amgh_launch_count": ([], _I64),
     "amgh_aggregate_noalloc": ([_I, _P, _P, _P, _D, _P, _P, _P], _I),
     "amgh_batch_create": ([_P, _I, _P], _I),
@@ -139,6 +140,11 @@ def _ptr(t):
     if isinstance(t, np.ndarray):
         return t.ctypes.data_as(C.c_void_p)
     return C.c_void_p(t.data_ptr())
+
+
+def debug_limits(bulk_first_polls: int = -1, mis_round_cap: int = -1):
+    """amgh_debug_limits: lower the bounded waits' limits for tests (-1 = default)."""
+    check(lib().amgh_debug_limits(int(bulk_first_polls), int(mis_round_cap)), "amgh_debug_limits")
 
 
 def launch_count() -> int:

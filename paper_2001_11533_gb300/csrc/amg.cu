@@ -217,6 +217,10 @@ __global__ void k_phase3(int n, const int *__restrict__ fr, const int *__restric
     if (i < n && fr[i]) agg[i] = nroots + frank[i];
 }
 
+// cap on the MIS-2 rounds (0: n + 1); lowered only by amgh_debug_limits
+static int g_mis_round_cap = 0;
+void mis_set_round_cap(int cap) { g_mis_round_cap = cap > 0 ? cap : 0; }
+
 int amg_aggregate(amgh_problem *p, const DevCsr &a, double theta2, int *agg, int *nagg_out)
 {
     cudaStream_t s = p->stream;
@@ -264,7 +268,8 @@ int amg_aggregate(amgh_problem *p, const DevCsr &a, double theta2, int *agg, int
         CU(cudaStreamSynchronize(s));
         rounds++;
         if (h == 0) break;
-        if (rounds > n + 1) return AMGH_ERR_TIMEOUT; // each round fixes at least one vertex
+        // each round fixes at least one vertex, so n + 1 rounds always suffice
+        if (rounds > (g_mis_round_cap > 0 ? g_mis_round_cap : n + 1)) return AMGH_ERR_TIMEOUT;
     }
     // phases
     int *flag = nullptr, *rank = nullptr, *agg1 = nullptr, *fr = nullptr, *frank = nullptr;

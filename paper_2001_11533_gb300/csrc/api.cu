@@ -461,15 +461,25 @@ extern "C" int amgh_amg_setup(amgh_problem *p, const amgh_amg_opts *opts)
         if (!(p)->setup_done) return AMGH_ERR_NOT_SETUP; \
     } while (0)
 
+// End of a solve-phase entry point: wait for the stream, then report a staged
+// copy that timed out in place of any other status, since it invalidates every
+// value the call produced.
+static int finish_call(amgh_problem *p, int st)
+{
+    int s2 = sync_stream(p);
+    int s3 = s2 == AMGH_OK ? bulk_timeout_check(p->stream) : s2;
+    if (s3 == AMGH_ERR_TIMEOUT) return s3;
+    return st != AMGH_OK ? st : s3;
+}
+
 extern "C" int amgh_hessian_apply(amgh_problem *p, const double *u, double *hu, int ncols)
 {
     NEED_SETUP(p);
     StreamScope ss_(p->stream);
     if (!u || !hu || ncols < 1) return AMGH_ERR_INVALID_ARG;
-    if (ncols > 1) TRY(block_hessian_apply(p, u, hu, ncols));
-    else TRY(hessian_level(p, 0, u, hu));
-    TRY(timer_collect(p));
-    return sync_stream(p);
+    int st = ncols > 1 ? block_hessian_apply(p, u, hu, ncols) : hessian_level(p, 0, u, hu);
+    if (st == AMGH_OK) st = timer_collect(p);
+    return finish_call(p, st);
 }
 
 extern "C" int amgh_precond_apply(amgh_problem *p, const double *r, double *z, int ncols)
@@ -477,10 +487,9 @@ extern "C" int amgh_precond_apply(amgh_problem *p, const double *r, double *z, i
     NEED_SETUP(p);
     StreamScope ss_(p->stream);
     if (!r || !z || ncols < 1) return AMGH_ERR_INVALID_ARG;
-    if (ncols > 1) TRY(block_precond_apply(p, r, z, ncols));
-    else TRY(mlas_Q(p, 0, r, z));
-    TRY(timer_collect(p));
-    return sync_stream(p);
+    int st = ncols > 1 ? block_precond_apply(p, r, z, ncols) : mlas_Q(p, 0, r, z);
+    if (st == AMGH_OK) st = timer_collect(p);
+    return finish_call(p, st);
 }
 
 extern "C" int amgh_rhs(amgh_problem *p, double *b)
@@ -488,8 +497,7 @@ extern "C" int amgh_rhs(amgh_problem *p, double *b)
     NEED_SETUP(p);
     StreamScope ss_(p->stream);
     if (!b) return AMGH_ERR_INVALID_ARG;
-    TRY(rhs_apply(p, b));
-    return sync_stream(p);
+    return finish_call(p, rhs_apply(p, b));
 }
 
 static void fill_info(amgh_problem *p, amgh_solve_info *info)
@@ -542,9 +550,7 @@ extern "C" int amgh_solve(amgh_problem *p, const double *u0, double *u, double *
     if (info) *info = loc;
     int st2 = timer_collect(p);
     if (st == AMGH_OK) st = st2;
-    if (st == AMGH_OK) st = sync_stream(p);
-    if (st == AMGH_OK) st = bulk_timeout_check(p->stream);
-    return st;
+    return finish_call(p, st);
 }
 
 extern "C" int amgh_solve_block(amgh_problem *p, const double *yd, int ncols, double *u,
@@ -582,10 +588,7 @@ extern "C" int amgh_solve_block(amgh_problem *p, const double *yd, int ncols, do
     loc.fallbacks = fallbacks;
     loc.t_solve_s = now_s() - t0;
     if (info) *info = loc;
-    int st2 = sync_stream(p);
-    if (st == AMGH_OK) st = st2;
-    if (st == AMGH_OK) st = bulk_timeout_check(p->stream);
-    return st;
+    return finish_call(p, st);
 }
 
 extern "C" int amgh_solve_host(amgh_problem *p, const double *u0_host, double *u_host, double *y_host,
@@ -623,7 +626,8 @@ extern "C" int amgh_state_solve(amgh_problem *p, const double *u, double *y, dou
     CtrlLevel &C = p->cl[0];
     StateLevel &S = p->sl[0];
     TRY(spmv(p, C.Myu, u, C.t1, nullptr, 0));
-    TRY(state_solve(p, 0, C.t1, y, p->sopts.inner_tol, nullptr));
+    int st = state_solve(p, 0, C.t1, y, p->sopts.inner_tol, nullptr);
+    if (st != AMGH_OK) return finish_call(p, st);
     if (J) {
         int m = p->m, n = p->n;
         k_sub<<<ceil_div(m, 256), 256, 0, p->stream>>>(m, y, p->yd_state, C.t1);
@@ -637,7 +641,7 @@ extern "C" int amgh_state_solve(amgh_problem *p, const double *u, double *y, dou
         CU(cudaStreamSynchronize(p->stream));
         *J = 0.5 * h[0] + 0.5 * p->beta * h[1];
     }
-    return sync_stream(p);
+    return finish_call(p, AMGH_OK);
 }
 
 extern "C" int amgh_gradient(amgh_problem *p, const double *u, const double *y, double *g)
@@ -651,9 +655,9 @@ extern "C" int amgh_gradient(amgh_problem *p, const double *u, const double *y, 
     k_sub<<<ceil_div(m, 256), 256, 0, p->stream>>>(m, y, p->yd_state, C.t1);
     LAUNCH_CHECK();
     TRY(spmv(p, S.My, C.t1, C.t2, nullptr, 0));
-    TRY(state_solve(p, 0, C.t2, C.ps, p->sopts.inner_tol, nullptr));
-    TRY(spmv2(p, C.Myut, C.ps, C.Mu, u, p->beta, g, nullptr));
-    return sync_stream(p);
+    int st = state_solve(p, 0, C.t2, C.ps, p->sopts.inner_tol, nullptr);
+    if (st == AMGH_OK) st = spmv2(p, C.Myut, C.ps, C.Mu, u, p->beta, g, nullptr);
+    return finish_call(p, st);
 }
 
 extern "C" int amgh_state_adjoint(amgh_problem *p, const double *w, double *g)
@@ -663,9 +667,9 @@ extern "C" int amgh_state_adjoint(amgh_problem *p, const double *w, double *g)
     if (!w || !g) return AMGH_ERR_INVALID_ARG;
     CtrlLevel &C = p->cl[0];
     // A is symmetric, so A^-T w is one more AMG-CG solve
-    TRY(state_solve(p, 0, w, C.ps, p->sopts.inner_tol, nullptr));
-    TRY(spmv(p, C.Myut, C.ps, g, nullptr, 0));
-    return sync_stream(p);
+    int st = state_solve(p, 0, w, C.ps, p->sopts.inner_tol, nullptr);
+    if (st == AMGH_OK) st = spmv(p, C.Myut, C.ps, g, nullptr, 0);
+    return finish_call(p, st);
 }
 
 // ------------------------------------------------------------------ level-wise
@@ -674,8 +678,7 @@ extern "C" int amgh_vcycle(amgh_problem *p, int level, const double *b, double *
     NEED_SETUP(p);
     StreamScope ss_(p->stream);
     if (level < 0 || level >= p->Ls || !b || !x) return AMGH_ERR_INVALID_ARG;
-    TRY(vcycle_run(p, level, 0, b, x, nullptr));
-    return sync_stream(p);
+    return finish_call(p, vcycle_run(p, level, 0, b, x, nullptr));
 }
 
 extern "C" int amgh_state_solve_level(amgh_problem *p, int level, const double *f, double *y, double tol,
@@ -684,8 +687,7 @@ extern "C" int amgh_state_solve_level(amgh_problem *p, int level, const double *
     NEED_SETUP(p);
     StreamScope ss_(p->stream);
     if (level < 0 || level >= p->Ls || !f || !y || !(tol > 0.0)) return AMGH_ERR_INVALID_ARG;
-    TRY(state_solve(p, level, f, y, tol, iters));
-    return sync_stream(p);
+    return finish_call(p, state_solve(p, level, f, y, tol, iters));
 }
 
 extern "C" int amgh_mass_solve(amgh_problem *p, int level, const double *b, double *x, int64_t *iters)
@@ -702,8 +704,7 @@ extern "C" int amgh_hessian_apply_level(amgh_problem *p, int level, const double
     NEED_SETUP(p);
     StreamScope ss_(p->stream);
     if (level < 0 || level >= p->ell || !v || !hv) return AMGH_ERR_INVALID_ARG;
-    TRY(hessian_level(p, level, v, hv));
-    return sync_stream(p);
+    return finish_call(p, hessian_level(p, level, v, hv));
 }
 
 extern "C" int amgh_precond_apply_level(amgh_problem *p, int which, int level, const double *b, double *z)
@@ -711,12 +712,8 @@ extern "C" int amgh_precond_apply_level(amgh_problem *p, int which, int level, c
     NEED_SETUP(p);
     StreamScope ss_(p->stream);
     if (level < 0 || level >= p->ell || !b || !z) return AMGH_ERR_INVALID_ARG;
-    if (which == 0) TRY(mlas_Q(p, level, b, z));
-    else {
-        if (level >= p->ell - 1) return AMGH_ERR_INVALID_ARG;
-        TRY(mlas_R(p, level, b, z));
-    }
-    return sync_stream(p);
+    if (which != 0 && level >= p->ell - 1) return AMGH_ERR_INVALID_ARG;
+    return finish_call(p, which == 0 ? mlas_Q(p, level, b, z) : mlas_R(p, level, b, z));
 }
 
 // ------------------------------------------------------------------ queries
@@ -819,6 +816,13 @@ extern "C" int amgh_get_level_counters(const amgh_problem *p, int64_t *inner, in
         if (mass) mass[l] = p->c_mass_lvl[l];
     }
     return AMGH_OK;
+}
+
+extern "C" int amgh_debug_limits(int bulk_first_polls, int mis_round_cap)
+{
+    if (bulk_first_polls < -1 || mis_round_cap < -1) return AMGH_ERR_INVALID_ARG;
+    mis_set_round_cap(mis_round_cap);
+    return bulk_set_first_polls(bulk_first_polls);
 }
 
 extern "C" int amgh_kernel_timing(amgh_problem *p, int enable)

@@ -324,6 +324,11 @@ int prepare_operator(Arena &ar, DevCsr &a, cudaStream_t s, int force_tpr = 0);
 int prepare_tuned(amgh_problem *p, Arena &ar, DevCsr &a, int is_state_matrix);
 // AMGH_ERR_TIMEOUT (and the flag cleared) if a staged copy timed out
 int bulk_timeout_check(cudaStream_t s);
+// poll limit of the staged smoother's first wait (< 0: the default; 0: give
+// up at once, the copies still drain); test hook behind amgh_debug_limits
+int bulk_set_first_polls(int polls);
+// rounds the MIS-2 loop may take before AMGH_ERR_TIMEOUT (<= 0: n + 1)
+void mis_set_round_cap(int cap);
 // b = (float)a
 int to_f32(amgh_problem *p, const double *a, int64_t n, float *b);
 // build a.lo32 (after prepare_operator)

@@ -126,10 +126,12 @@ extern "C" int amgh_aggregate_noalloc(int n, const int32_t *rp, const int32_t *c
     if (n <= 0 || !rp || !ci || !v || !agg || !nagg || !(theta >= 0.0)) return AMGH_ERR_INVALID_ARG;
     if (n > NOALLOC_MAX_ROWS) return AMGH_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
-    int nnz = 0;
+    int first = -1, nnz = 0;
+    CU(cudaMemcpyAsync(&first, rp, sizeof(int), cudaMemcpyDeviceToHost, s));
     CU(cudaMemcpyAsync(&nnz, rp + n, sizeof(int), cudaMemcpyDeviceToHost, s));
     CU(cudaStreamSynchronize(s));
-    if (nnz < 0 || nnz > NOALLOC_MAX_NNZ) return AMGH_ERR_INVALID_ARG;
+    // a CSR must start at entry 0; the entry count bounds every scratch array
+    if (first != 0 || nnz < 0 || nnz > NOALLOC_MAX_NNZ) return AMGH_ERR_INVALID_ARG;
     unsigned char *base = nullptr;
     TRY(scratch_address(&base));
     size_t off = 0;

@@ -426,11 +426,20 @@ __global__ void k_cheb_first(int n, const T *__restrict__ invd, const T *__restr
 // transaction while the threads load their rows' b, D^-1, d and x; then
 // each thread gathers x at its row's columns, summing in the same order as
 // row_sum in the register-loading kernel.  A copy that has not landed
-// after the poll limit sets g_bulk_timeout and the block computes nothing.
+// after g_bulk_first_polls polls sets g_bulk_timeout and the block computes
+// nothing: it then waits (again bounded, with a far larger limit) for its
+// copies to land before it exits, so that no copy is still writing into
+// shared memory that a later block on the SM may own.  The host turns the
+// flag into AMGH_ERR_TIMEOUT for the whole call: every value that call
+// produced is invalid.
 #define ELL_SLICES 8
 #define ELL_MAX_W 16
 #define BULK_POLLS (1 << 16)
+#define BULK_DRAIN_POLLS (1 << 22)
 __device__ int g_bulk_timeout = 0;
+// poll limit of the first wait; lowered only by amgh_debug_limits (tests of
+// the timeout path), read by every block so captured graphs see changes
+__device__ int g_bulk_first_polls = BULK_POLLS;
 
 template <bool D16>
 __global__ void __launch_bounds__(32 * ELL_SLICES)
@@ -465,9 +474,9 @@ __global__ void __launch_bounds__(32 * ELL_SLICES)
         xr = x[row];
     }
     __syncthreads(); // the barrier is initialised before anyone polls it
-    if (!mbar_wait(&bar, 0, BULK_POLLS)) {
+    if (!mbar_wait(&bar, 0, *(volatile int *)&g_bulk_first_polls)) {
         if (threadIdx.x == 0) atomicExch(&g_bulk_timeout, 1);
-        mbar_wait(&bar, 0, BULK_POLLS); // let the copies into this block's memory finish
+        mbar_wait(&bar, 0, BULK_DRAIN_POLLS); // let the copies into this block's memory finish
         return;
     }
     if (!ok) return;
@@ -738,6 +747,14 @@ int spmv(amgh_problem *p, const DevCsr &a, const double *x, double *y, const int
 int spmv32(amgh_problem *p, const DevCsr &a, const float *x, float *y, const int *skip, int timed)
 {
     return spmv_t<float>(p, a, x, y, skip, timed);
+}
+
+int bulk_set_first_polls(int polls)
+{
+    int v = polls > 0 ? polls : BULK_POLLS;
+    if (polls == 0) v = 0;
+    CU(cudaMemcpyToSymbol(g_bulk_first_polls, &v, sizeof(int)));
+    return AMGH_OK;
 }
 
 // nonzero once a staged copy has timed out (then cleared)

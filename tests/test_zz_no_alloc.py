@@ -55,3 +55,24 @@ def test_noalloc_rejects_oversized_input():
     with pytest.raises(amgh.AmghError) as e:
         amgh.aggregate_noalloc(rp, ci, v, 0.08, out)
     assert e.value.code == -1
+
+
+def test_noalloc_rejects_too_many_entries_and_bad_rowptr():
+    """Rows within the limit but more stored entries than the scratch holds, and a
+    row-pointer array that does not start at 0: both refused before any kernel."""
+    import torch
+    from paper_2001_11533_gb300 import amgh
+    n, per_row = 1000, 300                       # 300,000 entries > 262,144
+    rp = torch.arange(n + 1, dtype=torch.int32, device="cuda") * per_row
+    ci = torch.arange(per_row, dtype=torch.int32, device="cuda").repeat(n)
+    v = torch.ones(n * per_row, dtype=torch.float64, device="cuda")
+    out = torch.empty(n, dtype=torch.int32, device="cuda")
+    with pytest.raises(amgh.AmghError) as e:
+        amgh.aggregate_noalloc(rp, ci, v, 0.08, out)
+    assert e.value.code == -1
+    rp1 = torch.arange(n + 1, dtype=torch.int32, device="cuda") + 1
+    ci1 = torch.arange(n + 1, dtype=torch.int32, device="cuda") % n
+    v1 = torch.ones(n + 1, dtype=torch.float64, device="cuda")
+    with pytest.raises(amgh.AmghError) as e:
+        amgh.aggregate_noalloc(rp1, ci1, v1, 0.08, out)
+    assert e.value.code == -1
