@@ -70,6 +70,15 @@ def parse():
     ap.add_argument("--batch-steps", type=int, default=2)
     ap.add_argument("--forms", default="mixed,fp64,refine",
                     help="mixed = FP64 CG + FP32 V-cycles; fp64; refine = FP32 CG in FP64 refinement")
+    ap.add_argument("--no-cube", action="store_true",
+                    help="skip the 257^3 slab-cube block (mixed and FP64, >= 6 AMG levels)")
+    ap.add_argument("--cube-N", type=int, default=257)
+    ap.add_argument("--cube-steps", type=int, default=1)
+    ap.add_argument("--cube-warmup", type=int, default=1)
+    ap.add_argument("--cube-coarse-max", type=int, default=16,
+                    help="AMG coarsening of the cube block stops at or below this many rows")
+    ap.add_argument("--cpu-budget", type=float, default=12.0,
+                    help="seconds of oracle Hessian applies per CPU-baseline leg (one core, all cores)")
     return ap.parse_args()
 
 
@@ -265,22 +274,35 @@ def run_amgh(args, rank, world, local):
             "clocks": clk.summary(),
             "levels": {"state": sizes["state"], "control": sizes["control"], "ell": sizes["ell"]},
         }
-    # end-to-end through the host-buffer entry points (H2D of the inputs, D2H of u and y)
+    # end-to-end through the host-buffer entry points (H2D of the inputs from
+    # pinned memory, D2H of u and y), timed as `value`: the same number of
+    # steps, CUDA events on the launching stream, L2 flushed between steps
     head = forms[0]
     precision = PRECISION[head]
-    step(precision, e2e=True)
+    for _ in range(args.warmup):
+        step(precision, e2e=True)
     torch.cuda.synchronize()
     barrier()
-    t0 = time.perf_counter()
-    e_happ = 0
-    for k in range(max(1, min(args.steps, 3))):
+    e_times, e_happ = [], 0
+    for k in range(args.steps):
+        flush.zero_()
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
         info, _, sizes = step(precision, e2e=True)
+        ev1.record(stream)
+        ev1.synchronize()
+        e_times.append(ev0.elapsed_time(ev1))
         e_happ += info["hessian_applies"]
     torch.cuda.synchronize()
-    e2e_t = time.perf_counter() - t0
+    barrier()
+    e2e_t = sum(e_times) / 1000.0
+    (e2e_t,), (e_happ,) = replicas.combine([e2e_t], [e_happ], device="cuda")
     h2d = sum(a.nbytes for a in host)
     d2h = 8 * (sizes["n"] + sizes["m"])
-    e2e = {"value": e_happ / e2e_t, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+    e2e = {"value": e_happ / e2e_t, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+           "ms_per_step": 1000.0 * e2e_t / args.steps,
+           "timing": "CUDA events on the launching stream, same steps as value, 256 MB L2 flush between steps"}
     return w, results, e2e
 
 
@@ -344,6 +366,84 @@ def run_batch(args, rank, world, local):
     return out
 
 
+def run_cube(args, rank, world, local):
+    """The large 3D high-contrast case: 257^3 Kuhn cube (16.6M states), kappa in
+    10 jittered slabs of {1, 1e6}, beta = 1e-6, 32 bumps, with the multilevel
+    Hessian preconditioner over all AMG levels (coarsening to <= cube_coarse_max
+    rows: >= 6 levels), the coarsest Hessian level dense up to 4096 dofs else by
+    CG, and the level fallback on.  One step as in the headline (assembly +
+    setup + rhs + outer CG to 1e-8 + true residual), in the mixed and the FP64
+    form; CUDA events on the launching stream, L2 flushed before each step.
+    Every rank runs its own replica."""
+    import torch
+
+    from paper_2001_11533_gb300 import amgh, replicas, workloads
+    w = workloads.cube_slabs(N=args.cube_N)
+    dev = [torch.from_numpy(np.ascontiguousarray(a)).cuda()
+           for a in (w.coords, w.elements.astype(np.int32), w.dirichlet.astype(np.uint8), w.kappa, w.y_d)]
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    tols = dict(tol=1e-8, inner_tol=args.inner_tol, mass_tol=args.precond_tol, precond_tol=args.precond_tol,
+                level_fallback=1)
+
+    def step(precision, timing=False):
+        prob = amgh.Problem(w.dim, dev[0], dev[1], dev[2], dev[3], w.beta, dev[4], on_device=True)
+        prob.amg_setup(precision=precision, coarse_max=args.cube_coarse_max, smooth_degree=args.degree,
+                       coarse_solve=2)
+        if timing:
+            prob.kernel_timing(True)
+        u, y, info = prob.solve(want_y=False, **tols)
+        ks = prob.kernel_stats() if timing else None
+        sizes = prob.sizes
+        prob.close()
+        return info, ks, sizes
+
+    out = {"workload": f"cube{args.cube_N}_slabs", "m": w.n_interior, "n": w.n_vertices, "beta": w.beta,
+           "kappa": "10 jittered slabs {1,1e6}", "coarse_max": args.cube_coarse_max,
+           "steps": args.cube_steps, "warmup": args.cube_warmup,
+           "timing": "CUDA events per step on the launching stream, 256 MB L2 flush before each step"}
+    for form in ("mixed", "fp64"):
+        precision = PRECISION[form]
+        for _ in range(args.cube_warmup):
+            step(precision)
+        torch.cuda.synchronize()
+        times, infos = [], []
+        with ClockSampler(local) as clk:
+            for _ in range(args.cube_steps):
+                flush.zero_()
+                ev0 = torch.cuda.Event(enable_timing=True)
+                ev1 = torch.cuda.Event(enable_timing=True)
+                ev0.record(stream)
+                info, _, sizes = step(precision)
+                ev1.record(stream)
+                ev1.synchronize()
+                times.append(ev0.elapsed_time(ev1) / 1000.0)
+                infos.append(info)
+        t = sum(times)
+        happ = sum(i["hessian_applies"] for i in infos)
+        (t,), (happ_all,) = replicas.combine([t], [happ], device="cuda")
+        last = infos[-1]
+        res = {"time_to_1e-8_s": t / args.cube_steps, "hessian_matvecs_per_s": happ_all / t,
+               "outer_iters": last["outer_iters"], "inner_iters": last["inner_iters"],
+               "mass_iters": last["mass_iters"], "coarse_iters": last["coarse_iters"],
+               "hessian_applies": last["hessian_applies"], "final_relres": last["final_relres"],
+               "setup_s": last["t_setup_s"], "solve_s": last["t_solve_s"], "status": last["status"],
+               "fallbacks": last["fallbacks"], "hessian_levels": last["hessian_levels"],
+               "levels": {"state": sizes["state"], "control": sizes["control"], "ell": sizes["ell"]},
+               "clocks": clk.summary()}
+        if form == "mixed":
+            flush.zero_()
+            _, ks, _ = step(precision, timing=True)
+            res["roofline"] = roofline_from({"kstats": ks}, args, kernel_note="level-0 Chebyshev smoother "
+                                            "step on the 3D uniform-width SELL-32 matrix (int32 columns)",
+                                            traffic=None)
+        out[form] = res
+    out["speedup_mixed_vs_fp64"] = out["fp64"]["time_to_1e-8_s"] / out["mixed"]["time_to_1e-8_s"]
+    del dev
+    torch.cuda.empty_cache()
+    return out
+
+
 def captured_traffic(args):
     """DRAM bytes per launch of the level-0 smoother step from the committed ncu
     summary, or None if the kernel source changed since that capture (or the
@@ -362,7 +462,7 @@ def captured_traffic(args):
         return None
 
 
-def roofline_from(res, args):
+def roofline_from(res, args, kernel_note=None, traffic="captured"):
     ks = res["kstats"]
     peaks = measured_peaks()
     if peaks and peaks.get("hbm_gbs"):
@@ -373,36 +473,74 @@ def roofline_from(res, args):
         return None
     achieved = ks["bytes"] / (ks["ms"] / 1000.0) / 1e9
     return {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-            "frac": round(achieved / peak, 4), "traffic": captured_traffic(args), "peak_source": src,
-            "kernel": "level-0 Chebyshev smoother step (k_cheb_step_ell: uniform-width SELL-32 staged into shared memory by bulk copies)",
+            "frac": round(achieved / peak, 4),
+            "traffic": captured_traffic(args) if traffic == "captured" else traffic, "peak_source": src,
+            "kernel": kernel_note or "level-0 Chebyshev smoother step (k_cheb_step_ell: uniform-width SELL-32 "
+                                     "staged into shared memory by bulk copies)",
             "launches": ks["launches"], "avg_us": round(1000.0 * ks["ms"] / ks["launches"], 2)}
 
 
 # ------------------------------------------------------------------------- oracle (CPU)
-def oracle_apply_rate(w, budget_s, args, applies=None):
-    """Time the FP64 oracle's Hessian apply on the host (setup untimed)."""
+def host_cpu():
+    """The host's CPU as lscpu reports it (model, sockets, cores), read in this run."""
+    info = {"nproc": os.cpu_count()}
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=20).stdout
+        keep = ("Architecture", "Model name", "Vendor ID", "CPU(s)", "Thread(s) per core",
+                "Core(s) per socket", "Socket(s)", "CPU max MHz")
+        for line in out.splitlines():
+            k, _, v = line.partition(":")
+            if k.strip() in keep and k.strip() not in info:
+                info[k.strip()] = v.strip()
+    except Exception as e:  # lscpu missing: keep nproc only
+        info["lscpu"] = f"unavailable ({type(e).__name__})"
+    return info
+
+
+def oracle_for(w, args, omp=True):
     from oracle.oracle import Oracle
-    orc = Oracle(w, hessian_levels=args.hessian_levels, coarse_max=args.coarse_max, degree=args.degree,
-                 inner_tol=args.inner_tol)
-    u = np.random.default_rng(0).standard_normal(w.n_vertices)
+    return Oracle(w, hessian_levels=args.hessian_levels, coarse_max=args.coarse_max, degree=args.degree,
+                  inner_tol=args.inner_tol, omp=omp)
+
+
+def oracle_apply_rate(orc, budget_s, threads):
+    """Time the FP64 oracle's Hessian apply on `threads` host threads (setup untimed):
+    whole applies until the budget is spent.  Returns (applies, seconds, threads used)."""
+    from oracle import oracle as orc_mod
+    used = orc_mod.set_threads(threads)
+    u = np.random.default_rng(0).standard_normal(orc.n)
     n, t = 0, 0.0
-    while (applies is None and (t < budget_s or n == 0)) or (applies is not None and n < applies):
+    while t < budget_s or n == 0:
         t0 = time.perf_counter()
         orc.hessian(u)
         t += time.perf_counter() - t0
         n += 1
-    return n, t
+    return n, t, used
+
+
+def cpu_baseline(w, args):
+    """The oracle's Hessian apply on the same workload, on one host core and on
+    every host core (the -fopenmp build: row loops split over threads, dot
+    products sequential, results bit-identical)."""
+    orc = oracle_for(w, args, omp=True)
+    n1, t1, c1 = oracle_apply_rate(orc, args.cpu_budget, 1)
+    nall = os.cpu_count() or 1
+    n, t, c = oracle_apply_rate(orc, args.cpu_budget, nall)
+    return {"value": n / t, "unit": UNIT, "cores": c, "kind": "oracle",
+            "sample": f"{n} Hessian applies of the FP64 oracle on the same workload on {c} host threads "
+                      f"({t:.1f} s, setup untimed; each apply = 2 AMG-CG solves to the inner tolerance)",
+            "single_core": {"value": n1 / t1, "cores": c1, "sample": f"{n1} applies in {t1:.1f} s"},
+            "host": host_cpu()}
 
 
 def run_reference(args, rank, world):
     if rank != 0:
         return
     from oracle import oracle as orc_mod
-    from paper_2001_11533_gb300 import workloads
-    orc_mod.build()
+    orc_mod.build(omp=True)
     w, wname, _, _, _ = make_workload(args)
-    from oracle.oracle import Oracle
-    orc = Oracle(w, hessian_levels=args.hessian_levels, coarse_max=args.coarse_max, degree=args.degree)
+    orc = oracle_for(w, args, omp=True)
+    cores = orc_mod.set_threads(os.cpu_count() or 1)
     u = np.random.default_rng(0).standard_normal(w.n_vertices)
     for _ in range(args.warmup):
         orc.hessian(u)
@@ -419,8 +557,9 @@ def run_reference(args, rank, world):
             "data": "synthetic",
             "config": {"workload": wname, "m": w.n_interior, "n": w.n_vertices,
                        "beta": w.beta, "step": "one fine-level Hessian apply of the FP64 CPU oracle"},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"{args.steps} Hessian applies (2 AMG-CG solves to 1e-10 each)"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{args.steps} Hessian applies (2 AMG-CG solves to 1e-10 each) on "
+                                       f"{cores} host threads", "host": host_cpu()},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -508,6 +647,7 @@ def main():
     w, results, e2e = run_amgh(args, rank, world, local)
     wname, kdesc = workload_names(args)
     batch = None if args.no_batch else run_batch(args, rank, world, local)
+    cube = None if (args.no_cube or args.workload == "cube") else run_cube(args, rank, world, local)
     if rank != 0:
         return
     forms = list(results)
@@ -540,11 +680,10 @@ def main():
         line["speedup_mixed_vs_fp64"] = results["mixed"]["value"] / results["fp64"]["value"]
     if "refine" in results and "fp64" in results:
         line["speedup_refine_vs_fp64"] = results["refine"]["value"] / results["fp64"]["value"]
+    if cube is not None:
+        line["cube"] = cube
     if world == 1 and not args.no_cpu_baseline and args.workload == "lshape":
-        n, t = oracle_apply_rate(w, 15.0, args)
-        line["cpu_baseline"] = {"value": n / t, "unit": UNIT, "cores": 1, "kind": "oracle",
-                                "sample": f"{n} Hessian applies of the FP64 oracle on the same workload "
-                                          f"({t:.1f} s, setup untimed)"}
+        line["cpu_baseline"] = cpu_baseline(w, args)
     print(json.dumps(line), flush=True)
 
 

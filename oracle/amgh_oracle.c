@@ -52,6 +52,19 @@
 #define MAXL 32
 #define DENSE_MAX 4096
 
+/* Row loops of the solve phase may be split over threads when the file is
+ * compiled with -fopenmp (the multi-core CPU timing of the benchmark).  Each
+ * row is still computed by one thread in the same order and every dot
+ * product stays sequential, so the results are bit-identical to the plain
+ * sequential build used by the tests. */
+#ifdef _OPENMP
+#include <omp.h>
+/* the loop's trip count must be a variable named n */
+#define ORC_ROWS _Pragma("omp parallel for schedule(static) if(n > 16384)")
+#else
+#define ORC_ROWS
+#endif
+
 typedef struct {
     int rows, cols;
     int *rp, *ci;
@@ -144,7 +157,9 @@ static long csr_find(const csr_t *a, int r, int c)
 /* y = a x  (row by row, ascending columns) */
 static void spmv(const csr_t *a, const double *x, double *y)
 {
-    for (int i = 0; i < a->rows; i++) {
+    int n = a->rows;
+    ORC_ROWS
+    for (int i = 0; i < n; i++) {
         double s = 0.0;
         for (int k = a->rp[i]; k < a->rp[i + 1]; k++) s += a->v[k] * x[a->ci[k]];
         y[i] = s;
@@ -794,11 +809,14 @@ static void smooth(orc_t *o, int l, const double *b, double *x, int zero_init, d
     int n = A->rows;
     for (int s = 0; s < o->nsteps; s++) {
         if (s == 0 && zero_init) {
+            ORC_ROWS
             for (int i = 0; i < n; i++) r[i] = b[i];
         } else {
             spmv(A, x, r);
+            ORC_ROWS
             for (int i = 0; i < n; i++) r[i] = b[i] - r[i];
         }
+        ORC_ROWS
         for (int i = 0; i < n; i++) {
             double ri = r[i] / o->dl1[l][i];
             double prev = (s == 0) ? 0.0 : d[i];
@@ -830,10 +848,12 @@ static int vcycle(orc_t *o, int l, const double *b, double *x)
     if (!d || !r || !bc || !ec || !t) return ORC_OOM;
     smooth(o, l, b, x, 1, d, r);
     spmv(&o->A[l], x, r);
+    ORC_ROWS
     for (int i = 0; i < n; i++) r[i] = b[i] - r[i];
     spmv(&o->St[l], r, bc);
     int st = vcycle(o, l + 1, bc, ec);
     spmv(&o->S[l], ec, t);
+    ORC_ROWS
     for (int i = 0; i < n; i++) x[i] = x[i] + t[i];
     smooth(o, l, b, x, 0, d, r);
     free(d);
@@ -877,6 +897,7 @@ static int pcg(orc_t *o, int level, int n, apply_fn op, apply_fn prec, const dou
         double pq = dot(n, p, q);
         if (!(pq > 0.0)) { st = (pq == pq) ? ORC_INDEFINITE : ORC_NUMERIC; goto done; }
         double alpha = rz / pq;
+        ORC_ROWS
         for (int i = 0; i < n; i++) {
             x[i] = x[i] + alpha * p[i];
             r[i] = r[i] - alpha * q[i];
@@ -889,6 +910,7 @@ static int pcg(orc_t *o, int level, int n, apply_fn op, apply_fn prec, const dou
         if (!(rzn > 0.0)) { st = (rzn == rzn) ? ORC_INDEFINITE : ORC_NUMERIC; goto done; }
         double beta = rzn / rz;
         rz = rzn;
+        ORC_ROWS
         for (int i = 0; i < n; i++) p[i] = z[i] + beta * p[i];
     }
     if (k > maxit) { k = maxit; st = ORC_NOT_CONVERGED; }
@@ -916,7 +938,9 @@ static int op_Mu(orc_t *o, int l, const double *x, double *y)
 static int prec_Jmu(orc_t *o, int l, const double *x, double *y)
 {
     const csr_t *M = &o->Mu[l];
-    for (int i = 0; i < M->rows; i++) y[i] = x[i] / M->v[csr_find(M, i, i)];
+    int n = M->rows;
+    ORC_ROWS
+    for (int i = 0; i < n; i++) y[i] = x[i] / M->v[csr_find(M, i, i)];
     return ORC_OK;
 }
 
@@ -959,6 +983,7 @@ static int hessian(orc_t *o, int l, const double *v, double *hv)
     if ((st = state_solve(o, l, t2, p, tol))) goto done;
     spmv(&o->Myut[l], p, hv);
     spmv(&o->Mu[l], v, w);
+    ORC_ROWS
     for (int i = 0; i < n; i++) hv[i] = hv[i] + o->beta * w[i];
     o->happlies += (l == 0);
 done:
@@ -990,6 +1015,7 @@ static int mlas_R(orc_t *o, int j, const double *b, double *out)
     if ((st = mass_solve(o, j + 1, bc, wc))) goto done;
     spmv(&o->P[j], qc, ta);
     spmv(&o->P[j], wc, tb);
+    ORC_ROWS
     for (int i = 0; i < n; i++) out[i] = ta[i] + (w1[i] - tb[i]) / o->beta;
 done:
     free(bc);
@@ -1505,6 +1531,27 @@ int orc_solve(void *h, int precond, double tol, int maxit, double *u, double *y,
     }
     free(b);
     return st;
+}
+
+/* threads the row loops use (1 in the sequential build) */
+int orc_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+/* set the threads of the row loops (no effect in the sequential build) */
+int orc_set_threads(int t)
+{
+#ifdef _OPENMP
+    if (t > 0) omp_set_num_threads(t);
+#else
+    (void)t;
+#endif
+    return ORC_OK;
 }
 
 int orc_counters(void *h, long *inner, long *mass, long *happ)

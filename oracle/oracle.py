@@ -4,7 +4,9 @@ TEST INFRASTRUCTURE ONLY: the test-suite, the smoke check and the
 benchmark's CPU-baseline / reference leg are the only callers.  The oracle
 shares no code with the CUDA path; this module only compiles the C file with
 gcc (-O2 -ffp-contract=off, no fused multiply-add) and marshals numpy arrays
-through ctypes.
+through ctypes.  A second build with -fopenmp (omp=True) splits the
+solve-phase row loops over the host's cores for the benchmark's multi-core
+CPU timing; its results are bit-identical to the sequential build.
 """
 from __future__ import annotations
 
@@ -19,8 +21,9 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "amgh_oracle.c")
 _BUILD = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD, "libamgh_oracle.so")
+_LIB_OMP = os.path.join(_BUILD, "libamgh_oracle_omp.so")
 _lock = threading.Lock()
-_lib = None
+_libs = {}
 
 OK, INVALID, NOT_SETUP, OOM, NOT_CONVERGED, INDEFINITE, NUMERIC = 0, -1, -2, -4, -5, -6, -7
 MATRIX = {"A": 0, "My": 1, "Myu": 2, "S": 3, "KN": 4, "Mu": 5, "P": 6, "Kfull": 7, "Mfull": 8}
@@ -32,25 +35,28 @@ class OracleError(RuntimeError):
         self.code = code
 
 
-def build(force: bool = False) -> str:
-    """Compile the oracle into oracle/_build (idempotent)."""
+def build(force: bool = False, omp: bool = False) -> str:
+    """Compile the oracle into oracle/_build (idempotent); omp=True: the
+    -fopenmp build of the same file."""
     os.makedirs(_BUILD, exist_ok=True)
-    if (not force and os.path.exists(_LIB_PATH)
-            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
-        return _LIB_PATH
-    tmp = _LIB_PATH + f".{os.getpid()}.tmp"
+    path = _LIB_OMP if omp else _LIB_PATH
+    if (not force and os.path.exists(path)
+            and os.path.getmtime(path) >= os.path.getmtime(_SRC)):
+        return path
+    tmp = path + f".{os.getpid()}.tmp"
     cmd = ["gcc", "-O2", "-std=c99", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
            "-o", tmp, _SRC, "-lm"]
+    if omp:
+        cmd.insert(1, "-fopenmp")
     subprocess.run(cmd, check=True)
-    os.replace(tmp, _LIB_PATH)
-    return _LIB_PATH
+    os.replace(tmp, path)
+    return path
 
 
-def lib():
-    global _lib
+def lib(omp: bool = False):
     with _lock:
-        if _lib is None:
-            L = C.CDLL(build())
+        if omp not in _libs:
+            L = C.CDLL(build(omp=omp))
             P, I, L64, D = C.c_void_p, C.c_int, C.c_long, C.c_double
             sig = {
                 "orc_create": [I, L64, P, L64, P, P, P, D, P, P],
@@ -83,8 +89,23 @@ def lib():
             L.orc_destroy.restype = None
             L.orc_priority.argtypes = [C.c_uint64]
             L.orc_priority.restype = C.c_uint64
-            _lib = L
-    return _lib
+            L.orc_threads.argtypes = []
+            L.orc_threads.restype = C.c_int
+            L.orc_set_threads.argtypes = [C.c_int]
+            L.orc_set_threads.restype = C.c_int
+            _libs[omp] = L
+    return _libs[omp]
+
+
+def threads(omp: bool = True) -> int:
+    """Threads the row loops of that build use."""
+    return int(lib(omp).orc_threads())
+
+
+def set_threads(t: int) -> int:
+    """Threads of the -fopenmp build's row loops; returns the number in effect."""
+    lib(True).orc_set_threads(int(t))
+    return threads(True)
 
 
 def _p(a):
@@ -119,9 +140,9 @@ class Oracle:
 
     def __init__(self, w, max_levels=25, hessian_levels=0, theta=0.08, coarse_max=256,
                  smoother=1, degree=2, smooth_prolongator=1, inner_tol=1e-10, mass_tol=1e-10,
-                 inner_maxit=1000, mass_maxit=1000, setup=True):
+                 inner_maxit=1000, mass_maxit=1000, setup=True, omp=False):
         self.w = w
-        L = lib()
+        self._L = L = lib(omp)
         self._coords = np.ascontiguousarray(w.coords, dtype=np.float64)
         self._elems = np.ascontiguousarray(w.elements, dtype=np.int32)
         self._dir = np.ascontiguousarray(w.dirichlet, dtype=np.uint8)
@@ -143,7 +164,7 @@ class Oracle:
     def __del__(self):
         try:
             if getattr(self, "h", None):
-                lib().orc_destroy(self.h)
+                self._L.orc_destroy(self.h)
                 self.h = None
         except Exception:
             pass
@@ -151,35 +172,35 @@ class Oracle:
     # -- setup / queries
     def setup(self, max_levels=25, hessian_levels=0, theta=0.08, coarse_max=256, smoother=1,
               degree=2, smooth_prolongator=1):
-        _check(lib().orc_setup(self.h, max_levels, hessian_levels, theta, coarse_max, smoother,
+        _check(self._L.orc_setup(self.h, max_levels, hessian_levels, theta, coarse_max, smoother,
                                degree, smooth_prolongator), "setup")
         self.set_tols(1e-10, 1e-10, 1000, 1000)
 
     def set_tols(self, inner_tol, mass_tol, inner_maxit=1000, mass_maxit=1000):
-        _check(lib().orc_set_tols(self.h, inner_tol, mass_tol, inner_maxit, mass_maxit), "tols")
+        _check(self._L.orc_set_tols(self.h, inner_tol, mass_tol, inner_maxit, mass_maxit), "tols")
 
     def set_precond_tol(self, pc_inner_tol):
         """Tolerance of the coarse-level state solves inside the preconditioner."""
-        _check(lib().orc_set_precond_tol(self.h, pc_inner_tol), "set_precond_tol")
+        _check(self._L.orc_set_precond_tol(self.h, pc_inner_tol), "set_precond_tol")
 
     def set_coarse_solve(self, mode, tol=1e-4, maxit=1000):
         """Coarsest Hessian level: 0 = dense Cholesky, 1 = plain CG to `tol`
         (Sec. 5.2).  Returns the coarse CG iterations since the last call."""
         it = C.c_long()
-        _check(lib().orc_set_coarse_solve(self.h, mode, float(tol), int(maxit), C.byref(it)),
+        _check(self._L.orc_set_coarse_solve(self.h, mode, float(tol), int(maxit), C.byref(it)),
                "set_coarse_solve")
         return it.value
 
     def set_yd(self, yd):
         self._yd = np.ascontiguousarray(yd, dtype=np.float64)
-        _check(lib().orc_set_yd(self.h, _p(self._yd)), "set_yd")
+        _check(self._L.orc_set_yd(self.h, _p(self._yd)), "set_yd")
 
     def sizes(self):
         m, n = C.c_long(), C.c_long()
         Ls, Lc, ell = C.c_int(), C.c_int(), C.c_int()
         ss = np.zeros(32, dtype=np.int64)
         cs = np.zeros(32, dtype=np.int64)
-        _check(lib().orc_sizes(self.h, C.byref(m), C.byref(n), C.byref(Ls), C.byref(Lc),
+        _check(self._L.orc_sizes(self.h, C.byref(m), C.byref(n), C.byref(Ls), C.byref(Lc),
                                C.byref(ell), _p(ss), _p(cs)), "sizes")
         return {"m": m.value, "n": n.value, "Ls": Ls.value, "Lc": Lc.value, "ell": ell.value,
                 "state": ss[:Ls.value].tolist(), "control": cs[:Lc.value].tolist()}
@@ -188,12 +209,12 @@ class Oracle:
         """CSR of a level matrix as (rowptr, col, val, shape)."""
         wid = MATRIX[which] if isinstance(which, str) else int(which)
         r, c, z = C.c_long(), C.c_long(), C.c_long()
-        _check(lib().orc_matrix_info(self.h, wid, level, C.byref(r), C.byref(c), C.byref(z)),
+        _check(self._L.orc_matrix_info(self.h, wid, level, C.byref(r), C.byref(c), C.byref(z)),
                f"matrix_info {which}@{level}")
         rp = np.empty(r.value + 1, dtype=np.int32)
         ci = np.empty(z.value, dtype=np.int32)
         v = np.empty(z.value, dtype=np.float64)
-        _check(lib().orc_matrix_copy(self.h, wid, level, _p(rp), _p(ci), _p(v)), "matrix_copy")
+        _check(self._L.orc_matrix_copy(self.h, wid, level, _p(rp), _p(ci), _p(v)), "matrix_copy")
         return rp, ci, v, (r.value, c.value)
 
     def scipy(self, which, level=0):
@@ -205,60 +226,60 @@ class Oracle:
         rows = self.sizes()["state" if hier == 0 else "control"][level]
         agg = np.empty(rows, dtype=np.int32)
         nagg = C.c_int()
-        _check(lib().orc_aggregates(self.h, hier, level, _p(agg), C.byref(nagg)), "aggregates")
+        _check(self._L.orc_aggregates(self.h, hier, level, _p(agg), C.byref(nagg)), "aggregates")
         return agg, nagg.value
 
     # -- operators
     def vcycle(self, level, b):
         b = np.ascontiguousarray(b, dtype=np.float64)
         x = np.zeros_like(b)
-        _check(lib().orc_vcycle(self.h, level, _p(b), _p(x)), "vcycle")
+        _check(self._L.orc_vcycle(self.h, level, _p(b), _p(x)), "vcycle")
         return x
 
     def smooth(self, level, b, x0=None):
         """The level's polynomial smoother alone for A_l x = b, from x0 (None: from zero)."""
         b = np.ascontiguousarray(b, dtype=np.float64)
         x = np.zeros_like(b) if x0 is None else np.array(x0, dtype=np.float64, copy=True)
-        _check(lib().orc_smooth(self.h, level, _p(b), _p(x), 1 if x0 is None else 0), "smooth")
+        _check(self._L.orc_smooth(self.h, level, _p(b), _p(x), 1 if x0 is None else 0), "smooth")
         return x
 
     def state_solve(self, f, level=0, tol=1e-10):
         f = np.ascontiguousarray(f, dtype=np.float64)
         y = np.zeros_like(f)
         it = C.c_long()
-        _check(lib().orc_state_solve(self.h, level, tol, _p(f), _p(y), C.byref(it)), "state_solve")
+        _check(self._L.orc_state_solve(self.h, level, tol, _p(f), _p(y), C.byref(it)), "state_solve")
         return y, it.value
 
     def mass_solve(self, b, level=0):
         b = np.ascontiguousarray(b, dtype=np.float64)
         x = np.zeros_like(b)
         it = C.c_long()
-        _check(lib().orc_mass_solve(self.h, level, _p(b), _p(x), C.byref(it)), "mass_solve")
+        _check(self._L.orc_mass_solve(self.h, level, _p(b), _p(x), C.byref(it)), "mass_solve")
         return x, it.value
 
     def hessian(self, u, level=0):
         u = np.ascontiguousarray(u, dtype=np.float64)
         hu = np.zeros_like(u)
-        _check(lib().orc_hessian(self.h, level, _p(u), _p(hu)), "hessian")
+        _check(self._L.orc_hessian(self.h, level, _p(u), _p(hu)), "hessian")
         return hu
 
     def precond(self, r, level=0):
         """Q_level r (Algorithm MLAS, M_u-scaled)."""
         r = np.ascontiguousarray(r, dtype=np.float64)
         z = np.zeros_like(r)
-        _check(lib().orc_mlas(self.h, 0, level, _p(r), _p(z)), "mlas Q")
+        _check(self._L.orc_mlas(self.h, 0, level, _p(r), _p(z)), "mlas Q")
         return z
 
     def R(self, r, level=0):
         """R_level r, the M_u-scaled two-grid operator T_j^-1 M_{u,j}^-1."""
         r = np.ascontiguousarray(r, dtype=np.float64)
         z = np.zeros_like(r)
-        _check(lib().orc_mlas(self.h, 1, level, _p(r), _p(z)), "mlas R")
+        _check(self._L.orc_mlas(self.h, 1, level, _p(r), _p(z)), "mlas R")
         return z
 
     def rhs(self):
         b = np.zeros(self.n)
-        _check(lib().orc_rhs(self.h, _p(b)), "rhs")
+        _check(self._L.orc_rhs(self.h, _p(b)), "rhs")
         return b
 
     def objective(self, u, grad=True):
@@ -266,19 +287,19 @@ class Oracle:
         y = np.zeros(self.m)
         J = C.c_double()
         g = np.zeros(self.n) if grad else None
-        _check(lib().orc_objective(self.h, _p(u), _p(y), C.byref(J), _p(g)), "objective")
+        _check(self._L.orc_objective(self.h, _p(u), _p(y), C.byref(J), _p(g)), "objective")
         return J.value, y, g
 
     def solve(self, precond=1, tol=1e-8, maxit=500):
         u = np.zeros(self.n)
         y = np.zeros(self.m)
         it, rel, happ = C.c_int(), C.c_double(), C.c_long()
-        st = lib().orc_solve(self.h, precond, tol, maxit, _p(u), _p(y), C.byref(it),
+        st = self._L.orc_solve(self.h, precond, tol, maxit, _p(u), _p(y), C.byref(it),
                              C.byref(rel), C.byref(happ))
         _check(st, "solve")
         return u, y, {"outer_iters": it.value, "relres": rel.value, "hessian_applies": happ.value}
 
     def counters(self):
         a, b, c = C.c_long(), C.c_long(), C.c_long()
-        lib().orc_counters(self.h, C.byref(a), C.byref(b), C.byref(c))
+        self._L.orc_counters(self.h, C.byref(a), C.byref(b), C.byref(c))
         return {"inner_iters": a.value, "mass_iters": b.value, "hessian_applies": c.value}

@@ -36,3 +36,18 @@ def test_reference_other_ranks_exit_quietly():
                           "--gpus", "2"], cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
     assert out.returncode == 0, out.stderr[-2000:]
     assert not [l for l in out.stdout.splitlines() if l.startswith("{")]
+
+
+def test_cpu_baseline_one_core_and_all_cores():
+    """The CPU baseline times the oracle on one host core and on every core, and
+    records the host CPU as lscpu reports it."""
+    import argparse
+    sys.path.insert(0, ROOT)
+    import bench
+    from paper_2001_11533_gb300 import workloads as W
+    args = argparse.Namespace(hessian_levels=0, coarse_max=1000, degree=2, inner_tol=1e-10, cpu_budget=0.2)
+    cb = bench.cpu_baseline(W.lshape_checkerboard(N=33), args)
+    assert cb["kind"] == "oracle" and cb["value"] > 0 and cb["unit"] == bench.UNIT
+    assert cb["cores"] == (os.cpu_count() or 1)
+    assert cb["single_core"]["cores"] == 1 and cb["single_core"]["value"] > 0
+    assert cb["host"]["nproc"] == os.cpu_count()

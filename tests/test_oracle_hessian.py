@@ -197,3 +197,18 @@ def test_preconditioned_fewer_and_not_growing():
         assert all(p < q for p, q in zip(pre, non)), (beta, pre, non)
         assert 1.5 * pre[-1] <= non[-1], (beta, pre, non)
         assert max(pre[1:]) <= pre[0], (beta, pre)
+
+
+def test_openmp_build_is_bit_identical():
+    """The -fopenmp build (multi-core CPU timing) splits only row loops, so its
+    Hessian apply and preconditioner equal the sequential build's bit for bit,
+    on a mesh large enough for the threaded branch to run."""
+    from oracle import oracle as orc_mod
+    w = W.unit_square(161, beta=1e-3, jitter=0.2, cfg=151)
+    u = np.random.default_rng(7).standard_normal(w.n_vertices)
+    res = []
+    for omp in (False, True):
+        o = Oracle(w, coarse_max=200, omp=omp)
+        res.append((o.hessian(u), o.precond(u)))
+    assert np.array_equal(res[0][0], res[1][0]) and np.array_equal(res[0][1], res[1][1])
+    assert orc_mod.threads(False) == 1

@@ -31,3 +31,19 @@ def test_seeded_reproducible():
     batch = W.batch_squares(sizes=(9, 17), per_size=2, rhs=3)
     assert len(batch) == 4 and batch[0].y_d.shape == (3, 81)
     assert all(1e-6 <= p.beta <= 1e-2 for p in batch)
+
+
+def test_separable_bumps_match_direct_sum():
+    N = 9
+    coords, _ = W.grid3d_kuhn(N)
+    cen, amps = W._bump_params(W._rng(4, 9), 5, 3, lambda p: True)
+    a = W.gaussian_bumps(coords, cen, amps, 0.2)
+    b = W.gaussian_bumps_grid3(N, cen, amps, 0.2)
+    assert np.allclose(a, b, rtol=1e-13, atol=1e-15)
+
+
+def test_cube_slabs_kappa_from_centroid_height():
+    w = W.cube_slabs(N=9)
+    z = W.centroids(w.coords, w.elements)[:, 2]
+    bnd = np.sort(np.arange(1, 10) / 10.0 + W._rng(4, 8).uniform(-0.02, 0.02, size=9))
+    assert np.array_equal(w.kappa, np.where(np.searchsorted(bnd, z) % 2 == 0, 1.0, 1e6))
