@@ -74,7 +74,7 @@ def test_central_differences_full_cube_129():
     g = u.grad.detach()
     D = W.random_vectors(n, 20, 2, 5)
     h = 1e-6
-    worst = 0.0
+    rel_err, j_err = [], []
     for d in D:
         d = _cuda(d / np.linalg.norm(d))
         with torch.no_grad():
@@ -82,6 +82,11 @@ def test_central_differences_full_cube_129():
             jm = reduced_cost(u.detach() - h * d, prob).item()
         fd = (jp - jm) / (2 * h)
         gd = float((g * d).sum())
-        bound = 1e-6 * abs(gd) + 1e-12 * abs(J.item()) / h
-        worst = max(worst, abs(fd - gd) / bound)
-    assert worst <= 1.0, worst
+        rel_err.append(abs(fd - gd) / abs(gd))
+        # J is quadratic: fd - g.d is the error of the two values of J (rounding
+        # and the inner solves' tolerance, 1e-13 relative) divided by 2h
+        j_err.append(abs(fd - gd) * 2 * h / abs(J.item()))
+    print(f"central differences, 20 directions: worst |fd - g.d|/|g.d| = {max(rel_err):.3e}, "
+          f"worst |fd - g.d| 2h/|J| = {max(j_err):.3e}, |J| = {J.item():.6e}")
+    assert max(j_err) <= 1e-12, (max(rel_err), max(j_err))
+    assert max(rel_err) <= 1e-3, (max(rel_err), max(j_err))

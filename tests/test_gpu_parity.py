@@ -225,17 +225,22 @@ def test_loose_preconditioner_tolerance():
     assert rel(z, zo) <= 1e-6   # both sides solve to 1e-8 inside Q_0
 
 
-def test_objective_and_gradient():
-    w, prob, orc = pair("lshape65")
-    prob.set_solve_opts(**TIGHT)
+@pytest.mark.parametrize("precision", [0, 2])
+def test_objective_and_gradient(precision):
+    """J, y and the adjoint gradient against the oracle: FP64 path at inner 1e-13
+    (J to 1e-11, y and grad J to 1e-10); mixed path (double-float CG, FP32
+    V-cycles) at inner 1e-12 (J to 1e-10, y and grad J to 1e-9)."""
+    w, prob, orc = pair("lshape65", precision=precision)
+    tight = precision == 0
+    prob.set_solve_opts(**(TIGHT if tight else dict(inner_tol=1e-12, mass_tol=1e-12)))
     orc.set_tols(1e-13, 1e-13)
     u = np.random.default_rng(18).standard_normal(prob.sizes["n"])
     y, J = prob.state_solve(cuda(u))
     g = prob.gradient(cuda(u), y)
     Jo, yo, go = orc.objective(u)
-    assert abs(J - Jo) <= 1e-11 * abs(Jo)
-    assert rel(host(y), yo) <= 1e-10
-    assert rel(host(g), go) <= 1e-10
+    assert abs(J - Jo) <= (1e-11 if tight else 1e-10) * abs(Jo)
+    assert rel(host(y), yo) <= (1e-10 if tight else 1e-9)
+    assert rel(host(g), go) <= (1e-10 if tight else 1e-9)
 
 
 def test_unpreconditioned_and_two_grid():
@@ -397,20 +402,66 @@ def test_full_size_lshape_1025():
 
 
 @pytest.mark.slow
+def test_full_size_lshape_1025_control_parity():
+    """The bench workload at full size (1025^2 L-shape, 784,385 states), with the
+    bench's hierarchy (coarsening to <= 1000 rows, 4 levels): the converged
+    control u and state y of the FP64 path (outer 1e-12, inner 1e-13 on both
+    sides) within 1e-10 of the oracle's, and of the mixed path (double-float CG,
+    FP32 V-cycles; outer 1e-11, inner 1e-12) within 1e-8; then J and grad J of
+    the mixed path at the oracle's optimum; then the mixed path as the
+    benchmark runs it (outer 1e-8, inner 1e-10, preconditioner 1e-8), whose
+    error against the converged control is bounded by what a relative residual
+    of 1e-8 allows and is printed.  The oracle runs its -fopenmp build (row
+    loops on every host core, results bit-identical to the sequential build)."""
+    import os
+    from oracle import oracle as orc_mod
+    from paper_2001_11533_gb300 import amgh
+    w = W.lshape_checkerboard()
+    orc_mod.set_threads(os.cpu_count() or 1)
+    orc = Oracle(w, coarse_max=1000, inner_tol=1e-13, mass_tol=1e-13, omp=True)
+    uo, yo, io = orc.solve(precond=1, tol=1e-12)
+    Jo, _, go = orc.objective(uo)
+    errs = {}
+    for prec, outer, inner, lim in ((0, 1e-12, 1e-13, 1e-10), (2, 1e-11, 1e-12, 1e-8)):
+        p = amgh.Problem.from_workload(w).amg_setup(precision=prec, coarse_max=1000)
+        assert p.sizes["state"] == orc.sizes()["state"]
+        u, y, info = p.solve(tol=outer, inner_tol=inner, mass_tol=inner, precond_tol=inner)
+        errs[prec] = (rel(host(u), uo), rel(host(y), yo))
+        assert errs[prec][0] <= lim and errs[prec][1] <= lim, (prec, errs[prec], info, io)
+        if prec == 2:
+            yg, J = p.state_solve(cuda(uo))
+            g = p.gradient(cuda(uo), yg)
+            errs["J"], errs["grad"] = abs(J - Jo) / abs(Jo), rel(host(g), go)
+            # at the optimum grad J = H u - b is the outer residual: compare to ||b||
+            b = orc.rhs()
+            assert errs["J"] <= 1e-10 and np.linalg.norm(host(g) - go) <= 1e-9 * np.linalg.norm(b), errs
+            u8, _, info8 = p.solve(tol=1e-8, inner_tol=1e-10, mass_tol=1e-8, precond_tol=1e-8, want_y=False)
+            errs["bench"] = rel(host(u8), uo)
+            assert info8["final_relres"] <= 1.5e-8
+            assert errs["bench"] <= 1e-6, errs
+        p.close()
+    print("full-size control parity (relative 2-norm):", errs)
+    orc_mod.set_threads(1)
+
+
+@pytest.mark.slow
 def test_full_size_cube257_slabs():
     """The large 3D case (257^3 Kuhn cube, 16.6M states, kappa in {1, 1e6} on
-    10 slabs, beta = 1e-6) at full size, checked by properties that hold at any
-    size: at least five AMG levels, both precision forms reach 1e-8 on the true
-    residual and agree with each other, and H is symmetric."""
+    10 slabs, beta = 1e-6) at full size with the multilevel preconditioner over
+    at least six AMG levels (coarsening to <= 16 rows), checked by properties
+    that hold at any size (an oracle run at this size is beyond the test's
+    budget): both precision forms reach their outer tolerance 1e-10 on the true
+    residual and agree with each other to 1e-8, and H is symmetric."""
     from paper_2001_11533_gb300 import amgh
     w = W.cube_slabs(N=257)
     res = {}
     for prec in (2, 0):
-        p = amgh.Problem.from_workload(w).amg_setup(precision=prec, coarse_solve=2, coarse_max=1000)
-        assert p.sizes["Ls"] >= 5
-        u, _, info = p.solve(tol=1e-8, precond_tol=1e-8, mass_tol=1e-8, level_fallback=1, want_y=False)
-        assert info["final_relres"] <= 1.5e-8
-        res[prec] = host(u)
+        p = amgh.Problem.from_workload(w).amg_setup(precision=prec, coarse_solve=2, coarse_max=16)
+        assert p.sizes["Ls"] >= 6 and p.sizes["Lc"] >= 6, p.sizes
+        u, _, info = p.solve(tol=1e-10, inner_tol=1e-12, precond_tol=1e-8, mass_tol=1e-8, level_fallback=1,
+                             want_y=False)
+        assert info["final_relres"] <= 1.5e-10, info
+        res[prec] = (host(u), info)
         if prec == 0:
             rng = np.random.default_rng(23)
             a, b = rng.standard_normal((2, w.n_vertices))
@@ -418,4 +469,7 @@ def test_full_size_cube257_slabs():
             ha, hb = host(p.hessian_apply(cuda(a))), host(p.hessian_apply(cuda(b)))
             assert abs(a @ hb - b @ ha) <= 1e-8 * np.linalg.norm(a) * np.linalg.norm(hb)
         p.close()
-    assert rel(res[2], res[0]) <= 1e-6
+    d = rel(res[2][0], res[0][0])
+    print(f"cube257: mixed vs FP64 controls differ by {d:.3e}; levels used "
+          f"{res[2][1]['hessian_levels']} / {res[0][1]['hessian_levels']}")
+    assert d <= 1e-8
