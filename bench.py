@@ -218,7 +218,7 @@ def run_amgh(args, rank, world, local):
             u, y, info = prob.solve_host(**tols)
         else:
             u, y, info = prob.solve(**tols)
-        ks = prob.kernel_stats() if timing else None
+        ks = {"chebl0": prob.kernel_stats(), "classes": prob.kernel_class_stats()} if timing else None
         sizes = prob.sizes
         prob.close()
         return info, ks, sizes
@@ -234,6 +234,7 @@ def run_amgh(args, rank, world, local):
         torch.cuda.synchronize()
         times, happ, infos = [], 0, []
         kstats = {"launches": 0, "ms": 0.0, "bytes": 0.0}
+        classes = {}
         launches0 = amgh.launch_count()
         with ClockSampler(local) as clk:
             for k in range(args.steps):
@@ -255,7 +256,11 @@ def run_amgh(args, rank, world, local):
             flush.zero_()
             _, ks, _ = step(precision, timing=True)
             for key in kstats:
-                kstats[key] += ks[key]
+                kstats[key] += ks["chebl0"][key]
+            for name, c in ks["classes"].items():
+                acc = classes.setdefault(name, {"launches": 0, "ms": 0.0, "bytes": 0.0})
+                for key in acc:
+                    acc[key] += c[key]
         t_total = sum(times) / 1000.0
         # max over ranks of the timed total, sum of work
         (t_total,), (happ_all,) = replicas.combine([t_total], [happ], device="cuda")
@@ -271,6 +276,10 @@ def run_amgh(args, rank, world, local):
             "refinements": infos[-1]["refinements"],
             "gpu_launches": launches,
             "kstats": kstats,
+            "kernel_classes": classes,
+            # algorithmic bytes of the solve phase (every kernel of the outer CG,
+            # its Hessian applies and the preconditioner), from the last timed step
+            "solve_phase": solve_phase(infos[-1]),
             "clocks": clk.summary(),
             "levels": {"state": sizes["state"], "control": sizes["control"], "ell": sizes["ell"]},
         }
@@ -393,7 +402,7 @@ def run_cube(args, rank, world, local):
         if timing:
             prob.kernel_timing(True)
         u, y, info = prob.solve(want_y=False, **tols)
-        ks = prob.kernel_stats() if timing else None
+        ks = {"chebl0": prob.kernel_stats(), "classes": prob.kernel_class_stats()} if timing else None
         sizes = prob.sizes
         prob.close()
         return info, ks, sizes
@@ -434,9 +443,11 @@ def run_cube(args, rank, world, local):
         if form == "mixed":
             flush.zero_()
             _, ks, _ = step(precision, timing=True)
-            res["roofline"] = roofline_from({"kstats": ks}, args, kernel_note="level-0 Chebyshev smoother "
-                                            "step on the 3D uniform-width SELL-32 matrix (int32 columns)",
+            res["roofline"] = roofline_from({"kstats": ks["chebl0"]}, args, kernel_note="level-0 Chebyshev "
+                                            "smoother step on the 3D uniform-width SELL-32 matrix (int32 columns)",
                                             traffic=None)
+            res["kernels"] = kernel_table(ks["classes"])
+        res["solve_phase"] = solve_phase(last)
         out[form] = res
     out["speedup_mixed_vs_fp64"] = out["fp64"]["time_to_1e-8_s"] / out["mixed"]["time_to_1e-8_s"]
     del dev
@@ -460,6 +471,46 @@ def captured_traffic(args):
         return traffic if hashlib.sha256(src).hexdigest() == want else None
     except Exception:
         return None
+
+
+def hbm_peak():
+    peaks = measured_peaks()
+    if peaks and peaks.get("hbm_gbs"):
+        return float(peaks["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def solve_phase(info):
+    """Bytes per Hessian apply and the HBM fraction of the whole solve phase:
+    the algorithmic bytes of every kernel the solve ran over its host-clock
+    duration (outer CG, every Hessian apply and preconditioner application)."""
+    peak, src = hbm_peak()
+    b, t, happ = info.get("alg_bytes", 0.0), info["t_solve_s"], max(info["hessian_applies"], 1)
+    if not b or t <= 0:
+        return None
+    return {"alg_bytes": b, "bytes_per_hessian_apply": b / happ, "solve_s": t,
+            "achieved_GBs": round(b / t / 1e9, 1), "frac": round(b / t / 1e9 / peak, 4),
+            "peak_GBs": peak, "peak_source": src,
+            "note": "solve-phase bytes include preconditioner work and coarse levels that live in L2"}
+
+
+def kernel_table(classes):
+    """Per kernel class from the instrumented pass: launches, mean duration, achieved
+    GB/s on algorithmic bytes, fraction of the measured HBM copy peak, and share of
+    the timed kernel time.  Classes without '_l0' work on coarse levels whose
+    operands fit in the 129 MB L2: their bytes/s is labelled L2-resident."""
+    peak, _ = hbm_peak()
+    total = sum(c["ms"] for c in classes.values()) or 1.0
+    out = {}
+    for name, c in sorted(classes.items(), key=lambda kv: -kv[1]["ms"]):
+        if c["launches"] == 0 or c["ms"] <= 0:
+            continue
+        gbs = c["bytes"] / (c["ms"] / 1000.0) / 1e9
+        out[name] = {"launches": c["launches"], "avg_us": round(1000.0 * c["ms"] / c["launches"], 2),
+                     "share": round(c["ms"] / total, 4), "achieved_GBs": round(gbs, 1),
+                     "frac_of_hbm": round(gbs / peak, 4),
+                     "residency": "hbm" if name.endswith("_l0") else "l2-resident"}
+    return out
 
 
 def roofline_from(res, args, kernel_note=None, traffic="captured"):
@@ -671,8 +722,11 @@ def main():
         "gpu_launches": head["gpu_launches"],
         "clocks": head["clocks"],
         "roofline": roofline_from(head, args),
+        "kernels": kernel_table(head["kernel_classes"]),
+        "solve_phase": head["solve_phase"],
         "e2e": e2e,
-        "forms": {f: {k: v for k, v in r.items() if k not in ("kstats", "clocks")} for f, r in results.items()},
+        "forms": {f: {k: (kernel_table(v) if k == "kernel_classes" else v) for k, v in r.items()
+                      if k not in ("kstats", "clocks")} for f, r in results.items()},
     }
     if batch is not None:
         line["batch"] = batch

@@ -166,6 +166,10 @@ typedef struct {
     int hessian_levels;      /* levels l of the preconditioner at the end */
     int fallbacks;           /* levels dropped by level_fallback */
     int64_t coarse_iters;    /* coarsest-level CG iterations (coarse_solve = 1) */
+    double alg_bytes;        /* algorithmic (compulsory) bytes of every kernel the
+                                single-column solve phase ran, from sizes: matrix
+                                entries and indices, gathered and streamed vectors;
+                                the block solver does not count (0) */
 } amgh_solve_info;
 
 /* Defaults: max_levels 25, hessian_levels 0, theta 0.08, coarse_max 256,
@@ -343,14 +347,23 @@ int amgh_get_level_counters(const amgh_problem *p, int64_t *inner_host, int64_t 
 int amgh_reset_counters(amgh_problem *p);
 
 /* Kernel timing for roofline reporting: when enabled, CG iterations are
- * launched kernel by kernel instead of as CUDA graphs, and every launch of the
- * level-0 Chebyshev smoother step (SpMV fused with the smoother update) is
- * bracketed by CUDA events on the problem's stream.  amgh_kernel_stats
- * returns the number of timed launches, their summed duration in ms, and
- * their summed algorithmic bytes (nnz*(v+4) + 4*(rows+1) + v*(rows+cols) +
- * 4*v*rows per launch, v = value bytes). */
+ * launched kernel by kernel (one iteration per host check) instead of as CUDA
+ * graphs, and every solve-phase launch of the single-column path is bracketed
+ * by CUDA events on the problem's stream and filed under its kernel class
+ * (0 .. AMGH_KCLASSES-1; the launches the device skips, the V-cycle of a CG
+ * iteration that converged, are not filed).  amgh_kernel_stats returns class
+ * 0, the level-0 Chebyshev smoother step (SpMV fused with the smoother
+ * update); amgh_kernel_class_stats any class, with its name.  Each returns
+ * the number of timed launches, their summed duration in ms, and their
+ * summed algorithmic bytes (for a sparse product nnz*(v+i) + v*(rows+cols),
+ * v = value bytes, i = index bytes, plus 4*(rows+1) for CSR row pointers;
+ * vectors read and written once each).  Enabling or disabling clears them.
+ * Errors: INVALID_ARG for a class out of range. */
+#define AMGH_KCLASSES 15
 int amgh_kernel_timing(amgh_problem *p, int enable);
 int amgh_kernel_stats(amgh_problem *p, int64_t *launches, double *ms, double *bytes);
+int amgh_kernel_class_stats(amgh_problem *p, int cls, int64_t *launches, double *ms, double *bytes,
+                            const char **name);
 
 /* Test hook for the bounded waits (no counterpart in the paper; process-wide,
  * not for production use).
@@ -366,8 +379,12 @@ int amgh_kernel_stats(amgh_problem *p, int64_t *launches, double *ms, double *by
  *                     loop may take before amgh_amg_setup returns
  *                     AMGH_ERR_TIMEOUT (-1: the default, n + 1 rounds, which
  *                     always suffice).
+ *   prol_row_cap      aggregates a row of the smoothed prolongator may reach
+ *                     before its construction moves from the per-thread
+ *                     register path to the one-block-per-row path for long
+ *                     rows (-1: the default, 256); results are identical.
  * Errors: INVALID_ARG for values below -1, CUDA. */
-int amgh_debug_limits(int bulk_first_polls, int mis_round_cap);
+int amgh_debug_limits(int bulk_first_polls, int mis_round_cap, int prol_row_cap);
 
 /* Batched solves of many independent problems (the batching pattern: many
  * desired states, many meshes of uneven size).  Every (problem, desired

@@ -51,13 +51,15 @@ class amgh_solve_info(C.Structure):
     _fields_ = [("status", C.c_int), ("outer_iters", C.c_int), ("hessian_applies", C.c_int64),
                 ("inner_iters", C.c_int64), ("mass_iters", C.c_int64), ("refinements", C.c_int64),
                 ("final_relres", C.c_double), ("t_setup_s", C.c_double), ("t_solve_s", C.c_double),
-                ("hessian_levels", C.c_int), ("fallbacks", C.c_int), ("coarse_iters", C.c_int64)]
+                ("hessian_levels", C.c_int), ("fallbacks", C.c_int), ("coarse_iters", C.c_int64),
+                ("alg_bytes", C.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 _P, _I, _I64, _D = C.c_void_p, C.c_int, C.c_int64, C.c_double
+KCLASSES = 15  # AMGH_KCLASSES
 _SIGS = {
     "amgh_amg_opts_default": ([_P], None),
     "amgh_solve_opts_default": ([_P], None),
@@ -89,7 +91,8 @@ _SIGS = {
     "amgh_get_level_counters": ([_P, _P, _P], _I),
     "amgh_kernel_timing": ([_P, _I], _I),
     "amgh_kernel_stats": ([_P, _P, _P, _P], _I),
-    "amgh_debug_limits": ([_I, _I], _I),
+    "amgh_kernel_class_stats": ([_P, _I, _P, _P, _P, _P], _I),
+    "amgh_debug_limits": ([_I, _I, _I], _I),
     "amgh_launch_count": ([], _I64),
     "amgh_aggregate_noalloc": ([_I, _P, _P, _P, _D, _P, _P, _P], _I),
     "amgh_batch_create": ([_P, _I, _P], _I),
@@ -128,8 +131,10 @@ def lib():
 
 def check(code: int, what: str):
     if code != OK:
-        if code == -3:  # CUDA: say which call failed and where
-            what = f"{what} [{lib().amgh_last_error().decode()}]"
+        if code in (-1, -3):  # INVALID_ARG / CUDA: say what failed (and where)
+            msg = lib().amgh_last_error().decode()
+            if msg:
+                what = f"{what} [{msg}]"
         raise AmghError(code, what)
 
 
@@ -142,9 +147,11 @@ def _ptr(t):
     return C.c_void_p(t.data_ptr())
 
 
-def debug_limits(bulk_first_polls: int = -1, mis_round_cap: int = -1):
-    """amgh_debug_limits: lower the bounded waits' limits for tests (-1 = default)."""
-    check(lib().amgh_debug_limits(int(bulk_first_polls), int(mis_round_cap)), "amgh_debug_limits")
+def debug_limits(bulk_first_polls: int = -1, mis_round_cap: int = -1, prol_row_cap: int = -1):
+    """amgh_debug_limits: lower the bounded waits' limits and the prolongator's
+    register row capacity for tests (-1 = default)."""
+    check(lib().amgh_debug_limits(int(bulk_first_polls), int(mis_round_cap), int(prol_row_cap)),
+          "amgh_debug_limits")
 
 
 def launch_count() -> int:
@@ -436,6 +443,16 @@ class Problem:
         n, ms, b = C.c_int64(), C.c_double(), C.c_double()
         check(lib().amgh_kernel_stats(self.h, C.byref(n), C.byref(ms), C.byref(b)), "amgh_kernel_stats")
         return {"launches": n.value, "ms": ms.value, "bytes": b.value}
+
+    def kernel_class_stats(self):
+        """{class name: {launches, ms, bytes}} for every kernel class (amgh_kernel_class_stats)."""
+        out = {}
+        for c in range(KCLASSES):
+            n, ms, b, name = C.c_int64(), C.c_double(), C.c_double(), C.c_char_p()
+            check(lib().amgh_kernel_class_stats(self.h, c, C.byref(n), C.byref(ms), C.byref(b), C.byref(name)),
+                  "amgh_kernel_class_stats")
+            out[name.value.decode()] = {"launches": n.value, "ms": ms.value, "bytes": b.value}
+        return out
 
 
 class Batch:

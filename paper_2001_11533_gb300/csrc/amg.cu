@@ -220,6 +220,10 @@ __global__ void k_phase3(int n, const int *__restrict__ fr, const int *__restric
 // cap on the MIS-2 rounds (0: n + 1); lowered only by amgh_debug_limits
 static int g_mis_round_cap = 0;
 void mis_set_round_cap(int cap) { g_mis_round_cap = cap > 0 ? cap : 0; }
+// aggregates a prolongator row may reach before k_prol hands it to
+// k_prol_long (MAXROW; lowered only by amgh_debug_limits to test that path)
+static int g_prol_rowcap = 0;
+void prol_set_row_cap(int cap) { g_prol_rowcap = cap > 0 && cap < MAXROW ? cap : 0; }
 
 int amg_aggregate(amgh_problem *p, const DevCsr &a, double theta2, int *agg, int *nagg_out)
 {
@@ -316,7 +320,8 @@ __global__ void k_rho(int n, const int *__restrict__ rp, const int *__restrict__
 // row i: columns {agg(j)}, values [agg(i)==J] - (omega/a_ii) * sum_{agg(j)=J} a_ij
 __global__ void k_prol(int n, const int *__restrict__ rp, const int *__restrict__ ci, const double *__restrict__ v,
                        const int *__restrict__ agg, double omega, const int *__restrict__ prp,
-                       int *__restrict__ cnt, int *__restrict__ pci, double *__restrict__ pv, int *__restrict__ bad)
+                       int *__restrict__ cnt, int *__restrict__ pci, double *__restrict__ pv, int *__restrict__ bad,
+                       int rowcap)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -341,9 +346,10 @@ __global__ void k_prol(int n, const int *__restrict__ rp, const int *__restrict_
             }
         }
         if (!found) {
-            if (c >= MAXROW) {
-                atomicOr(bad, 1);
-                if (!prp) cnt[i] = 0;
+            if (c >= rowcap) {
+                // more aggregates than the register list holds: k_prol_long
+                // takes the row (count pass: marked -1; fill pass: left to it)
+                if (!prp) cnt[i] = -1;
                 return;
             }
             for (int t = c; t > pos; t--) {
@@ -368,6 +374,72 @@ __global__ void k_prol(int n, const int *__restrict__ rp, const int *__restrict_
         pci[base + t] = cols[t];
         pv[base + t] = __dsub_rn(delta, __dmul_rn(wi, acc[t]));
     }
+}
+
+// Rows of k_prol that reach more than MAXROW aggregates, one block per row:
+// the row's (aggregate, entry) pairs are ranked in shared memory by aggregate
+// and then entry position (a stable sort), after which one thread sums each
+// aggregate's entries in entry order -- the order k_prol and the sequential
+// definition use -- so the values are identical.  Rows longer than
+// PROL_LONG_MAX entries raise `bad`.
+#define PROL_LONG_MAX 8192
+__global__ void __launch_bounds__(256)
+    k_prol_long(const int *__restrict__ rows, int nrows, const int *__restrict__ rp, const int *__restrict__ ci,
+                const double *__restrict__ v, const int *__restrict__ agg, double omega, const int *__restrict__ prp,
+                int *__restrict__ cnt, int *__restrict__ pci, double *__restrict__ pv, int *__restrict__ bad)
+{
+    extern __shared__ __align__(16) unsigned char pl_sm[];
+    if ((int)blockIdx.x >= nrows) return;
+    const int i = rows[blockIdx.x];
+    const int beg = rp[i], len = rp[i + 1] - beg;
+    if (len > PROL_LONG_MAX) {
+        if (threadIdx.x == 0) atomicOr(bad, 1);
+        return;
+    }
+    double *sval = (double *)pl_sm;                  // values in sorted order
+    int *key = (int *)(sval + PROL_LONG_MAX);         // aggregate of entry t
+    int *skey = key + PROL_LONG_MAX;                  // aggregates in sorted order
+    for (int t = threadIdx.x; t < len; t += blockDim.x) key[t] = agg[ci[beg + t]];
+    __syncthreads();
+    for (int t = threadIdx.x; t < len; t += blockDim.x) {
+        const int kt = key[t];
+        int r = 0;
+        for (int u = 0; u < len; u++) {
+            const int ku = key[u];
+            r += (ku < kt) || (ku == kt && u < t);
+        }
+        skey[r] = kt;
+        sval[r] = v[beg + t];
+    }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    if (!prp) {
+        int c = 0;
+        for (int t = 0; t < len; t++) c += (t == 0 || skey[t] != skey[t - 1]);
+        cnt[i] = c;
+        return;
+    }
+    double aii = 0.0;
+    for (int k = beg; k < beg + len; k++)
+        if (ci[k] == i) aii = v[k];
+    const double wi = __ddiv_rn(omega, aii);
+    const int ai = agg[i];
+    int out = prp[i];
+    for (int t = 0; t < len;) {
+        const int J = skey[t];
+        double acc = 0.0;
+        for (; t < len && skey[t] == J; t++) acc = __dadd_rn(acc, sval[t]);
+        pci[out] = J;
+        pv[out] = __dsub_rn(J == ai ? 1.0 : 0.0, __dmul_rn(wi, acc));
+        out++;
+    }
+}
+
+// rows with cnt[i] < 0 listed (any order: each row is handled alone)
+__global__ void k_list_negative(int n, const int *__restrict__ cnt, int *__restrict__ list, int *__restrict__ nlist)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n && cnt[i] < 0) list[atomicAdd(nlist, 1)] = i;
 }
 
 __global__ void k_tentative(int n, const int *__restrict__ agg, int *__restrict__ rp, int *__restrict__ ci,
@@ -416,22 +488,50 @@ int amg_prolongator(amgh_problem *p, Arena &ar, const DevCsr &a, const int *agg,
     memcpy(&rho, &hb, sizeof(double));
     if (!(rho > 0.0)) return AMGH_ERR_NUMERIC;
     double omega = 4.0 / (3.0 * rho);
-    k_prol<<<ceil_div(n, 128), 128, 0, s>>>(n, a.rp, a.ci, a.v, agg, omega, nullptr, cnt, nullptr, nullptr, bad);
+    const int rowcap = g_prol_rowcap > 0 ? g_prol_rowcap : MAXROW;
+    k_prol<<<ceil_div(n, 128), 128, 0, s>>>(n, a.rp, a.ci, a.v, agg, omega, nullptr, cnt, nullptr, nullptr, bad,
+                                            rowcap);
     LAUNCH_CHECK();
+    // rows over MAXROW aggregates go to the one-block-per-row kernel
+    int *longrows = nullptr, *nlong_dev = nullptr;
+    TRY(sc.alloc(&longrows, n));
+    TRY(sc.alloc(&nlong_dev, 1));
+    CU(cudaMemsetAsync(nlong_dev, 0, sizeof(int), s));
+    k_list_negative<<<nb, 256, 0, s>>>(n, cnt, longrows, nlong_dev);
+    LAUNCH_CHECK();
+    int nlong = 0;
+    CU(cudaMemcpyAsync(&nlong, nlong_dev, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
+    const size_t long_smem = (size_t)PROL_LONG_MAX * (sizeof(double) + 2 * sizeof(int));
+    if (nlong > 0) {
+        CU(cudaFuncSetAttribute(k_prol_long, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)long_smem));
+        k_prol_long<<<nlong, 256, long_smem, s>>>(longrows, nlong, a.rp, a.ci, a.v, agg, omega, nullptr, cnt, nullptr,
+                                                  nullptr, bad);
+        LAUNCH_CHECK();
+    }
     int hbad = 0;
     CU(cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
     CU(cudaStreamSynchronize(s));
-    if (hbad) return AMGH_ERR_INVALID_ARG;
+    if (hbad) {
+        amgh_note_msg("prolongator: a row of A has more than 8192 entries");
+        return AMGH_ERR_INVALID_ARG;
+    }
     TRY(ar.alloc(&S.rp, n + 1));
     int nnz = 0;
     TRY(exclusive_scan<int>(cnt, S.rp, n, s, &nnz));
     S.nnz = nnz;
     TRY(ar.alloc(&S.ci, nnz));
     TRY(ar.alloc(&S.v, nnz));
-    k_prol<<<ceil_div(n, 128), 128, 0, s>>>(n, a.rp, a.ci, a.v, agg, omega, S.rp, cnt, S.ci, S.v, bad);
+    k_prol<<<ceil_div(n, 128), 128, 0, s>>>(n, a.rp, a.ci, a.v, agg, omega, S.rp, cnt, S.ci, S.v, bad, rowcap);
     LAUNCH_CHECK();
+    if (nlong > 0) {
+        k_prol_long<<<nlong, 256, long_smem, s>>>(longrows, nlong, a.rp, a.ci, a.v, agg, omega, S.rp, cnt, S.ci,
+                                                  S.v, bad);
+        LAUNCH_CHECK();
+    }
     CU(cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
     CU(cudaStreamSynchronize(s));
+    if (hbad) amgh_note_msg("prolongator: a row of A has more than 8192 entries");
     return hbad ? AMGH_ERR_INVALID_ARG : AMGH_OK;
 }
 
@@ -1092,6 +1192,7 @@ int symmetrize_upper(amgh_problem *p, DevCsr &c)
     int h = 0;
     CU(cudaMemcpyAsync(&h, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
     CU(cudaStreamSynchronize(s));
+    if (h) amgh_note_msg("Galerkin product: sparsity pattern not symmetric");
     return h ? AMGH_ERR_INVALID_ARG : AMGH_OK;
 }
 

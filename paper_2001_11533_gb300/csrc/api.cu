@@ -294,7 +294,10 @@ static void smoother_coeffs(amgh_problem *p)
 
 static int dense_inverse_of(amgh_problem *p, const DevCsr &a, Dense &out)
 {
-    if (a.rows > AMGH_DENSE_MAX) return AMGH_ERR_INVALID_ARG;
+    if (a.rows > AMGH_DENSE_MAX) {
+        amgh_note_msg("coarsest AMG level has more than 4096 rows (coarsening stalled): no dense inverse");
+        return AMGH_ERR_INVALID_ARG;
+    }
     int n = a.rows;
     Scratch sc;
     double *g = nullptr;
@@ -319,7 +322,10 @@ static int coarse_hessian_setup(amgh_problem *p, int ell)
     if (mode == 2) mode = p->cl[c].Mu.rows <= AMGH_DENSE_MAX ? 0 : 1;
     p->coarse_cg = mode == 1;
     if (mode == 0) {
-        if (p->cl[c].Mu.rows > AMGH_DENSE_MAX) return AMGH_ERR_INVALID_ARG;
+        if (p->cl[c].Mu.rows > AMGH_DENSE_MAX) {
+            amgh_note_msg("coarsest Hessian level has more than 4096 controls: use coarse_solve 1 or 2");
+            return AMGH_ERR_INVALID_ARG;
+        }
         const double *ainv = p->Acoarse.inv;
         if (c != p->Ls - 1) {
             TRY(dense_inverse_of(p, p->sl[c].A, p->Aell));
@@ -442,6 +448,7 @@ extern "C" int amgh_amg_setup(amgh_problem *p, const amgh_amg_opts *opts)
         return AMGH_ERR_INVALID_ARG;
     double t0 = now_s();
     StreamScope ss_(p->stream);
+    amgh_note_msg("");
     reset_hierarchy(p);
     p->aopts = o;
     int st = setup_impl(p);
@@ -455,6 +462,14 @@ extern "C" int amgh_amg_setup(amgh_problem *p, const amgh_amg_opts *opts)
 }
 
 // ------------------------------------------------------------------ applies
+// Every solve-phase entry point works on the problem's stream and counts its
+// kernels' algorithmic bytes into the problem's counter.
+struct CallScope {
+    StreamScope ss;
+    ByteSink bs;
+    explicit CallScope(amgh_problem *p) : ss(p->stream), bs(&p->c_bytes) {}
+};
+
 #define NEED_SETUP(p)                          \
     do {                                       \
         if (!(p)) return AMGH_ERR_INVALID_ARG; \
@@ -475,7 +490,7 @@ static int finish_call(amgh_problem *p, int st)
 extern "C" int amgh_hessian_apply(amgh_problem *p, const double *u, double *hu, int ncols)
 {
     NEED_SETUP(p);
-    StreamScope ss_(p->stream);
+    CallScope cs_(p);
     if (!u || !hu || ncols < 1) return AMGH_ERR_INVALID_ARG;
     int st = ncols > 1 ? block_hessian_apply(p, u, hu, ncols) : hessian_level(p, 0, u, hu);
     if (st == AMGH_OK) st = timer_collect(p);
@@ -485,7 +500,7 @@ extern "C" int amgh_hessian_apply(amgh_problem *p, const double *u, double *hu, 
 extern "C" int amgh_precond_apply(amgh_problem *p, const double *r, double *z, int ncols)
 {
     NEED_SETUP(p);
-    StreamScope ss_(p->stream);
+    CallScope cs_(p);
     if (!r || !z || ncols < 1) return AMGH_ERR_INVALID_ARG;
     int st = ncols > 1 ? block_precond_apply(p, r, z, ncols) : mlas_Q(p, 0, r, z);
     if (st == AMGH_OK) st = timer_collect(p);
@@ -495,7 +510,7 @@ extern "C" int amgh_precond_apply(amgh_problem *p, const double *r, double *z, i
 extern "C" int amgh_rhs(amgh_problem *p, double *b)
 {
     NEED_SETUP(p);
-    StreamScope ss_(p->stream);
+    CallScope cs_(p);
     if (!b) return AMGH_ERR_INVALID_ARG;
     return finish_call(p, rhs_apply(p, b));
 }
@@ -509,13 +524,14 @@ static void fill_info(amgh_problem *p, amgh_solve_info *info)
     info->t_setup_s = p->t_setup;
     info->hessian_levels = p->ell;
     info->coarse_iters = p->c_coarse;
+    info->alg_bytes = p->c_bytes;
 }
 
 extern "C" int amgh_solve(amgh_problem *p, const double *u0, double *u, double *y, const amgh_solve_opts *opts,
                           amgh_solve_info *info)
 {
     NEED_SETUP(p);
-    StreamScope ss_(p->stream);
+    CallScope cs_(p);
     if (!u) return AMGH_ERR_INVALID_ARG;
     amgh_solve_opts o;
     if (opts) o = *opts;
@@ -540,7 +556,7 @@ extern "C" int amgh_solve(amgh_problem *p, const double *u0, double *u, double *
     }
     if (st == AMGH_OK && y) {
         CtrlLevel &C = p->cl[0];
-        int s2 = spmv(p, C.Myu, u, C.t1, nullptr, 0);
+        int s2 = spmv(p, C.Myu, u, C.t1, nullptr, KC_SPMV);
         if (s2 == AMGH_OK) s2 = state_solve(p, 0, C.t1, y, p->sopts.inner_tol, nullptr);
         st = s2;
     }
@@ -557,7 +573,7 @@ extern "C" int amgh_solve_block(amgh_problem *p, const double *yd, int ncols, do
                                 const amgh_solve_opts *opts, amgh_solve_info *info)
 {
     NEED_SETUP(p);
-    StreamScope ss_(p->stream);
+    CallScope cs_(p);
     if (!yd || !u || ncols < 1) return AMGH_ERR_INVALID_ARG;
     amgh_solve_opts o;
     if (opts) o = *opts;
@@ -595,7 +611,7 @@ extern "C" int amgh_solve_host(amgh_problem *p, const double *u0_host, double *u
                                const amgh_solve_opts *opts, amgh_solve_info *info)
 {
     NEED_SETUP(p);
-    StreamScope ss_(p->stream);
+    CallScope cs_(p);
     if (!u_host) return AMGH_ERR_INVALID_ARG;
     Scratch sc;
     double *u0 = nullptr, *u = nullptr, *y = nullptr;
@@ -621,19 +637,19 @@ __global__ void k_sub(int n, const double *__restrict__ a, const double *__restr
 extern "C" int amgh_state_solve(amgh_problem *p, const double *u, double *y, double *J)
 {
     NEED_SETUP(p);
-    StreamScope ss_(p->stream);
+    CallScope cs_(p);
     if (!u || !y) return AMGH_ERR_INVALID_ARG;
     CtrlLevel &C = p->cl[0];
     StateLevel &S = p->sl[0];
-    TRY(spmv(p, C.Myu, u, C.t1, nullptr, 0));
+    TRY(spmv(p, C.Myu, u, C.t1, nullptr, KC_SPMV));
     int st = state_solve(p, 0, C.t1, y, p->sopts.inner_tol, nullptr);
     if (st != AMGH_OK) return finish_call(p, st);
     if (J) {
         int m = p->m, n = p->n;
         k_sub<<<ceil_div(m, 256), 256, 0, p->stream>>>(m, y, p->yd_state, C.t1);
         LAUNCH_CHECK();
-        TRY(spmv(p, S.My, C.t1, C.t2, nullptr, 0));
-        TRY(spmv(p, C.Mu, u, p->oq, nullptr, 0));
+        TRY(spmv(p, S.My, C.t1, C.t2, nullptr, KC_SPMV));
+        TRY(spmv(p, C.Mu, u, p->oq, nullptr, KC_SPMV));
         TRY(vec_dot(p, p->ored, m, C.t1, C.t2, p->dscratch));
         TRY(vec_dot(p, p->ored, n, u, p->oq, p->dscratch + 1));
         double h[2];
@@ -647,14 +663,14 @@ extern "C" int amgh_state_solve(amgh_problem *p, const double *u, double *y, dou
 extern "C" int amgh_gradient(amgh_problem *p, const double *u, const double *y, double *g)
 {
     NEED_SETUP(p);
-    StreamScope ss_(p->stream);
+    CallScope cs_(p);
     if (!u || !y || !g) return AMGH_ERR_INVALID_ARG;
     CtrlLevel &C = p->cl[0];
     StateLevel &S = p->sl[0];
     int m = p->m;
     k_sub<<<ceil_div(m, 256), 256, 0, p->stream>>>(m, y, p->yd_state, C.t1);
     LAUNCH_CHECK();
-    TRY(spmv(p, S.My, C.t1, C.t2, nullptr, 0));
+    TRY(spmv(p, S.My, C.t1, C.t2, nullptr, KC_SPMV));
     int st = state_solve(p, 0, C.t2, C.ps, p->sopts.inner_tol, nullptr);
     if (st == AMGH_OK) st = spmv2(p, C.Myut, C.ps, C.Mu, u, p->beta, g, nullptr);
     return finish_call(p, st);
@@ -663,12 +679,12 @@ extern "C" int amgh_gradient(amgh_problem *p, const double *u, const double *y, 
 extern "C" int amgh_state_adjoint(amgh_problem *p, const double *w, double *g)
 {
     NEED_SETUP(p);
-    StreamScope ss_(p->stream);
+    CallScope cs_(p);
     if (!w || !g) return AMGH_ERR_INVALID_ARG;
     CtrlLevel &C = p->cl[0];
     // A is symmetric, so A^-T w is one more AMG-CG solve
     int st = state_solve(p, 0, w, C.ps, p->sopts.inner_tol, nullptr);
-    if (st == AMGH_OK) st = spmv(p, C.Myut, C.ps, g, nullptr, 0);
+    if (st == AMGH_OK) st = spmv(p, C.Myut, C.ps, g, nullptr, KC_SPMV);
     return finish_call(p, st);
 }
 
@@ -676,7 +692,7 @@ extern "C" int amgh_state_adjoint(amgh_problem *p, const double *w, double *g)
 extern "C" int amgh_vcycle(amgh_problem *p, int level, const double *b, double *x)
 {
     NEED_SETUP(p);
-    StreamScope ss_(p->stream);
+    CallScope cs_(p);
     if (level < 0 || level >= p->Ls || !b || !x) return AMGH_ERR_INVALID_ARG;
     return finish_call(p, vcycle_run(p, level, 0, b, x, nullptr));
 }
@@ -685,7 +701,7 @@ extern "C" int amgh_state_solve_level(amgh_problem *p, int level, const double *
                                       int64_t *iters)
 {
     NEED_SETUP(p);
-    StreamScope ss_(p->stream);
+    CallScope cs_(p);
     if (level < 0 || level >= p->Ls || !f || !y || !(tol > 0.0)) return AMGH_ERR_INVALID_ARG;
     return finish_call(p, state_solve(p, level, f, y, tol, iters));
 }
@@ -693,7 +709,7 @@ extern "C" int amgh_state_solve_level(amgh_problem *p, int level, const double *
 extern "C" int amgh_mass_solve(amgh_problem *p, int level, const double *b, double *x, int64_t *iters)
 {
     NEED_SETUP(p);
-    StreamScope ss_(p->stream);
+    CallScope cs_(p);
     if (level < 0 || level >= p->Lc || !b || !x) return AMGH_ERR_INVALID_ARG;
     TRY(mass_solve(p, level, b, x, iters));
     return sync_stream(p);
@@ -702,7 +718,7 @@ extern "C" int amgh_mass_solve(amgh_problem *p, int level, const double *b, doub
 extern "C" int amgh_hessian_apply_level(amgh_problem *p, int level, const double *v, double *hv)
 {
     NEED_SETUP(p);
-    StreamScope ss_(p->stream);
+    CallScope cs_(p);
     if (level < 0 || level >= p->ell || !v || !hv) return AMGH_ERR_INVALID_ARG;
     return finish_call(p, hessian_level(p, level, v, hv));
 }
@@ -710,7 +726,7 @@ extern "C" int amgh_hessian_apply_level(amgh_problem *p, int level, const double
 extern "C" int amgh_precond_apply_level(amgh_problem *p, int which, int level, const double *b, double *z)
 {
     NEED_SETUP(p);
-    StreamScope ss_(p->stream);
+    CallScope cs_(p);
     if (level < 0 || level >= p->ell || !b || !z) return AMGH_ERR_INVALID_ARG;
     if (which != 0 && level >= p->ell - 1) return AMGH_ERR_INVALID_ARG;
     return finish_call(p, which == 0 ? mlas_Q(p, level, b, z) : mlas_R(p, level, b, z));
@@ -798,6 +814,7 @@ extern "C" int amgh_get_counters(const amgh_problem *p, amgh_solve_info *info)
 static void zero_counters(amgh_problem *p)
 {
     p->c_inner = p->c_mass = p->c_happ = p->c_refine = p->c_coarse = 0;
+    p->c_bytes = 0.0;
     for (int l = 0; l < AMGH_MAXL; l++) p->c_inner_lvl[l] = p->c_mass_lvl[l] = 0;
 }
 
@@ -818,10 +835,11 @@ extern "C" int amgh_get_level_counters(const amgh_problem *p, int64_t *inner, in
     return AMGH_OK;
 }
 
-extern "C" int amgh_debug_limits(int bulk_first_polls, int mis_round_cap)
+extern "C" int amgh_debug_limits(int bulk_first_polls, int mis_round_cap, int prol_row_cap)
 {
-    if (bulk_first_polls < -1 || mis_round_cap < -1) return AMGH_ERR_INVALID_ARG;
+    if (bulk_first_polls < -1 || mis_round_cap < -1 || prol_row_cap < -1) return AMGH_ERR_INVALID_ARG;
     mis_set_round_cap(mis_round_cap);
+    prol_set_row_cap(prol_row_cap);
     return bulk_set_first_polls(bulk_first_polls);
 }
 
@@ -830,20 +848,29 @@ extern "C" int amgh_kernel_timing(amgh_problem *p, int enable)
     if (!p) return AMGH_ERR_INVALID_ARG;
     TRY(timer_collect(p));
     p->timer.enabled = enable ? 1 : 0;
-    p->timer.launches = 0;
-    p->timer.ms = 0.0;
-    p->timer.bytes = 0.0;
+    for (int c = 0; c < KC_N; c++) {
+        p->timer.launches[c] = 0;
+        p->timer.ms[c] = 0.0;
+        p->timer.bytes[c] = 0.0;
+    }
+    return AMGH_OK;
+}
+
+extern "C" int amgh_kernel_class_stats(amgh_problem *p, int cls, int64_t *launches, double *ms, double *bytes,
+                                       const char **name)
+{
+    if (!p || cls < 0 || cls >= KC_N) return AMGH_ERR_INVALID_ARG;
+    TRY(timer_collect(p));
+    if (launches) *launches = p->timer.launches[cls];
+    if (ms) *ms = p->timer.ms[cls];
+    if (bytes) *bytes = p->timer.bytes[cls];
+    if (name) *name = kclass_name(cls);
     return AMGH_OK;
 }
 
 extern "C" int amgh_kernel_stats(amgh_problem *p, int64_t *launches, double *ms, double *bytes)
 {
-    if (!p) return AMGH_ERR_INVALID_ARG;
-    TRY(timer_collect(p));
-    if (launches) *launches = p->timer.launches;
-    if (ms) *ms = p->timer.ms;
-    if (bytes) *bytes = p->timer.bytes;
-    return AMGH_OK;
+    return amgh_kernel_class_stats(p, KC_CHEB0, launches, ms, bytes, nullptr);
 }
 
 extern "C" void amgh_problem_destroy(amgh_problem *p)

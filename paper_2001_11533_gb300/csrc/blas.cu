@@ -463,6 +463,8 @@ static int cg2_spmv_df(amgh_problem *p, RedSlot &red, const DevCsr &a, const Z *
 {
     MatView<float> A = view<float>(a);
     const float *lo = a.lo32;
+    const int cls = fine_cls(p, a.rows, KC_CGSPMV0, KC_CGSPMV);
+    timer_begin(p, cls);
     switch (A.tpr) {
     case 2: pdl_launch(k_cg2_spmv_df<Z, 2>, dim3(rows_grid(A.rows, 2)), dim3(TPB), 0, p->stream, A, lo, z, r, s, sc, red.partials, red.ticket); break;
     case 4: pdl_launch(k_cg2_spmv_df<Z, 4>, dim3(rows_grid(A.rows, 4)), dim3(TPB), 0, p->stream, A, lo, z, r, s, sc, red.partials, red.ticket); break;
@@ -472,6 +474,8 @@ static int cg2_spmv_df(amgh_problem *p, RedSlot &red, const DevCsr &a, const Z *
     default: pdl_launch(k_cg2_spmv_df<Z, 1>, dim3(rows_grid(A.rows, 1)), dim3(TPB), 0, p->stream, A, lo, z, r, s, sc, red.partials, red.ticket); break;
     }
     LAUNCH_CHECK();
+    // FP32 hi and lo values, indices, z gathered; FP64 r read and s written
+    timer_end(p, cls, spmv_bytes(a, 4) + 4.0 * a.nnz + (16.0 - 4.0) * a.rows);
     return AMGH_OK;
 }
 
@@ -482,8 +486,10 @@ int cg2_spmv(amgh_problem *p, RedSlot &red, const DevCsr &a, const Z *z, const T
     // products on the FP32 pipe
     if (sizeof(T) == 8 && sizeof(Z) == 4 && a.lo32 && p->df_spmv)
         return cg2_spmv_df<Z>(p, red, a, z, (const double *)r, (double *)s, sc);
+    (void)timed;
     MatView<T> A = view<T>(a);
-    timer_begin(p, timed);
+    const int cls = fine_cls(p, a.rows, KC_CGSPMV0, KC_CGSPMV);
+    timer_begin(p, cls);
     switch (A.tpr) {
     case 2: pdl_launch(k_cg2_spmv<T, Z, 2>, dim3(rows_grid(A.rows, 2)), dim3(TPB), 0, p->stream, A, z, r, s, sc, red.partials, red.ticket); break;
     case 4: pdl_launch(k_cg2_spmv<T, Z, 4>, dim3(rows_grid(A.rows, 4)), dim3(TPB), 0, p->stream, A, z, r, s, sc, red.partials, red.ticket); break;
@@ -494,7 +500,7 @@ int cg2_spmv(amgh_problem *p, RedSlot &red, const DevCsr &a, const Z *z, const T
     }
     LAUNCH_CHECK();
     // matrix + gather of z + reads of r, z + write of s
-    timer_end(p, timed, spmv_bytes(a, sizeof(T)) - (double)sizeof(T) * a.cols + (double)sizeof(Z) * a.cols +
+    timer_end(p, cls, spmv_bytes(a, sizeof(T)) - (double)sizeof(T) * a.cols + (double)sizeof(Z) * a.cols +
                             (double)(sizeof(T) + sizeof(Z)) * a.rows);
     return AMGH_OK;
 }
@@ -503,9 +509,16 @@ template <typename T, typename Z>
 int cg2_update(amgh_problem *p, RedSlot &red, int n, Z *z, const T *s, T *pv, T *q, T *x, T *r, float *r32,
                const double *invd, CgScal *sc, T *vd, T *vx, const T *vinvd, double c0)
 {
+    const int cls = fine_cls(p, n, KC_CGUPD0, KC_CGUPD);
+    timer_begin(p, cls);
     pdl_launch(k_cg2_update<T, Z>, dim3(vec_blocks(n)), dim3(TPB), 0, p->stream, n, z, s, pv, q, x, r, r32, invd,
                vd, vx, vinvd, (T)c0, sc, red.partials, red.ticket);
     LAUNCH_CHECK();
+    // z, s, p, q, x, r read; p, q, x, r written; the optional FP32 copy of r,
+    // Jacobi z and the V-cycle's first step
+    const double tb = sizeof(T);
+    timer_end(p, cls, n * (sizeof(Z) + 9.0 * tb + (r32 ? 4.0 : 0.0) + (invd ? 8.0 + sizeof(Z) : 0.0) +
+                           (vd ? 3.0 * tb : 0.0)));
     return AMGH_OK;
 }
 
@@ -530,8 +543,10 @@ int cg_start(amgh_problem *p, RedSlot &red, int n, const T *f, T *x, T *r, CgSca
              int zero_x)
 {
     TRY(set_scal(p, sc, tol, maxit));
+    timer_begin(p, KC_VEC);
     pdl_launch(k_cg_start<T>, dim3(vec_blocks(n)), dim3(TPB), 0, p->stream, n, f, x, r, sc, zero_x, red.partials, red.ticket, F_START);
     LAUNCH_CHECK();
+    timer_end(p, KC_VEC, 3.0 * sizeof(T) * n);
     return AMGH_OK;
 }
 template int cg_start<double>(amgh_problem *, RedSlot &, int, const double *, double *, double *, CgScal *, double,
@@ -542,8 +557,10 @@ template int cg_start<float>(amgh_problem *, RedSlot &, int, const float *, floa
 int cg_update_outer(amgh_problem *p, RedSlot &red, int n, double *x, double *r, const double *pv, const double *q,
                     CgScal *sc)
 {
+    timer_begin(p, KC_VEC);
     pdl_launch(k_update, dim3(vec_blocks(n)), dim3(TPB), 0, p->stream, n, x, r, pv, q, sc, red.partials, red.ticket);
     LAUNCH_CHECK();
+    timer_end(p, KC_VEC, 48.0 * n);
     return AMGH_OK;
 }
 
@@ -552,16 +569,20 @@ int mass_start(amgh_problem *p, RedSlot &red, int n, const double *f, double *x,
                const double *invd, CgScal *sc, double tol, int maxit)
 {
     TRY(set_scal(p, sc, tol, maxit));
+    timer_begin(p, KC_VEC);
     pdl_launch(k_mass_start, dim3(vec_blocks(n)), dim3(TPB), 0, p->stream, n, f, x, r, z, invd, sc, red.partials, red.ticket);
     LAUNCH_CHECK();
+    timer_end(p, KC_VEC, 40.0 * n);
     return AMGH_OK;
 }
 
 // outer CG pieces (operator applied by the host between them)
 int outer_dot(amgh_problem *p, RedSlot &red, int n, const double *x, const double *y, CgScal *sc, int mode)
 {
+    timer_begin(p, KC_VEC);
     pdl_launch(k_dot, dim3(vec_blocks(n)), dim3(TPB), 0, p->stream, n, x, y, sc, mode, nullptr, red.partials, red.ticket);
     LAUNCH_CHECK();
+    timer_end(p, KC_VEC, 16.0 * n);
     return AMGH_OK;
 }
 
@@ -573,19 +594,25 @@ int outer_pq(amgh_problem *p, RedSlot &red, int n, const double *pv, const doubl
 int outer_rz(amgh_problem *p, RedSlot &red, int n, const double *r, const double *z, double *pv, CgScal *sc,
              int first)
 {
+    timer_begin(p, KC_VEC);
     pdl_launch(k_rz<double>, dim3(vec_blocks(n)), dim3(TPB), 0, p->stream, n, r, z, pv, sc, first, red.partials, red.ticket);
     LAUNCH_CHECK();
+    timer_end(p, KC_VEC, (first ? 24.0 : 16.0) * n);
     if (!first) {
+        timer_begin(p, KC_VEC);
         pdl_launch(k_xpay<double>, dim3(vec_blocks(n)), dim3(TPB), 0, p->stream, n, z, pv, sc);
         LAUNCH_CHECK();
+        timer_end(p, KC_VEC, 24.0 * n);
     }
     return AMGH_OK;
 }
 
 int vec_dot(amgh_problem *p, RedSlot &red, int n, const double *x, const double *y, double *out_dev)
 {
+    timer_begin(p, KC_VEC);
     pdl_launch(k_dot, dim3(vec_blocks(n)), dim3(TPB), 0, p->stream, n, x, y, nullptr, F_STORE, out_dev, red.partials, red.ticket);
     LAUNCH_CHECK();
+    timer_end(p, KC_VEC, 16.0 * n);
     return AMGH_OK;
 }
 
@@ -594,16 +621,20 @@ int ref_start(amgh_problem *p, RedSlot &red, int n, const double *f, double *y, 
               int maxit)
 {
     TRY(set_scal(p, rs, tol, maxit));
+    timer_begin(p, KC_VEC);
     pdl_launch(k_cg_start<double>, dim3(vec_blocks(n)), dim3(TPB), 0, p->stream, n, f, y, r, rs, 1, red.partials, red.ticket,
                                                              F_REF_START);
     LAUNCH_CHECK();
+    timer_end(p, KC_VEC, 24.0 * n);
     return AMGH_OK;
 }
 
 int ref_to32(amgh_problem *p, RedSlot & /*red*/, int n, const double *r, float *r32, CgScal *rs)
 {
+    timer_begin(p, KC_VEC);
     pdl_launch(k_ref_to32, dim3(vec_blocks(n)), dim3(TPB), 0, p->stream, n, r, r32, rs);
     LAUNCH_CHECK();
+    timer_end(p, KC_VEC, 12.0 * n);
     return AMGH_OK;
 }
 
@@ -611,9 +642,12 @@ int ref_update(amgh_problem *p, RedSlot &red, const DevCsr &a, const double *f, 
                double *r, CgScal *rs)
 {
     int n = a.rows;
+    timer_begin(p, KC_VEC);
     pdl_launch(k_ref_add, dim3(vec_blocks(n)), dim3(TPB), 0, p->stream, n, y, e32, rs);
     LAUNCH_CHECK();
+    timer_end(p, KC_VEC, 20.0 * n);
     MatView<double> A = view<double>(a);
+    timer_begin(p, KC_SPMV);
     switch (A.tpr) {
     case 2: pdl_launch(k_ref_resid<double, 2>, dim3(rows_grid(n, 2)), dim3(TPB), 0, p->stream, A, f, y, r, rs, red.partials, red.ticket); break;
     case 4: pdl_launch(k_ref_resid<double, 4>, dim3(rows_grid(n, 4)), dim3(TPB), 0, p->stream, A, f, y, r, rs, red.partials, red.ticket); break;
@@ -623,22 +657,27 @@ int ref_update(amgh_problem *p, RedSlot &red, const DevCsr &a, const double *f, 
     default: pdl_launch(k_ref_resid<double, 1>, dim3(rows_grid(n, 1)), dim3(TPB), 0, p->stream, A, f, y, r, rs, red.partials, red.ticket); break;
     }
     LAUNCH_CHECK();
+    timer_end(p, KC_SPMV, spmv_bytes(a, 8) + 8.0 * n);
     return AMGH_OK;
 }
 
 int vec_axpby(amgh_problem *p, int n, double a, const double *x, double b, const double *y, double *out)
 {
     if (n == 0) return AMGH_OK;
+    timer_begin(p, KC_VEC);
     pdl_launch(k_axpby, dim3(vec_blocks(n)), dim3(TPB), 0, p->stream, n, a, x, b, y, out);
     LAUNCH_CHECK();
+    timer_end(p, KC_VEC, (y ? 24.0 : 16.0) * n);
     return AMGH_OK;
 }
 
 int vec_fill(amgh_problem *p, int n, double v, double *x)
 {
     if (n == 0) return AMGH_OK;
+    timer_begin(p, KC_VEC);
     pdl_launch(k_fill, dim3(vec_blocks(n)), dim3(TPB), 0, p->stream, n, v, x);
     LAUNCH_CHECK();
+    timer_end(p, KC_VEC, 8.0 * n);
     return AMGH_OK;
 }
 
@@ -835,11 +874,15 @@ int dfcg_start(amgh_problem *p, RedSlot &red, int n, const double *f, double *x,
                int maxit)
 {
     TRY(set_scal(p, sc, tol, maxit));
+    timer_begin(p, KC_VEC);
     pdl_launch(k_df_norm, dim3(vec_blocks(n)), dim3(TPB), 0, p->stream, n, f, sc, red.partials, red.ticket);
     LAUNCH_CHECK();
+    timer_end(p, KC_VEC, 8.0 * n);
+    timer_begin(p, KC_VEC);
     pdl_launch(k_df_start, dim3(std::min(vec_blocks(n), resident_grid((const void *)k_df_start, TPB))), dim3(TPB), 0, p->stream, n, f, hi_of(x), lo_of(x, n), hi_of(r), lo_of(r, n), sc,
                                                     red.partials, red.ticket);
     LAUNCH_CHECK();
+    timer_end(p, KC_VEC, 24.0 * n);
     return AMGH_OK;
 }
 
@@ -850,6 +893,8 @@ int dfcg_spmv(amgh_problem *p, RedSlot &red, const DevCsr &a, const float *z, co
     MatView<float> A = view<float>(a);
     int n = a.rows;
     const float *lo = a.lo32;
+    const int cls = fine_cls(p, n, KC_CGSPMV0, KC_CGSPMV);
+    timer_begin(p, cls);
 #define DFSPMV(TPR)                                                                                            \
     pdl_launch(k_df_spmv<TPR>,                                                                                 \
                dim3(std::min(rows_grid(n, TPR), resident_grid((const void *)k_df_spmv<TPR>, TPB))), dim3(TPB), \
@@ -864,16 +909,23 @@ int dfcg_spmv(amgh_problem *p, RedSlot &red, const DevCsr &a, const float *z, co
     }
 #undef DFSPMV
     LAUNCH_CHECK();
+    // FP32 hi and lo values, indices, z gathered; r read and s written as hi + lo
+    timer_end(p, cls, spmv_bytes(a, 4) + 4.0 * a.nnz + (16.0 - 4.0) * n);
     return AMGH_OK;
 }
 
 int dfcg_update(amgh_problem *p, RedSlot &red, int n, const float *z, const double *s, double *pv, double *q,
                 double *x, double *r, CgScal *sc, const float *invd32, float *vd, float *vx, double c0)
 {
+    const int cls = fine_cls(p, n, KC_CGUPD0, KC_CGUPD);
+    timer_begin(p, cls);
     pdl_launch(k_df_update, dim3(std::min(vec_blocks(n), resident_grid((const void *)k_df_update, TPB))), dim3(TPB), 0, p->stream, n, z, hi_of(s), lo_of(s, n), hi_of(pv), lo_of(pv, n),
                                                      hi_of(q), lo_of(q, n), hi_of(x), lo_of(x, n), hi_of(r),
                                                      lo_of(r, n), invd32, (float *)z, vd, vx, (float)c0, sc, red.partials, red.ticket);
     LAUNCH_CHECK();
+    // z (FP32), s, p, q, x, r (hi + lo) read; p, q, x, r written; D^-1 read
+    // and either z (Jacobi) or the V-cycle's d and x written
+    timer_end(p, cls, n * (4.0 + 9.0 * 8.0 + (invd32 ? 4.0 + (vd ? 8.0 : 4.0) : 0.0)));
     return AMGH_OK;
 }
 
@@ -887,14 +939,18 @@ __global__ void k_df_jacobi(int n, const float *__restrict__ rh, const float *__
 
 int dfcg_jacobi(amgh_problem *p, int n, const double *r, const float *invd32, float *z)
 {
+    timer_begin(p, KC_VEC);
     pdl_launch(k_df_jacobi, dim3(std::min(vec_blocks(n), resident_grid((const void *)k_df_jacobi, TPB))), dim3(TPB), 0, p->stream, n, hi_of(r), invd32, z);
     LAUNCH_CHECK();
+    timer_end(p, KC_VEC, 12.0 * n);
     return AMGH_OK;
 }
 
 int df_to_double(amgh_problem *p, int n, const double *x, const CgScal *sc, double *y)
 {
+    timer_begin(p, KC_VEC);
     pdl_launch(k_df_to_double, dim3(std::min(vec_blocks(n), resident_grid((const void *)k_df_to_double, TPB))), dim3(TPB), 0, p->stream, n, hi_of(x), lo_of(x, n), sc, y);
     LAUNCH_CHECK();
+    timer_end(p, KC_VEC, 16.0 * n);
     return AMGH_OK;
 }

@@ -293,7 +293,9 @@ int fused_vcycle(amgh_problem *p, const float *b, float *x, int preinit, const i
     cfg.stream = p->stream;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
+    timer_begin(p, KC_COARSE);
     CU(cudaLaunchKernelEx(&cfg, k_vcycle_fused, (const FusedCycle *)p->fuse_table, b, x, preinit, skip));
     amgh_count_launch();
+    timer_end(p, KC_COARSE, vcycle_bytes(p, p->fuse_c0, 4));
     return AMGH_OK;
 }

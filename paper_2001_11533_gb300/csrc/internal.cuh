@@ -201,6 +201,9 @@ enum { CG_RUNNING = 0, CG_CONVERGED = 1, CG_INDEFINITE = 2, CG_NUMERIC = 3, CG_M
 struct CgGraph {
     cudaGraphExec_t start = nullptr, iter = nullptr;
     int nodes_start = 0, nodes_iter = 0;
+    // algorithmic bytes of one replay, and of the iteration's V-cycle alone
+    // (skipped in the iteration that converges)
+    double bytes_start = 0.0, bytes_iter = 0.0, bytes_vc = 0.0;
 };
 
 struct StateLevel {
@@ -247,14 +250,56 @@ struct Dense {
     int ld32 = 0;
 };
 
+// Kernel classes of the solve phase: per-class launch counts, durations and
+// algorithmic bytes (the *0 classes are the finest level, whose operands do
+// not fit in L2; the others are the coarse levels and control-side work).
+enum KClass {
+    KC_CHEB0,     // Chebyshev / l1-Jacobi step, level 0
+    KC_CHEB,      // the same on coarse levels (and the first step from zero)
+    KC_RESID0,    // residual b - A x, level 0
+    KC_RESID,
+    KC_RESTRICT0, // S^T r (fused with the coarse level's first smoother step)
+    KC_RESTRICT,
+    KC_PROLONG0,  // x += S e
+    KC_PROLONG,
+    KC_CGSPMV0,   // CG operator product with its dot products, level 0
+    KC_CGSPMV,
+    KC_CGUPD0,    // CG vector update with its reduction, level 0
+    KC_CGUPD,
+    KC_COARSE,    // dense coarsest solve, fused coarse V-cycle
+    KC_SPMV,      // other sparse products (M_yu, M_y, M_u, P, P^T, ...)
+    KC_VEC,       // other vector kernels
+    KC_N
+};
+static_assert(KC_N == AMGH_KCLASSES, "kernel classes of the ABI");
+const char *kclass_name(int c);
+
 struct KernelTimer {
     int enabled = 0;
     std::vector<cudaEvent_t> ev; // pairs
-    int64_t launches = 0;
-    double ms = 0.0, bytes = 0.0;
+    std::vector<int> cls;        // class of each pending pair
     std::vector<double> pending_bytes;
     std::vector<cudaEvent_t> pool;
+    int64_t launches[KC_N] = {};
+    double ms[KC_N] = {}, bytes[KC_N] = {};
+    size_t vc_mark = 0; // event count before the V-cycle of the last CG iteration
 };
+
+// Algorithmic bytes of the solve phase: every launch wrapper reports its
+// kernel's compulsory traffic (from sizes, not counters) to the calling
+// thread's sink.  Entry points point the sink at the problem's counter; graph
+// capture points it at the graph's own total, which the CG loops then add
+// once per iteration actually executed.
+extern thread_local double *g_byte_sink;
+struct ByteSink {
+    double *prev;
+    explicit ByteSink(double *s) : prev(g_byte_sink) { g_byte_sink = s; }
+    ~ByteSink() { g_byte_sink = prev; }
+};
+static inline void count_bytes(double b)
+{
+    if (g_byte_sink) *g_byte_sink += b;
+}
 
 struct BlockWork; // work space of the block solver (block.cu)
 
@@ -306,6 +351,8 @@ struct amgh_problem {
     CgScal *h_scal = nullptr; // pinned
     // counters
     int64_t c_inner = 0, c_mass = 0, c_happ = 0, c_refine = 0, c_coarse = 0;
+    double c_bytes = 0.0;  // algorithmic bytes of the solve-phase kernels run
+    double vc_bytes = 0.0; // bytes of the V-cycle inside the last CG iteration body
     int64_t c_inner_lvl[AMGH_MAXL], c_mass_lvl[AMGH_MAXL];
     double t_setup = 0.0;
     KernelTimer timer;
@@ -314,6 +361,13 @@ struct amgh_problem {
     int mchunk_hint[AMGH_MAXL];
     BlockWork *blk = nullptr; // allocated by the first block call
 };
+
+// class c0 for vectors / operators of the finest state or control level
+// (larger than L2 on the benchmark meshes), c for every coarser one
+static inline int fine_cls(const amgh_problem *p, int rows, int c0, int c)
+{
+    return (rows == p->m || rows == p->n) ? c0 : c;
+}
 
 // ------------------------------------------------------------------ sparse.cu
 int csr_to_sell(Arena &ar, DevCsr &a, int want32, cudaStream_t s);
@@ -329,14 +383,17 @@ int bulk_timeout_check(cudaStream_t s);
 int bulk_set_first_polls(int polls);
 // rounds the MIS-2 loop may take before AMGH_ERR_TIMEOUT (<= 0: n + 1)
 void mis_set_round_cap(int cap);
+// aggregates per prolongator row kept in registers (<= 0: the default)
+void prol_set_row_cap(int cap);
 // b = (float)a
 int to_f32(amgh_problem *p, const double *a, int64_t n, float *b);
 // build a.lo32 (after prepare_operator)
 int build_lo_parts(Arena &ar, DevCsr &a, cudaStream_t s);
 int csr_transpose(Arena &ar, const DevCsr &a, DevCsr &t, cudaStream_t s);
 // y = A x (FP64 or FP32 SELL)
-int spmv(amgh_problem *p, const DevCsr &a, const double *x, double *y, const int *skip, int timed);
-int spmv32(amgh_problem *p, const DevCsr &a, const float *x, float *y, const int *skip, int timed);
+// cls: the KClass the launch is timed and counted under
+int spmv(amgh_problem *p, const DevCsr &a, const double *x, double *y, const int *skip, int cls);
+int spmv32(amgh_problem *p, const DevCsr &a, const float *x, float *y, const int *skip, int cls);
 // y = A1 x1 + c * A2 x2 (same row count)
 int spmv2(amgh_problem *p, const DevCsr &a1, const double *x1, const DevCsr &a2, const double *x2,
           double c, double *y, const int *skip);
@@ -355,7 +412,7 @@ int cheb_step(amgh_problem *p, const DevCsr &a, const T *invd, const T *b, const
 template <typename T>
 int residual(amgh_problem *p, const DevCsr &a, const T *b, const T *x, T *r, const int *skip, int timed);
 template <typename T>
-int spmv_t(amgh_problem *p, const DevCsr &a, const T *x, T *y, const int *skip, int timed);
+int spmv_t(amgh_problem *p, const DevCsr &a, const T *x, T *y, const int *skip, int cls);
 template <typename T>
 int restrict_first(amgh_problem *p, const DevCsr &st, const T *r, T *bc, const T *invd_c, T *d_c, T *x_c,
                    double c0, const int *skip);
@@ -463,7 +520,13 @@ int block_precond_apply(amgh_problem *p, const double *r, double *z, int ncols);
 int block_solve(amgh_problem *p, const double *yd, int ncols, double *u, const amgh_solve_opts &o,
                 amgh_solve_info *info);
 
-// timing of fine-level SpMV-class kernels
-void timer_begin(amgh_problem *p, int timed);
-void timer_end(amgh_problem *p, int timed, double bytes);
+// per-launch timing (when enabled, outside graph capture) and byte counting of
+// a solve-phase kernel of class cls; timer_end always counts the bytes
+void timer_begin(amgh_problem *p, int cls);
+void timer_end(amgh_problem *p, int cls, double bytes);
 int timer_collect(amgh_problem *p);
+// drop the pending timings recorded since `mark` (launches that the device
+// skipped: the V-cycle of a CG iteration that converged)
+void timer_drop_from(amgh_problem *p, size_t mark);
+// bytes of one V-cycle at level l (value bytes vb) for the fused coarse launch
+double vcycle_bytes(const amgh_problem *p, int l, int vb);

@@ -183,14 +183,14 @@ static int vcyc(amgh_problem *p, int l, const T *b, T *x, const int *skip, int p
         nxt = t;
     }
     // coarse-grid correction
-    TRY(residual<T>(p, S.A, b, cur, r, skip, 0));
+    TRY(residual<T>(p, S.A, b, cur, r, skip, timed));
     StateLevel &Sc = p->sl[l + 1];
     T *bc = VBuf<T>::b(Sc), *xc = VBuf<T>::x(Sc);
     if (l + 1 < p->Ls - 1) {
         TRY(restrict_first<T>(p, S.St, r, bc, VBuf<T>::invd(Sc), VBuf<T>::d(Sc), VBuf<T>::x2(Sc), p->cr[0], skip));
         TRY(vcyc<T>(p, l + 1, bc, xc, skip, 1));
     } else {
-        TRY(spmv_t<T>(p, S.St, r, bc, skip, 0));
+        TRY(spmv_t<T>(p, S.St, r, bc, skip, l == 0 ? KC_RESTRICT0 : KC_RESTRICT));
         TRY(vcyc<T>(p, l + 1, bc, xc, skip));
     }
     TRY(prolong_add<T>(p, S.S, xc, cur, skip));
@@ -202,10 +202,28 @@ static int vcyc(amgh_problem *p, int l, const T *b, T *x, const int *skip, int p
         nxt = t;
     }
     if (cur != x) {
+        timer_begin(p, KC_VEC);
         pdl_launch(k_copy<T>, dim3(ceil_div(n, 256)), dim3(256), 0, p->stream, n, cur, x, skip);
         LAUNCH_CHECK();
+        timer_end(p, KC_VEC, 2.0 * sizeof(T) * n);
     }
     return AMGH_OK;
+}
+
+// algorithmic bytes of one V-cycle from level l down (value bytes vb), launch
+// by launch as vcyc runs it
+double vcycle_bytes(const amgh_problem *p, int l, int vb)
+{
+    const StateLevel &S = p->sl[l];
+    const double n = S.A.rows;
+    if (l == p->Ls - 1) return vb == 4 ? 4.0 * n * p->Acoarse.ld32 + 8.0 * n : 8.0 * n * n + 2.0 * vb * n;
+    const double step = spmv_bytes(S.A, vb) + 4.0 * vb * n;
+    double b = 4.0 * vb * n + (p->nsteps - 1) * step;                 // pre-smoothing from zero
+    b += spmv_bytes(S.A, vb) + vb * n;                                 // residual
+    b += spmv_bytes(S.St, vb) + 3.0 * vb * S.St.rows;                  // restriction (+ first coarse step)
+    b += vcycle_bytes(p, l + 1, vb);
+    b += spmv_bytes(S.S, vb) + vb * n;                                 // prolongation
+    return b + p->nsteps * step;                                       // post-smoothing
 }
 
 int vcycle_run(amgh_problem *p, int l0, int prec32, const void *b, void *x, const int *skip)
@@ -221,8 +239,10 @@ int vcycle_run(amgh_problem *p, int l0, int prec32, const void *b, void *x, cons
 // and every kernel returns at once when the loop's `done` flag is set, so the
 // host can replay a whole chunk of iterations before reading the flag back.
 template <typename F>
-static int capture(amgh_problem *p, F body, cudaGraphExec_t *exec, int *nodes)
+static int capture(amgh_problem *p, F body, cudaGraphExec_t *exec, int *nodes, double *bytes = nullptr)
 {
+    double local = 0.0;
+    ByteSink sink_(&local); // the body's launches are counted per replay by the caller
     cudaStream_t orig = p->stream;
     p->stream = p->cap_stream;
     p->capturing = 1;
@@ -248,6 +268,7 @@ static int capture(amgh_problem *p, F body, cudaGraphExec_t *exec, int *nodes)
     cudaGraphDestroy(g);
     if (e != cudaSuccess) return AMGH_ERR_CUDA;
     *nodes = (int)n;
+    if (bytes) *bytes = local;
     return AMGH_OK;
 }
 
@@ -278,7 +299,7 @@ static bool use_graphs(amgh_problem *p) { return !p->timer.enabled; }
 
 int graph_capture(amgh_problem *p, const std::function<int()> &body, cudaGraphExec_t *exec, int *nodes)
 {
-    return capture(p, body, exec, nodes);
+    return capture(p, body, exec, nodes, nullptr);
 }
 
 int graph_replay(amgh_problem *p, cudaGraphExec_t exec, int nodes) { return replay(p, exec, nodes); }
@@ -313,6 +334,19 @@ static int cg_body_start(amgh_problem *p, int l, int mode)
     return vcyc<float>(p, l, (const float *)S.cr, S.gz, &S.scal->done);
 }
 
+// The V-cycle that closes a CG iteration.  Its pending timings and bytes are
+// marked, so that for the iteration that converges -- whose V-cycle the
+// device skips -- they can be taken back.
+template <typename F>
+static int closing_vcycle(amgh_problem *p, F vc)
+{
+    p->timer.vc_mark = p->timer.ev.size();
+    const double before = g_byte_sink ? *g_byte_sink : 0.0;
+    int st = vc();
+    p->vc_bytes = g_byte_sink ? *g_byte_sink - before : 0.0;
+    return st;
+}
+
 static int cg_body_iter(amgh_problem *p, int l, int mode)
 {
     StateLevel &S = p->sl[l];
@@ -325,23 +359,23 @@ static int cg_body_iter(amgh_problem *p, int l, int mode)
         TRY((cg2_spmv<float, float>(p, S.red, S.A, S.gz, S.gr, S.gs, S.scal32, timed)));
         TRY((cg2_update<float, float>(p, S.red, n, S.gz, S.gs, S.gp, S.gq, S.gx, S.gr, nullptr, nullptr, S.scal32,
                                       pre ? S.fd : nullptr, pre ? S.fx : nullptr, S.invd32, p->cr[0])));
-        return vcyc<float>(p, l, S.gr, S.gz, &S.scal32->done, pre ? 1 : 0);
+        return closing_vcycle(p, [&] { return vcyc<float>(p, l, S.gr, S.gz, &S.scal32->done, pre ? 1 : 0); });
     }
     if (mode == 0) {
         TRY((cg2_spmv<double, double>(p, S.red, S.A, S.cz, S.cr, S.cs, S.scal, timed)));
         TRY((cg2_update<double, double>(p, S.red, n, S.cz, S.cs, S.cp, S.cq, S.cx, S.cr, nullptr, nullptr, S.scal,
                                         pre ? S.vd : nullptr, pre ? S.vx : nullptr, S.invd, p->cr[0])));
-        return vcyc<double>(p, l, S.cr, S.cz, &S.scal->done, pre ? 1 : 0);
+        return closing_vcycle(p, [&] { return vcyc<double>(p, l, S.cr, S.cz, &S.scal->done, pre ? 1 : 0); });
     }
     TRY(dfcg_spmv(p, S.red, S.A, S.gz, S.cr, S.cs, S.scal, timed));
     // on a smoothing level the update also takes the V-cycle's first step
     // (d and the level's other x buffer from the new residual)
     if (l < p->Ls - 1) {
         TRY(dfcg_update(p, S.red, n, S.gz, S.cs, S.cp, S.cq, S.cx, S.cr, S.scal, S.invd32, S.fd, S.fx, p->cr[0]));
-        return vcyc<float>(p, l, (const float *)S.cr, S.gz, &S.scal->done, 1);
+        return closing_vcycle(p, [&] { return vcyc<float>(p, l, (const float *)S.cr, S.gz, &S.scal->done, 1); });
     }
     TRY(dfcg_update(p, S.red, n, S.gz, S.cs, S.cp, S.cq, S.cx, S.cr, S.scal));
-    return vcyc<float>(p, l, (const float *)S.cr, S.gz, &S.scal->done);
+    return closing_vcycle(p, [&] { return vcyc<float>(p, l, (const float *)S.cr, S.gz, &S.scal->done); });
 }
 
 // PCG for A_l x = f preconditioned by V_l; the solution is left in S.cx (FP64
@@ -357,26 +391,54 @@ static int pcg_run(amgh_problem *p, int l, int mode, const void *f, double tol, 
     CgGraph &g = S.graph[mode];
     bool gr = use_graphs(p);
     if (gr && !g.iter) {
-        TRY(capture(p, [&] { return cg_body_start(p, l, mode); }, &g.start, &g.nodes_start));
-        TRY(capture(p, [&] { return cg_body_iter(p, l, mode); }, &g.iter, &g.nodes_iter));
+        TRY(capture(p, [&] { return cg_body_start(p, l, mode); }, &g.start, &g.nodes_start, &g.bytes_start));
+        TRY(capture(
+            p,
+            [&] {
+                int st = cg_body_iter(p, l, mode);
+                g.bytes_vc = p->vc_bytes;
+                return st;
+            },
+            &g.iter, &g.nodes_iter, &g.bytes_iter));
     }
+    // bytes of the start, of one iteration and of its closing V-cycle: the
+    // graphs' totals, or counted on the first direct launches
+    double b_start = g.bytes_start, b_iter = g.bytes_iter, b_vc = g.bytes_vc;
     if (gr) TRY(replay(p, g.start, g.nodes_start));
-    else TRY(cg_body_start(p, l, mode));
+    else {
+        b_start = 0.0;
+        ByteSink bs_(&b_start);
+        TRY(cg_body_start(p, l, mode));
+    }
     int *hint = mode == 1 ? &p->chunk_hint32[l] : &p->chunk_hint[l];
-    // first chunk: most of the previous solve's count (replays past convergence are no-ops)
-    int chunk = *hint > 1 ? (*hint * 7) / 8 : 1;
+    // first chunk: most of the previous solve's count (replays past convergence are
+    // no-ops); one iteration at a time while kernels are timed, so that no
+    // skipped launch is timed
+    int chunk = (*hint > 1 && gr) ? (*hint * 7) / 8 : 1;
     int enq = 0;
     CgScal h;
     for (;;) {
         for (int c = 0; c < chunk; c++) {
             if (gr) TRY(replay(p, g.iter, g.nodes_iter));
-            else TRY(cg_body_iter(p, l, mode));
+            else {
+                double b = 0.0;
+                {
+                    ByteSink bs_(&b);
+                    TRY(cg_body_iter(p, l, mode));
+                }
+                if (enq + c == 0) {
+                    b_iter = b;
+                    b_vc = p->vc_bytes;
+                }
+            }
         }
         enq += chunk;
         TRY(read_scal(p, sc, &h));
+        if (!gr && h.done) timer_drop_from(p, p->timer.vc_mark); // that V-cycle was skipped
         if (h.done || enq > maxit + 2) break;
-        chunk = h.iters / 8 > 1 ? h.iters / 8 : 1;
+        chunk = (h.iters / 8 > 1 && gr) ? h.iters / 8 : 1;
     }
+    if (h.iters > 0) count_bytes(b_start + (double)h.iters * b_iter - (h.done ? b_vc : 0.0));
     p->c_inner_lvl[l] += h.iters;
     if (h.iters > 0) *hint = h.iters;
     if (iters) *iters = h.iters;
@@ -398,8 +460,10 @@ int state_solve(amgh_problem *p, int l, const double *f, double *y, double tol, 
         int st = pcg_run(p, l, prec == 2 ? 2 : 0, f, tol, maxit, iters);
         if (prec == 2) TRY(df_to_double(p, n, S.cx, S.scal, y));
         else {
+            timer_begin(p, KC_VEC);
             pdl_launch(k_copy<double>, dim3(ceil_div(n, 256)), dim3(256), 0, p->stream, n, S.cx, y, nullptr);
             LAUNCH_CHECK();
+            timer_end(p, KC_VEC, 16.0 * n);
         }
         return st;
     }
@@ -450,20 +514,29 @@ int mass_solve(amgh_problem *p, int l, const double *b, double *x, int64_t *iter
         return cg2_update<double, double>(p, C.red, n, C.mz, C.ms, C.mp, C.mq, C.mx, C.mr, nullptr, C.mu_invdiag,
                                           C.mscal);
     };
-    if (gr && !g.iter) TRY(capture(p, body, &g.iter, &g.nodes_iter));
-    int chunk = p->mchunk_hint[l] > 1 ? (p->mchunk_hint[l] * 7) / 8 : 1;
+    if (gr && !g.iter) TRY(capture(p, body, &g.iter, &g.nodes_iter, &g.bytes_iter));
+    double b_iter = g.bytes_iter;
+    int chunk = (p->mchunk_hint[l] > 1 && gr) ? (p->mchunk_hint[l] * 7) / 8 : 1;
     int enq = 0;
     CgScal h;
     for (;;) {
         for (int c = 0; c < chunk; c++) {
             if (gr) TRY(replay(p, g.iter, g.nodes_iter));
-            else TRY(body());
+            else {
+                double b = 0.0;
+                {
+                    ByteSink bs_(&b);
+                    TRY(body());
+                }
+                if (enq + c == 0) b_iter = b;
+            }
         }
         enq += chunk;
         TRY(read_scal(p, C.mscal, &h));
         if (h.done || enq > p->sopts.mass_max_iter + 2) break;
-        chunk = h.iters / 8 > 1 ? h.iters / 8 : 1;
+        chunk = (h.iters / 8 > 1 && gr) ? h.iters / 8 : 1;
     }
+    count_bytes((double)h.iters * b_iter);
     p->c_mass_lvl[l] += h.iters;
     if (h.iters > 0) p->mchunk_hint[l] = h.iters;
     if (iters) *iters = h.iters;
@@ -471,8 +544,10 @@ int mass_solve(amgh_problem *p, int l, const double *b, double *x, int64_t *iter
     if (df) {
         TRY(df_to_double(p, n, C.mx, C.mscal, x));
     } else {
+        timer_begin(p, KC_VEC);
         pdl_launch(k_copy<double>, dim3(ceil_div(n, 256)), dim3(256), 0, p->stream, n, C.mx, x, nullptr);
         LAUNCH_CHECK();
+        timer_end(p, KC_VEC, 16.0 * n);
     }
     if (!h.done) return AMGH_ERR_NOT_CONVERGED;
     return cg_status(h);
@@ -486,9 +561,9 @@ int hessian_level(amgh_problem *p, int l, const double *v, double *hv)
     // level 0 is the outer CG's operator; levels >= 1 occur only inside the
     // preconditioner (Algorithm MLAS) and use the preconditioner tolerance
     double tol = l == 0 ? p->sopts.inner_tol : p->sopts.precond_tol;
-    TRY(spmv(p, C.Myu, v, C.t1, nullptr, 0));
+    TRY(spmv(p, C.Myu, v, C.t1, nullptr, KC_SPMV));
     TRY(state_solve(p, l, C.t1, C.ys, tol, nullptr));
-    TRY(spmv(p, S.My, C.ys, C.t2, nullptr, 0));
+    TRY(spmv(p, S.My, C.ys, C.t2, nullptr, KC_SPMV));
     TRY(state_solve(p, l, C.t2, C.ps, tol, nullptr));
     TRY(spmv2(p, C.Myut, C.ps, C.Mu, v, p->beta, hv, nullptr));
     if (l == 0) p->c_happ += 1;
@@ -508,14 +583,16 @@ int mlas_R(amgh_problem *p, int j, const double *b, double *out)
 {
     CtrlLevel &C = p->cl[j], &Cc = p->cl[j + 1];
     int n = C.Mu.rows;
-    TRY(spmv(p, C.Pt, b, Cc.bc, nullptr, 0));
+    TRY(spmv(p, C.Pt, b, Cc.bc, nullptr, KC_SPMV));
     TRY(mlas_Q(p, j + 1, Cc.bc, Cc.qc));
     TRY(mass_solve(p, j, b, C.w1, nullptr));
     TRY(mass_solve(p, j + 1, Cc.bc, Cc.wc, nullptr));
-    TRY(spmv(p, C.P, Cc.qc, C.ta, nullptr, 0));
-    TRY(spmv(p, C.P, Cc.wc, C.tb, nullptr, 0));
+    TRY(spmv(p, C.P, Cc.qc, C.ta, nullptr, KC_SPMV));
+    TRY(spmv(p, C.P, Cc.wc, C.tb, nullptr, KC_SPMV));
+    timer_begin(p, KC_VEC);
     pdl_launch(k_r_combine, dim3(ceil_div(n, 256)), dim3(256), 0, p->stream, n, C.ta, C.w1, C.tb, p->beta, out);
     LAUNCH_CHECK();
+    timer_end(p, KC_VEC, 32.0 * n);
     return AMGH_OK;
 }
 
@@ -581,9 +658,9 @@ int rhs_apply(amgh_problem *p, double *b)
 {
     StateLevel &S = p->sl[0];
     CtrlLevel &C = p->cl[0];
-    TRY(spmv(p, S.My, p->yd_state, C.t2, nullptr, 0));
+    TRY(spmv(p, S.My, p->yd_state, C.t2, nullptr, KC_SPMV));
     TRY(state_solve(p, 0, C.t2, C.ps, p->sopts.inner_tol, nullptr));
-    TRY(spmv(p, C.Myut, C.ps, b, nullptr, 0));
+    TRY(spmv(p, C.Myut, C.ps, b, nullptr, KC_SPMV));
     return AMGH_OK;
 }
 

@@ -587,9 +587,11 @@ int dense_gemv32(amgh_problem *p, int n, int ld, const float *inv32, const float
 {
     if (n == 0) return AMGH_OK;
     int g = ceil_div((int64_t)n * 32, TPB);
+    timer_begin(p, KC_COARSE);
     if (((uintptr_t)b & 15) == 0) pdl_launch(k_dense_gemv32<true>, dim3(g), dim3(TPB), 0, p->stream, n, ld, inv32, b, x, skip);
     else pdl_launch(k_dense_gemv32<false>, dim3(g), dim3(TPB), 0, p->stream, n, ld, inv32, b, x, skip);
     LAUNCH_CHECK();
+    timer_end(p, KC_COARSE, 4.0 * n * (double)n + 8.0 * n);
     return AMGH_OK;
 }
 
@@ -727,26 +729,26 @@ int prepare_tuned(amgh_problem *p, Arena &ar, DevCsr &a, int is_state_matrix)
 }
 
 template <typename T>
-int spmv_t(amgh_problem *p, const DevCsr &a, const T *x, T *y, const int *skip, int timed)
+int spmv_t(amgh_problem *p, const DevCsr &a, const T *x, T *y, const int *skip, int cls)
 {
     if (a.rows == 0) return AMGH_OK;
-    timer_begin(p, timed);
+    timer_begin(p, cls);
     MatView<T> A = view<T>(a);
     LAUNCH_TPR(k_spmv, T, A.tpr, A.rows, p->stream, A, x, y, skip);
     LAUNCH_CHECK();
-    timer_end(p, timed, spmv_bytes(a, sizeof(T)));
+    timer_end(p, cls, spmv_bytes(a, sizeof(T)));
     return AMGH_OK;
 }
 template int spmv_t<double>(amgh_problem *, const DevCsr &, const double *, double *, const int *, int);
 template int spmv_t<float>(amgh_problem *, const DevCsr &, const float *, float *, const int *, int);
 
-int spmv(amgh_problem *p, const DevCsr &a, const double *x, double *y, const int *skip, int timed)
+int spmv(amgh_problem *p, const DevCsr &a, const double *x, double *y, const int *skip, int cls)
 {
-    return spmv_t<double>(p, a, x, y, skip, timed);
+    return spmv_t<double>(p, a, x, y, skip, cls);
 }
-int spmv32(amgh_problem *p, const DevCsr &a, const float *x, float *y, const int *skip, int timed)
+int spmv32(amgh_problem *p, const DevCsr &a, const float *x, float *y, const int *skip, int cls)
 {
-    return spmv_t<float>(p, a, x, y, skip, timed);
+    return spmv_t<float>(p, a, x, y, skip, cls);
 }
 
 int bulk_set_first_polls(int polls)
@@ -778,12 +780,14 @@ int spmv2(amgh_problem *p, const DevCsr &a1, const double *x1, const DevCsr &a2,
     MatView<double> A1 = view<double>(a1), A2 = view<double>(a2);
     if (A1.tpr != A2.tpr) {
         // mixed layouts: two passes through y
-        TRY(spmv_t<double>(p, a2, x2, y, skip, 0));
+        TRY(spmv_t<double>(p, a2, x2, y, skip, KC_SPMV));
         TRY(vec_axpby_spmv(p, a1, x1, c, y, skip));
         return AMGH_OK;
     }
+    timer_begin(p, KC_SPMV);
     LAUNCH_TPR(k_spmv2, double, A1.tpr, A1.rows, p->stream, A1, x1, A2, x2, c, y, skip);
     LAUNCH_CHECK();
+    timer_end(p, KC_SPMV, spmv_bytes(a1, 8) + spmv_bytes(a2, 8) - 8.0 * a1.rows);
     return AMGH_OK;
 }
 
@@ -802,8 +806,10 @@ __global__ void k_spmv_axpy(MatView<T> A, const T *__restrict__ x, T c, T *__res
 int vec_axpby_spmv(amgh_problem *p, const DevCsr &a, const double *x, double c, double *y, const int *skip)
 {
     MatView<double> A = view<double>(a);
+    timer_begin(p, KC_SPMV);
     LAUNCH_TPR(k_spmv_axpy, double, A.tpr, A.rows, p->stream, A, x, c, y, skip);
     LAUNCH_CHECK();
+    timer_end(p, KC_SPMV, spmv_bytes(a, 8) + 8.0 * a.rows);
     return AMGH_OK;
 }
 
@@ -811,17 +817,20 @@ template <typename T>
 int cheb_first(amgh_problem *p, int n, const T *invd, const T *b, T *d, T *x, double c, const int *skip)
 {
     if (n == 0) return AMGH_OK;
+    timer_begin(p, KC_CHEB);
     pdl_launch(k_cheb_first<T>, dim3(ceil_div(n, TPB)), dim3(TPB), 0, p->stream, n, invd, b, d, x, (T)c, skip);
     LAUNCH_CHECK();
+    timer_end(p, KC_CHEB, 4.0 * sizeof(T) * n);
     return AMGH_OK;
 }
 
 template <typename T>
 int cheb_step(amgh_problem *p, const DevCsr &a, const T *invd, const T *b, const T *x, T *d, T *xn, double cdv,
-              double crv, const int *skip, int timed)
+              double crv, const int *skip, int lvl0)
 {
     if (a.rows == 0) return AMGH_OK;
-    timer_begin(p, timed);
+    const int cls = lvl0 ? KC_CHEB0 : KC_CHEB;
+    timer_begin(p, cls);
     MatView<T> A = view<T>(a);
     const void *ellcols = a.sl_ci16 ? (const void *)a.sl_ci16 : (const void *)a.sl_ci;
     if (sizeof(T) == sizeof(float) && a.tpr <= 1 && a.ellw > 0 && a.ellw <= ELL_MAX_W &&
@@ -841,19 +850,20 @@ int cheb_step(amgh_problem *p, const DevCsr &a, const T *invd, const T *b, const
     }
     LAUNCH_CHECK();
     // algorithmic bytes: matrix + x gather + b, invd, d (read+write), xn
-    timer_end(p, timed, spmv_bytes(a, sizeof(T)) + 4.0 * sizeof(T) * a.rows);
+    timer_end(p, cls, spmv_bytes(a, sizeof(T)) + 4.0 * sizeof(T) * a.rows);
     return AMGH_OK;
 }
 
 template <typename T>
-int residual(amgh_problem *p, const DevCsr &a, const T *b, const T *x, T *r, const int *skip, int timed)
+int residual(amgh_problem *p, const DevCsr &a, const T *b, const T *x, T *r, const int *skip, int lvl0)
 {
     if (a.rows == 0) return AMGH_OK;
-    timer_begin(p, timed);
+    const int cls = lvl0 ? KC_RESID0 : KC_RESID;
+    timer_begin(p, cls);
     MatView<T> A = view<T>(a);
     LAUNCH_TPR(k_residual, T, A.tpr, A.rows, p->stream, A, b, x, r, skip);
     LAUNCH_CHECK();
-    timer_end(p, timed, spmv_bytes(a, sizeof(T)) + sizeof(T) * (double)a.rows);
+    timer_end(p, cls, spmv_bytes(a, sizeof(T)) + sizeof(T) * (double)a.rows);
     return AMGH_OK;
 }
 
@@ -863,8 +873,12 @@ int restrict_first(amgh_problem *p, const DevCsr &st, const T *r, T *bc, const T
 {
     if (st.rows == 0) return AMGH_OK;
     MatView<T> A = view<T>(st);
+    const int cls = st.cols == p->m ? KC_RESTRICT0 : KC_RESTRICT;
+    timer_begin(p, cls);
     LAUNCH_TPR(k_restrict_first, T, A.tpr, A.rows, p->stream, A, r, bc, invd_c, d_c, x_c, (T)c0, skip);
     LAUNCH_CHECK();
+    // S^T r, then D_c^-1 read and d_c, x_c written on the coarse level
+    timer_end(p, cls, spmv_bytes(st, sizeof(T)) + 3.0 * sizeof(T) * st.rows);
     return AMGH_OK;
 }
 
@@ -873,8 +887,12 @@ int prolong_add(amgh_problem *p, const DevCsr &s, const T *e, T *x, const int *s
 {
     if (s.rows == 0) return AMGH_OK;
     MatView<T> A = view<T>(s);
+    const int cls = s.rows == p->m ? KC_PROLONG0 : KC_PROLONG;
+    timer_begin(p, cls);
     LAUNCH_TPR(k_prolong_add, T, A.tpr, A.rows, p->stream, A, e, x, skip);
     LAUNCH_CHECK();
+    // S e, and x read before it is written
+    timer_end(p, cls, spmv_bytes(s, sizeof(T)) + sizeof(T) * (double)s.rows);
     return AMGH_OK;
 }
 
@@ -882,8 +900,10 @@ template <typename T>
 int dense_gemv(amgh_problem *p, int n, const double *inv, const T *b, T *x, const int *skip)
 {
     if (n == 0) return AMGH_OK;
+    timer_begin(p, KC_COARSE);
     pdl_launch(k_dense_gemv<T>, dim3(ceil_div((int64_t)n * 32, TPB)), dim3(TPB), 0, p->stream, n, inv, b, x, skip);
     LAUNCH_CHECK();
+    timer_end(p, KC_COARSE, 8.0 * n * (double)n + 2.0 * sizeof(T) * n);
     return AMGH_OK;
 }
 

@@ -237,21 +237,44 @@ static cudaEvent_t pool_get(KernelTimer &t)
     return e;
 }
 
-void timer_begin(amgh_problem *p, int timed)
+thread_local double *g_byte_sink = nullptr;
+
+const char *kclass_name(int c)
 {
-    if (!timed || !p->timer.enabled || p->capturing) return;
+    static const char *names[KC_N] = {"cheb_step_l0", "cheb_step_coarse", "residual_l0", "residual_coarse",
+                                      "restrict_l0", "restrict_coarse", "prolong_l0", "prolong_coarse",
+                                      "cg_spmv_l0", "cg_spmv_coarse", "cg_update_l0", "cg_update_coarse",
+                                      "coarsest", "spmv_other", "vector_other"};
+    return c >= 0 && c < KC_N ? names[c] : "?";
+}
+
+void timer_begin(amgh_problem *p, int cls)
+{
+    if (cls < 0 || !p->timer.enabled || p->capturing) return;
     cudaEvent_t a = pool_get(p->timer);
     cudaEventRecord(a, p->stream);
     p->timer.ev.push_back(a);
 }
 
-void timer_end(amgh_problem *p, int timed, double bytes)
+void timer_end(amgh_problem *p, int cls, double bytes)
 {
-    if (!timed || !p->timer.enabled || p->capturing) return;
+    count_bytes(bytes);
+    if (cls < 0 || !p->timer.enabled || p->capturing) return;
     cudaEvent_t b = pool_get(p->timer);
     cudaEventRecord(b, p->stream);
     p->timer.ev.push_back(b);
+    p->timer.cls.push_back(cls);
     p->timer.pending_bytes.push_back(bytes);
+}
+
+void timer_drop_from(amgh_problem *p, size_t mark)
+{
+    KernelTimer &t = p->timer;
+    if (mark >= t.ev.size()) return;
+    for (size_t k = mark; k < t.ev.size(); k++) t.pool.push_back(t.ev[k]);
+    t.ev.resize(mark);
+    t.cls.resize(mark / 2);
+    t.pending_bytes.resize(mark / 2);
 }
 
 int timer_collect(amgh_problem *p)
@@ -262,12 +285,14 @@ int timer_collect(amgh_problem *p)
     for (size_t k = 0; k + 1 < t.ev.size(); k += 2) {
         float ms = 0.f;
         cudaEventElapsedTime(&ms, t.ev[k], t.ev[k + 1]);
-        t.ms += ms;
-        t.launches += 1;
-        t.bytes += t.pending_bytes[k / 2];
+        int c = t.cls[k / 2];
+        t.ms[c] += ms;
+        t.launches[c] += 1;
+        t.bytes[c] += t.pending_bytes[k / 2];
     }
     for (auto e : t.ev) t.pool.push_back(e);
     t.ev.clear();
+    t.cls.clear();
     t.pending_bytes.clear();
     return AMGH_OK;
 }

@@ -225,6 +225,29 @@ def test_loose_preconditioner_tolerance():
     assert rel(z, zo) <= 1e-6   # both sides solve to 1e-8 inside Q_0
 
 
+@pytest.mark.parametrize("name", ["lshape65", "cube9"])
+def test_long_row_prolongator_path_bit_exact(name):
+    """Prolongator rows that reach more aggregates than the per-thread register
+    list holds are built one block per row; with that capacity lowered to 2 every
+    row of every level takes the long-row path, and the hierarchy (S, P, coarse
+    A and M_u, aggregates) must still equal the oracle's bit for bit."""
+    from paper_2001_11533_gb300 import amgh
+    w, opts = _case(name)
+    try:
+        amgh.debug_limits(prol_row_cap=2)
+        prob = amgh.Problem.from_workload(w).amg_setup(**opts)
+    finally:
+        amgh.debug_limits(-1, -1, -1)
+    orc = Oracle(w, **{k: v for k, v in opts.items() if k in ("max_levels", "hessian_levels", "coarse_max")})
+    sz = orc.sizes()
+    assert prob.sizes["state"] == sz["state"] and prob.sizes["control"] == sz["control"]
+    for which, L in (("S", sz["Ls"] - 1), ("P", sz["Lc"] - 1), ("A", sz["Ls"]), ("Mu", sz["Lc"])):
+        for l in range(L):
+            for a, b in zip(prob.matrix(which, l)[:3], orc.matrix(which, l)[:3]):
+                assert np.array_equal(a, b), (which, l)
+    prob.close()
+
+
 @pytest.mark.parametrize("precision", [0, 2])
 def test_objective_and_gradient(precision):
     """J, y and the adjoint gradient against the oracle: FP64 path at inner 1e-13
@@ -431,14 +454,16 @@ def test_full_size_lshape_1025_control_parity():
         if prec == 2:
             yg, J = p.state_solve(cuda(uo))
             g = p.gradient(cuda(uo), yg)
-            errs["J"], errs["grad"] = abs(J - Jo) / abs(Jo), rel(host(g), go)
-            # at the optimum grad J = H u - b is the outer residual: compare to ||b||
+            # at the optimum grad J = H u - b is the outer residual, near zero:
+            # its error is measured against ||b||
             b = orc.rhs()
-            assert errs["J"] <= 1e-10 and np.linalg.norm(host(g) - go) <= 1e-9 * np.linalg.norm(b), errs
+            errs["J"] = abs(J - Jo) / abs(Jo)
+            errs["grad_vs_b"] = np.linalg.norm(host(g) - go) / np.linalg.norm(b)
+            assert errs["J"] <= 1e-10 and errs["grad_vs_b"] <= 1e-9, errs
             u8, _, info8 = p.solve(tol=1e-8, inner_tol=1e-10, mass_tol=1e-8, precond_tol=1e-8, want_y=False)
             errs["bench"] = rel(host(u8), uo)
             assert info8["final_relres"] <= 1.5e-8
-            assert errs["bench"] <= 1e-6, errs
+            assert errs["bench"] <= 1e-8, errs
         p.close()
     print("full-size control parity (relative 2-norm):", errs)
     orc_mod.set_threads(1)
