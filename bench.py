@@ -34,6 +34,10 @@ sys.path.insert(0, ROOT)
 # (read once, when CUDA is first initialised in this process)
 os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
 
+# kernel classes timed together in one instrumented pass (bit c = class c of
+# amgh_kernel_class_stats): each level-0 class alone, then all the others
+TIMING_GROUPS = [1 << 0, 1 << 2, 1 << 4, 1 << 6, 1 << 8, 1 << 10,
+                 ((1 << 15) - 1) & ~((1 << 0) | (1 << 2) | (1 << 4) | (1 << 6) | (1 << 8) | (1 << 10))]
 METRIC = "Hessian-CG time-to-1e-8 and Hessian matvecs/s, mixed vs FP64, same GB300"
 PRECISION = {"fp64": 0, "refine": 1, "mixed": 2}
 UNIT = "Hessian-matvecs/s"
@@ -70,6 +74,8 @@ def parse():
     ap.add_argument("--batch-steps", type=int, default=2)
     ap.add_argument("--forms", default="mixed,fp64,refine",
                     help="mixed = FP64 CG + FP32 V-cycles; fp64; refine = FP32 CG in FP64 refinement")
+    ap.add_argument("--fuse-coarse", type=int, default=0,
+                    help="0: V-cycle level by level; 2: levels of <= 262144 rows in one cooperative launch")
     ap.add_argument("--no-cube", action="store_true",
                     help="skip the 257^3 slab-cube block (mixed and FP64, >= 6 AMG levels)")
     ap.add_argument("--cube-N", type=int, default=257)
@@ -203,15 +209,15 @@ def run_amgh(args, rank, world, local):
             import torch.distributed as dist
             dist.barrier()
 
-    def step(precision, e2e=False, timing=False):
+    def step(precision, e2e=False, timing=0):
         if e2e:
             prob = amgh.Problem(w.dim, *pinned_np[:4], w.beta, pinned_np[4], on_device=False)
         else:
             prob = amgh.Problem(w.dim, dev[0], dev[1], dev[2], dev[3], w.beta, dev[4], on_device=True)
         prob.amg_setup(precision=precision, hessian_levels=args.hessian_levels, coarse_max=args.coarse_max,
-                       smooth_degree=args.degree, autotune=args.autotune, **xsetup)
+                       smooth_degree=args.degree, autotune=args.autotune, fuse_coarse=args.fuse_coarse, **xsetup)
         if timing:
-            prob.kernel_timing(True)
+            prob.kernel_timing_mask(timing)
         tols = dict(tol=1e-8, inner_tol=args.inner_tol, mass_tol=args.precond_tol, precond_tol=args.precond_tol,
                     **xsolve)
         if e2e:
@@ -251,12 +257,15 @@ def run_amgh(args, rank, world, local):
         torch.cuda.synchronize()
         barrier()
         launches = amgh.launch_count() - launches0
-        # instrumented pass (not timed): per-launch events on the fine-level kernels
-        for k in range(min(args.steps, 2)):
+        # instrumented passes (not timed): CUDA events around the launches of
+        # one group of kernel classes per pass (events keep a launch from
+        # overlapping its neighbours, so each level-0 class is timed alone)
+        for mask in TIMING_GROUPS:
             flush.zero_()
-            _, ks, _ = step(precision, timing=True)
-            for key in kstats:
-                kstats[key] += ks["chebl0"][key]
+            _, ks, _ = step(precision, timing=mask)
+            if mask & 1:
+                for key in kstats:
+                    kstats[key] += ks["chebl0"][key]
             for name, c in ks["classes"].items():
                 acc = classes.setdefault(name, {"launches": 0, "ms": 0.0, "bytes": 0.0})
                 for key in acc:
@@ -395,12 +404,12 @@ def run_cube(args, rank, world, local):
     tols = dict(tol=1e-8, inner_tol=args.inner_tol, mass_tol=args.precond_tol, precond_tol=args.precond_tol,
                 level_fallback=1)
 
-    def step(precision, timing=False):
+    def step(precision, timing=0):
         prob = amgh.Problem(w.dim, dev[0], dev[1], dev[2], dev[3], w.beta, dev[4], on_device=True)
         prob.amg_setup(precision=precision, coarse_max=args.cube_coarse_max, smooth_degree=args.degree,
-                       coarse_solve=2)
+                       coarse_solve=2, fuse_coarse=args.fuse_coarse)
         if timing:
-            prob.kernel_timing(True)
+            prob.kernel_timing_mask(timing)
         u, y, info = prob.solve(want_y=False, **tols)
         ks = {"chebl0": prob.kernel_stats(), "classes": prob.kernel_class_stats()} if timing else None
         sizes = prob.sizes
@@ -442,7 +451,8 @@ def run_cube(args, rank, world, local):
                "clocks": clk.summary()}
         if form == "mixed":
             flush.zero_()
-            _, ks, _ = step(precision, timing=True)
+            # kernels of 10 us and more here: one pass times every class
+            _, ks, _ = step(precision, timing=(1 << 15) - 1)
             res["roofline"] = roofline_from({"kstats": ks["chebl0"]}, args, kernel_note="level-0 Chebyshev "
                                             "smoother step on the 3D uniform-width SELL-32 matrix (int32 columns)",
                                             traffic=None)
@@ -495,10 +505,10 @@ def solve_phase(info):
 
 
 def kernel_table(classes):
-    """Per kernel class from the instrumented pass: launches, mean duration, achieved
+    """Per kernel class from the instrumented passes: launches, mean duration, achieved
     GB/s on algorithmic bytes, fraction of the measured HBM copy peak, and share of
-    the timed kernel time.  Classes without '_l0' work on coarse levels whose
-    operands fit in the 129 MB L2: their bytes/s is labelled L2-resident."""
+    the timed kernel time.  A coarse class moving under 32 MB per launch works on
+    operands that stay in the 129 MB L2: its bytes/s is labelled L2-resident."""
     peak, _ = hbm_peak()
     total = sum(c["ms"] for c in classes.values()) or 1.0
     out = {}
@@ -506,10 +516,11 @@ def kernel_table(classes):
         if c["launches"] == 0 or c["ms"] <= 0:
             continue
         gbs = c["bytes"] / (c["ms"] / 1000.0) / 1e9
+        per = c["bytes"] / c["launches"]
         out[name] = {"launches": c["launches"], "avg_us": round(1000.0 * c["ms"] / c["launches"], 2),
                      "share": round(c["ms"] / total, 4), "achieved_GBs": round(gbs, 1),
-                     "frac_of_hbm": round(gbs / peak, 4),
-                     "residency": "hbm" if name.endswith("_l0") else "l2-resident"}
+                     "frac_of_hbm": round(gbs / peak, 4), "mb_per_launch": round(per / 1e6, 2),
+                     "residency": "hbm" if (name.endswith("_l0") or per >= 32e6) else "l2-resident"}
     return out
 
 
@@ -713,7 +724,7 @@ def main():
                    "beta": w.beta, "kappa": kdesc, "tol": 1e-8,
                    "hessian_levels": args.hessian_levels, "coarse_max": args.coarse_max,
                    "chebyshev_degree": args.degree, "inner_tol": args.inner_tol,
-                   "autotune": args.autotune,
+                   "autotune": args.autotune, "fuse_coarse": args.fuse_coarse,
                    "precond_and_mass_tol": args.precond_tol,
                    "precision": forms[0], "parallelism": "replicas" if world > 1 else "single",
                    "l2": "256 MB buffer written between timed steps",

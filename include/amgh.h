@@ -85,10 +85,14 @@ typedef struct {
  *                  where H_{l-1} has at most 4096 dofs, else CG
  *  fuse_coarse     1 = FP32 V-cycles run their levels of at most 32768 rows
  *                  (down to the dense coarsest solve) as one launch on a
- *                  thread-block cluster; same result to the bit as 0 =
- *                  one launch per smoother step and transfer (the default:
- *                  on GB300 one cluster of 16 SMs is slower than the
- *                  whole-GPU kernels for a 9,585-row level)
+ *                  thread-block cluster; 2 = their levels of at most 262144
+ *                  rows as one cooperative launch over every SM, phases
+ *                  separated by a bounded software grid barrier (a barrier
+ *                  that gives up makes the call return AMGH_ERR_TIMEOUT;
+ *                  handles from amgh_problem_share, which run concurrently,
+ *                  use 0 instead); both give the same result to the bit as
+ *                  0 = one launch per smoother step and transfer (the
+ *                  default)
  *  autotune        1 = for every state matrix A_l of at least 4096 rows,
  *                  time four back-to-back FP32 Chebyshev steps in each layout
  *                  (SELL-32, or 2..32 lanes per CSR row; L2 flushed first
@@ -358,9 +362,13 @@ int amgh_reset_counters(amgh_problem *p);
  * summed algorithmic bytes (for a sparse product nnz*(v+i) + v*(rows+cols),
  * v = value bytes, i = index bytes, plus 4*(rows+1) for CSR row pointers;
  * vectors read and written once each).  Enabling or disabling clears them.
+ * The events around a launch keep it from overlapping its neighbours, so
+ * amgh_kernel_timing_mask times only the classes whose bit is set in mask
+ * (bit c = class c; 0 turns timing off), leaving the others to run as usual.
  * Errors: INVALID_ARG for a class out of range. */
 #define AMGH_KCLASSES 15
 int amgh_kernel_timing(amgh_problem *p, int enable);
+int amgh_kernel_timing_mask(amgh_problem *p, unsigned mask);
 int amgh_kernel_stats(amgh_problem *p, int64_t *launches, double *ms, double *bytes);
 int amgh_kernel_class_stats(amgh_problem *p, int cls, int64_t *launches, double *ms, double *bytes,
                             const char **name);

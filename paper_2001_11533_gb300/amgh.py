@@ -92,6 +92,7 @@ _SIGS = {
     "amgh_kernel_timing": ([_P, _I], _I),
     "amgh_kernel_stats": ([_P, _P, _P, _P], _I),
     "amgh_kernel_class_stats": ([_P, _I, _P, _P, _P, _P], _I),
+    "amgh_kernel_timing_mask": ([_P, C.c_uint], _I),
     "amgh_debug_limits": ([_I, _I, _I], _I),
     "amgh_launch_count": ([], _I64),
     "amgh_aggregate_noalloc": ([_I, _P, _P, _P, _D, _P, _P, _P], _I),
@@ -443,6 +444,10 @@ class Problem:
         n, ms, b = C.c_int64(), C.c_double(), C.c_double()
         check(lib().amgh_kernel_stats(self.h, C.byref(n), C.byref(ms), C.byref(b)), "amgh_kernel_stats")
         return {"launches": n.value, "ms": ms.value, "bytes": b.value}
+
+    def kernel_timing_mask(self, mask):
+        """Time only the kernel classes whose bit is set (amgh_kernel_timing_mask)."""
+        check(lib().amgh_kernel_timing_mask(self.h, C.c_uint(mask)), "amgh_kernel_timing_mask")
 
     def kernel_class_stats(self):
         """{class name: {launches, ms, bytes}} for every kernel class (amgh_kernel_class_stats)."""

@@ -443,7 +443,7 @@ extern "C" int amgh_amg_setup(amgh_problem *p, const amgh_amg_opts *opts)
     else amgh_amg_opts_default(&o);
     if (o.max_levels < 1 || o.max_levels > AMGH_MAXL || o.smooth_degree < 1 || o.smooth_degree > 16 ||
         o.coarse_max < 1 || !(o.theta >= 0.0) || (o.smoother != 0 && o.smoother != 1) ||
-        o.precision < 0 || o.precision > 2 || o.hessian_levels < 0 || o.coarse_solve < 0 || o.coarse_solve > 2 || (o.fuse_coarse != 0 && o.fuse_coarse != 1) ||
+        o.precision < 0 || o.precision > 2 || o.hessian_levels < 0 || o.coarse_solve < 0 || o.coarse_solve > 2 || (o.fuse_coarse < 0 || o.fuse_coarse > 2) ||
         (o.autotune != 0 && o.autotune != 1))
         return AMGH_ERR_INVALID_ARG;
     double t0 = now_s();
@@ -483,7 +483,9 @@ static int finish_call(amgh_problem *p, int st)
 {
     int s2 = sync_stream(p);
     int s3 = s2 == AMGH_OK ? bulk_timeout_check(p->stream) : s2;
-    if (s3 == AMGH_ERR_TIMEOUT) return s3;
+    int s4 = s2 == AMGH_OK ? grid_timeout_check(p) : s2;
+    if (s3 == AMGH_ERR_TIMEOUT || s4 == AMGH_ERR_TIMEOUT) return AMGH_ERR_TIMEOUT;
+    if (s3 == AMGH_OK) s3 = s4;
     return st != AMGH_OK ? st : s3;
 }
 
@@ -843,17 +845,23 @@ extern "C" int amgh_debug_limits(int bulk_first_polls, int mis_round_cap, int pr
     return bulk_set_first_polls(bulk_first_polls);
 }
 
-extern "C" int amgh_kernel_timing(amgh_problem *p, int enable)
+extern "C" int amgh_kernel_timing_mask(amgh_problem *p, unsigned mask)
 {
     if (!p) return AMGH_ERR_INVALID_ARG;
     TRY(timer_collect(p));
-    p->timer.enabled = enable ? 1 : 0;
+    p->timer.mask = mask & ((1u << KC_N) - 1u);
+    p->timer.enabled = p->timer.mask ? 1 : 0;
     for (int c = 0; c < KC_N; c++) {
         p->timer.launches[c] = 0;
         p->timer.ms[c] = 0.0;
         p->timer.bytes[c] = 0.0;
     }
     return AMGH_OK;
+}
+
+extern "C" int amgh_kernel_timing(amgh_problem *p, int enable)
+{
+    return amgh_kernel_timing_mask(p, enable ? (1u << KC_N) - 1u : 0u);
 }
 
 extern "C" int amgh_kernel_class_stats(amgh_problem *p, int cls, int64_t *launches, double *ms, double *bytes,

@@ -1,17 +1,26 @@
 // fused.cu -- the coarse end of the FP32 V-cycle in one launch.
 //
-// Below a few ten thousand rows a V-cycle level is a handful of kernels of a
-// few microseconds each, too small to fill the GPU and each paying a launch.
-// From the first level with at most FUSE_MAX_ROWS rows down to the dense
-// coarsest solve, the whole V-cycle (pre-smoothing, residual, restriction,
-// dense solve, prolongation, post-smoothing at every level, in the order of
-// vcyc in solver.cu) runs in one thread-block cluster; the phases are
-// separated by the hardware cluster barrier, which also orders the global
-// memory writes of one phase before the reads of the next.  Every row does the
-// same arithmetic as in the level-by-level kernels (the row sums and the
-// point-wise helpers of spmv.cuh), so the result is the same to the bit.
-// Vectors written inside the kernel are read through L2 (ld.global.cg); the
-// matrices, read-only, through the ordinary path.
+// Below a few hundred thousand rows a V-cycle level is a handful of kernels
+// of a few microseconds each, too small to fill the GPU and each paying a
+// launch.  From the first level small enough down to the dense coarsest
+// solve, the whole V-cycle (pre-smoothing, residual, restriction, dense
+// solve, prolongation, post-smoothing at every level, in the order of vcyc in
+// solver.cu) runs in one launch, in one of two scopes:
+//   cluster (fuse_coarse = 1): one thread-block cluster of 8 or 16 CTAs for
+//     levels of at most FUSE_MAX_ROWS rows, phases separated by the hardware
+//     cluster barrier;
+//   grid (fuse_coarse = 2): a cooperative launch of one 1024-thread block per
+//     SM for levels of at most GRID_FUSE_MAX_ROWS rows, phases separated by a
+//     software grid barrier (an arrival counter and a generation word in
+//     global memory) whose wait is bounded: a block that gives up raises
+//     g_grid_timeout and every block leaves at its next barrier, and the host
+//     reports AMGH_ERR_TIMEOUT.
+// Each barrier also orders the global memory writes of one phase before the
+// reads of the next.  Every row does the same arithmetic as in the
+// level-by-level kernels (the row sums and the point-wise helpers of
+// spmv.cuh), so the result is the same to the bit.  Vectors written inside the
+// kernel are read through L2 (ld.global.cg); the matrices, read-only, through
+// the ordinary path.
 #include <cooperative_groups.h>
 
 #include "internal.cuh"
@@ -21,6 +30,62 @@ namespace cg = cooperative_groups;
 
 #define FUSE_TPB 1024
 #define FUSE_MAX_ROWS 32768
+#define GRID_FUSE_MAX_ROWS 262144
+#define GRID_POLLS (1 << 20)
+
+// arrival counter and generation of the software grid barrier (zero at rest)
+struct GridBar {
+    unsigned count, gen;
+};
+__device__ int g_grid_timeout = 0;
+
+// Bounded grid-wide barrier: the last block to arrive resets the counter and
+// advances the generation; the others poll the generation (at most GRID_POLLS
+// times, leaving early once any block has given up).  Returns false if this
+// block gave up or another one has.
+__device__ __forceinline__ bool grid_sync(GridBar *gb, unsigned nblocks)
+{
+    __shared__ int ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned *vgen = &gb->gen;
+        volatile int *vto = &g_grid_timeout;
+        const unsigned g0 = *vgen;
+        int good = 1;
+        __threadfence(); // this block's writes of the phase before its arrival
+        if (atomicAdd(&gb->count, 1u) == nblocks - 1) {
+            atomicExch(&gb->count, 0u);
+            __threadfence();
+            atomicAdd(&gb->gen, 1u);
+        } else {
+            for (int polls = 0; *vgen == g0; polls++) {
+                if (polls >= GRID_POLLS || *vto) {
+                    atomicExch(&g_grid_timeout, 1);
+                    good = 0;
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+        ok = good;
+    }
+    __syncthreads();
+    return ok != 0;
+}
+
+struct ClusterScope {
+    __device__ bool sync()
+    {
+        cg::this_cluster().sync();
+        return true;
+    }
+};
+struct GridScope {
+    GridBar *gb;
+    unsigned nb;
+    __device__ bool sync() { return grid_sync(gb, nb); }
+};
 
 struct FusedLevel {
     MatView<float> A, St, S; // St: rows of level l+1; S: rows of level l
@@ -118,14 +183,10 @@ __device__ void ph_prolong(const FusedLevel &L, const float *e, float *x, int g,
     });
 }
 
-__global__ void __launch_bounds__(FUSE_TPB, 1)
-    k_vcycle_fused(const FusedCycle *__restrict__ fc, const float *b0, float *x0, int preinit,
-                   const int *__restrict__ skip)
+template <typename Scope>
+__device__ __forceinline__ void vcycle_body(const FusedCycle *__restrict__ fc, const float *b0, float *x0,
+                                            int preinit, int g, int T, Scope &cl)
 {
-    if (skip && *skip) return; // the flag is not written while this kernel runs: uniform
-    cg::cluster_group cl = cg::this_cluster();
-    const int T = (int)(cl.num_blocks() * blockDim.x);
-    const int g = (int)(cl.block_rank() * blockDim.x + threadIdx.x);
     const int c0 = fc->c0, last = fc->last, ns = fc->nsteps;
     float *cur[AMGH_MAXL], *nxt[AMGH_MAXL];
     // down-sweep: levels c0 .. last-1
@@ -141,13 +202,13 @@ __global__ void __launch_bounds__(FUSE_TPB, 1)
                 L.d[i] = v;
                 c[i] = v;
             }
-            cl.sync();
+            if (!cl.sync()) return;
         }
         for (int s = 1; s < ns; s++) {
 #define CALL(K) ph_cheb<K>(L, b, c, nx, fc->cd[s], fc->cr[s], g, T)
             TPR_DISPATCH(L.A.tpr, CALL)
 #undef CALL
-            cl.sync();
+            if (!cl.sync()) return;
             float *t = c;
             c = nx;
             nx = t;
@@ -155,12 +216,12 @@ __global__ void __launch_bounds__(FUSE_TPB, 1)
 #define CALL(K) ph_residual<K>(L, b, c, g, T)
         TPR_DISPATCH(L.A.tpr, CALL)
 #undef CALL
-        cl.sync();
+        if (!cl.sync()) return;
         const FusedLevel &C = fc->lv[l + 1];
 #define CALL(K) ph_restrict<K>(L, C, l + 1 < last, fc->cr[0], g, T)
         TPR_DISPATCH(L.St.tpr, CALL)
 #undef CALL
-        cl.sync();
+        if (!cl.sync()) return;
         cur[l] = c;
         nxt[l] = nx;
     }
@@ -173,7 +234,7 @@ __global__ void __launch_bounds__(FUSE_TPB, 1)
                                  : dense_row32<false>(fc->cinv, fc->cld, w, fc->cn, C.b, lane);
             if (lane == 0) C.x[w] = acc;
         }
-        cl.sync();
+        if (!cl.sync()) return;
     }
     // up-sweep: levels last-1 .. c0
     for (int l = last - 1; l >= c0; l--) {
@@ -184,21 +245,45 @@ __global__ void __launch_bounds__(FUSE_TPB, 1)
 #define CALL(K) ph_prolong<K>(L, fc->lv[l + 1].x, c, g, T)
         TPR_DISPATCH(L.S.tpr, CALL)
 #undef CALL
-        cl.sync();
+        if (!cl.sync()) return;
         for (int s = 0; s < ns; s++) {
 #define CALL(K) ph_cheb<K>(L, b, c, nx, s == 0 ? 0.f : fc->cd[s], fc->cr[s], g, T)
             TPR_DISPATCH(L.A.tpr, CALL)
 #undef CALL
-            cl.sync();
+            if (!cl.sync()) return;
             float *t = c;
             c = nx;
             nx = t;
         }
         if (c != x) {
             for (int i = g; i < L.n; i += T) x[i] = __ldcg(c + i);
-            cl.sync();
+            if (!cl.sync()) return;
         }
     }
+}
+
+__global__ void __launch_bounds__(FUSE_TPB, 1)
+    k_vcycle_fused(const FusedCycle *__restrict__ fc, const float *b0, float *x0, int preinit,
+                   const int *__restrict__ skip)
+{
+    if (skip && *skip) return; // the flag is not written while this kernel runs: uniform
+    cg::cluster_group cl = cg::this_cluster();
+    ClusterScope sc;
+    vcycle_body(fc, b0, x0, preinit, (int)(cl.block_rank() * blockDim.x + threadIdx.x),
+                (int)(cl.num_blocks() * blockDim.x), sc);
+}
+
+// the same V-cycle over the whole GPU: a cooperative launch of gridDim.x
+// blocks, all resident at once, phases separated by grid_sync
+__global__ void __launch_bounds__(FUSE_TPB, 1)
+    k_vcycle_grid(const FusedCycle *__restrict__ fc, const float *b0, float *x0, int preinit,
+                  const int *__restrict__ skip, GridBar *gb)
+{
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    if (skip && *skip) return; // uniform: the flag is not written while this kernel runs
+    GridScope sc{gb, gridDim.x};
+    vcycle_body(fc, b0, x0, preinit, (int)(blockIdx.x * blockDim.x + threadIdx.x), (int)(gridDim.x * blockDim.x),
+                sc);
 }
 
 // Fill the level table and pick the cluster size (16 CTAs where the GPU can
@@ -207,10 +292,18 @@ int fused_setup(amgh_problem *p)
 {
     p->fuse_c0 = -1;
     p->fuse_cluster = 0;
-    if (!p->aopts.fuse_coarse || p->Ls < 2) return AMGH_OK;
+    p->fuse_grid = 0;
+    p->fuse_bar = nullptr;
+    int mode = p->aopts.fuse_coarse;
+    // handles sharing a hierarchy run concurrently in the batch runtime: two
+    // grid-wide launches there could each hold part of the GPU, so they take
+    // the level-by-level kernels
+    if (mode == 2 && p->parent) mode = 0;
+    if (!mode || p->Ls < 2) return AMGH_OK;
+    const int maxrows = mode == 2 ? GRID_FUSE_MAX_ROWS : FUSE_MAX_ROWS;
     int c0 = -1;
     for (int l = 0; l < p->Ls - 1; l++)
-        if (p->sl[l].A.rows <= FUSE_MAX_ROWS) {
+        if (p->sl[l].A.rows <= maxrows) {
             c0 = l;
             break;
         }
@@ -248,6 +341,23 @@ int fused_setup(amgh_problem *p)
     TRY(p->harena.alloc(&dev, 1));
     CU(cudaMemcpyAsync(dev, &h, sizeof(h), cudaMemcpyHostToDevice, p->stream));
     CU(cudaStreamSynchronize(p->stream));
+    if (mode == 2) {
+        // one block per SM, if one fits (cooperative launch: all resident)
+        int dev_id = 0, sms = 0, per_sm = 0;
+        CU(cudaGetDevice(&dev_id));
+        CU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev_id));
+        CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_vcycle_grid, FUSE_TPB, 0));
+        if (per_sm < 1 || sms < 1) return AMGH_OK;
+        GridBar *bar = nullptr;
+        TRY(p->harena.alloc(&bar, 1));
+        CU(cudaMemsetAsync(bar, 0, sizeof(GridBar), p->stream));
+        CU(cudaStreamSynchronize(p->stream));
+        p->fuse_table = dev;
+        p->fuse_bar = bar;
+        p->fuse_grid = sms;
+        p->fuse_c0 = c0;
+        return AMGH_OK;
+    }
     // cluster size: 16 if it can be scheduled, else 8
     int cluster = 0;
     for (int want : {16, 8}) {
@@ -280,8 +390,38 @@ int fused_setup(amgh_problem *p)
     return AMGH_OK;
 }
 
+int grid_timeout_check(amgh_problem *p)
+{
+    int h = 0;
+    CU(cudaMemcpyFromSymbolAsync(&h, g_grid_timeout, sizeof(int), 0, cudaMemcpyDeviceToHost, p->stream));
+    CU(cudaStreamSynchronize(p->stream));
+    if (!h) return AMGH_OK;
+    int zero = 0;
+    CU(cudaMemcpyToSymbolAsync(g_grid_timeout, &zero, sizeof(int), 0, cudaMemcpyHostToDevice, p->stream));
+    if (p->fuse_bar) CU(cudaMemsetAsync(p->fuse_bar, 0, sizeof(GridBar), p->stream));
+    CU(cudaStreamSynchronize(p->stream));
+    return AMGH_ERR_TIMEOUT;
+}
+
 int fused_vcycle(amgh_problem *p, const float *b, float *x, int preinit, const int *skip)
 {
+    if (p->fuse_grid > 0) {
+        cudaLaunchConfig_t cfg = {};
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeCooperative;
+        attr[0].val.cooperative = 1;
+        cfg.gridDim = dim3(p->fuse_grid, 1, 1);
+        cfg.blockDim = dim3(FUSE_TPB, 1, 1);
+        cfg.stream = p->stream;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        timer_begin(p, KC_COARSE);
+        CU(cudaLaunchKernelEx(&cfg, k_vcycle_grid, (const FusedCycle *)p->fuse_table, b, x, preinit, skip,
+                              (GridBar *)p->fuse_bar));
+        amgh_count_launch();
+        timer_end(p, KC_COARSE, vcycle_bytes(p, p->fuse_c0, 4));
+        return AMGH_OK;
+    }
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;

@@ -276,6 +276,7 @@ const char *kclass_name(int c);
 
 struct KernelTimer {
     int enabled = 0;
+    unsigned mask = 0; // classes timed (bit c = class c)
     std::vector<cudaEvent_t> ev; // pairs
     std::vector<int> cls;        // class of each pending pair
     std::vector<double> pending_bytes;
@@ -334,6 +335,8 @@ struct amgh_problem {
     // fused coarse end of the FP32 V-cycle (fused.cu): first fused level or -1
     int fuse_c0 = -1, fuse_cluster = 0;
     void *fuse_table = nullptr;
+    int fuse_grid = 0;       // > 0: grid scope, blocks of the cooperative launch
+    void *fuse_bar = nullptr; // its barrier state
     StateLevel sl[AMGH_MAXL];
     CtrlLevel cl[AMGH_MAXL];
     Dense Acoarse;  // inverse of A[Ls-1]
@@ -423,6 +426,9 @@ int dense_gemv(amgh_problem *p, int n, const double *inv, const T *b, T *x, cons
 // fused.cu: table and cluster size of the fused coarse V-cycle; one launch of it
 int fused_setup(amgh_problem *p);
 int fused_vcycle(amgh_problem *p, const float *b, float *x, int preinit, const int *skip);
+// AMGH_ERR_TIMEOUT (flag cleared, the problem's barrier reset) if a grid
+// barrier of the fused V-cycle gave up
+int grid_timeout_check(amgh_problem *p);
 // x = inv b with the FP32 copy (rows padded to ld, 16-byte aligned)
 int dense_gemv32(amgh_problem *p, int n, int ld, const float *inv32, const float *b, float *x, const int *skip);
 // FP32 copy of a dense inverse with rows padded to a multiple of 4

@@ -250,7 +250,7 @@ const char *kclass_name(int c)
 
 void timer_begin(amgh_problem *p, int cls)
 {
-    if (cls < 0 || !p->timer.enabled || p->capturing) return;
+    if (cls < 0 || !p->timer.enabled || p->capturing || !(p->timer.mask >> cls & 1u)) return;
     cudaEvent_t a = pool_get(p->timer);
     cudaEventRecord(a, p->stream);
     p->timer.ev.push_back(a);
@@ -259,7 +259,7 @@ void timer_begin(amgh_problem *p, int cls)
 void timer_end(amgh_problem *p, int cls, double bytes)
 {
     count_bytes(bytes);
-    if (cls < 0 || !p->timer.enabled || p->capturing) return;
+    if (cls < 0 || !p->timer.enabled || p->capturing || !(p->timer.mask >> cls & 1u)) return;
     cudaEvent_t b = pool_get(p->timer);
     cudaEventRecord(b, p->stream);
     p->timer.ev.push_back(b);
