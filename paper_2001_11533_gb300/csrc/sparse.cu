@@ -500,133 +500,6 @@ __global__ void __launch_bounds__(32 * ELL_SLICES)
     xn[row] = xv2;
 }
 
-// ------------------------------------------------------------------ pipelined staged smoother
-// The level-0 Chebyshev step as a resident grid: each block walks chunks of
-// PIPE_SLICES slices (c = blockIdx.x, c + gridDim.x, ...) through two
-// shared-memory stages.  While the threads work on chunk k out of one stage,
-// the copy engine fills the other with chunk k+1 (one bulk copy of its values
-// and one of its column offsets on that stage's mbarrier), so the matrix
-// stream never waits for the gathers.  Stage s is used by chunks k = s, s+2,
-// ..., its barrier phase parity flipping with each use.  Every wait is
-// bounded: if any thread of the block misses its copy, the block (by a vote)
-// raises g_bulk_timeout, waits for every copy it issued to land (the drain
-// limit), and leaves.  Per row the arithmetic and summation order are those
-// of k_cheb_step_ell and row_sum, so the results are identical to the bit.
-#ifndef PIPE_SLICES
-#define PIPE_SLICES 4
-#endif
-#ifndef PIPE_BLOCKS_PER_SM
-#define PIPE_BLOCKS_PER_SM 12
-#endif
-// the pipelined kernel serves levels with more than PIPE_MIN_WAVES chunks per
-// resident block (smaller ones take k_cheb_step_ell, one chunk per block)
-#ifndef PIPE_MIN_WAVES
-#define PIPE_MIN_WAVES 2
-#endif
-// register budget: 64K / (32 PIPE_SLICES x PIPE_MIN_BLOCKS) per thread
-#ifndef PIPE_MIN_BLOCKS
-#define PIPE_MIN_BLOCKS (PIPE_SLICES == 4 ? 12 : 6)
-#endif
-
-template <bool D16>
-__global__ void __launch_bounds__(32 * PIPE_SLICES, PIPE_MIN_BLOCKS)
-    k_cheb_step_pipe(int rows, int nslices, int W, const float *__restrict__ v, const void *__restrict__ cols,
-                     const float *__restrict__ invd, const float *__restrict__ b, const float *__restrict__ x,
-                     float *__restrict__ d, float *__restrict__ xn, float cdv, float crv, const int *__restrict__ skip)
-{
-    pdl_enter();
-    if (skip && *skip) return;
-    extern __shared__ __align__(16) unsigned char pipe_sm[];
-    __shared__ __align__(8) uint64_t bar[2];
-    constexpr uint32_t ib = D16 ? 2 : 4;
-    const uint32_t stage_ent = (uint32_t)PIPE_SLICES * 32 * W;
-    // stage st: values at pipe_sm + st * 4 stage_ent, offsets after both value stages
-    auto sv = [&](int st) { return (float *)pipe_sm + st * stage_ent; };
-    auto sc = [&](int st) { return pipe_sm + 8 * (size_t)stage_ent + st * stage_ent * ib; };
-    const int nchunks = (nslices + PIPE_SLICES - 1) / PIPE_SLICES;
-    if (threadIdx.x == 0) {
-        mbar_init(&bar[0], 1);
-        mbar_init(&bar[1], 1);
-    }
-    __syncthreads();
-    auto issue = [&](int c, int st) { // thread 0: chunk c into stage st
-        const int s0 = c * PIPE_SLICES;
-        const uint32_t nent = (uint32_t)min(PIPE_SLICES, nslices - s0) * 32 * W;
-        const int64_t first = (int64_t)s0 * 32 * W;
-        mbar_expect_tx(&bar[st], nent * (4 + ib));
-        bulk_g2s(sv(st), v + first, nent * 4, &bar[st]);
-        bulk_g2s(sc(st), (const unsigned char *)cols + first * ib, nent * ib, &bar[st]);
-    };
-    if (threadIdx.x == 0 && (int)blockIdx.x < nchunks) issue(blockIdx.x, 0);
-    const int polls = *(volatile int *)&g_bulk_first_polls;
-    int k = 0;
-    for (int c = blockIdx.x; c < nchunks; c += gridDim.x, k++) {
-        const int st = k & 1;
-        const uint32_t parity = (uint32_t)(k >> 1) & 1u;
-        const int cn = c + gridDim.x;
-        // the other stage was last read in iteration k-1, closed by a barrier
-        if (threadIdx.x == 0 && cn < nchunks) issue(cn, st ^ 1);
-        const int row = c * PIPE_SLICES * 32 + (int)threadIdx.x;
-        const bool ok = row < rows;
-        float br = 0.f, ir = 0.f, dr = 0.f, xr = 0.f;
-        if (ok) {
-            br = b[row];
-            ir = invd[row];
-            dr = d[row];
-            xr = x[row];
-        }
-        const bool got = mbar_wait(&bar[st], parity, polls);
-        if (!__syncthreads_and(got)) {
-            if (threadIdx.x == 0) atomicExch(&g_bulk_timeout, 1);
-            mbar_wait(&bar[st], parity, BULK_DRAIN_POLLS);
-            if (cn < nchunks) mbar_wait(&bar[st ^ 1], (uint32_t)((k + 1) >> 1) & 1u, BULK_DRAIN_POLLS);
-            return;
-        }
-        if (ok) {
-            const int base = ((int)threadIdx.x >> 5) * 32 * W + ((int)threadIdx.x & 31);
-            const float *vs = sv(st);
-            const unsigned char *cs = sc(st);
-            float xv[ELL_MAX_W];
-#pragma unroll
-            for (int j = 0; j < ELL_MAX_W; j++) {
-                if (j < W) {
-                    int kk = base + 32 * j;
-                    int col = D16 ? row + (int)((const short *)cs)[kk] : ((const int *)cs)[kk];
-                    xv[j] = __ldg(&x[col]);
-                }
-            }
-            float ax = 0.f;
-#pragma unroll
-            for (int j = 0; j < ELL_MAX_W; j++)
-                if (j < W) ax += vs[base + 32 * j] * xv[j];
-            float dn, xv2;
-            cheb_point(br, ax, ir, dr, xr, cdv, crv, dn, xv2);
-            d[row] = dn;
-            xn[row] = xv2;
-        }
-        __syncthreads(); // stage st is free for the copy two chunks on
-    }
-}
-
-// blocks of k_cheb_step_pipe resident on the current device with `smem`
-// bytes of stages each (at most PIPE_BLOCKS_PER_SM per SM), 0 if none fits
-static int pipe_resident(bool d16, size_t smem)
-{
-    const void *fn = d16 ? (const void *)k_cheb_step_pipe<true> : (const void *)k_cheb_step_pipe<false>;
-    if (smem > 48 * 1024 &&
-        cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
-        cudaGetLastError();
-        return 0;
-    }
-    int dev = 0, sms = 0, per_sm = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 32 * PIPE_SLICES, smem) != cudaSuccess) {
-        cudaGetLastError();
-        return 0;
-    }
-    return sms * std::min(per_sm, PIPE_BLOCKS_PER_SM);
-}
-
 template <typename T, int TPR>
 __global__ void k_residual(MatView<T> A, const T *__restrict__ b, const T *__restrict__ x, T *__restrict__ res,
                            const int *__restrict__ skip)
@@ -962,32 +835,16 @@ int cheb_step(amgh_problem *p, const DevCsr &a, const T *invd, const T *b, const
     const void *ellcols = a.sl_ci16 ? (const void *)a.sl_ci16 : (const void *)a.sl_ci;
     if (sizeof(T) == sizeof(float) && a.tpr <= 1 && a.ellw > 0 && a.ellw <= ELL_MAX_W &&
         ((uintptr_t)a.sl_v32 & 15) == 0 && ((uintptr_t)ellcols & 15) == 0) {
+        size_t smem = (size_t)ELL_SLICES * 32 * a.ellw * (sizeof(float) + (a.sl_ci16 ? 2 : 4));
+        dim3 g(ceil_div(a.nslices, ELL_SLICES)), blk(32 * ELL_SLICES);
         const float *fi = (const float *)invd, *fb = (const float *)b, *fx = (const float *)x;
         float *fd = (float *)d, *fxn = (float *)xn;
-        const int ib = a.sl_ci16 ? 2 : 4;
-        const int nchunks = ceil_div(a.nslices, PIPE_SLICES);
-        const size_t psmem = 2 * (size_t)PIPE_SLICES * 32 * a.ellw * (sizeof(float) + ib);
-        const int president = pipe_resident(a.sl_ci16 != nullptr, psmem);
-        if (president > 0 && nchunks > PIPE_MIN_WAVES * president) {
-            // large level: resident grid, double-buffered stages
-            size_t smem = psmem;
-            dim3 g(president), blk(32 * PIPE_SLICES);
-            if (a.sl_ci16)
-                pdl_launch(k_cheb_step_pipe<true>, g, blk, smem, p->stream, a.rows, a.nslices, a.ellw, a.sl_v32,
-                           (const void *)a.sl_ci16, fi, fb, fx, fd, fxn, (float)cdv, (float)crv, skip);
-            else
-                pdl_launch(k_cheb_step_pipe<false>, g, blk, smem, p->stream, a.rows, a.nslices, a.ellw, a.sl_v32,
-                           (const void *)a.sl_ci, fi, fb, fx, fd, fxn, (float)cdv, (float)crv, skip);
-        } else {
-            size_t smem = (size_t)ELL_SLICES * 32 * a.ellw * (sizeof(float) + ib);
-            dim3 g(ceil_div(a.nslices, ELL_SLICES)), blk(32 * ELL_SLICES);
-            if (a.sl_ci16)
-                pdl_launch(k_cheb_step_ell<true>, g, blk, smem, p->stream, a.rows, a.nslices, a.ellw, a.sl_v32,
-                           (const void *)a.sl_ci16, fi, fb, fx, fd, fxn, (float)cdv, (float)crv, skip);
-            else
-                pdl_launch(k_cheb_step_ell<false>, g, blk, smem, p->stream, a.rows, a.nslices, a.ellw, a.sl_v32,
-                           (const void *)a.sl_ci, fi, fb, fx, fd, fxn, (float)cdv, (float)crv, skip);
-        }
+        if (a.sl_ci16)
+            pdl_launch(k_cheb_step_ell<true>, g, blk, smem, p->stream, a.rows, a.nslices, a.ellw, a.sl_v32,
+                       (const void *)a.sl_ci16, fi, fb, fx, fd, fxn, (float)cdv, (float)crv, skip);
+        else
+            pdl_launch(k_cheb_step_ell<false>, g, blk, smem, p->stream, a.rows, a.nslices, a.ellw, a.sl_v32,
+                       (const void *)a.sl_ci, fi, fb, fx, fd, fxn, (float)cdv, (float)crv, skip);
     } else {
         LAUNCH_TPR(k_cheb_step, T, A.tpr, A.rows, p->stream, A, invd, b, x, d, xn, (T)cdv, (T)crv, skip);
     }

@@ -41,30 +41,6 @@ def test_staged_copy_timeout_is_reported_then_recovers():
     prob.close()
 
 
-def test_pipelined_staged_copy_timeout_is_reported_then_recovers():
-    """The same on the 1025^2 L-shape, whose level-0 smoother runs the
-    double-buffered resident-grid kernel (two stages of bulk copies in flight
-    per block): the block votes, drains both stages and leaves."""
-    import torch
-    from paper_2001_11533_gb300 import amgh
-    w = W.lshape_checkerboard(N=1025)
-    prob = amgh.Problem.from_workload(w).amg_setup(precision=2, coarse_max=1000)
-    b = torch.from_numpy(np.random.default_rng(4).standard_normal(prob.sizes["m"])).cuda()
-    prob.set_solve_opts(inner_max_iter=40)
-    clean, it = prob.state_solve_level(0, b, 1e-8)
-    clean = clean.cpu().numpy()
-    try:
-        amgh.debug_limits(bulk_first_polls=0)
-        with pytest.raises(amgh.AmghError) as e:
-            prob.state_solve_level(0, b, 1e-8)
-        assert e.value.code == TIMEOUT
-    finally:
-        amgh.debug_limits(-1, -1)
-    again, it2 = prob.state_solve_level(0, b, 1e-8)
-    assert it2 == it and np.array_equal(again.cpu().numpy(), clean)
-    prob.close()
-
-
 def test_mis_round_cap_is_reported_then_recovers():
     from paper_2001_11533_gb300 import amgh
     w = W.unit_square(65, jitter=0.2, cfg=142)
