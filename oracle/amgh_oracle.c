@@ -85,6 +85,8 @@ typedef struct {
     csr_t Kfull, Mfull;
     /* options */
     int max_levels, hess_levels, coarse_max, smoother, degree, smooth_p;
+    int aggressive; /* level 0 aggregated twice (aggregates of aggregates) */
+    int geometric;  /* nested structured-grid interpolation instead of AMG */
     double theta;
     int setup_done;
     /* state hierarchy */
@@ -721,6 +723,87 @@ static int prolongator(const csr_t *a, const int *agg, int nagg, int smooth, csr
     return ORC_OK;
 }
 
+/*
+ * Aggressive first-level coarsening (Sec. 5.1 uses it for the first level
+ * of BoomerAMG; reading for smoothed aggregation): aggregate A, form the
+ * tentative (unsmoothed) Galerkin matrix S_hat^T A S_hat of those aggregates,
+ * aggregate that matrix with the next level's threshold, and give every
+ * vertex the aggregate of its aggregate.
+ */
+static int aggregate_aggressive(const csr_t *a, double theta2, int *agg, int *nagg_out)
+{
+    int n = a->rows, n1 = 0, n2 = 0;
+    int *agg1 = malloc(sizeof(int) * (size_t)(n > 0 ? n : 1));
+    if (!agg1) return ORC_OOM;
+    int st = aggregate(a, theta2, agg1, &n1, NULL);
+    if (st) return st;
+    csr_t sh = {0}, sht = {0}, t = {0};
+    if ((st = prolongator(a, agg1, n1, 0, &sh))) return st;
+    if ((st = csr_transpose(&sh, &sht))) return st;
+    if ((st = galerkin(&sht, a, &sh, 1, &t))) return st;
+    int *agg2 = malloc(sizeof(int) * (size_t)(n1 > 0 ? n1 : 1));
+    if (!agg2) return ORC_OOM;
+    if ((st = aggregate(&t, theta2 * 0.25, agg2, &n2, NULL))) return st;
+    for (int i = 0; i < n; i++) agg[i] = agg2[agg1[i]];
+    *nagg_out = n2;
+    free(agg1);
+    free(agg2);
+    csr_free(&sh);
+    csr_free(&sht);
+    csr_free(&t);
+    return ORC_OK;
+}
+
+/*
+ * Geometric hierarchy of the structured N x N square grid (vertex i + N j,
+ * squares split along the (i,j)-(i+1,j+1) diagonal; the setting of the
+ * geometric comparison of Sec. 5.4): the coarse grid takes every other
+ * vertex, Nc = (N+1)/2, and the P1 interpolation from it is
+ *   (2I, 2J)           <- coarse (I, J)                         weight 1
+ *   (2I+1, 2J)         <- (I, J), (I+1, J)                      weights 1/2
+ *   (2I, 2J+1)         <- (I, J), (I, J+1)                      weights 1/2
+ *   (2I+1, 2J+1)       <- (I, J), (I+1, J+1) (the diagonal)     weights 1/2.
+ * The state interpolation is its restriction to interior rows and columns.
+ */
+static int geometric_interp(int N, csr_t *p)
+{
+    int Nc = (N + 1) / 2, n = N * N;
+    p->rows = n;
+    p->cols = Nc * Nc;
+    p->rp = xcalloc((size_t)n + 1, sizeof(int));
+    p->ci = xcalloc((size_t)2 * n, sizeof(int));
+    p->v = xcalloc((size_t)2 * n, sizeof(double));
+    if (!p->rp || !p->ci || !p->v) return ORC_OOM;
+    int k = 0;
+    for (int j = 0; j < N; j++)
+        for (int i = 0; i < N; i++) {
+            int I = i / 2, J = j / 2;
+            if (i % 2 == 0 && j % 2 == 0) {
+                p->ci[k] = I + Nc * J;
+                p->v[k++] = 1.0;
+            } else {
+                int I2 = I + (i % 2), J2 = J + (j % 2);
+                p->ci[k] = I + Nc * J;
+                p->v[k++] = 0.5;
+                p->ci[k] = I2 + Nc * J2;
+                p->v[k++] = 0.5;
+            }
+            p->rp[i + N * j + 1] = k;
+        }
+    return ORC_OK;
+}
+
+/* map of the N x N grid's vertices to interior numbering (-1 on the boundary) */
+static int *grid_interior(int N)
+{
+    int *map = malloc(sizeof(int) * (size_t)N * N), m = 0;
+    if (!map) return NULL;
+    for (int j = 0; j < N; j++)
+        for (int i = 0; i < N; i++)
+            map[i + N * j] = (i > 0 && j > 0 && i < N - 1 && j < N - 1) ? m++ : -1;
+    return map;
+}
+
 /* ---------------------------------------------------------------- dense */
 
 /* lower Cholesky factor of the n x n matrix g (row-major); INDEFINITE on a
@@ -1228,6 +1311,42 @@ int orc_setup(void *h, int max_levels, int hessian_levels, double theta, int coa
     if ((st = extract(&o->Kfull, all, o->n, all, o->n, &o->KN[0]))) return st;
     if ((st = extract(&o->Mfull, all, o->n, all, o->n, &o->Mu[0]))) return st;
     free(all);
+    if (o->geometric) {
+        /* the mesh must be the structured square grid with its whole boundary Dirichlet */
+        int N = (int)lround(sqrt((double)o->n));
+        if (o->dim != 2 || N * N != o->n || N < 3) return ORC_INVALID;
+        int *bmap = grid_interior(N);
+        for (int v = 0; v < o->n; v++)
+            if ((bmap[v] >= 0) != (o->state_of_vertex[v] >= 0)) return ORC_INVALID;
+        free(bmap);
+        o->Ls = o->Lc = 1;
+        for (int l = 0; l + 1 < max_levels && N >= 5 && N % 2 == 1 && o->KN[l].rows > coarse_max; l++) {
+            int Nc = (N + 1) / 2;
+            int *fi = grid_interior(N), *ci = grid_interior(Nc);
+            int *allc = malloc(sizeof(int) * (size_t)Nc * Nc);
+            for (int v = 0; v < Nc * Nc; v++) allc[v] = v;
+            csr_t pg = {0};
+            if ((st = geometric_interp(N, &pg))) return st;
+            if ((st = extract(&pg, fi, (N - 2) * (N - 2), ci, (Nc - 2) * (Nc - 2), &o->S[l]))) return st;
+            int *allf = malloc(sizeof(int) * (size_t)N * N);
+            for (int v = 0; v < N * N; v++) allf[v] = v;
+            if ((st = extract(&pg, allf, N * N, allc, Nc * Nc, &o->P[l]))) return st;
+            free(allf);
+            free(allc);
+            free(fi);
+            free(ci);
+            csr_free(&pg);
+            if ((st = csr_transpose(&o->S[l], &o->St[l]))) return st;
+            if ((st = galerkin(&o->St[l], &o->A[l], &o->S[l], 1, &o->A[l + 1]))) return st;
+            if ((st = galerkin(&o->St[l], &o->My[l], &o->S[l], 1, &o->My[l + 1]))) return st;
+            if ((st = csr_transpose(&o->P[l], &o->Pt[l]))) return st;
+            if ((st = galerkin(&o->Pt[l], &o->KN[l], &o->P[l], 1, &o->KN[l + 1]))) return st;
+            if ((st = galerkin(&o->Pt[l], &o->Mu[l], &o->P[l], 1, &o->Mu[l + 1]))) return st;
+            o->Ls = o->Lc = l + 2;
+            N = Nc;
+        }
+        goto hierarchies_done;
+    }
     /* coarsen: strength threshold theta at level 0, halved per level */
     double th = theta;
     o->Ls = 1;
@@ -1235,7 +1354,9 @@ int orc_setup(void *h, int max_levels, int hessian_levels, double theta, int coa
         int n = o->A[l].rows;
         int *agg = malloc(sizeof(int) * (size_t)n);
         int nagg = 0;
-        if ((st = aggregate(&o->A[l], th * th, agg, &nagg, NULL))) return st;
+        if (l == 0 && o->aggressive) st = aggregate_aggressive(&o->A[l], th * th, agg, &nagg);
+        else st = aggregate(&o->A[l], th * th, agg, &nagg, NULL);
+        if (st) return st;
         if ((double)n < 1.2 * (double)nagg) { free(agg); break; }
         o->sagg[l] = agg;
         o->snagg[l] = nagg;
@@ -1252,7 +1373,9 @@ int orc_setup(void *h, int max_levels, int hessian_levels, double theta, int coa
         int n = o->KN[l].rows;
         int *agg = malloc(sizeof(int) * (size_t)n);
         int nagg = 0;
-        if ((st = aggregate(&o->KN[l], th * th, agg, &nagg, NULL))) return st;
+        if (l == 0 && o->aggressive) st = aggregate_aggressive(&o->KN[l], th * th, agg, &nagg);
+        else st = aggregate(&o->KN[l], th * th, agg, &nagg, NULL);
+        if (st) return st;
         if ((double)n < 1.2 * (double)nagg) { free(agg); break; }
         o->cagg[l] = agg;
         o->cnagg[l] = nagg;
@@ -1263,6 +1386,7 @@ int orc_setup(void *h, int max_levels, int hessian_levels, double theta, int coa
         o->Lc = l + 2;
         th = th * 0.5;
     }
+hierarchies_done:;
     int lmin = o->Ls < o->Lc ? o->Ls : o->Lc;
     for (int l = 0; l + 1 < lmin; l++)
         if ((st = galerkin(&o->St[l], &o->Myu[l], &o->P[l], 0, &o->Myu[l + 1]))) return st;
@@ -1288,6 +1412,17 @@ int orc_setup(void *h, int max_levels, int hessian_levels, double theta, int coa
     o->mass_maxit = 1000;
     if ((st = build_coarse_hessian(o))) return st;
     o->setup_done = 1;
+    return ORC_OK;
+}
+
+/* hierarchy kind for the next orc_setup: aggressive first-level coarsening,
+ * or the geometric hierarchy of a structured square grid */
+int orc_set_hierarchy(void *h, int aggressive, int geometric)
+{
+    orc_t *o = h;
+    if (aggressive < 0 || aggressive > 1 || geometric < 0 || geometric > 1) return ORC_INVALID;
+    o->aggressive = aggressive;
+    o->geometric = geometric;
     return ORC_OK;
 }
 
@@ -1376,7 +1511,7 @@ int orc_aggregates(void *h, int hier, int l, int *agg, int *nagg)
 {
     orc_t *o = h;
     int L = hier ? o->Lc : o->Ls;
-    if (l < 0 || l + 1 >= L) return ORC_INVALID;
+    if (l < 0 || l + 1 >= L || o->geometric) return ORC_INVALID;
     int n = hier ? o->KN[l].rows : o->A[l].rows;
     memcpy(agg, hier ? o->cagg[l] : o->sagg[l], sizeof(int) * (size_t)n);
     *nagg = hier ? o->cnagg[l] : o->snagg[l];

@@ -64,6 +64,7 @@ def lib(omp: bool = False):
                 "orc_setup": [P, I, I, D, I, I, I, I],
                 "orc_set_tols": [P, D, D, I, I],
                 "orc_set_precond_tol": [P, D],
+                "orc_set_hierarchy": [P, I, I],
                 "orc_set_coarse_solve": [P, I, D, I, P],
                 "orc_sizes": [P, P, P, P, P, P, P, P],
                 "orc_matrix_info": [P, I, I, P, P, P],
@@ -140,7 +141,7 @@ class Oracle:
 
     def __init__(self, w, max_levels=25, hessian_levels=0, theta=0.08, coarse_max=256,
                  smoother=1, degree=2, smooth_prolongator=1, inner_tol=1e-10, mass_tol=1e-10,
-                 inner_maxit=1000, mass_maxit=1000, setup=True, omp=False):
+                 inner_maxit=1000, mass_maxit=1000, setup=True, omp=False, aggressive=0, geometric=0):
         self.w = w
         self._L = L = lib(omp)
         self._coords = np.ascontiguousarray(w.coords, dtype=np.float64)
@@ -156,6 +157,7 @@ class Oracle:
         self.h = h
         self.m = int(w.n_interior)
         self.n = int(w.n_vertices)
+        _check(L.orc_set_hierarchy(self.h, int(aggressive), int(geometric)), "set_hierarchy")
         if setup:
             self.setup(max_levels, hessian_levels, theta, coarse_max, smoother, degree,
                        smooth_prolongator)

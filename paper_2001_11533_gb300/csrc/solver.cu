@@ -14,7 +14,9 @@
 #include <math.h>
 #include <string.h>
 
+#include <algorithm>
 #include <chrono>
+#include <vector>
 
 #include "internal.cuh"
 #include "util.cuh"
@@ -411,21 +413,24 @@ static int pcg_run(amgh_problem *p, int l, int mode, const void *f, double tol, 
         TRY(cg_body_start(p, l, mode));
     }
     int *hint = mode == 1 ? &p->chunk_hint32[l] : &p->chunk_hint[l];
-    // first chunk: most of the previous solve's count (replays past convergence are
-    // no-ops); one iteration at a time while kernels are timed, so that no
-    // skipped launch is timed
-    int chunk = (*hint > 1 && gr) ? (*hint * 7) / 8 : 1;
-    int enq = 0;
+    // first chunk: most of the previous solve's count (replays past convergence are no-ops)
+    int chunk = *hint > 1 ? (*hint * 7) / 8 : 1;
+    int enq = 0, prev_iters = 0;
     CgScal h;
+    std::vector<size_t> it_mark, vc_mark; // direct launches: timings of each enqueued iteration
     for (;;) {
+        it_mark.clear();
+        vc_mark.clear();
         for (int c = 0; c < chunk; c++) {
             if (gr) TRY(replay(p, g.iter, g.nodes_iter));
             else {
                 double b = 0.0;
+                it_mark.push_back(p->timer.ev.size());
                 {
                     ByteSink bs_(&b);
                     TRY(cg_body_iter(p, l, mode));
                 }
+                vc_mark.push_back(p->timer.vc_mark);
                 if (enq + c == 0) {
                     b_iter = b;
                     b_vc = p->vc_bytes;
@@ -434,9 +439,18 @@ static int pcg_run(amgh_problem *p, int l, int mode, const void *f, double tol, 
         }
         enq += chunk;
         TRY(read_scal(p, sc, &h));
-        if (!gr && h.done) timer_drop_from(p, p->timer.vc_mark); // that V-cycle was skipped
+        if (!gr) {
+            // the device skipped every iteration past convergence and the
+            // closing V-cycle of the converging one: their timings go
+            const int ran = h.iters - prev_iters;
+            size_t cut = (size_t)-1;
+            if (ran >= 0 && ran < chunk) cut = it_mark[ran];
+            if (h.done && ran >= 1 && ran <= chunk) cut = std::min(cut, vc_mark[ran - 1]);
+            if (cut != (size_t)-1) timer_drop_from(p, cut);
+        }
+        prev_iters = h.iters;
         if (h.done || enq > maxit + 2) break;
-        chunk = (h.iters / 8 > 1 && gr) ? h.iters / 8 : 1;
+        chunk = h.iters / 8 > 1 ? h.iters / 8 : 1;
     }
     if (h.iters > 0) count_bytes(b_start + (double)h.iters * b_iter - (h.done ? b_vc : 0.0));
     p->c_inner_lvl[l] += h.iters;
@@ -516,14 +530,17 @@ int mass_solve(amgh_problem *p, int l, const double *b, double *x, int64_t *iter
     };
     if (gr && !g.iter) TRY(capture(p, body, &g.iter, &g.nodes_iter, &g.bytes_iter));
     double b_iter = g.bytes_iter;
-    int chunk = (p->mchunk_hint[l] > 1 && gr) ? (p->mchunk_hint[l] * 7) / 8 : 1;
-    int enq = 0;
+    int chunk = p->mchunk_hint[l] > 1 ? (p->mchunk_hint[l] * 7) / 8 : 1;
+    int enq = 0, prev_iters = 0;
     CgScal h;
+    std::vector<size_t> it_mark;
     for (;;) {
+        it_mark.clear();
         for (int c = 0; c < chunk; c++) {
             if (gr) TRY(replay(p, g.iter, g.nodes_iter));
             else {
                 double b = 0.0;
+                it_mark.push_back(p->timer.ev.size());
                 {
                     ByteSink bs_(&b);
                     TRY(body());
@@ -533,8 +550,11 @@ int mass_solve(amgh_problem *p, int l, const double *b, double *x, int64_t *iter
         }
         enq += chunk;
         TRY(read_scal(p, C.mscal, &h));
+        const int ran = h.iters - prev_iters;
+        if (!gr && ran >= 0 && ran < chunk) timer_drop_from(p, it_mark[ran]); // skipped iterations
+        prev_iters = h.iters;
         if (h.done || enq > p->sopts.mass_max_iter + 2) break;
-        chunk = (h.iters / 8 > 1 && gr) ? h.iters / 8 : 1;
+        chunk = h.iters / 8 > 1 ? h.iters / 8 : 1;
     }
     count_bytes((double)h.iters * b_iter);
     p->c_mass_lvl[l] += h.iters;
