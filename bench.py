@@ -76,6 +76,9 @@ def parse():
                     help="mixed = FP64 CG + FP32 V-cycles; fp64; refine = FP32 CG in FP64 refinement")
     ap.add_argument("--fuse-coarse", type=int, default=0,
                     help="0: V-cycle level by level; 2: levels of <= 262144 rows in one cooperative launch")
+    ap.add_argument("--experiments", action="store_true",
+                    help="run the paper's Tables 1-2 (a_j), 5 (two-grid, geometric vs AMG) and 7 (level "
+                         "sweep, ball inclusion) on the GPU and print them as one JSON line")
     ap.add_argument("--no-cube", action="store_true",
                     help="skip the 257^3 slab-cube block (mixed and FP64, >= 6 AMG levels)")
     ap.add_argument("--cube-N", type=int, default=257)
@@ -702,6 +705,18 @@ def main():
         return
     if args.block_apply:
         block_apply(args)
+        return
+    if args.experiments:
+        from paper_2001_11533_gb300 import _build, experiments
+        _build.build()
+        out = {}
+        for name, fn in (("tables_1_2_a_numbers", experiments.a_numbers_table),
+                         ("table_5_two_grid", experiments.two_grid_table),
+                         ("table_7_level_sweep", experiments.level_sweep_table)):
+            t0 = time.perf_counter()
+            out[name] = fn()
+            out[name]["wall_s"] = round(time.perf_counter() - t0, 1)
+            print(json.dumps({name: out[name]}), flush=True)
         return
     if args.impl == "reference":
         run_reference(args, rank, world)

@@ -102,7 +102,22 @@ typedef struct {
  *                  a row in different orders, so results may differ in the
  *                  last bits from the default heuristic (0: by mean row
  *                  length), which is reproducible across processes.  On the
- *                  1025^2 L-shape the heuristic's layouts were as fast */
+ *                  1025^2 L-shape the heuristic's layouts were as fast
+ *  aggressive      1 = aggressive first-level coarsening in both hierarchies
+ *                  (Sec. 5.1; read for smoothed aggregation): the level-0
+ *                  aggregates are aggregated once more on their tentative
+ *                  Galerkin matrix S_hat^T A S_hat (strength threshold
+ *                  theta/2), and every vertex takes the aggregate of its
+ *                  aggregate; the smoothed prolongator is built on the result
+ *  geometric       1 = the geometric hierarchy of Sec. 5.4 instead of AMG:
+ *                  the mesh must be the structured N x N square grid (vertex
+ *                  i + N j, squares split along the (i,j)-(i+1,j+1) diagonal,
+ *                  the whole boundary Dirichlet; else INVALID_ARG), and each
+ *                  level takes every other grid line (N odd, N >= 5) with P1
+ *                  interpolation (weights 1 and 1/2); S_j is its restriction
+ *                  to interior vertices; coarse matrices are Galerkin
+ *                  products as for AMG (theta, smooth_prolongator and
+ *                  aggressive are not used; amgh_get_aggregates is invalid) */
 typedef struct {
     int max_levels;
     int hessian_levels;
@@ -115,6 +130,8 @@ typedef struct {
     int coarse_solve;
     int fuse_coarse;
     int autotune;
+    int aggressive;
+    int geometric;
 } amgh_amg_opts;
 
 /* Solve options (Sec. 5.2-5.3).
@@ -178,7 +195,7 @@ typedef struct {
 
 /* Defaults: max_levels 25, hessian_levels 0, theta 0.08, coarse_max 256,
  * Chebyshev degree 2, precision 0, smoothed prolongator, coarse_solve 0, fuse_coarse 0,
- * autotune 0;
+ * autotune 0, aggressive 0, geometric 0;
  * tol 1e-8, max_iter 200, inner/mass tol 1e-10, precond 1, ncols 1, caps
  * 1000, precond_tol 0 (= inner_tol), coarse_tol 1e-4, coarse_max_iter 1000,
  * level_fallback 0. */
@@ -340,6 +357,23 @@ int amgh_get_matrix_info(const amgh_problem *p, int which, int level, int64_t *r
                          int64_t *cols, int64_t *nnz);
 int amgh_get_matrix(const amgh_problem *p, int which, int level, int32_t *rowptr_host,
                     int32_t *col_host, double *val_host);
+
+/* Two-level approximation numbers of the multilevel analysis (Sec. 4,
+ * Assumption with a_j; Sec. 5.1, Tables 1-2), by the power method on the
+ * GPU.  With K_j = A_j^-1 M_yu,j, Pi_j = M_u,j+1^-1 P_j^T M_u,j and
+ * D_j = K_j - S_j K_j+1 Pi_j on level j:
+ *   weighted 0: a~_j = ||D_j||_2 (Eq. aj-tilde), from D_j^T D_j;
+ *   weighted 1: a_j = ||M_y,j^1/2 D_j M_u,j^-1/2||_2 (Eq. ajnumerical),
+ *               from M_u,j^-1 D_j^T M_y,j D_j in the M_u,j inner product.
+ *   level   j, 0 <= j <= min(Ls, Lc) - 2
+ *   iters   power iterations (>= 1); each applies D_j and D_j^T (four AMG-CG
+ *           state solves and two or three mass solves at the set tolerances)
+ *   v0_dev  start vector, n_j doubles on the device (not changed)
+ *   est     host: the estimate after `iters` iterations (a lower bound that
+ *           increases to the norm)
+ * Errors: INVALID_ARG (level, iters, a zero start vector), NOT_SETUP, the
+ * solves' statuses. */
+int amgh_aj_estimate(amgh_problem *p, int level, int weighted, int iters, const double *v0_dev, double *est);
 
 /* Counters since the last reset (fields as amgh_solve_info). */
 int amgh_get_counters(const amgh_problem *p, amgh_solve_info *info);

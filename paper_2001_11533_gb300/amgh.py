@@ -37,7 +37,8 @@ class amgh_amg_opts(C.Structure):
     _fields_ = [("max_levels", C.c_int), ("hessian_levels", C.c_int), ("theta", C.c_double),
                 ("coarse_max", C.c_int), ("smoother", C.c_int), ("smooth_degree", C.c_int),
                 ("precision", C.c_int), ("smooth_prolongator", C.c_int), ("coarse_solve", C.c_int),
-                ("fuse_coarse", C.c_int), ("autotune", C.c_int)]
+                ("fuse_coarse", C.c_int), ("autotune", C.c_int), ("aggressive", C.c_int),
+                ("geometric", C.c_int)]
 
 
 class amgh_solve_opts(C.Structure):
@@ -94,6 +95,7 @@ _SIGS = {
     "amgh_kernel_class_stats": ([_P, _I, _P, _P, _P, _P], _I),
     "amgh_kernel_timing_mask": ([_P, C.c_uint], _I),
     "amgh_debug_limits": ([_I, _I, _I], _I),
+    "amgh_aj_estimate": ([_P, _I, _I, _I, _P, _P], _I),
     "amgh_launch_count": ([], _I64),
     "amgh_aggregate_noalloc": ([_I, _P, _P, _P, _D, _P, _P, _P], _I),
     "amgh_batch_create": ([_P, _I, _P], _I),
@@ -444,6 +446,14 @@ class Problem:
         n, ms, b = C.c_int64(), C.c_double(), C.c_double()
         check(lib().amgh_kernel_stats(self.h, C.byref(n), C.byref(ms), C.byref(b)), "amgh_kernel_stats")
         return {"launches": n.value, "ms": ms.value, "bytes": b.value}
+
+    def aj_estimate(self, level, v0, weighted=False, iters=30):
+        """a~_j (weighted False) or a_j (True) on `level` by the power method
+        from the CUDA vector v0 (amgh_aj_estimate)."""
+        est = C.c_double()
+        check(lib().amgh_aj_estimate(self.h, int(level), 1 if weighted else 0, int(iters), _ptr(v0),
+                                     C.byref(est)), "amgh_aj_estimate")
+        return est.value
 
     def kernel_timing_mask(self, mask):
         """Time only the kernel classes whose bit is set (amgh_kernel_timing_mask)."""

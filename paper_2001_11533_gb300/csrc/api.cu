@@ -30,6 +30,8 @@ extern "C" void amgh_amg_opts_default(amgh_amg_opts *o)
     o->coarse_solve = 0;
     o->fuse_coarse = 0;
     o->autotune = 0;
+    o->aggressive = 0;
+    o->geometric = 0;
 }
 
 extern "C" void amgh_solve_opts_default(amgh_solve_opts *o)
@@ -353,6 +355,11 @@ static int setup_impl(amgh_problem *p)
     TRY(extract_sub(ar, p->Mfull, p->state_of_vertex, p->m, nullptr, p->n, C0.Myu, s));
     TRY(extract_sub(ar, p->Kfull, nullptr, p->n, nullptr, p->n, C0.KN, s));
     TRY(extract_sub(ar, p->Mfull, nullptr, p->n, nullptr, p->n, C0.Mu, s));
+    if (o.geometric) {
+        TRY(geometric_hierarchy(p));
+        goto hierarchies_done;
+    }
+    {
     // state hierarchy on A (theta halved per level)
     double th = o.theta;
     p->Ls = 1;
@@ -361,7 +368,8 @@ static int setup_impl(amgh_problem *p)
         int n = S.A.rows;
         TRY(ar.alloc(&S.agg, n));
         int nagg = 0;
-        TRY(amg_aggregate(p, S.A, th * th, S.agg, &nagg));
+        if (l == 0 && o.aggressive) TRY(amg_aggregate_aggressive(p, S.A, th * th, S.agg, &nagg));
+        else TRY(amg_aggregate(p, S.A, th * th, S.agg, &nagg));
         if ((double)n < 1.2 * (double)nagg) break;
         S.nagg = nagg;
         TRY(amg_prolongator(p, ar, S.A, S.agg, nagg, o.smooth_prolongator, S.S));
@@ -378,7 +386,8 @@ static int setup_impl(amgh_problem *p)
         int n = C.KN.rows;
         TRY(ar.alloc(&C.agg, n));
         int nagg = 0;
-        TRY(amg_aggregate(p, C.KN, th * th, C.agg, &nagg));
+        if (l == 0 && o.aggressive) TRY(amg_aggregate_aggressive(p, C.KN, th * th, C.agg, &nagg));
+        else TRY(amg_aggregate(p, C.KN, th * th, C.agg, &nagg));
         if ((double)n < 1.2 * (double)nagg) break;
         C.nagg = nagg;
         TRY(amg_prolongator(p, ar, C.KN, C.agg, nagg, o.smooth_prolongator, C.P));
@@ -387,6 +396,8 @@ static int setup_impl(amgh_problem *p)
         p->Lc = l + 2;
         th = th * 0.5;
     }
+    }
+hierarchies_done:
     int lmin = p->Ls < p->Lc ? p->Ls : p->Lc;
     for (int l = 0; l + 1 < lmin; l++)
         TRY(galerkin(p, ar, p->sl[l].St, p->cl[l].Myu, p->cl[l].P, 0, p->cl[l + 1].Myu));
@@ -444,7 +455,8 @@ extern "C" int amgh_amg_setup(amgh_problem *p, const amgh_amg_opts *opts)
     if (o.max_levels < 1 || o.max_levels > AMGH_MAXL || o.smooth_degree < 1 || o.smooth_degree > 16 ||
         o.coarse_max < 1 || !(o.theta >= 0.0) || (o.smoother != 0 && o.smoother != 1) ||
         o.precision < 0 || o.precision > 2 || o.hessian_levels < 0 || o.coarse_solve < 0 || o.coarse_solve > 2 || (o.fuse_coarse < 0 || o.fuse_coarse > 2) ||
-        (o.autotune != 0 && o.autotune != 1))
+        (o.autotune != 0 && o.autotune != 1) || (o.aggressive != 0 && o.aggressive != 1) ||
+        (o.geometric != 0 && o.geometric != 1))
         return AMGH_ERR_INVALID_ARG;
     double t0 = now_s();
     StreamScope ss_(p->stream);
@@ -734,6 +746,18 @@ extern "C" int amgh_precond_apply_level(amgh_problem *p, int which, int level, c
     return finish_call(p, which == 0 ? mlas_Q(p, level, b, z) : mlas_R(p, level, b, z));
 }
 
+// ------------------------------------------------------------------ diagnostics
+extern "C" int amgh_aj_estimate(amgh_problem *p, int level, int weighted, int iters, const double *v0,
+                                double *est)
+{
+    NEED_SETUP(p);
+    CallScope cs_(p);
+    int lmin = p->Ls < p->Lc ? p->Ls : p->Lc;
+    if (level < 0 || level + 1 >= lmin || iters < 1 || !v0 || !est || (weighted != 0 && weighted != 1))
+        return AMGH_ERR_INVALID_ARG;
+    return finish_call(p, aj_estimate(p, level, weighted, iters, v0, est));
+}
+
 // ------------------------------------------------------------------ queries
 extern "C" int amgh_query_sizes(const amgh_problem *p, int64_t *m, int64_t *n, int *Ls, int *Lc, int *ell,
                                 int64_t *ssz, int64_t *csz)
@@ -754,7 +778,7 @@ extern "C" int amgh_get_aggregates(const amgh_problem *p, int hier, int level, i
     if (!p || !agg) return AMGH_ERR_INVALID_ARG;
     if (!p->setup_done) return AMGH_ERR_NOT_SETUP;
     int L = hier ? p->Lc : p->Ls;
-    if (level < 0 || level + 1 >= L) return AMGH_ERR_INVALID_ARG;
+    if (level < 0 || level + 1 >= L || p->aopts.geometric) return AMGH_ERR_INVALID_ARG;
     const int *src = hier ? p->cl[level].agg : p->sl[level].agg;
     int rows = hier ? p->cl[level].Mu.rows : p->sl[level].A.rows;
     CU(cudaMemcpyAsync(agg, src, sizeof(int) * rows, cudaMemcpyDeviceToHost, p->stream));

@@ -480,6 +480,12 @@ int extract_sub(Arena &ar, const DevCsr &a, const int *rmap, int nr, const int *
 
 // ------------------------------------------------------------------ amg.cu
 int amg_aggregate(amgh_problem *p, const DevCsr &a, double theta2, int *agg, int *nagg);
+// aggressive first-level aggregation: the aggregates of a, aggregated once
+// more on their tentative Galerkin matrix (threshold theta2 / 4), composed
+int amg_aggregate_aggressive(amgh_problem *p, const DevCsr &a, double theta2, int *agg, int *nagg);
+// the geometric hierarchy of a structured N x N square grid (aopts.geometric):
+// fills S, St, P, Pt and the Galerkin A, M_y, K_N, M_u of every level, Ls = Lc
+int geometric_hierarchy(amgh_problem *p);
 int amg_prolongator(amgh_problem *p, Arena &ar, const DevCsr &a, const int *agg, int nagg,
                     int smooth, DevCsr &s);
 int spgemm(amgh_problem *p, Arena &ar, const DevCsr &a, const DevCsr &b, DevCsr &c);
@@ -514,6 +520,10 @@ int sync_stream(amgh_problem *p);
 int graph_capture(amgh_problem *p, const std::function<int()> &body, cudaGraphExec_t *exec, int *nodes);
 int graph_replay(amgh_problem *p, cudaGraphExec_t exec, int nodes);
 bool graphs_enabled(amgh_problem *p);
+
+// ------------------------------------------------------------------ diag.cu
+// a~_j (weighted 0) or a_j (weighted 1) by `iters` power iterations from v0
+int aj_estimate(amgh_problem *p, int j, int weighted, int iters, const double *v0, double *est);
 
 // ------------------------------------------------------------------ block.cu
 // K columns (K = 2, 4, 8) advanced together; the column-major inputs hold

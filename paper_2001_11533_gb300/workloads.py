@@ -349,6 +349,22 @@ def cube_slabs(N: int = 257, cfg: int = 4) -> Workload:
     return Workload(f"cube{N}_slabs", 3, coords, elems, dirichlet, kappa, 1e-6, yd, {"N": N})
 
 
+def cube_ball(N: int = 33, contrast: float = 1e-2, cfg: int = 5) -> Workload:
+    """The varying-coefficient setting of Sec. 5.6 (Table 7) on an N^3 Kuhn grid:
+    kappa = contrast inside the ball |x - (1/2,1/2,1/2)| <= 1/4 (element centroid)
+    and 1 outside, so the mesh does not follow the coefficient; zero Dirichlet
+    condition on the face x3 = 0 only (homogeneous Neumann elsewhere); desired
+    state y_d = 1; beta = 1.  Unjittered, so cfg is unused."""
+    coords, elems = grid3d_kuhn(N)
+    dirichlet = (np.abs(coords[:, 2]) < 0.5 / (N - 1)).astype(np.uint8)
+    c = centroids(coords, elems)
+    inside = ((c - 0.5) ** 2).sum(axis=1) <= 0.25 ** 2
+    kappa = np.where(inside, float(contrast), 1.0)
+    yd = np.ones(coords.shape[0])
+    return Workload(f"cube{N}_ball{contrast:g}", 3, coords, elems, dirichlet, kappa, 1.0, yd,
+                    {"N": N, "contrast": contrast})
+
+
 def random_vectors(n: int, k: int, cfg: int, stream: int) -> np.ndarray:
     """Seeded standard normal test vectors, shape (k, n)."""
     return _rng(cfg, stream).standard_normal((k, n))

@@ -47,3 +47,15 @@ def test_cube_slabs_kappa_from_centroid_height():
     z = W.centroids(w.coords, w.elements)[:, 2]
     bnd = np.sort(np.arange(1, 10) / 10.0 + W._rng(4, 8).uniform(-0.02, 0.02, size=9))
     assert np.array_equal(w.kappa, np.where(np.searchsorted(bnd, z) % 2 == 0, 1.0, 1e6))
+
+
+def test_cube_ball_boundary_and_coefficient():
+    w = W.cube_ball(N=9, contrast=1e-3)
+    z = w.coords[:, 2]
+    assert np.array_equal(w.dirichlet.astype(bool), z == 0.0)
+    assert w.n_interior == 9 * 9 * 8
+    c = W.centroids(w.coords, w.elements)
+    inside = np.linalg.norm(c - 0.5, axis=1) <= 0.25
+    assert inside.any() and (~inside).any()
+    assert np.array_equal(w.kappa, np.where(inside, 1e-3, 1.0)) and w.beta == 1.0
+    assert np.all(w.y_d == 1.0)
