@@ -380,6 +380,11 @@ def run_batch(args, rank, world, local):
         for p in probs:
             p.close()
     out["speedup_mixed_vs_fp64"] = out["fp64"]["time_to_1e-8_s"] / out["mixed"]["time_to_1e-8_s"]
+    out["speedup_matrix_free_vs_assembled_mixed"] = (out["mixed"]["time_to_1e-8_s"]
+                                                     / out["mixed_matrix_free"]["time_to_1e-8_s"])
+    out["mixed_matrix_free"]["note"] = ("level-0 smoother and residual of the FP32 V-cycles applied from the "
+                                        "element coefficients (kappa, FP32) instead of the assembled matrix; "
+                                        "its kernel bytes are on that basis")
     out["speedup_block_vs_columns_mixed"] = (out["mixed"]["time_to_1e-8_s"]
                                              / out["mixed_block"]["time_to_1e-8_s"])
     out["workload"] = "16 squares 65^2..513^2, 8 desired states each (128 outer CGs to 1e-8)"
@@ -407,10 +412,10 @@ def run_cube(args, rank, world, local):
     tols = dict(tol=1e-8, inner_tol=args.inner_tol, mass_tol=args.precond_tol, precond_tol=args.precond_tol,
                 level_fallback=1)
 
-    def step(precision, timing=0):
+    def step(precision, timing=0, mf=0):
         prob = amgh.Problem(w.dim, dev[0], dev[1], dev[2], dev[3], w.beta, dev[4], on_device=True)
         prob.amg_setup(precision=precision, coarse_max=args.cube_coarse_max, smooth_degree=args.degree,
-                       coarse_solve=2, fuse_coarse=args.fuse_coarse)
+                       coarse_solve=2, fuse_coarse=args.fuse_coarse, matrix_free=mf)
         if timing:
             prob.kernel_timing_mask(timing)
         u, y, info = prob.solve(want_y=False, **tols)
@@ -423,10 +428,13 @@ def run_cube(args, rank, world, local):
            "kappa": "10 jittered slabs {1,1e6}", "coarse_max": args.cube_coarse_max,
            "steps": args.cube_steps, "warmup": args.cube_warmup,
            "timing": "CUDA events per step on the launching stream, 256 MB L2 flush before each step"}
-    for form in ("mixed", "fp64"):
-        precision = PRECISION[form]
+    # "mixed_matrix_free": the mixed form with the level-0 smoother steps and
+    # residual applied matrix-free from the element coefficients
+    for form in ("mixed", "fp64", "mixed_matrix_free"):
+        mf = 1 if form == "mixed_matrix_free" else 0
+        precision = PRECISION[form.split("_")[0]]
         for _ in range(args.cube_warmup):
-            step(precision)
+            step(precision, mf=mf)
         torch.cuda.synchronize()
         times, infos = [], []
         with ClockSampler(local) as clk:
@@ -435,7 +443,7 @@ def run_cube(args, rank, world, local):
                 ev0 = torch.cuda.Event(enable_timing=True)
                 ev1 = torch.cuda.Event(enable_timing=True)
                 ev0.record(stream)
-                info, _, sizes = step(precision)
+                info, _, sizes = step(precision, mf=mf)
                 ev1.record(stream)
                 ev1.synchronize()
                 times.append(ev0.elapsed_time(ev1) / 1000.0)
@@ -452,10 +460,10 @@ def run_cube(args, rank, world, local):
                "fallbacks": last["fallbacks"], "hessian_levels": last["hessian_levels"],
                "levels": {"state": sizes["state"], "control": sizes["control"], "ell": sizes["ell"]},
                "clocks": clk.summary()}
-        if form == "mixed":
+        if form in ("mixed", "mixed_matrix_free"):
             flush.zero_()
             # kernels of 10 us and more here: one pass times every class
-            _, ks, _ = step(precision, timing=(1 << 15) - 1)
+            _, ks, _ = step(precision, timing=(1 << 15) - 1, mf=mf)
             res["roofline"] = roofline_from({"kstats": ks["chebl0"]}, args, kernel_note="level-0 Chebyshev "
                                             "smoother step on the 3D uniform-width SELL-32 matrix (int32 columns)",
                                             traffic=None)
@@ -463,6 +471,11 @@ def run_cube(args, rank, world, local):
         res["solve_phase"] = solve_phase(last)
         out[form] = res
     out["speedup_mixed_vs_fp64"] = out["fp64"]["time_to_1e-8_s"] / out["mixed"]["time_to_1e-8_s"]
+    out["speedup_matrix_free_vs_assembled_mixed"] = (out["mixed"]["time_to_1e-8_s"]
+                                                     / out["mixed_matrix_free"]["time_to_1e-8_s"])
+    out["mixed_matrix_free"]["note"] = ("level-0 smoother and residual of the FP32 V-cycles applied from the "
+                                        "element coefficients (kappa, FP32) instead of the assembled matrix; "
+                                        "its kernel bytes are on that basis")
     del dev
     torch.cuda.empty_cache()
     return out

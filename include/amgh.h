@@ -117,7 +117,12 @@ typedef struct {
  *                  interpolation (weights 1 and 1/2); S_j is its restriction
  *                  to interior vertices; coarse matrices are Galerkin
  *                  products as for AMG (theta, smooth_prolongator and
- *                  aggressive are not used; amgh_get_aggregates is invalid) */
+ *                  aggressive are not used; amgh_get_aggregates is invalid)
+ *  matrix_free     1 = on the structured Kuhn cube (see amgh_kuhn_apply;
+ *                  else INVALID_ARG) the level-0 smoother steps and residual
+ *                  of FP32 V-cycles apply the stiffness matrix-free from the
+ *                  element coefficients instead of reading the assembled
+ *                  matrix; same operator, different rounding */
 typedef struct {
     int max_levels;
     int hessian_levels;
@@ -132,6 +137,7 @@ typedef struct {
     int autotune;
     int aggressive;
     int geometric;
+    int matrix_free;
 } amgh_amg_opts;
 
 /* Solve options (Sec. 5.2-5.3).
@@ -195,7 +201,7 @@ typedef struct {
 
 /* Defaults: max_levels 25, hessian_levels 0, theta 0.08, coarse_max 256,
  * Chebyshev degree 2, precision 0, smoothed prolongator, coarse_solve 0, fuse_coarse 0,
- * autotune 0, aggressive 0, geometric 0;
+ * autotune 0, aggressive 0, geometric 0, matrix_free 0;
  * tol 1e-8, max_iter 200, inner/mass tol 1e-10, precond 1, ncols 1, caps
  * 1000, precond_tol 0 (= inner_tol), coarse_tol 1e-4, coarse_max_iter 1000,
  * level_fallback 0. */
@@ -357,6 +363,21 @@ int amgh_get_matrix_info(const amgh_problem *p, int which, int level, int64_t *r
                          int64_t *cols, int64_t *nnz);
 int amgh_get_matrix(const amgh_problem *p, int which, int level, int32_t *rowptr_host,
                     int32_t *col_host, double *val_host);
+
+/* y = A x with the level-0 state stiffness applied matrix-free, for meshes
+ * that are the structured Kuhn cube: N^3 vertices at (i,j,k)/(N-1) (vertex
+ * i + N j + N^2 k), 6 (N-1)^3 tetrahedra cell by cell, the 6 of a cell in
+ * lexicographic order of the axis permutation (a,b,c), each the path
+ * o, o+e_a, o+e_a+e_b, o+(1,1,1).  Every such tetrahedron has the P1
+ * stiffness kappa_T h/6 tridiag(-1, [1 2 2 1], -1) in path order (Sec. 2),
+ * so only kappa is read (no matrix).  The first call checks the mesh (and
+ * keeps an FP32 copy of kappa): make it before any stream capture.
+ *   prec32  0: x, y double (m each, state order); 1: float
+ *   x, y    device vectors of the m states (y = A x, Dirichlet vertices
+ *           eliminated as in the assembled A)
+ * Errors: INVALID_ARG if the mesh is not such a cube, CUDA.  Works before
+ * amgh_amg_setup. */
+int amgh_kuhn_apply(amgh_problem *p, int prec32, const void *x_dev, void *y_dev);
 
 /* Two-level approximation numbers of the multilevel analysis (Sec. 4,
  * Assumption with a_j; Sec. 5.1, Tables 1-2), by the power method on the

@@ -38,7 +38,7 @@ class amgh_amg_opts(C.Structure):
                 ("coarse_max", C.c_int), ("smoother", C.c_int), ("smooth_degree", C.c_int),
                 ("precision", C.c_int), ("smooth_prolongator", C.c_int), ("coarse_solve", C.c_int),
                 ("fuse_coarse", C.c_int), ("autotune", C.c_int), ("aggressive", C.c_int),
-                ("geometric", C.c_int)]
+                ("geometric", C.c_int), ("matrix_free", C.c_int)]
 
 
 class amgh_solve_opts(C.Structure):
@@ -96,6 +96,7 @@ _SIGS = {
     "amgh_kernel_timing_mask": ([_P, C.c_uint], _I),
     "amgh_debug_limits": ([_I, _I, _I], _I),
     "amgh_aj_estimate": ([_P, _I, _I, _I, _P, _P], _I),
+    "amgh_kuhn_apply": ([_P, _I, _P, _P], _I),
     "amgh_launch_count": ([], _I64),
     "amgh_aggregate_noalloc": ([_I, _P, _P, _P, _D, _P, _P, _P], _I),
     "amgh_batch_create": ([_P, _I, _P], _I),
@@ -454,6 +455,15 @@ class Problem:
         check(lib().amgh_aj_estimate(self.h, int(level), 1 if weighted else 0, int(iters), _ptr(v0),
                                      C.byref(est)), "amgh_aj_estimate")
         return est.value
+
+    def kuhn_apply(self, x, out=None):
+        """A x by the matrix-free Kuhn-cube operator (amgh_kuhn_apply); x float64
+        or float32 CUDA tensor of the m states."""
+        import torch
+        out = torch.empty_like(x) if out is None else out
+        prec32 = 1 if x.dtype == torch.float32 else 0
+        check(lib().amgh_kuhn_apply(self.h, prec32, _ptr(x), _ptr(out)), "amgh_kuhn_apply")
+        return out
 
     def kernel_timing_mask(self, mask):
         """Time only the kernel classes whose bit is set (amgh_kernel_timing_mask)."""

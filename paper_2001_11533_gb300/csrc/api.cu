@@ -32,6 +32,7 @@ extern "C" void amgh_amg_opts_default(amgh_amg_opts *o)
     o->autotune = 0;
     o->aggressive = 0;
     o->geometric = 0;
+    o->matrix_free = 0;
 }
 
 extern "C" void amgh_solve_opts_default(amgh_solve_opts *o)
@@ -198,6 +199,9 @@ extern "C" int amgh_problem_share(amgh_problem *parent, amgh_problem **out)
         p->cr[k] = parent->cr[k];
     }
     p->t_setup = parent->t_setup;
+    p->kuhn_checked = parent->kuhn_checked;
+    p->kuhn_N = parent->kuhn_N;
+    p->kappa32 = parent->kappa32;
     int st = AMGH_OK;
     {
         StreamScope ss_(p->stream);
@@ -347,6 +351,13 @@ static int setup_impl(amgh_problem *p)
     cudaStream_t s = p->stream;
     Arena &ar = p->harena;
     const amgh_amg_opts &o = p->aopts;
+    if (o.matrix_free) {
+        TRY(kuhn_detect(p));
+        if (!p->kuhn_N) {
+            amgh_note_msg("matrix_free: the mesh is not the structured Kuhn cube");
+            return AMGH_ERR_INVALID_ARG;
+        }
+    }
     // level 0: state dofs = non-Dirichlet vertices, control dofs = all vertices
     StateLevel &S0 = p->sl[0];
     CtrlLevel &C0 = p->cl[0];
@@ -456,7 +467,7 @@ extern "C" int amgh_amg_setup(amgh_problem *p, const amgh_amg_opts *opts)
         o.coarse_max < 1 || !(o.theta >= 0.0) || (o.smoother != 0 && o.smoother != 1) ||
         o.precision < 0 || o.precision > 2 || o.hessian_levels < 0 || o.coarse_solve < 0 || o.coarse_solve > 2 || (o.fuse_coarse < 0 || o.fuse_coarse > 2) ||
         (o.autotune != 0 && o.autotune != 1) || (o.aggressive != 0 && o.aggressive != 1) ||
-        (o.geometric != 0 && o.geometric != 1))
+        (o.geometric != 0 && o.geometric != 1) || (o.matrix_free != 0 && o.matrix_free != 1))
         return AMGH_ERR_INVALID_ARG;
     double t0 = now_s();
     StreamScope ss_(p->stream);
@@ -744,6 +755,19 @@ extern "C" int amgh_precond_apply_level(amgh_problem *p, int which, int level, c
     if (level < 0 || level >= p->ell || !b || !z) return AMGH_ERR_INVALID_ARG;
     if (which != 0 && level >= p->ell - 1) return AMGH_ERR_INVALID_ARG;
     return finish_call(p, which == 0 ? mlas_Q(p, level, b, z) : mlas_R(p, level, b, z));
+}
+
+// ------------------------------------------------------------------ matrix-free
+extern "C" int amgh_kuhn_apply(amgh_problem *p, int prec32, const void *x, void *y)
+{
+    if (!p || !x || !y || (prec32 != 0 && prec32 != 1)) return AMGH_ERR_INVALID_ARG;
+    CallScope cs_(p);
+    TRY(kuhn_detect(p));
+    if (!p->kuhn_N) {
+        amgh_note_msg("amgh_kuhn_apply: the mesh is not the structured Kuhn cube");
+        return AMGH_ERR_INVALID_ARG;
+    }
+    return finish_call(p, kuhn_apply(p, prec32, x, y));
 }
 
 // ------------------------------------------------------------------ diagnostics

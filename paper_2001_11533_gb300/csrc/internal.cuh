@@ -363,6 +363,9 @@ struct amgh_problem {
     int chunk_hint32[AMGH_MAXL];
     int mchunk_hint[AMGH_MAXL];
     BlockWork *blk = nullptr; // allocated by the first block call
+    // structured Kuhn cube (kuhn.cu): N of the N^3 grid once detected, else 0
+    int kuhn_checked = 0, kuhn_N = 0;
+    float *kappa32 = nullptr;
 };
 
 // class c0 for vectors / operators of the finest state or control level
@@ -520,6 +523,14 @@ int sync_stream(amgh_problem *p);
 int graph_capture(amgh_problem *p, const std::function<int()> &body, cudaGraphExec_t *exec, int *nodes);
 int graph_replay(amgh_problem *p, cudaGraphExec_t exec, int nodes);
 bool graphs_enabled(amgh_problem *p);
+
+// ------------------------------------------------------------------ kuhn.cu
+// matrix-free level-0 stiffness of the structured Kuhn cube
+int kuhn_detect(amgh_problem *p);
+int kuhn_apply(amgh_problem *p, int prec32, const void *x, void *y);
+int kuhn_cheb_step(amgh_problem *p, const float *invd, const float *b, const float *x, float *d, float *xn,
+                   double cdv, double crv, const int *skip);
+int kuhn_residual(amgh_problem *p, const float *b, const float *x, float *r, const int *skip);
 
 // ------------------------------------------------------------------ diag.cu
 // a~_j (weighted 0) or a_j (weighted 1) by `iters` power iterations from v0

@@ -178,14 +178,21 @@ static int vcyc(amgh_problem *p, int l, const T *b, T *x, const int *skip, int p
     T *cur = tmp, *nxt = x;
     // pre-smoothing from zero
     if (!preinit) TRY(cheb_first<T>(p, n, invd, b, d, cur, p->cr[0], skip));
+    // level 0 of an FP32 cycle on the structured Kuhn cube: matrix-free operator
+    const bool mf = sizeof(T) == sizeof(float) && l == 0 && p->aopts.matrix_free && p->kuhn_N > 0;
     for (int s = 1; s < p->nsteps; s++) {
-        TRY(cheb_step<T>(p, S.A, invd, b, cur, d, nxt, p->cd[s], p->cr[s], skip, timed));
+        if (mf)
+            TRY(kuhn_cheb_step(p, (const float *)invd, (const float *)b, (const float *)cur, (float *)d,
+                               (float *)nxt, p->cd[s], p->cr[s], skip));
+        else
+            TRY(cheb_step<T>(p, S.A, invd, b, cur, d, nxt, p->cd[s], p->cr[s], skip, timed));
         T *t = cur;
         cur = nxt;
         nxt = t;
     }
     // coarse-grid correction
-    TRY(residual<T>(p, S.A, b, cur, r, skip, timed));
+    if (mf) TRY(kuhn_residual(p, (const float *)b, (const float *)cur, (float *)r, skip));
+    else TRY(residual<T>(p, S.A, b, cur, r, skip, timed));
     StateLevel &Sc = p->sl[l + 1];
     T *bc = VBuf<T>::b(Sc), *xc = VBuf<T>::x(Sc);
     if (l + 1 < p->Ls - 1) {
@@ -198,7 +205,11 @@ static int vcyc(amgh_problem *p, int l, const T *b, T *x, const int *skip, int p
     TRY(prolong_add<T>(p, S.S, xc, cur, skip));
     // post-smoothing with the same polynomial
     for (int s = 0; s < p->nsteps; s++) {
-        TRY(cheb_step<T>(p, S.A, invd, b, cur, d, nxt, s == 0 ? 0.0 : p->cd[s], p->cr[s], skip, timed));
+        if (mf)
+            TRY(kuhn_cheb_step(p, (const float *)invd, (const float *)b, (const float *)cur, (float *)d,
+                               (float *)nxt, s == 0 ? 0.0 : p->cd[s], p->cr[s], skip));
+        else
+            TRY(cheb_step<T>(p, S.A, invd, b, cur, d, nxt, s == 0 ? 0.0 : p->cd[s], p->cr[s], skip, timed));
         T *t = cur;
         cur = nxt;
         nxt = t;

@@ -130,3 +130,25 @@ def test_all_dirichlet_mesh_rejected():
     assert w.n_interior == 0
     with pytest.raises(OracleError):
         Oracle(w)
+
+
+def test_kuhn_cell_stiffness_is_scaled_tridiagonal():
+    """Every Kuhn tetrahedron of the structured cube has the P1 stiffness
+    kappa_T h/6 tridiag(-1, [1 2 2 1], -1) in path order (the closed form the
+    matrix-free operator applies): one cell, six tetrahedra with different
+    kappa, against the oracle's assembly."""
+    import itertools
+    from oracle.oracle import Oracle
+    for N in (2, 3):
+        coords, elems = W.grid3d_kuhn(N)
+        h = 1.0 / (N - 1)
+        kappa = 1.0 + np.arange(elems.shape[0]) * 0.37
+        w = W.Workload("kuhn", 3, coords, elems, np.zeros(coords.shape[0], np.uint8), kappa, 1.0,
+                       np.zeros(coords.shape[0]), {})
+        o = Oracle(w, setup=False)
+        K = o.scipy("Kfull").toarray()
+        T = np.array([[1, -1, 0, 0], [-1, 2, -1, 0], [0, -1, 2, -1], [0, 0, -1, 1]], float)
+        ref = np.zeros_like(K)
+        for e, ev in enumerate(elems):
+            ref[np.ix_(ev, ev)] += kappa[e] * h / 6.0 * T
+        assert np.abs(K - ref).max() <= 1e-14 * np.abs(ref).max()
