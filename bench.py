@@ -380,11 +380,6 @@ def run_batch(args, rank, world, local):
         for p in probs:
             p.close()
     out["speedup_mixed_vs_fp64"] = out["fp64"]["time_to_1e-8_s"] / out["mixed"]["time_to_1e-8_s"]
-    out["speedup_matrix_free_vs_assembled_mixed"] = (out["mixed"]["time_to_1e-8_s"]
-                                                     / out["mixed_matrix_free"]["time_to_1e-8_s"])
-    out["mixed_matrix_free"]["note"] = ("level-0 smoother and residual of the FP32 V-cycles applied from the "
-                                        "element coefficients (kappa, FP32) instead of the assembled matrix; "
-                                        "its kernel bytes are on that basis")
     out["speedup_block_vs_columns_mixed"] = (out["mixed"]["time_to_1e-8_s"]
                                              / out["mixed_block"]["time_to_1e-8_s"])
     out["workload"] = "16 squares 65^2..513^2, 8 desired states each (128 outer CGs to 1e-8)"
