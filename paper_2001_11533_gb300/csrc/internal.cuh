@@ -169,6 +169,9 @@ struct DevCsr {
     // uniform-width SELL only: column - row as int16 when every entry fits
     // (2 instead of 4 bytes of index per stored entry)
     short *sl_ci16 = nullptr;
+    // entries the solve-phase copy holds: the SELL copy leaves out entries
+    // whose value is exactly zero (-1: all nnz entries are held)
+    int nnz_solve = -1;
 };
 
 // ------------------------------------------------------------------ reductions

@@ -17,8 +17,8 @@
 // over the 24 tetrahedra T containing v, L(T) the position of v on T's path,
 // d_L = 1 at the path ends and 2 inside, prev/next its path neighbours (zero
 // on Dirichlet vertices).  The only per-element data is kappa, so the matrix
-// stream of 8-12 bytes per stored entry becomes ~6 x (value bytes) per
-// vertex.  Results equal the assembled product up to rounding.
+// stream of 8-12 bytes per stored entry (15 per row) becomes ~6 x (value
+// bytes) per vertex.  Results equal the assembled product up to rounding.
 #include <math.h>
 
 #include "internal.cuh"
@@ -59,8 +59,29 @@ __global__ void k_to_f32_kappa(int64_t n, const double *__restrict__ a, float *_
     if (i < n) b[i] = (float)a[i];
 }
 
-// (A x)_r for state row r, accumulated in type T in a fixed order (cells
-// dk, dj, di = 0, 1; tetrahedra t = 0..5)
+// Consecutive path points of a Kuhn tetrahedron differ by one unit vector and
+// the element matrix couples only consecutive points, so the operator is a
+// 7-point stencil: the off-diagonal coefficient of the edge v -- v+e is minus
+// h/6 times the sum of kappa over the tetrahedra whose path runs along that
+// edge.  (The assembled matrix has the 15-point pattern of the mesh; its 8
+// other entries per row are exact zeros.)  Index 0..5 of the axis neighbours
+// +x, -x, +y, -y, +z, -z, -1 for any other offset.
+__host__ __device__ constexpr int kuhn_nbr(int di, int dj, int dk)
+{
+    return (di == 1 && dj == 0 && dk == 0)    ? 0
+           : (di == -1 && dj == 0 && dk == 0) ? 1
+           : (di == 0 && dj == 1 && dk == 0)  ? 2
+           : (di == 0 && dj == -1 && dk == 0) ? 3
+           : (di == 0 && dj == 0 && dk == 1)  ? 4
+           : (di == 0 && dj == 0 && dk == -1) ? 5
+                                              : -1;
+}
+
+// (A x)_r for state row r.  The row's 6 off-diagonal coefficients and its
+// diagonal are first summed from the kappa of the 24 tetrahedra around the
+// vertex (cells dk, dj, di = 0, 1 in that order, tetrahedra t = 0..5; every
+// index below is a compile-time constant once the loops are unrolled), then
+// the 6 neighbour values are loaded together and combined in a fixed order.
 template <typename T, typename K>
 __device__ __forceinline__ T kuhn_row(int N, T h6, const K *__restrict__ kappa, const int *__restrict__ sov,
                                       const int *__restrict__ vos, const T *__restrict__ x, int r)
@@ -68,10 +89,11 @@ __device__ __forceinline__ T kuhn_row(int N, T h6, const K *__restrict__ kappa, 
     const int64_t v = vos[r];
     const int i = (int)(v % N), j = (int)((v / N) % N), k = (int)(v / ((int64_t)N * N));
     const int M = N - 1;
-    // the permutation table again as compile-time constants, so that with the
-    // loops unrolled every axis index below is known to the compiler
     constexpr int PERM[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
-    T diag = (T)0, off = (T)0;
+    T coef[6];
+#pragma unroll
+    for (int q = 0; q < 6; q++) coef[q] = (T)0;
+    T diag = (T)0;
 #pragma unroll
     for (int dk = 0; dk < 2; dk++)
 #pragma unroll
@@ -83,7 +105,6 @@ __device__ __forceinline__ T kuhn_row(int N, T h6, const K *__restrict__ kappa, 
                 const int dmask = di | (dj << 1) | (dk << 2);
                 const int s = di + dj + dk;
                 const int64_t cell = oi + (int64_t)M * (oj + (int64_t)M * ok);
-                const int64_t o = oi + (int64_t)N * oj + (int64_t)N * N * ok;
 #pragma unroll
                 for (int t = 0; t < 6; t++) {
                     const int a = PERM[t][0], b = PERM[t][1], c = PERM[t][2];
@@ -93,23 +114,29 @@ __device__ __forceinline__ T kuhn_row(int N, T h6, const K *__restrict__ kappa, 
                     else if (s == 1 && ((dmask >> a) & 1)) L = 1;
                     else if (s == 2 && !((dmask >> c) & 1)) L = 2;
                     if (L < 0) continue;
-                    const int64_t sa = a == 0 ? 1 : a == 1 ? (int64_t)N : (int64_t)N * N;
-                    const int64_t sb = b == 0 ? 1 : b == 1 ? (int64_t)N : (int64_t)N * N;
-                    const int64_t path[4] = {o, o + sa, o + sa + sb, o + 1 + N + (int64_t)N * N};
-                    T nb = (T)0;
-                    if (L > 0) {
-                        const int q = sov[path[L - 1]];
-                        if (q >= 0) nb += x[q];
-                    }
-                    if (L < 3) {
-                        const int q = sov[path[L + 1]];
-                        if (q >= 0) nb += x[q];
-                    }
+                    // path points p_0..p_3 of the tetrahedron relative to its cell
+                    const int px[4] = {0, a == 0, (a == 0) + (b == 0), 1};
+                    const int py[4] = {0, a == 1, (a == 1) + (b == 1), 1};
+                    const int pz[4] = {0, a == 2, (a == 2) + (b == 2), 1};
                     const T kt = (T)kappa[6 * cell + t];
                     diag += kt * (T)((L == 0 || L == 3) ? 1 : 2);
-                    off += kt * nb;
+                    if (L > 0) coef[kuhn_nbr(px[L - 1] - di, py[L - 1] - dj, pz[L - 1] - dk)] += kt;
+                    if (L < 3) coef[kuhn_nbr(px[L + 1] - di, py[L + 1] - dj, pz[L + 1] - dk)] += kt;
                 }
             }
+    constexpr int OFF[6][3] = {{1, 0, 0}, {-1, 0, 0}, {0, 1, 0}, {0, -1, 0}, {0, 0, 1}, {0, 0, -1}};
+    T xn[6];
+#pragma unroll
+    for (int q = 0; q < 6; q++) {
+        const int ni = i + OFF[q][0], nj = j + OFF[q][1], nk = k + OFF[q][2];
+        int st = -1;
+        if (ni >= 0 && nj >= 0 && nk >= 0 && ni < N && nj < N && nk < N)
+            st = sov[ni + (int64_t)N * nj + (int64_t)N * N * nk];
+        xn[q] = st >= 0 ? x[st] : (T)0;
+    }
+    T off = (T)0;
+#pragma unroll
+    for (int q = 0; q < 6; q++) off += coef[q] * xn[q];
     return h6 * (diag * x[r] - off);
 }
 

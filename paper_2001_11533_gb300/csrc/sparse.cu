@@ -301,7 +301,84 @@ static int max_row_length(const DevCsr &a, cudaStream_t s, int *out)
     return AMGH_OK;
 }
 
+__global__ void k_count_nonzero(int rows, const int *__restrict__ rp, const double *__restrict__ v, int *__restrict__ cnt)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= rows) return;
+    int c = 0;
+    for (int k = rp[i]; k < rp[i + 1]; k++) c += v[k] != 0.0;
+    cnt[i] = c;
+}
+
+__global__ void k_drop_zeros(int rows, const int *__restrict__ rp, const int *__restrict__ ci,
+                             const double *__restrict__ v, const int *__restrict__ rp2, int *__restrict__ ci2,
+                             double *__restrict__ v2)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= rows) return;
+    int q = rp2[i];
+    for (int k = rp[i]; k < rp[i + 1]; k++)
+        if (v[k] != 0.0) {
+            ci2[q] = ci[k];
+            v2[q] = v[k];
+            q++;
+        }
+}
+
+static int prepare_layout(Arena &ar, DevCsr &a, cudaStream_t s, int force_tpr);
+
+// Solve-phase layout of a.  Entries whose value is exactly zero (the P1
+// stiffness of the Kuhn cube stores 8 of its 15 entries per row as exact
+// zeros) are left out of the SELL copy: a zero term adds nothing to any row
+// sum, so the products are unchanged while the matrix stream shrinks.  The
+// canonical CSR (rp, ci, v) keeps every entry for the setup.
 int prepare_operator(Arena &ar, DevCsr &a, cudaStream_t s, int force_tpr)
+{
+    if (a.rows > 0 && a.nnz > 0 && force_tpr <= 1) {
+        Scratch sc;
+        int *cnt = nullptr, *rp2 = nullptr;
+        TRY(sc.alloc(&cnt, a.rows + 1));
+        TRY(sc.alloc(&rp2, a.rows + 1));
+        k_count_nonzero<<<ceil_div(a.rows, 256), 256, 0, s>>>(a.rows, a.rp, a.v, cnt);
+        LAUNCH_CHECK();
+        int nz = 0;
+        TRY(exclusive_scan<int>(cnt, rp2, a.rows, s, &nz));
+        if ((double)nz < 0.95 * a.nnz) {
+            DevCsr c = a;
+            c.rp = rp2;
+            c.nnz = nz;
+            TRY(sc.alloc(&c.ci, nz));
+            TRY(sc.alloc(&c.v, nz));
+            k_drop_zeros<<<ceil_div(a.rows, 256), 256, 0, s>>>(a.rows, a.rp, a.ci, a.v, rp2, c.ci, c.v);
+            LAUNCH_CHECK();
+            int longest = 0;
+            TRY(max_row_length(c, s, &longest));
+            const double avg = (double)nz / a.rows;
+            const bool uniform = (double)longest * a.rows <= 1.05 * nz;
+            if (!(avg > 16.0 || (avg > 12.0 && !uniform))) { // SELL-32 for the compacted rows
+                c.tpr = 1;
+                c.wmax = longest;
+                TRY(csr_to_sell(ar, c, 1, s));
+                a.tpr = 1;
+                a.wmax = c.wmax;
+                a.nslices = c.nslices;
+                a.sell_nnz = c.sell_nnz;
+                a.ellw = c.ellw;
+                a.sl_ptr = c.sl_ptr;
+                a.sl_ci = c.sl_ci;
+                a.sl_v = c.sl_v;
+                a.sl_v32 = c.sl_v32;
+                a.sl_ci16 = c.sl_ci16;
+                a.nnz_solve = nz;
+                CU(cudaStreamSynchronize(s));
+                return AMGH_OK;
+            }
+        }
+    }
+    return prepare_layout(ar, a, s, force_tpr);
+}
+
+static int prepare_layout(Arena &ar, DevCsr &a, cudaStream_t s, int force_tpr)
 {
     double avg = a.rows > 0 ? (double)a.nnz / a.rows : 0.0;
     int longest = 0;
@@ -609,9 +686,10 @@ int dense_make32(amgh_problem *p, Arena &ar, Dense &d)
 double spmv_bytes(const DevCsr &a, int vb)
 {
     // index bytes per entry and slice / row pointers as the kernels read them
+    const double nnz = a.nnz_solve >= 0 ? a.nnz_solve : a.nnz;
     if (a.tpr <= 1 && a.ellw > 0)
-        return (double)a.nnz * (vb + (a.sl_ci16 ? 2 : 4)) + (double)vb * (a.rows + a.cols);
-    return (double)a.nnz * (vb + 4) + 4.0 * (a.rows + 1) + (double)vb * (a.rows + a.cols);
+        return nnz * (vb + (a.sl_ci16 ? 2 : 4)) + (double)vb * (a.rows + a.cols);
+    return nnz * (vb + 4) + 4.0 * (a.rows + 1) + (double)vb * (a.rows + a.cols);
 }
 
 // ------------------------------------------------------------------ autotuning
