@@ -460,10 +460,10 @@ __device__ void fin_rr(BScal *bs, const double (&t)[K])
 }
 
 // ------------------------------------------------------------------ CG kernels
-// x = 0, r = f, optionally z = invd f (Jacobi); f.f per column
-template <int K>
+// x = 0, r = f, optionally z = invd f (Jacobi, in the type Z of z); f.f per column
+template <typename Z, int K>
 __global__ void kb_cg_start(int n, const double *__restrict__ f, double *__restrict__ x, double *__restrict__ r,
-                            double *__restrict__ z, const double *__restrict__ invd, BScal *bs, double tol2,
+                            Z *__restrict__ z, const double *__restrict__ invd, BScal *bs, double tol2,
                             int maxit, double *partials, unsigned *ticket)
 {
     pdl_enter();
@@ -479,9 +479,10 @@ __global__ void kb_cg_start(int n, const double *__restrict__ f, double *__restr
         stk<K>(x + o, zero);
         stk<K>(r + o, fv);
         if (z) {
-            double iv = invd[i], zv[K];
+            double iv = invd[i];
+            Z zv[K];
 #pragma unroll
-            for (int c = 0; c < K; c++) zv[c] = iv * fv[c];
+            for (int c = 0; c < K; c++) zv[c] = (Z)(iv * fv[c]);
             stk<K>(z + o, zv);
         }
 #pragma unroll
@@ -1318,7 +1319,7 @@ struct Blk {
         int n = S.A.rows;
         int maxit = p->sopts.inner_max_iter;
         const bool f32 = sizeof(T) == sizeof(float);
-        pdl_launch(kb_cg_start<K>, dim3(vblocks(n)), dim3(TPB), 0, p->stream, n, f, B.x, B.r, (double *)nullptr,
+        pdl_launch(kb_cg_start<double, K>, dim3(vblocks(n)), dim3(TPB), 0, p->stream, n, f, B.x, B.r, (double *)nullptr,
                    (const double *)nullptr, B.bs, tol * tol, maxit, B.red.partials, B.red.ticket);
         LAUNCH_CHECK();
         const T *vin = f32 ? (const T *)B.r32 : (const T *)B.r;
@@ -1358,14 +1359,30 @@ struct Blk {
         int n = C.Mu.rows;
         int maxit = p->sopts.mass_max_iter;
         double tol = p->sopts.mass_tol;
-        pdl_launch(kb_cg_start<K>, dim3(vblocks(n)), dim3(TPB), 0, p->stream, n, b, D.mx, D.mr, D.mz,
-                   (const double *)C.mu_invdiag, D.mbs, tol * tol, maxit, D.red.partials, D.red.ticket);
+        // with FP32 V-cycles the Jacobi direction z is kept in FP32 as in the
+        // single-column double-float mass CG: the products stay double-float
+        // from A's FP32 parts, and only the preconditioner is rounded
+        const bool z32 = W.f32 != 0;
+        if (z32)
+            pdl_launch(kb_cg_start<float, K>, dim3(vblocks(n)), dim3(TPB), 0, p->stream, n, b, D.mx, D.mr,
+                       (float *)D.mz, (const double *)C.mu_invdiag, D.mbs, tol * tol, maxit, D.red.partials,
+                       D.red.ticket);
+        else
+            pdl_launch(kb_cg_start<double, K>, dim3(vblocks(n)), dim3(TPB), 0, p->stream, n, b, D.mx, D.mr, D.mz,
+                       (const double *)C.mu_invdiag, D.mbs, tol * tol, maxit, D.red.partials, D.red.ticket);
         LAUNCH_CHECK();
         std::function<int()> iter = [&]() {
-            TRY(cg_spmv<double>(p, C.Mu, D.mz, D.mr, D.ms, D.mbs, D.red));
-            pdl_launch(kb_cg_update<double, K>, dim3(update_blocks<K>(n)), dim3(TPB), 0, p->stream, n, D.mz,
-                       (const double *)D.ms, D.mp, D.mq, D.mx, D.mr, (float *)nullptr,
-                       (const double *)C.mu_invdiag, D.mbs, D.red.partials, D.red.ticket);
+            if (z32) {
+                TRY(cg_spmv<float>(p, C.Mu, (const float *)D.mz, D.mr, D.ms, D.mbs, D.red));
+                pdl_launch(kb_cg_update<float, K>, dim3(update_blocks<K>(n)), dim3(TPB), 0, p->stream, n,
+                           (float *)D.mz, (const double *)D.ms, D.mp, D.mq, D.mx, D.mr, (float *)nullptr,
+                           (const double *)C.mu_invdiag, D.mbs, D.red.partials, D.red.ticket);
+            } else {
+                TRY(cg_spmv<double>(p, C.Mu, D.mz, D.mr, D.ms, D.mbs, D.red));
+                pdl_launch(kb_cg_update<double, K>, dim3(update_blocks<K>(n)), dim3(TPB), 0, p->stream, n, D.mz,
+                           (const double *)D.ms, D.mp, D.mq, D.mx, D.mr, (float *)nullptr,
+                           (const double *)C.mu_invdiag, D.mbs, D.red.partials, D.red.ticket);
+            }
             LAUNCH_CHECK();
             return AMGH_OK;
         };
