@@ -340,6 +340,7 @@ def run_batch(args, rank, world, local):
 
     from paper_2001_11533_gb300 import amgh, replicas, workloads
     every = workloads.batch_squares()
+    tuned = "columns"
     ws = [every[i] for i in replicas.deal(len(every), rank, world)]
     yds = [torch.from_numpy(np.ascontiguousarray(w.y_d)).cuda() for w in ws]
     out = {}
@@ -353,8 +354,22 @@ def run_batch(args, rank, world, local):
         sopts = dict(tol=1e-8, inner_tol=args.inner_tol, mass_tol=args.precond_tol,
                      precond_tol=args.precond_tol, level_fallback=1)
         controls = {}
-        for mode in ("columns", "block"):
-            batch.set_block(mode == "block")
+        for mode in ("columns", "block", "autotuned"):
+            tuning = None
+            if mode == "autotuned":
+                # slot count and block width picked by timing the candidates on this
+                # batch (mixed form, at a looser tolerance); the FP64 form reuses it
+                if form == "mixed":
+                    tuned_choice, tuning = batch.autotune(yds, **dict(sopts, tol=1e-6))
+                    tuned = tuned_choice
+                choice = tuned
+                block, workers = {"columns": (0, 0), "block K=8": (1, 1), "block K=4 x 2 slots": (1, 2),
+                                  "block K=2 x 4 slots": (1, 4)}[choice]
+                batch.set_block(block)
+                batch.set_workers(workers)
+            else:
+                batch.set_block(mode == "block")
+                batch.set_workers(0)
             batch.solve(yds, **sopts)
             times, infos = [], None
             for _ in range(args.batch_steps):
@@ -365,23 +380,31 @@ def run_batch(args, rank, world, local):
             t = max(times)
             happ = sum(i["hessian_applies"] for i in infos)
             (t, ts), (happ,) = replicas.combine([t, t_setup], [happ], device="cuda")
-            out[form if mode == "columns" else form + "_block"] = {
+            key = form if mode == "columns" else form + "_" + mode
+            out[key] = {
                 "time_to_1e-8_s": t, "hessian_matvecs_per_s": happ / t, "hessian_applies": happ,
                 "setup_s": ts, "status": int(st),
                 "outer_iters": sum(i["outer_iters"] for i in infos),
                 "fallbacks": sum(i["fallbacks"] for i in infos),
                 "max_final_relres": max(i["final_relres"] for i in infos),
                 "hessian_levels": [i["hessian_levels"] for i in infos]}
+            if mode == "autotuned":
+                out[key]["choice"] = choice
+                if tuning:
+                    out[key]["tuning_s"] = {k: round(v, 3) for k, v in tuning.items()}
         # both modes run the same method per desired state: controls agree to the tolerance
-        out[form + "_block"]["max_rel_diff_vs_columns"] = max(
-            float(np.linalg.norm(a[c] - b[c]) / max(np.linalg.norm(b[c]), 1e-300))
-            for a, b in zip(controls["block"], controls["columns"]) for c in range(a.shape[0]))
+        for mode in ("block", "autotuned"):
+            out[form + "_" + mode]["max_rel_diff_vs_columns"] = max(
+                float(np.linalg.norm(a[c] - b[c]) / max(np.linalg.norm(b[c]), 1e-300))
+                for a, b in zip(controls[mode], controls["columns"]) for c in range(a.shape[0]))
         batch.close()
         for p in probs:
             p.close()
     out["speedup_mixed_vs_fp64"] = out["fp64"]["time_to_1e-8_s"] / out["mixed"]["time_to_1e-8_s"]
     out["speedup_block_vs_columns_mixed"] = (out["mixed"]["time_to_1e-8_s"]
                                              / out["mixed_block"]["time_to_1e-8_s"])
+    out["speedup_autotuned_vs_columns_mixed"] = (out["mixed"]["time_to_1e-8_s"]
+                                                 / out["mixed_autotuned"]["time_to_1e-8_s"])
     out["workload"] = "16 squares 65^2..513^2, 8 desired states each (128 outer CGs to 1e-8)"
     out["timing"] = "host clock around the synchronous batched solve; max of steps"
     return out

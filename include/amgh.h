@@ -488,6 +488,17 @@ int amgh_batch_set_block(amgh_batch *b, int block);
 int amgh_batch_solve(amgh_batch *b, const double *const *yd_dev, const int *ncols, double *const *u_dev,
                      const amgh_solve_opts *opts, amgh_solve_info *info);
 void amgh_batch_destroy(amgh_batch *b);
+/* Autotuner of the batch's block width and slot count (no counterpart in the
+ * paper; the batching pattern): tries, on the given desired states, one slot
+ * per desired state (block 0), then block solves with K = 8, 4 and 2 columns
+ * on 8/K slots per problem; each candidate solves the batch once (capturing
+ * its graphs) and once more under the host clock, and the fastest stays set
+ * for later amgh_batch_solve calls.  Arguments as amgh_batch_solve (opts may
+ * use a looser tolerance than the real solves); times (4 doubles, host, may
+ * be NULL) receive the candidates' seconds and *choice (may be NULL) the
+ * index kept.  Errors: as amgh_batch_solve. */
+int amgh_batch_autotune(amgh_batch *b, const double *const *yd_dev, const int *ncols, double *const *u_dev,
+                        const amgh_solve_opts *opts, double *times, int *choice);
 
 /* Aggregation of a caller's matrix that allocates no device memory.  The
  * paper has no counterpart: this is a service for callers that cannot call

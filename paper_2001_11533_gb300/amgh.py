@@ -103,6 +103,7 @@ _SIGS = {
     "amgh_batch_setup": ([_P, _P], _I),
     "amgh_batch_set_workers": ([_P, _I], _I),
     "amgh_batch_set_block": ([_P, _I], _I),
+    "amgh_batch_autotune": ([_P, _P, _P, _P, _P, _P, _P], _I),
     "amgh_problem_share": ([_P, _P], _I),
     "amgh_batch_solve": ([_P, _P, _P, _P, _P, _P], _I),
     "amgh_batch_destroy": ([_P], None),
@@ -499,6 +500,30 @@ class Batch:
     def set_block(self, block=True):
         check(lib().amgh_batch_set_block(self.h, 1 if block else 0), "amgh_batch_set_block")
         return self
+
+    def set_workers(self, workers):
+        check(lib().amgh_batch_set_workers(self.h, int(workers)), "amgh_batch_set_workers")
+        return self
+
+    CANDIDATES = ("columns", "block K=8", "block K=4 x 2 slots", "block K=2 x 4 slots")
+
+    def autotune(self, yds, **kw):
+        """amgh_batch_autotune: time the four slot / block-width candidates on
+        these desired states and keep the fastest; returns (choice, seconds)."""
+        import torch
+        np_ = len(self.problems)
+        yds = [y.contiguous() for y in yds]
+        us = [torch.empty_like(y) for y in yds]
+        ycols = (C.c_int * np_)(*[int(y.shape[0]) for y in yds])
+        yptr = (C.c_void_p * np_)(*[y.data_ptr() for y in yds])
+        uptr = (C.c_void_p * np_)(*[u.data_ptr() for u in us])
+        times = (C.c_double * 4)()
+        choice = C.c_int()
+        o = solve_opts(**kw)
+        torch.cuda.synchronize()
+        check(lib().amgh_batch_autotune(self.h, yptr, ycols, uptr, C.byref(o), times, C.byref(choice)),
+              "amgh_batch_autotune")
+        return self.CANDIDATES[choice.value], dict(zip(self.CANDIDATES, list(times)))
 
     def setup(self, **kw):
         o = amg_opts(**kw)

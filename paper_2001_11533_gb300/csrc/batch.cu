@@ -13,6 +13,7 @@
 // more threads than cores do not spin against each other.
 #include <string.h>
 
+#include <chrono>
 #include <new>
 #include <thread>
 #include <vector>
@@ -237,6 +238,36 @@ extern "C" int amgh_batch_solve(amgh_batch *b, const double *const *yd, const in
         for (int i = 0; i < np; i++) info[i] = out[i];
     for (int i = 0; i < np; i++)
         if (out[i].status != AMGH_OK) return out[i].status;
+    return AMGH_OK;
+}
+
+// The block width and slot count autotuner: every candidate -- one slot per
+// desired state, or block solves of K = 8, 4 or 2 columns on 8/K slots per
+// problem -- solves the whole batch once to capture its graphs and once more
+// under the host clock; the fastest is kept for the batch's later solves.
+extern "C" int amgh_batch_autotune(amgh_batch *b, const double *const *yd, const int *ncols, double *const *u,
+                                   const amgh_solve_opts *opts, double *times, int *choice)
+{
+    if (!b) return AMGH_ERR_INVALID_ARG;
+    static const int cand[4][2] = {{0, 0}, {1, 1}, {1, 2}, {1, 4}}; // {block, workers}
+    int best = 0;
+    double tbest = 0.0;
+    for (int k = 0; k < 4; k++) {
+        b->block = cand[k][0];
+        b->workers = cand[k][1];
+        TRY(amgh_batch_solve(b, yd, ncols, u, opts, nullptr));
+        auto t0 = std::chrono::steady_clock::now();
+        TRY(amgh_batch_solve(b, yd, ncols, u, opts, nullptr));
+        double t = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        if (times) times[k] = t;
+        if (k == 0 || t < tbest) {
+            tbest = t;
+            best = k;
+        }
+    }
+    b->block = cand[best][0];
+    b->workers = cand[best][1];
+    if (choice) *choice = best;
     return AMGH_OK;
 }
 

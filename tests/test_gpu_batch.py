@@ -117,3 +117,29 @@ def test_full_batch_16_problems_128_rhs():
     assert st == 0
     assert sum(i["outer_iters"] for i in infos) > 0
     assert all(i["final_relres"] <= 1.5e-8 for i in infos)
+
+
+def test_batch_autotune_keeps_a_candidate_and_the_method():
+    """The block-width / slot autotuner times its four candidates, keeps one, and
+    the batch then still solves every desired state to the same controls (the
+    candidates run the same method per column)."""
+    import torch
+    from paper_2001_11533_gb300 import amgh
+    ws = W.batch_squares(sizes=(33, 65), per_size=1, rhs=4)
+    yds = [torch.from_numpy(np.ascontiguousarray(w.y_d)).cuda() for w in ws]
+    probs = [amgh.Problem.from_workload(w) for w in ws]
+    batch = amgh.Batch(probs).setup(coarse_max=64, precision=2)
+    sopts = dict(tol=1e-10, inner_tol=1e-12, mass_tol=1e-12, precond_tol=1e-12)
+    ref, _, _ = batch.solve(yds, **sopts)
+    choice, times = batch.autotune(yds, **sopts)
+    assert choice in amgh.Batch.CANDIDATES and len(times) == 4 and all(t > 0 for t in times.values())
+    assert times[choice] == min(times.values())
+    us, infos, st = batch.solve(yds, **sopts)
+    assert st == 0
+    for a, b in zip(us, ref):
+        a, b = a.cpu().numpy(), b.cpu().numpy()
+        for c in range(a.shape[0]):
+            assert np.linalg.norm(a[c] - b[c]) <= 1e-8 * np.linalg.norm(b[c])
+    batch.close()
+    for p in probs:
+        p.close()
