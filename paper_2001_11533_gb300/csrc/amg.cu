@@ -305,16 +305,30 @@ int amg_aggregate(amgh_problem *p, const DevCsr &a, double theta2, int *agg, int
 __global__ void k_rho(int n, const int *__restrict__ rp, const int *__restrict__ ci, const double *__restrict__ v,
                       unsigned long long *__restrict__ rho_bits)
 {
+    __shared__ unsigned long long wmax[32];
     int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    double s = 0.0, aii = 0.0;
-    for (int k = rp[i]; k < rp[i + 1]; k++) {
-        s = __dadd_rn(s, fabs(v[k]));
-        if (ci[k] == i) aii = v[k];
+    unsigned long long b = 0;
+    if (i < n) {
+        double s = 0.0, aii = 0.0;
+        for (int k = rp[i]; k < rp[i + 1]; k++) {
+            s = __dadd_rn(s, fabs(v[k]));
+            if (ci[k] == i) aii = v[k];
+        }
+        // non-negative doubles order like their bit patterns
+        b = (unsigned long long)__double_as_longlong(__ddiv_rn(s, aii));
     }
-    double r = __ddiv_rn(s, aii);
-    // non-negative doubles order like their bit patterns
-    atomicMax(rho_bits, (unsigned long long)__double_as_longlong(r));
+    // one atomic per block: the maximum over bit patterns is the same in any order
+    for (int o = 16; o; o >>= 1) {
+        unsigned long long t = __shfl_xor_sync(0xffffffffu, b, o);
+        b = t > b ? t : b;
+    }
+    int warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    if ((threadIdx.x & 31) == 0) wmax[warp] = b;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < nw; w++) b = wmax[w] > b ? wmax[w] : b;
+        atomicMax(rho_bits, b);
+    }
 }
 
 // row i: columns {agg(j)}, values [agg(i)==J] - (omega/a_ii) * sum_{agg(j)=J} a_ij

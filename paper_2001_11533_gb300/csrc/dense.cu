@@ -6,9 +6,10 @@
 //     on Hessian level l-1 and its explicit inverse -- the exact coarsest
 //     inverse G_{l-1}^-1 assumed by the theory (Sec. 3.2).
 // Both inverses come from a blocked right-looking Cholesky factorisation
-// A = L L^T (INDEFINITE if a pivot is not positive), the triangular inverse
-// W = L^-1 computed column by column (one warp per column) and A^-1 = W^T W
-// (upper triangle only, then mirrored).  All FP64 on CUDA cores.
+// A = L L^T (INDEFINITE if a pivot is not positive) whose panel steps also
+// form W = L^-1, then A^-1 = W^T W (upper triangle only, then mirrored).  All
+// FP64 on CUDA cores: GB300's FP64 rate is the same on the tensor pipe, and the
+// K = 32 products that carry the flops run at that rate already.
 #include <math.h>
 
 #include "internal.cuh"
@@ -31,120 +32,306 @@ int dense_from_csr(amgh_problem *p, const DevCsr &a, double *g)
     return AMGH_OK;
 }
 
-// Blocked right-looking Cholesky with NB-wide panels (lower triangle, row-major):
-// for each panel k: factor the NB x NB diagonal block in shared memory, solve
-// the panel below it (L_ik L_kk^T = A_ik, one thread per row), and subtract
-// L_ik L_jk^T from the trailing lower triangle.
+// Blocked right-looking Cholesky A = L L^T (lower triangle, row-major, NB-wide
+// panels) fused with the forward sweep that forms W = L^-1, so that both share
+// the panel steps.  With B = I at the start, panel k does
+//   1. the factorisation of A_kk and D_k = L_kk^-1 (one block, in shared memory);
+//   2. L_ik = A_ik D_k^T for the rows below the panel, and W_k. = D_k B_k.
+//      for block row k of W (columns left of and on the diagonal block);
+//   3. A_ij -= L_ik L_jk^T on the trailing lower triangle and
+//      B_i. -= L_ik W_k. on the rows of W below the panel.
+// Step 3 first updates the next panel's columns alone, then the rest, and the
+// launch that does the rest also runs step 1 of the next panel in its block 0:
+// the serial chain of the diagonal factorisation overlaps the K = NB products
+// that carry the flops.
+//
+// FP64 on this GPU: every FP64 warp instruction holds its SM sub-partition's
+// FP64 unit for the same time whatever the number of active lanes, so the
+// kernels spread FP64 work over all four sub-partitions and over the elements
+// that change, and keep the per-pivot chain to five dependent FP64 operations.
 #define NB 32
+#define DIAG_TRI (NB * (NB - 1) / 2)
 
-__global__ void k_potrf_diag(int n, int k0, double *__restrict__ g, int *__restrict__ info)
+// the single-precision estimate of 1 / sqrt(d) or 1 / d, for d > 0 with a
+// binary exponent within +-120, as a double (exact bit moves, no FP64 work)
+__device__ __forceinline__ double seed_from_float(double d, bool rsq)
 {
-    __shared__ double a[NB][NB + 1];
+    long long b = __double_as_longlong(d);
+    int e = (int)((b >> 52) & 0x7ff) - 1023;
+    float f = __int_as_float(((e + 127) << 23) | (int)((b >> 29) & 0x7fffff));
+    float yf = rsq ? rsqrtf(f) : __fdividef(1.0f, f);
+    int fb = __float_as_int(yf);
+    return __longlong_as_double(((long long)(((fb >> 23) & 0xff) - 127 + 1023) << 52) |
+                                ((long long)(fb & 0x7fffff) << 29));
+}
+
+__device__ __forceinline__ bool seed_range(double d)
+{
+    int e = (int)((__double_as_longlong(d) >> 52) & 0x7ff) - 1023;
+    return e >= -120 && e <= 120;
+}
+
+// Newton-Raphson from the float estimate (relative error about 2^-22, squared
+// by each step, so two steps reach rounding):
+//   1 / d:        y <- y + y (1 - d y)
+//   1 / sqrt(d):  y <- y (3 - d y^2) / 2
+__device__ __forceinline__ double recip_newton(double d)
+{
+    if (!seed_range(d)) return 1.0 / d;
+    double y = seed_from_float(d, false);
+    y = fma(y, fma(-d, y, 1.0), y);
+    return fma(y, fma(-d, y, 1.0), y);
+}
+
+__device__ __forceinline__ double rsqrt_newton(double d)
+{
+    if (!seed_range(d)) return 1.0 / sqrt(d);
+    double y = seed_from_float(d, true), nh = -0.5 * d;
+    y = y * fma(nh, y * y, 1.5);
+    return y * fma(nh, y * y, 1.5);
+}
+
+// positive and finite, from the bits (no FP64 compare on the chain)
+__device__ __forceinline__ bool pivot_ok(double d)
+{
+    long long b = __double_as_longlong(d);
+    return b > 0 && b < 0x7ff0000000000000ll;
+}
+
+// Step 1 for the panel at k0, on a whole block (blockDim.x a multiple of 128).
+// A_kk = L_u diag(p) L_u^T (L_u unit lower) in the right-looking order: pivot
+// p_j, then a_ic -= (a_ij / p_j) a_cj for j < c <= i, one barrier per pivot.
+// Thread 0 updates the next pivot and takes its reciprocal while the warps
+// off its sub-partition update the rest (warps 4w share thread 0's FP64 unit
+// and get no elements).  The columns are scaled to L_u afterwards.  Then
+// X = L_u^-1 by recursive doubling over 2b x 2b diagonal blocks,
+// b = 1, 2, 4, 8, 16: X_21 = -X_22 (L_21 X_11), and D = L^-1 = diag(p)^-1/2 X.
+// Rows past the matrix are the identity, so the ragged last panel needs no
+// special case.  A pivot that is not positive sets *info (1-based row) and is
+// replaced by 1.
+__device__ void diag_factor(int n, int k0, const double *__restrict__ g, double *__restrict__ dinv,
+                            int *__restrict__ info)
+{
+    __shared__ double a[NB][NB + 1], x[NB][NB + 1], tmp[NB][NB + 1];
+    __shared__ double piv[NB], rr[NB];
+    __shared__ unsigned short tab[DIAG_TRI]; // row-major lower triangle (i, c <= i) of a 31 x 31 block
+    int t = threadIdx.x, nt = blockDim.x;
     int nb = min(NB, n - k0);
-    int t = threadIdx.x;
-    for (int e = t; e < nb * nb; e += blockDim.x) a[e / nb][e % nb] = g[(int64_t)(k0 + e / nb) * n + k0 + e % nb];
+    for (int e = t; e < NB * NB; e += nt) {
+        int r = e / NB, c = e % NB;
+        a[r][c] = r < nb && c < nb ? (c <= r ? g[(int64_t)(k0 + r) * n + k0 + c] : 0.0) : (r == c ? 1.0 : 0.0);
+        x[r][c] = r == c ? 1.0 : 0.0;
+    }
+    for (int i = t; i < NB - 1; i += nt)
+        for (int c = 0; c <= i; c++) tab[i * (i + 1) / 2 + c] = (unsigned short)((i << 8) | c);
+    auto take_pivot = [&](int j, double p) {
+        if (!pivot_ok(p)) {
+            atomicCAS(info, 0, k0 + j + 1);
+            p = 1.0;
+        }
+        piv[j] = p;
+        rr[j] = recip_newton(p);
+    };
+    __syncthreads();
+    if (t == 0) take_pivot(0, a[0][0]);
+    int warp = t >> 5;
+    bool worker = (warp & 3) != 0;
+    int wk = (warp - (warp >> 2) - 1) * 32 + (t & 31), nwk = nt / 4 * 3;
     __syncthreads();
     for (int j = 0; j < nb; j++) {
+        double r = rr[j];
+        int m = nb - 1 - j, E = m * (m + 1) / 2;
         if (t == 0) {
-            double d = a[j][j];
-            if (!(d > 0.0)) {
-                atomicCAS(info, 0, k0 + j + 1);
-                d = 1.0;
+            if (E > 0) {
+                double u = a[j + 1][j];
+                double p = fma(-(u * r), u, a[j + 1][j + 1]);
+                a[j + 1][j + 1] = p;
+                take_pivot(j + 1, p);
             }
-            a[j][j] = sqrt(d);
-        }
-        __syncthreads();
-        double ljj = a[j][j];
-        for (int i = j + 1 + t; i < nb; i += blockDim.x) a[i][j] /= ljj;
-        __syncthreads();
-        for (int e = t; e < (nb - j - 1) * (nb - j - 1); e += blockDim.x) {
-            int i = j + 1 + e / (nb - j - 1), c = j + 1 + e % (nb - j - 1);
-            if (c <= i) a[i][c] -= a[i][j] * a[c][j];
+        } else if (worker) {
+            for (int e = 1 + wk; e < E; e += nwk) {
+                int pk = tab[e], i = j + 1 + (pk >> 8), c = j + 1 + (pk & 255);
+                a[i][c] = fma(-(a[i][j] * r), a[c][j], a[i][c]);
+            }
         }
         __syncthreads();
     }
-    for (int e = t; e < nb * nb; e += blockDim.x) {
-        int i = e / nb, c = e % nb;
-        g[(int64_t)(k0 + i) * n + k0 + c] = c <= i ? a[i][c] : 0.0;
-    }
-}
-
-// rows i >= k0 + NB: solve x L_kk^T = g[i, k0:k0+nb] by forward substitution,
-// one warp per row: lane c holds x_c's running value and subtracts
-// x_q l_cq for q = 0, 1, ... in order, x_q broadcast from lane q when final
-#define TRSM_WARPS 8
-__global__ void k_trsm_panel(int n, int k0, double *__restrict__ g)
-{
-    __shared__ double l[NB][NB + 1];
-    int nb = min(NB, n - k0);
-    for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) l[e / nb][e % nb] = g[(int64_t)(k0 + e / nb) * n + k0 + e % nb];
-    __syncthreads();
-    int lane = threadIdx.x & 31;
-    int i = k0 + nb + blockIdx.x * TRSM_WARPS + (threadIdx.x >> 5);
-    if (i >= n) return; // warp-uniform
-    double *row = g + (int64_t)i * n + k0;
-    double sc = lane < nb ? row[lane] : 0.0;
-    for (int q = 0; q < nb; q++) {
-        double xq = __shfl_sync(0xffffffffu, sc / l[q][q], q); // final on lane q
-        if (lane == q) sc = xq;
-        if (lane > q && lane < nb) sc -= xq * l[lane][q];
-    }
-    if (lane < nb) row[lane] = sc;
-}
-
-// trailing update g[i][j] -= sum_c L[i][k0+c] L[j][k0+c] for k0+nb <= j <= i (16x16 tiles)
-__global__ void k_syrk_update(int n, int k0, double *__restrict__ g)
-{
-    __shared__ double Ai[16][NB + 1], Aj[16][NB + 1];
-    int nb = min(NB, n - k0);
-    int base = k0 + nb;
-    int ti = blockIdx.y * 16, tj = blockIdx.x * 16;
-    if (tj > ti) return; // upper tiles untouched (block-uniform)
-    int t = threadIdx.y * 16 + threadIdx.x;
-    for (int e = t; e < 16 * nb; e += 256) {
-        int r = e / nb, c = e % nb;
-        int gi = base + ti + r, gj = base + tj + r;
-        Ai[r][c] = gi < n ? g[(int64_t)gi * n + k0 + c] : 0.0;
-        Aj[r][c] = gj < n ? g[(int64_t)gj * n + k0 + c] : 0.0;
+    for (int e = t; e < DIAG_TRI; e += nt) { // l_rq = a_rq / p_q below the diagonal
+        int pk = tab[e], r = (pk >> 8) + 1, q = pk & 255;
+        if (q < nb) a[r][q] *= rr[q];
     }
     __syncthreads();
-    int i = base + ti + threadIdx.y, j = base + tj + threadIdx.x;
-    if (i >= n || j > i) return;
-    double s = 0.0;
-    for (int c = 0; c < nb; c++) s += Ai[threadIdx.y][c] * Aj[threadIdx.x][c];
-    g[(int64_t)i * n + j] -= s;
+    for (int lb = 0; lb < 5; lb++) { // b = 2^lb; 16 / b pairs of b x b blocks
+        int b = 1 << lb, sh = 2 * lb;
+        for (int e = t; e < 16 * b; e += nt) { // tmp = L_21 X_11
+            int o = (e >> sh) * 2 * b, r = (e & (b * b - 1)) >> lb, c = e & (b - 1);
+            double s0 = 0.0, s1 = 0.0;
+            int q = c;
+            for (; q + 1 < b; q += 2) {
+                s0 = fma(a[o + b + r][o + q], x[o + q][o + c], s0);
+                s1 = fma(a[o + b + r][o + q + 1], x[o + q + 1][o + c], s1);
+            }
+            if (q < b) s0 = fma(a[o + b + r][o + q], x[o + q][o + c], s0);
+            tmp[o + b + r][o + c] = s0 + s1;
+        }
+        __syncthreads();
+        for (int e = t; e < 16 * b; e += nt) { // X_21 = -X_22 tmp
+            int o = (e >> sh) * 2 * b, r = (e & (b * b - 1)) >> lb, c = e & (b - 1);
+            double s0 = 0.0, s1 = 0.0;
+            int q = 0;
+            for (; q + 1 <= r; q += 2) {
+                s0 = fma(x[o + b + r][o + b + q], tmp[o + b + q][o + c], s0);
+                s1 = fma(x[o + b + r][o + b + q + 1], tmp[o + b + q + 1][o + c], s1);
+            }
+            if (q <= r) s0 = fma(x[o + b + r][o + b + q], tmp[o + b + q][o + c], s0);
+            x[o + b + r][o + c] = -(s0 + s1);
+        }
+        __syncthreads();
+    }
+    if (t < nb) rr[t] = rsqrt_newton(piv[t]);
+    __syncthreads();
+    double *d = dinv + (int64_t)(k0 / NB) * NB * NB;
+    for (int e = t; e < NB * NB; e += nt) {
+        int r = e / NB, c = e % NB;
+        d[e] = c <= r ? (r < nb ? x[r][c] * rr[r] : x[r][c]) : 0.0;
+    }
 }
 
-// column k of W = L^-1 (one warp per column): w_k = 1 / l_kk and, for i > k,
-// w_i = -(sum_{k <= j < i} l_ij w_j) / l_ii; the column is kept in shared memory
-#define TRINV_WARPS 4
-__global__ void k_trinv(int n, const double *__restrict__ L, double *__restrict__ W)
+__global__ void __launch_bounds__(128) k_potrf_diag(int n, int k0, const double *__restrict__ g,
+                                                    double *__restrict__ dinv, int *__restrict__ info)
 {
-    extern __shared__ double wsh[];
+    diag_factor(n, k0, g, dinv, info);
+}
+
+// step 2: blocks [0, rb) turn 4 rows each of the panel into L_ik; the next
+// (k0/NB + 1) * NB/PANEL_WARPS blocks each form 4 rows of one 32-column strip
+// of W_k. (one row per warp, so that no warp issues more than NB FP64 FMAs).
+#define PANEL_WARPS 4
+__global__ void __launch_bounds__(32 * PANEL_WARPS) k_panel(int n, int k0, int rb, double *__restrict__ g,
+                                                            const double *__restrict__ dinv, double *__restrict__ W)
+{
+    __shared__ double d[NB][NB + 1], sb[NB][NB + 1];
+    const double *dk = dinv + (int64_t)(k0 / NB) * NB * NB;
+    for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) d[e / NB][e % NB] = dk[e];
+    int nb = min(NB, n - k0);
     int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    int k = blockIdx.x * TRINV_WARPS + warp;
-    if (k >= n) return; // warp-uniform
-    double *w = wsh + (int64_t)warp * n;
-    if (lane == 0) w[k] = 1.0 / L[(int64_t)k * n + k];
-    __syncwarp();
-    for (int i = k + 1; i < n; i++) {
-        const double *row = L + (int64_t)i * n;
-        double s = 0.0;
-        for (int j = k + lane; j < i; j += 32) s += row[j] * w[j];
-        s = warp_sum(s);
-        if (lane == 0) w[i] = -s / row[i];
-        __syncwarp();
+    if (blockIdx.x < rb) {
+        __syncthreads();
+        int i = k0 + nb + blockIdx.x * PANEL_WARPS + warp;
+        if (i >= n) return; // warp-uniform, no block barrier follows
+        double *row = g + (int64_t)i * n + k0;
+        double gq = lane < nb ? row[lane] : 0.0;
+        double acc0 = 0.0, acc1 = 0.0; // two chains: FP64 latency, not issue, bounds one warp
+#pragma unroll
+        for (int q = 0; q < NB; q += 2) {
+            acc0 = fma(__shfl_sync(0xffffffffu, gq, q), d[lane][q], acc0);
+            acc1 = fma(__shfl_sync(0xffffffffu, gq, q + 1), d[lane][q + 1], acc1);
+        }
+        if (lane < nb) row[lane] = acc0 + acc1;
+        return;
     }
-    for (int i = lane; i < n; i += 32) W[(int64_t)i * n + k] = i >= k ? w[i] : 0.0;
+    int sblk = blockIdx.x - rb, strip = sblk / (NB / PANEL_WARPS), c0 = strip * NB, col = c0 + lane;
+    int r = (sblk % (NB / PANEL_WARPS)) * PANEL_WARPS + warp;
+    if (c0 == k0) { // the diagonal block: B_kk = I
+        __syncthreads();
+        if (r < nb && lane < nb) W[(int64_t)(k0 + r) * n + col] = d[r][lane];
+        return;
+    }
+    for (int q = warp; q < NB; q += PANEL_WARPS) sb[q][lane] = q < nb ? W[(int64_t)(k0 + q) * n + col] : 0.0;
+    __syncthreads();
+    if (r >= nb) return;
+    double y0 = 0.0, y1 = 0.0;
+#pragma unroll
+    for (int q = 0; q < NB; q += 2) {
+        y0 = fma(d[r][q], sb[q][lane], y0);
+        y1 = fma(d[r][q + 1], sb[q + 1][lane], y1);
+    }
+    W[(int64_t)(k0 + r) * n + col] = y0 + y1;
+}
+
+// step 3 tiles, 16 x 16 on 256 threads.  An A tile (ti, tj), tj <= ti, of the
+// trailing matrix below and right of the panel at k0: A_ij -= sum_c L_ic L_jc
+// on and below the diagonal.  A W tile: rows below the panel times the first
+// k0 + nb columns, B_ij -= sum_c L_ic W_(k0+c)j.
+__device__ __forceinline__ void trail_tile(int n, int k0, int ti, int tj, bool wtile, double *__restrict__ g,
+                                           double *__restrict__ W)
+{
+    __shared__ double Li[16][NB + 1], Rj[NB][17];
+    int nb = min(NB, n - k0), base = k0 + nb;
+    int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    int r0 = base + ti * 16, j0 = wtile ? tj * 16 : base + tj * 16;
+    for (int e = threadIdx.x; e < 16 * NB; e += 256) {
+        int r = e / NB, c = e % NB;
+        Li[r][c] = r0 + r < n && c < nb ? g[(int64_t)(r0 + r) * n + k0 + c] : 0.0;
+        if (!wtile) Rj[c][r] = j0 + r < n && c < nb ? g[(int64_t)(j0 + r) * n + k0 + c] : 0.0;
+    }
+    if (wtile)
+        for (int e = threadIdx.x; e < NB * 16; e += 256) {
+            int c = e / 16, q = e % 16;
+            Rj[c][q] = c < nb && j0 + q < base ? W[(int64_t)(k0 + c) * n + j0 + q] : 0.0;
+        }
+    __syncthreads();
+    int i = r0 + ty, j = j0 + tx;
+    if (i >= n || (wtile ? j >= base : j > i)) return;
+    double s0 = 0.0, s1 = 0.0;
+#pragma unroll
+    for (int c = 0; c < NB; c += 2) {
+        s0 = fma(Li[ty][c], Rj[c][tx], s0);
+        s1 = fma(Li[ty][c + 1], Rj[c + 1][tx], s1);
+    }
+    double *out = wtile ? W : g;
+    out[(int64_t)i * n + j] -= s0 + s1;
+}
+
+__device__ __forceinline__ void tri_decode(int t, int &ti, int &tj)
+{
+    ti = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
+    while ((ti + 1) * (ti + 2) / 2 <= t) ti++;
+    while (ti * (ti + 1) / 2 > t) ti--;
+    tj = t - ti * (ti + 1) / 2;
+}
+
+// the next panel's columns: A tiles (ti, 0) for ti < T and (ti, 1) for 1 <= ti < T
+__global__ void __launch_bounds__(256) k_trail_next(int n, int k0, int T, double *__restrict__ g)
+{
+    int t = blockIdx.x;
+    if (t < T) trail_tile(n, k0, t, 0, false, g, nullptr);
+    else trail_tile(n, k0, t - T + 1, 1, false, g, nullptr);
+}
+
+// the rest: block 0 factors the next panel's diagonal block (updated by
+// k_trail_next), blocks [1, 1 + ta) the A tiles with 2 <= tj <= ti, the rest
+// the W tiles (T rows x tw columns of tiles)
+__global__ void __launch_bounds__(256) k_trail_rest(int n, int k0, int T, int ta, int tw, double *__restrict__ g,
+                                                    double *__restrict__ W, double *__restrict__ dinv,
+                                                    int *__restrict__ info)
+{
+    int t = blockIdx.x;
+    if (t == 0) {
+        diag_factor(n, k0 + NB, g, dinv, info);
+        return;
+    }
+    t -= 1;
+    if (t < ta) {
+        int ti, tj;
+        tri_decode(t, ti, tj);
+        trail_tile(n, k0, ti + 2, tj + 2, false, g, W);
+        return;
+    }
+    t -= ta;
+    trail_tile(n, k0, t / tw, t % tw, true, g, W);
 }
 
 // C = op(A) B (+ beta D), all row-major; transA: A is k x m and used as A^T
 #define TILE 16
+// lower != 0: only the tiles on and below the diagonal (C symmetric, and only
+// its lower triangle is read afterwards)
 __global__ void k_gemm(int m, int n, int kdim, const double *__restrict__ A, int transA,
                        const double *__restrict__ B, double beta, const double *__restrict__ D,
-                       double *__restrict__ C)
+                       double *__restrict__ C, int lower)
 {
     __shared__ double As[TILE][TILE + 1], Bs[TILE][TILE + 1];
+    if (lower && blockIdx.x > blockIdx.y) return; // block-uniform
     int row = blockIdx.y * TILE + threadIdx.y, col = blockIdx.x * TILE + threadIdx.x;
     double acc = 0.0;
     for (int k0 = 0; k0 < kdim; k0 += TILE) {
@@ -166,10 +353,10 @@ __global__ void k_gemm(int m, int n, int kdim, const double *__restrict__ A, int
 }
 
 static int gemm(amgh_problem *p, int m, int n, int k, const double *A, int transA, const double *B, double beta,
-                const double *D, double *C)
+                const double *D, double *C, int lower)
 {
     dim3 blk(TILE, TILE), grd(ceil_div(n, TILE), ceil_div(m, TILE));
-    k_gemm<<<grd, blk, 0, p->stream>>>(m, n, k, A, transA, B, beta, D, C);
+    k_gemm<<<grd, blk, 0, p->stream>>>(m, n, k, A, transA, B, beta, D, C, lower);
     LAUNCH_CHECK();
     return AMGH_OK;
 }
@@ -228,42 +415,39 @@ static int csr_dense(amgh_problem *p, const DevCsr &a, const double *D, int ld, 
 
 int dense_spd_inverse(amgh_problem *p, double *g, int n, double *inv, int *info_dev)
 {
+    if (n <= 0) return AMGH_OK;
     cudaStream_t s = p->stream;
+    Scratch sc;
+    double *W = nullptr, *dinv = nullptr;
+    TRY(sc.alloc(&W, (int64_t)n * n));
+    TRY(sc.alloc(&dinv, (int64_t)ceil_div(n, NB) * NB * NB));
     CU(cudaMemsetAsync(info_dev, 0, sizeof(int), s));
+    CU(cudaMemsetAsync(W, 0, sizeof(double) * (size_t)n * n, s));
+    k_potrf_diag<<<1, 128, 0, s>>>(n, 0, g, dinv, info_dev);
+    LAUNCH_CHECK();
     for (int k0 = 0; k0 < n; k0 += NB) {
-        k_potrf_diag<<<1, 256, 0, s>>>(n, k0, g, info_dev);
+        int nb = n - k0 < NB ? n - k0 : NB, m = n - k0 - nb;
+        int rb = ceil_div(m, PANEL_WARPS);
+        k_panel<<<rb + (k0 / NB + 1) * (NB / PANEL_WARPS), 32 * PANEL_WARPS, 0, s>>>(n, k0, rb, g, dinv, W);
         LAUNCH_CHECK();
-        int rest = n - k0 - NB;
-        if (rest > 0) {
-            k_trsm_panel<<<ceil_div(rest, TRSM_WARPS), 32 * TRSM_WARPS, 0, s>>>(n, k0, g);
+        if (m > 0) {
+            int T = ceil_div(m, 16), tw = ceil_div(k0 + nb, 16), ta = T > 2 ? (T - 2) * (T - 1) / 2 : 0;
+            k_trail_next<<<T > 1 ? 2 * T - 1 : 1, 256, 0, s>>>(n, k0, T, g);
             LAUNCH_CHECK();
-            int tiles = ceil_div(rest, 16);
-            k_syrk_update<<<dim3(tiles, tiles), dim3(16, 16), 0, s>>>(n, k0, g);
+            k_trail_rest<<<1 + ta + T * tw, 256, 0, s>>>(n, k0, T, ta, tw, g, W, dinv, info_dev);
             LAUNCH_CHECK();
         }
     }
-    int info = 0;
-    CU(cudaMemcpyAsync(&info, info_dev, sizeof(int), cudaMemcpyDeviceToHost, s));
-    CU(cudaStreamSynchronize(s));
-    if (info) return AMGH_ERR_INDEFINITE;
     // A^-1 = L^-T L^-1 = W^T W
-    Scratch sc;
-    double *W = nullptr;
-    TRY(sc.alloc(&W, (int64_t)n * n));
-    size_t shm = sizeof(double) * (size_t)n * TRINV_WARPS;
-    // per-function limit, set to the largest case (n <= AMGH_DENSE_MAX) so that
-    // setups on several host threads never lower it under one another
-    CU(cudaFuncSetAttribute(k_trinv, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                            (int)(sizeof(double) * (size_t)AMGH_DENSE_MAX * TRINV_WARPS)));
-    k_trinv<<<ceil_div(n, TRINV_WARPS), 32 * TRINV_WARPS, shm, s>>>(n, g, W);
-    LAUNCH_CHECK();
     int tiles = ceil_div(n, TILE);
     k_wtw_upper<<<dim3(tiles, tiles), dim3(TILE, TILE), 0, s>>>(n, W, inv);
     LAUNCH_CHECK();
     k_mirror_lower<<<dim3(tiles, tiles), dim3(TILE, TILE), 0, s>>>(n, inv);
     LAUNCH_CHECK();
+    int info = 0;
+    CU(cudaMemcpyAsync(&info, info_dev, sizeof(int), cudaMemcpyDeviceToHost, s));
     CU(cudaStreamSynchronize(s));
-    return AMGH_OK;
+    return info ? AMGH_ERR_INDEFINITE : AMGH_OK;
 }
 
 // H_c on Hessian level c and its inverse (hinv, n_c x n_c).  With W =
@@ -285,6 +469,6 @@ int dense_coarse_hessian(amgh_problem *p, int c, const double *ainv, double *hin
     TRY(dense_from_csr(p, C.Mu, Mu));
     TRY(csr_dense(p, C.Myut, ainv, m, m, 0, W)); // W = M_yu^T A^-1   (n x m)
     TRY(csr_dense(p, S.My, W, m, n, 1, U));      // U = M_y W^T       (m x n)
-    TRY(gemm(p, n, n, m, W, 0, U, p->beta, Mu, H)); // H = W U + beta M_u
+    TRY(gemm(p, n, n, m, W, 0, U, p->beta, Mu, H, 1)); // H = W U + beta M_u, lower triangle
     return dense_spd_inverse(p, H, n, hinv, info);
 }

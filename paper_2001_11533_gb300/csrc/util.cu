@@ -129,93 +129,98 @@ void Arena::free_all()
 }
 
 // ------------------------------------------------------------------ scans
-// Exclusive prefix sum of `n` values into out[0..n] (out[n] = total), in three
-// passes: per-block sums, a single-block scan of the block sums, per-block
-// scans with the block offset.  Integer addition, so the result is exact.
+// Exclusive prefix sum of `n` values into out[0..n] (out[n] = total).  Up to
+// SCAN_ONE values: one block, each thread a contiguous chunk.  Beyond: three
+// passes (per-block sums, a single-block scan of the block sums, per-block
+// scans with the block offset; the last block also writes the total).  Integer
+// addition, so the result is exact in any order.  in == out is allowed: every
+// element is read and then written by the same thread.
+#define SCAN_ONE 16384
+
+// inclusive scan of one value per thread over a block of 1024 threads
 template <typename T>
-__global__ void k_scan_blocksum(const T *__restrict__ in, int64_t n, T *__restrict__ bsum)
+__device__ __forceinline__ T block_incl_scan(T v, T *wsum)
 {
-    __shared__ T sh[1024];
-    int64_t i = (int64_t)blockIdx.x * 1024 + threadIdx.x;
-    sh[threadIdx.x] = i < n ? in[i] : (T)0;
-    __syncthreads();
-    for (int s = 512; s > 0; s >>= 1) {
-        if ((int)threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
-        __syncthreads();
+    int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int o = 1; o < 32; o <<= 1) {
+        T t = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += t;
     }
-    if (threadIdx.x == 0) bsum[blockIdx.x] = sh[0];
+    if (lane == 31) wsum[warp] = v;
+    __syncthreads();
+    if (warp == 0) {
+        T w = wsum[lane];
+        for (int o = 1; o < 32; o <<= 1) {
+            T t = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += t;
+        }
+        wsum[lane] = w;
+    }
+    __syncthreads();
+    return warp ? v + wsum[warp - 1] : v;
 }
 
 template <typename T>
-__global__ void k_scan_single(T *__restrict__ a, int64_t n, T *__restrict__ total)
+__global__ void __launch_bounds__(1024) k_scan_one(const T *in, int64_t n, T *out)
 {
-    // one block of 1024 threads; each thread scans a contiguous chunk
-    __shared__ T sh[1024];
-    int64_t chunk = (n + 1023) / 1024;
-    int64_t beg = threadIdx.x * chunk, end = beg + chunk < n ? beg + chunk : n;
+    __shared__ T wsum[32];
+    int chunk = (int)((n + 1023) / 1024);
+    int64_t beg = (int64_t)threadIdx.x * chunk, end = beg + chunk < n ? beg + chunk : n;
     T s = 0;
-    for (int64_t i = beg; i < end; i++) s += a[i];
-    sh[threadIdx.x] = s;
-    __syncthreads();
-    // Hillis-Steele inclusive scan of the 1024 chunk sums
-    for (int off = 1; off < 1024; off <<= 1) {
-        T v = (int)threadIdx.x >= off ? sh[threadIdx.x - off] : (T)0;
-        __syncthreads();
-        sh[threadIdx.x] += v;
-        __syncthreads();
-    }
-    T run = threadIdx.x ? sh[threadIdx.x - 1] : (T)0;
+    for (int64_t i = beg; i < end; i++) s += in[i];
+    T incl = block_incl_scan<T>(s, wsum);
+    T run = incl - s;
     for (int64_t i = beg; i < end; i++) {
-        T v = a[i];
-        a[i] = run;
+        T v = in[i];
+        out[i] = run;
         run += v;
     }
-    if (threadIdx.x == 1023 && total) *total = sh[1023];
+    if (threadIdx.x == 1023) out[n] = incl;
 }
 
 template <typename T>
-__global__ void k_scan_apply(const T *__restrict__ in, int64_t n, const T *__restrict__ boff,
-                             T *__restrict__ out)
+__global__ void __launch_bounds__(1024) k_scan_blocksum(const T *__restrict__ in, int64_t n, T *__restrict__ bsum)
 {
-    __shared__ T sh[1024];
+    __shared__ T wsum[32];
+    int64_t i = (int64_t)blockIdx.x * 1024 + threadIdx.x;
+    T incl = block_incl_scan<T>(i < n ? in[i] : (T)0, wsum);
+    if (threadIdx.x == 1023) bsum[blockIdx.x] = incl;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(1024) k_scan_apply(const T *in, int64_t n, const T *__restrict__ boff, T *out)
+{
+    __shared__ T wsum[32];
     int64_t i = (int64_t)blockIdx.x * 1024 + threadIdx.x;
     T v = i < n ? in[i] : (T)0;
-    sh[threadIdx.x] = v;
-    __syncthreads();
-    for (int off = 1; off < 1024; off <<= 1) {
-        T t = (int)threadIdx.x >= off ? sh[threadIdx.x - off] : (T)0;
-        __syncthreads();
-        sh[threadIdx.x] += t;
-        __syncthreads();
-    }
-    if (i < n) out[i] = boff[blockIdx.x] + sh[threadIdx.x] - v;
+    T incl = block_incl_scan<T>(v, wsum);
+    if (i < n) out[i] = boff[blockIdx.x] + incl - v;
+    if (i == n - 1) out[n] = boff[blockIdx.x] + incl;
 }
-
-template <typename T>
-__global__ void k_set_total(T *out, int64_t n, const T *total) { out[n] = *total; }
 
 template <typename T>
 int exclusive_scan(const T *in, T *out, int64_t n, cudaStream_t s, T *total_host)
 {
-    // out has n+1 entries; in may alias out only if in == out is not required
-    int nb = ceil_div(n > 0 ? n : 1, 1024);
-    Scratch sc;
-    T *bsum = nullptr, *tot = nullptr;
-    TRY(sc.alloc(&bsum, nb));
-    TRY(sc.alloc(&tot, 1));
-    k_scan_blocksum<T><<<nb, 1024, 0, s>>>(in, n, bsum);
-    LAUNCH_CHECK();
-    k_scan_single<T><<<1, 1024, 0, s>>>(bsum, nb, tot);
-    LAUNCH_CHECK();
-    k_scan_apply<T><<<nb, 1024, 0, s>>>(in, n, bsum, out);
-    LAUNCH_CHECK();
-    k_set_total<T><<<1, 1, 0, s>>>(out, n, tot);
-    LAUNCH_CHECK();
+    if (n <= SCAN_ONE) {
+        k_scan_one<T><<<1, 1024, 0, s>>>(in, n, out);
+        LAUNCH_CHECK();
+    } else {
+        int nb = (int)ceil_div(n, 1024);
+        Scratch sc;
+        T *bsum = nullptr;
+        TRY(sc.alloc(&bsum, nb + 1));
+        k_scan_blocksum<T><<<nb, 1024, 0, s>>>(in, n, bsum);
+        LAUNCH_CHECK();
+        k_scan_one<T><<<1, 1024, 0, s>>>(bsum, nb, bsum); // block offsets, in place
+        LAUNCH_CHECK();
+        k_scan_apply<T><<<nb, 1024, 0, s>>>(in, n, bsum, out);
+        LAUNCH_CHECK();
+    } // bsum is freed in stream order
     if (total_host) {
-        CU(cudaMemcpyAsync(total_host, tot, sizeof(T), cudaMemcpyDeviceToHost, s));
+        CU(cudaMemcpyAsync(total_host, out + n, sizeof(T), cudaMemcpyDeviceToHost, s));
         CU(cudaStreamSynchronize(s));
     }
-    return AMGH_OK; // bsum / tot are freed in stream order
+    return AMGH_OK;
 }
 
 template int exclusive_scan<int>(const int *, int *, int64_t, cudaStream_t, int *);
