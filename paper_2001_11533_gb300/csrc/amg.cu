@@ -603,6 +603,13 @@ __device__ int g_spgemm_bad = 0;
 
 __device__ __forceinline__ unsigned hslot(int key, unsigned mask) { return ((unsigned)key * 2654435761u) & mask; }
 
+// 0.0 + x for finite x (the first term of a sum that starts from +0): only -0
+// changes, to +0; done on the bits, off the FP64 pipe
+__device__ __forceinline__ double plus_zero(double x)
+{
+    return __double_as_longlong(x) == (long long)0x8000000000000000ull ? 0.0 : x;
+}
+
 __global__ void k_gemm_ub(int n, const int *__restrict__ arp, const int *__restrict__ aci,
                           const int *__restrict__ brp, long long *__restrict__ ub, int *__restrict__ path_of,
                           int small_n, int use_dense, int bhash_u, int *__restrict__ umax3,
@@ -670,19 +677,24 @@ __global__ void k_gemm_hash(int n, const int *__restrict__ arp, const int *__res
             for (int q = 0; q < NV; q++) aij[q] = V.a[q][k];
             for (int e = brp[j]; e < brp[j + 1]; e++) {
                 int J = bci[e];
+                // the products before the probe loop, where the warp still runs
+                // together: an FP64 warp instruction costs the same with one
+                // active lane as with 32
+                double prod[NV];
+#pragma unroll
+                for (int q = 0; q < NV; q++) prod[q] = __dmul_rn(aij[q], V.b[q][e]);
                 unsigned h = hslot(J, mask);
                 for (;;) {
                     int kk = key[h];
                     if (kk == J) {
 #pragma unroll
-                        for (int q = 0; q < NV; q++)
-                            T.v[q][base + h] = __dadd_rn(T.v[q][base + h], __dmul_rn(aij[q], V.b[q][e]));
+                        for (int q = 0; q < NV; q++) T.v[q][base + h] = __dadd_rn(T.v[q][base + h], prod[q]);
                         break;
                     }
                     if (kk < 0) {
                         key[h] = J;
 #pragma unroll
-                        for (int q = 0; q < NV; q++) T.v[q][base + h] = __dadd_rn(0.0, __dmul_rn(aij[q], V.b[q][e]));
+                        for (int q = 0; q < NV; q++) T.v[q][base + h] = plus_zero(prod[q]);
                         c++;
                         break;
                     }
@@ -694,19 +706,51 @@ __global__ void k_gemm_hash(int n, const int *__restrict__ arp, const int *__res
     cnt[i] = c;
 }
 
-// path 0 output: the table's entries in ascending column order
+// path 0 output: the table's entries in ascending column order.  Each thread
+// insertion-sorts (column, slot) pairs of its row in shared memory (thread t's
+// k-th pair at [k][t], so a warp's accesses fall in distinct banks) and then
+// writes every entry once; a row with more than OUT_CAP entries sorts in the
+// output arrays instead.
+#define OUT_TPB 128
+#define OUT_CAP 48
 template <int NV>
-__global__ void k_gemm_out(int n, const long long *__restrict__ toff, const int *__restrict__ path_of,
-                           const int *__restrict__ tkey, GemmOut<NV> T, const int *__restrict__ crp,
-                           int *__restrict__ cci, GemmOut<NV> C)
+__global__ void __launch_bounds__(OUT_TPB)
+    k_gemm_out(int n, const long long *__restrict__ toff, const int *__restrict__ path_of,
+               const int *__restrict__ tkey, GemmOut<NV> T, const int *__restrict__ crp, int *__restrict__ cci,
+               GemmOut<NV> C)
 {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    __shared__ int sk[OUT_CAP][OUT_TPB];
+    __shared__ unsigned short ss[OUT_CAP][OUT_TPB];
+    int t = threadIdx.x;
+    int i = blockIdx.x * blockDim.x + t;
     if (i >= n || path_of[i]) return;
     long long base = toff[i];
     unsigned size = (unsigned)(toff[i + 1] - base);
     int b = crp[i], c = 0;
-    for (unsigned t = 0; t < size; t++) {
-        int key = tkey[base + t];
+    if (crp[i + 1] - b <= OUT_CAP && size <= 65536) {
+        for (unsigned u = 0; u < size; u++) {
+            int key = tkey[base + u];
+            if (key < 0) continue;
+            int j = c - 1;
+            while (j >= 0 && sk[j][t] > key) {
+                sk[j + 1][t] = sk[j][t];
+                ss[j + 1][t] = ss[j][t];
+                j--;
+            }
+            sk[j + 1][t] = key;
+            ss[j + 1][t] = (unsigned short)u;
+            c++;
+        }
+        for (int k = 0; k < c; k++) {
+            unsigned u = ss[k][t];
+            cci[b + k] = sk[k][t];
+#pragma unroll
+            for (int q = 0; q < NV; q++) C.v[q][b + k] = T.v[q][base + u];
+        }
+        return;
+    }
+    for (unsigned u = 0; u < size; u++) {
+        int key = tkey[base + u];
         if (key < 0) continue;
         int j = b + c - 1;
         while (j >= b && cci[j] > key) {
@@ -717,7 +761,7 @@ __global__ void k_gemm_out(int n, const long long *__restrict__ toff, const int 
         }
         cci[j + 1] = key;
 #pragma unroll
-        for (int q = 0; q < NV; q++) C.v[q][j + 1] = T.v[q][base + t];
+        for (int q = 0; q < NV; q++) C.v[q][j + 1] = T.v[q][base + u];
         c++;
     }
 }
@@ -1142,7 +1186,7 @@ static int spgemm_nv(amgh_problem *p, Arena &ar, const DevCsr &a, const double *
         Cv.v[q] = cv[q];
     }
     c.v = cv[0];
-    k_gemm_out<NV><<<nb, 128, 0, s>>>(n, toff, path, tkey, T, c.rp, c.ci, Cv);
+    k_gemm_out<NV><<<ceil_div(n, OUT_TPB), OUT_TPB, 0, s>>>(n, toff, path, tkey, T, c.rp, c.ci, Cv);
     LAUNCH_CHECK();
     TRY(launch_lists(1, nullptr, c.rp, c.ci, Cv));
     int bad = 0;

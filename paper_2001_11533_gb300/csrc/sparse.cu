@@ -528,6 +528,7 @@ __global__ void __launch_bounds__(32 * ELL_SLICES)
     if (skip && *skip) return;
     extern __shared__ __align__(16) unsigned char ell_sm[];
     __shared__ __align__(8) uint64_t bar;
+    const int first_polls = *(volatile int *)&g_bulk_first_polls; // issued early: off the wait's path
     const int s0 = blockIdx.x * ELL_SLICES;
     const int ns = min(ELL_SLICES, nslices - s0);
     const int64_t first = (int64_t)s0 * 32 * W;
@@ -551,7 +552,7 @@ __global__ void __launch_bounds__(32 * ELL_SLICES)
         xr = x[row];
     }
     __syncthreads(); // the barrier is initialised before anyone polls it
-    if (!mbar_wait(&bar, 0, *(volatile int *)&g_bulk_first_polls)) {
+    if (!mbar_wait(&bar, 0, first_polls)) {
         if (threadIdx.x == 0) atomicExch(&g_bulk_timeout, 1);
         mbar_wait(&bar, 0, BULK_DRAIN_POLLS); // let the copies into this block's memory finish
         return;
