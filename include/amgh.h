@@ -523,6 +523,24 @@ int amgh_aggregate_noalloc(int n, const int32_t *rowptr_dev, const int32_t *col_
                            const double *val_dev, double theta, void *stream, int32_t *agg_dev,
                            int32_t *nagg_host);
 
+/* Inverse of a dense symmetric positive definite matrix: the kernel sequence
+ * that forms the exact coarsest inverses of the V-cycle (A_{L-1}^-1) and of
+ * the Hessian preconditioner (G_{l-1}^-1, Sec. 3.2), exposed on its own.
+ * Blocked right-looking Cholesky A = L L^T in 32-wide panels fused with the
+ * forward sweep that forms W = L^-1, then A^-1 = W^T W; FP64 throughout.
+ *   n          1 .. 4096 (else AMGH_ERR_INVALID_ARG)
+ *   a_dev      n x n row-major FP64 on the current device; only the lower
+ *              triangle (j <= i) is read, the argument is not modified
+ *   inv_dev    n x n row-major FP64 output (device), the full symmetric
+ *              inverse; undefined if the call does not return AMGH_OK
+ *   stream     cudaStream_t to run on (NULL = legacy default stream)
+ *   info       (host, may be NULL) 0, or the 1-based row of the first pivot
+ *              that was not positive
+ * Errors: INDEFINITE (a pivot <= 0 or not finite: A is not numerically SPD),
+ * INVALID_ARG, OOM, CUDA.  Scratch (2 n^2 doubles) is taken from the
+ * library's stream-ordered pool; the call synchronises `stream`. */
+int amgh_dense_spd_inverse(int n, const double *a_dev, double *inv_dev, void *stream, int *info);
+
 /* Number of kernels this library launched since load (all problems). */
 int64_t amgh_launch_count(void);
 

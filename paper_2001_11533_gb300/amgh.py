@@ -99,6 +99,7 @@ _SIGS = {
     "amgh_kuhn_apply": ([_P, _I, _P, _P], _I),
     "amgh_launch_count": ([], _I64),
     "amgh_aggregate_noalloc": ([_I, _P, _P, _P, _D, _P, _P, _P], _I),
+    "amgh_dense_spd_inverse": ([_I, _P, _P, _P, _P], _I),
     "amgh_batch_create": ([_P, _I, _P], _I),
     "amgh_batch_setup": ([_P, _P], _I),
     "amgh_batch_set_workers": ([_P, _I], _I),
@@ -177,6 +178,23 @@ def aggregate_noalloc(rowptr, col, val, theta, agg_out, stream=None):
                                        C.c_void_p(stream) if stream else None, _ptr(agg_out),
                                        C.byref(nagg)), "amgh_aggregate_noalloc")
     return nagg.value
+
+
+ERR_INDEFINITE = -6
+
+
+def dense_spd_inverse(a, inv_out, stream=None):
+    """amgh_dense_spd_inverse on CUDA float64 tensors (n x n, row-major; the
+    lower triangle of a is read).  Returns (status, info): status 0 or
+    ERR_INDEFINITE (-6), info the 1-based row of the first non-positive pivot;
+    other errors raise AmghError."""
+    n = int(a.shape[0])
+    info = C.c_int32()
+    st = lib().amgh_dense_spd_inverse(n, _ptr(a), _ptr(inv_out), C.c_void_p(stream) if stream else None,
+                                      C.byref(info))
+    if st not in (0, ERR_INDEFINITE):
+        check(st, "amgh_dense_spd_inverse")
+    return st, info.value
 
 
 def _fill(o, kw):

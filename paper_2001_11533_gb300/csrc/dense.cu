@@ -413,10 +413,12 @@ static int csr_dense(amgh_problem *p, const DevCsr &a, const double *D, int ld, 
     return AMGH_OK;
 }
 
-int dense_spd_inverse(amgh_problem *p, double *g, int n, double *inv, int *info_dev)
+// the inverse of the SPD matrix in g (n x n, lower triangle read, overwritten)
+// into inv on stream s; *info_host (if given) gets the 1-based row of the
+// first pivot that was not positive, 0 if none
+static int spd_inverse_on(cudaStream_t s, double *g, int n, double *inv, int *info_dev, int *info_host)
 {
     if (n <= 0) return AMGH_OK;
-    cudaStream_t s = p->stream;
     Scratch sc;
     double *W = nullptr, *dinv = nullptr;
     TRY(sc.alloc(&W, (int64_t)n * n));
@@ -447,7 +449,28 @@ int dense_spd_inverse(amgh_problem *p, double *g, int n, double *inv, int *info_
     int info = 0;
     CU(cudaMemcpyAsync(&info, info_dev, sizeof(int), cudaMemcpyDeviceToHost, s));
     CU(cudaStreamSynchronize(s));
+    if (info_host) *info_host = info;
     return info ? AMGH_ERR_INDEFINITE : AMGH_OK;
+}
+
+int dense_spd_inverse(amgh_problem *p, double *g, int n, double *inv, int *info_dev)
+{
+    return spd_inverse_on(p->stream, g, n, inv, info_dev, nullptr);
+}
+
+extern "C" int amgh_dense_spd_inverse(int n, const double *a_dev, double *inv_dev, void *stream, int *info)
+{
+    if (info) *info = 0;
+    if (n <= 0 || n > AMGH_DENSE_MAX || !a_dev || !inv_dev) return AMGH_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    StreamScope ss(s);
+    Scratch sc;
+    double *g = nullptr;
+    int *info_dev = nullptr;
+    TRY(sc.alloc(&g, (int64_t)n * n));
+    TRY(sc.alloc(&info_dev, 1));
+    CU(cudaMemcpyAsync(g, a_dev, sizeof(double) * (size_t)n * n, cudaMemcpyDeviceToDevice, s));
+    return spd_inverse_on(s, g, n, inv_dev, info_dev, info);
 }
 
 // H_c on Hessian level c and its inverse (hinv, n_c x n_c).  With W =
