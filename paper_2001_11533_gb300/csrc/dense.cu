@@ -203,10 +203,12 @@ __global__ void __launch_bounds__(128) k_potrf_diag(int n, int k0, const double 
     diag_factor(n, k0, g, dinv, info);
 }
 
-// step 2: blocks [0, rb) turn 4 rows each of the panel into L_ik; the next
-// (k0/NB + 1) * NB/PANEL_WARPS blocks each form 4 rows of one 32-column strip
-// of W_k. (one row per warp, so that no warp issues more than NB FP64 FMAs).
-#define PANEL_WARPS 4
+// step 2: blocks [0, rb) turn PANEL_WARPS rows each of the panel into L_ik;
+// the next k0/NB + 1 blocks each form one 32-column strip of W_k. in place,
+// one row per warp (so that no warp issues more than NB FP64 FMAs).  A strip
+// is read whole before any of its rows is written, so it must not be split
+// over blocks: a block that starts late would read rows already replaced.
+#define PANEL_WARPS 32
 __global__ void __launch_bounds__(32 * PANEL_WARPS) k_panel(int n, int k0, int rb, double *__restrict__ g,
                                                             const double *__restrict__ dinv, double *__restrict__ W)
 {
@@ -230,8 +232,8 @@ __global__ void __launch_bounds__(32 * PANEL_WARPS) k_panel(int n, int k0, int r
         if (lane < nb) row[lane] = acc0 + acc1;
         return;
     }
-    int sblk = blockIdx.x - rb, strip = sblk / (NB / PANEL_WARPS), c0 = strip * NB, col = c0 + lane;
-    int r = (sblk % (NB / PANEL_WARPS)) * PANEL_WARPS + warp;
+    int strip = blockIdx.x - rb, c0 = strip * NB, col = c0 + lane;
+    int r = warp;
     if (c0 == k0) { // the diagonal block: B_kk = I
         __syncthreads();
         if (r < nb && lane < nb) W[(int64_t)(k0 + r) * n + col] = d[r][lane];
@@ -430,7 +432,7 @@ static int spd_inverse_on(cudaStream_t s, double *g, int n, double *inv, int *in
     for (int k0 = 0; k0 < n; k0 += NB) {
         int nb = n - k0 < NB ? n - k0 : NB, m = n - k0 - nb;
         int rb = ceil_div(m, PANEL_WARPS);
-        k_panel<<<rb + (k0 / NB + 1) * (NB / PANEL_WARPS), 32 * PANEL_WARPS, 0, s>>>(n, k0, rb, g, dinv, W);
+        k_panel<<<rb + k0 / NB + 1, 32 * PANEL_WARPS, 0, s>>>(n, k0, rb, g, dinv, W);
         LAUNCH_CHECK();
         if (m > 0) {
             int T = ceil_div(m, 16), tw = ceil_div(k0 + nb, 16), ta = T > 2 ? (T - 2) * (T - 1) / 2 : 0;

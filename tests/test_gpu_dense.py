@@ -82,3 +82,40 @@ def test_indefinite_two_by_two_and_limits():
         with pytest.raises(amgh.AmghError) as e:
             amgh.dense_spd_inverse(a, torch.empty_like(a))
         assert e.value.code == -1
+
+
+def test_concurrent_inverses_on_several_streams():
+    """Eight host threads, each on its own CUDA stream, invert different
+    matrices at once (as the batch runtime's solve slots do when each falls
+    back to a coarser Hessian level): every result must still be the inverse.
+    Contention changes when each block of a launch starts, so a kernel whose
+    blocks read data that other blocks of the same launch overwrite fails here."""
+    import threading
+    import torch
+    from paper_2001_11533_gb300 import amgh
+    n, jobs = 1000, 8
+    mats = [spd(n, seed=100 + j) for j in range(jobs)]
+    refs = [np.linalg.inv(a) for a in mats]
+    devs = [torch.from_numpy(np.tril(a)).cuda() for a in mats]
+    outs = [torch.empty_like(d) for d in devs]
+    streams = [torch.cuda.Stream() for _ in range(jobs)]
+    torch.cuda.synchronize()
+    errors = []
+
+    def work(j):
+        try:
+            for _ in range(3):
+                st, info = amgh.dense_spd_inverse(devs[j], outs[j], stream=streams[j].cuda_stream)
+                assert st == 0 and info == 0
+                x = outs[j].cpu().numpy()
+                err = np.linalg.norm(x - refs[j]) / np.linalg.norm(refs[j])
+                assert err <= 1e-9, (j, err)
+        except Exception as e:  # reported on the main thread
+            errors.append(e)
+
+    threads = [threading.Thread(target=work, args=(j,)) for j in range(jobs)]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join()
+    assert not errors, errors
