@@ -18,12 +18,14 @@
 // column that fails (indefinite, non-finite, cap reached) is marked failed and
 // dropped; the other columns carry on.
 //
-// Precision: precision 0 runs FP64 V-cycles and FP64 CG products, as the
-// single-column FP64 path; precisions 1 and 2 run FP32 V-cycles, and the CG
-// operator products A z and M z are accumulated in double-float on the FP32
-// pipe from A = A_hi + A_lo (the refinement form of precision 1 has no block
-// variant).  CG vectors are FP64 throughout, and the control-side operators
-// (M_yu, M_y, M_u, P and their transposes) are applied in FP64.
+// Precision: precision 0 runs FP64 V-cycles and an FP64 CG, as the
+// single-column FP64 path; precisions 1 and 2 run FP32 V-cycles and a
+// double-float CG as the single-column double-float path: vectors, updates,
+// operator products A z and M z (from A = A_hi + A_lo) and reductions on the
+// FP32 pipe, which on GB300 is about 64 times wider than the FP64 one (the
+// refinement form of precision 1 has no block variant).  The control-side
+// operators (M_yu, M_y, M_u, P and their transposes) and the outer CG are
+// applied in FP64.
 #include <math.h>
 #include <string.h>
 
@@ -232,13 +234,15 @@ __device__ __forceinline__ void row_sum_k(const MatView<T> &m, int row, const T 
     }
 }
 
-// row of (A_hi + A_lo) times K columns of z, accumulated in double-float
+// row of (A_hi + A_lo) times K columns of z, accumulated in double-float;
+// every lane of the group returns the K normalised sums
 template <typename Z, int TPR, int K>
 __device__ __forceinline__ void row_sum_df_k(const MatView<float> &m, const float *__restrict__ lo, int row,
-                                             const Z *__restrict__ z, double (&out)[K])
+                                             const Z *__restrict__ z, DF (&out)[K])
 {
     constexpr int STEP = TPR == 1 ? 32 : TPR;
-    constexpr int U = Chunk<Z, K>::U;
+    // K = 8 double-float accumulators already take 16 registers: gather in half chunks
+    constexpr int U = K >= 8 ? ROW_UNROLL / 2 : Chunk<Z, K>::U;
     DF acc[K];
 #pragma unroll
     for (int c = 0; c < K; c++) acc[c] = DF{0.f, 0.f};
@@ -296,7 +300,7 @@ __device__ __forceinline__ void row_sum_df_k(const MatView<float> &m, const floa
         }
     }
 #pragma unroll
-    for (int c = 0; c < K; c++) out[c] = (double)acc[c].hi + (double)acc[c].lo;
+    for (int c = 0; c < K; c++) quick_two_sum(acc[c].hi, acc[c].lo, out[c].hi, out[c].lo);
 }
 
 // ------------------------------------------------------------------ reductions
@@ -354,6 +358,68 @@ __device__ bool reduce_k(const double (&val)[NV], double *partials, unsigned *ti
     return true;
 }
 
+// The same in double-float for the double-float block CG: values transposed
+// through shared memory as in reduce_k, warps summing columns of it, block
+// partials as FP32 pairs, and the last block loading all NV partials of a
+// block at once.
+template <int NV>
+__device__ bool reduce_dfk(const DF (&val)[NV], double *partials, unsigned *ticket, double (&tot)[NV])
+{
+    __shared__ float shh[NV][TPB_K], shl[NV][TPB_K];
+    __shared__ DF stot[NV];
+    __shared__ bool is_last;
+    const int t = threadIdx.x, w = t >> 5, l = t & 31, nb = gridDim.x;
+    float2 *part = reinterpret_cast<float2 *>(partials);
+#pragma unroll
+    for (int q = 0; q < NV; q++) {
+        shh[q][t] = val[q].hi;
+        shl[q][t] = val[q].lo;
+    }
+    __syncthreads();
+    for (int q = w; q < NV; q += TPB_K / 32) {
+        DF s = {0.f, 0.f};
+#pragma unroll
+        for (int j = l; j < TPB_K; j += 32) s = df_add_fast(s, DF{shh[q][j], shl[q][j]});
+        s = df_warp_sum(s);
+        if (l == 0) part[q * nb + blockIdx.x] = make_float2(s.hi, s.lo);
+    }
+    __threadfence();
+    __syncthreads();
+    if (t == 0) is_last = atomicAdd(ticket, 1u) == (unsigned)nb - 1;
+    __syncthreads();
+    if (!is_last) return false;
+    __threadfence();
+    DF s[NV];
+#pragma unroll
+    for (int q = 0; q < NV; q++) s[q] = DF{0.f, 0.f};
+    for (int b = t; b < nb; b += TPB_K) {
+        float2 v[NV];
+#pragma unroll
+        for (int q = 0; q < NV; q++) v[q] = __ldcg(&part[q * nb + b]); // L2: written by other blocks
+#pragma unroll
+        for (int q = 0; q < NV; q++) s[q] = df_add_fast(s[q], DF{v[q].x, v[q].y});
+    }
+#pragma unroll
+    for (int q = 0; q < NV; q++) {
+        shh[q][t] = s[q].hi;
+        shl[q][t] = s[q].lo;
+    }
+    __syncthreads();
+    for (int q = w; q < NV; q += TPB_K / 32) {
+        DF u = {0.f, 0.f};
+#pragma unroll
+        for (int j = l; j < TPB_K; j += 32) u = df_add_fast(u, DF{shh[q][j], shl[q][j]});
+        u = df_warp_sum(u);
+        if (l == 0) stot[q] = u;
+    }
+    __syncthreads();
+    if (t != 0) return false;
+#pragma unroll
+    for (int q = 0; q < NV; q++) tot[q] = df_to_double(stot[q]);
+    *ticket = 0u;
+    return true;
+}
+
 // ------------------------------------------------------------------ finalisers
 __device__ __forceinline__ bool nonfinite(double x) { return !(x == x) || isinf(x); }
 
@@ -367,8 +433,10 @@ __device__ void bs_all(BScal *bs)
 }
 
 // f.f per column: stopping threshold tol^2 f.f; a zero column has converged
+// df: the CG runs on the right side scaled by `scale` (double-float vectors),
+// so r.r and the threshold are kept in scaled units
 template <int K>
-__device__ void fin_start(BScal *bs, const double (&t)[K], double tol2, int maxit)
+__device__ void fin_start(BScal *bs, const double (&t)[K], double tol2, int maxit, bool df = false)
 {
     for (int c = 0; c < K; c++) {
         CgScal &s = bs->c[c];
@@ -389,6 +457,12 @@ __device__ void fin_start(BScal *bs, const double (&t)[K], double tol2, int maxi
         // preconditioner), which keeps tiny residuals inside FP32's range
         double nrm = sqrt(ff);
         s.scale = (nrm > 0.0 && !nonfinite(nrm)) ? exp2(-rint(log2(nrm))) : 1.0;
+        s.ahi = s.alo = s.bhi = s.blo = 0.f;
+        if (df) {
+            double s2 = s.scale * s.scale; // a power of two: exact
+            s.rr = ff * s2;
+            s.thr = tol2 * ff * s2;
+        }
         if (nonfinite(ff)) {
             s.status = CG_NUMERIC;
             s.done = 1;
@@ -429,6 +503,10 @@ __device__ void fin_cg2(BScal *bs, const double (&t)[2 * K])
         s.rz = g;
         s.alpha = alpha;
         s.beta = beta;
+        s.ahi = (float)alpha;
+        s.alo = (float)(alpha - (double)s.ahi);
+        s.bhi = (float)beta;
+        s.blo = (float)(beta - (double)s.bhi);
         s.k1 += 1;
     }
     bs_all<K>(bs);
@@ -491,58 +569,8 @@ __global__ void kb_cg_start(int n, const double *__restrict__ f, double *__restr
     if (reduce_k<K>(v, partials, ticket, tot)) fin_start<K>(bs, tot, tol2, maxit);
 }
 
-// r32 = (float)(scale_c r): input of the FP32 V-cycle
-template <int K>
-__global__ void kb_r32(int n, const double *__restrict__ r, float *__restrict__ r32, const BScal *bs)
-{
-    pdl_enter();
-    if (bs->all) return;
-    double sc[K];
-#pragma unroll
-    for (int c = 0; c < K; c++) sc[c] = bs->c[c].scale;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        int64_t o = (int64_t)i * K;
-        double rv[K];
-        float f[K];
-        ldk<K>(r + o, rv);
-#pragma unroll
-        for (int c = 0; c < K; c++) f[c] = (float)(rv[c] * sc[c]);
-        stk<K>(r32 + o, f);
-    }
-}
-
-// s = A z (double-float products), (r, z) and (z, s) per column -> alpha, beta
-template <typename Z, int TPR, int K>
-__global__ void kb_cg_spmv(MatView<float> A, const float *__restrict__ lo, const Z *__restrict__ z,
-                           const double *__restrict__ r, double *__restrict__ s, BScal *bs, double *partials,
-                           unsigned *ticket)
-{
-    pdl_enter();
-    if (bs->all) return;
-    int row = my_row<TPR>();
-    double sv[K];
-    row_sum_df_k<Z, TPR, K>(A, lo, row, z, sv);
-    double a[2 * K], tot[2 * K];
-#pragma unroll
-    for (int q = 0; q < 2 * K; q++) a[q] = 0.0;
-    if (row < A.rows && row_leader<TPR>()) {
-        int64_t o = (int64_t)row * K;
-        stk<K>(s + o, sv);
-        Z zr[K];
-        double rr[K];
-        ldk_ro<K>(z + o, zr);
-        ldk<K>(r + o, rr);
-#pragma unroll
-        for (int c = 0; c < K; c++) {
-            double zc = (double)zr[c];
-            a[c] = rr[c] * zc;
-            a[K + c] = zc * sv[c];
-        }
-    }
-    if (reduce_k<2 * K>(a, partials, ticket, tot)) fin_cg2<K>(bs, tot);
-}
-
-// the same with FP64 products (precision 0, as the single-column FP64 CG)
+// s = A z with (r, z) and (z, s) per column -> alpha, beta, in FP64 (precision 0,
+// as the single-column FP64 CG)
 template <int TPR, int K>
 __global__ void kb_cg_spmv64(MatView<double> A, const double *__restrict__ z, const double *__restrict__ r,
                              double *__restrict__ s, BScal *bs, double *partials, unsigned *ticket)
@@ -570,13 +598,13 @@ __global__ void kb_cg_spmv64(MatView<double> A, const double *__restrict__ z, co
     if (reduce_k<2 * K>(a, partials, ticket, tot)) fin_cg2<K>(bs, tot);
 }
 
-// p = z + beta p, q = s + beta q, x += alpha p, r -= alpha q per running
-// column; optionally r32 = (float)(scale_c r) or, for Jacobi, z = invd r; r.r
-// per column.  For K = 8 two threads share a row, four columns each.
+// FP64 CG update (precision 0): p = z + beta p, q = s + beta q, x += alpha p,
+// r -= alpha q per running column; for Jacobi z = invd r; r.r per column.
+// For K = 8 two threads share a row, four columns each.
 template <typename Z, int K>
 __global__ void kb_cg_update(int n, Z *z, const double *__restrict__ s, double *__restrict__ pv,
                              double *__restrict__ q, double *__restrict__ x, double *__restrict__ r,
-                             float *__restrict__ r32, const double *__restrict__ invd, BScal *bs, double *partials,
+                             const double *__restrict__ invd, BScal *bs, double *partials,
                              unsigned *ticket)
 {
     constexpr int H = K > 4 ? 2 : 1; // threads per row
@@ -591,14 +619,13 @@ __global__ void kb_cg_update(int n, Z *z, const double *__restrict__ s, double *
     int64_t it0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     // the half a thread takes is fixed (stride is even), so are its scalars
     const int h = H == 1 ? 0 : (int)(it0 & 1);
-    double al[KH], be[KH], scl[KH];
+    double al[KH], be[KH];
     bool run[KH], first[KH];
 #pragma unroll
     for (int c = 0; c < KH; c++) {
         const CgScal &sc = bs->c[h * KH + c];
         al[c] = sc.alpha;
         be[c] = sc.beta;
-        scl[c] = sc.scale;
         run[c] = !sc.done;
         first[c] = sc.beta == 0.0;
     }
@@ -631,12 +658,6 @@ __global__ void kb_cg_update(int n, Z *z, const double *__restrict__ s, double *
         stk<KH>(q + o, qq);
         stk<KH>(x + o, xx);
         stk<KH>(r + o, rr);
-        if (r32) {
-            float f[KH];
-#pragma unroll
-            for (int c = 0; c < KH; c++) f[c] = (float)(rr[c] * scl[c]);
-            stk<KH>(r32 + o, f);
-        }
         if (invd) {
             double iv = invd[i];
             Z zn[KH];
@@ -653,6 +674,203 @@ __global__ void kb_cg_update(int n, Z *z, const double *__restrict__ s, double *
         else v[KH + c] = vh[c];
     }
     if (reduce_k<K>(v, partials, ticket, tot)) fin_rr<K>(bs, tot);
+}
+
+// ------------------------------------------------------------------ double-float CG kernels
+// CG of precisions 1 and 2 (FP32 V-cycles): x, r, p, q and s are double-float,
+// each FP64-sized buffer of n*K doubles used as two FP32 arrays, hi = [0, nK)
+// and lo = [nK, 2nK), interleaved by column like every block vector.  The
+// CG solves for the right side scaled by an exact power of two per column
+// (scale, from ||f||), so the FP32 halves stay far from FP32's exponent
+// limits; the V-cycle reads r's hi half as its input.  Every per-element step
+// and every reduction is on the FP32 pipe, as in the single-column
+// double-float CG; only the conversions from f and to x, once per solve, use
+// FP64.
+
+// 1 / s for s an exact power of two in FP64's normal range, on the bits
+__device__ __forceinline__ double inv_pow2(double s)
+{
+    long long e = (__double_as_longlong(s) >> 52) & 0x7ff;
+    return __longlong_as_double((2046ll - e) << 52);
+}
+
+// f.f per column (FP64, once per solve) -> scale and the scaled threshold
+template <int K>
+__global__ void kbd_norm(int n, const double *__restrict__ f, BScal *bs, double tol2, int maxit,
+                         double *partials, unsigned *ticket)
+{
+    pdl_enter();
+    double v[K], tot[K];
+#pragma unroll
+    for (int c = 0; c < K; c++) v[c] = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        double fv[K];
+        ldk<K>(f + (int64_t)i * K, fv);
+#pragma unroll
+        for (int c = 0; c < K; c++) v[c] = fma(fv[c], fv[c], v[c]);
+    }
+    if (reduce_k<K>(v, partials, ticket, tot)) fin_start<K>(bs, tot, tol2, maxit, true);
+}
+
+// r = scale_c f (split into hi/lo), x = 0; for Jacobi also z = invd r_hi
+template <int K>
+__global__ void kbd_start(int64_t nk, const double *__restrict__ f, float *__restrict__ xh, float *__restrict__ xl,
+                          float *__restrict__ rh, float *__restrict__ rl, float *__restrict__ z,
+                          const float *__restrict__ invd32, const BScal *bs)
+{
+    pdl_enter();
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nk; e += (int64_t)gridDim.x * blockDim.x) {
+        double v = f[e] * bs->c[e & (K - 1)].scale;
+        float h = (float)v, l = (float)(v - (double)h);
+        rh[e] = h;
+        rl[e] = l;
+        xh[e] = 0.f;
+        xl[e] = 0.f;
+        if (z) z[e] = invd32[e / K] * h;
+    }
+}
+
+// s = A z in double-float (A = A_hi + A_lo, FP32 z) with (r, z) and (z, s)
+// per column -> alpha, beta
+template <int TPR, int K>
+__global__ void __launch_bounds__(TPB_K, 3) kbd_spmv(MatView<float> A, const float *__restrict__ lo,
+                                                     const float *__restrict__ z, const float *__restrict__ rh,
+                                                     const float *__restrict__ rl, float *__restrict__ sh,
+                                                     float *__restrict__ sl, BScal *bs, double *partials,
+                                                     unsigned *ticket)
+{
+    pdl_enter();
+    if (bs->all) return;
+    int row = my_row<TPR>();
+    DF sv[K];
+    row_sum_df_k<float, TPR, K>(A, lo, row, z, sv);
+    DF a[2 * K];
+    double tot[2 * K];
+#pragma unroll
+    for (int q = 0; q < 2 * K; q++) a[q] = DF{0.f, 0.f};
+    if (row < A.rows && row_leader<TPR>()) {
+        int64_t o = (int64_t)row * K;
+        float h[K], l[K], zr[K], rhv[K], rlv[K];
+#pragma unroll
+        for (int c = 0; c < K; c++) {
+            h[c] = sv[c].hi;
+            l[c] = sv[c].lo;
+        }
+        stk<K>(sh + o, h);
+        stk<K>(sl + o, l);
+        ldk_ro<K>(z + o, zr);
+        ldk<K>(rh + o, rhv);
+        ldk<K>(rl + o, rlv);
+#pragma unroll
+        for (int c = 0; c < K; c++) {
+            a[c] = df_mulf(DF{rhv[c], rlv[c]}, zr[c]);
+            a[K + c] = df_mulf(sv[c], zr[c]);
+        }
+    }
+    if (reduce_dfk<2 * K>(a, partials, ticket, tot)) fin_cg2<K>(bs, tot);
+}
+
+// p = z + beta p, q = s + beta q, x += alpha p, r -= alpha q per running
+// column in double-float; with invd32 (Jacobi) z = invd r_hi; r.r per column.
+// For K = 8 two threads share a row, four columns each.
+template <int K>
+__global__ void kbd_update(int n, float *z, const float *__restrict__ sh, const float *__restrict__ sl,
+                           float *__restrict__ ph, float *__restrict__ pl, float *__restrict__ qh,
+                           float *__restrict__ ql, float *__restrict__ xh, float *__restrict__ xl,
+                           float *__restrict__ rh, float *__restrict__ rl, const float *__restrict__ invd32,
+                           BScal *bs, double *partials, unsigned *ticket)
+{
+    constexpr int H = K > 4 ? 2 : 1; // threads per row
+    constexpr int KH = K / H;        // columns per thread
+    pdl_enter();
+    if (bs->all) return;
+    const int64_t items = (int64_t)n * H;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    int64_t it0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int h = H == 1 ? 0 : (int)(it0 & 1); // fixed: the stride is even
+    DF al[KH], nal[KH], be[KH];
+    bool run[KH], first[KH];
+#pragma unroll
+    for (int c = 0; c < KH; c++) {
+        const CgScal &sc = bs->c[h * KH + c];
+        al[c] = DF{sc.ahi, sc.alo};
+        nal[c] = DF{-sc.ahi, -sc.alo};
+        be[c] = DF{sc.bhi, sc.blo};
+        run[c] = !sc.done;
+        first[c] = sc.bhi == 0.f && sc.blo == 0.f;
+    }
+    DF vh[KH];
+#pragma unroll
+    for (int c = 0; c < KH; c++) vh[c] = DF{0.f, 0.f};
+    for (int64_t it = it0; it < items; it += stride) {
+        int64_t i = it / H;
+        int64_t o = i * K + h * KH;
+        float zv[KH], s1[KH], s2[KH], p1[KH], p2[KH], q1[KH], q2[KH], x1[KH], x2[KH], r1[KH], r2[KH];
+        ldk<KH>(z + o, zv);
+        ldk<KH>(sh + o, s1);
+        ldk<KH>(sl + o, s2);
+        ldk<KH>(ph + o, p1);
+        ldk<KH>(pl + o, p2);
+        ldk<KH>(qh + o, q1);
+        ldk<KH>(ql + o, q2);
+        ldk<KH>(xh + o, x1);
+        ldk<KH>(xl + o, x2);
+        ldk<KH>(rh + o, r1);
+        ldk<KH>(rl + o, r2);
+#pragma unroll
+        for (int c = 0; c < KH; c++) {
+            if (!run[c]) continue;
+            DF zi = {zv[c], 0.f}, si = {s1[c], s2[c]};
+            DF pi = first[c] ? zi : df_add2(zi, df_mul2(be[c], DF{p1[c], p2[c]}));
+            DF qi = first[c] ? si : df_add2(si, df_mul2(be[c], DF{q1[c], q2[c]}));
+            DF xi = df_add2(DF{x1[c], x2[c]}, df_mul2(al[c], pi));
+            DF ri = df_add2(DF{r1[c], r2[c]}, df_mul2(nal[c], qi));
+            p1[c] = pi.hi;
+            p2[c] = pi.lo;
+            q1[c] = qi.hi;
+            q2[c] = qi.lo;
+            x1[c] = xi.hi;
+            x2[c] = xi.lo;
+            r1[c] = ri.hi;
+            r2[c] = ri.lo;
+            vh[c] = df_add_fast(vh[c], df_mul2(ri, ri)); // squares: no cancellation
+        }
+        stk<KH>(ph + o, p1);
+        stk<KH>(pl + o, p2);
+        stk<KH>(qh + o, q1);
+        stk<KH>(ql + o, q2);
+        stk<KH>(xh + o, x1);
+        stk<KH>(xl + o, x2);
+        stk<KH>(rh + o, r1);
+        stk<KH>(rl + o, r2);
+        if (invd32) {
+            float iv = invd32[i], zn[KH];
+#pragma unroll
+            for (int c = 0; c < KH; c++) zn[c] = iv * r1[c];
+            stk<KH>(z + o, zn);
+        }
+    }
+    DF v[K];
+    double tot[K];
+#pragma unroll
+    for (int c = 0; c < K; c++) v[c] = DF{0.f, 0.f};
+#pragma unroll
+    for (int q = 0; q < H; q++)
+        if (q == h) {
+#pragma unroll
+            for (int c = 0; c < KH; c++) v[q * KH + c] = vh[c];
+        }
+    if (reduce_dfk<K>(v, partials, ticket, tot)) fin_rr<K>(bs, tot);
+}
+
+// x = (x_hi + x_lo) / scale_c (FP64, once per solve)
+template <int K>
+__global__ void kbd_out(int64_t nk, const float *__restrict__ xh, const float *__restrict__ xl, const BScal *bs,
+                        double *__restrict__ y)
+{
+    pdl_enter();
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nk; e += (int64_t)gridDim.x * blockDim.x)
+        y[e] = ((double)xh[e] + (double)xl[e]) * inv_pow2(bs->c[e & (K - 1)].scale);
 }
 
 // ------------------------------------------------------------------ V-cycle kernels
@@ -915,7 +1133,6 @@ struct BGraph {
 struct BState {
     double *x = nullptr, *r = nullptr, *pv = nullptr, *q = nullptr, *s = nullptr;
     void *z = nullptr;     // V-cycle output (FP32 or FP64)
-    float *r32 = nullptr;  // FP32 copy of r (FP32 V-cycle input)
     void *vb = nullptr, *vx = nullptr, *vx2 = nullptr, *vd = nullptr, *vr = nullptr;
     BScal *bs = nullptr;
     RedSlot red;
@@ -1030,7 +1247,6 @@ static int block_alloc_into(amgh_problem *p, BlockWork *W, int K)
         TRY(ar.alloc(&B.pv, n));
         TRY(ar.alloc(&B.q, n));
         TRY(ar.alloc(&B.s, n));
-        TRY(ar.alloc(&B.r32, f32 ? n : 1));
         char *v = nullptr;
         TRY(ar.alloc(&v, (int64_t)(6 * n * vs)));
         void **dst[6] = {&B.z, &B.vb, &B.vx, &B.vx2, &B.vd, &B.vr};
@@ -1243,33 +1459,66 @@ struct Blk {
         return AMGH_OK;
     }
 
-    // s = A z with (r, z), (z, s) -> alpha, beta: products in FP64 for
-    // precision 0, else in double-float from the FP32 parts of A
+    // s = A z with (r, z), (z, s) -> alpha, beta in FP64 (precision 0)
     template <typename Z>
     static int cg_spmv(amgh_problem *p, const DevCsr &a, const Z *z, const double *r, double *s, BScal *bs,
                        RedSlot &red)
     {
-        if constexpr (sizeof(Z) == sizeof(double)) {
-            if (!p->blk->f32) {
-                MatView<double> A = bview<double>(a);
-                if (!with_tpr(A.tpr, [&](auto t) {
-                        constexpr int TPR = decltype(t)::value;
-                        pdl_launch(kb_cg_spmv64<TPR, K>, dim3(rows_grid(A.rows, TPR)), dim3(TPB), 0, p->stream, A,
-                                   z, r, s, bs, red.partials, red.ticket);
-                    }))
-                    return AMGH_ERR_INVALID_ARG;
-                LAUNCH_CHECK();
-                return AMGH_OK;
-            }
-        }
+        MatView<double> A = bview<double>(a);
+        if (!with_tpr(A.tpr, [&](auto t) {
+                constexpr int TPR = decltype(t)::value;
+                pdl_launch(kb_cg_spmv64<TPR, K>, dim3(rows_grid(A.rows, TPR)), dim3(TPB), 0, p->stream, A,
+                           (const double *)z, r, s, bs, red.partials, red.ticket);
+            }))
+            return AMGH_ERR_INVALID_ARG;
+        LAUNCH_CHECK();
+        return AMGH_OK;
+    }
+
+    // ---- double-float CG pieces (FP32 V-cycles): v is an FP64-sized buffer of
+    // n*K doubles holding hi = [0, nK) and lo = [nK, 2nK)
+    static float *hi(double *v) { return (float *)v; }
+    static float *lo(double *v, int n) { return (float *)v + (int64_t)n * K; }
+
+    static int df_start(amgh_problem *p, int n, const double *f, double *x, double *r, float *z, const float *invd32,
+                        BScal *bs, RedSlot &red, double tol, int maxit)
+    {
+        pdl_launch(kbd_norm<K>, dim3(vblocks(n)), dim3(TPB), 0, p->stream, n, f, bs, tol * tol, maxit, red.partials,
+                   red.ticket);
+        LAUNCH_CHECK();
+        int64_t nk = (int64_t)n * K;
+        pdl_launch(kbd_start<K>, dim3(vblocks(nk)), dim3(TPB), 0, p->stream, nk, f, hi(x), lo(x, n), hi(r), lo(r, n),
+                   z, invd32, (const BScal *)bs);
+        LAUNCH_CHECK();
+        return AMGH_OK;
+    }
+
+    static int df_iter(amgh_problem *p, const DevCsr &a, float *z, double *r, double *s, double *pv, double *q,
+                       double *x, const float *invd32, BScal *bs, RedSlot &red)
+    {
+        int n = a.rows;
         MatView<float> A = bview<float>(a);
         if (!a.lo32) return AMGH_ERR_INVALID_ARG;
         if (!with_tpr(A.tpr, [&](auto t) {
                 constexpr int TPR = decltype(t)::value;
-                pdl_launch(kb_cg_spmv<Z, TPR, K>, dim3(rows_grid(A.rows, TPR)), dim3(TPB), 0, p->stream, A,
-                           (const float *)a.lo32, z, r, s, bs, red.partials, red.ticket);
+                pdl_launch(kbd_spmv<TPR, K>, dim3(rows_grid(A.rows, TPR)), dim3(TPB), 0, p->stream, A,
+                           (const float *)a.lo32, (const float *)z, (const float *)hi(r), (const float *)lo(r, n),
+                           hi(s), lo(s, n), bs, red.partials, red.ticket);
             }))
             return AMGH_ERR_INVALID_ARG;
+        LAUNCH_CHECK();
+        pdl_launch(kbd_update<K>, dim3(update_blocks<K>(n)), dim3(TPB), 0, p->stream, n, z, (const float *)hi(s),
+                   (const float *)lo(s, n), hi(pv), lo(pv, n), hi(q), lo(q, n), hi(x), lo(x, n), hi(r), lo(r, n),
+                   invd32, bs, red.partials, red.ticket);
+        LAUNCH_CHECK();
+        return AMGH_OK;
+    }
+
+    static int df_out(amgh_problem *p, int n, double *x, const BScal *bs, double *y)
+    {
+        int64_t nk = (int64_t)n * K;
+        pdl_launch(kbd_out<K>, dim3(vblocks(nk)), dim3(TPB), 0, p->stream, nk, (const float *)hi(x),
+                   (const float *)lo(x, n), bs, y);
         LAUNCH_CHECK();
         return AMGH_OK;
     }
@@ -1319,27 +1568,33 @@ struct Blk {
         int n = S.A.rows;
         int maxit = p->sopts.inner_max_iter;
         const bool f32 = sizeof(T) == sizeof(float);
-        pdl_launch(kb_cg_start<double, K>, dim3(vblocks(n)), dim3(TPB), 0, p->stream, n, f, B.x, B.r, (double *)nullptr,
-                   (const double *)nullptr, B.bs, tol * tol, maxit, B.red.partials, B.red.ticket);
-        LAUNCH_CHECK();
-        const T *vin = f32 ? (const T *)B.r32 : (const T *)B.r;
         T *z = (T *)B.z;
-        std::function<int()> start = [&]() {
-            if (f32) {
-                pdl_launch(kb_r32<K>, dim3(vblocks(n)), dim3(TPB), 0, p->stream, n, (const double *)B.r, B.r32,
-                           (const BScal *)B.bs);
-                LAUNCH_CHECK();
-            }
-            return vcyc(p, l, vin, z, B.bs);
-        };
-        std::function<int()> iter = [&]() {
-            TRY(cg_spmv<T>(p, S.A, z, B.r, B.s, B.bs, B.red));
-            pdl_launch(kb_cg_update<T, K>, dim3(update_blocks<K>(n)), dim3(TPB), 0, p->stream, n, z, (const double *)B.s,
-                       B.pv, B.q, B.x, B.r, f32 ? B.r32 : (float *)nullptr, (const double *)nullptr, B.bs,
-                       B.red.partials, B.red.ticket);
+        std::function<int()> start, iter;
+        if constexpr (sizeof(T) == sizeof(float)) {
+            // double-float CG; the FP32 V-cycle reads r's hi half
+            TRY(df_start(p, n, f, B.x, B.r, (float *)nullptr, (const float *)nullptr, B.bs, B.red, tol, maxit));
+            const T *vin = (const T *)hi(B.r);
+            start = [&]() { return vcyc(p, l, vin, z, B.bs); };
+            iter = [&]() {
+                TRY(df_iter(p, S.A, (float *)z, B.r, B.s, B.pv, B.q, B.x, (const float *)nullptr, B.bs, B.red));
+                return vcyc(p, l, vin, z, B.bs);
+            };
+        } else {
+            pdl_launch(kb_cg_start<double, K>, dim3(vblocks(n)), dim3(TPB), 0, p->stream, n, f, B.x, B.r,
+                       (double *)nullptr, (const double *)nullptr, B.bs, tol * tol, maxit, B.red.partials,
+                       B.red.ticket);
             LAUNCH_CHECK();
-            return vcyc(p, l, vin, z, B.bs);
-        };
+            const T *vin = (const T *)B.r;
+            start = [&]() { return vcyc(p, l, vin, z, B.bs); };
+            iter = [&]() {
+                TRY(cg_spmv<T>(p, S.A, z, B.r, B.s, B.bs, B.red));
+                pdl_launch(kb_cg_update<T, K>, dim3(update_blocks<K>(n)), dim3(TPB), 0, p->stream, n, z,
+                           (const double *)B.s, B.pv, B.q, B.x, B.r, (const double *)nullptr, B.bs,
+                           B.red.partials, B.red.ticket);
+                LAUNCH_CHECK();
+                return vcyc(p, l, vin, z, B.bs);
+            };
+        }
         BScal h;
         TRY(run_loop(p, B.g, start, iter, B.bs, maxit, &B.hint, &h));
         for (int c = 0; c < K; c++) {
@@ -1347,6 +1602,7 @@ struct Blk {
             p->c_inner_lvl[l] += h.c[c].iters;
             note_fail(W, c, col_status(h.c[c]));
         }
+        if (f32) return df_out(p, n, B.x, B.bs, y);
         return copy(p, (int64_t)n * K, B.x, y);
     }
 
@@ -1359,33 +1615,30 @@ struct Blk {
         int n = C.Mu.rows;
         int maxit = p->sopts.mass_max_iter;
         double tol = p->sopts.mass_tol;
-        // with FP32 V-cycles the Jacobi direction z is kept in FP32 as in the
-        // single-column double-float mass CG: the products stay double-float
-        // from A's FP32 parts, and only the preconditioner is rounded
+        // with FP32 V-cycles the mass CG is double-float with the Jacobi
+        // direction z in FP32, as the single-column double-float mass CG
         const bool z32 = W.f32 != 0;
-        if (z32)
-            pdl_launch(kb_cg_start<float, K>, dim3(vblocks(n)), dim3(TPB), 0, p->stream, n, b, D.mx, D.mr,
-                       (float *)D.mz, (const double *)C.mu_invdiag, D.mbs, tol * tol, maxit, D.red.partials,
-                       D.red.ticket);
-        else
+        std::function<int()> iter;
+        if (z32) {
+            TRY(df_start(p, n, b, D.mx, D.mr, (float *)D.mz, (const float *)C.mu_invdiag32, D.mbs, D.red, tol,
+                         maxit));
+            iter = [&]() {
+                return df_iter(p, C.Mu, (float *)D.mz, D.mr, D.ms, D.mp, D.mq, D.mx, (const float *)C.mu_invdiag32,
+                               D.mbs, D.red);
+            };
+        } else {
             pdl_launch(kb_cg_start<double, K>, dim3(vblocks(n)), dim3(TPB), 0, p->stream, n, b, D.mx, D.mr, D.mz,
                        (const double *)C.mu_invdiag, D.mbs, tol * tol, maxit, D.red.partials, D.red.ticket);
-        LAUNCH_CHECK();
-        std::function<int()> iter = [&]() {
-            if (z32) {
-                TRY(cg_spmv<float>(p, C.Mu, (const float *)D.mz, D.mr, D.ms, D.mbs, D.red));
-                pdl_launch(kb_cg_update<float, K>, dim3(update_blocks<K>(n)), dim3(TPB), 0, p->stream, n,
-                           (float *)D.mz, (const double *)D.ms, D.mp, D.mq, D.mx, D.mr, (float *)nullptr,
-                           (const double *)C.mu_invdiag, D.mbs, D.red.partials, D.red.ticket);
-            } else {
+            LAUNCH_CHECK();
+            iter = [&]() {
                 TRY(cg_spmv<double>(p, C.Mu, D.mz, D.mr, D.ms, D.mbs, D.red));
                 pdl_launch(kb_cg_update<double, K>, dim3(update_blocks<K>(n)), dim3(TPB), 0, p->stream, n, D.mz,
-                           (const double *)D.ms, D.mp, D.mq, D.mx, D.mr, (float *)nullptr,
-                           (const double *)C.mu_invdiag, D.mbs, D.red.partials, D.red.ticket);
-            }
-            LAUNCH_CHECK();
-            return AMGH_OK;
-        };
+                           (const double *)D.ms, D.mp, D.mq, D.mx, D.mr, (const double *)C.mu_invdiag, D.mbs,
+                           D.red.partials, D.red.ticket);
+                LAUNCH_CHECK();
+                return AMGH_OK;
+            };
+        }
         BScal h;
         TRY(run_loop(p, D.mg, std::function<int()>(), iter, D.mbs, maxit, &D.mhint, &h));
         for (int c = 0; c < K; c++) {
@@ -1393,6 +1646,7 @@ struct Blk {
             p->c_mass_lvl[l] += h.c[c].iters;
             note_fail(W, c, col_status(h.c[c]));
         }
+        if (z32) return df_out(p, n, D.mx, D.mbs, x);
         return copy(p, (int64_t)n * K, D.mx, x);
     }
 

@@ -127,3 +127,63 @@ __device__ __forceinline__ DF df_warp_sum(DF v)
     }
     return v;
 }
+
+// Sum over the grid of NV double-float values per thread: warp butterflies,
+// then warp 0 of each block, then the last block to finish sums the blocks'
+// partials (double-float, two FP32 halves in each 8-byte slot of partials,
+// [NV][gridDim.x]) in fixed order.  Returns true in thread 0 of that block,
+// with the sums (as FP64) in tot.  Every FP64 instruction costs ~64 FP32
+// issue slots on GB300, so the tree stays on the FP32 pipe.
+template <int NV>
+__device__ bool reduce_df_last_block(const DF (&val)[NV], double *partials, unsigned *ticket, double (&tot)[NV])
+{
+    // the partial sums stay double-float (two FP32 halves in each 8-byte
+    // slot): on GB300 every FP64 instruction costs ~64 FP32 issue slots
+    __shared__ DF shw[NV][32];
+    __shared__ bool is_last;
+    float2 *part = reinterpret_cast<float2 *>(partials);
+    int nb = gridDim.x, w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int q = 0; q < NV; q++) {
+        DF s = df_warp_sum(val[q]);
+        if (l == 0) shw[q][w] = s;
+    }
+    __syncthreads();
+    if (w == 0) {
+#pragma unroll
+        for (int q = 0; q < NV; q++) {
+            DF t = l < nw ? shw[q][l] : DF{0.f, 0.f};
+            t = df_warp_sum(t);
+            if (l == 0) part[q * nb + blockIdx.x] = make_float2(t.hi, t.lo);
+        }
+        if (l == 0) {
+            __threadfence();
+            unsigned tk = atomicAdd(ticket, 1u);
+            is_last = (tk == (unsigned)nb - 1);
+        }
+    }
+    __syncthreads();
+    if (!is_last) return false;
+    __threadfence();
+#pragma unroll
+    for (int q = 0; q < NV; q++) {
+        DF s = {0.f, 0.f};
+        for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+            float2 v = __ldcg(&part[q * nb + b]); // L2: written by other blocks
+            s = df_add_fast(s, DF{v.x, v.y});
+        }
+        s = df_warp_sum(s);
+        if (l == 0) shw[q][w] = s;
+    }
+    __syncthreads();
+    if (w == 0) {
+#pragma unroll
+        for (int q = 0; q < NV; q++) {
+            DF t = l < nw ? shw[q][l] : DF{0.f, 0.f};
+            t = df_warp_sum(t);
+            tot[q] = df_to_double(t);
+        }
+        if (l == 0) *ticket = 0u;
+    }
+    return threadIdx.x == 0;
+}
