@@ -706,49 +706,14 @@ __global__ void k_gemm_hash(int n, const int *__restrict__ arp, const int *__res
     cnt[i] = c;
 }
 
-// path 0 output: the table's entries in ascending column order.  Each thread
-// insertion-sorts (column, slot) pairs of its row in shared memory (thread t's
-// k-th pair at [k][t], so a warp's accesses fall in distinct banks) and then
-// writes every entry once; a row with more than OUT_CAP entries sorts in the
-// output arrays instead.
-#define OUT_TPB 128
-#define OUT_CAP 48
+// path 0 output: the table's entries in ascending column order, sorted in
+// place in the output arrays (insertion sort)
 template <int NV>
-__global__ void __launch_bounds__(OUT_TPB)
-    k_gemm_out(int n, const long long *__restrict__ toff, const int *__restrict__ path_of,
-               const int *__restrict__ tkey, GemmOut<NV> T, const int *__restrict__ crp, int *__restrict__ cci,
-               GemmOut<NV> C)
+__device__ __forceinline__ void out_row_inplace(long long base, unsigned size, const int *__restrict__ tkey,
+                                                const GemmOut<NV> &T, int b, int *__restrict__ cci,
+                                                const GemmOut<NV> &C)
 {
-    __shared__ int sk[OUT_CAP][OUT_TPB];
-    __shared__ unsigned short ss[OUT_CAP][OUT_TPB];
-    int t = threadIdx.x;
-    int i = blockIdx.x * blockDim.x + t;
-    if (i >= n || path_of[i]) return;
-    long long base = toff[i];
-    unsigned size = (unsigned)(toff[i + 1] - base);
-    int b = crp[i], c = 0;
-    if (crp[i + 1] - b <= OUT_CAP && size <= 65536) {
-        for (unsigned u = 0; u < size; u++) {
-            int key = tkey[base + u];
-            if (key < 0) continue;
-            int j = c - 1;
-            while (j >= 0 && sk[j][t] > key) {
-                sk[j + 1][t] = sk[j][t];
-                ss[j + 1][t] = ss[j][t];
-                j--;
-            }
-            sk[j + 1][t] = key;
-            ss[j + 1][t] = (unsigned short)u;
-            c++;
-        }
-        for (int k = 0; k < c; k++) {
-            unsigned u = ss[k][t];
-            cci[b + k] = sk[k][t];
-#pragma unroll
-            for (int q = 0; q < NV; q++) C.v[q][b + k] = T.v[q][base + u];
-        }
-        return;
-    }
+    int c = 0;
     for (unsigned u = 0; u < size; u++) {
         int key = tkey[base + u];
         if (key < 0) continue;
@@ -763,6 +728,65 @@ __global__ void __launch_bounds__(OUT_TPB)
 #pragma unroll
         for (int q = 0; q < NV; q++) C.v[q][j + 1] = T.v[q][base + u];
         c++;
+    }
+}
+
+template <int NV>
+__global__ void k_gemm_out(int n, const long long *__restrict__ toff, const int *__restrict__ path_of,
+                           const int *__restrict__ tkey, GemmOut<NV> T, const int *__restrict__ crp,
+                           int *__restrict__ cci, GemmOut<NV> C)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n || path_of[i]) return;
+    long long base = toff[i];
+    out_row_inplace<NV>(base, (unsigned)(toff[i + 1] - base), tkey, T, crp[i], cci, C);
+}
+
+// The same for products with short rows (on average at most OUT_AVG entries):
+// each thread insertion-sorts (column, slot) pairs of its row in shared
+// memory (thread t's k-th pair at [k][t], so a warp's accesses fall in
+// distinct banks) and then writes every entry once; a row with more than
+// OUT_CAP entries sorts in place.  Its shared memory lowers occupancy, so
+// long-row products (3D) keep the kernel above.
+#define OUT_TPB 128
+#define OUT_CAP 48
+#define OUT_AVG 24
+template <int NV>
+__global__ void __launch_bounds__(OUT_TPB)
+    k_gemm_out_sm(int n, const long long *__restrict__ toff, const int *__restrict__ path_of,
+                  const int *__restrict__ tkey, GemmOut<NV> T, const int *__restrict__ crp, int *__restrict__ cci,
+                  GemmOut<NV> C)
+{
+    __shared__ int sk[OUT_CAP][OUT_TPB];
+    __shared__ unsigned short ss[OUT_CAP][OUT_TPB];
+    int t = threadIdx.x;
+    int i = blockIdx.x * blockDim.x + t;
+    if (i >= n || path_of[i]) return;
+    long long base = toff[i];
+    unsigned size = (unsigned)(toff[i + 1] - base);
+    int b = crp[i], c = 0;
+    if (crp[i + 1] - b > OUT_CAP || size > 65536) {
+        out_row_inplace<NV>(base, size, tkey, T, b, cci, C);
+        return;
+    }
+    for (unsigned u = 0; u < size; u++) {
+        int key = tkey[base + u];
+        if (key < 0) continue;
+        int j = c - 1;
+        while (j >= 0 && sk[j][t] > key) {
+            sk[j + 1][t] = sk[j][t];
+            ss[j + 1][t] = ss[j][t];
+            j--;
+        }
+        sk[j + 1][t] = key;
+        ss[j + 1][t] = (unsigned short)u;
+        c++;
+    }
+    for (int k = 0; k < c; k++) {
+        unsigned u = ss[k][t];
+        cci[b + k] = sk[k][t];
+#pragma unroll
+        for (int q = 0; q < NV; q++) C.v[q][b + k] = T.v[q][base + u];
     }
 }
 
@@ -1186,7 +1210,10 @@ static int spgemm_nv(amgh_problem *p, Arena &ar, const DevCsr &a, const double *
         Cv.v[q] = cv[q];
     }
     c.v = cv[0];
-    k_gemm_out<NV><<<ceil_div(n, OUT_TPB), OUT_TPB, 0, s>>>(n, toff, path, tkey, T, c.rp, c.ci, Cv);
+    if ((int64_t)nnz <= (int64_t)OUT_AVG * n)
+        k_gemm_out_sm<NV><<<ceil_div(n, OUT_TPB), OUT_TPB, 0, s>>>(n, toff, path, tkey, T, c.rp, c.ci, Cv);
+    else
+        k_gemm_out<NV><<<ceil_div(n, 128), 128, 0, s>>>(n, toff, path, tkey, T, c.rp, c.ci, Cv);
     LAUNCH_CHECK();
     TRY(launch_lists(1, nullptr, c.rp, c.ci, Cv));
     int bad = 0;
