@@ -204,13 +204,15 @@ __global__ void __launch_bounds__(128) k_potrf_diag(int n, int k0, const double 
 }
 
 // step 2: blocks [0, rb) turn PANEL_WARPS rows each of the panel into L_ik;
-// the next k0/NB + 1 blocks each form one 32-column strip of W_k. in place,
-// one row per warp (so that no warp issues more than NB FP64 FMAs).  A strip
-// is read whole before any of its rows is written, so it must not be split
-// over blocks: a block that starts late would read rows already replaced.
-#define PANEL_WARPS 32
+// the next (k0/NB + 1) * NB/PANEL_WARPS blocks each form PANEL_WARPS rows of
+// one 32-column strip of Y_k = D_k B_k. (one row per warp, so that no warp
+// issues more than NB FP64 FMAs) into ybuf (NB x n, row-major).  B_k. stays in
+// W until the next launch copies Y_k over it: a strip is read by all its
+// blocks, so none of them may overwrite it.
+#define PANEL_WARPS 4
 __global__ void __launch_bounds__(32 * PANEL_WARPS) k_panel(int n, int k0, int rb, double *__restrict__ g,
-                                                            const double *__restrict__ dinv, double *__restrict__ W)
+                                                            const double *__restrict__ dinv,
+                                                            const double *__restrict__ W, double *__restrict__ ybuf)
 {
     __shared__ double d[NB][NB + 1], sb[NB][NB + 1];
     const double *dk = dinv + (int64_t)(k0 / NB) * NB * NB;
@@ -232,11 +234,11 @@ __global__ void __launch_bounds__(32 * PANEL_WARPS) k_panel(int n, int k0, int r
         if (lane < nb) row[lane] = acc0 + acc1;
         return;
     }
-    int strip = blockIdx.x - rb, c0 = strip * NB, col = c0 + lane;
-    int r = warp;
+    int sblk = blockIdx.x - rb, strip = sblk / (NB / PANEL_WARPS), c0 = strip * NB, col = c0 + lane;
+    int r = (sblk % (NB / PANEL_WARPS)) * PANEL_WARPS + warp;
     if (c0 == k0) { // the diagonal block: B_kk = I
         __syncthreads();
-        if (r < nb && lane < nb) W[(int64_t)(k0 + r) * n + col] = d[r][lane];
+        if (r < nb && lane < nb) ybuf[(int64_t)r * n + col] = d[r][lane];
         return;
     }
     for (int q = warp; q < NB; q += PANEL_WARPS) sb[q][lane] = q < nb ? W[(int64_t)(k0 + q) * n + col] : 0.0;
@@ -248,15 +250,15 @@ __global__ void __launch_bounds__(32 * PANEL_WARPS) k_panel(int n, int k0, int r
         y0 = fma(d[r][q], sb[q][lane], y0);
         y1 = fma(d[r][q + 1], sb[q + 1][lane], y1);
     }
-    W[(int64_t)(k0 + r) * n + col] = y0 + y1;
+    ybuf[(int64_t)r * n + col] = y0 + y1;
 }
 
 // step 3 tiles, 16 x 16 on 256 threads.  An A tile (ti, tj), tj <= ti, of the
 // trailing matrix below and right of the panel at k0: A_ij -= sum_c L_ic L_jc
 // on and below the diagonal.  A W tile: rows below the panel times the first
-// k0 + nb columns, B_ij -= sum_c L_ic W_(k0+c)j.
+// k0 + nb columns, B_ij -= sum_c L_ic Y_cj (Y_k in ybuf).
 __device__ __forceinline__ void trail_tile(int n, int k0, int ti, int tj, bool wtile, double *__restrict__ g,
-                                           double *__restrict__ W)
+                                           double *__restrict__ W, const double *__restrict__ ybuf)
 {
     __shared__ double Li[16][NB + 1], Rj[NB][17];
     int nb = min(NB, n - k0), base = k0 + nb;
@@ -270,7 +272,7 @@ __device__ __forceinline__ void trail_tile(int n, int k0, int ti, int tj, bool w
     if (wtile)
         for (int e = threadIdx.x; e < NB * 16; e += 256) {
             int c = e / 16, q = e % 16;
-            Rj[c][q] = c < nb && j0 + q < base ? W[(int64_t)(k0 + c) * n + j0 + q] : 0.0;
+            Rj[c][q] = c < nb && j0 + q < base ? ybuf[(int64_t)c * n + j0 + q] : 0.0;
         }
     __syncthreads();
     int i = r0 + ty, j = j0 + tx;
@@ -297,31 +299,44 @@ __device__ __forceinline__ void tri_decode(int t, int &ti, int &tj)
 __global__ void __launch_bounds__(256) k_trail_next(int n, int k0, int T, double *__restrict__ g)
 {
     int t = blockIdx.x;
-    if (t < T) trail_tile(n, k0, t, 0, false, g, nullptr);
-    else trail_tile(n, k0, t - T + 1, 1, false, g, nullptr);
+    if (t < T) trail_tile(n, k0, t, 0, false, g, nullptr, nullptr);
+    else trail_tile(n, k0, t - T + 1, 1, false, g, nullptr, nullptr);
 }
 
 // the rest: block 0 factors the next panel's diagonal block (updated by
-// k_trail_next), blocks [1, 1 + ta) the A tiles with 2 <= tj <= ti, the rest
-// the W tiles (T rows x tw columns of tiles)
+// k_trail_next; none after the last panel), blocks [1, 1 + ta) the A tiles
+// with 2 <= tj <= ti, the next T * tw the W tiles (T rows x tw columns of
+// tiles), the last cb copy Y_k from ybuf into block row k of W (rows no other
+// block of this launch reads or writes)
+#define COPY_TPB 256
 __global__ void __launch_bounds__(256) k_trail_rest(int n, int k0, int T, int ta, int tw, double *__restrict__ g,
-                                                    double *__restrict__ W, double *__restrict__ dinv,
-                                                    int *__restrict__ info)
+                                                    double *__restrict__ W, const double *__restrict__ ybuf,
+                                                    double *__restrict__ dinv, int *__restrict__ info)
 {
     int t = blockIdx.x;
     if (t == 0) {
-        diag_factor(n, k0 + NB, g, dinv, info);
+        if (k0 + NB < n) diag_factor(n, k0 + NB, g, dinv, info);
         return;
     }
     t -= 1;
     if (t < ta) {
         int ti, tj;
         tri_decode(t, ti, tj);
-        trail_tile(n, k0, ti + 2, tj + 2, false, g, W);
+        trail_tile(n, k0, ti + 2, tj + 2, false, g, W, ybuf);
         return;
     }
     t -= ta;
-    trail_tile(n, k0, t / tw, t % tw, true, g, W);
+    if (t < T * tw) {
+        trail_tile(n, k0, t / tw, t % tw, true, g, W, ybuf);
+        return;
+    }
+    t -= T * tw;
+    int nb = min(NB, n - k0), width = k0 + nb;
+    int64_t e = (int64_t)t * COPY_TPB + threadIdx.x;
+    if (e < (int64_t)nb * width) {
+        int r = (int)(e / width), c = (int)(e % width);
+        W[(int64_t)(k0 + r) * n + c] = ybuf[(int64_t)r * n + c];
+    }
 }
 
 // C = op(A) B (+ beta D), all row-major; transA: A is k x m and used as A^T
@@ -422,9 +437,10 @@ static int spd_inverse_on(cudaStream_t s, double *g, int n, double *inv, int *in
 {
     if (n <= 0) return AMGH_OK;
     Scratch sc;
-    double *W = nullptr, *dinv = nullptr;
+    double *W = nullptr, *dinv = nullptr, *ybuf = nullptr;
     TRY(sc.alloc(&W, (int64_t)n * n));
     TRY(sc.alloc(&dinv, (int64_t)ceil_div(n, NB) * NB * NB));
+    TRY(sc.alloc(&ybuf, (int64_t)NB * n));
     CU(cudaMemsetAsync(info_dev, 0, sizeof(int), s));
     CU(cudaMemsetAsync(W, 0, sizeof(double) * (size_t)n * n, s));
     k_potrf_diag<<<1, 128, 0, s>>>(n, 0, g, dinv, info_dev);
@@ -432,15 +448,16 @@ static int spd_inverse_on(cudaStream_t s, double *g, int n, double *inv, int *in
     for (int k0 = 0; k0 < n; k0 += NB) {
         int nb = n - k0 < NB ? n - k0 : NB, m = n - k0 - nb;
         int rb = ceil_div(m, PANEL_WARPS);
-        k_panel<<<rb + k0 / NB + 1, 32 * PANEL_WARPS, 0, s>>>(n, k0, rb, g, dinv, W);
+        k_panel<<<rb + (k0 / NB + 1) * (NB / PANEL_WARPS), 32 * PANEL_WARPS, 0, s>>>(n, k0, rb, g, dinv, W, ybuf);
         LAUNCH_CHECK();
+        int T = ceil_div(m, 16), tw = ceil_div(k0 + nb, 16), ta = T > 2 ? (T - 2) * (T - 1) / 2 : 0;
+        int cb = ceil_div((int64_t)nb * (k0 + nb), COPY_TPB);
         if (m > 0) {
-            int T = ceil_div(m, 16), tw = ceil_div(k0 + nb, 16), ta = T > 2 ? (T - 2) * (T - 1) / 2 : 0;
             k_trail_next<<<T > 1 ? 2 * T - 1 : 1, 256, 0, s>>>(n, k0, T, g);
             LAUNCH_CHECK();
-            k_trail_rest<<<1 + ta + T * tw, 256, 0, s>>>(n, k0, T, ta, tw, g, W, dinv, info_dev);
-            LAUNCH_CHECK();
         }
+        k_trail_rest<<<1 + ta + T * tw + cb, 256, 0, s>>>(n, k0, T, ta, tw, g, W, ybuf, dinv, info_dev);
+        LAUNCH_CHECK();
     }
     // A^-1 = L^-T L^-1 = W^T W
     int tiles = ceil_div(n, TILE);
