@@ -614,6 +614,40 @@ def oracle_apply_rate(orc, budget_s, threads):
     return n, t, used
 
 
+def dense_fp64(n_coarse):
+    """The FP64 rates the dense coarsest-level kernels are bound by (FMA pipe and
+    mma.m8n8k4.f64, measured), and one dense SPD inverse at the coarsest size:
+    Cholesky, L^-1 and W^T W are about n^3 / 3 flops each (n^3 in all), timed
+    with CUDA events on the launching stream, median of 5."""
+    import torch
+
+    from paper_2001_11533_gb300 import amgh
+    s = torch.cuda.current_stream()
+    dfma = amgh.fp64_peak(0, s.cuda_stream)
+    dmma = amgh.fp64_peak(1, s.cuda_stream)
+    n = int(n_coarse)
+    b = torch.randn(n, n, dtype=torch.float64, device="cuda", generator=torch.Generator("cuda").manual_seed(5))
+    a = b @ b.T / n + 1e-3 * torch.eye(n, dtype=torch.float64, device="cuda")
+    inv = torch.empty_like(a)
+    times = []
+    for k in range(6):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        st, info = amgh.dense_spd_inverse(a, inv, stream=s.cuda_stream)
+        e1.record(s)
+        e1.synchronize()
+        if st != 0:
+            return {"dfma_tflops": dfma, "dmma_tflops": dmma, "spd_inverse": {"n": n, "status": st}}
+        if k:
+            times.append(e0.elapsed_time(e1))
+    ms = sorted(times)[len(times) // 2]
+    tf = float(n) ** 3 / (ms * 1e-3) * 1e-12
+    return {"dfma_tflops": round(dfma, 3), "dmma_tflops": round(dmma, 3),
+            "spd_inverse": {"n": n, "ms": round(ms, 3), "tflops": round(tf, 3),
+                            "frac_of_dfma": round(tf / dfma, 3),
+                            "note": "fused panel Cholesky + L^-1 sweep with lookahead, then W^T W"}}
+
+
 def cpu_baseline(w, args):
     """The oracle's Hessian apply on the same workload, on one host core and on
     every host core (the -fopenmp build: row loops split over threads, dot
@@ -793,6 +827,8 @@ def main():
         line["speedup_refine_vs_fp64"] = results["refine"]["value"] / results["fp64"]["value"]
     if cube is not None:
         line["cube"] = cube
+    if args.workload == "lshape":
+        line["dense_fp64"] = dense_fp64(head["levels"]["state"][-1])
     if world == 1 and not args.no_cpu_baseline and args.workload == "lshape":
         line["cpu_baseline"] = cpu_baseline(w, args)
     print(json.dumps(line), flush=True)

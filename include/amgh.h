@@ -541,6 +541,15 @@ int amgh_aggregate_noalloc(int n, const int32_t *rowptr_dev, const int32_t *col_
  * library's stream-ordered pool; the call synchronises `stream`. */
 int amgh_dense_spd_inverse(int n, const double *a_dev, double *inv_dev, void *stream, int *info);
 
+/* The FP64 rate of this GPU, measured: kind 0 = fused multiply-adds on the
+ * FP64 pipe (every SM busy, eight independent chains per thread), kind 1 =
+ * the FP64 tensor instruction mma.m8n8k4.f64 (four independent accumulators
+ * per warp).  *tflops = the rate of one timed launch of about 10 ms after a
+ * warm-up.  The dense coarsest-level kernels (amgh_dense_spd_inverse, the
+ * coarse Hessian product) are bound by it.  Errors: INVALID_ARG (kind not 0
+ * or 1, tflops NULL), OOM, CUDA.  Synchronises `stream`. */
+int amgh_fp64_peak(int kind, void *stream, double *tflops);
+
 /* Number of kernels this library launched since load (all problems). */
 int64_t amgh_launch_count(void);
 

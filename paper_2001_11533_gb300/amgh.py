@@ -100,6 +100,7 @@ _SIGS = {
     "amgh_launch_count": ([], _I64),
     "amgh_aggregate_noalloc": ([_I, _P, _P, _P, _D, _P, _P, _P], _I),
     "amgh_dense_spd_inverse": ([_I, _P, _P, _P, _P], _I),
+    "amgh_fp64_peak": ([_I, _P, _P], _I),
     "amgh_batch_create": ([_P, _I, _P], _I),
     "amgh_batch_setup": ([_P, _P], _I),
     "amgh_batch_set_workers": ([_P, _I], _I),
@@ -195,6 +196,13 @@ def dense_spd_inverse(a, inv_out, stream=None):
     if st not in (0, ERR_INDEFINITE):
         check(st, "amgh_dense_spd_inverse")
     return st, info.value
+
+
+def fp64_peak(kind: int, stream=None) -> float:
+    """amgh_fp64_peak: measured FP64 TFLOP/s, kind 0 = FMA pipe, 1 = mma.m8n8k4.f64."""
+    t = C.c_double()
+    check(lib().amgh_fp64_peak(int(kind), C.c_void_p(stream) if stream else None, C.byref(t)), "amgh_fp64_peak")
+    return t.value
 
 
 def _fill(o, kw):

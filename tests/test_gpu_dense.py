@@ -119,3 +119,16 @@ def test_concurrent_inverses_on_several_streams():
     for t in threads:
         t.join()
     assert not errors, errors
+
+
+def test_fp64_peak_is_measured():
+    """amgh_fp64_peak: both forms give a positive rate, within a plausible band
+    of the part's FP64 rate (GB300: about 1.25 TFLOP/s nominal for either);
+    an unknown kind is refused."""
+    from paper_2001_11533_gb300 import amgh
+    for kind in (0, 1):
+        t = amgh.fp64_peak(kind)
+        assert 0.1 < t < 200.0, (kind, t)
+    with pytest.raises(amgh.AmghError) as e:
+        amgh.fp64_peak(2)
+    assert e.value.code == -1
