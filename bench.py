@@ -67,6 +67,8 @@ def parse():
     ap.add_argument("--block-apply", action="store_true",
                     help="block solver against single-column solves on one 513^2 square with 8 desired "
                          "states (prints its own JSON line)")
+    ap.add_argument("--no-slots", action="store_true",
+                    help="with --block-apply: leave out the concurrent-slot batch solve (host threads)")
     ap.add_argument("--autotune", type=int, default=0,
                     help="time the SpMV layouts of every operator at setup (remembered per matrix shape)")
     ap.add_argument("--no-batch", action="store_true",
@@ -752,9 +754,18 @@ def block_apply(args):
             prob.set_yd(Y[c])
             prob.solve(want_y=False, **sopts)
     t_ss = best(singles)
-    batch = amgh.Batch([amgh.Problem.from_workload(w)]).setup(**amg)
-    t_sc = best(lambda: batch.solve([Y], **sopts))
-    batch.close()
+    t_sc = None
+    if not args.no_slots:
+        batch = amgh.Batch([amgh.Problem.from_workload(w)]).setup(**amg)
+        t_sc = best(lambda: batch.solve([Y], **sopts))
+        batch.close()
+    # one more block solve inside a profiler range, for
+    # `ncu --profile-from-start off` launch lists of exactly one block solve
+    torch.cuda.synchronize()
+    torch.cuda.profiler.start()
+    prob.solve_block(Y, **sopts)
+    torch.cuda.synchronize()
+    torch.cuda.profiler.stop()
     print(json.dumps({"block_apply": {
         "workload": "jittered 513^2 square, 8 desired states, mixed form", "K": 8,
         "hessian_apply_block_s": t_hb, "hessian_apply_8_single_s": t_hs,
