@@ -772,13 +772,31 @@ __global__ void k_df_update(int n, const float *z, const float *__restrict__ sh,
     bool first = sc->beta == 0.0;
     DF acc = {0.f, 0.f}, tot_df[1];
     double tot[1];
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        DF zi = {z[i], 0.f};
-        DF si = {sh[i], sl[i]};
-        DF pi = first ? zi : df_add2(zi, df_mul2(be, DF{ph[i], pl[i]}));
-        DF qi = first ? si : df_add2(si, df_mul2(be, DF{qh[i], ql[i]}));
-        DF xi = df_add2(DF{xh[i], xl[i]}, df_mul2(al, pi));
-        DF ri = df_add2(DF{rh[i], rl[i]}, df_mul2(nal, qi));
+    // operands of one element: z, s, p, q, x, r (hi/lo) and D^-1
+    struct In {
+        float z, s1, s2, p1, p2, q1, q2, x1, x2, r1, r2, iv;
+    };
+    auto load = [&](int i, In &e) {
+        e.z = z[i];
+        e.s1 = sh[i];
+        e.s2 = sl[i];
+        e.p1 = ph[i];
+        e.p2 = pl[i];
+        e.q1 = qh[i];
+        e.q2 = ql[i];
+        e.x1 = xh[i];
+        e.x2 = xl[i];
+        e.r1 = rh[i];
+        e.r2 = rl[i];
+        e.iv = invd32 ? invd32[i] : 0.f;
+    };
+    auto step = [&](int i, const In &e) {
+        DF zi = {e.z, 0.f};
+        DF si = {e.s1, e.s2};
+        DF pi = first ? zi : df_add2(zi, df_mul2(be, DF{e.p1, e.p2}));
+        DF qi = first ? si : df_add2(si, df_mul2(be, DF{e.q1, e.q2}));
+        DF xi = df_add2(DF{e.x1, e.x2}, df_mul2(al, pi));
+        DF ri = df_add2(DF{e.r1, e.r2}, df_mul2(nal, qi));
         ph[i] = pi.hi;
         pl[i] = pi.lo;
         qh[i] = qi.hi;
@@ -789,13 +807,24 @@ __global__ void k_df_update(int n, const float *z, const float *__restrict__ sh,
         rl[i] = ri.lo;
         if (vd) {
             // the V-cycle's first smoother step from zero on the new residual
-            float v = cheb_first_point(ri.hi, invd32[i], c0);
+            float v = cheb_first_point(ri.hi, e.iv, c0);
             vd[i] = v;
             vx[i] = v;
         } else if (invd32) {
-            znew[i] = ri.hi * invd32[i];
+            znew[i] = ri.hi * e.iv;
         }
         acc = df_add_fast(acc, df_mul2(ri, ri)); // squares: no cancellation
+    };
+    // two elements (one stride apart) per pass with all their loads issued
+    // first; r.r takes them in the order one element per pass would
+    const int stride = gridDim.x * blockDim.x;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += 2 * stride) {
+        const int j = i + stride;
+        In e0, e1;
+        load(i, e0);
+        if (j < n) load(j, e1);
+        step(i, e0);
+        if (j < n) step(j, e1);
     }
     tot_df[0] = acc;
     if (reduce_df_last_block<1>(tot_df, partials, ticket, tot)) cg_finalize(F_RR, tot, sc, nullptr);
