@@ -8,8 +8,9 @@
 // Both inverses come from a blocked right-looking Cholesky factorisation
 // A = L L^T (INDEFINITE if a pivot is not positive) whose panel steps also
 // form W = L^-1, then A^-1 = W^T W (upper triangle only, then mirrored).  All
-// FP64 on CUDA cores: GB300's FP64 rate is the same on the tensor pipe, and the
-// K = 32 products that carry the flops run at that rate already.
+// FP64 on the FMA pipe: on GB300 the FP64 tensor instruction is only about 4 %
+// faster (amgh_fp64_peak measures both), and the products that carry the
+// flops already keep the FP64 pipe busy almost all the time.
 #include <math.h>
 
 #include "internal.cuh"
