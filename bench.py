@@ -748,6 +748,9 @@ def block_apply(args):
     t_hb = best(lambda: prob.hessian_apply(U))
     t_hs = best(lambda: [prob.hessian_apply(U[c]) for c in range(8)])
     t_sb = best(lambda: prob.solve_block(Y, **sopts))
+    prob_p = amgh.Problem.from_workload(w).amg_setup(persistent_cg=1, **amg)
+    t_sbp = best(lambda: prob_p.solve_block(Y, **sopts))
+    prob_p.close()
 
     def singles():
         for c in range(8):
@@ -769,7 +772,8 @@ def block_apply(args):
     print(json.dumps({"block_apply": {
         "workload": "jittered 513^2 square, 8 desired states, mixed form", "K": 8,
         "hessian_apply_block_s": t_hb, "hessian_apply_8_single_s": t_hs,
-        "solve_block_s": t_sb, "solve_8_concurrent_slots_s": t_sc, "solve_8_single_s": t_ss,
+        "solve_block_s": t_sb, "solve_block_persistent_mass_cg_s": t_sbp,
+        "solve_8_concurrent_slots_s": t_sc, "solve_8_single_s": t_ss,
         "timing": "host clock around synchronous calls, best of 3 after a warm-up"}}), flush=True)
 
 

@@ -122,7 +122,15 @@ typedef struct {
  *                  else INVALID_ARG) the level-0 smoother steps and residual
  *                  of FP32 V-cycles apply the stiffness matrix-free from the
  *                  element coefficients instead of reading the assembled
- *                  matrix; same operator, different rounding */
+ *                  matrix; same operator, different rounding
+ *  persistent_cg   1 = the block solver's mass CGs (precisions 1 and 2) run
+ *                  all their iterations in one cooperative launch over the
+ *                  GPU (grid-stride rows, two bounded software grid barriers
+ *                  per iteration; a barrier that gives up makes the call
+ *                  return AMGH_ERR_TIMEOUT) instead of graph-replayed
+ *                  kernels; handles from amgh_problem_share use 0.  Same
+ *                  arithmetic per row, sums grouped differently: results
+ *                  agree with 0 to the CG tolerance, not to the bit */
 typedef struct {
     int max_levels;
     int hessian_levels;
@@ -138,6 +146,7 @@ typedef struct {
     int aggressive;
     int geometric;
     int matrix_free;
+    int persistent_cg;
 } amgh_amg_opts;
 
 /* Solve options (Sec. 5.2-5.3).
@@ -201,7 +210,7 @@ typedef struct {
 
 /* Defaults: max_levels 25, hessian_levels 0, theta 0.08, coarse_max 256,
  * Chebyshev degree 2, precision 0, smoothed prolongator, coarse_solve 0, fuse_coarse 0,
- * autotune 0, aggressive 0, geometric 0, matrix_free 0;
+ * autotune 0, aggressive 0, geometric 0, matrix_free 0, persistent_cg 0;
  * tol 1e-8, max_iter 200, inner/mass tol 1e-10, precond 1, ncols 1, caps
  * 1000, precond_tol 0 (= inner_tol), coarse_tol 1e-4, coarse_max_iter 1000,
  * level_fallback 0. */
@@ -549,6 +558,12 @@ int amgh_dense_spd_inverse(int n, const double *a_dev, double *inv_dev, void *st
  * coarse Hessian product) are bound by it.  Errors: INVALID_ARG (kind not 0
  * or 1, tflops NULL), OOM, CUDA.  Synchronises `stream`. */
 int amgh_fp64_peak(int kind, void *stream, double *tflops);
+
+/* Test hook: the number of polls every software grid barrier wait (the
+ * grid-fused V-cycle, the persistent block mass CG) makes before it gives up
+ * and the call returns AMGH_ERR_TIMEOUT; -1 restores the default (2^20 polls
+ * of about 64 ns).  Process-wide.  Errors: INVALID_ARG below -1, CUDA. */
+int amgh_debug_grid_polls(int polls);
 
 /* Number of kernels this library launched since load (all problems). */
 int64_t amgh_launch_count(void);

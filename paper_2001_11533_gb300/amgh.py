@@ -38,7 +38,7 @@ class amgh_amg_opts(C.Structure):
                 ("coarse_max", C.c_int), ("smoother", C.c_int), ("smooth_degree", C.c_int),
                 ("precision", C.c_int), ("smooth_prolongator", C.c_int), ("coarse_solve", C.c_int),
                 ("fuse_coarse", C.c_int), ("autotune", C.c_int), ("aggressive", C.c_int),
-                ("geometric", C.c_int), ("matrix_free", C.c_int)]
+                ("geometric", C.c_int), ("matrix_free", C.c_int), ("persistent_cg", C.c_int)]
 
 
 class amgh_solve_opts(C.Structure):
@@ -101,6 +101,7 @@ _SIGS = {
     "amgh_aggregate_noalloc": ([_I, _P, _P, _P, _D, _P, _P, _P], _I),
     "amgh_dense_spd_inverse": ([_I, _P, _P, _P, _P], _I),
     "amgh_fp64_peak": ([_I, _P, _P], _I),
+    "amgh_debug_grid_polls": ([_I], _I),
     "amgh_batch_create": ([_P, _I, _P], _I),
     "amgh_batch_setup": ([_P, _P], _I),
     "amgh_batch_set_workers": ([_P, _I], _I),
@@ -182,6 +183,7 @@ def aggregate_noalloc(rowptr, col, val, theta, agg_out, stream=None):
 
 
 ERR_INDEFINITE = -6
+ERR_TIMEOUT = -8
 
 
 def dense_spd_inverse(a, inv_out, stream=None):
@@ -196,6 +198,12 @@ def dense_spd_inverse(a, inv_out, stream=None):
     if st not in (0, ERR_INDEFINITE):
         check(st, "amgh_dense_spd_inverse")
     return st, info.value
+
+
+def debug_grid_polls(polls: int = -1):
+    """amgh_debug_grid_polls: poll limit of every software grid barrier wait
+    (-1 = default); a test hook for the timeout path."""
+    check(lib().amgh_debug_grid_polls(int(polls)), "amgh_debug_grid_polls")
 
 
 def fp64_peak(kind: int, stream=None) -> float:

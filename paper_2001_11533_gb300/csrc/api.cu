@@ -33,6 +33,7 @@ extern "C" void amgh_amg_opts_default(amgh_amg_opts *o)
     o->aggressive = 0;
     o->geometric = 0;
     o->matrix_free = 0;
+    o->persistent_cg = 0;
 }
 
 extern "C" void amgh_solve_opts_default(amgh_solve_opts *o)
@@ -467,7 +468,8 @@ extern "C" int amgh_amg_setup(amgh_problem *p, const amgh_amg_opts *opts)
         o.coarse_max < 1 || !(o.theta >= 0.0) || (o.smoother != 0 && o.smoother != 1) ||
         o.precision < 0 || o.precision > 2 || o.hessian_levels < 0 || o.coarse_solve < 0 || o.coarse_solve > 2 || (o.fuse_coarse < 0 || o.fuse_coarse > 2) ||
         (o.autotune != 0 && o.autotune != 1) || (o.aggressive != 0 && o.aggressive != 1) ||
-        (o.geometric != 0 && o.geometric != 1) || (o.matrix_free != 0 && o.matrix_free != 1))
+        (o.geometric != 0 && o.geometric != 1) || (o.matrix_free != 0 && o.matrix_free != 1) ||
+        (o.persistent_cg != 0 && o.persistent_cg != 1))
         return AMGH_ERR_INVALID_ARG;
     double t0 = now_s();
     StreamScope ss_(p->stream);
@@ -507,7 +509,9 @@ static int finish_call(amgh_problem *p, int st)
     int s2 = sync_stream(p);
     int s3 = s2 == AMGH_OK ? bulk_timeout_check(p->stream) : s2;
     int s4 = s2 == AMGH_OK ? grid_timeout_check(p) : s2;
-    if (s3 == AMGH_ERR_TIMEOUT || s4 == AMGH_ERR_TIMEOUT) return AMGH_ERR_TIMEOUT;
+    int s5 = s2 == AMGH_OK ? block_grid_timeout_check(p) : s2;
+    if (s3 == AMGH_ERR_TIMEOUT || s4 == AMGH_ERR_TIMEOUT || s5 == AMGH_ERR_TIMEOUT) return AMGH_ERR_TIMEOUT;
+    if (s4 == AMGH_OK) s4 = s5;
     if (s3 == AMGH_OK) s3 = s4;
     return st != AMGH_OK ? st : s3;
 }
@@ -891,6 +895,13 @@ extern "C" int amgh_debug_limits(int bulk_first_polls, int mis_round_cap, int pr
     mis_set_round_cap(mis_round_cap);
     prol_set_row_cap(prol_row_cap);
     return bulk_set_first_polls(bulk_first_polls);
+}
+
+extern "C" int amgh_debug_grid_polls(int polls)
+{
+    if (polls < -1) return AMGH_ERR_INVALID_ARG;
+    TRY(fused_set_grid_polls(polls));
+    return block_set_grid_polls(polls);
 }
 
 extern "C" int amgh_kernel_timing_mask(amgh_problem *p, unsigned mask)

@@ -139,6 +139,33 @@ __device__ __forceinline__ void ldk_ro(const double *p, double (&v)[K])
     }
 }
 
+// loads through L2 (ld.global.cg): vectors that other blocks of the same
+// launch have written (the persistent kernel; L1 is not coherent across SMs)
+template <int K>
+__device__ __forceinline__ void ldk_cg(const float *p, float (&v)[K])
+{
+    if constexpr (K % 4 == 0) {
+#pragma unroll
+        for (int i = 0; i < K / 4; i++) {
+            float4 w = __ldcg(reinterpret_cast<const float4 *>(p) + i);
+            v[4 * i] = w.x;
+            v[4 * i + 1] = w.y;
+            v[4 * i + 2] = w.z;
+            v[4 * i + 3] = w.w;
+        }
+    } else if constexpr (K % 2 == 0) {
+#pragma unroll
+        for (int i = 0; i < K / 2; i++) {
+            float2 w = __ldcg(reinterpret_cast<const float2 *>(p) + i);
+            v[2 * i] = w.x;
+            v[2 * i + 1] = w.y;
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < K; i++) v[i] = __ldcg(p + i);
+    }
+}
+
 template <int K>
 __device__ __forceinline__ void stk(float *p, const float (&v)[K])
 {
@@ -236,10 +263,11 @@ __device__ __forceinline__ void row_sum_k(const MatView<T> &m, int row, const T 
 
 // row of (A_hi + A_lo) times K columns of z, accumulated in double-float;
 // every lane of the group returns the K normalised sums
-template <typename Z, int TPR, int K>
+template <typename Z, int TPR, int K, bool CG = false>
 __device__ __forceinline__ void row_sum_df_k(const MatView<float> &m, const float *__restrict__ lo, int row,
                                              const Z *__restrict__ z, DF (&out)[K])
 {
+    // CG: z is written by other blocks of the same launch: gathers through L2
     constexpr int STEP = TPR == 1 ? 32 : TPR;
     // K = 8 double-float accumulators already take 16 registers: gather in half chunks
     constexpr int U = K >= 8 ? ROW_UNROLL / 2 : Chunk<Z, K>::U;
@@ -264,8 +292,10 @@ __device__ __forceinline__ void row_sum_df_k(const MatView<float> &m, const floa
                 Z zv[U][K];
 #pragma unroll
                 for (int j = 0; j < U; j++) {
-                    if (cc[j0 + j] >= 0) ldk_ro<K>(z + (int64_t)cc[j0 + j] * K, zv[j]);
-                    else {
+                    if (cc[j0 + j] >= 0) {
+                        if constexpr (CG) ldk_cg<K>(z + (int64_t)cc[j0 + j] * K, zv[j]);
+                        else ldk_ro<K>(z + (int64_t)cc[j0 + j] * K, zv[j]);
+                    } else {
 #pragma unroll
                         for (int c = 0; c < K; c++) zv[j][c] = (Z)0;
                     }
@@ -282,7 +312,8 @@ __device__ __forceinline__ void row_sum_df_k(const MatView<float> &m, const floa
             for (; k < end; k += STEP) {
                 float ah = m.v[k], al = lo[k];
                 Z zv[K];
-                ldk_ro<K>(z + (int64_t)col_of(m, row, k) * K, zv);
+                if constexpr (CG) ldk_cg<K>(z + (int64_t)col_of(m, row, k) * K, zv);
+                else ldk_ro<K>(z + (int64_t)col_of(m, row, k) * K, zv);
 #pragma unroll
                 for (int c = 0; c < K; c++) df_term<Z>(acc[c], ah, al, zv[c]);
             }
@@ -360,16 +391,23 @@ __device__ bool reduce_k(const double (&val)[NV], double *partials, unsigned *ti
 
 // The same in double-float for the double-float block CG: values transposed
 // through shared memory as in reduce_k, warps summing columns of it, block
-// partials as FP32 pairs, and the last block loading all NV partials of a
-// block at once.
+// partials as FP32 pairs ([NV][nb]), and the last block loading all NV
+// partials of a block at once.
+// shared staging of NV double-float values per thread (one buffer per kernel,
+// passed to both helpers below)
 template <int NV>
-__device__ bool reduce_dfk(const DF (&val)[NV], double *partials, unsigned *ticket, double (&tot)[NV])
+struct DfStage {
+    float hi[NV][TPB_K], lo[NV][TPB_K];
+    DF tot[NV];
+};
+
+template <int NV, int NVMAX = NV>
+__device__ void block_df_partials(const DF (&val)[NV], float2 *part, int nb, int bid, DfStage<NVMAX> &st)
 {
-    __shared__ float shh[NV][TPB_K], shl[NV][TPB_K];
-    __shared__ DF stot[NV];
-    __shared__ bool is_last;
-    const int t = threadIdx.x, w = t >> 5, l = t & 31, nb = gridDim.x;
-    float2 *part = reinterpret_cast<float2 *>(partials);
+    static_assert(NV <= NVMAX, "staging buffer too small");
+    float(&shh)[NVMAX][TPB_K] = st.hi;
+    float(&shl)[NVMAX][TPB_K] = st.lo;
+    const int t = threadIdx.x, w = t >> 5, l = t & 31;
 #pragma unroll
     for (int q = 0; q < NV; q++) {
         shh[q][t] = val[q].hi;
@@ -381,14 +419,20 @@ __device__ bool reduce_dfk(const DF (&val)[NV], double *partials, unsigned *tick
 #pragma unroll
         for (int j = l; j < TPB_K; j += 32) s = df_add_fast(s, DF{shh[q][j], shl[q][j]});
         s = df_warp_sum(s);
-        if (l == 0) part[q * nb + blockIdx.x] = make_float2(s.hi, s.lo);
+        if (l == 0) part[q * nb + bid] = make_float2(s.hi, s.lo);
     }
-    __threadfence();
-    __syncthreads();
-    if (t == 0) is_last = atomicAdd(ticket, 1u) == (unsigned)nb - 1;
-    __syncthreads();
-    if (!is_last) return false;
-    __threadfence();
+}
+
+// the NV sums over the nb block partials, in fixed order; thread 0 returns them
+template <int NV, int NVMAX = NV>
+__device__ void sum_df_partials(const float2 *part, int nb, double (&tot)[NV], DfStage<NVMAX> &st)
+{
+    static_assert(NV <= NVMAX, "staging buffer too small");
+    float(&shh)[NVMAX][TPB_K] = st.hi;
+    float(&shl)[NVMAX][TPB_K] = st.lo;
+    DF(&stot)[NVMAX] = st.tot;
+    const int t = threadIdx.x, w = t >> 5, l = t & 31;
+    __syncthreads(); // the staging buffer may still be read by a previous step
     DF s[NV];
 #pragma unroll
     for (int q = 0; q < NV; q++) s[q] = DF{0.f, 0.f};
@@ -413,9 +457,28 @@ __device__ bool reduce_dfk(const DF (&val)[NV], double *partials, unsigned *tick
         if (l == 0) stot[q] = u;
     }
     __syncthreads();
-    if (t != 0) return false;
+    if (t == 0) {
 #pragma unroll
-    for (int q = 0; q < NV; q++) tot[q] = df_to_double(stot[q]);
+        for (int q = 0; q < NV; q++) tot[q] = df_to_double(stot[q]);
+    }
+}
+
+template <int NV>
+__device__ bool reduce_dfk(const DF (&val)[NV], double *partials, unsigned *ticket, double (&tot)[NV])
+{
+    __shared__ bool is_last;
+    __shared__ DfStage<NV> st;
+    const int t = threadIdx.x, nb = gridDim.x;
+    float2 *part = reinterpret_cast<float2 *>(partials);
+    block_df_partials<NV>(val, part, nb, blockIdx.x, st);
+    __threadfence();
+    __syncthreads();
+    if (t == 0) is_last = atomicAdd(ticket, 1u) == (unsigned)nb - 1;
+    __syncthreads();
+    if (!is_last) return false;
+    __threadfence();
+    sum_df_partials<NV>(part, nb, tot, st);
+    if (t != 0) return false;
     *ticket = 0u;
     return true;
 }
@@ -873,6 +936,151 @@ __global__ void kbd_out(int64_t nk, const float *__restrict__ xh, const float *_
         y[e] = ((double)xh[e] + (double)xl[e]) * inv_pow2(bs->c[e & (K - 1)].scale);
 }
 
+// ------------------------------------------------------------------ persistent block mass CG
+// The whole Jacobi-preconditioned double-float block CG of one mass solve as
+// one cooperative launch (every block resident; rows and elements walked
+// grid-stride).  Per iteration: s = M z with (r, z) and (z, s) per column,
+// grid barrier; every block then sums the block partials in the same fixed
+// order and takes the scalar step on its own shared copy of the per-column
+// scalars, so all blocks reach the same alpha, beta and stopping decisions
+// without another barrier; then p, q, x, r, z = D^-1 r_hi and r.r, grid
+// barrier, and the stopping test the same way.  Block 0 writes the scalars
+// back.  Row and element arithmetic are those of kbd_spmv and kbd_update; the
+// sums are grouped by this launch's blocks.  Vectors written during the
+// launch are read through L2.  A barrier that runs out makes every block
+// leave at its next barrier (the call then returns AMGH_ERR_TIMEOUT).
+#include "gridbar.cuh"
+
+template <int TPR, int K>
+__global__ void __launch_bounds__(TPB_K) kbp_mass_cg(MatView<float> A, const float *__restrict__ lo,
+                                                    const float *__restrict__ invd32, float *z, float *sh,
+                                                    float *sl, float *ph, float *pl, float *qh, float *ql, float *xh,
+                                                    float *xl, float *rh, float *rl, BScal *bs, float2 *p1,
+                                                    float2 *p2, GridBar *gb, int cap)
+{
+    constexpr int H = K > 4 ? 2 : 1; // threads per element in the update
+    constexpr int KH = K / H;
+    __shared__ BScal sb;
+    __shared__ DfStage<2 * K> st;
+    const int t = threadIdx.x, nb = gridDim.x, n = A.rows;
+    if (t == 0) sb = *bs;
+    __syncthreads();
+    const int stride = nb * blockDim.x, slots = n * TPR;
+    for (int it = 0; it <= cap && !sb.all; it++) {
+        // ---- s = A z, (r, z), (z, s)
+        DF a[2 * K];
+        double tot[2 * K];
+#pragma unroll
+        for (int q = 0; q < 2 * K; q++) a[q] = DF{0.f, 0.f};
+        for (int base = blockIdx.x * blockDim.x; base < slots; base += stride) {
+            int row = (base + t) / TPR;
+            DF sv[K];
+            row_sum_df_k<float, TPR, K, true>(A, lo, row, z, sv);
+            if (row < n && row_leader<TPR>()) {
+                int64_t o = (int64_t)row * K;
+                float hv[K], lv[K], zr[K], rhv[K], rlv[K];
+#pragma unroll
+                for (int c = 0; c < K; c++) {
+                    hv[c] = sv[c].hi;
+                    lv[c] = sv[c].lo;
+                }
+                stk<K>(sh + o, hv);
+                stk<K>(sl + o, lv);
+                ldk_cg<K>(z + o, zr);
+                ldk_cg<K>(rh + o, rhv);
+                ldk_cg<K>(rl + o, rlv);
+#pragma unroll
+                for (int c = 0; c < K; c++) {
+                    a[c] = df_add_fast(a[c], df_mulf(DF{rhv[c], rlv[c]}, zr[c]));
+                    a[K + c] = df_add_fast(a[K + c], df_mulf(sv[c], zr[c]));
+                }
+            }
+        }
+        block_df_partials<2 * K>(a, p1, nb, blockIdx.x, st);
+        if (!grid_sync(gb, nb)) return;
+        sum_df_partials<2 * K>(p1, nb, tot, st);
+        if (t == 0) fin_cg2<K>(&sb, tot);
+        __syncthreads();
+        // ---- p = z + beta p, q = s + beta q, x += alpha p, r -= alpha q, z = D^-1 r_hi, r.r
+        const int64_t items = (int64_t)n * H;
+        int64_t it0 = (int64_t)blockIdx.x * blockDim.x + t;
+        const int h = H == 1 ? 0 : (int)(it0 & 1); // fixed: the stride is even
+        DF al[KH], nal[KH], be[KH], vh[KH];
+        bool run[KH], first[KH];
+#pragma unroll
+        for (int c = 0; c < KH; c++) {
+            const CgScal &sc = sb.c[h * KH + c];
+            al[c] = DF{sc.ahi, sc.alo};
+            nal[c] = DF{-sc.ahi, -sc.alo};
+            be[c] = DF{sc.bhi, sc.blo};
+            run[c] = !sc.done;
+            first[c] = sc.bhi == 0.f && sc.blo == 0.f;
+            vh[c] = DF{0.f, 0.f};
+        }
+        for (int64_t e = it0; e < items; e += stride) {
+            int64_t i = e / H;
+            int64_t o = i * K + h * KH;
+            float zv[KH], s1[KH], s2[KH], q1[KH], q2[KH], x1[KH], x2[KH], r1[KH], r2[KH], pp1[KH], pp2[KH];
+            ldk_cg<KH>(z + o, zv);
+            ldk_cg<KH>(sh + o, s1);
+            ldk_cg<KH>(sl + o, s2);
+            ldk_cg<KH>(ph + o, pp1);
+            ldk_cg<KH>(pl + o, pp2);
+            ldk_cg<KH>(qh + o, q1);
+            ldk_cg<KH>(ql + o, q2);
+            ldk_cg<KH>(xh + o, x1);
+            ldk_cg<KH>(xl + o, x2);
+            ldk_cg<KH>(rh + o, r1);
+            ldk_cg<KH>(rl + o, r2);
+#pragma unroll
+            for (int c = 0; c < KH; c++) {
+                if (!run[c]) continue;
+                DF zi = {zv[c], 0.f}, si = {s1[c], s2[c]};
+                DF pi = first[c] ? zi : df_add2(zi, df_mul2(be[c], DF{pp1[c], pp2[c]}));
+                DF qi = first[c] ? si : df_add2(si, df_mul2(be[c], DF{q1[c], q2[c]}));
+                DF xi = df_add2(DF{x1[c], x2[c]}, df_mul2(al[c], pi));
+                DF ri = df_add2(DF{r1[c], r2[c]}, df_mul2(nal[c], qi));
+                pp1[c] = pi.hi;
+                pp2[c] = pi.lo;
+                q1[c] = qi.hi;
+                q2[c] = qi.lo;
+                x1[c] = xi.hi;
+                x2[c] = xi.lo;
+                r1[c] = ri.hi;
+                r2[c] = ri.lo;
+                vh[c] = df_add_fast(vh[c], df_mul2(ri, ri));
+            }
+            stk<KH>(ph + o, pp1);
+            stk<KH>(pl + o, pp2);
+            stk<KH>(qh + o, q1);
+            stk<KH>(ql + o, q2);
+            stk<KH>(xh + o, x1);
+            stk<KH>(xl + o, x2);
+            stk<KH>(rh + o, r1);
+            stk<KH>(rl + o, r2);
+            float iv = invd32[i], zn[KH];
+#pragma unroll
+            for (int c = 0; c < KH; c++) zn[c] = iv * r1[c];
+            stk<KH>(z + o, zn);
+        }
+        DF v[K];
+        double rr[K];
+#pragma unroll
+        for (int c = 0; c < K; c++) v[c] = DF{0.f, 0.f};
+#pragma unroll
+        for (int c = 0; c < KH; c++) {
+            if (H == 1 || h == 0) v[c] = vh[c];
+            else v[KH + c] = vh[c];
+        }
+        block_df_partials<K, 2 * K>(v, p2, nb, blockIdx.x, st);
+        if (!grid_sync(gb, nb)) return;
+        sum_df_partials<K, 2 * K>(p2, nb, rr, st);
+        if (t == 0) fin_rr<K>(&sb, rr);
+        __syncthreads();
+    }
+    if (blockIdx.x == 0 && t == 0) *bs = sb;
+}
+
 // ------------------------------------------------------------------ V-cycle kernels
 // first smoother step from zero: d = x = c D^-1 b
 template <typename T, int K>
@@ -1161,8 +1369,13 @@ struct BlockWork {
     RedSlot ored;
     BScal *h_bs = nullptr;
     double *h_dots = nullptr;
+    // persistent mass CG (persistent_cg): barrier and block partials of its
+    // cooperative launch, up to PERSIST_MAX_BLOCKS blocks
+    GridBar *pbar = nullptr;
+    float2 *pp1 = nullptr, *pp2 = nullptr;
     int fail[KB]; // sticky per-column status of the current call
 };
+#define PERSIST_MAX_BLOCKS (152 * 8)
 
 static void free_bgraph(BGraph &g)
 {
@@ -1280,6 +1493,12 @@ static int block_alloc_into(amgh_problem *p, BlockWork *W, int K)
     TRY(bred_alloc(ar, W->ored, vblocks(p->n > p->m ? p->n : p->m), K));
     CU(cudaHostAlloc((void **)&W->h_bs, sizeof(BScal), cudaHostAllocDefault));
     CU(cudaHostAlloc((void **)&W->h_dots, sizeof(double) * KB, cudaHostAllocDefault));
+    if (f32 && p->aopts.persistent_cg && !p->parent) {
+        TRY(ar.alloc(&W->pbar, 1));
+        CU(cudaMemsetAsync(W->pbar, 0, sizeof(GridBar), g_alloc_stream));
+        TRY(ar.alloc(&W->pp1, (int64_t)PERSIST_MAX_BLOCKS * 2 * K));
+        TRY(ar.alloc(&W->pp2, (int64_t)PERSIST_MAX_BLOCKS * K));
+    }
     return AMGH_OK;
 }
 
@@ -1514,6 +1733,54 @@ struct Blk {
         return AMGH_OK;
     }
 
+    // the mass CG's iterations as one cooperative launch (persistent_cg)
+    static int persistent_mass(amgh_problem *p, const DevCsr &a, BCtrl &D, const float *invd32, int maxit)
+    {
+        BlockWork &W = *p->blk;
+        int n = a.rows, dev = 0, sms = 0;
+        MatView<float> A = bview<float>(a);
+        if (!a.lo32 || !W.pbar) return AMGH_ERR_INVALID_ARG;
+        CU(cudaGetDevice(&dev));
+        CU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        cudaError_t err = cudaSuccess;
+        if (!with_tpr(A.tpr, [&](auto t) {
+                constexpr int TPR = decltype(t)::value;
+                auto kern = kbp_mass_cg<TPR, K>;
+                int per_sm = 0;
+                err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, TPB, 0);
+                if (err != cudaSuccess) return;
+                int64_t want = ceil_div((int64_t)n * (TPR > 2 ? TPR : 2), TPB);
+                int64_t grid = (int64_t)per_sm * sms;
+                if (grid > PERSIST_MAX_BLOCKS) grid = PERSIST_MAX_BLOCKS;
+                if (grid > want) grid = want;
+                if (grid < 1 || per_sm < 1) {
+                    err = cudaErrorInvalidConfiguration;
+                    return;
+                }
+                cudaLaunchConfig_t cfg = {};
+                cudaLaunchAttribute attr[1];
+                attr[0].id = cudaLaunchAttributeCooperative;
+                attr[0].val.cooperative = 1;
+                cfg.gridDim = dim3((unsigned)grid, 1, 1);
+                cfg.blockDim = dim3(TPB, 1, 1);
+                cfg.stream = p->stream;
+                cfg.attrs = attr;
+                cfg.numAttrs = 1;
+                err = cudaLaunchKernelEx(&cfg, kern, A, (const float *)a.lo32, invd32, (float *)D.mz, hi(D.ms),
+                                         lo(D.ms, n), hi(D.mp), lo(D.mp, n), hi(D.mq), lo(D.mq, n), hi(D.mx),
+                                         lo(D.mx, n), hi(D.mr), lo(D.mr, n), D.mbs, W.pp1, W.pp2, (GridBar *)W.pbar,
+                                         maxit + 2);
+                amgh_count_launch();
+            }))
+            return AMGH_ERR_INVALID_ARG;
+        if (err != cudaSuccess) {
+            cudaGetLastError();
+            amgh_note_error((int)err, __FILE__, __LINE__);
+            return AMGH_ERR_CUDA;
+        }
+        return AMGH_OK;
+    }
+
     static int df_out(amgh_problem *p, int n, double *x, const BScal *bs, double *y)
     {
         int64_t nk = (int64_t)n * K;
@@ -1619,6 +1886,7 @@ struct Blk {
         // direction z in FP32, as the single-column double-float mass CG
         const bool z32 = W.f32 != 0;
         std::function<int()> iter;
+        const bool persist = z32 && W.pbar != nullptr;
         if (z32) {
             TRY(df_start(p, n, b, D.mx, D.mr, (float *)D.mz, (const float *)C.mu_invdiag32, D.mbs, D.red, tol,
                          maxit));
@@ -1640,7 +1908,12 @@ struct Blk {
             };
         }
         BScal h;
-        TRY(run_loop(p, D.mg, std::function<int()>(), iter, D.mbs, maxit, &D.mhint, &h));
+        if (persist) {
+            TRY(persistent_mass(p, C.Mu, D, (const float *)C.mu_invdiag32, maxit));
+            TRY(read_bscal(p, D.mbs, &h));
+        } else {
+            TRY(run_loop(p, D.mg, std::function<int()>(), iter, D.mbs, maxit, &D.mhint, &h));
+        }
         for (int c = 0; c < K; c++) {
             p->c_mass += h.c[c].iters;
             p->c_mass_lvl[l] += h.c[c].iters;
@@ -2081,4 +2354,27 @@ int block_solve(amgh_problem *p, const double *yd, int ncols, double *u, const a
     else st = dispatch_solve<double>(p, K, yd, ncols, u, o, info, &first);
     if (st != AMGH_OK) return st;
     return first;
+}
+
+// poll limit of this file's grid barrier waits (-1: default)
+int block_set_grid_polls(int polls)
+{
+    int v = polls < 0 ? GRIDBAR_POLLS : polls;
+    CU(cudaMemcpyToSymbol(g_gridbar_polls, &v, sizeof(int)));
+    return AMGH_OK;
+}
+
+// AMGH_ERR_TIMEOUT (and the flag and barrier reset) if a persistent block CG
+// of this problem gave up at a barrier
+int block_grid_timeout_check(amgh_problem *p)
+{
+    int h = 0;
+    CU(cudaMemcpyFromSymbolAsync(&h, g_gridbar_timeout, sizeof(int), 0, cudaMemcpyDeviceToHost, p->stream));
+    CU(cudaStreamSynchronize(p->stream));
+    if (!h) return AMGH_OK;
+    int zero = 0;
+    CU(cudaMemcpyToSymbolAsync(g_gridbar_timeout, &zero, sizeof(int), 0, cudaMemcpyHostToDevice, p->stream));
+    if (p->blk && p->blk->pbar) CU(cudaMemsetAsync(p->blk->pbar, 0, sizeof(GridBar), p->stream));
+    CU(cudaStreamSynchronize(p->stream));
+    return AMGH_ERR_TIMEOUT;
 }

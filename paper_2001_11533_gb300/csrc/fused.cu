@@ -12,9 +12,9 @@
 //   grid (fuse_coarse = 2): a cooperative launch of one 1024-thread block per
 //     SM for levels of at most GRID_FUSE_MAX_ROWS rows, phases separated by a
 //     software grid barrier (an arrival counter and a generation word in
-//     global memory) whose wait is bounded: a block that gives up raises
-//     g_grid_timeout and every block leaves at its next barrier, and the host
-//     reports AMGH_ERR_TIMEOUT.
+//     global memory, gridbar.cuh) whose wait is bounded: a block that gives
+//     up raises the timeout flag and every block leaves at its next barrier,
+//     and the host reports AMGH_ERR_TIMEOUT.
 // Each barrier also orders the global memory writes of one phase before the
 // reads of the next.  Every row does the same arithmetic as in the
 // level-by-level kernels (the row sums and the point-wise helpers of
@@ -23,6 +23,7 @@
 // the ordinary path.
 #include <cooperative_groups.h>
 
+#include "gridbar.cuh"
 #include "internal.cuh"
 #include "spmv.cuh"
 
@@ -31,49 +32,6 @@ namespace cg = cooperative_groups;
 #define FUSE_TPB 1024
 #define FUSE_MAX_ROWS 32768
 #define GRID_FUSE_MAX_ROWS 262144
-#define GRID_POLLS (1 << 20)
-
-// arrival counter and generation of the software grid barrier (zero at rest)
-struct GridBar {
-    unsigned count, gen;
-};
-__device__ int g_grid_timeout = 0;
-
-// Bounded grid-wide barrier: the last block to arrive resets the counter and
-// advances the generation; the others poll the generation (at most GRID_POLLS
-// times, leaving early once any block has given up).  Returns false if this
-// block gave up or another one has.
-__device__ __forceinline__ bool grid_sync(GridBar *gb, unsigned nblocks)
-{
-    __shared__ int ok;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        volatile unsigned *vgen = &gb->gen;
-        volatile int *vto = &g_grid_timeout;
-        const unsigned g0 = *vgen;
-        int good = 1;
-        __threadfence(); // this block's writes of the phase before its arrival
-        if (atomicAdd(&gb->count, 1u) == nblocks - 1) {
-            atomicExch(&gb->count, 0u);
-            __threadfence();
-            atomicAdd(&gb->gen, 1u);
-        } else {
-            for (int polls = 0; *vgen == g0; polls++) {
-                if (polls >= GRID_POLLS || *vto) {
-                    atomicExch(&g_grid_timeout, 1);
-                    good = 0;
-                    break;
-                }
-                __nanosleep(64);
-            }
-        }
-        __threadfence();
-        ok = good;
-    }
-    __syncthreads();
-    return ok != 0;
-}
-
 struct ClusterScope {
     __device__ bool sync()
     {
@@ -393,11 +351,11 @@ int fused_setup(amgh_problem *p)
 int grid_timeout_check(amgh_problem *p)
 {
     int h = 0;
-    CU(cudaMemcpyFromSymbolAsync(&h, g_grid_timeout, sizeof(int), 0, cudaMemcpyDeviceToHost, p->stream));
+    CU(cudaMemcpyFromSymbolAsync(&h, g_gridbar_timeout, sizeof(int), 0, cudaMemcpyDeviceToHost, p->stream));
     CU(cudaStreamSynchronize(p->stream));
     if (!h) return AMGH_OK;
     int zero = 0;
-    CU(cudaMemcpyToSymbolAsync(g_grid_timeout, &zero, sizeof(int), 0, cudaMemcpyHostToDevice, p->stream));
+    CU(cudaMemcpyToSymbolAsync(g_gridbar_timeout, &zero, sizeof(int), 0, cudaMemcpyHostToDevice, p->stream));
     if (p->fuse_bar) CU(cudaMemsetAsync(p->fuse_bar, 0, sizeof(GridBar), p->stream));
     CU(cudaStreamSynchronize(p->stream));
     return AMGH_ERR_TIMEOUT;
@@ -437,5 +395,13 @@ int fused_vcycle(amgh_problem *p, const float *b, float *x, int preinit, const i
     CU(cudaLaunchKernelEx(&cfg, k_vcycle_fused, (const FusedCycle *)p->fuse_table, b, x, preinit, skip));
     amgh_count_launch();
     timer_end(p, KC_COARSE, vcycle_bytes(p, p->fuse_c0, 4));
+    return AMGH_OK;
+}
+
+// poll limit of the grid barrier waits of the fused V-cycle (-1: default)
+int fused_set_grid_polls(int polls)
+{
+    int v = polls < 0 ? GRIDBAR_POLLS : polls;
+    CU(cudaMemcpyToSymbol(g_gridbar_polls, &v, sizeof(int)));
     return AMGH_OK;
 }

@@ -435,6 +435,9 @@ int fused_vcycle(amgh_problem *p, const float *b, float *x, int preinit, const i
 // AMGH_ERR_TIMEOUT (flag cleared, the problem's barrier reset) if a grid
 // barrier of the fused V-cycle gave up
 int grid_timeout_check(amgh_problem *p);
+int block_grid_timeout_check(amgh_problem *p);
+int block_set_grid_polls(int polls);
+int fused_set_grid_polls(int polls);
 // x = inv b with the FP32 copy (rows padded to ld, 16-byte aligned)
 int dense_gemv32(amgh_problem *p, int n, int ld, const float *inv32, const float *b, float *x, const int *skip);
 // FP32 copy of a dense inverse with rows padded to a multiple of 4

@@ -217,3 +217,61 @@ def test_more_columns_than_one_block():
     for c in (1, 8, 9):
         u1, _, st = prob.solve_block(cuda(Y[c:c + 1]), tol=1e-10)
         assert st == 0 and np.array_equal(host(u1[0]), host(u[c])), c
+
+
+@pytest.mark.parametrize("k", [3, 8])
+def test_persistent_mass_cg_matches_graph_replay_and_oracle(k):
+    """persistent_cg = 1: the block mass CGs as one cooperative launch each.
+    Same arithmetic per row, sums grouped by that launch's blocks: the
+    controls agree with the graph-replayed block solve to the CG tolerance
+    and with the oracle's single solves per column (mixed bound 1e-8);
+    reruns give the same bits."""
+    w = _lshape()
+    Y = _desired_states(w, k)
+    opts = dict(coarse_max=32, precision=2)
+    ref = _problem(w, **opts)
+    per = _problem(w, persistent_cg=1, **opts)
+    sopts = dict(tol=1e-10, inner_tol=1e-12, mass_tol=1e-12)
+    u0, i0, st0 = ref.solve_block(cuda(Y), **sopts)
+    u1, i1, st1 = per.solve_block(cuda(Y), **sopts)
+    assert st0 == 0 and st1 == 0
+    assert i1["mass_iters"] > 0
+    for c in range(k):
+        assert rel(host(u1[c]), host(u0[c])) <= 1e-9, c
+    u2, _, st2 = per.solve_block(cuda(Y), **sopts)
+    assert st2 == 0 and np.array_equal(host(u1), host(u2))
+    orc = Oracle(w, coarse_max=32, **TIGHT)
+    for c in (0, k - 1):
+        orc.set_yd(Y[c])
+        uo, _, _ = orc.solve(precond=1, tol=1e-12)
+        assert rel(host(u1[c]), uo) <= 1e-8, c
+
+
+def test_grid_barriers_time_out_and_recover():
+    """Both software grid barriers (the persistent block mass CG and the
+    grid-fused V-cycle) driven to give up at their first wait: the call
+    returns AMGH_ERR_TIMEOUT, no GPU wait is left hanging, and the next call
+    with the default limit gives the clean result bit for bit."""
+    from paper_2001_11533_gb300 import amgh
+    w = _lshape()
+    Y = _desired_states(w, 2)
+    per = _problem(w, coarse_max=32, precision=2, persistent_cg=1)
+    sopts = dict(tol=1e-10, inner_tol=1e-12, mass_tol=1e-12)
+    clean, _, st = per.solve_block(cuda(Y), **sopts)
+    assert st == 0
+    fused = amgh.Problem.from_workload(w).amg_setup(coarse_max=32, precision=2, fuse_coarse=2)
+    fused.set_yd(cuda(Y[0]))
+    fclean, _, finfo = fused.solve(tol=1e-10, want_y=False)
+    try:
+        amgh.debug_grid_polls(0)
+        _, _, st = per.solve_block(cuda(Y), raise_on_error=False, **sopts)
+        assert st == amgh.ERR_TIMEOUT
+        with pytest.raises(amgh.AmghError) as e:
+            fused.solve(tol=1e-10, want_y=False)
+        assert e.value.code == amgh.ERR_TIMEOUT
+    finally:
+        amgh.debug_grid_polls(-1)
+    again, _, st = per.solve_block(cuda(Y), **sopts)
+    assert st == 0 and np.array_equal(host(again), host(clean))
+    fagain, _, _ = fused.solve(tol=1e-10, want_y=False)
+    assert np.array_equal(host(fagain), host(fclean))
