@@ -76,6 +76,9 @@ def parse():
     ap.add_argument("--batch-steps", type=int, default=2)
     ap.add_argument("--forms", default="mixed,fp64,refine",
                     help="mixed = FP64 CG + FP32 V-cycles; fp64; refine = FP32 CG in FP64 refinement")
+    ap.add_argument("--persistent-cg", type=int, default=1,
+                    help="1 (default): mass CGs as one cooperative launch each (amg option persistent_cg; "
+                         "the mixed form's single-column and block mass CGs), 0: graph-replayed kernels")
     ap.add_argument("--fuse-coarse", type=int, default=0,
                     help="0: V-cycle level by level; 2: levels of <= 262144 rows in one cooperative launch")
     ap.add_argument("--experiments", action="store_true",
@@ -220,7 +223,8 @@ def run_amgh(args, rank, world, local):
         else:
             prob = amgh.Problem(w.dim, dev[0], dev[1], dev[2], dev[3], w.beta, dev[4], on_device=True)
         prob.amg_setup(precision=precision, hessian_levels=args.hessian_levels, coarse_max=args.coarse_max,
-                       smooth_degree=args.degree, autotune=args.autotune, fuse_coarse=args.fuse_coarse, **xsetup)
+                       smooth_degree=args.degree, autotune=args.autotune, fuse_coarse=args.fuse_coarse,
+                       persistent_cg=args.persistent_cg, **xsetup)
         if timing:
             prob.kernel_timing_mask(timing)
         tols = dict(tol=1e-8, inner_tol=args.inner_tol, mass_tol=args.precond_tol, precond_tol=args.precond_tol,
@@ -435,7 +439,7 @@ def run_cube(args, rank, world, local):
     def step(precision, timing=0, mf=0):
         prob = amgh.Problem(w.dim, dev[0], dev[1], dev[2], dev[3], w.beta, dev[4], on_device=True)
         prob.amg_setup(precision=precision, coarse_max=args.cube_coarse_max, smooth_degree=args.degree,
-                       coarse_solve=2, fuse_coarse=args.fuse_coarse, matrix_free=mf)
+                       coarse_solve=2, fuse_coarse=args.fuse_coarse, matrix_free=mf, persistent_cg=args.persistent_cg)
         if timing:
             prob.kernel_timing_mask(timing)
         u, y, info = prob.solve(want_y=False, **tols)
@@ -706,7 +710,8 @@ def single_step(args):
     w, _, _, xsetup, xsolve = make_workload(args)
     prob = amgh.Problem.from_workload(w)
     prob.amg_setup(precision=PRECISION[args.forms.split(",")[0]], hessian_levels=args.hessian_levels,
-                   coarse_max=args.coarse_max, smooth_degree=args.degree, autotune=args.autotune, **xsetup)
+                   coarse_max=args.coarse_max, smooth_degree=args.degree, autotune=args.autotune,
+                   persistent_cg=args.persistent_cg, **xsetup)
     u, y, info = prob.solve(tol=1e-8, inner_tol=args.inner_tol, mass_tol=args.precond_tol,
                             precond_tol=args.precond_tol, **xsolve)
     torch.cuda.synchronize()
@@ -820,6 +825,7 @@ def main():
                    "hessian_levels": args.hessian_levels, "coarse_max": args.coarse_max,
                    "chebyshev_degree": args.degree, "inner_tol": args.inner_tol,
                    "autotune": args.autotune, "fuse_coarse": args.fuse_coarse,
+                   "persistent_cg": args.persistent_cg,
                    "precond_and_mass_tol": args.precond_tol,
                    "precision": forms[0], "parallelism": "replicas" if world > 1 else "single",
                    "l2": "256 MB buffer written between timed steps",

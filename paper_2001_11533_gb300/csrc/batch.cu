@@ -138,8 +138,17 @@ extern "C" int amgh_batch_setup(amgh_batch *b, const amgh_amg_opts *amg)
         }
     }
     std::vector<int> st(np, AMGH_OK);
+    // the batch runs its handles beside each other: no cooperative launches
+    // (grid-fused V-cycle, persistent mass CG), which would compete for
+    // residency with the other handles' kernels
+    amgh_amg_opts o;
+    if (amg) o = *amg;
+    else amgh_amg_opts_default(&o);
+    if (o.fuse_coarse == 2) o.fuse_coarse = 0;
+    o.persistent_cg = 0;
+    for (int i = 0; i < np; i++) b->probs[i]->in_batch = 1;
     run_all(b, np, [&](int i) {
-        if (!b->probs[i]->setup_done) st[i] = amgh_amg_setup(b->probs[i], amg);
+        if (!b->probs[i]->setup_done) st[i] = amgh_amg_setup(b->probs[i], &o);
     });
     for (int s : st)
         if (s != AMGH_OK) return s;

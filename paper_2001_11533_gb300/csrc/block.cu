@@ -1493,7 +1493,7 @@ static int block_alloc_into(amgh_problem *p, BlockWork *W, int K)
     TRY(bred_alloc(ar, W->ored, vblocks(p->n > p->m ? p->n : p->m), K));
     CU(cudaHostAlloc((void **)&W->h_bs, sizeof(BScal), cudaHostAllocDefault));
     CU(cudaHostAlloc((void **)&W->h_dots, sizeof(double) * KB, cudaHostAllocDefault));
-    if (f32 && p->aopts.persistent_cg && !p->parent) {
+    if (f32 && p->aopts.persistent_cg && !p->parent && !p->in_batch) {
         TRY(ar.alloc(&W->pbar, 1));
         CU(cudaMemsetAsync(W->pbar, 0, sizeof(GridBar), g_alloc_stream));
         TRY(ar.alloc(&W->pp1, (int64_t)PERSIST_MAX_BLOCKS * 2 * K));
@@ -2375,6 +2375,98 @@ int block_grid_timeout_check(amgh_problem *p)
     int zero = 0;
     CU(cudaMemcpyToSymbolAsync(g_gridbar_timeout, &zero, sizeof(int), 0, cudaMemcpyHostToDevice, p->stream));
     if (p->blk && p->blk->pbar) CU(cudaMemsetAsync(p->blk->pbar, 0, sizeof(GridBar), p->stream));
+    if (p->pm_bar) CU(cudaMemsetAsync(p->pm_bar, 0, sizeof(GridBar), p->stream));
     CU(cudaStreamSynchronize(p->stream));
     return AMGH_ERR_TIMEOUT;
+}
+
+// The single-column double-float mass CG of precision 2 (persistent_cg) with
+// the K = 1 kernels of the block solver: norm and start, all iterations in
+// one cooperative launch, and the output.  Same method as the graph-replayed
+// double-float mass CG (scaled right side, Jacobi direction in FP32); sums
+// grouped by this launch's blocks.
+int persistent_mass_single(amgh_problem *p, int l, const double *b, double *x, int64_t *iters)
+{
+    CtrlLevel &C = p->cl[l];
+    const DevCsr &a = C.Mu;
+    int n = a.rows, maxit = p->sopts.mass_max_iter, dev = 0, sms = 0;
+    if (n == 0) return AMGH_OK;
+    if (!a.lo32 || !C.mu_invdiag32) return AMGH_ERR_INVALID_ARG;
+    Arena &ar = p->harena;
+    if (!p->pm_bs) {
+        BScal *bs = nullptr;
+        float2 *p1 = nullptr, *p2 = nullptr;
+        GridBar *bar = nullptr;
+        TRY(ar.alloc(&bs, 1));
+        TRY(ar.alloc(&p1, (int64_t)PERSIST_MAX_BLOCKS * 2));
+        TRY(ar.alloc(&p2, (int64_t)PERSIST_MAX_BLOCKS));
+        TRY(ar.alloc(&bar, 1));
+        CU(cudaMemsetAsync(bs, 0, sizeof(BScal), p->stream));
+        CU(cudaMemsetAsync(bar, 0, sizeof(GridBar), p->stream));
+        p->pm_bs = bs;
+        p->pm_p1 = p1;
+        p->pm_p2 = p2;
+        p->pm_bar = bar;
+    }
+    BScal *bs = (BScal *)p->pm_bs;
+    auto hi = [&](double *v) { return (float *)v; };
+    auto lo = [&](double *v) { return (float *)v + n; };
+    double tol = p->sopts.mass_tol;
+    pdl_launch(kbd_norm<1>, dim3(vblocks(n)), dim3(TPB), 0, p->stream, n, b, bs, tol * tol, maxit, C.red.partials,
+               C.red.ticket);
+    LAUNCH_CHECK();
+    pdl_launch(kbd_start<1>, dim3(vblocks(n)), dim3(TPB), 0, p->stream, (int64_t)n, b, hi(C.mx), lo(C.mx), hi(C.mr),
+               lo(C.mr), (float *)C.mz, (const float *)C.mu_invdiag32, (const BScal *)bs);
+    LAUNCH_CHECK();
+    CU(cudaGetDevice(&dev));
+    CU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    MatView<float> A = bview<float>(a);
+    cudaError_t err = cudaSuccess;
+    if (!with_tpr(A.tpr, [&](auto t) {
+            constexpr int TPR = decltype(t)::value;
+            auto kern = kbp_mass_cg<TPR, 1>;
+            int per_sm = 0;
+            err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, TPB, 0);
+            if (err != cudaSuccess) return;
+            int64_t want = ceil_div((int64_t)n * TPR, TPB), grid = (int64_t)per_sm * sms;
+            if (grid > PERSIST_MAX_BLOCKS) grid = PERSIST_MAX_BLOCKS;
+            if (grid > want) grid = want;
+            if (grid < 1 || per_sm < 1) {
+                err = cudaErrorInvalidConfiguration;
+                return;
+            }
+            cudaLaunchConfig_t cfg = {};
+            cudaLaunchAttribute attr[1];
+            attr[0].id = cudaLaunchAttributeCooperative;
+            attr[0].val.cooperative = 1;
+            cfg.gridDim = dim3((unsigned)grid, 1, 1);
+            cfg.blockDim = dim3(TPB, 1, 1);
+            cfg.stream = p->stream;
+            cfg.attrs = attr;
+            cfg.numAttrs = 1;
+            err = cudaLaunchKernelEx(&cfg, kern, A, (const float *)a.lo32, (const float *)C.mu_invdiag32,
+                                     (float *)C.mz, hi(C.ms), lo(C.ms), hi(C.mp), lo(C.mp), hi(C.mq), lo(C.mq),
+                                     hi(C.mx), lo(C.mx), hi(C.mr), lo(C.mr), bs, (float2 *)p->pm_p1,
+                                     (float2 *)p->pm_p2, (GridBar *)p->pm_bar, maxit + 2);
+            amgh_count_launch();
+        }))
+        return AMGH_ERR_INVALID_ARG;
+    if (err != cudaSuccess) {
+        cudaGetLastError();
+        amgh_note_error((int)err, __FILE__, __LINE__);
+        return AMGH_ERR_CUDA;
+    }
+    pdl_launch(kbd_out<1>, dim3(vblocks(n)), dim3(TPB), 0, p->stream, (int64_t)n, (const float *)hi(C.mx),
+               (const float *)lo(C.mx), (const BScal *)bs, x);
+    LAUNCH_CHECK();
+    CgScal h;
+    CU(cudaMemcpyAsync(&h, &bs->c[0], sizeof(CgScal), cudaMemcpyDeviceToHost, p->stream));
+    TRY(sync_stream(p));
+    // algorithmic bytes: per iteration those of the graph-replayed pair (the
+    // double-float SpMV with its dots, the update with the Jacobi direction)
+    count_bytes((double)h.iters * (spmv_bytes(a, 4) + 4.0 * a.nnz + 12.0 * n + 84.0 * n) + 48.0 * n);
+    p->c_mass_lvl[l] += h.iters;
+    p->c_mass += h.iters;
+    if (iters) *iters = h.iters;
+    return AMGH_OK;
 }

@@ -313,6 +313,10 @@ struct amgh_problem {
     // work space, desired state, streams, graphs and counters
     const amgh_problem *parent = nullptr;
     cudaEvent_t wait_ev = nullptr; // blocking-sync event for host waits (else spin)
+    int in_batch = 0;              // run by the batch runtime beside other handles
+    // single-column persistent mass CG (persistent_cg): scalars, block
+    // partials and barrier of its cooperative launch, allocated on first use
+    void *pm_bs = nullptr, *pm_p1 = nullptr, *pm_p2 = nullptr, *pm_bar = nullptr;
     int dim = 0;
     int64_t nv = 0, ne = 0;
     double beta = 0.0;
@@ -436,6 +440,7 @@ int fused_vcycle(amgh_problem *p, const float *b, float *x, int preinit, const i
 // barrier of the fused V-cycle gave up
 int grid_timeout_check(amgh_problem *p);
 int block_grid_timeout_check(amgh_problem *p);
+int persistent_mass_single(amgh_problem *p, int l, const double *b, double *x, int64_t *iters);
 int block_set_grid_polls(int polls);
 int fused_set_grid_polls(int polls);
 // x = inv b with the FP32 copy (rows padded to ld, 16-byte aligned)

@@ -520,6 +520,8 @@ int mass_solve(amgh_problem *p, int l, const double *b, double *x, int64_t *iter
     int n = C.Mu.rows;
     // precision 2: the mass CG in double-float too, Jacobi from FP32 copies
     bool df = p->aopts.precision == 2;
+    if (df && p->aopts.persistent_cg && !p->parent && !p->in_batch && !p->capturing)
+        return persistent_mass_single(p, l, b, x, iters);
     if (df) {
         TRY(dfcg_start(p, C.red, n, b, C.mx, C.mr, C.mscal, p->sopts.mass_tol, p->sopts.mass_max_iter));
         TRY(dfcg_jacobi(p, n, C.mr, C.mu_invdiag32, (float *)C.mz));
