@@ -601,10 +601,12 @@ __global__ void k_restrict_first(MatView<T> St, const T *__restrict__ r, T *__re
     pdl_enter();
     SKIP_RETURN();
     int i = my_row<TPR>();
+    bool lead = i < St.rows && row_leader<TPR>();
+    T ir = lead ? invd[i] : (T)0;
     T b = row_sum<T, TPR>(St, i, [&](int c) { return __ldg(&r[c]); });
-    if (i < St.rows && row_leader<TPR>()) {
+    if (lead) {
         bc[i] = b;
-        T v = cheb_first_point(b, invd[i], c0);
+        T v = cheb_first_point(b, ir, c0);
         d[i] = v;
         x[i] = v;
     }
@@ -617,8 +619,10 @@ __global__ void k_prolong_add(MatView<T> S, const T *__restrict__ e, T *__restri
     pdl_enter();
     SKIP_RETURN();
     int i = my_row<TPR>();
+    bool lead = i < S.rows && row_leader<TPR>();
+    T xi = lead ? x[i] : (T)0;
     T v = row_sum<T, TPR>(S, i, [&](int c) { return __ldg(&e[c]); });
-    if (i < S.rows && row_leader<TPR>()) x[i] = radd(x[i], v);
+    if (lead) x[i] = radd(xi, v);
 }
 
 // x = inv b, one warp per row of the dense explicit inverse

@@ -38,10 +38,10 @@ inline MatView<float> view<float>(const DevCsr &a)
     return {a.rows, a.cols, a.tpr, a.wmax, 0, a.rp, a.ci, a.v32, nullptr};
 }
 
-// Rows of at most ROW_UNROLL entries per lane are read with all their value
-// and index loads issued first, then all gathers, then the sum in the same
-// order as the loop (so the result does not depend on the path): two memory
-// round trips per row instead of one per group of four entries.
+// A lane's entries of a row are read ROW_UNROLL at a time: all value and
+// index loads of the chunk first, then all its gathers, then the sum in entry
+// order (so the result does not depend on the chunking): two memory round
+// trips per chunk instead of one per entry or small group of entries.
 #define ROW_UNROLL 8
 
 // column of stored entry k of `row`
@@ -95,25 +95,25 @@ __device__ __forceinline__ T row_sum(const MatView<T> &m, int row, F xf)
     if (row < m.rows) {
         int k, end;
         lane_range<T, TPR>(m, row, k, end);
-        if (m.wmax <= ROW_UNROLL) {
+        auto chunk = [&](int k0) {
             T vv[ROW_UNROLL];
             int cc[ROW_UNROLL];
 #pragma unroll
             for (int j = 0; j < ROW_UNROLL; j++) {
-                bool ok = k + STEP * j < end;
-                vv[j] = ok ? m.v[k + STEP * j] : (T)0;
-                cc[j] = ok ? col_of(m, row, k + STEP * j) : 0;
+                bool ok = k0 + STEP * j < end;
+                vv[j] = ok ? m.v[k0 + STEP * j] : (T)0;
+                cc[j] = ok ? col_of(m, row, k0 + STEP * j) : 0;
             }
             T xv[ROW_UNROLL];
 #pragma unroll
-            for (int j = 0; j < ROW_UNROLL; j++) xv[j] = k + STEP * j < end ? xf(cc[j]) : (T)0;
+            for (int j = 0; j < ROW_UNROLL; j++) xv[j] = k0 + STEP * j < end ? xf(cc[j]) : (T)0;
 #pragma unroll
             for (int j = 0; j < ROW_UNROLL; j++)
-                if (k + STEP * j < end) acc += vv[j] * xv[j];
-        } else {
-#pragma unroll 4
-            for (; k < end; k += STEP) acc += m.v[k] * xf(col_of(m, row, k));
-        }
+                if (k0 + STEP * j < end) acc += vv[j] * xv[j];
+        };
+        if (m.wmax <= ROW_UNROLL) chunk(k);
+        else
+            for (; k < end; k += STEP * ROW_UNROLL) chunk(k);
     }
     if (TPR > 1) {
 #pragma unroll
@@ -146,26 +146,26 @@ __device__ __forceinline__ DF row_sum_df_acc(const MatView<float> &m, const floa
     if (row < m.rows) {
         int k, end;
         lane_range<float, TPR>(m, row, k, end);
-        if (m.wmax <= ROW_UNROLL) {
+        auto chunk = [&](int k0) {
             float vh[ROW_UNROLL], vl[ROW_UNROLL];
             int cc[ROW_UNROLL];
 #pragma unroll
             for (int j = 0; j < ROW_UNROLL; j++) {
-                bool ok = k + STEP * j < end;
-                vh[j] = ok ? m.v[k + STEP * j] : 0.f;
-                vl[j] = ok ? lo[k + STEP * j] : 0.f;
-                cc[j] = ok ? col_of(m, row, k + STEP * j) : 0;
+                bool ok = k0 + STEP * j < end;
+                vh[j] = ok ? m.v[k0 + STEP * j] : 0.f;
+                vl[j] = ok ? lo[k0 + STEP * j] : 0.f;
+                cc[j] = ok ? col_of(m, row, k0 + STEP * j) : 0;
             }
             Z zv[ROW_UNROLL];
 #pragma unroll
-            for (int j = 0; j < ROW_UNROLL; j++) zv[j] = k + STEP * j < end ? __ldg(&z[cc[j]]) : (Z)0;
+            for (int j = 0; j < ROW_UNROLL; j++) zv[j] = k0 + STEP * j < end ? __ldg(&z[cc[j]]) : (Z)0;
 #pragma unroll
             for (int j = 0; j < ROW_UNROLL; j++)
-                if (k + STEP * j < end) df_term<Z>(acc, vh[j], vl[j], zv[j]);
-        } else {
-#pragma unroll 4
-            for (; k < end; k += STEP) df_term<Z>(acc, m.v[k], lo[k], __ldg(&z[col_of(m, row, k)]));
-        }
+                if (k0 + STEP * j < end) df_term<Z>(acc, vh[j], vl[j], zv[j]);
+        };
+        if (m.wmax <= ROW_UNROLL) chunk(k);
+        else
+            for (; k < end; k += STEP * ROW_UNROLL) chunk(k);
     }
     if (TPR > 1) {
 #pragma unroll
