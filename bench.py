@@ -566,11 +566,7 @@ def kernel_table(classes):
 
 def roofline_from(res, args, kernel_note=None, traffic="captured"):
     ks = res["kstats"]
-    peaks = measured_peaks()
-    if peaks and peaks.get("hbm_gbs"):
-        peak, src = float(peaks["hbm_gbs"]), "measured"
-    else:
-        peak, src = 6800.0, "fallback"
+    peak, src = hbm_peak()
     if ks["launches"] == 0 or ks["ms"] <= 0:
         return None
     achieved = ks["bytes"] / (ks["ms"] / 1000.0) / 1e9
