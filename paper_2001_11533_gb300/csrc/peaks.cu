@@ -60,23 +60,27 @@ extern "C" int amgh_fp64_peak(int kind, void *stream, double *tflops)
     Scratch sc;
     double *out = nullptr;
     TRY(sc.alloc(&out, (int64_t)blocks * threads));
-    cudaEvent_t e0 = nullptr, e1 = nullptr;
-    CU(cudaEventCreate(&e0));
-    CU(cudaEventCreate(&e1));
     auto launch = [&]() {
         if (kind == 0) k_peak_dfma<<<blocks, threads, 0, s>>>(out, iters, 0.9999999);
         else k_peak_dmma<<<blocks, threads, 0, s>>>(out, iters);
+        return cudaGetLastError();
     };
-    launch(); // warm-up
-    cudaEventRecord(e0, s);
-    launch();
-    cudaEventRecord(e1, s);
-    cudaError_t err = cudaEventSynchronize(e1);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
     float ms = 0.f;
+    cudaError_t err = cudaEventCreate(&e0);
+    if (err == cudaSuccess) err = cudaEventCreate(&e1);
+    if (err == cudaSuccess) err = launch(); // warm-up
+    if (err == cudaSuccess) err = cudaEventRecord(e0, s);
+    if (err == cudaSuccess) err = launch();
+    if (err == cudaSuccess) err = cudaEventRecord(e1, s);
+    if (err == cudaSuccess) err = cudaEventSynchronize(e1);
     if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    if (err != cudaSuccess) return AMGH_ERR_CUDA;
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (err != cudaSuccess) {
+        amgh_note_error((int)err, __FILE__, __LINE__);
+        return AMGH_ERR_CUDA;
+    }
     double flops = kind == 0 ? 2.0 * 8 * iters * (double)blocks * threads
                              : 512.0 * 4 * iters * (double)blocks * (threads / 32);
     *tflops = ms > 0.f ? flops / (ms * 1e-3) * 1e-12 : 0.0;
