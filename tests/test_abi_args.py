@@ -71,3 +71,23 @@ def test_defaults_and_status_strings():
         assert amgh.lib().amgh_status_string(code)
     with pytest.raises(TypeError):
         amgh.amg_opts(no_such_field=1)
+
+
+def test_dense_probe_and_debug_entry_points_reject_bad_arguments():
+    """The dense inverse, the FP64 rate probe and the grid-barrier test hook check
+    their arguments before touching the device (n in 1..4096, non-null buffers,
+    kind 0 or 1, a poll limit of -1 or more)."""
+    L = amgh.lib()
+    buf = np.zeros(4, dtype=np.float64)
+    p = C.c_void_p(buf.ctypes.data)
+    info = C.c_int32(7)
+    for n, a, inv in [(0, p, p), (-3, p, p), (4097, p, p), (2, None, p), (2, p, None)]:
+        info.value = 7
+        assert L.amgh_dense_spd_inverse(n, a, inv, None, C.byref(info)) == -1
+        assert info.value == 0  # info is cleared even when the call is refused
+    assert L.amgh_dense_spd_inverse(0, p, p, None, None) == -1
+    t = C.c_double(5.0)
+    assert L.amgh_fp64_peak(2, None, C.byref(t)) == -1
+    assert L.amgh_fp64_peak(-1, None, C.byref(t)) == -1
+    assert L.amgh_fp64_peak(0, None, None) == -1
+    assert L.amgh_debug_grid_polls(-2) == -1
