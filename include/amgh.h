@@ -123,14 +123,16 @@ typedef struct {
  *                  of FP32 V-cycles apply the stiffness matrix-free from the
  *                  element coefficients instead of reading the assembled
  *                  matrix; same operator, different rounding
- *  persistent_cg   1 = the block solver's mass CGs (precisions 1 and 2) run
- *                  all their iterations in one cooperative launch over the
- *                  GPU (grid-stride rows, two bounded software grid barriers
- *                  per iteration; a barrier that gives up makes the call
- *                  return AMGH_ERR_TIMEOUT) instead of graph-replayed
- *                  kernels; handles from amgh_problem_share use 0.  Same
- *                  arithmetic per row, sums grouped differently: results
- *                  agree with 0 to the CG tolerance, not to the bit */
+ *  persistent_cg   1 = the block solver's mass CGs (precisions 1 and 2), and
+ *                  the single-column mass CGs of precision 2, run all their
+ *                  iterations in one cooperative launch over the GPU
+ *                  (grid-stride rows, two bounded software grid barriers per
+ *                  iteration; a barrier that gives up makes the call return
+ *                  AMGH_ERR_TIMEOUT) instead of graph-replayed kernels;
+ *                  handles from amgh_problem_share and the batch runtime's
+ *                  handles use 0.  Same arithmetic per row, sums grouped
+ *                  differently: results agree with 0 to the CG tolerance, not
+ *                  to the bit */
 typedef struct {
     int max_levels;
     int hessian_levels;
